@@ -1,0 +1,436 @@
+// Layout, operator views, renormalization and H_eff task lists.
+#include "core.hpp"
+
+#include <algorithm>
+#include <cmath>
+#include <stdexcept>
+#include <tuple>
+
+namespace qd {
+
+const QN SITE_QN[NSITE] = {{0, 0}, {1, 1}, {1, -1}, {2, 0}};
+
+void Basis::add(QN qq, int d) {
+  if (!q.empty() && !(q.back() < qq)) throw std::runtime_error("Basis::add: labels must increase");
+  idx[qq] = (int)q.size();
+  q.push_back(qq);
+  dim.push_back(d);
+}
+
+int64_t Basis::total() const {
+  int64_t t = 0;
+  for (int d : dim) t += d;
+  return t;
+}
+
+QN ProdBasis::sub_qn(int s) const { return prod.q[subs[s].prod]; }
+int ProdBasis::blk_parity(int s) const { return (blk->q[subs[s].blk].n & 1) ? -1 : 1; }
+int ProdBasis::site_parity(int s) const { return (SITE_QN[subs[s].st].n & 1) ? -1 : 1; }
+
+ProdBasis make_prod(const Basis& blk, bool left) {
+  ProdBasis pb;
+  pb.left = left;
+  pb.blk = &blk;
+  std::vector<std::tuple<QN, int, int, int>> items;  // label, first, second, (blk, st)
+  for (int b = 0; b < blk.nsec(); ++b)
+    for (int st = 0; st < NSITE; ++st) {
+      QN q = blk.q[b] + SITE_QN[st];
+      if (left) items.emplace_back(q, b, st, 0);
+      else items.emplace_back(q, st, b, 0);
+    }
+  std::sort(items.begin(), items.end(), [](const auto& a, const auto& b) {
+    if (std::get<0>(a) != std::get<0>(b)) return std::get<0>(a) < std::get<0>(b);
+    if (std::get<1>(a) != std::get<1>(b)) return std::get<1>(a) < std::get<1>(b);
+    return std::get<2>(a) < std::get<2>(b);
+  });
+  pb.subidx.assign(blk.nsec() * NSITE, -1);
+  for (auto& it : items) {
+    QN q = std::get<0>(it);
+    int b = left ? std::get<1>(it) : std::get<2>(it);
+    int st = left ? std::get<2>(it) : std::get<1>(it);
+    int p = pb.prod.find(q);
+    if (p < 0) {
+      pb.prod.add(q, 0);
+      p = pb.prod.nsec() - 1;
+      pb.prod_subs.emplace_back();
+    }
+    Sub s;
+    s.blk = b;
+    s.st = st;
+    s.prod = p;
+    s.off = pb.prod.dim[p];
+    s.dim = blk.dim[b];
+    pb.prod.dim[p] += s.dim;
+    pb.subidx[b * NSITE + st] = (int)pb.subs.size();
+    pb.prod_subs[p].push_back((int)pb.subs.size());
+    pb.subs.push_back(s);
+  }
+  return pb;
+}
+
+OpView transpose(const OpView& o) {
+  OpView t;
+  t.odd = o.odd;
+  t.blocks.reserve(o.blocks.size());
+  for (const BRef& b : o.blocks) {
+    BRef x = b;
+    std::swap(x.r, x.c);
+    std::swap(x.rows, x.cols);
+    x.tr = !b.tr;
+    t.blocks.push_back(x);
+  }
+  return t;
+}
+
+double Integrals::t(int k, int l) const {
+  if ((k & 1) != (l & 1)) return 0.0;
+  return h[(k >> 1) * L + (l >> 1)];
+}
+
+double Integrals::w(int i, int j, int k, int l) const {
+  // w_ijkl = (p_i p_l | p_j p_k) d(s_i, s_l) d(s_j, s_k)
+  if ((i & 1) != (l & 1) || (j & 1) != (k & 1)) return 0.0;
+  int64_t pi = i >> 1, pj = j >> 1, pk = k >> 1, pl = l >> 1;
+  return V[((pi * L + pl) * L + pj) * L + pk];
+}
+
+Mat4 Mat4::id() {
+  Mat4 m;
+  for (int i = 0; i < 4; ++i) m(i, i) = 1.0;
+  return m;
+}
+Mat4 Mat4::operator*(const Mat4& o) const {
+  Mat4 r;
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      double s = 0;
+      for (int k = 0; k < 4; ++k) s += (*this)(i, k) * o(k, j);
+      r(i, j) = s;
+    }
+  return r;
+}
+Mat4 Mat4::operator+(const Mat4& o) const {
+  Mat4 r;
+  for (int i = 0; i < 16; ++i) r.v[i] = v[i] + o.v[i];
+  return r;
+}
+Mat4 Mat4::operator*(double s) const {
+  Mat4 r;
+  for (int i = 0; i < 16; ++i) r.v[i] = v[i] * s;
+  return r;
+}
+Mat4 Mat4::T() const {
+  Mat4 r;
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) r(i, j) = (*this)(j, i);
+  return r;
+}
+bool Mat4::zero() const {
+  for (double x : v)
+    if (x != 0.0) return false;
+  return true;
+}
+
+Mat4 cre(int sigma) {
+  Mat4 m;
+  if (sigma == 0) {
+    m(1, 0) = 1.0;   // a+_up |0> = |up>
+    m(3, 2) = 1.0;   // a+_up |dn> = |updn>
+  } else {
+    m(2, 0) = 1.0;   // a+_dn |0> = |dn>
+    m(3, 1) = -1.0;  // a+_dn |up> = -|updn>
+  }
+  return m;
+}
+Mat4 ann(int sigma) { return cre(sigma).T(); }
+
+// ---------------------------------------------------------------------------
+// Renormalization: O_new = U^T O U (left) or V O V^T (right), two stages.
+// ---------------------------------------------------------------------------
+void renormalize(const Enlarged& E, const Basis& nb, const std::vector<int>& nb_of_prod,
+                 uint64_t tensor, const std::vector<int64_t>& toff, Executor& ex,
+                 EnvBlock& out, int64_t tmp_budget, double* flops) {
+  const ProdBasis& pb = E.pb;
+  const bool left = E.left;
+  out.left = left;
+  out.basis = nb;
+  out.ops.clear();
+  // storage plan: every output block is allocated in one buffer
+  struct OutBlk { int nq, nq2; int64_t off; };
+  std::map<Key, std::map<std::pair<int, int>, int64_t>> layout;
+  int64_t total = 0;
+  for (auto& kv : E.ops) {
+    auto& lay = layout[kv.first];
+    for (const BRef& b : kv.second.blocks) {
+      int q = pb.subs[b.r].prod, q2 = pb.subs[b.c].prod;
+      int nq = nb_of_prod[q], nq2 = nb_of_prod[q2];
+      if (nq < 0 || nq2 < 0) continue;
+      auto key = std::make_pair(nq, nq2);
+      if (!lay.count(key)) {
+        lay[key] = total;
+        total += (int64_t)nb.dim[nq] * nb.dim[nq2];
+      }
+    }
+  }
+  uint64_t store = total ? ex.alloc(total) : 0;
+  if (store) out.owned.push_back(store);
+  auto sub_ptr = [&](int s) -> uint64_t {
+    const Sub& S = pb.subs[s];
+    int nq = nb_of_prod[S.prod];
+    if (left) return tensor + 8ull * (toff[S.prod] + (int64_t)S.off * nb.dim[nq]);
+    return tensor + 8ull * (toff[S.prod] + S.off);
+  };
+  Launch s1, s2;
+  int64_t tused = 0;
+  double fl = 0;
+  auto flush = [&]() {
+    if (s1.empty() && s2.empty()) return;
+    if (tused) ex.tmp(tused);
+    if (!s1.empty()) ex.run(s1, 0, 0);
+    if (!s2.empty()) ex.run(s2, 0, 0);
+    fl += s1.flops + s2.flops;
+    s1.clear();
+    s2.clear();
+    tused = 0;
+  };
+  for (auto& kv : E.ops) {
+    const OpView& op = kv.second;
+    auto& lay = layout[kv.first];
+    OpView nv;
+    nv.odd = op.odd;
+    // count scratch of this op
+    int64_t need = 0;
+    for (const BRef& b : op.blocks) {
+      int nq2 = nb_of_prod[pb.subs[b.c].prod];
+      if (nq2 < 0 || nb_of_prod[pb.subs[b.r].prod] < 0 || b.ident()) continue;
+      need += (int64_t)b.rows * nb.dim[nq2];
+    }
+    if (tused && tused + need > tmp_budget) flush();
+    std::map<std::pair<int, int>, std::vector<Seg>> segs;
+    for (const BRef& b : op.blocks) {
+      const Sub& Sr = pb.subs[b.r];
+      const Sub& Sc = pb.subs[b.c];
+      int nq = nb_of_prod[Sr.prod], nq2 = nb_of_prod[Sc.prod];
+      if (nq < 0 || nq2 < 0) continue;
+      int dq = nb.dim[nq], dq2 = nb.dim[nq2];
+      int pq = pb.prod.dim[Sr.prod], pq2 = pb.prod.dim[Sc.prod];
+      Seg g;
+      g.sc = b.sc;
+      g.k = Sr.dim;
+      if (left) {  // U_r^T (op U_c)
+        g.a = sub_ptr(b.r); g.abuf = B_ABS; g.lda = dq; g.ta = 1;
+      } else {     // V_r (op V_c^T)
+        g.a = sub_ptr(b.r); g.abuf = B_ABS; g.lda = pq; g.ta = 0;
+      }
+      if (b.ident()) {
+        if (left) { g.b = sub_ptr(b.c); g.bbuf = B_ABS; g.ldb = dq2; g.tb = 0; }
+        else { g.b = sub_ptr(b.c); g.bbuf = B_ABS; g.ldb = pq2; g.tb = 1; }
+      } else {
+        Prob p;
+        p.c = (uint64_t)tused; p.cbuf = B_TMP;
+        p.m = b.rows; p.n = dq2; p.ldc = dq2; p.beta = 0;
+        p.seg0 = (int)s1.segs.size(); p.nseg = 1;
+        Seg h;
+        h.a = b.ptr; h.abuf = B_ABS; h.lda = b.ld; h.ta = b.tr ? 1 : 0;
+        h.b = sub_ptr(b.c); h.bbuf = B_ABS; h.k = b.cols;
+        if (left) { h.ldb = dq2; h.tb = 0; } else { h.ldb = pq2; h.tb = 1; }
+        s1.segs.push_back(h);
+        s1.probs.push_back(p);
+        s1.flops += 2.0 * p.m * p.n * h.k;
+        g.b = (uint64_t)tused; g.bbuf = B_TMP; g.ldb = dq2; g.tb = 0;
+        tused += (int64_t)b.rows * dq2;
+      }
+      segs[{nq, nq2}].push_back(g);
+      s2.flops += 2.0 * dq * dq2 * g.k;
+    }
+    for (auto& sv : segs) {
+      int nq = sv.first.first, nq2 = sv.first.second;
+      Prob p;
+      p.c = store + 8ull * lay[sv.first]; p.cbuf = B_ABS;
+      p.m = nb.dim[nq]; p.n = nb.dim[nq2]; p.ldc = p.n; p.beta = 0;
+      p.seg0 = (int)s2.segs.size(); p.nseg = (int)sv.second.size();
+      for (auto& g : sv.second) s2.segs.push_back(g);
+      s2.probs.push_back(p);
+      BRef r;
+      r.r = nq; r.c = nq2; r.ptr = p.c; r.rows = p.m; r.cols = p.n; r.ld = p.n; r.tr = false; r.sc = 1.0;
+      nv.blocks.push_back(r);
+    }
+    out.ops[kv.first] = nv;
+  }
+  flush();
+  if (flops) *flops += fl;
+}
+
+// ---------------------------------------------------------------------------
+// Two-site wavefunction layout and H_eff psi plan.
+// ---------------------------------------------------------------------------
+PsiLayout make_psi_layout(const ProdBasis& Lp, const ProdBasis& Rp, QN target) {
+  PsiLayout lay;
+  const Basis& X = *Lp.blk;
+  const Basis& Y = *Rp.blk;
+  for (int x = 0; x < X.nsec(); ++x)
+    for (int i = 0; i < NSITE; ++i)
+      for (int j = 0; j < NSITE; ++j)
+        for (int y = 0; y < Y.nsec(); ++y) {
+          QN t = X.q[x] + SITE_QN[i] + SITE_QN[j] + Y.q[y];
+          if (t != target) continue;
+          PsiLayout::Blk b;
+          b.x = x; b.i = i; b.j = j; b.y = y;
+          b.lsub = Lp.find(x, i);
+          b.rsub = Rp.find(y, j);
+          b.rows = X.dim[x];
+          b.cols = Y.dim[y];
+          b.off = lay.size;
+          lay.size += (int64_t)b.rows * b.cols;
+          lay.by_sub[{b.lsub, b.rsub}] = (int)lay.blks.size();
+          lay.blks.push_back(b);
+        }
+  return lay;
+}
+
+namespace {
+struct Term {
+  const OpView* L;
+  bool LT;
+  const OpView* R;
+  bool RT;
+  double coef;
+};
+}  // namespace
+
+HeffPlan plan_heff(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay,
+                   const Integrals& I, int64_t tmp_budget) {
+  HeffPlan plan;
+  const int c = Lp.cut;  // L' = [0, c), R' = [c, L)
+  const int L = I.L;
+  std::vector<Term> terms;
+  auto get = [](const Enlarged& E, Key k) -> const OpView* {
+    auto it = E.ops.find(k);
+    if (it == E.ops.end() || it->second.empty()) return nullptr;
+    return &it->second;
+  };
+  const OpView* IL = get(Lp, Key(F_I));
+  const OpView* IR = get(Rp, Key(F_I));
+  // H = H_L' + H_R' + e_core
+  if (auto h = get(Lp, Key(F_H))) terms.push_back({h, false, IR, false, 1.0});
+  if (auto h = get(Rp, Key(F_H))) terms.push_back({IL, false, h, false, 1.0});
+  if (I.ecore != 0.0) terms.push_back({IL, false, IR, false, I.ecore});
+  // sum_{i in L'} ( a+_i S^R_i - a_i (S^R_i)^+ )
+  for (int i = 0; i < 2 * c; ++i) {
+    auto C = get(Lp, Key(F_C, i));
+    auto S = get(Rp, Key(F_S, i));
+    if (!C || !S) continue;
+    terms.push_back({C, false, S, false, 1.0});
+    terms.push_back({C, true, S, true, -1.0});
+  }
+  // sum_{m in R'} ( -S^L_m a+_m + (S^L_m)^+ a_m )
+  for (int m = 2 * c; m < 2 * L; ++m) {
+    auto S = get(Lp, Key(F_S, m));
+    auto C = get(Rp, Key(F_C, m));
+    if (!C || !S) continue;
+    terms.push_back({S, false, C, false, -1.0});
+    terms.push_back({S, true, C, true, 1.0});
+  }
+  // 2 sum_{i<j} (A_ij P_ij + A_ij^+ P_ij^+) + sum_{il} B_il Q_il
+  for (int i = 0; i < 2 * c; ++i)
+    for (int j = i + 1; j < 2 * c; ++j) {
+      auto A = get(Lp, Key(F_A, i, j));
+      auto P = get(Rp, Key(F_P, i, j));
+      if (!A || !P) continue;
+      terms.push_back({A, false, P, false, 2.0});
+      terms.push_back({A, true, P, true, 2.0});
+    }
+  for (int i = 0; i < 2 * c; ++i)
+    for (int l = 0; l < 2 * c; ++l) {
+      auto B = get(Lp, Key(F_B, i, l));
+      auto Q = get(Rp, Key(F_Q, i, l));
+      if (!B || !Q) continue;
+      terms.push_back({B, false, Q, false, 1.0});
+    }
+  plan.nterms = (int)terms.size();
+
+  const ProdBasis& LB = Lp.pb;
+  Launch s1, s2;
+  std::map<int, std::vector<Seg>> out;  // psi block -> segments
+  int64_t tused = 0;
+  auto flush = [&]() {
+    if (out.empty() && s1.empty()) return;
+    for (auto& kv : out) {
+      const auto& pbk = lay.blks[kv.first];
+      Prob p;
+      p.c = (uint64_t)pbk.off; p.cbuf = B_SIG;
+      p.m = pbk.rows; p.n = pbk.cols; p.ldc = pbk.cols; p.beta = 1;
+      p.seg0 = (int)s2.segs.size(); p.nseg = (int)kv.second.size();
+      for (auto& g : kv.second) s2.segs.push_back(g);
+      s2.probs.push_back(p);
+    }
+    plan.flops += s1.flops + s2.flops;
+    plan.stage1.push_back(s1);
+    plan.stage2.push_back(s2);
+    plan.tmp_elems = std::max(plan.tmp_elems, tused);
+    s1.clear();
+    s2.clear();
+    out.clear();
+    tused = 0;
+  };
+  for (const Term& t : terms) {
+    OpView Lv = t.LT ? transpose(*t.L) : *t.L;
+    OpView Rv = t.RT ? transpose(*t.R) : *t.R;
+    std::map<int, std::vector<const BRef*>> lby;  // col sub -> blocks
+    for (const BRef& b : Lv.blocks) lby[b.c].push_back(&b);
+    int64_t need = 0;
+    for (const BRef& bR : Rv.blocks) {
+      if (bR.ident()) continue;
+      for (auto& kv : lby) {
+        auto it = lay.by_sub.find({kv.first, bR.c});
+        if (it != lay.by_sub.end()) need += (int64_t)lay.blks[it->second].rows * bR.rows;
+      }
+    }
+    if (tused && tused + need > tmp_budget) flush();
+    for (const BRef& bR : Rv.blocks) {
+      for (auto& kv : lby) {
+        int cL = kv.first;
+        auto it = lay.by_sub.find({cL, bR.c});
+        if (it == lay.by_sub.end()) continue;
+        const auto& pin = lay.blks[it->second];
+        uint64_t Tb;
+        int Tbuf, ldT = bR.rows;
+        if (bR.ident()) {
+          Tb = (uint64_t)pin.off; Tbuf = B_PSI; ldT = pin.cols;
+        } else {
+          Prob p;
+          p.c = (uint64_t)tused; p.cbuf = B_TMP;
+          p.m = pin.rows; p.n = bR.rows; p.ldc = bR.rows; p.beta = 0;
+          p.seg0 = (int)s1.segs.size(); p.nseg = 1;
+          Seg h;
+          h.a = (uint64_t)pin.off; h.abuf = B_PSI; h.lda = pin.cols; h.ta = 0;
+          h.b = bR.ptr; h.bbuf = B_ABS; h.ldb = bR.ld; h.tb = bR.tr ? 0 : 1;
+          h.k = bR.cols;
+          s1.segs.push_back(h);
+          s1.probs.push_back(p);
+          s1.flops += 2.0 * p.m * p.n * h.k;
+          Tb = (uint64_t)tused; Tbuf = B_TMP;
+          tused += (int64_t)p.m * p.n;
+        }
+        int par = 1;
+        if (Rv.odd) par = (LB.prod.q[LB.subs[cL].prod].n & 1) ? -1 : 1;
+        for (const BRef* bL : kv.second) {
+          auto ot = lay.by_sub.find({bL->r, bR.r});
+          if (ot == lay.by_sub.end()) continue;
+          Seg g;
+          if (bL->ident()) { g.a = 0; g.abuf = B_ABS; g.lda = 0; g.ta = 0; }
+          else { g.a = bL->ptr; g.abuf = B_ABS; g.lda = bL->ld; g.ta = bL->tr ? 1 : 0; }
+          g.b = Tb; g.bbuf = Tbuf; g.ldb = ldT; g.tb = 0;
+          g.k = bL->cols;
+          g.sc = t.coef * bL->sc * bR.sc * par;
+          out[ot->second].push_back(g);
+          if (!bL->ident()) s2.flops += 2.0 * bL->rows * bR.rows * (double)bL->cols;
+        }
+      }
+    }
+  }
+  flush();
+  return plan;
+}
+
+}  // namespace qd

@@ -1,0 +1,223 @@
+// Host-side core of the two-site DMRG hot path: quantum-number layout,
+// operator views, complementary-operator rules and segmented-GEMM task lists.
+//
+// The renormalized-operator formulation is the quantum-chemical DMRG of the
+// paper's Method section (memory O(N^2 D^2), compute O(N^4 D^3)): normal
+// operators a+_k, a+_k a+_l, a+_k a_l of a block and complementary operators
+// S_m, P_ij, Q_il and the block Hamiltonian, built from h_pq and V_pqrs. The
+// paper gives no formulas of its own; the ones used are written out next to
+// each rule in rules.cpp.
+#pragma once
+#include <cstdint>
+#include <map>
+#include <string>
+#include <vector>
+
+namespace qd {
+
+struct QN {
+  int n = 0, s = 0;  // particle number, 2Sz
+  bool operator<(const QN& o) const { return n != o.n ? n < o.n : s < o.s; }
+  bool operator==(const QN& o) const { return n == o.n && s == o.s; }
+  bool operator!=(const QN& o) const { return !(*this == o); }
+  QN operator+(const QN& o) const { return {n + o.n, s + o.s}; }
+  QN operator-(const QN& o) const { return {n - o.n, s - o.s}; }
+};
+
+// Site basis: 0 = |0>, 1 = a+_up|0>, 2 = a+_dn|0>, 3 = a+_up a+_dn|0>.
+constexpr int NSITE = 4;
+extern const QN SITE_QN[NSITE];
+
+// Sectors of a block basis, sorted by label.
+struct Basis {
+  std::vector<QN> q;
+  std::vector<int> dim;
+  std::map<QN, int> idx;
+  void add(QN qq, int d);   // call with increasing labels
+  int find(QN qq) const {
+    auto it = idx.find(qq);
+    return it == idx.end() ? -1 : it->second;
+  }
+  int nsec() const { return (int)q.size(); }
+  int64_t total() const;
+};
+
+// Enlarged basis of a block and one site. Left: X (x) site, sub-block (x, i).
+// Right: site (x) Y, sub-block (j, y). Product sectors group the sub-blocks;
+// inside a product sector sub-blocks follow (x, i) (left) or (j, y) (right).
+struct Sub {
+  int blk, st;   // block sector, site state
+  int prod;      // product sector id
+  int off;       // row offset inside the product sector
+  int dim;
+};
+struct ProdBasis {
+  bool left = true;
+  const Basis* blk = nullptr;
+  std::vector<Sub> subs;
+  Basis prod;
+  std::vector<std::vector<int>> prod_subs;  // sub ids of each product sector
+  std::vector<int> subidx;                  // blk * NSITE + st -> sub id
+  int find(int b, int st) const { return subidx[b * NSITE + st]; }
+  int nsub() const { return (int)subs.size(); }
+  QN sub_qn(int s) const;
+  int blk_parity(int s) const;   // (-1)^n of the block part
+  int site_parity(int s) const;  // (-1)^n of the site part
+};
+ProdBasis make_prod(const Basis& blk, bool left);
+
+// Reference to one dense block of an operator. ptr == 0: identity block.
+struct BRef {
+  int r = 0, c = 0;        // row / column sector (or sub-block) ids
+  uint64_t ptr = 0;        // device address of the stored block
+  int rows = 0, cols = 0;  // logical shape
+  int ld = 0;              // leading dimension of the stored block
+  bool tr = false;         // logical block = stored^T
+  double sc = 1.0;
+  bool ident() const { return ptr == 0; }
+};
+struct OpView {
+  bool odd = false;
+  std::vector<BRef> blocks;
+  bool empty() const { return blocks.empty(); }
+};
+OpView transpose(const OpView& o);
+
+// Operator keys.
+enum Fam : int { F_I = 0, F_C, F_A, F_B, F_S, F_P, F_Q, F_H };
+struct Key {
+  int f, a, b;
+  Key(int f_ = 0, int a_ = -1, int b_ = -1) : f(f_), a(a_), b(b_) {}
+  bool operator<(const Key& o) const {
+    if (f != o.f) return f < o.f;
+    if (a != o.a) return a < o.a;
+    return b < o.b;
+  }
+};
+
+// Segmented GEMM task lists. Address fields name a buffer (0 = absolute
+// device address, 1 = psi, 2 = sigma, 3 = scratch) plus an element offset,
+// so that one list can be replayed on any psi / sigma.
+enum Buf : int { B_ABS = 0, B_PSI = 1, B_SIG = 2, B_TMP = 3 };
+struct Seg {
+  uint64_t a = 0, b = 0;   // a == 0 && abuf == 0: A is the identity
+  int abuf = 0, bbuf = 0;  // b == 0 && bbuf == 0: B is the identity too
+  int lda = 0, ldb = 0, k = 0;
+  int ta = 0, tb = 0;
+  double sc = 1.0;
+};
+struct Prob {
+  uint64_t c = 0;
+  int cbuf = 0;
+  int m = 0, n = 0, ldc = 0;
+  int beta = 0;             // 1: accumulate into C
+  int seg0 = 0, nseg = 0;
+};
+struct Launch {
+  std::vector<Prob> probs;
+  std::vector<Seg> segs;
+  double flops = 0;         // algorithmic 2mnk over GEMM segments
+  void clear() { probs.clear(); segs.clear(); flops = 0; }
+  bool empty() const { return probs.empty(); }
+};
+
+// Memory and execution backend.
+struct Executor {
+  virtual ~Executor() {}
+  virtual uint64_t alloc(int64_t nelem) = 0;          // zero-initialised doubles
+  virtual void release(uint64_t p) = 0;
+  virtual uint64_t tmp(int64_t nelem) = 0;            // scratch buffer base (grows)
+  virtual void run(const Launch& l, uint64_t psi, uint64_t sig) = 0;
+  virtual void upload(uint64_t dst, const double* h, int64_t n) = 0;
+  virtual void download(double* h, uint64_t src, int64_t n) = 0;
+  virtual void zero(uint64_t p, int64_t n) = 0;
+};
+
+// Integrals; spin-orbital form t_kl, w_ijkl with k = 2p + sigma.
+struct Integrals {
+  int L = 0;
+  std::vector<double> h, V;
+  double ecore = 0;
+  double t(int k, int l) const;
+  double w(int i, int j, int k, int l) const;
+  double q(int i, int j, int k, int l) const { return w(i, j, k, l) - w(i, j, l, k); }
+};
+
+struct Mat4 {
+  double v[16];
+  Mat4() { for (double& x : v) x = 0; }
+  static Mat4 id();
+  double& operator()(int i, int j) { return v[i * 4 + j]; }
+  double operator()(int i, int j) const { return v[i * 4 + j]; }
+  Mat4 operator*(const Mat4& o) const;
+  Mat4 operator+(const Mat4& o) const;
+  Mat4 operator*(double s) const;
+  Mat4 T() const;
+  bool zero() const;
+};
+Mat4 cre(int sigma);
+Mat4 ann(int sigma);
+
+// One term of an enlarged operator:
+//   left  (L' = X (x) s): coef * (O_X P_X^par) (x) o
+//   right (R' = s (x) Y): coef * (o P_s^par)   (x) O_Y
+// src == nullptr: O is the block identity.
+struct Contrib {
+  const OpView* src = nullptr;
+  bool srcT = false;
+  Mat4 o;
+  double coef = 1.0;
+  bool par = false;
+};
+
+// Enlarged block: product basis and the views of its operators.
+struct Enlarged {
+  bool left = true;
+  int cut = 0;              // the enlarged block covers [0, cut) or [cut, L)
+  ProdBasis pb;
+  std::map<Key, OpView> ops;
+  std::vector<uint64_t> owned;   // materialized storage
+};
+
+// Renormalized block. Left block at cut c: sites [0, c); right: [c, L).
+struct EnvBlock {
+  bool left = true;
+  int cut = 0;
+  Basis basis;
+  std::map<Key, OpView> ops;
+  std::vector<uint64_t> owned;
+};
+
+// Op-key list of a block at a cut (left-normal / right-complementary layout).
+std::vector<Key> block_keys(bool left, int cut, int L);
+
+// Build the enlarged views from a renormalized block and one site.
+void enlarge(const EnvBlock& B, const Integrals& I, Executor& ex, Enlarged& out, double* flops);
+
+// Renormalize enlarged operators with the new site tensor: for each product
+// sector that is kept, a dense matrix (left: [dim_prod x d_new], right:
+// [d_new x dim_prod]) at device address tensor + off[prod sector].
+void renormalize(const Enlarged& E, const Basis& nb, const std::vector<int>& nb_of_prod,
+                 uint64_t tensor, const std::vector<int64_t>& tensor_off, Executor& ex,
+                 EnvBlock& out, int64_t tmp_budget, double* flops);
+
+// Two-site wavefunction layout: sub-blocks (x, i, j, y), sorted, row-major.
+struct PsiLayout {
+  struct Blk { int x, i, j, y, lsub, rsub; int64_t off; int rows, cols; };
+  std::vector<Blk> blks;
+  std::map<std::pair<int, int>, int> by_sub;   // (lsub, rsub) -> index
+  int64_t size = 0;
+};
+PsiLayout make_psi_layout(const ProdBasis& Lp, const ProdBasis& Rp, QN target);
+
+// H_eff psi task lists (chunks of stage-1 / stage-2 launches).
+struct HeffPlan {
+  std::vector<Launch> stage1, stage2;
+  double flops = 0;
+  int64_t tmp_elems = 0;
+  int nterms = 0;
+};
+HeffPlan plan_heff(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay,
+                   const Integrals& I, int64_t tmp_budget);
+
+}  // namespace qd
