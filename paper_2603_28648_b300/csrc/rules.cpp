@@ -1,0 +1,434 @@
+// Complementary-operator rules: how the operators of an enlarged block
+// (block (x) site) are written in terms of the block's renormalized operators
+// and exact single-site matrices.
+//
+// Spin-orbital form of the active-space Hamiltonian (k = 2p + sigma):
+//   H = sum t_kl a+_k a_l + 1/2 sum w_ijkl a+_i a+_j a_k a_l,
+//   t_kl = h_{p_k p_l} d(s_k, s_l),  w_ijkl = (p_i p_l | p_j p_k) d(s_i, s_l) d(s_j, s_k).
+// Operators kept by a block at cut c (left = sites [0,c), right = [c,L)):
+//   left : I, C_k = a+_k, A_kl = a+_k a+_l (k<l), B_kl = a+_k a_l   (k, l in block)
+//          S_m (m outside), H
+//   right: I, C_k (k in block), S_m (m outside, i.e. m < 2c),
+//          P_ij = 1/2 sum_{kl in block} w_ijkl a_k a_l            (i<j<2c)
+//          Q_il = sum_{jk in block} (w_ijkl - w_ijlk) a+_j a_k     (i,l<2c)
+//          H
+//   S^B_m = 1/2 sum_{j in B} t_mj a_j + sum_{jkl in B} w_mjkl a+_j a_k a_l.
+// Decomposition at a cut L|R (normal pairs on the left):
+//   H = H_L + H_R + sum_{i in L} (a+_i S^R_i - a_i (S^R_i)^+)
+//     + sum_{m in R} (-S^L_m a+_m + (S^L_m)^+ a_m)
+//     + 2 sum_{i<j in L} (A_ij P_ij + A_ij^+ P_ij^+) + sum_{il in L} B_il Q_il.
+// A product O_X O_s on X (x) site acts as (O_X P_X^{p(O_s)}) (x) O_s; a
+// product O_s O_Y on site (x) Y as (O_s P_s^{p(O_Y)}) (x) O_Y.
+#include <cmath>
+#include <stdexcept>
+
+#include "core.hpp"
+
+namespace qd {
+
+std::vector<Key> block_keys(bool left, int c, int L) {
+  std::vector<Key> k;
+  k.push_back(Key(F_I));
+  if (left) {
+    for (int a = 0; a < 2 * c; ++a) k.push_back(Key(F_C, a));
+    for (int a = 0; a < 2 * c; ++a)
+      for (int b = a + 1; b < 2 * c; ++b) k.push_back(Key(F_A, a, b));
+    for (int a = 0; a < 2 * c; ++a)
+      for (int b = 0; b < 2 * c; ++b) k.push_back(Key(F_B, a, b));
+    for (int m = 2 * c; m < 2 * L; ++m) k.push_back(Key(F_S, m));
+  } else {
+    for (int a = 2 * c; a < 2 * L; ++a) k.push_back(Key(F_C, a));
+    for (int a = 0; a < 2 * c; ++a)
+      for (int b = a + 1; b < 2 * c; ++b) k.push_back(Key(F_P, a, b));
+    for (int a = 0; a < 2 * c; ++a)
+      for (int b = 0; b < 2 * c; ++b) k.push_back(Key(F_Q, a, b));
+    for (int m = 0; m < 2 * c; ++m) k.push_back(Key(F_S, m));
+  }
+  k.push_back(Key(F_H));
+  return k;
+}
+
+namespace {
+
+struct Ctx {
+  const EnvBlock& B;
+  const Integrals& I;
+  Enlarged& E;
+  const ProdBasis& pb;
+  Launch mat;
+  int64_t mat_total = 0;
+  std::vector<std::pair<Key, std::vector<BRef>>> pending;  // to materialize
+  Ctx(const EnvBlock& b, const Integrals& i, Enlarged& e) : B(b), I(i), E(e), pb(e.pb) {}
+
+  const OpView* get(Key k) const {
+    auto it = B.ops.find(k);
+    if (it == B.ops.end() || it->second.empty()) return nullptr;
+    return &it->second;
+  }
+
+  // expand one contribution into references on the enlarged basis
+  void expand(const Contrib& c, std::vector<BRef>& out) const {
+    if (c.coef == 0.0 || c.o.zero()) return;
+    std::vector<BRef> src;
+    if (c.src) {
+      if (c.srcT) src = transpose(*c.src).blocks;
+      else src = c.src->blocks;
+    } else {
+      for (int x = 0; x < B.basis.nsec(); ++x) {
+        BRef b;
+        b.r = b.c = x;
+        b.ptr = 0;
+        b.rows = b.cols = b.ld = B.basis.dim[x];
+        src.push_back(b);
+      }
+    }
+    for (const BRef& b : src) {
+      for (int i = 0; i < NSITE; ++i)
+        for (int i2 = 0; i2 < NSITE; ++i2) {
+          double o = c.o(i, i2);
+          if (o == 0.0) continue;
+          BRef r = b;
+          double sgn = 1.0;
+          if (E.left) {
+            r.r = pb.find(b.r, i);
+            r.c = pb.find(b.c, i2);
+            if (c.par && (B.basis.q[b.c].n & 1)) sgn = -1.0;
+          } else {
+            r.r = pb.find(b.r, i);
+            r.c = pb.find(b.c, i2);
+            if (c.par && (SITE_QN[i2].n & 1)) sgn = -1.0;
+          }
+          r.sc = b.sc * c.coef * o * sgn;
+          out.push_back(r);
+        }
+    }
+  }
+
+  void view(Key k, const std::vector<Contrib>& cs, bool odd) {
+    OpView v;
+    v.odd = odd;
+    for (auto& c : cs) expand(c, v.blocks);
+    if (!v.blocks.empty()) E.ops[k] = v;
+  }
+
+  void materialize(Key k, const std::vector<Contrib>& cs) {
+    std::vector<BRef> refs;
+    for (auto& c : cs) expand(c, refs);
+    if (refs.empty()) return;
+    pending.emplace_back(k, std::move(refs));
+  }
+
+  void finish(Executor& ex, const std::map<Key, bool>& odd, double* flops) {
+    // group by (r, c), allocate and emit gather-AXPY problems
+    struct G { std::map<std::pair<int, int>, std::vector<const BRef*>> g; };
+    std::vector<G> groups(pending.size());
+    int64_t total = 0;
+    for (size_t n = 0; n < pending.size(); ++n) {
+      for (const BRef& b : pending[n].second) groups[n].g[{b.r, b.c}].push_back(&b);
+      for (auto& kv : groups[n].g)
+        total += (int64_t)pb.subs[kv.first.first].dim * pb.subs[kv.first.second].dim;
+    }
+    if (!total) return;
+    uint64_t store = ex.alloc(total);
+    E.owned.push_back(store);
+    int64_t pos = 0;
+    Launch l;
+    for (size_t n = 0; n < pending.size(); ++n) {
+      OpView v;
+      v.odd = odd.at(pending[n].first);
+      for (auto& kv : groups[n].g) {
+        int r = kv.first.first, c = kv.first.second;
+        int m = pb.subs[r].dim, nn = pb.subs[c].dim;
+        Prob p;
+        p.c = store + 8ull * pos; p.cbuf = B_ABS;
+        p.m = m; p.n = nn; p.ldc = nn; p.beta = 0;
+        p.seg0 = (int)l.segs.size(); p.nseg = 0;
+        for (const BRef* b : kv.second) {
+          Seg s;
+          s.a = 0; s.abuf = B_ABS; s.k = m; s.sc = b->sc;
+          if (b->ident()) { s.b = 0; s.bbuf = B_ABS; }
+          else { s.b = b->ptr; s.bbuf = B_ABS; s.ldb = b->ld; s.tb = b->tr ? 1 : 0; }
+          l.segs.push_back(s);
+          p.nseg++;
+        }
+        l.probs.push_back(p);
+        BRef o;
+        o.r = r; o.c = c; o.ptr = p.c; o.rows = m; o.cols = nn; o.ld = nn; o.tr = false; o.sc = 1.0;
+        v.blocks.push_back(o);
+        pos += (int64_t)m * nn;
+      }
+      E.ops[pending[n].first] = v;
+    }
+    ex.run(l, 0, 0);
+    (void)flops;
+  }
+};
+
+Mat4 site_three(const Integrals& I, int m, const int sm[2]) {
+  Mat4 r;
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b)
+      for (int c = 0; c < 2; ++c) {
+        double w = I.w(m, sm[a], sm[b], sm[c]);
+        if (w != 0.0) r = r + cre(a) * ann(b) * ann(c) * w;
+      }
+  return r;
+}
+
+// S^s_m of a single site for m outside the site
+Mat4 site_S(const Integrals& I, int m, const int sm[2]) {
+  Mat4 r = site_three(I, m, sm);
+  for (int j = 0; j < 2; ++j) r = r + ann(j) * (0.5 * I.t(m, sm[j]));
+  return r;
+}
+
+Mat4 site_H(const Integrals& I, const int sm[2]) {
+  Mat4 r;
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) {
+      r = r + cre(a) * ann(b) * I.t(sm[a], sm[b]);
+      for (int c = 0; c < 2; ++c)
+        for (int d = 0; d < 2; ++d) {
+          double w = I.w(sm[a], sm[b], sm[c], sm[d]);
+          if (w != 0.0) r = r + cre(a) * cre(b) * ann(c) * ann(d) * (0.5 * w);
+        }
+    }
+  return r;
+}
+
+Contrib C_(const OpView* src, bool T, const Mat4& o, double coef, bool par) {
+  Contrib c;
+  c.src = src;
+  c.srcT = T;
+  c.o = o;
+  c.coef = coef;
+  c.par = par;
+  return c;
+}
+
+}  // namespace
+
+void enlarge(const EnvBlock& B, const Integrals& I, Executor& ex, Enlarged& E, double* flops) {
+  const int L = I.L;
+  E.left = B.left;
+  E.ops.clear();
+  E.pb = make_prod(B.basis, B.left);
+  Ctx x(B, I, E);
+  const Mat4 I4 = Mat4::id();
+  std::map<Key, bool> odd;
+  auto nonnull = [](const OpView* p) { return p != nullptr; };
+  (void)nonnull;
+  if (B.left) {
+    const int c = B.cut;          // X = [0, c), site p = c
+    E.cut = c + 1;
+    const int sm[2] = {2 * c, 2 * c + 1};
+    const int nx = 2 * c;
+    x.view(Key(F_I), {C_(nullptr, false, I4, 1.0, false)}, false);
+    for (int k = 0; k < nx; ++k)
+      if (auto C = x.get(Key(F_C, k))) x.view(Key(F_C, k), {C_(C, false, I4, 1.0, false)}, true);
+    for (int s = 0; s < 2; ++s) x.view(Key(F_C, sm[s]), {C_(nullptr, false, cre(s), 1.0, true)}, true);
+    // A'_kl, k < l
+    for (int k = 0; k < nx; ++k)
+      for (int l = k + 1; l < nx; ++l)
+        if (auto A = x.get(Key(F_A, k, l))) x.view(Key(F_A, k, l), {C_(A, false, I4, 1.0, false)}, false);
+    for (int k = 0; k < nx; ++k)
+      for (int s = 0; s < 2; ++s)
+        if (auto C = x.get(Key(F_C, k))) x.view(Key(F_A, k, sm[s]), {C_(C, false, cre(s), 1.0, true)}, false);
+    x.view(Key(F_A, sm[0], sm[1]), {C_(nullptr, false, cre(0) * cre(1), 1.0, false)}, false);
+    // B'_kl
+    for (int k = 0; k < nx; ++k)
+      for (int l = 0; l < nx; ++l)
+        if (auto Bk = x.get(Key(F_B, k, l))) x.view(Key(F_B, k, l), {C_(Bk, false, I4, 1.0, false)}, false);
+    for (int k = 0; k < nx; ++k)
+      for (int s = 0; s < 2; ++s)
+        if (auto C = x.get(Key(F_C, k))) {
+          x.view(Key(F_B, k, sm[s]), {C_(C, false, ann(s), 1.0, true)}, false);       // a+_k(X) a_l(s)
+          x.view(Key(F_B, sm[s], k), {C_(C, true, cre(s), -1.0, true)}, false);       // a+_k(s) a_l(X) = -a_l a+_k
+        }
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b)
+        x.view(Key(F_B, sm[a], sm[b]), {C_(nullptr, false, cre(a) * ann(b), 1.0, false)}, false);
+    // S'_m, m outside the enlarged block
+    for (int m = 2 * (c + 1); m < 2 * L; ++m) {
+      std::vector<Contrib> cs;
+      if (auto S = x.get(Key(F_S, m))) cs.push_back(C_(S, false, I4, 1.0, false));
+      for (int j = 0; j < 2; ++j) cs.push_back(C_(nullptr, false, ann(j), 0.5 * I.t(m, sm[j]), true));
+      for (int s = 0; s < 2; ++s) {
+        const int l = sm[s];
+        for (int j = 0; j < nx; ++j)
+          for (int k = 0; k < nx; ++k) {
+            auto Bjk = x.get(Key(F_B, j, k));
+            if (!Bjk) continue;
+            double w1 = I.w(m, j, k, l);       // (X,X,s): (a+_j a_k)_X (a_l)_s
+            double w2 = -I.w(m, j, l, k);      // (X,s,X): -(a+_j a_k)_X (a_l)_s, roles k<->l
+            if (w1 + w2 != 0.0) cs.push_back(C_(Bjk, false, ann(s), w1 + w2, true));
+          }
+        // (s,X,X): (a_k a_l)_X (a+_j)_s with j = site mode; (a_k a_l) = -A_kl^T (k<l)
+        const int j = sm[s];
+        for (int k = 0; k < nx; ++k)
+          for (int l2 = k + 1; l2 < nx; ++l2) {
+            auto A = x.get(Key(F_A, k, l2));
+            if (!A) continue;
+            double w = -I.w(m, j, k, l2) + I.w(m, j, l2, k);
+            if (w != 0.0) cs.push_back(C_(A, true, cre(s), w, true));
+          }
+      }
+      for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+          for (int j = 0; j < nx; ++j) {
+            auto C = x.get(Key(F_C, j));
+            if (!C) continue;
+            double w = I.w(m, j, sm[a], sm[b]);                 // (X,s,s): a+_j (a_a a_b)_s
+            if (w != 0.0) cs.push_back(C_(C, false, ann(a) * ann(b), w, false));
+            double w2 = -I.w(m, sm[a], j, sm[b]) + I.w(m, sm[a], sm[b], j);  // (s,X,s) + (s,s,X)
+            if (w2 != 0.0) cs.push_back(C_(C, true, cre(a) * ann(b), w2, false));
+          }
+        }
+      cs.push_back(C_(nullptr, false, site_three(I, m, sm), 1.0, true));
+      odd[Key(F_S, m)] = true;
+      x.materialize(Key(F_S, m), cs);
+    }
+    // H'
+    {
+      std::vector<Contrib> cs;
+      if (auto H = x.get(Key(F_H))) cs.push_back(C_(H, false, I4, 1.0, false));
+      cs.push_back(C_(nullptr, false, site_H(I, sm), 1.0, false));
+      for (int i = 0; i < nx; ++i)
+        if (auto C = x.get(Key(F_C, i))) {
+          Mat4 Ss = site_S(I, i, sm);
+          cs.push_back(C_(C, false, Ss, 1.0, true));
+          cs.push_back(C_(C, true, Ss.T(), -1.0, true));
+        }
+      for (int s = 0; s < 2; ++s)
+        if (auto S = x.get(Key(F_S, sm[s]))) {
+          cs.push_back(C_(S, false, cre(s), -1.0, true));
+          cs.push_back(C_(S, true, ann(s), 1.0, true));
+        }
+      for (int i = 0; i < nx; ++i)
+        for (int j = i + 1; j < nx; ++j)
+          if (auto A = x.get(Key(F_A, i, j))) {
+            Mat4 P;
+            for (int a = 0; a < 2; ++a)
+              for (int b = 0; b < 2; ++b) P = P + ann(a) * ann(b) * (0.5 * I.w(i, j, sm[a], sm[b]));
+            cs.push_back(C_(A, false, P, 2.0, false));
+            cs.push_back(C_(A, true, P.T(), 2.0, false));
+          }
+      for (int i = 0; i < nx; ++i)
+        for (int l = 0; l < nx; ++l)
+          if (auto Bil = x.get(Key(F_B, i, l))) {
+            Mat4 Q;
+            for (int a = 0; a < 2; ++a)
+              for (int b = 0; b < 2; ++b) Q = Q + cre(a) * ann(b) * I.q(i, sm[a], sm[b], l);
+            cs.push_back(C_(Bil, false, Q, 1.0, false));
+          }
+      odd[Key(F_H)] = false;
+      x.materialize(Key(F_H), cs);
+    }
+  } else {
+    const int c = B.cut - 1;      // site p = c, Y = [c+1, L)
+    E.cut = c;
+    const int sm[2] = {2 * c, 2 * c + 1};
+    const int y0 = 2 * (c + 1);
+    x.view(Key(F_I), {C_(nullptr, false, I4, 1.0, false)}, false);
+    for (int s = 0; s < 2; ++s) x.view(Key(F_C, sm[s]), {C_(nullptr, false, cre(s), 1.0, false)}, true);
+    for (int k = y0; k < 2 * L; ++k)
+      if (auto C = x.get(Key(F_C, k))) x.view(Key(F_C, k), {C_(C, false, I4, 1.0, true)}, true);
+    // P'_ij, i < j < 2c
+    for (int i = 0; i < 2 * c; ++i)
+      for (int j = i + 1; j < 2 * c; ++j) {
+        std::vector<Contrib> cs;
+        if (auto P = x.get(Key(F_P, i, j))) cs.push_back(C_(P, false, I4, 1.0, false));
+        for (int s = 0; s < 2; ++s)
+          for (int l = y0; l < 2 * L; ++l) {
+            auto C = x.get(Key(F_C, l));
+            if (!C) continue;
+            double w = 0.5 * (I.w(i, j, sm[s], l) - I.w(i, j, l, sm[s]));
+            if (w != 0.0) cs.push_back(C_(C, true, ann(s), w, true));
+          }
+        Mat4 P;
+        for (int a = 0; a < 2; ++a)
+          for (int b = 0; b < 2; ++b) P = P + ann(a) * ann(b) * (0.5 * I.w(i, j, sm[a], sm[b]));
+        cs.push_back(C_(nullptr, false, P, 1.0, false));
+        odd[Key(F_P, i, j)] = false;
+        x.materialize(Key(F_P, i, j), cs);
+      }
+    // Q'_il, i, l < 2c
+    for (int i = 0; i < 2 * c; ++i)
+      for (int l = 0; l < 2 * c; ++l) {
+        std::vector<Contrib> cs;
+        if (auto Q = x.get(Key(F_Q, i, l))) cs.push_back(C_(Q, false, I4, 1.0, false));
+        for (int s = 0; s < 2; ++s)
+          for (int k = y0; k < 2 * L; ++k) {
+            auto C = x.get(Key(F_C, k));
+            if (!C) continue;
+            double q1 = I.q(i, sm[s], k, l);    // (s,Y): a+_j(s) a_k(Y)
+            if (q1 != 0.0) cs.push_back(C_(C, true, cre(s), q1, true));
+            double q2 = -I.q(i, k, sm[s], l);   // (Y,s): a+_j(Y) a_k(s) = -a_k a+_j
+            if (q2 != 0.0) cs.push_back(C_(C, false, ann(s), q2, true));
+          }
+        Mat4 Q;
+        for (int a = 0; a < 2; ++a)
+          for (int b = 0; b < 2; ++b) Q = Q + cre(a) * ann(b) * I.q(i, sm[a], sm[b], l);
+        cs.push_back(C_(nullptr, false, Q, 1.0, false));
+        odd[Key(F_Q, i, l)] = false;
+        x.materialize(Key(F_Q, i, l), cs);
+      }
+    // S'_m, m < 2c
+    for (int m = 0; m < 2 * c; ++m) {
+      std::vector<Contrib> cs;
+      if (auto S = x.get(Key(F_S, m))) cs.push_back(C_(S, false, I4, 1.0, true));
+      Mat4 t1;
+      for (int j = 0; j < 2; ++j) t1 = t1 + ann(j) * (0.5 * I.t(m, sm[j]));
+      cs.push_back(C_(nullptr, false, t1, 1.0, false));
+      for (int s = 0; s < 2; ++s) {
+        if (auto P = x.get(Key(F_P, m, sm[s]))) cs.push_back(C_(P, false, cre(s), 2.0, false));
+        if (auto Q = x.get(Key(F_Q, m, sm[s]))) cs.push_back(C_(Q, false, ann(s), 1.0, false));
+      }
+      for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+          for (int k = y0; k < 2 * L; ++k) {
+            auto C = x.get(Key(F_C, k));
+            if (!C) continue;
+            // (s,s,Y): (a+_a a_b)_s (a_k)_Y ; (s,Y,s): -(a+_a a_b)_s (a_k)_Y
+            double w1 = I.w(m, sm[a], sm[b], k) - I.w(m, sm[a], k, sm[b]);
+            if (w1 != 0.0) cs.push_back(C_(C, true, cre(a) * ann(b), w1, true));
+            // (Y,s,s): (a_a a_b)_s (a+_k)_Y
+            double w2 = I.w(m, k, sm[a], sm[b]);
+            if (w2 != 0.0) cs.push_back(C_(C, false, ann(a) * ann(b), w2, true));
+          }
+      cs.push_back(C_(nullptr, false, site_three(I, m, sm), 1.0, false));
+      odd[Key(F_S, m)] = true;
+      x.materialize(Key(F_S, m), cs);
+    }
+    // H'
+    {
+      std::vector<Contrib> cs;
+      cs.push_back(C_(nullptr, false, site_H(I, sm), 1.0, false));
+      if (auto H = x.get(Key(F_H))) cs.push_back(C_(H, false, I4, 1.0, false));
+      for (int s = 0; s < 2; ++s)
+        if (auto S = x.get(Key(F_S, sm[s]))) {
+          cs.push_back(C_(S, false, cre(s), 1.0, true));
+          cs.push_back(C_(S, true, ann(s), -1.0, true));
+        }
+      for (int m = y0; m < 2 * L; ++m)
+        if (auto C = x.get(Key(F_C, m))) {
+          Mat4 Ss = site_S(I, m, sm);
+          cs.push_back(C_(C, false, Ss, -1.0, true));
+          cs.push_back(C_(C, true, Ss.T(), 1.0, true));
+        }
+      if (auto P = x.get(Key(F_P, sm[0], sm[1]))) {
+        Mat4 A = cre(0) * cre(1);
+        cs.push_back(C_(P, false, A, 2.0, false));
+        cs.push_back(C_(P, true, A.T(), 2.0, false));
+      }
+      for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+          if (auto Q = x.get(Key(F_Q, sm[a], sm[b]))) cs.push_back(C_(Q, false, cre(a) * ann(b), 1.0, false));
+      odd[Key(F_H)] = false;
+      x.materialize(Key(F_H), cs);
+    }
+  }
+  x.finish(ex, odd, flops);
+}
+
+}  // namespace qd
