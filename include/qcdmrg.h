@@ -1,0 +1,155 @@
+/*
+ * qcdmrg: C ABI of the two-site DMRG H_eff.psi hot path on B300 (sm_103a).
+ *
+ * The method is the ab initio DMRG of arXiv 2603.28648 (Method section,
+ * Eq. (mps)): a matrix product state of L spatial orbitals with the local
+ * basis {|0>, |up>, |dn>, |updn>} is optimised site pair by site pair; the
+ * Davidson / Lanczos sigma step H_eff psi contracts the renormalized
+ * operators of the left and right blocks (normal and complementary
+ * operators built from h_pq and V_pqrs) with the two-site wavefunction,
+ * one quantum-number block at a time (Method and Numerical procedure
+ * sections; the cost model O(N^2 D^2) memory, O(N^4 D^3) compute is the
+ * Method section's).
+ *
+ * Conventions
+ *   - Every call returns an int status: QCDMRG_OK (0) or a negative code.
+ *     qcdmrg_last_error() gives the message of the last failure on a context.
+ *   - The library owns all device memory, the operators and the MPS. Caller
+ *     arrays are copied on input; output arrays are caller-allocated.
+ *   - Pointers are host pointers unless the function name ends in _dev; _dev
+ *     functions take device pointers and a cudaStream_t (NULL: the context's
+ *     stream).
+ *   - Dense arrays are row-major FP64. A context is not thread-safe;
+ *     separate contexts are independent.
+ *   - Hamiltonian: H = sum_pq h_pq E_pq + 1/2 sum_pqrs V_pqrs (E_pq E_rs -
+ *     d_qr E_ps) + e_core with chemist-notation V_pqrs = (pq|rs).
+ */
+#ifndef QCDMRG_H
+#define QCDMRG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QCDMRG_OK 0
+#define QCDMRG_EINVAL (-1)   /* bad argument or inconsistent input */
+#define QCDMRG_ENOMEM (-2)   /* device or host allocation failed */
+#define QCDMRG_ECUDA (-3)    /* CUDA runtime error */
+#define QCDMRG_ESTATE (-4)   /* call out of order (e.g. apply before build_env) */
+#define QCDMRG_ENOTCONV (-5) /* iteration limit reached; results are still written */
+#define QCDMRG_ETIMEOUT (-6) /* a bounded device wait gave up */
+#define QCDMRG_EIO (-7)      /* file error */
+
+/* symmetry */
+#define QCDMRG_U1 0 /* U(1)xU(1): sector labels (N, 2Sz) */
+
+/* precision of the block contractions */
+#define QCDMRG_FP64 0
+
+typedef struct qcdmrg_ctx qcdmrg_ctx;
+
+typedef struct {
+  int symmetry;         /* QCDMRG_U1 */
+  int device;           /* CUDA device ordinal */
+  double tmp_budget_gb; /* scratch for stage-1 intermediates (0: 2 GB) */
+} qcdmrg_config;
+
+/*
+ * MPS description for import. Bond b (0..L) separates sites [0,b) and [b,L).
+ * Bonds b <= center carry the (N, 2Sz) labels of the block on their left,
+ * bonds b >= center+2 those of the block on their right; bond center+1 is
+ * not used (give 0 sectors). bond_nsec[b] sectors of bond b are listed in
+ * bond_sec as (n, two_sz, dim) triples, bonds concatenated, labels strictly
+ * increasing by (n, two_sz) inside a bond.
+ *
+ * Data layout (FP64, concatenated in this order):
+ *   left sites p = 0 .. center-1: for each sector q of the product basis
+ *     (bond p) x site, in label order, that is present in bond p+1: the
+ *     matrix U_q [rows = product rows, cols = dim_q] row-major; product rows
+ *     run over (x, i) pairs (x = sector of bond p, i = site state) in
+ *     (x, i) order, each x contributing dim_x rows;
+ *   right sites p = center+2 .. L-1: for each sector q of site x (bond p+1)
+ *     in label order present in bond p: the matrix V_q [dim_q x product
+ *     cols], product columns over (j, y) pairs in (j, y) order;
+ *   the two-site wavefunction: sub-blocks (x, i, j, y) with x a sector of
+ *     bond center, y a sector of bond center+2, labels adding up to the
+ *     target, sorted by (x, i, j, y); each sub-block dim_x x dim_y row-major.
+ * Site states: 0 = |0>, 1 = a+_up|0>, 2 = a+_dn|0>, 3 = a+_up a+_dn|0>.
+ */
+typedef struct {
+  int L;
+  int center; /* two-site centre: sites (center, center+1) */
+  const int* bond_nsec;
+  const int* bond_sec;
+} qcdmrg_mps_desc;
+
+typedef struct {
+  double heff_flops;     /* algorithmic 2mnk of one H_eff psi (all block GEMMs) */
+  double heff_seconds;   /* device time of the last H_eff psi */
+  double env_flops;      /* flops of the last environment build */
+  double env_seconds;    /* wall time of the last environment build */
+  int64_t psi_size;      /* elements of the two-site wavefunction */
+  int64_t device_bytes;  /* bytes allocated on the device by the context */
+  int nterms;            /* operator-product terms of H_eff */
+  int nlaunch;           /* kernel launches per H_eff psi */
+} qcdmrg_stats;
+
+/* Create a context on cfg->device. Errors: EINVAL, ECUDA, ENOMEM. */
+int qcdmrg_create(qcdmrg_ctx** out, const qcdmrg_config* cfg);
+int qcdmrg_destroy(qcdmrg_ctx* ctx);
+/* Message of the last failed call (empty if none); owned by the context. */
+const char* qcdmrg_last_error(const qcdmrg_ctx* ctx);
+
+/*
+ * Load the active-space integrals: h (L*L) and V (L^4, (pq|rs) at
+ * ((p*L+q)*L+r)*L+s). The arrays are copied. Errors: EINVAL for L < 2,
+ * non-finite values or a non-symmetric h.
+ */
+int qcdmrg_load_integrals(qcdmrg_ctx* ctx, int L, const double* h, const double* V,
+                          double e_core);
+
+/* Target particle number and 2Sz (U1). Errors: EINVAL on parity mismatch. */
+int qcdmrg_set_target(qcdmrg_ctx* ctx, int N, int two_s);
+
+/*
+ * Import a mixed-canonical MPS around a two-site centre (layout above). The
+ * tensors must be canonical (left tensors U_q with orthonormal columns,
+ * right tensors V_q with orthonormal rows); they are copied to the device.
+ * n is the number of doubles in data. Errors: EINVAL (layout mismatch),
+ * ESTATE (integrals or target missing).
+ */
+int qcdmrg_import_mps(qcdmrg_ctx* ctx, const qcdmrg_mps_desc* desc, const double* data,
+                      size_t n);
+
+/*
+ * Renormalize the left block up to the centre and the right block down to
+ * it (the operator renormalization of every truncation step, replayed for
+ * the imported tensors), enlarge both by their dot site and build the
+ * H_eff task list. Errors: ESTATE (no MPS), ECUDA, ENOMEM.
+ */
+int qcdmrg_build_env(qcdmrg_ctx* ctx);
+
+/* Number of elements of the two-site wavefunction (after build_env). */
+int qcdmrg_psi_size(const qcdmrg_ctx* ctx, size_t* n);
+
+/*
+ * sigma = H_eff psi on host arrays of psi_size elements (layout above).
+ * precision: QCDMRG_FP64. Errors: ESTATE (no environment), EINVAL.
+ */
+int qcdmrg_apply_heff(qcdmrg_ctx* ctx, int precision, const double* psi, double* sigma);
+
+/* Same on device arrays, enqueued on stream (NULL: context stream); returns
+ * after enqueueing. psi and sigma must not overlap. */
+int qcdmrg_apply_heff_dev(qcdmrg_ctx* ctx, int precision, const void* psi, void* sigma,
+                          void* stream);
+
+/* Counters of the last calls. */
+int qcdmrg_stats(const qcdmrg_ctx* ctx, qcdmrg_stats* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

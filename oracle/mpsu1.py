@@ -238,3 +238,59 @@ class Projector:
 
     def heff(self, fci, psi):
         return self.apply_t(fci.apply(self.apply(psi)))
+
+
+def export_abi(mps):
+    """Flatten a mixed-canonical MPS into the C-ABI import layout.
+
+    Returns (bond_nsec, bond_sec, data) as numpy arrays: left sites as
+    product-sector matrices U_q [(x, i) rows, kept states], right sites as
+    V_q [kept states, (j, y) columns], then the two-site wavefunction.
+    """
+    L, c = mps.L, mps.center
+    bonds = {}
+    for b in range(0, c + 1):
+        bonds[b] = mps.lbonds[b]
+    for b in range(c + 2, L + 1):
+        bonds[b] = mps.rbonds[b]
+    nsec, sec = [], []
+    for b in range(L + 1):
+        if b in bonds:
+            items = sorted(bonds[b].sectors.items())
+            nsec.append(len(items))
+            for q, (st, d) in items:
+                sec += [q[0], q[1], d]
+        else:
+            nsec.append(0)
+    data = []
+    for p in range(c):
+        bl, br = mps.lbonds[p], mps.lbonds[p + 1]
+        prods = {}
+        for q, (x0, dx) in sorted(bl.sectors.items()):
+            for i, si in enumerate(SITE_QN):
+                lab = (q[0] + si[0], q[1] + si[1])
+                prods.setdefault(lab, []).append((q, i))
+        for lab in sorted(prods):
+            if lab not in br.sectors:
+                continue
+            c0, dc = br.sectors[lab]
+            rows = [mps.A[p][bl.sectors[q][0]:bl.sectors[q][0] + bl.sectors[q][1], i, c0:c0 + dc]
+                    for q, i in sorted(prods[lab], key=lambda t: (t[0], t[1]))]
+            data.append(np.concatenate(rows, axis=0).reshape(-1))
+    for p in range(c + 2, L):
+        bn, bR = mps.rbonds[p], mps.rbonds[p + 1]
+        prods = {}
+        for j, sj in enumerate(SITE_QN):
+            for q, (y0, dy) in sorted(bR.sectors.items()):
+                lab = (sj[0] + q[0], sj[1] + q[1])
+                prods.setdefault(lab, []).append((j, q))
+        for lab in sorted(prods):
+            if lab not in bn.sectors:
+                continue
+            r0, dr = bn.sectors[lab]
+            cols = [mps.R[p][r0:r0 + dr, j, bR.sectors[q][0]:bR.sectors[q][0] + bR.sectors[q][1]]
+                    for j, q in sorted(prods[lab], key=lambda t: (t[0], t[1]))]
+            data.append(np.concatenate(cols, axis=1).reshape(-1))
+    data.append(mps.psi_to_flat())
+    return (np.array(nsec, dtype=np.int32), np.array(sec, dtype=np.int32),
+            np.concatenate(data).astype(np.float64))

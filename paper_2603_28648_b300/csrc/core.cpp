@@ -160,6 +160,7 @@ void renormalize(const Enlarged& E, const Basis& nb, const std::vector<int>& nb_
   std::map<Key, std::map<std::pair<int, int>, int64_t>> layout;
   int64_t total = 0;
   for (auto& kv : E.ops) {
+    if (kv.first.f == F_I) continue;  // the identity is never stored
     auto& lay = layout[kv.first];
     for (const BRef& b : kv.second.blocks) {
       int q = pb.subs[b.r].prod, q2 = pb.subs[b.c].prod;
@@ -194,6 +195,7 @@ void renormalize(const Enlarged& E, const Basis& nb, const std::vector<int>& nb_
     tused = 0;
   };
   for (auto& kv : E.ops) {
+    if (kv.first.f == F_I) continue;
     const OpView& op = kv.second;
     auto& lay = layout[kv.first];
     OpView nv;

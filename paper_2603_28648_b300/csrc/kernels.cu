@@ -1,0 +1,335 @@
+// CUDA backend: device memory, task-list upload and the FP64 segmented
+// grouped GEMM that executes every block contraction of H_eff psi,
+// renormalization and complementary-operator materialization.
+//
+// One launch runs a list of output problems; problem p owns C_p (m x n) and
+// computes C_p = beta*C_p + sum_s sc_s op(A_s) op(B_s) over its segments.
+// Identity segments (A = I, or A = B = I) implement gather-AXPY. Each CTA
+// owns one 64x64 output tile and loops over all segments of its problem, so
+// no output is written by two CTAs and no atomics are needed.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "core.hpp"
+#include "kernels.hpp"
+
+namespace qd {
+
+#define CK(x)                                                                      \
+  do {                                                                             \
+    cudaError_t e_ = (x);                                                          \
+    if (e_ != cudaSuccess)                                                         \
+      throw std::runtime_error(std::string("CUDA: ") + cudaGetErrorString(e_) +    \
+                               " at " + __FILE__ + ":" + std::to_string(__LINE__)); \
+  } while (0)
+
+struct GSeg {
+  unsigned long long a, b;
+  int lda, ldb, k;
+  unsigned char abuf, bbuf, ta, tb;
+  double sc;
+};
+struct GProb {
+  unsigned long long c;
+  int m, n, ldc, beta, seg0, nseg, cbuf, pad;
+};
+struct GTile {
+  int prob, m0, n0, pad;
+};
+struct Bases {
+  unsigned long long b[4];
+};
+
+constexpr int TM = 64, TN = 64, TK = 16;
+
+__device__ __forceinline__ const double* res(unsigned long long v, int buf, const Bases& B) {
+  return buf == 0 ? reinterpret_cast<const double*>(v)
+                  : reinterpret_cast<const double*>(B.b[buf] + v * 8ull);
+}
+
+__global__ void __launch_bounds__(256) seg_gemm_f64(const GProb* __restrict__ probs,
+                                                    const GSeg* __restrict__ segs,
+                                                    const GTile* __restrict__ tiles, int ntiles,
+                                                    Bases bases) {
+  const int t = blockIdx.x;
+  if (t >= ntiles) return;
+  const GTile tl = tiles[t];
+  const GProb p = probs[tl.prob];
+  __shared__ double As[TK][TM + 1];
+  __shared__ double Bs[TK][TN + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
+  const int m0 = tl.m0, n0 = tl.n0;
+  for (int s = 0; s < p.nseg; ++s) {
+    const GSeg g = segs[p.seg0 + s];
+    const bool aid = (g.a == 0ull && g.abuf == 0);
+    const bool bid = (g.b == 0ull && g.bbuf == 0);
+    if (aid) {
+      if (bid) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            if (m0 + ty + 16 * r == n0 + tx + 16 * c) acc[r][c] += g.sc;
+      } else {
+        const double* Bp = res(g.b, g.bbuf, bases);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int row = m0 + ty + 16 * r;
+          if (row >= p.m) continue;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int col = n0 + tx + 16 * c;
+            if (col >= p.n) continue;
+            const double v = g.tb ? Bp[(size_t)col * g.ldb + row] : Bp[(size_t)row * g.ldb + col];
+            acc[r][c] += g.sc * v;
+          }
+        }
+      }
+      continue;
+    }
+    const double* Ap = res(g.a, g.abuf, bases);
+    const double* Bp = res(g.b, g.bbuf, bases);
+    for (int k0 = 0; k0 < g.k; k0 += TK) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int idx = tid + 256 * e;
+        int row, kk;
+        if (g.ta) { kk = idx >> 6; row = idx & 63; }
+        else { row = idx >> 4; kk = idx & 15; }
+        const int gr = m0 + row, gk = k0 + kk;
+        double v = 0.0;
+        if (gr < p.m && gk < g.k)
+          v = g.ta ? Ap[(size_t)gk * g.lda + gr] : Ap[(size_t)gr * g.lda + gk];
+        As[kk][row] = v * g.sc;
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int idx = tid + 256 * e;
+        int col, kk;
+        if (g.tb) { col = idx >> 4; kk = idx & 15; }
+        else { kk = idx >> 6; col = idx & 63; }
+        const int gc = n0 + col, gk = k0 + kk;
+        double v = 0.0;
+        if (gc < p.n && gk < g.k)
+          v = g.tb ? Bp[(size_t)gc * g.ldb + gk] : Bp[(size_t)gk * g.ldb + gc];
+        Bs[kk][col] = v;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < TK; ++kk) {
+        double a[4], b[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) a[r] = As[kk][ty + 16 * r];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + 16 * c];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+      }
+      __syncthreads();
+    }
+  }
+  double* Cp = const_cast<double*>(res(p.c, p.cbuf, bases));
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int row = m0 + ty + 16 * r;
+    if (row >= p.m) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int col = n0 + tx + 16 * c;
+      if (col >= p.n) continue;
+      double* dst = Cp + (size_t)row * p.ldc + col;
+      *dst = p.beta ? *dst + acc[r][c] : acc[r][c];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+struct DevLaunch {
+  GProb* p = nullptr;
+  GSeg* s = nullptr;
+  GTile* t = nullptr;
+  int ntiles = 0;
+  double flops = 0;
+};
+
+static void build_host(const Launch& l, std::vector<GProb>& P, std::vector<GSeg>& S,
+                       std::vector<GTile>& T) {
+  P.resize(l.probs.size());
+  S.resize(l.segs.size());
+  T.clear();
+  for (size_t i = 0; i < l.probs.size(); ++i) {
+    const Prob& q = l.probs[i];
+    GProb& g = P[i];
+    g.c = q.c; g.m = q.m; g.n = q.n; g.ldc = q.ldc; g.beta = q.beta;
+    g.seg0 = q.seg0; g.nseg = q.nseg; g.cbuf = q.cbuf; g.pad = 0;
+    for (int m0 = 0; m0 < q.m; m0 += TM)
+      for (int n0 = 0; n0 < q.n; n0 += TN) T.push_back({(int)i, m0, n0, 0});
+  }
+  for (size_t i = 0; i < l.segs.size(); ++i) {
+    const Seg& q = l.segs[i];
+    GSeg& g = S[i];
+    g.a = q.a; g.b = q.b; g.lda = q.lda; g.ldb = q.ldb; g.k = q.k;
+    g.abuf = (unsigned char)q.abuf; g.bbuf = (unsigned char)q.bbuf;
+    g.ta = (unsigned char)q.ta; g.tb = (unsigned char)q.tb; g.sc = q.sc;
+  }
+}
+
+class CudaExec : public Executor, public PreparedRunner {
+ public:
+  explicit CudaExec(int device) : dev_(device) {
+    CK(cudaSetDevice(dev_));
+    CK(cudaStreamCreateWithFlags(&st_, cudaStreamNonBlocking));
+  }
+  ~CudaExec() override {
+    cudaSetDevice(dev_);
+    cudaStreamSynchronize(st_);
+    for (auto& d : prepared_) free_dev(d);
+    if (tmp_) cudaFree(reinterpret_cast<void*>(tmp_));
+    if (sp_) cudaFree(sp_);
+    if (ss_) cudaFree(ss_);
+    if (stt_) cudaFree(stt_);
+    cudaStreamDestroy(st_);
+  }
+  uint64_t alloc(int64_t n) override {
+    void* p = nullptr;
+    if (n <= 0) n = 1;
+    CK(cudaMalloc(&p, (size_t)n * 8));
+    CK(cudaMemsetAsync(p, 0, (size_t)n * 8, st_));
+    bytes_ += n * 8;
+    return reinterpret_cast<uint64_t>(p);
+  }
+  void release(uint64_t p) override {
+    if (p) {
+      CK(cudaStreamSynchronize(st_));
+      CK(cudaFree(reinterpret_cast<void*>(p)));
+    }
+  }
+  uint64_t tmp(int64_t n) override {
+    if (n > tmpcap_) {
+      CK(cudaStreamSynchronize(st_));
+      if (tmp_) CK(cudaFree(reinterpret_cast<void*>(tmp_)));
+      void* p = nullptr;
+      CK(cudaMalloc(&p, (size_t)n * 8));
+      tmp_ = reinterpret_cast<uint64_t>(p);
+      tmpcap_ = n;
+    }
+    return tmp_;
+  }
+  void run(const Launch& l, uint64_t psi, uint64_t sig) override {
+    if (l.empty()) return;
+    std::vector<GProb> P;
+    std::vector<GSeg> S;
+    std::vector<GTile> T;
+    build_host(l, P, S, T);
+    CK(cudaStreamSynchronize(st_));
+    grow(&sp_, &spcap_, P.size() * sizeof(GProb));
+    grow(&ss_, &sscap_, S.size() * sizeof(GSeg));
+    grow(&stt_, &stcap_, T.size() * sizeof(GTile));
+    CK(cudaMemcpyAsync(sp_, P.data(), P.size() * sizeof(GProb), cudaMemcpyHostToDevice, st_));
+    CK(cudaMemcpyAsync(ss_, S.data(), S.size() * sizeof(GSeg), cudaMemcpyHostToDevice, st_));
+    CK(cudaMemcpyAsync(stt_, T.data(), T.size() * sizeof(GTile), cudaMemcpyHostToDevice, st_));
+    launch((GProb*)sp_, (GSeg*)ss_, (GTile*)stt_, (int)T.size(), psi, sig, st_);
+    CK(cudaStreamSynchronize(st_));
+  }
+  void upload(uint64_t dst, const double* h, int64_t n) override {
+    CK(cudaMemcpyAsync(reinterpret_cast<void*>(dst), h, (size_t)n * 8, cudaMemcpyHostToDevice, st_));
+    CK(cudaStreamSynchronize(st_));
+  }
+  void download(double* h, uint64_t src, int64_t n) override {
+    CK(cudaMemcpyAsync(h, reinterpret_cast<void*>(src), (size_t)n * 8, cudaMemcpyDeviceToHost, st_));
+    CK(cudaStreamSynchronize(st_));
+  }
+  void zero(uint64_t p, int64_t n) override {
+    CK(cudaMemsetAsync(reinterpret_cast<void*>(p), 0, (size_t)n * 8, st_));
+  }
+
+  // prepared launches (uploaded once, replayed on any psi / sigma)
+  int prepare(const Launch& l) override {
+    DevLaunch d;
+    std::vector<GProb> P;
+    std::vector<GSeg> S;
+    std::vector<GTile> T;
+    build_host(l, P, S, T);
+    d.ntiles = (int)T.size();
+    d.flops = l.flops;
+    if (d.ntiles) {
+      CK(cudaMalloc(&d.p, P.size() * sizeof(GProb)));
+      CK(cudaMalloc(&d.s, std::max<size_t>(1, S.size()) * sizeof(GSeg)));
+      CK(cudaMalloc(&d.t, T.size() * sizeof(GTile)));
+      CK(cudaMemcpy(d.p, P.data(), P.size() * sizeof(GProb), cudaMemcpyHostToDevice));
+      if (!S.empty()) CK(cudaMemcpy(d.s, S.data(), S.size() * sizeof(GSeg), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(d.t, T.data(), T.size() * sizeof(GTile), cudaMemcpyHostToDevice));
+    }
+    prepared_.push_back(d);
+    return (int)prepared_.size() - 1;
+  }
+  void drop_prepared() override {
+    CK(cudaStreamSynchronize(st_));
+    for (auto& d : prepared_) free_dev(d);
+    prepared_.clear();
+  }
+  void run_prepared(int h, uint64_t psi, uint64_t sig, void* stream) override {
+    const DevLaunch& d = prepared_.at(h);
+    if (!d.ntiles) return;
+    cudaStream_t s = stream ? (cudaStream_t)stream : st_;
+    launch(d.p, d.s, d.t, d.ntiles, psi, sig, s);
+  }
+  void* stream() override { return st_; }
+  void sync(void* stream) override { CK(cudaStreamSynchronize(stream ? (cudaStream_t)stream : st_)); }
+  void zero_async(uint64_t p, int64_t n, void* stream) override {
+    CK(cudaMemsetAsync(reinterpret_cast<void*>(p), 0, (size_t)n * 8,
+                       stream ? (cudaStream_t)stream : st_));
+  }
+  int64_t bytes_allocated() const override { return bytes_; }
+
+ private:
+  void launch(GProb* P, GSeg* S, GTile* T, int nt, uint64_t psi, uint64_t sig, cudaStream_t s) {
+    Bases B;
+    B.b[0] = 0;
+    B.b[1] = psi;
+    B.b[2] = sig;
+    B.b[3] = tmp_;
+    seg_gemm_f64<<<nt, 256, 0, s>>>(P, S, T, nt, B);
+    CK(cudaGetLastError());
+  }
+  void grow(void** p, size_t* cap, size_t need) {
+    if (need <= *cap) return;
+    if (*p) CK(cudaFree(*p));
+    CK(cudaMalloc(p, need));
+    *cap = need;
+  }
+  static void free_dev(DevLaunch& d) {
+    if (d.p) cudaFree(d.p);
+    if (d.s) cudaFree(d.s);
+    if (d.t) cudaFree(d.t);
+    d.p = nullptr; d.s = nullptr; d.t = nullptr;
+  }
+  int dev_;
+  cudaStream_t st_ = nullptr;
+  uint64_t tmp_ = 0;
+  int64_t tmpcap_ = 0;
+  void *sp_ = nullptr, *ss_ = nullptr, *stt_ = nullptr;
+  size_t spcap_ = 0, sscap_ = 0, stcap_ = 0;
+  std::vector<DevLaunch> prepared_;
+  int64_t bytes_ = 0;
+};
+
+Backend make_backend(int device) {
+  auto* e = new CudaExec(device);
+  return Backend{e, e};
+}
+
+}  // namespace qd
