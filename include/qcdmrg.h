@@ -95,7 +95,7 @@ typedef struct {
   int64_t device_bytes;  /* bytes allocated on the device by the context */
   int nterms;            /* operator-product terms of H_eff */
   int nlaunch;           /* kernel launches per H_eff psi */
-} qcdmrg_stats;
+} qcdmrg_stats_t;
 
 /* Create a context on cfg->device. Errors: EINVAL, ECUDA, ENOMEM. */
 int qcdmrg_create(qcdmrg_ctx** out, const qcdmrg_config* cfg);
@@ -147,7 +147,7 @@ int qcdmrg_apply_heff_dev(qcdmrg_ctx* ctx, int precision, const void* psi, void*
                           void* stream);
 
 /* Counters of the last calls. */
-int qcdmrg_stats(const qcdmrg_ctx* ctx, qcdmrg_stats* out);
+int qcdmrg_stats(const qcdmrg_ctx* ctx, qcdmrg_stats_t* out);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,160 @@
+"""Python binding of libqcdmrg (two-site DMRG H_eff.psi on B300).
+
+Argument marshalling only: every step of the computation runs inside the
+CUDA library. Importing the package does not load the library; creating a
+Context does, and fails loudly if libqcdmrg.so is missing or no CUDA device
+is usable.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libqcdmrg.so")
+
+QCDMRG_OK = 0
+U1 = 0
+FP64 = 0
+
+_ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ESTATE", -5: "ENOTCONV",
+           -6: "ETIMEOUT", -7: "EIO"}
+
+
+class QcdmrgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"qcdmrg {_ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("symmetry", ctypes.c_int), ("device", ctypes.c_int),
+                ("tmp_budget_gb", ctypes.c_double)]
+
+
+class MpsDesc(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int), ("center", ctypes.c_int),
+                ("bond_nsec", ctypes.POINTER(ctypes.c_int)),
+                ("bond_sec", ctypes.POINTER(ctypes.c_int))]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("heff_flops", ctypes.c_double), ("heff_seconds", ctypes.c_double),
+                ("env_flops", ctypes.c_double), ("env_seconds", ctypes.c_double),
+                ("psi_size", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("nterms", ctypes.c_int), ("nlaunch", ctypes.c_int)]
+
+
+EXPORTS = [
+    "qcdmrg_create", "qcdmrg_destroy", "qcdmrg_last_error", "qcdmrg_load_integrals",
+    "qcdmrg_set_target", "qcdmrg_import_mps", "qcdmrg_build_env", "qcdmrg_psi_size",
+    "qcdmrg_apply_heff", "qcdmrg_apply_heff_dev", "qcdmrg_stats",
+]
+
+_lib = None
+
+
+def load(path=None):
+    """Load the shared library (once). Raises if it is missing."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise FileNotFoundError(f"{p} not built: run __graft_entry__.build()")
+    lib = ctypes.CDLL(p)
+    P = ctypes.c_void_p
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.qcdmrg_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(Config)]
+    lib.qcdmrg_destroy.argtypes = [P]
+    lib.qcdmrg_last_error.argtypes = [P]
+    lib.qcdmrg_last_error.restype = ctypes.c_char_p
+    lib.qcdmrg_load_integrals.argtypes = [P, ctypes.c_int, dp, dp, ctypes.c_double]
+    lib.qcdmrg_set_target.argtypes = [P, ctypes.c_int, ctypes.c_int]
+    lib.qcdmrg_import_mps.argtypes = [P, ctypes.POINTER(MpsDesc), dp, ctypes.c_size_t]
+    lib.qcdmrg_build_env.argtypes = [P]
+    lib.qcdmrg_psi_size.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
+    lib.qcdmrg_apply_heff.argtypes = [P, ctypes.c_int, dp, dp]
+    lib.qcdmrg_apply_heff_dev.argtypes = [P, ctypes.c_int, P, P, P]
+    lib.qcdmrg_stats.argtypes = [P, ctypes.POINTER(Stats)]
+    for f in EXPORTS:
+        getattr(lib, f).restype = getattr(lib, f).restype or ctypes.c_int
+    lib.qcdmrg_last_error.restype = ctypes.c_char_p
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class Context:
+    """One qcdmrg context (one device, one problem)."""
+
+    def __init__(self, device=0, symmetry=U1, tmp_budget_gb=0.0, lib=None):
+        self.lib = lib or load()
+        self.h = ctypes.c_void_p()
+        cfg = Config(symmetry, device, tmp_budget_gb)
+        rc = self.lib.qcdmrg_create(ctypes.byref(self.h), ctypes.byref(cfg))
+        if rc != QCDMRG_OK:
+            raise QcdmrgError(rc, "context creation failed (no usable CUDA device?)")
+
+    def _check(self, rc):
+        if rc != QCDMRG_OK:
+            raise QcdmrgError(rc, self.lib.qcdmrg_last_error(self.h).decode())
+        return rc
+
+    def close(self):
+        if self.h:
+            self.lib.qcdmrg_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load_integrals(self, h, V, e_core=0.0):
+        h = np.ascontiguousarray(h, dtype=np.float64)
+        V = np.ascontiguousarray(V, dtype=np.float64)
+        self._check(self.lib.qcdmrg_load_integrals(self.h, h.shape[0], _dptr(h), _dptr(V), e_core))
+
+    def set_target(self, N, two_s):
+        self._check(self.lib.qcdmrg_set_target(self.h, N, two_s))
+
+    def import_mps(self, L, center, bond_nsec, bond_sec, data):
+        nsec = np.ascontiguousarray(bond_nsec, dtype=np.int32)
+        sec = np.ascontiguousarray(bond_sec, dtype=np.int32)
+        if sec.size == 0:
+            sec = np.zeros(3, dtype=np.int32)
+        data = np.ascontiguousarray(data, dtype=np.float64)
+        d = MpsDesc(L, center, nsec.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                    sec.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+        self._check(self.lib.qcdmrg_import_mps(self.h, ctypes.byref(d), _dptr(data), data.size))
+
+    def build_env(self):
+        self._check(self.lib.qcdmrg_build_env(self.h))
+
+    def psi_size(self):
+        n = ctypes.c_size_t()
+        self._check(self.lib.qcdmrg_psi_size(self.h, ctypes.byref(n)))
+        return n.value
+
+    def apply_heff(self, psi, precision=FP64):
+        psi = np.ascontiguousarray(psi, dtype=np.float64)
+        out = np.empty_like(psi)
+        self._check(self.lib.qcdmrg_apply_heff(self.h, precision, _dptr(psi), _dptr(out)))
+        return out
+
+    def apply_heff_dev(self, psi_ptr, sigma_ptr, stream=0, precision=FP64):
+        self._check(self.lib.qcdmrg_apply_heff_dev(self.h, precision, ctypes.c_void_p(psi_ptr),
+                                                   ctypes.c_void_p(sigma_ptr),
+                                                   ctypes.c_void_p(stream)))
+
+    def stats(self):
+        s = Stats()
+        self._check(self.lib.qcdmrg_stats(self.h, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in Stats._fields_}

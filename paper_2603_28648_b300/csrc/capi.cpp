@@ -36,7 +36,7 @@ struct qcdmrg_ctx {
   HeffPlan plan;
   std::vector<std::pair<int, int>> prepared;      // (stage1, stage2) handles
   uint64_t dpsi = 0, dsig = 0;
-  qcdmrg_stats st{};
+  qcdmrg_stats_t st{};
   std::string err;
 
   ~qcdmrg_ctx() { free_env(); free_mps(); if (dpsi) be.ex->release(dpsi); if (dsig) be.ex->release(dsig); delete be.ex; }
@@ -334,7 +334,7 @@ int qcdmrg_apply_heff_dev(qcdmrg_ctx* ctx, int precision, const void* psi, void*
   });
 }
 
-int qcdmrg_stats(const qcdmrg_ctx* ctx, qcdmrg_stats* out) {
+int qcdmrg_stats(const qcdmrg_ctx* ctx, qcdmrg_stats_t* out) {
   if (!ctx || !out) return QCDMRG_EINVAL;
   *out = ctx->st;
   out->device_bytes = ctx->be.pr ? ctx->be.pr->bytes_allocated() : 0;
