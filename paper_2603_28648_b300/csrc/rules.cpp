@@ -20,6 +20,7 @@
 // A product O_X O_s on X (x) site acts as (O_X P_X^{p(O_s)}) (x) O_s; a
 // product O_s O_Y on site (x) Y as (O_s P_s^{p(O_Y)}) (x) O_Y.
 #include <cmath>
+#include <map>
 #include <stdexcept>
 
 #include "core.hpp"
@@ -50,14 +51,66 @@ std::vector<Key> block_keys(bool left, int c, int L) {
 
 namespace {
 
+// Site-operator monomials: normal-ordered products of a+_up, a+_dn, a_up,
+// a_dn on one site. The 16 of them are a basis of the 4x4 matrices; every
+// site factor of a contribution is split on this basis so that the block
+// parts multiplying the same monomial can be summed once.
+struct Monos {
+  Mat4 m[16];
+  double inv[16][16];
+  Monos() {
+    const Mat4 I4 = Mat4::id();
+    Mat4 c0 = cre(0), c1 = cre(1), a0 = ann(0), a1 = ann(1);
+    Mat4 list[16] = {I4, c0, c1, a0, a1, c0 * c1, c0 * a0, c0 * a1, c1 * a0, c1 * a1, a0 * a1,
+                     c0 * c1 * a0, c0 * c1 * a1, c0 * a0 * a1, c1 * a0 * a1, c0 * c1 * a0 * a1};
+    double M[16][32];
+    for (int k = 0; k < 16; ++k) {
+      m[k] = list[k];
+      for (int e = 0; e < 16; ++e) M[e][k] = list[k].v[e];
+    }
+    for (int r = 0; r < 16; ++r)
+      for (int c = 0; c < 16; ++c) M[r][16 + c] = (r == c);
+    for (int c = 0; c < 16; ++c) {  // Gauss-Jordan with partial pivoting
+      int piv = c;
+      for (int r = c + 1; r < 16; ++r)
+        if (std::fabs(M[r][c]) > std::fabs(M[piv][c])) piv = r;
+      for (int k = 0; k < 32; ++k) std::swap(M[c][k], M[piv][k]);
+      double d = M[c][c];
+      for (int k = 0; k < 32; ++k) M[c][k] /= d;
+      for (int r = 0; r < 16; ++r)
+        if (r != c && M[r][c] != 0.0) {
+          double f = M[r][c];
+          for (int k = 0; k < 32; ++k) M[r][k] -= f * M[c][k];
+        }
+    }
+    for (int r = 0; r < 16; ++r)
+      for (int c = 0; c < 16; ++c) inv[r][c] = M[r][16 + c];
+  }
+  // coefficients x_k with o = sum_k x_k m[k]
+  void split(const Mat4& o, double x[16]) const {
+    for (int k = 0; k < 16; ++k) {
+      double s = 0;
+      for (int e = 0; e < 16; ++e) s += inv[k][e] * o.v[e];
+      x[k] = std::fabs(s) < 1e-15 ? 0.0 : s;
+    }
+  }
+};
+const Monos& monos() {
+  static Monos M;
+  return M;
+}
+
 struct Ctx {
   const EnvBlock& B;
   const Integrals& I;
   Enlarged& E;
   const ProdBasis& pb;
-  Launch mat;
-  int64_t mat_total = 0;
-  std::vector<std::pair<Key, std::vector<BRef>>> pending;  // to materialize
+  struct Pending {
+    Key key;
+    bool odd;
+    std::vector<Contrib> cs;
+  };
+  std::vector<Pending> pending;
   Ctx(const EnvBlock& b, const Integrals& i, Enlarged& e) : B(b), I(i), E(e), pb(e.pb) {}
 
   const OpView* get(Key k) const {
@@ -66,101 +119,153 @@ struct Ctx {
     return &it->second;
   }
 
-  // expand one contribution into references on the enlarged basis
-  void expand(const Contrib& c, std::vector<BRef>& out) const {
-    if (c.coef == 0.0 || c.o.zero()) return;
-    std::vector<BRef> src;
-    if (c.src) {
-      if (c.srcT) src = transpose(*c.src).blocks;
-      else src = c.src->blocks;
-    } else {
-      for (int x = 0; x < B.basis.nsec(); ++x) {
-        BRef b;
-        b.r = b.c = x;
-        b.ptr = 0;
-        b.rows = b.cols = b.ld = B.basis.dim[x];
-        src.push_back(b);
-      }
-    }
+  // expand coef * (src (x) o) into references on the enlarged basis
+  void expand(const std::vector<BRef>& src, const Mat4& o, double coef, bool par,
+              std::vector<BRef>& out) const {
+    if (coef == 0.0 || o.zero()) return;
     for (const BRef& b : src) {
       for (int i = 0; i < NSITE; ++i)
         for (int i2 = 0; i2 < NSITE; ++i2) {
-          double o = c.o(i, i2);
-          if (o == 0.0) continue;
+          double v = o(i, i2);
+          if (v == 0.0) continue;
           BRef r = b;
           double sgn = 1.0;
-          if (E.left) {
-            r.r = pb.find(b.r, i);
-            r.c = pb.find(b.c, i2);
-            if (c.par && (B.basis.q[b.c].n & 1)) sgn = -1.0;
-          } else {
-            r.r = pb.find(b.r, i);
-            r.c = pb.find(b.c, i2);
-            if (c.par && (SITE_QN[i2].n & 1)) sgn = -1.0;
+          r.r = pb.find(b.r, i);
+          r.c = pb.find(b.c, i2);
+          if (par) {
+            if (E.left) { if (B.basis.q[b.c].n & 1) sgn = -1.0; }
+            else if (SITE_QN[i2].n & 1) sgn = -1.0;
           }
-          r.sc = b.sc * c.coef * o * sgn;
+          r.sc = b.sc * coef * v * sgn;
           out.push_back(r);
         }
     }
+  }
+  std::vector<BRef> src_blocks(const OpView* src, bool T) const {
+    if (src) return T ? transpose(*src).blocks : src->blocks;
+    std::vector<BRef> v;
+    for (int x = 0; x < B.basis.nsec(); ++x) {
+      BRef b;
+      b.r = b.c = x;
+      b.ptr = 0;
+      b.rows = b.cols = b.ld = B.basis.dim[x];
+      v.push_back(b);
+    }
+    return v;
   }
 
   void view(Key k, const std::vector<Contrib>& cs, bool odd) {
     OpView v;
     v.odd = odd;
-    for (auto& c : cs) expand(c, v.blocks);
+    for (auto& c : cs) expand(src_blocks(c.src, c.srcT), c.o, c.coef, c.par, v.blocks);
     if (!v.blocks.empty()) E.ops[k] = v;
   }
 
-  void materialize(Key k, const std::vector<Contrib>& cs) {
-    std::vector<BRef> refs;
-    for (auto& c : cs) expand(c, refs);
-    if (refs.empty()) return;
-    pending.emplace_back(k, std::move(refs));
+  void materialize(Key k, const std::vector<Contrib>& cs, bool odd) {
+    pending.push_back({k, odd, cs});
   }
 
-  void finish(Executor& ex, const std::map<Key, bool>& odd, double* flops) {
-    // group by (r, c), allocate and emit gather-AXPY problems
-    struct G { std::map<std::pair<int, int>, std::vector<const BRef*>> g; };
-    std::vector<G> groups(pending.size());
-    int64_t total = 0;
+  // Group every pending operator's contributions by (site monomial, parity
+  // flag). A group with one block operator stays a reference; a group with
+  // several is summed once into new storage on the block basis.
+  void finish(Executor& ex) {
+    const Monos& M = monos();
+    struct Item { const OpView* src; bool T; double coef; };
+    struct Group { Mat4 o; bool par; std::vector<Item> items; };
+    struct Plan { std::vector<Group> groups; };
+    std::vector<Plan> plans(pending.size());
     for (size_t n = 0; n < pending.size(); ++n) {
-      for (const BRef& b : pending[n].second) groups[n].g[{b.r, b.c}].push_back(&b);
-      for (auto& kv : groups[n].g)
-        total += (int64_t)pb.subs[kv.first.first].dim * pb.subs[kv.first.second].dim;
-    }
-    if (!total) return;
-    uint64_t store = ex.alloc(total);
-    E.owned.push_back(store);
-    int64_t pos = 0;
-    Launch l;
-    for (size_t n = 0; n < pending.size(); ++n) {
-      OpView v;
-      v.odd = odd.at(pending[n].first);
-      for (auto& kv : groups[n].g) {
-        int r = kv.first.first, c = kv.first.second;
-        int m = pb.subs[r].dim, nn = pb.subs[c].dim;
-        Prob p;
-        p.c = store + 8ull * pos; p.cbuf = B_ABS;
-        p.m = m; p.n = nn; p.ldc = nn; p.beta = 0;
-        p.seg0 = (int)l.segs.size(); p.nseg = 0;
-        for (const BRef* b : kv.second) {
-          Seg s;
-          s.a = 0; s.abuf = B_ABS; s.k = m; s.sc = b->sc;
-          if (b->ident()) { s.b = 0; s.bbuf = B_ABS; }
-          else { s.b = b->ptr; s.bbuf = B_ABS; s.ldb = b->ld; s.tb = b->tr ? 1 : 0; }
-          l.segs.push_back(s);
-          p.nseg++;
+      std::map<std::pair<int, int>, int> gi;   // (monomial or -1-identity-slot, par) -> group
+      auto& G = plans[n].groups;
+      for (const Contrib& c : pending[n].cs) {
+        if (c.coef == 0.0 || c.o.zero()) continue;
+        double x[16];
+        M.split(c.o, x);
+        for (int k = 0; k < 16; ++k) {
+          if (x[k] == 0.0) continue;
+          auto key = std::make_pair(k, (int)c.par);
+          auto it = gi.find(key);
+          int g;
+          if (it == gi.end()) {
+            g = (int)G.size();
+            gi[key] = g;
+            G.push_back({M.m[k], c.par, {}});
+          } else {
+            g = it->second;
+          }
+          bool merged = false;
+          for (auto& itm : G[g].items)
+            if (itm.src == c.src && itm.T == c.srcT) { itm.coef += c.coef * x[k]; merged = true; break; }
+          if (!merged) G[g].items.push_back({c.src, c.srcT, c.coef * x[k]});
         }
-        l.probs.push_back(p);
-        BRef o;
-        o.r = r; o.c = c; o.ptr = p.c; o.rows = m; o.cols = nn; o.ld = nn; o.tr = false; o.sc = 1.0;
-        v.blocks.push_back(o);
-        pos += (int64_t)m * nn;
       }
-      E.ops[pending[n].first] = v;
     }
-    ex.run(l, 0, 0);
-    (void)flops;
+    // storage for summed groups
+    int64_t total = 0;
+    struct Mat { size_t n, g; std::map<std::pair<int, int>, std::pair<int64_t, std::pair<int, int>>> blk; };
+    std::vector<Mat> mats;
+    for (size_t n = 0; n < plans.size(); ++n)
+      for (size_t g = 0; g < plans[n].groups.size(); ++g) {
+        auto& grp = plans[n].groups[g];
+        if (grp.items.size() < 2) continue;
+        Mat mt{n, g, {}};
+        for (auto& itm : grp.items)
+          for (const BRef& b : src_blocks(itm.src, itm.T)) {
+            auto key = std::make_pair(b.r, b.c);
+            if (!mt.blk.count(key)) {
+              mt.blk[key] = {total, {b.rows, b.cols}};
+              total += (int64_t)b.rows * b.cols;
+            }
+          }
+        mats.push_back(mt);
+      }
+    uint64_t store = total ? ex.alloc(total) : 0;
+    if (store) E.owned.push_back(store);
+    Launch l;
+    std::map<std::pair<size_t, size_t>, std::vector<BRef>> summed;
+    for (auto& mt : mats) {
+      auto& grp = plans[mt.n].groups[mt.g];
+      std::map<std::pair<int, int>, std::vector<Seg>> segs;
+      for (auto& itm : grp.items)
+        for (const BRef& b : src_blocks(itm.src, itm.T)) {
+          Seg s;
+          s.a = 0; s.abuf = B_ABS; s.k = b.rows; s.sc = itm.coef * b.sc;
+          if (b.ident()) { s.b = 0; s.bbuf = B_ABS; }
+          else { s.b = b.ptr; s.bbuf = B_ABS; s.ldb = b.ld; s.tb = b.tr ? 1 : 0; }
+          segs[{b.r, b.c}].push_back(s);
+        }
+      std::vector<BRef> refs;
+      for (auto& kv : mt.blk) {
+        Prob p;
+        p.c = store + 8ull * kv.second.first; p.cbuf = B_ABS;
+        p.m = kv.second.second.first; p.n = kv.second.second.second; p.ldc = p.n; p.beta = 0;
+        p.seg0 = (int)l.segs.size();
+        auto& sv = segs[kv.first];
+        p.nseg = (int)sv.size();
+        for (auto& s : sv) l.segs.push_back(s);
+        l.probs.push_back(p);
+        BRef r;
+        r.r = kv.first.first; r.c = kv.first.second; r.ptr = p.c;
+        r.rows = p.m; r.cols = p.n; r.ld = p.n; r.tr = false; r.sc = 1.0;
+        refs.push_back(r);
+      }
+      summed[{mt.n, mt.g}] = refs;
+    }
+    if (!l.empty()) ex.run(l, 0, 0);
+    for (size_t n = 0; n < plans.size(); ++n) {
+      OpView v;
+      v.odd = pending[n].odd;
+      for (size_t g = 0; g < plans[n].groups.size(); ++g) {
+        auto& grp = plans[n].groups[g];
+        if (grp.items.size() >= 2) {
+          expand(summed[{n, g}], grp.o, 1.0, grp.par, v.blocks);
+        } else if (grp.items.size() == 1) {
+          auto& itm = grp.items[0];
+          expand(src_blocks(itm.src, itm.T), grp.o, itm.coef, grp.par, v.blocks);
+        }
+      }
+      if (!v.blocks.empty()) E.ops[pending[n].key] = v;
+    }
   }
 };
 
@@ -215,7 +320,6 @@ void enlarge(const EnvBlock& B, const Integrals& I, Executor& ex, Enlarged& E, d
   E.pb = make_prod(B.basis, B.left);
   Ctx x(B, I, E);
   const Mat4 I4 = Mat4::id();
-  std::map<Key, bool> odd;
   auto nonnull = [](const OpView* p) { return p != nullptr; };
   (void)nonnull;
   if (B.left) {
@@ -285,8 +389,7 @@ void enlarge(const EnvBlock& B, const Integrals& I, Executor& ex, Enlarged& E, d
           }
         }
       cs.push_back(C_(nullptr, false, site_three(I, m, sm), 1.0, true));
-      odd[Key(F_S, m)] = true;
-      x.materialize(Key(F_S, m), cs);
+      x.materialize(Key(F_S, m), cs, true);
     }
     // H'
     {
@@ -321,8 +424,7 @@ void enlarge(const EnvBlock& B, const Integrals& I, Executor& ex, Enlarged& E, d
               for (int b = 0; b < 2; ++b) Q = Q + cre(a) * ann(b) * I.q(i, sm[a], sm[b], l);
             cs.push_back(C_(Bil, false, Q, 1.0, false));
           }
-      odd[Key(F_H)] = false;
-      x.materialize(Key(F_H), cs);
+      x.materialize(Key(F_H), cs, false);
     }
   } else {
     const int c = B.cut - 1;      // site p = c, Y = [c+1, L)
@@ -349,8 +451,7 @@ void enlarge(const EnvBlock& B, const Integrals& I, Executor& ex, Enlarged& E, d
         for (int a = 0; a < 2; ++a)
           for (int b = 0; b < 2; ++b) P = P + ann(a) * ann(b) * (0.5 * I.w(i, j, sm[a], sm[b]));
         cs.push_back(C_(nullptr, false, P, 1.0, false));
-        odd[Key(F_P, i, j)] = false;
-        x.materialize(Key(F_P, i, j), cs);
+        x.materialize(Key(F_P, i, j), cs, false);
       }
     // Q'_il, i, l < 2c
     for (int i = 0; i < 2 * c; ++i)
@@ -370,8 +471,7 @@ void enlarge(const EnvBlock& B, const Integrals& I, Executor& ex, Enlarged& E, d
         for (int a = 0; a < 2; ++a)
           for (int b = 0; b < 2; ++b) Q = Q + cre(a) * ann(b) * I.q(i, sm[a], sm[b], l);
         cs.push_back(C_(nullptr, false, Q, 1.0, false));
-        odd[Key(F_Q, i, l)] = false;
-        x.materialize(Key(F_Q, i, l), cs);
+        x.materialize(Key(F_Q, i, l), cs, false);
       }
     // S'_m, m < 2c
     for (int m = 0; m < 2 * c; ++m) {
@@ -397,8 +497,7 @@ void enlarge(const EnvBlock& B, const Integrals& I, Executor& ex, Enlarged& E, d
             if (w2 != 0.0) cs.push_back(C_(C, false, ann(a) * ann(b), w2, true));
           }
       cs.push_back(C_(nullptr, false, site_three(I, m, sm), 1.0, false));
-      odd[Key(F_S, m)] = true;
-      x.materialize(Key(F_S, m), cs);
+      x.materialize(Key(F_S, m), cs, true);
     }
     // H'
     {
@@ -424,11 +523,11 @@ void enlarge(const EnvBlock& B, const Integrals& I, Executor& ex, Enlarged& E, d
       for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b)
           if (auto Q = x.get(Key(F_Q, sm[a], sm[b]))) cs.push_back(C_(Q, false, cre(a) * ann(b), 1.0, false));
-      odd[Key(F_H)] = false;
-      x.materialize(Key(F_H), cs);
+      x.materialize(Key(F_H), cs, false);
     }
   }
-  x.finish(ex, odd, flops);
+  x.finish(ex);
+  (void)flops;
 }
 
 }  // namespace qd
