@@ -125,6 +125,24 @@ int qcdmrg_import_mps(qcdmrg_ctx* ctx, const qcdmrg_mps_desc* desc, const double
                       size_t n);
 
 /*
+ * Random initial MPS at bond dimension D around the centre (center,
+ * center+1): sector dimensions from the sector rule (block-state counts,
+ * Gaussian weights around N b / L and Sz = 0, water filling with caps), i.i.d.
+ * normal entries from a counter-based generator (splitmix64 of seed and
+ * element index, Box-Muller), each product-sector matrix made orthonormal by
+ * QR on the device, and a normalised random two-site wavefunction. Errors:
+ * ESTATE (integrals or target missing), EINVAL.
+ */
+int qcdmrg_init_mps(qcdmrg_ctx* ctx, int D, uint64_t seed, int center);
+
+/* Sectors of bond b of the current MPS as (n, two_sz, dim) triples; sec may be
+ * NULL to query *nsec only; cap is the length of sec in ints. */
+int qcdmrg_get_bond(const qcdmrg_ctx* ctx, int bond, int* nsec, int* sec, int cap);
+
+/* Copy the current two-site wavefunction (n = its size). */
+int qcdmrg_get_psi(const qcdmrg_ctx* ctx, double* out, size_t n);
+
+/*
  * Renormalize the left block up to the centre and the right block down to
  * it (the operator renormalization of every truncation step, replayed for
  * the imported tensors), enlarge both by their dot site and build the

@@ -49,7 +49,8 @@ class Stats(ctypes.Structure):
 EXPORTS = [
     "qcdmrg_create", "qcdmrg_destroy", "qcdmrg_last_error", "qcdmrg_load_integrals",
     "qcdmrg_set_target", "qcdmrg_import_mps", "qcdmrg_build_env", "qcdmrg_psi_size",
-    "qcdmrg_apply_heff", "qcdmrg_apply_heff_dev", "qcdmrg_stats",
+    "qcdmrg_apply_heff", "qcdmrg_apply_heff_dev", "qcdmrg_stats", "qcdmrg_init_mps",
+    "qcdmrg_get_bond", "qcdmrg_get_psi",
 ]
 
 _lib = None
@@ -78,6 +79,10 @@ def load(path=None):
     lib.qcdmrg_apply_heff.argtypes = [P, ctypes.c_int, dp, dp]
     lib.qcdmrg_apply_heff_dev.argtypes = [P, ctypes.c_int, P, P, P]
     lib.qcdmrg_stats.argtypes = [P, ctypes.POINTER(Stats)]
+    lib.qcdmrg_init_mps.argtypes = [P, ctypes.c_int, ctypes.c_uint64, ctypes.c_int]
+    ip = ctypes.POINTER(ctypes.c_int)
+    lib.qcdmrg_get_bond.argtypes = [P, ctypes.c_int, ip, ip, ctypes.c_int]
+    lib.qcdmrg_get_psi.argtypes = [P, dp, ctypes.c_size_t]
     for f in EXPORTS:
         getattr(lib, f).restype = getattr(lib, f).restype or ctypes.c_int
     lib.qcdmrg_last_error.restype = ctypes.c_char_p
@@ -134,6 +139,22 @@ class Context:
         d = MpsDesc(L, center, nsec.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                     sec.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
         self._check(self.lib.qcdmrg_import_mps(self.h, ctypes.byref(d), _dptr(data), data.size))
+
+    def init_mps(self, D, seed, center):
+        self._check(self.lib.qcdmrg_init_mps(self.h, D, seed, center))
+
+    def bond(self, b):
+        n = ctypes.c_int()
+        self._check(self.lib.qcdmrg_get_bond(self.h, b, ctypes.byref(n), None, 0))
+        buf = (ctypes.c_int * max(1, 3 * n.value))()
+        self._check(self.lib.qcdmrg_get_bond(self.h, b, ctypes.byref(n), buf, 3 * n.value))
+        return {(buf[3 * i], buf[3 * i + 1]): buf[3 * i + 2] for i in range(n.value)}
+
+    def psi(self):
+        n = self.psi_size()
+        out = np.empty(n)
+        self._check(self.lib.qcdmrg_get_psi(self.h, _dptr(out), n))
+        return out
 
     def build_env(self):
         self._check(self.lib.qcdmrg_build_env(self.h))

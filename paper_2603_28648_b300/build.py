@@ -4,7 +4,7 @@ import os
 import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRC = ["csrc/core.cpp", "csrc/rules.cpp", "csrc/capi.cpp", "csrc/kernels.cu"]
+SRC = ["csrc/core.cpp", "csrc/rules.cpp", "csrc/init.cpp", "csrc/capi.cpp", "csrc/kernels.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -12,7 +12,7 @@ def build(verbose=False):
     out = os.path.join(HERE, "libqcdmrg.so")
     cmd = (["nvcc", "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-shared"] + ARCH +
            ["-Xptxas", "-v" if verbose else "-O3"] + [os.path.join(HERE, s) for s in SRC] +
-           ["-o", out, "-lcudart"])
+           ["-o", out, "-lcudart", "-lcusolver"])
     subprocess.run(cmd, check=True, cwd=HERE)
     return out
 

@@ -1,4 +1,5 @@
 // C ABI: context, integral and MPS import, environment build, H_eff psi.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -232,6 +233,126 @@ int qcdmrg_import_mps(qcdmrg_ctx* ctx, const qcdmrg_mps_desc* d, const double* d
   });
 }
 
+int qcdmrg_init_mps(qcdmrg_ctx* ctx, int D, uint64_t seed, int center) {
+  return guard(ctx, [&]() {
+    if (!ctx->have_int || !ctx->have_target) throw Fail{QCDMRG_ESTATE, "load integrals and target first"};
+    const int L = ctx->I.L;
+    if (D < 1) throw Fail{QCDMRG_EINVAL, "D must be positive"};
+    if (center < 0 || center + 1 >= L) throw Fail{QCDMRG_EINVAL, "centre out of range"};
+    ctx->free_env();
+    ctx->free_mps();
+    auto st = mps_structure(L, ctx->N, ctx->two_s, D);
+    for (int b = 1; b < L; ++b)
+      if (st[b].empty()) throw Fail{QCDMRG_EINVAL, "target not reachable: empty bond"};
+    std::vector<Basis> bonds(L + 1);
+    for (int b = 0; b <= center; ++b)
+      for (auto& kv : st[b]) bonds[b].add(kv.first, kv.second);
+    for (int b = center + 2; b <= L; ++b)
+      for (auto& kv : st[L - b]) bonds[b].add(kv.first, kv.second);
+    Executor& ex = *ctx->be.ex;
+    ctx->site.assign(L, 0);
+    ctx->site_off.assign(L, {});
+    ctx->site_nb.assign(L, {});
+    auto mix = [](uint64_t a, uint64_t b) {
+      uint64_t x = a ^ (b + 0x9E3779B97F4A7C15ull + (a << 6) + (a >> 2));
+      x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+      x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+      return x ^ (x >> 31);
+    };
+    for (int p = 0; p < L; ++p) {
+      if (p == center || p == center + 1) continue;
+      const bool left = p < center;
+      const Basis& from = left ? bonds[p] : bonds[p + 1];
+      const Basis& to = left ? bonds[p + 1] : bonds[p];
+      ProdBasis pb = make_prod(from, left);
+      std::vector<int64_t> so(pb.prod.nsec(), -1);
+      std::vector<int> nb(pb.prod.nsec(), -1);
+      int64_t tot = 0, maxblk = 0;
+      for (int q = 0; q < pb.prod.nsec(); ++q) {
+        int t = to.find(pb.prod.q[q]);
+        if (t < 0) continue;
+        so[q] = tot;
+        nb[q] = t;
+        int64_t sz = (int64_t)pb.prod.dim[q] * to.dim[t];
+        tot += sz;
+        maxblk = std::max(maxblk, sz);
+      }
+      uint64_t dev = ex.alloc(tot);
+      uint64_t scratch = left ? ex.alloc(maxblk) : 0;
+      for (int q = 0; q < pb.prod.nsec(); ++q) {
+        if (nb[q] < 0) continue;
+        int rows = pb.prod.dim[q], d = to.dim[nb[q]];
+        uint64_t sd = mix(mix(seed, (uint64_t)p), (uint64_t)q);
+        if (left) {
+          // orthonormal columns of a rows x d matrix, stored row-major
+          ex.randn(scratch, (int64_t)rows * d, sd);
+          ex.orthonormal_cols(scratch, rows, d);
+          Launch l;
+          Prob pr;
+          pr.c = dev + 8ull * so[q]; pr.m = rows; pr.n = d; pr.ldc = d; pr.nseg = 1;
+          Seg g;
+          g.a = 0; g.b = scratch; g.ldb = rows; g.tb = 1; g.k = rows;
+          l.segs.push_back(g);
+          l.probs.push_back(pr);
+          ex.run(l, 0, 0);
+        } else {
+          // orthonormal rows of a d x cols matrix = orthonormal columns of its
+          // column-major transpose
+          uint64_t dst = dev + 8ull * so[q];
+          ex.randn(dst, (int64_t)rows * d, sd);
+          ex.orthonormal_cols(dst, rows, d);
+        }
+      }
+      if (scratch) ex.release(scratch);
+      ctx->site[p] = dev;
+      ctx->site_off[p] = so;
+      ctx->site_nb[p] = nb;
+    }
+    ProdBasis Lp = make_prod(bonds[center], true), Rp = make_prod(bonds[center + 2], false);
+    PsiLayout lay = make_psi_layout(Lp, Rp, QN{ctx->N, ctx->two_s});
+    uint64_t tp = ex.alloc(std::max<int64_t>(1, lay.size));
+    ex.randn(tp, lay.size, mix(seed, 0xC0FFEEull));
+    double nrm = std::sqrt(ex.dot(tp, tp, lay.size));
+    ex.scale(tp, 1.0 / nrm, lay.size);
+    ctx->psi0.resize(lay.size);
+    ex.download(ctx->psi0.data(), tp, lay.size);
+    ex.release(tp);
+    ctx->bonds = bonds;
+    ctx->L = L;
+    ctx->center = center;
+    return QCDMRG_OK;
+  });
+}
+
+int qcdmrg_get_bond(const qcdmrg_ctx* cctx, int bond, int* nsec, int* sec, int cap) {
+  qcdmrg_ctx* ctx = const_cast<qcdmrg_ctx*>(cctx);
+  return guard(ctx, [&]() {
+    if (ctx->center < 0) throw Fail{QCDMRG_ESTATE, "no MPS"};
+    if (bond < 0 || bond > ctx->L || !nsec) throw Fail{QCDMRG_EINVAL, "bad bond"};
+    const Basis& b = ctx->bonds[bond];
+    *nsec = b.nsec();
+    if (sec) {
+      if (cap < 3 * b.nsec()) throw Fail{QCDMRG_EINVAL, "sector buffer too small"};
+      for (int i = 0; i < b.nsec(); ++i) {
+        sec[3 * i] = b.q[i].n;
+        sec[3 * i + 1] = b.q[i].s;
+        sec[3 * i + 2] = b.dim[i];
+      }
+    }
+    return QCDMRG_OK;
+  });
+}
+
+int qcdmrg_get_psi(const qcdmrg_ctx* cctx, double* out, size_t n) {
+  qcdmrg_ctx* ctx = const_cast<qcdmrg_ctx*>(cctx);
+  return guard(ctx, [&]() {
+    if (ctx->center < 0) throw Fail{QCDMRG_ESTATE, "no MPS"};
+    if (!out || n != ctx->psi0.size()) throw Fail{QCDMRG_EINVAL, "output size differs from the wavefunction"};
+    std::copy(ctx->psi0.begin(), ctx->psi0.end(), out);
+    return QCDMRG_OK;
+  });
+}
+
 int qcdmrg_build_env(qcdmrg_ctx* ctx) {
   return guard(ctx, [&]() {
     if (ctx->center < 0) throw Fail{QCDMRG_ESTATE, "import an MPS first"};
@@ -293,8 +414,8 @@ int qcdmrg_build_env(qcdmrg_ctx* ctx) {
 
 int qcdmrg_psi_size(const qcdmrg_ctx* ctx, size_t* n) {
   if (!ctx || !n) return QCDMRG_EINVAL;
-  if (!ctx->have_env) return QCDMRG_ESTATE;
-  *n = (size_t)ctx->lay.size;
+  if (ctx->center < 0) return QCDMRG_ESTATE;
+  *n = ctx->psi0.size();
   return QCDMRG_OK;
 }
 

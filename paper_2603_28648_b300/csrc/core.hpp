@@ -131,6 +131,14 @@ struct Executor {
   virtual void upload(uint64_t dst, const double* h, int64_t n) = 0;
   virtual void download(double* h, uint64_t src, int64_t n) = 0;
   virtual void zero(uint64_t p, int64_t n) = 0;
+  // i.i.d. N(0,1) numbers from a counter-based generator (splitmix64 of
+  // seed and element index, Box-Muller)
+  virtual void randn(uint64_t p, int64_t n, uint64_t seed) = 0;
+  // in place: the column-major rows x cols matrix gets orthonormal columns
+  // (QR, rows >= cols)
+  virtual void orthonormal_cols(uint64_t p, int rows, int cols) = 0;
+  virtual double dot(uint64_t x, uint64_t y, int64_t n) = 0;
+  virtual void scale(uint64_t x, double a, int64_t n) = 0;
 };
 
 // Integrals; spin-orbital form t_kl, w_ijkl with k = 2p + sigma.
@@ -187,6 +195,9 @@ struct EnvBlock {
   std::map<Key, OpView> ops;
   std::vector<uint64_t> owned;
 };
+
+// Sector rule of the initial MPS (left labels, bonds 0..L).
+std::vector<std::map<QN, int>> mps_structure(int L, int N, int two_s, int D);
 
 // Op-key list of a block at a cut (left-normal / right-complementary layout).
 std::vector<Key> block_keys(bool left, int cut, int L);

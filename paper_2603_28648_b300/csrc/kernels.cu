@@ -8,8 +8,10 @@
 // owns one 64x64 output tile and loops over all segments of its problem, so
 // no output is written by two CTAs and no atomics are needed.
 #include <cuda_runtime.h>
+#include <cusolverDn.h>
 
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <stdexcept>
 #include <string>
@@ -157,6 +159,47 @@ __global__ void __launch_bounds__(256) seg_gemm_f64(const GProb* __restrict__ pr
 }
 
 // ---------------------------------------------------------------------------
+// Vector kernels (initial MPS, norms).
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+__global__ void randn_kernel(double* p, long long n, unsigned long long seed) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    unsigned long long z1 = splitmix64(seed ^ splitmix64((unsigned long long)i));
+    unsigned long long z2 = splitmix64(z1);
+    double u1 = ((z1 >> 11) + 1.0) * 0x1.0p-53;   // (0, 1]
+    double u2 = (z2 >> 11) * 0x1.0p-53;           // [0, 1)
+    p[i] = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+  }
+}
+
+__global__ void dot_partial(const double* x, const double* y, long long n, double* part) {
+  __shared__ double sh[256];
+  double s = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    s = fma(x[i], y[i], s);
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void scale_kernel(double* x, double a, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] *= a;
+}
+
+// ---------------------------------------------------------------------------
 struct DevLaunch {
   GProb* p = nullptr;
   GSeg* s = nullptr;
@@ -201,6 +244,10 @@ class CudaExec : public Executor, public PreparedRunner {
     if (sp_) cudaFree(sp_);
     if (ss_) cudaFree(ss_);
     if (stt_) cudaFree(stt_);
+    if (part_) cudaFree(part_);
+    if (work_) cudaFree(work_);
+    if (info_) cudaFree(info_);
+    if (sol_) cusolverDnDestroy(sol_);
     cudaStreamDestroy(st_);
   }
   uint64_t alloc(int64_t n) override {
@@ -254,6 +301,62 @@ class CudaExec : public Executor, public PreparedRunner {
   }
   void zero(uint64_t p, int64_t n) override {
     CK(cudaMemsetAsync(reinterpret_cast<void*>(p), 0, (size_t)n * 8, st_));
+  }
+  void randn(uint64_t p, int64_t n, uint64_t seed) override {
+    if (n <= 0) return;
+    int blocks = (int)std::min<int64_t>((n + 255) / 256, 148 * 16);
+    randn_kernel<<<blocks, 256, 0, st_>>>(reinterpret_cast<double*>(p), n, seed);
+    CK(cudaGetLastError());
+  }
+  void orthonormal_cols(uint64_t p, int rows, int cols) override {
+    if (rows < cols) throw std::runtime_error("orthonormal_cols: rows < cols");
+    if (!sol_) {
+      if (cusolverDnCreate(&sol_) != CUSOLVER_STATUS_SUCCESS) throw std::runtime_error("CUDA: cusolverDnCreate failed");
+      cusolverDnSetStream(sol_, st_);
+      CK(cudaMalloc(&info_, sizeof(int)));
+    }
+    double* A = reinterpret_cast<double*>(p);
+    int l1 = 0, l2 = 0;
+    if (cusolverDnDgeqrf_bufferSize(sol_, rows, cols, A, rows, &l1) != CUSOLVER_STATUS_SUCCESS ||
+        cusolverDnDorgqr_bufferSize(sol_, rows, cols, cols, A, rows, (double*)tau_, &l2) != CUSOLVER_STATUS_SUCCESS)
+      throw std::runtime_error("CUDA: cusolver buffer query failed");
+    size_t need = (size_t)std::max(l1, l2) + cols;
+    if (need > work_cap_) {
+      CK(cudaStreamSynchronize(st_));
+      if (work_) CK(cudaFree(work_));
+      CK(cudaMalloc(&work_, need * 8));
+      work_cap_ = need;
+    }
+    double* tau = (double*)work_;
+    double* wk = tau + cols;
+    int lw = (int)(work_cap_ - cols);
+    if (cusolverDnDgeqrf(sol_, rows, cols, A, rows, tau, wk, lw, info_) != CUSOLVER_STATUS_SUCCESS ||
+        cusolverDnDorgqr(sol_, rows, cols, cols, A, rows, tau, wk, lw, info_) != CUSOLVER_STATUS_SUCCESS)
+      throw std::runtime_error("CUDA: cusolver QR failed");
+    int info = 0;
+    CK(cudaMemcpyAsync(&info, info_, sizeof(int), cudaMemcpyDeviceToHost, st_));
+    CK(cudaStreamSynchronize(st_));
+    if (info != 0) throw std::runtime_error("CUDA: QR reported info " + std::to_string(info));
+  }
+  double dot(uint64_t x, uint64_t y, int64_t n) override {
+    if (n <= 0) return 0.0;
+    const int nb = 1024;
+    grow(&part_, &part_cap_, nb * sizeof(double));
+    dot_partial<<<nb, 256, 0, st_>>>(reinterpret_cast<const double*>(x), reinterpret_cast<const double*>(y), n,
+                                      (double*)part_);
+    CK(cudaGetLastError());
+    double h[1024];
+    CK(cudaMemcpyAsync(h, part_, nb * sizeof(double), cudaMemcpyDeviceToHost, st_));
+    CK(cudaStreamSynchronize(st_));
+    double s = 0;
+    for (int i = 0; i < nb; ++i) s += h[i];
+    return s;
+  }
+  void scale(uint64_t x, double a, int64_t n) override {
+    if (n <= 0) return;
+    int blocks = (int)std::min<int64_t>((n + 255) / 256, 148 * 16);
+    scale_kernel<<<blocks, 256, 0, st_>>>(reinterpret_cast<double*>(x), a, n);
+    CK(cudaGetLastError());
   }
 
   // prepared launches (uploaded once, replayed on any psi / sigma)
@@ -325,6 +428,13 @@ class CudaExec : public Executor, public PreparedRunner {
   size_t spcap_ = 0, sscap_ = 0, stcap_ = 0;
   std::vector<DevLaunch> prepared_;
   int64_t bytes_ = 0;
+  cusolverDnHandle_t sol_ = nullptr;
+  int* info_ = nullptr;
+  void* work_ = nullptr;
+  size_t work_cap_ = 0;
+  void* tau_ = nullptr;
+  void* part_ = nullptr;
+  size_t part_cap_ = 0;
 };
 
 Backend make_backend(int device) {
