@@ -1,0 +1,37 @@
+"""Host-side checks of the C ABI: the library builds, loads and exports every
+function the header declares; no compute calls (no GPU here)."""
+import ctypes
+import subprocess
+
+import pytest
+
+from tests._lib import ensure_built, header_functions, HEADER
+
+
+def test_library_exports_every_declared_symbol():
+    path = ensure_built()
+    lib = ctypes.CDLL(path)
+    names = header_functions()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_lists_the_header():
+    import paper_2603_28648_b300 as qd
+    assert sorted(qd.EXPORTS) == header_functions()
+
+
+def test_create_without_device_fails_cleanly():
+    import paper_2603_28648_b300 as qd
+    from tests._lib import cuda_available
+    if cuda_available():
+        pytest.skip("a device is present")
+    ensure_built()
+    with pytest.raises(qd.QcdmrgError):
+        qd.Context()
+
+
+def test_header_compiles_as_c():
+    r = subprocess.run(["gcc", "-fsyntax-only", "-x", "c", HEADER], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
