@@ -17,8 +17,8 @@
  *   - The library owns all device memory, the operators and the MPS. Caller
  *     arrays are copied on input; output arrays are caller-allocated.
  *   - Pointers are host pointers unless the function name ends in _dev; _dev
- *     functions take device pointers and a cudaStream_t (NULL: the context's
- *     stream).
+ *     functions take device pointers and a cudaStream_t on which the work is
+ *     enqueued (NULL is the CUDA legacy default stream, as everywhere in CUDA).
  *   - Dense arrays are row-major FP64. A context is not thread-safe;
  *     separate contexts are independent.
  *   - Hamiltonian: H = sum_pq h_pq E_pq + 1/2 sum_pqrs V_pqrs (E_pq E_rs -
@@ -159,8 +159,9 @@ int qcdmrg_psi_size(const qcdmrg_ctx* ctx, size_t* n);
  */
 int qcdmrg_apply_heff(qcdmrg_ctx* ctx, int precision, const double* psi, double* sigma);
 
-/* Same on device arrays, enqueued on stream (NULL: context stream); returns
- * after enqueueing. psi and sigma must not overlap. */
+/* Same on device arrays, enqueued on stream (a cudaStream_t; NULL is the
+ * legacy default stream); returns after enqueueing. psi and sigma must not
+ * overlap and must stay alive until the stream reaches the work. */
 int qcdmrg_apply_heff_dev(qcdmrg_ctx* ctx, int precision, const void* psi, void* sigma,
                           void* stream);
 

@@ -436,8 +436,9 @@ int qcdmrg_apply_heff(qcdmrg_ctx* ctx, int precision, const double* psi, double*
     Executor& ex = *ctx->be.ex;
     ex.upload(ctx->dpsi, psi, ctx->lay.size);
     auto t0 = std::chrono::steady_clock::now();
-    heff_dev(ctx, ctx->dpsi, ctx->dsig, nullptr);
-    ctx->be.pr->sync(nullptr);
+    void* st = ctx->be.pr->stream();
+    heff_dev(ctx, ctx->dpsi, ctx->dsig, st);
+    ctx->be.pr->sync(st);
     auto t1 = std::chrono::steady_clock::now();
     ctx->st.heff_seconds = std::chrono::duration<double>(t1 - t0).count();
     ex.download(sigma, ctx->dsig, ctx->lay.size);

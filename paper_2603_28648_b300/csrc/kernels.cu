@@ -387,14 +387,12 @@ class CudaExec : public Executor, public PreparedRunner {
   void run_prepared(int h, uint64_t psi, uint64_t sig, void* stream) override {
     const DevLaunch& d = prepared_.at(h);
     if (!d.ntiles) return;
-    cudaStream_t s = stream ? (cudaStream_t)stream : st_;
-    launch(d.p, d.s, d.t, d.ntiles, psi, sig, s);
+    launch(d.p, d.s, d.t, d.ntiles, psi, sig, (cudaStream_t)stream);
   }
   void* stream() override { return st_; }
-  void sync(void* stream) override { CK(cudaStreamSynchronize(stream ? (cudaStream_t)stream : st_)); }
+  void sync(void* stream) override { CK(cudaStreamSynchronize((cudaStream_t)stream)); }
   void zero_async(uint64_t p, int64_t n, void* stream) override {
-    CK(cudaMemsetAsync(reinterpret_cast<void*>(p), 0, (size_t)n * 8,
-                       stream ? (cudaStream_t)stream : st_));
+    CK(cudaMemsetAsync(reinterpret_cast<void*>(p), 0, (size_t)n * 8, (cudaStream_t)stream));
   }
   int64_t bytes_allocated() const override { return bytes_; }
 
