@@ -35,7 +35,7 @@ def parse():
     ap.add_argument("--D", type=int, default=1024)
     ap.add_argument("--L", type=int, default=36)
     ap.add_argument("--N", type=int, default=54)
-    ap.add_argument("--precision", default="fp64", choices=["fp64"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "tf32", "bf16", "bf16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -206,8 +206,10 @@ def run_ours(args, rank, world, local):
     sig = torch.empty_like(psi)
     stream = torch.cuda.current_stream()
 
+    prec = qd.PRECISIONS[args.precision]
+
     def step():
-        ctx.apply_heff_dev(psi.data_ptr(), sig.data_ptr(), stream.cuda_stream)
+        ctx.apply_heff_dev(psi.data_ptr(), sig.data_ptr(), stream.cuda_stream, prec)
 
     for _ in range(args.warmup):
         step()

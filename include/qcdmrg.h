@@ -46,8 +46,12 @@ extern "C" {
 /* symmetry */
 #define QCDMRG_U1 0 /* U(1)xU(1): sector labels (N, 2Sz) */
 
-/* precision of the block contractions */
-#define QCDMRG_FP64 0
+/* precision of the block contractions (all accumulate sigma in FP64 across
+ * problems; inside one output tile the tensor-core forms accumulate in FP32) */
+#define QCDMRG_FP64 0   /* FP64 FMA on CUDA cores */
+#define QCDMRG_TF32 1   /* tcgen05 kind::tf32, FP32 accumulation in tensor memory */
+#define QCDMRG_BF16 2   /* tcgen05 kind::f16 with bf16 inputs, FP32 accumulation */
+#define QCDMRG_BF16X3 3 /* three-term bf16 split of both operands, six products, FP32 accumulation */
 
 typedef struct qcdmrg_ctx qcdmrg_ctx;
 
@@ -155,7 +159,9 @@ int qcdmrg_psi_size(const qcdmrg_ctx* ctx, size_t* n);
 
 /*
  * sigma = H_eff psi on host arrays of psi_size elements (layout above).
- * precision: QCDMRG_FP64. Errors: ESTATE (no environment), EINVAL.
+ * precision: one of QCDMRG_FP64, _TF32, _BF16, _BF16X3. Errors: ESTATE (no
+ * environment), EINVAL, ETIMEOUT (a bounded wait of a tensor-core kernel gave
+ * up; sigma is then not valid).
  */
 int qcdmrg_apply_heff(qcdmrg_ctx* ctx, int precision, const double* psi, double* sigma);
 
@@ -164,6 +170,10 @@ int qcdmrg_apply_heff(qcdmrg_ctx* ctx, int precision, const double* psi, double*
  * overlap and must stay alive until the stream reaches the work. */
 int qcdmrg_apply_heff_dev(qcdmrg_ctx* ctx, int precision, const void* psi, void* sigma,
                           void* stream);
+
+/* Reads and clears the device error flag of the tensor-core kernels after
+ * _dev calls (synchronous). Errors: ETIMEOUT if a bounded wait gave up. */
+int qcdmrg_check_device(qcdmrg_ctx* ctx);
 
 /* Counters of the last calls. */
 int qcdmrg_stats(const qcdmrg_ctx* ctx, qcdmrg_stats_t* out);

@@ -16,7 +16,8 @@ LIB_PATH = os.path.join(_HERE, "libqcdmrg.so")
 
 QCDMRG_OK = 0
 U1 = 0
-FP64 = 0
+FP64, TF32, BF16, BF16X3 = 0, 1, 2, 3
+PRECISIONS = {"fp64": FP64, "tf32": TF32, "bf16": BF16, "bf16x3": BF16X3}
 
 _ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ESTATE", -5: "ENOTCONV",
            -6: "ETIMEOUT", -7: "EIO"}
@@ -50,7 +51,7 @@ EXPORTS = [
     "qcdmrg_create", "qcdmrg_destroy", "qcdmrg_last_error", "qcdmrg_load_integrals",
     "qcdmrg_set_target", "qcdmrg_import_mps", "qcdmrg_build_env", "qcdmrg_psi_size",
     "qcdmrg_apply_heff", "qcdmrg_apply_heff_dev", "qcdmrg_stats", "qcdmrg_init_mps",
-    "qcdmrg_get_bond", "qcdmrg_get_psi",
+    "qcdmrg_get_bond", "qcdmrg_get_psi", "qcdmrg_check_device",
 ]
 
 _lib = None
@@ -83,6 +84,7 @@ def load(path=None):
     ip = ctypes.POINTER(ctypes.c_int)
     lib.qcdmrg_get_bond.argtypes = [P, ctypes.c_int, ip, ip, ctypes.c_int]
     lib.qcdmrg_get_psi.argtypes = [P, dp, ctypes.c_size_t]
+    lib.qcdmrg_check_device.argtypes = [P]
     for f in EXPORTS:
         getattr(lib, f).restype = getattr(lib, f).restype or ctypes.c_int
     lib.qcdmrg_last_error.restype = ctypes.c_char_p
@@ -174,6 +176,9 @@ class Context:
         self._check(self.lib.qcdmrg_apply_heff_dev(self.h, precision, ctypes.c_void_p(psi_ptr),
                                                    ctypes.c_void_p(sigma_ptr),
                                                    ctypes.c_void_p(stream)))
+
+    def check_device(self):
+        self._check(self.lib.qcdmrg_check_device(self.h))
 
     def stats(self):
         s = Stats()

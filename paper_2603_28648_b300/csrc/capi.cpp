@@ -419,26 +419,31 @@ int qcdmrg_psi_size(const qcdmrg_ctx* ctx, size_t* n) {
   return QCDMRG_OK;
 }
 
-static void heff_dev(qcdmrg_ctx* ctx, uint64_t psi, uint64_t sig, void* stream) {
+static void heff_dev(qcdmrg_ctx* ctx, uint64_t psi, uint64_t sig, void* stream, int prec) {
   PreparedRunner& pr = *ctx->be.pr;
   pr.zero_async(sig, ctx->lay.size, stream);
   for (auto& h : ctx->prepared) {
-    pr.run_prepared(h.first, psi, sig, stream);
-    pr.run_prepared(h.second, psi, sig, stream);
+    pr.run_prepared(h.first, psi, sig, stream, prec);
+    pr.run_prepared(h.second, psi, sig, stream, prec);
   }
+}
+
+static bool valid_precision(int p) {
+  return p == QCDMRG_FP64 || p == QCDMRG_TF32 || p == QCDMRG_BF16 || p == QCDMRG_BF16X3;
 }
 
 int qcdmrg_apply_heff(qcdmrg_ctx* ctx, int precision, const double* psi, double* sigma) {
   return guard(ctx, [&]() {
     if (!ctx->have_env) throw Fail{QCDMRG_ESTATE, "build_env first"};
-    if (precision != QCDMRG_FP64) throw Fail{QCDMRG_EINVAL, "precision not available"};
+    if (!valid_precision(precision)) throw Fail{QCDMRG_EINVAL, "unknown precision"};
     if (!psi || !sigma) throw Fail{QCDMRG_EINVAL, "null argument"};
     Executor& ex = *ctx->be.ex;
     ex.upload(ctx->dpsi, psi, ctx->lay.size);
     auto t0 = std::chrono::steady_clock::now();
     void* st = ctx->be.pr->stream();
-    heff_dev(ctx, ctx->dpsi, ctx->dsig, st);
+    heff_dev(ctx, ctx->dpsi, ctx->dsig, st, precision);
     ctx->be.pr->sync(st);
+    if (ctx->be.pr->take_error()) throw Fail{QCDMRG_ETIMEOUT, "a tensor-core kernel wait gave up"};
     auto t1 = std::chrono::steady_clock::now();
     ctx->st.heff_seconds = std::chrono::duration<double>(t1 - t0).count();
     ex.download(sigma, ctx->dsig, ctx->lay.size);
@@ -449,9 +454,16 @@ int qcdmrg_apply_heff(qcdmrg_ctx* ctx, int precision, const double* psi, double*
 int qcdmrg_apply_heff_dev(qcdmrg_ctx* ctx, int precision, const void* psi, void* sigma, void* stream) {
   return guard(ctx, [&]() {
     if (!ctx->have_env) throw Fail{QCDMRG_ESTATE, "build_env first"};
-    if (precision != QCDMRG_FP64) throw Fail{QCDMRG_EINVAL, "precision not available"};
+    if (!valid_precision(precision)) throw Fail{QCDMRG_EINVAL, "unknown precision"};
     if (!psi || !sigma || psi == sigma) throw Fail{QCDMRG_EINVAL, "psi and sigma must be distinct device arrays"};
-    heff_dev(ctx, (uint64_t)psi, (uint64_t)sigma, stream);
+    heff_dev(ctx, (uint64_t)psi, (uint64_t)sigma, stream, precision);
+    return QCDMRG_OK;
+  });
+}
+
+int qcdmrg_check_device(qcdmrg_ctx* ctx) {
+  return guard(ctx, [&]() {
+    if (ctx->be.pr->take_error()) throw Fail{QCDMRG_ETIMEOUT, "a tensor-core kernel wait gave up"};
     return QCDMRG_OK;
   });
 }

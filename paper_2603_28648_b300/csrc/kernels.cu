@@ -19,6 +19,7 @@
 
 #include "core.hpp"
 #include "kernels.hpp"
+#include "tc_gemm.hpp"
 
 namespace qd {
 
@@ -29,23 +30,6 @@ namespace qd {
       throw std::runtime_error(std::string("CUDA: ") + cudaGetErrorString(e_) +    \
                                " at " + __FILE__ + ":" + std::to_string(__LINE__)); \
   } while (0)
-
-struct GSeg {
-  unsigned long long a, b;
-  int lda, ldb, k;
-  unsigned char abuf, bbuf, ta, tb;
-  double sc;
-};
-struct GProb {
-  unsigned long long c;
-  int m, n, ldc, beta, seg0, nseg, cbuf, pad;
-};
-struct GTile {
-  int prob, m0, n0, pad;
-};
-struct Bases {
-  unsigned long long b[4];
-};
 
 constexpr int TM = 64, TN = 64, TK = 16;
 
@@ -203,13 +187,14 @@ __global__ void scale_kernel(double* x, double a, long long n) {
 struct DevLaunch {
   GProb* p = nullptr;
   GSeg* s = nullptr;
-  GTile* t = nullptr;
-  int ntiles = 0;
+  GTile* t = nullptr;    // 64x64 tiles (FP64 kernel)
+  GTile* t2 = nullptr;   // 128x128 tiles (tcgen05 kernel)
+  int ntiles = 0, ntiles2 = 0;
   double flops = 0;
 };
 
 static void build_host(const Launch& l, std::vector<GProb>& P, std::vector<GSeg>& S,
-                       std::vector<GTile>& T) {
+                       std::vector<GTile>& T, int tile = TM) {
   P.resize(l.probs.size());
   S.resize(l.segs.size());
   T.clear();
@@ -218,8 +203,8 @@ static void build_host(const Launch& l, std::vector<GProb>& P, std::vector<GSeg>
     GProb& g = P[i];
     g.c = q.c; g.m = q.m; g.n = q.n; g.ldc = q.ldc; g.beta = q.beta;
     g.seg0 = q.seg0; g.nseg = q.nseg; g.cbuf = q.cbuf; g.pad = 0;
-    for (int m0 = 0; m0 < q.m; m0 += TM)
-      for (int n0 = 0; n0 < q.n; n0 += TN) T.push_back({(int)i, m0, n0, 0});
+    for (int m0 = 0; m0 < q.m; m0 += tile)
+      for (int n0 = 0; n0 < q.n; n0 += tile) T.push_back({(int)i, m0, n0, 0});
   }
   for (size_t i = 0; i < l.segs.size(); ++i) {
     const Seg& q = l.segs[i];
@@ -248,6 +233,7 @@ class CudaExec : public Executor, public PreparedRunner {
     if (work_) cudaFree(work_);
     if (info_) cudaFree(info_);
     if (sol_) cusolverDnDestroy(sol_);
+    if (err_) cudaFree(err_);
     cudaStreamDestroy(st_);
   }
   uint64_t alloc(int64_t n) override {
@@ -368,13 +354,20 @@ class CudaExec : public Executor, public PreparedRunner {
     build_host(l, P, S, T);
     d.ntiles = (int)T.size();
     d.flops = l.flops;
+    std::vector<GTile> T2;
+    for (size_t i = 0; i < P.size(); ++i)
+      for (int m0 = 0; m0 < P[i].m; m0 += TC_TILE)
+        for (int n0 = 0; n0 < P[i].n; n0 += TC_TILE) T2.push_back({(int)i, m0, n0, 0});
+    d.ntiles2 = (int)T2.size();
     if (d.ntiles) {
       CK(cudaMalloc(&d.p, P.size() * sizeof(GProb)));
       CK(cudaMalloc(&d.s, std::max<size_t>(1, S.size()) * sizeof(GSeg)));
       CK(cudaMalloc(&d.t, T.size() * sizeof(GTile)));
+      CK(cudaMalloc(&d.t2, T2.size() * sizeof(GTile)));
       CK(cudaMemcpy(d.p, P.data(), P.size() * sizeof(GProb), cudaMemcpyHostToDevice));
       if (!S.empty()) CK(cudaMemcpy(d.s, S.data(), S.size() * sizeof(GSeg), cudaMemcpyHostToDevice));
       CK(cudaMemcpy(d.t, T.data(), T.size() * sizeof(GTile), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(d.t2, T2.data(), T2.size() * sizeof(GTile), cudaMemcpyHostToDevice));
     }
     prepared_.push_back(d);
     return (int)prepared_.size() - 1;
@@ -384,10 +377,28 @@ class CudaExec : public Executor, public PreparedRunner {
     for (auto& d : prepared_) free_dev(d);
     prepared_.clear();
   }
-  void run_prepared(int h, uint64_t psi, uint64_t sig, void* stream) override {
+  void run_prepared(int h, uint64_t psi, uint64_t sig, void* stream, int precision) override {
     const DevLaunch& d = prepared_.at(h);
     if (!d.ntiles) return;
-    launch(d.p, d.s, d.t, d.ntiles, psi, sig, (cudaStream_t)stream);
+    if (precision == 0) {
+      launch(d.p, d.s, d.t, d.ntiles, psi, sig, (cudaStream_t)stream);
+      return;
+    }
+    if (!err_) {
+      CK(cudaMalloc(&err_, sizeof(int)));
+      CK(cudaMemset(err_, 0, sizeof(int)));
+    }
+    Bases B;
+    B.b[0] = 0; B.b[1] = psi; B.b[2] = sig; B.b[3] = tmp_;
+    int mode = precision == 1 ? TC_TF32 : precision == 2 ? TC_BF16 : TC_BF16X3;
+    CK(launch_tc(mode, d.p, d.s, d.t2, d.ntiles2, B, err_, (cudaStream_t)stream));
+  }
+  int take_error() override {
+    if (!err_) return 0;
+    int h = 0;
+    CK(cudaMemcpy(&h, err_, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) CK(cudaMemset(err_, 0, sizeof(int)));
+    return h;
   }
   void* stream() override { return st_; }
   void sync(void* stream) override { CK(cudaStreamSynchronize((cudaStream_t)stream)); }
@@ -416,7 +427,8 @@ class CudaExec : public Executor, public PreparedRunner {
     if (d.p) cudaFree(d.p);
     if (d.s) cudaFree(d.s);
     if (d.t) cudaFree(d.t);
-    d.p = nullptr; d.s = nullptr; d.t = nullptr;
+    if (d.t2) cudaFree(d.t2);
+    d.p = nullptr; d.s = nullptr; d.t = nullptr; d.t2 = nullptr;
   }
   int dev_;
   cudaStream_t st_ = nullptr;
@@ -426,6 +438,7 @@ class CudaExec : public Executor, public PreparedRunner {
   size_t spcap_ = 0, sscap_ = 0, stcap_ = 0;
   std::vector<DevLaunch> prepared_;
   int64_t bytes_ = 0;
+  int* err_ = nullptr;
   cusolverDnHandle_t sol_ = nullptr;
   int* info_ = nullptr;
   void* work_ = nullptr;

@@ -9,7 +9,10 @@ struct PreparedRunner {
   virtual ~PreparedRunner() {}
   virtual int prepare(const Launch& l) = 0;
   virtual void drop_prepared() = 0;
-  virtual void run_prepared(int handle, uint64_t psi, uint64_t sig, void* stream) = 0;
+  // precision: 0 FP64 (CUDA cores), 1 TF32, 2 BF16, 3 BF16x3 (tcgen05)
+  virtual void run_prepared(int handle, uint64_t psi, uint64_t sig, void* stream, int precision) = 0;
+  // returns and clears the device error flag of the tensor-core kernels
+  virtual int take_error() = 0;
   virtual void* stream() = 0;
   virtual void sync(void* stream) = 0;
   virtual void zero_async(uint64_t p, int64_t n, void* stream) = 0;

@@ -1,0 +1,364 @@
+// tcgen05 segmented grouped GEMM (BF16, BF16x3 split, TF32) for sm_103a.
+//
+// Same task lists as the FP64 kernel: one CTA owns a 128x128 output tile of a
+// problem and accumulates sum_s sc_s op(A_s) op(B_s) over all its segments in
+// one FP32 accumulator in tensor memory. Operand tiles are loaded from HBM by
+// all 128 threads (coalesced along the contiguous dimension of each operand),
+// scaled by the segment scalar, rounded to the MMA input type and stored in
+// shared memory in the K-major no-swizzle core-matrix layout; one thread then
+// issues tcgen05.mma for the chunk and tcgen05.commit signals an mbarrier when
+// the tensor core has consumed the stage (two stages in flight).
+//   BF16   : one bf16 MMA per K step.
+//   BF16x3 : x = x0 + x1 + x2 (bf16 each, x1 = bf16(x - x0), ...); six MMAs
+//            a_i b_j with i + j <= 2 per K step, FP32 accumulation
+//            (Henry, Tang, Heinecke, ARITH 2019).
+//   TF32   : FP32 operands, kind::tf32 MMA.
+// Every mbarrier wait is bounded (about one second of clock64 cycles); on a
+// timeout the kernel records an error code, waits once more (bounded) for its
+// own MMAs, frees its tensor memory and returns.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tc_gemm.hpp"
+
+namespace qd {
+
+namespace {
+
+constexpr int TCM = 128, TCN = 128;
+constexpr long long WAIT_CYCLES = 2000000000ll;  // ~1 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n"
+      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait; returns false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  long long t0 = clock64();
+  while (!mbar_try(bar, parity)) {
+    if (clock64() - t0 > WAIT_CYCLES) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+// shared-memory matrix descriptor, K-major, no swizzle
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+  d |= (uint64_t)((lbo & 0x3FFFF) >> 4) << 16;
+  d |= (uint64_t)((sbo & 0x3FFFF) >> 4) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
+  // base offset 0, relative LBO, layout type 0 = no swizzle
+  return d;
+}
+
+// instruction descriptor: FP32 accumulate, K-major A and B, M = 128, N = 128
+__host__ __device__ constexpr uint32_t idesc(uint32_t ab_format) {
+  return (1u << 4) | (ab_format << 7) | (ab_format << 10) | ((uint32_t)(TCN >> 3) << 17) |
+         ((uint32_t)(TCM >> 4) << 24);
+}
+
+template <int MODE>
+struct Cfg;
+template <>
+struct Cfg<TC_BF16> {
+  static constexpr int ES = 2, KC = 64, KS = 16, NSPLIT = 1;
+  static constexpr uint32_t FMT = 1;
+};
+template <>
+struct Cfg<TC_BF16X3> {
+  static constexpr int ES = 2, KC = 64, KS = 16, NSPLIT = 3;
+  static constexpr uint32_t FMT = 1;
+};
+template <>
+struct Cfg<TC_TF32> {
+  static constexpr int ES = 4, KC = 32, KS = 8, NSPLIT = 1;
+  static constexpr uint32_t FMT = 2;
+};
+
+__device__ __forceinline__ const double* resolve(unsigned long long v, int buf, const TcBases& B) {
+  return buf == 0 ? reinterpret_cast<const double*>(v)
+                  : reinterpret_cast<const double*>(B.b[buf] + v * 8ull);
+}
+
+// byte offset of element (r, k) of a 128 x KC K-major tile (core matrices of 8 x 16 B)
+template <int ES, int KC>
+__device__ __forceinline__ uint32_t tile_off(int r, int k) {
+  constexpr int KB = KC * ES / 16;  // 16-byte columns per row
+  const int kb = (k * ES) >> 4;
+  return (uint32_t)((((r >> 3) * KB + kb) << 7) + ((r & 7) << 4) + ((k * ES) & 15));
+}
+
+template <int MODE>
+__device__ __forceinline__ void put(unsigned char* base, uint32_t off, size_t split_stride, double v) {
+  if constexpr (MODE == TC_TF32) {
+    *reinterpret_cast<float*>(base + off) = (float)v;
+  } else if constexpr (MODE == TC_BF16) {
+    *reinterpret_cast<__nv_bfloat16*>(base + off) = __float2bfloat16_rn((float)v);
+  } else {
+    float x = (float)v;
+    __nv_bfloat16 h0 = __float2bfloat16_rn(x);
+    float r1 = x - __bfloat162float(h0);
+    __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
+    float r2 = r1 - __bfloat162float(h1);
+    __nv_bfloat16 h2 = __float2bfloat16_rn(r2);
+    *reinterpret_cast<__nv_bfloat16*>(base + off) = h0;
+    *reinterpret_cast<__nv_bfloat16*>(base + split_stride + off) = h1;
+    *reinterpret_cast<__nv_bfloat16*>(base + 2 * split_stride + off) = h2;
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(128, 1)
+    seg_gemm_tc(const TcProb* __restrict__ probs, const TcSeg* __restrict__ segs,
+                const TcTile* __restrict__ tiles, int ntiles, TcBases bases, int* err) {
+  using C = Cfg<MODE>;
+  constexpr int ES = C::ES, KC = C::KC, KS = C::KS, NS = C::NSPLIT;
+  constexpr uint32_t TILE = TCM * KC * ES;          // bytes of one operand split
+  constexpr uint32_t STAGE = 2 * NS * TILE;         // A splits then B splits
+  constexpr uint32_t LBO = 128;
+  constexpr uint32_t SBO = (KC * ES / 16) * 128;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * STAGE);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + 2 * STAGE + 16);
+  volatile int* wflag = reinterpret_cast<volatile int*>(smem + 2 * STAGE + 32);
+
+  const int t = blockIdx.x;
+  if (t >= ntiles) return;
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const TcTile tl = tiles[t];
+  const TcProb p = probs[tl.prob];
+  const int m0 = tl.m0, n0 = tl.n0;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(TCN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  int kt = 0;
+  bool ok = true;
+  for (int s = 0; s < p.nseg && ok; ++s) {
+    const TcSeg g = segs[p.seg0 + s];
+    if (g.a == 0ull && g.abuf == 0) continue;  // identity segments: epilogue
+    const double* Ap = resolve(g.a, g.abuf, bases);
+    const double* Bp = resolve(g.b, g.bbuf, bases);
+    const double sc = g.sc;
+    for (int k0 = 0; k0 < g.k; k0 += KC) {
+      const int st = kt & 1;
+      if (kt >= 2) {  // thread 0 waits; the outcome is shared so the block stays uniform
+        if (tid == 0) *wflag = mbar_wait(&mbar[st], ((kt - 2) >> 1) & 1) ? 1 : 0;
+        __syncthreads();
+        if (!*wflag) { ok = false; break; }
+      }
+      unsigned char* sA = smem + st * STAGE;
+      unsigned char* sB = sA + NS * TILE;
+      // A tile: rows m0.., k0..
+#pragma unroll 4
+      for (int e = 0; e < KC; ++e) {
+        const int idx = tid + 128 * e;
+        int r, k;
+        if (g.ta) { k = idx >> 7; r = idx & 127; }
+        else { r = idx / KC; k = idx % KC; }
+        const int gr = m0 + r, gk = k0 + k;
+        double v = 0.0;
+        if (gr < p.m && gk < g.k) v = sc * (g.ta ? Ap[(size_t)gk * g.lda + gr] : Ap[(size_t)gr * g.lda + gk]);
+        put<MODE>(sA, tile_off<ES, KC>(r, k), TILE, v);
+      }
+      // B tile stored N x K (K-major): element (k, n) of op(B)
+#pragma unroll 4
+      for (int e = 0; e < KC; ++e) {
+        const int idx = tid + 128 * e;
+        int n, k;
+        if (g.tb) { n = idx / KC; k = idx % KC; }
+        else { k = idx >> 7; n = idx & 127; }
+        const int gn = n0 + n, gk = k0 + k;
+        double v = 0.0;
+        if (gn < p.n && gk < g.k) v = g.tb ? Bp[(size_t)gn * g.ldb + gk] : Bp[(size_t)gk * g.ldb + gn];
+        put<MODE>(sB, tile_off<ES, KC>(n, k), TILE, v);
+      }
+      fence_async_smem();
+      __syncthreads();
+      if (tid == 0) {
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+#pragma unroll
+        for (int kk = 0; kk < KC / KS; ++kk) {
+          const uint32_t koff = kk * 2 * 128;  // two core matrices per K step
+          if constexpr (NS == 1) {
+            uint64_t da = sdesc(a0 + koff, LBO, SBO), db = sdesc(b0 + koff, LBO, SBO);
+            uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
+            if constexpr (MODE == TC_TF32) {
+              asm volatile(
+                  "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                  " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                  "l"(da), "l"(db), "r"(idesc(C::FMT)), "r"(acc));
+            } else {
+              asm volatile(
+                  "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                  "l"(da), "l"(db), "r"(idesc(C::FMT)), "r"(acc));
+            }
+          } else {
+            // (i, j) pairs with i + j <= 2, smallest terms first
+            const int pi[6] = {2, 1, 0, 1, 0, 0};
+            const int pj[6] = {0, 1, 2, 0, 1, 0};
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+              uint64_t da = sdesc(a0 + pi[q] * TILE + koff, LBO, SBO);
+              uint64_t db = sdesc(b0 + pj[q] * TILE + koff, LBO, SBO);
+              uint32_t acc = (kt > 0 || kk > 0 || q > 0) ? 1u : 0u;
+              asm volatile(
+                  "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                  "l"(da), "l"(db), "r"(idesc(C::FMT)), "r"(acc));
+            }
+          }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&mbar[st]))
+                     : "memory");
+      }
+      ++kt;
+    }
+  }
+  if (kt > 0) {
+    if (tid == 0) {
+      int w = mbar_wait(&mbar[(kt - 1) & 1], ((kt - 1) >> 1) & 1) ? 1 : 0;
+      if (!w) mbar_wait(&mbar[(kt - 1) & 1], ((kt - 1) >> 1) & 1);  // second bounded wait for our own MMAs
+      *wflag = w;
+    }
+    __syncthreads();
+    if (!*wflag) ok = false;
+  }
+  if (!ok && err && tid == 0) atomicExch(err, 1);
+  tc_fence_after();
+  // epilogue: warp w owns accumulator lanes (rows) 32w .. 32w+31
+  const int row = m0 + warp * 32 + lane;
+  double* Cp = const_cast<double*>(resolve(p.c, p.cbuf, bases));
+  for (int c0 = 0; c0 < TCN; c0 += 16) {
+    float acc[16];
+    if (kt > 0 && ok) {
+      uint32_t r[16];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int j = 0; j < 16; ++j) acc[j] = __uint_as_float(r[j]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) acc[j] = 0.f;
+    }
+    if (row < p.m && n0 + c0 < p.n) {
+      double out[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) out[j] = (double)acc[j];
+      for (int s = 0; s < p.nseg; ++s) {  // identity segments
+        const TcSeg g = segs[p.seg0 + s];
+        if (!(g.a == 0ull && g.abuf == 0)) continue;
+        if (g.b == 0ull && g.bbuf == 0) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (row == n0 + c0 + j) out[j] += g.sc;
+        } else {
+          const double* Bp = resolve(g.b, g.bbuf, bases);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int col = n0 + c0 + j;
+            if (col < p.n) out[j] += g.sc * (g.tb ? Bp[(size_t)col * g.ldb + row] : Bp[(size_t)row * g.ldb + col]);
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int col = n0 + c0 + j;
+        if (col < p.n) {
+          double* dst = Cp + (size_t)row * p.ldc + col;
+          *dst = p.beta ? *dst + out[j] : out[j];
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCN));
+  }
+}
+
+template <int MODE>
+size_t smem_bytes() {
+  using C = Cfg<MODE>;
+  return (size_t)2 * 2 * C::NSPLIT * TCM * C::KC * C::ES + 64;
+}
+
+template <int MODE>
+cudaError_t launch_mode(const TcProb* P, const TcSeg* S, const TcTile* T, int nt, TcBases B, int* err,
+                        cudaStream_t st) {
+  static bool init = false;
+  const size_t sm = smem_bytes<MODE>();
+  if (!init) {
+    cudaError_t e = cudaFuncSetAttribute(seg_gemm_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    init = true;
+  }
+  seg_gemm_tc<MODE><<<nt, 128, sm, st>>>(P, S, T, nt, B, err);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_tc(int mode, const TcProb* P, const TcSeg* S, const TcTile* T, int nt, TcBases B, int* err,
+                      cudaStream_t st) {
+  if (nt <= 0) return cudaSuccess;
+  switch (mode) {
+    case TC_BF16: return launch_mode<TC_BF16>(P, S, T, nt, B, err, st);
+    case TC_BF16X3: return launch_mode<TC_BF16X3>(P, S, T, nt, B, err, st);
+    case TC_TF32: return launch_mode<TC_TF32>(P, S, T, nt, B, err, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace qd
