@@ -37,6 +37,8 @@ def parse():
     ap.add_argument("--N", type=int, default=54)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "tf32", "bf16", "bf16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="bracket the timed region with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     return ap.parse_args()
 
 
@@ -220,10 +222,15 @@ def run_ours(args, rank, world, local):
         dist.barrier()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if args.profile:
+        torch.cuda.profiler.start()
     ev0.record(stream)
     for _ in range(args.steps):
         step()
     ev1.record(stream)
+    if args.profile:
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()

@@ -139,6 +139,14 @@ struct Executor {
   virtual void orthonormal_cols(uint64_t p, int rows, int cols) = 0;
   virtual double dot(uint64_t x, uint64_t y, int64_t n) = 0;
   virtual void scale(uint64_t x, double a, int64_t n) = 0;
+  // y = a x + b y
+  virtual void axpby(uint64_t y, double a, uint64_t x, double b, int64_t n) = 0;
+  // t = r / max(|d - theta|, floor) (Davidson preconditioner)
+  virtual void precond(uint64_t t, uint64_t r, uint64_t d, double theta, double floor, int64_t n) = 0;
+  // symmetric eigendecomposition in place: A (n x n, column-major) -> eigenvectors,
+  // w (host) -> ascending eigenvalues
+  virtual void eigh(uint64_t A, int n, double* w) = 0;
+  virtual void copy(uint64_t dst, uint64_t src, int64_t n) = 0;
 };
 
 // Integrals; spin-orbital form t_kl, w_ijkl with k = 2p + sigma.

@@ -32,6 +32,8 @@ namespace qd {
   } while (0)
 
 constexpr int TM = 64, TN = 64, TK = 16;
+constexpr int KMAX_F64 = 1024;   // summed K per work item before splitting (FP64 kernel)
+constexpr int KMAX_TC = 4096;    // same for the tensor-core kernel
 
 __device__ __forceinline__ const double* res(unsigned long long v, int buf, const Bases& B) {
   return buf == 0 ? reinterpret_cast<const double*>(v)
@@ -56,7 +58,7 @@ __global__ void __launch_bounds__(256) seg_gemm_f64(const GProb* __restrict__ pr
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
   const int m0 = tl.m0, n0 = tl.n0;
-  for (int s = 0; s < p.nseg; ++s) {
+  for (int s = tl.s0; s < tl.s1; ++s) {
     const GSeg g = segs[p.seg0 + s];
     const bool aid = (g.a == 0ull && g.abuf == 0);
     const bool bid = (g.b == 0ull && g.bbuf == 0);
@@ -137,7 +139,8 @@ __global__ void __launch_bounds__(256) seg_gemm_f64(const GProb* __restrict__ pr
       const int col = n0 + tx + 16 * c;
       if (col >= p.n) continue;
       double* dst = Cp + (size_t)row * p.ldc + col;
-      *dst = p.beta ? *dst + acc[r][c] : acc[r][c];
+      if (tl.split) atomicAdd(dst, acc[r][c]);
+      else *dst = p.beta ? *dst + acc[r][c] : acc[r][c];
     }
   }
 }
@@ -183,6 +186,22 @@ __global__ void scale_kernel(double* x, double a, long long n) {
     x[i] *= a;
 }
 
+__global__ void axpby_kernel(double* y, double a, const double* x, double b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = a * x[i] + b * y[i];
+}
+
+__global__ void precond_kernel(double* t, const double* r, const double* d, double theta, double fl,
+                               long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double den = d[i] - theta;
+    if (fabs(den) < fl) den = den < 0 ? -fl : fl;
+    t[i] = r[i] / den;
+  }
+}
+
 // ---------------------------------------------------------------------------
 struct DevLaunch {
   GProb* p = nullptr;
@@ -192,6 +211,32 @@ struct DevLaunch {
   int ntiles = 0, ntiles2 = 0;
   double flops = 0;
 };
+
+// Work items: every tile of every problem, with the problem's segments cut into
+// ranges whose summed K stays below kmax (split-K over segments).
+static void make_tiles(const Launch& l, int tile, int kmax, std::vector<GTile>& T) {
+  T.clear();
+  for (size_t i = 0; i < l.probs.size(); ++i) {
+    const Prob& q = l.probs[i];
+    std::vector<std::pair<int, int>> ranges;
+    int s0 = 0, ksum = 0;
+    for (int s = 0; s < q.nseg; ++s) {
+      const Seg& g = l.segs[q.seg0 + s];
+      int k = (g.a == 0 && g.abuf == 0) ? 1 : g.k;
+      if (s > s0 && ksum + k > kmax) {
+        ranges.push_back({s0, s});
+        s0 = s;
+        ksum = 0;
+      }
+      ksum += k;
+    }
+    ranges.push_back({s0, q.nseg});
+    const int split = ranges.size() > 1 ? 1 : 0;
+    for (int m0 = 0; m0 < q.m; m0 += tile)
+      for (int n0 = 0; n0 < q.n; n0 += tile)
+        for (auto& r : ranges) T.push_back({(int)i, m0, n0, r.first, r.second, split});
+  }
+}
 
 static void build_host(const Launch& l, std::vector<GProb>& P, std::vector<GSeg>& S,
                        std::vector<GTile>& T, int tile = TM) {
@@ -203,9 +248,8 @@ static void build_host(const Launch& l, std::vector<GProb>& P, std::vector<GSeg>
     GProb& g = P[i];
     g.c = q.c; g.m = q.m; g.n = q.n; g.ldc = q.ldc; g.beta = q.beta;
     g.seg0 = q.seg0; g.nseg = q.nseg; g.cbuf = q.cbuf; g.pad = 0;
-    for (int m0 = 0; m0 < q.m; m0 += tile)
-      for (int n0 = 0; n0 < q.n; n0 += tile) T.push_back({(int)i, m0, n0, 0});
   }
+  make_tiles(l, tile, KMAX_F64, T);
   for (size_t i = 0; i < l.segs.size(); ++i) {
     const Seg& q = l.segs[i];
     GSeg& g = S[i];
@@ -296,11 +340,7 @@ class CudaExec : public Executor, public PreparedRunner {
   }
   void orthonormal_cols(uint64_t p, int rows, int cols) override {
     if (rows < cols) throw std::runtime_error("orthonormal_cols: rows < cols");
-    if (!sol_) {
-      if (cusolverDnCreate(&sol_) != CUSOLVER_STATUS_SUCCESS) throw std::runtime_error("CUDA: cusolverDnCreate failed");
-      cusolverDnSetStream(sol_, st_);
-      CK(cudaMalloc(&info_, sizeof(int)));
-    }
+    solver();
     double* A = reinterpret_cast<double*>(p);
     int l1 = 0, l2 = 0;
     if (cusolverDnDgeqrf_bufferSize(sol_, rows, cols, A, rows, &l1) != CUSOLVER_STATUS_SUCCESS ||
@@ -338,6 +378,50 @@ class CudaExec : public Executor, public PreparedRunner {
     for (int i = 0; i < nb; ++i) s += h[i];
     return s;
   }
+  void axpby(uint64_t y, double a, uint64_t x, double b, int64_t n) override {
+    if (n <= 0) return;
+    int blocks = (int)std::min<int64_t>((n + 255) / 256, 148 * 16);
+    axpby_kernel<<<blocks, 256, 0, st_>>>(reinterpret_cast<double*>(y), a, reinterpret_cast<const double*>(x), b, n);
+    CK(cudaGetLastError());
+  }
+  void precond(uint64_t t, uint64_t r, uint64_t d, double theta, double fl, int64_t n) override {
+    if (n <= 0) return;
+    int blocks = (int)std::min<int64_t>((n + 255) / 256, 148 * 16);
+    precond_kernel<<<blocks, 256, 0, st_>>>(reinterpret_cast<double*>(t), reinterpret_cast<const double*>(r),
+                                            reinterpret_cast<const double*>(d), theta, fl, n);
+    CK(cudaGetLastError());
+  }
+  void copy(uint64_t dst, uint64_t src, int64_t n) override {
+    if (n <= 0) return;
+    CK(cudaMemcpyAsync(reinterpret_cast<void*>(dst), reinterpret_cast<void*>(src), (size_t)n * 8,
+                       cudaMemcpyDeviceToDevice, st_));
+  }
+  void eigh(uint64_t A, int n, double* w) override {
+    if (n <= 0) return;
+    solver();
+    double* dA = reinterpret_cast<double*>(A);
+    int lw = 0;
+    if (cusolverDnDsyevd_bufferSize(sol_, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, dA, n, nullptr,
+                                    &lw) != CUSOLVER_STATUS_SUCCESS)
+      throw std::runtime_error("CUDA: syevd buffer query failed");
+    size_t need = (size_t)lw + n;
+    if (need > work_cap_) {
+      CK(cudaStreamSynchronize(st_));
+      if (work_) CK(cudaFree(work_));
+      CK(cudaMalloc(&work_, need * 8));
+      work_cap_ = need;
+    }
+    double* dw = (double*)work_;
+    double* wk = dw + n;
+    if (cusolverDnDsyevd(sol_, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, dA, n, dw, wk,
+                         (int)(work_cap_ - n), info_) != CUSOLVER_STATUS_SUCCESS)
+      throw std::runtime_error("CUDA: syevd failed");
+    int info = 0;
+    CK(cudaMemcpyAsync(w, dw, (size_t)n * 8, cudaMemcpyDeviceToHost, st_));
+    CK(cudaMemcpyAsync(&info, info_, sizeof(int), cudaMemcpyDeviceToHost, st_));
+    CK(cudaStreamSynchronize(st_));
+    if (info != 0) throw std::runtime_error("CUDA: syevd reported info " + std::to_string(info));
+  }
   void scale(uint64_t x, double a, int64_t n) override {
     if (n <= 0) return;
     int blocks = (int)std::min<int64_t>((n + 255) / 256, 148 * 16);
@@ -355,9 +439,7 @@ class CudaExec : public Executor, public PreparedRunner {
     d.ntiles = (int)T.size();
     d.flops = l.flops;
     std::vector<GTile> T2;
-    for (size_t i = 0; i < P.size(); ++i)
-      for (int m0 = 0; m0 < P[i].m; m0 += TC_TILE)
-        for (int n0 = 0; n0 < P[i].n; n0 += TC_TILE) T2.push_back({(int)i, m0, n0, 0});
+    make_tiles(l, TC_TILE, KMAX_TC, T2);
     d.ntiles2 = (int)T2.size();
     if (d.ntiles) {
       CK(cudaMalloc(&d.p, P.size() * sizeof(GProb)));
@@ -408,6 +490,13 @@ class CudaExec : public Executor, public PreparedRunner {
   int64_t bytes_allocated() const override { return bytes_; }
 
  private:
+  void solver() {
+    if (!sol_) {
+      if (cusolverDnCreate(&sol_) != CUSOLVER_STATUS_SUCCESS) throw std::runtime_error("CUDA: cusolverDnCreate failed");
+      cusolverDnSetStream(sol_, st_);
+      CK(cudaMalloc(&info_, sizeof(int)));
+    }
+  }
   void launch(GProb* P, GSeg* S, GTile* T, int nt, uint64_t psi, uint64_t sig, cudaStream_t s) {
     Bases B;
     B.b[0] = 0;

@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(128, 1)
 
   int kt = 0;
   bool ok = true;
-  for (int s = 0; s < p.nseg && ok; ++s) {
+  for (int s = tl.s0; s < tl.s1 && ok; ++s) {
     const TcSeg g = segs[p.seg0 + s];
     if (g.a == 0ull && g.abuf == 0) continue;  // identity segments: epilogue
     const double* Ap = resolve(g.a, g.abuf, bases);
@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(128, 1)
       double out[16];
 #pragma unroll
       for (int j = 0; j < 16; ++j) out[j] = (double)acc[j];
-      for (int s = 0; s < p.nseg; ++s) {  // identity segments
+      for (int s = tl.s0; s < tl.s1; ++s) {  // identity segments
         const TcSeg g = segs[p.seg0 + s];
         if (!(g.a == 0ull && g.abuf == 0)) continue;
         if (g.b == 0ull && g.bbuf == 0) {
@@ -315,7 +315,8 @@ __global__ void __launch_bounds__(128, 1)
         const int col = n0 + c0 + j;
         if (col < p.n) {
           double* dst = Cp + (size_t)row * p.ldc + col;
-          *dst = p.beta ? *dst + out[j] : out[j];
+          if (tl.split) atomicAdd(dst, out[j]);
+          else *dst = p.beta ? *dst + out[j] : out[j];
         }
       }
     }

@@ -14,8 +14,11 @@ struct GProb {
   unsigned long long c;
   int m, n, ldc, beta, seg0, nseg, cbuf, pad;
 };
+// One work item: tile (m0, n0) of a problem over segments [s0, s1). A problem
+// split over several segment ranges is accumulated with FP64 atomics; every
+// output that is split is zero-initialised or has beta = 1.
 struct GTile {
-  int prob, m0, n0, pad;
+  int prob, m0, n0, s0, s1, split;
 };
 struct Bases {
   unsigned long long b[4];   // 0: absolute, 1: psi, 2: sigma, 3: scratch
