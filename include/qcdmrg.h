@@ -101,6 +101,34 @@ typedef struct {
   int nlaunch;           /* kernel launches per H_eff psi */
 } qcdmrg_stats_t;
 
+/* Davidson options (zero fields take the defaults in brackets). */
+typedef struct {
+  double tol;     /* residual 2-norm of the normalised vector [1e-6, the paper's Lanczos
+                     residual, Numerical procedure section] */
+  int max_iter;   /* [300] */
+  int m_max;      /* subspace size before a restart [32] */
+  int policy;     /* 0: every H psi in `precision`; 1: BF16 while the residual is above tau1,
+                     BF16x3 while above tau2, then FP64 H psi until converged (the final
+                     residual and energy are always from the FP64 form) */
+  int precision;  /* QCDMRG_FP64 / _TF32 / _BF16 / _BF16X3 for policy 0 */
+  double tau1;    /* [1e-2] */
+  double tau2;    /* [1e-5] */
+} qcdmrg_dav_opts;
+
+typedef struct {
+  int D;                 /* bond dimension kept by every truncation (U(1) states) */
+  qcdmrg_dav_opts dav;
+} qcdmrg_sweep_opts;
+
+typedef struct {
+  double energy;         /* energy of the last optimisation of the sweep */
+  double energy_mixed;   /* last Ritz value before the FP64 correction (policy 1) */
+  double max_trunc_err;  /* largest discarded weight of the sweep */
+  double seconds;        /* wall time of the sweep */
+  int n_hpsi[4];         /* H psi products per precision (FP64, TF32, BF16, BF16x3) */
+  int n_steps;           /* two-site optimisations (2L-4) */
+} qcdmrg_sweep_report;
+
 /* Create a context on cfg->device. Errors: EINVAL, ECUDA, ENOMEM. */
 int qcdmrg_create(qcdmrg_ctx** out, const qcdmrg_config* cfg);
 int qcdmrg_destroy(qcdmrg_ctx* ctx);
@@ -170,6 +198,44 @@ int qcdmrg_apply_heff(qcdmrg_ctx* ctx, int precision, const double* psi, double*
  * overlap and must stay alive until the stream reaches the work. */
 int qcdmrg_apply_heff_dev(qcdmrg_ctx* ctx, int precision, const void* psi, void* sigma,
                           void* stream);
+
+/* Diagonal of H_eff at the centre (psi layout, n = psi size), as used by the
+ * Davidson preconditioner: sum over terms of c_t diag(O_L) (x) diag(O_R)
+ * restricted to diagonal quantum-number blocks. */
+int qcdmrg_heff_diag(qcdmrg_ctx* ctx, double* out, size_t n);
+
+/*
+ * Davidson solve of the two-site problem at the centre (FP64 vectors, FP64
+ * Gram-Schmidt and subspace eigenproblem; H psi in the precision the policy
+ * selects), starting from the current wavefunction; the converged Ritz vector
+ * replaces it. Preconditioner (diag(H_eff) - theta)^-1 with |.| floored at
+ * 1e-8; restart keeps the Ritz vector. Any pointer may be NULL. Errors:
+ * ESTATE, ENOTCONV (results still written), ETIMEOUT.
+ */
+int qcdmrg_davidson(qcdmrg_ctx* ctx, const qcdmrg_dav_opts* opts, double* energy, double* resid,
+                    int* iters);
+
+/*
+ * Truncation step of the sweep: density matrix of the two-site wavefunction
+ * per quantum-number sector (rho = Psi Psi^T for dir = +1, Psi^T Psi for
+ * dir = -1), FP64 eigendecomposition, the D states of largest weight kept
+ * across sectors (ties: weight, then label, then in-sector order), new site
+ * tensor, renormalization of every operator of the grown block, and the
+ * transformed wavefunction as the guess at the moved centre. trunc_err gets
+ * the discarded weight. Errors: ESTATE, EINVAL.
+ */
+int qcdmrg_truncate(qcdmrg_ctx* ctx, int D, int dir, double* trunc_err);
+
+/* Move the centre without truncation (only weights below 1e-28 dropped). */
+int qcdmrg_move_center(qcdmrg_ctx* ctx, int target);
+
+/*
+ * One full sweep: the centre is first moved (exactly) to sites (0, 1), then
+ * optimised and moved right to (L-2, L-1), then back to (0, 1): 2L-4 two-site
+ * optimisations, each a Davidson solve followed by qcdmrg_truncate. Errors:
+ * ESTATE, EINVAL, ENOTCONV (a Davidson solve hit max_iter; the sweep completes).
+ */
+int qcdmrg_sweep(qcdmrg_ctx* ctx, const qcdmrg_sweep_opts* opts, qcdmrg_sweep_report* report);
 
 /* Reads and clears the device error flag of the tensor-core kernels after
  * _dev calls (synchronous). Errors: ETIMEOUT if a bounded wait gave up. */

@@ -40,6 +40,22 @@ class MpsDesc(ctypes.Structure):
                 ("bond_sec", ctypes.POINTER(ctypes.c_int))]
 
 
+class DavOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("m_max", ctypes.c_int),
+                ("policy", ctypes.c_int), ("precision", ctypes.c_int), ("tau1", ctypes.c_double),
+                ("tau2", ctypes.c_double)]
+
+
+class SweepOpts(ctypes.Structure):
+    _fields_ = [("D", ctypes.c_int), ("dav", DavOpts)]
+
+
+class SweepReport(ctypes.Structure):
+    _fields_ = [("energy", ctypes.c_double), ("energy_mixed", ctypes.c_double),
+                ("max_trunc_err", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("n_hpsi", ctypes.c_int * 4), ("n_steps", ctypes.c_int)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("heff_flops", ctypes.c_double), ("heff_seconds", ctypes.c_double),
                 ("env_flops", ctypes.c_double), ("env_seconds", ctypes.c_double),
@@ -51,7 +67,8 @@ EXPORTS = [
     "qcdmrg_create", "qcdmrg_destroy", "qcdmrg_last_error", "qcdmrg_load_integrals",
     "qcdmrg_set_target", "qcdmrg_import_mps", "qcdmrg_build_env", "qcdmrg_psi_size",
     "qcdmrg_apply_heff", "qcdmrg_apply_heff_dev", "qcdmrg_stats", "qcdmrg_init_mps",
-    "qcdmrg_get_bond", "qcdmrg_get_psi", "qcdmrg_check_device",
+    "qcdmrg_get_bond", "qcdmrg_get_psi", "qcdmrg_check_device", "qcdmrg_davidson",
+    "qcdmrg_truncate", "qcdmrg_move_center", "qcdmrg_sweep", "qcdmrg_heff_diag",
 ]
 
 _lib = None
@@ -85,6 +102,11 @@ def load(path=None):
     lib.qcdmrg_get_bond.argtypes = [P, ctypes.c_int, ip, ip, ctypes.c_int]
     lib.qcdmrg_get_psi.argtypes = [P, dp, ctypes.c_size_t]
     lib.qcdmrg_check_device.argtypes = [P]
+    lib.qcdmrg_davidson.argtypes = [P, ctypes.POINTER(DavOpts), dp, dp, ctypes.POINTER(ctypes.c_int)]
+    lib.qcdmrg_truncate.argtypes = [P, ctypes.c_int, ctypes.c_int, dp]
+    lib.qcdmrg_move_center.argtypes = [P, ctypes.c_int]
+    lib.qcdmrg_heff_diag.argtypes = [P, dp, ctypes.c_size_t]
+    lib.qcdmrg_sweep.argtypes = [P, ctypes.POINTER(SweepOpts), ctypes.POINTER(SweepReport)]
     for f in EXPORTS:
         getattr(lib, f).restype = getattr(lib, f).restype or ctypes.c_int
     lib.qcdmrg_last_error.restype = ctypes.c_char_p
@@ -176,6 +198,42 @@ class Context:
         self._check(self.lib.qcdmrg_apply_heff_dev(self.h, precision, ctypes.c_void_p(psi_ptr),
                                                    ctypes.c_void_p(sigma_ptr),
                                                    ctypes.c_void_p(stream)))
+
+    @staticmethod
+    def dav_opts(tol=1e-6, max_iter=300, m_max=32, policy=0, precision=FP64, tau1=1e-2, tau2=1e-5):
+        return DavOpts(tol, max_iter, m_max, policy, precision, tau1, tau2)
+
+    def davidson(self, allow_notconv=False, **kw):
+        """Returns (energy, residual, iterations)."""
+        e, r, it = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+        o = self.dav_opts(**kw)
+        rc = self.lib.qcdmrg_davidson(self.h, ctypes.byref(o), ctypes.byref(e), ctypes.byref(r),
+                                      ctypes.byref(it))
+        if not (allow_notconv and rc == -5):
+            self._check(rc)
+        return e.value, r.value, it.value
+
+    def heff_diag(self):
+        out = np.empty(self.psi_size())
+        self._check(self.lib.qcdmrg_heff_diag(self.h, _dptr(out), out.size))
+        return out
+
+    def truncate(self, D, direction):
+        err = ctypes.c_double()
+        self._check(self.lib.qcdmrg_truncate(self.h, D, direction, ctypes.byref(err)))
+        return err.value
+
+    def move_center(self, target):
+        self._check(self.lib.qcdmrg_move_center(self.h, target))
+
+    def sweep(self, D, allow_notconv=False, **kw):
+        o = SweepOpts(D, self.dav_opts(**kw))
+        r = SweepReport()
+        rc = self.lib.qcdmrg_sweep(self.h, ctypes.byref(o), ctypes.byref(r))
+        if not (allow_notconv and rc == -5):
+            self._check(rc)
+        return {"energy": r.energy, "energy_mixed": r.energy_mixed, "max_trunc_err": r.max_trunc_err,
+                "seconds": r.seconds, "n_hpsi": list(r.n_hpsi), "n_steps": r.n_steps}
 
     def check_device(self):
         self._check(self.lib.qcdmrg_check_device(self.h))

@@ -10,54 +10,36 @@
 
 #include "../../include/qcdmrg.h"
 #include "core.hpp"
+#include "engine.hpp"
 #include "kernels.hpp"
 
 using namespace qd;
 
 struct qcdmrg_ctx {
   Backend be;
+  Engine eng;
   int device = 0;
-  int64_t tmp_budget = 0;
-  Integrals I;
-  bool have_int = false;
-  int N = 0, two_s = 0;
-  bool have_target = false;
-  // MPS
-  int L = 0, center = -1;
-  std::vector<Basis> bonds;                      // 0..L (center+1 unused)
-  std::vector<uint64_t> site;                    // device storage per site
-  std::vector<std::vector<int64_t>> site_off;    // per product sector (-1: absent)
-  std::vector<std::vector<int>> site_nb;         // product sector -> new bond sector
-  std::vector<double> psi0;
-  // environment
-  bool have_env = false;
-  std::vector<EnvBlock> lenv, renv;
-  Enlarged Lp, Rp;
-  PsiLayout lay;
-  HeffPlan plan;
-  std::vector<std::pair<int, int>> prepared;      // (stage1, stage2) handles
-  uint64_t dpsi = 0, dsig = 0;
+  bool have_int = false, have_target = false;
+  uint64_t dpsi = 0, dsig = 0;   // host-API staging buffers
+  int64_t staged = 0;
   qcdmrg_stats_t st{};
   std::string err;
-
-  ~qcdmrg_ctx() { free_env(); free_mps(); if (dpsi) be.ex->release(dpsi); if (dsig) be.ex->release(dsig); delete be.ex; }
-  void free_env() {
+  ~qcdmrg_ctx() {
     if (!be.ex) return;
-    for (auto& e : lenv) for (auto p : e.owned) be.ex->release(p);
-    for (auto& e : renv) for (auto p : e.owned) be.ex->release(p);
-    for (auto p : Lp.owned) be.ex->release(p);
-    for (auto p : Rp.owned) be.ex->release(p);
-    lenv.clear(); renv.clear();
-    Lp = Enlarged(); Rp = Enlarged();
-    if (be.pr) be.pr->drop_prepared();
-    prepared.clear();
-    have_env = false;
+    eng.clear();
+    eng.ex = nullptr;  // the engine must not touch the executor after it is deleted
+    eng.pr = nullptr;
+    if (dpsi) be.ex->release(dpsi);
+    if (dsig) be.ex->release(dsig);
+    delete be.ex;
   }
-  void free_mps() {
-    if (!be.ex) return;
-    for (auto p : site) if (p) be.ex->release(p);
-    site.clear();
-    center = -1;
+  void staging(int64_t n) {
+    if (n <= staged && dpsi) return;
+    if (dpsi) be.ex->release(dpsi);
+    if (dsig) be.ex->release(dsig);
+    dpsi = be.ex->alloc(std::max<int64_t>(1, n));
+    dsig = be.ex->alloc(std::max<int64_t>(1, n));
+    staged = n;
   }
 };
 
@@ -88,14 +70,6 @@ int guard(qcdmrg_ctx* c, F&& f) {
   }
 }
 
-EnvBlock vacuum(bool left, int cut) {
-  EnvBlock b;
-  b.left = left;
-  b.cut = cut;
-  b.basis.add(QN{0, 0}, 1);
-  return b;
-}
-
 }  // namespace
 
 extern "C" {
@@ -109,7 +83,9 @@ int qcdmrg_create(qcdmrg_ctx** out, const qcdmrg_config* cfg) {
     c->device = cfg->device;
     c->be = make_backend(cfg->device);
     double gb = cfg->tmp_budget_gb > 0 ? cfg->tmp_budget_gb : 2.0;
-    c->tmp_budget = (int64_t)(gb * 1e9 / 8);
+    c->eng.ex = c->be.ex;
+    c->eng.pr = c->be.pr;
+    c->eng.tmp_budget = (int64_t)(gb * 1e9 / 8);
   } catch (const std::exception& e) {
     delete c;
     return QCDMRG_ECUDA;
@@ -139,12 +115,11 @@ int qcdmrg_load_integrals(qcdmrg_ctx* ctx, int L, const double* h, const double*
           throw Fail{QCDMRG_EINVAL, "h is not symmetric"};
     for (size_t i = 0; i < n4; ++i)
       if (!std::isfinite(V[i])) throw Fail{QCDMRG_EINVAL, "V has non-finite entries"};
-    ctx->free_env();
-    ctx->free_mps();
-    ctx->I.L = L;
-    ctx->I.h.assign(h, h + n2);
-    ctx->I.V.assign(V, V + n4);
-    ctx->I.ecore = e_core;
+    ctx->eng.clear();
+    ctx->eng.I.L = L;
+    ctx->eng.I.h.assign(h, h + n2);
+    ctx->eng.I.V.assign(V, V + n4);
+    ctx->eng.I.ecore = e_core;
     ctx->have_int = true;
     return QCDMRG_OK;
   });
@@ -153,11 +128,11 @@ int qcdmrg_load_integrals(qcdmrg_ctx* ctx, int L, const double* h, const double*
 int qcdmrg_set_target(qcdmrg_ctx* ctx, int N, int two_s) {
   return guard(ctx, [&]() {
     if (N < 0 || ((N + two_s) & 1)) throw Fail{QCDMRG_EINVAL, "N and 2Sz must have equal parity"};
-    if (ctx->have_int && (N > 2 * ctx->I.L || std::abs(two_s) > N))
+    if (ctx->have_int && (N > 2 * ctx->eng.I.L || std::abs(two_s) > N))
       throw Fail{QCDMRG_EINVAL, "target outside the Fock space"};
-    ctx->free_env();
-    ctx->N = N;
-    ctx->two_s = two_s;
+    ctx->eng.clear();
+    ctx->eng.N = N;
+    ctx->eng.two_s = two_s;
     ctx->have_target = true;
     return QCDMRG_OK;
   });
@@ -167,11 +142,11 @@ int qcdmrg_import_mps(qcdmrg_ctx* ctx, const qcdmrg_mps_desc* d, const double* d
   return guard(ctx, [&]() {
     if (!ctx->have_int || !ctx->have_target) throw Fail{QCDMRG_ESTATE, "load integrals and target first"};
     if (!d || !data || !d->bond_nsec || !d->bond_sec) throw Fail{QCDMRG_EINVAL, "null argument"};
+    Engine& E = ctx->eng;
     const int L = d->L;
-    if (L != ctx->I.L) throw Fail{QCDMRG_EINVAL, "MPS length differs from the integrals"};
+    if (L != E.I.L) throw Fail{QCDMRG_EINVAL, "MPS length differs from the integrals"};
     if (d->center < 0 || d->center + 1 >= L) throw Fail{QCDMRG_EINVAL, "centre out of range"};
-    ctx->free_env();
-    ctx->free_mps();
+    E.clear();
     std::vector<Basis> bonds(L + 1);
     int pos = 0;
     for (int b = 0; b <= L; ++b) {
@@ -193,9 +168,9 @@ int qcdmrg_import_mps(qcdmrg_ctx* ctx, const qcdmrg_mps_desc* d, const double* d
     if (bonds[L].nsec() != 1 || bonds[L].q[0] != QN{0, 0} || bonds[L].dim[0] != 1)
       throw Fail{QCDMRG_EINVAL, "bond L (right block of no sites) must be the vacuum"};
     size_t off = 0;
-    ctx->site.assign(L, 0);
-    ctx->site_off.assign(L, {});
-    ctx->site_nb.assign(L, {});
+    E.site.assign(L, 0);
+    E.site_off.assign(L, {});
+    E.site_nb.assign(L, {});
     auto take_site = [&](int p, const Basis& from, bool left, const Basis& to) {
       ProdBasis pb = make_prod(from, left);
       std::vector<int64_t> so(pb.prod.nsec(), -1);
@@ -215,20 +190,20 @@ int qcdmrg_import_mps(qcdmrg_ctx* ctx, const qcdmrg_mps_desc* d, const double* d
       uint64_t dev = ctx->be.ex->alloc(tot);
       ctx->be.ex->upload(dev, data + off, tot);
       off += tot;
-      ctx->site[p] = dev;
-      ctx->site_off[p] = so;
-      ctx->site_nb[p] = nb;
+      E.site[p] = dev;
+      E.site_off[p] = so;
+      E.site_nb[p] = nb;
     };
     for (int p = 0; p < c; ++p) take_site(p, bonds[p], true, bonds[p + 1]);
     for (int p = c + 2; p < L; ++p) take_site(p, bonds[p + 1], false, bonds[p]);
     // psi
     ProdBasis Lp = make_prod(bonds[c], true), Rp = make_prod(bonds[c + 2], false);
-    PsiLayout lay = make_psi_layout(Lp, Rp, QN{ctx->N, ctx->two_s});
+    PsiLayout lay = make_psi_layout(Lp, Rp, QN{E.N, E.two_s});
     if (off + lay.size != n) throw Fail{QCDMRG_EINVAL, "MPS data length does not match its layout"};
-    ctx->psi0.assign(data + off, data + off + lay.size);
-    ctx->bonds = bonds;
-    ctx->L = L;
-    ctx->center = c;
+    E.bonds = bonds;
+    E.L = L;
+    E.center = c;
+    E.set_psi_host(std::vector<double>(data + off, data + off + lay.size));
     return QCDMRG_OK;
   });
 }
@@ -236,12 +211,12 @@ int qcdmrg_import_mps(qcdmrg_ctx* ctx, const qcdmrg_mps_desc* d, const double* d
 int qcdmrg_init_mps(qcdmrg_ctx* ctx, int D, uint64_t seed, int center) {
   return guard(ctx, [&]() {
     if (!ctx->have_int || !ctx->have_target) throw Fail{QCDMRG_ESTATE, "load integrals and target first"};
-    const int L = ctx->I.L;
+    Engine& E = ctx->eng;
+    const int L = E.I.L;
     if (D < 1) throw Fail{QCDMRG_EINVAL, "D must be positive"};
     if (center < 0 || center + 1 >= L) throw Fail{QCDMRG_EINVAL, "centre out of range"};
-    ctx->free_env();
-    ctx->free_mps();
-    auto st = mps_structure(L, ctx->N, ctx->two_s, D);
+    E.clear();
+    auto st = mps_structure(L, E.N, E.two_s, D);
     for (int b = 1; b < L; ++b)
       if (st[b].empty()) throw Fail{QCDMRG_EINVAL, "target not reachable: empty bond"};
     std::vector<Basis> bonds(L + 1);
@@ -250,9 +225,9 @@ int qcdmrg_init_mps(qcdmrg_ctx* ctx, int D, uint64_t seed, int center) {
     for (int b = center + 2; b <= L; ++b)
       for (auto& kv : st[L - b]) bonds[b].add(kv.first, kv.second);
     Executor& ex = *ctx->be.ex;
-    ctx->site.assign(L, 0);
-    ctx->site_off.assign(L, {});
-    ctx->site_nb.assign(L, {});
+    E.site.assign(L, 0);
+    E.site_off.assign(L, {});
+    E.site_nb.assign(L, {});
     auto mix = [](uint64_t a, uint64_t b) {
       uint64_t x = a ^ (b + 0x9E3779B97F4A7C15ull + (a << 6) + (a >> 2));
       x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -304,22 +279,21 @@ int qcdmrg_init_mps(qcdmrg_ctx* ctx, int D, uint64_t seed, int center) {
         }
       }
       if (scratch) ex.release(scratch);
-      ctx->site[p] = dev;
-      ctx->site_off[p] = so;
-      ctx->site_nb[p] = nb;
+      E.site[p] = dev;
+      E.site_off[p] = so;
+      E.site_nb[p] = nb;
     }
     ProdBasis Lp = make_prod(bonds[center], true), Rp = make_prod(bonds[center + 2], false);
-    PsiLayout lay = make_psi_layout(Lp, Rp, QN{ctx->N, ctx->two_s});
+    PsiLayout lay = make_psi_layout(Lp, Rp, QN{E.N, E.two_s});
     uint64_t tp = ex.alloc(std::max<int64_t>(1, lay.size));
     ex.randn(tp, lay.size, mix(seed, 0xC0FFEEull));
     double nrm = std::sqrt(ex.dot(tp, tp, lay.size));
+    if (!(nrm > 0)) throw Fail{QCDMRG_EINVAL, "empty two-site wavefunction"};
     ex.scale(tp, 1.0 / nrm, lay.size);
-    ctx->psi0.resize(lay.size);
-    ex.download(ctx->psi0.data(), tp, lay.size);
-    ex.release(tp);
-    ctx->bonds = bonds;
-    ctx->L = L;
-    ctx->center = center;
+    E.bonds = bonds;
+    E.L = L;
+    E.center = center;
+    E.dpsi = tp;
     return QCDMRG_OK;
   });
 }
@@ -327,9 +301,9 @@ int qcdmrg_init_mps(qcdmrg_ctx* ctx, int D, uint64_t seed, int center) {
 int qcdmrg_get_bond(const qcdmrg_ctx* cctx, int bond, int* nsec, int* sec, int cap) {
   qcdmrg_ctx* ctx = const_cast<qcdmrg_ctx*>(cctx);
   return guard(ctx, [&]() {
-    if (ctx->center < 0) throw Fail{QCDMRG_ESTATE, "no MPS"};
-    if (bond < 0 || bond > ctx->L || !nsec) throw Fail{QCDMRG_EINVAL, "bad bond"};
-    const Basis& b = ctx->bonds[bond];
+    if (ctx->eng.center < 0) throw Fail{QCDMRG_ESTATE, "no MPS"};
+    if (bond < 0 || bond > ctx->eng.L || !nsec) throw Fail{QCDMRG_EINVAL, "bad bond"};
+    const Basis& b = ctx->eng.bonds[bond];
     *nsec = b.nsec();
     if (sec) {
       if (cap < 3 * b.nsec()) throw Fail{QCDMRG_EINVAL, "sector buffer too small"};
@@ -346,86 +320,36 @@ int qcdmrg_get_bond(const qcdmrg_ctx* cctx, int bond, int* nsec, int* sec, int c
 int qcdmrg_get_psi(const qcdmrg_ctx* cctx, double* out, size_t n) {
   qcdmrg_ctx* ctx = const_cast<qcdmrg_ctx*>(cctx);
   return guard(ctx, [&]() {
-    if (ctx->center < 0) throw Fail{QCDMRG_ESTATE, "no MPS"};
-    if (!out || n != ctx->psi0.size()) throw Fail{QCDMRG_EINVAL, "output size differs from the wavefunction"};
-    std::copy(ctx->psi0.begin(), ctx->psi0.end(), out);
+    if (ctx->eng.center < 0) throw Fail{QCDMRG_ESTATE, "no MPS"};
+    std::vector<double> h = ctx->eng.get_psi_host();
+    if (!out || n != h.size()) throw Fail{QCDMRG_EINVAL, "output size differs from the wavefunction"};
+    std::copy(h.begin(), h.end(), out);
     return QCDMRG_OK;
   });
 }
 
 int qcdmrg_build_env(qcdmrg_ctx* ctx) {
   return guard(ctx, [&]() {
-    if (ctx->center < 0) throw Fail{QCDMRG_ESTATE, "import an MPS first"};
-    auto t0 = std::chrono::steady_clock::now();
-    ctx->free_env();
-    Executor& ex = *ctx->be.ex;
-    const int L = ctx->L, c = ctx->center;
-    double fl = 0;
-    EnvBlock left = vacuum(true, 0);
-    for (int p = 0; p < c; ++p) {
-      Enlarged E;
-      enlarge(left, ctx->I, ex, E, &fl);
-      EnvBlock nb;
-      nb.cut = p + 1;
-      renormalize(E, ctx->bonds[p + 1], ctx->site_nb[p], ctx->site[p], ctx->site_off[p], ex, nb,
-                  ctx->tmp_budget, &fl);
-      for (auto q : E.owned) ex.release(q);
-      for (auto q : left.owned) ex.release(q);
-      left = nb;
-    }
-    EnvBlock right = vacuum(false, L);
-    for (int p = L - 1; p >= c + 2; --p) {
-      Enlarged E;
-      enlarge(right, ctx->I, ex, E, &fl);
-      EnvBlock nb;
-      nb.cut = p;
-      renormalize(E, ctx->bonds[p], ctx->site_nb[p], ctx->site[p], ctx->site_off[p], ex, nb,
-                  ctx->tmp_budget, &fl);
-      for (auto q : E.owned) ex.release(q);
-      for (auto q : right.owned) ex.release(q);
-      right = nb;
-    }
-    ctx->lenv.push_back(left);
-    ctx->renv.push_back(right);
-    enlarge(ctx->lenv.back(), ctx->I, ex, ctx->Lp, &fl);
-    enlarge(ctx->renv.back(), ctx->I, ex, ctx->Rp, &fl);
-    ctx->lay = make_psi_layout(ctx->Lp.pb, ctx->Rp.pb, QN{ctx->N, ctx->two_s});
-    if (ctx->lay.size != (int64_t)ctx->psi0.size()) throw Fail{QCDMRG_EINVAL, "wavefunction layout mismatch"};
-    ctx->plan = plan_heff(ctx->Lp, ctx->Rp, ctx->lay, ctx->I, ctx->tmp_budget);
-    ex.tmp(std::max<int64_t>(1, ctx->plan.tmp_elems));
-    for (size_t k = 0; k < ctx->plan.stage1.size(); ++k)
-      ctx->prepared.emplace_back(ctx->be.pr->prepare(ctx->plan.stage1[k]),
-                                 ctx->be.pr->prepare(ctx->plan.stage2[k]));
-    if (ctx->dpsi) ex.release(ctx->dpsi);
-    if (ctx->dsig) ex.release(ctx->dsig);
-    ctx->dpsi = ex.alloc(ctx->lay.size);
-    ctx->dsig = ex.alloc(ctx->lay.size);
-    ctx->have_env = true;
-    auto t1 = std::chrono::steady_clock::now();
-    ctx->st.env_flops = fl;
-    ctx->st.env_seconds = std::chrono::duration<double>(t1 - t0).count();
-    ctx->st.heff_flops = ctx->plan.flops;
-    ctx->st.psi_size = ctx->lay.size;
-    ctx->st.nterms = ctx->plan.nterms;
-    ctx->st.nlaunch = 2 * (int)ctx->plan.stage1.size();
+    Engine& E = ctx->eng;
+    if (E.center < 0) throw Fail{QCDMRG_ESTATE, "import or initialise an MPS first"};
+    E.build_env();
+    ctx->st.env_flops = E.env_flops;
+    ctx->st.env_seconds = E.env_seconds;
+    ctx->st.heff_flops = E.plan.flops;
+    ctx->st.psi_size = E.lay.size;
+    ctx->st.nterms = E.plan.nterms;
+    ctx->st.nlaunch = 2 * (int)E.plan.stage1.size();
     return QCDMRG_OK;
   });
 }
 
 int qcdmrg_psi_size(const qcdmrg_ctx* ctx, size_t* n) {
   if (!ctx || !n) return QCDMRG_EINVAL;
-  if (ctx->center < 0) return QCDMRG_ESTATE;
-  *n = ctx->psi0.size();
+  if (ctx->eng.center < 0) return QCDMRG_ESTATE;
+  ProdBasis a = make_prod(ctx->eng.bonds[ctx->eng.center], true);
+  ProdBasis b = make_prod(ctx->eng.bonds[ctx->eng.center + 2], false);
+  *n = (size_t)make_psi_layout(a, b, QN{ctx->eng.N, ctx->eng.two_s}).size;
   return QCDMRG_OK;
-}
-
-static void heff_dev(qcdmrg_ctx* ctx, uint64_t psi, uint64_t sig, void* stream, int prec) {
-  PreparedRunner& pr = *ctx->be.pr;
-  pr.zero_async(sig, ctx->lay.size, stream);
-  for (auto& h : ctx->prepared) {
-    pr.run_prepared(h.first, psi, sig, stream, prec);
-    pr.run_prepared(h.second, psi, sig, stream, prec);
-  }
 }
 
 static bool valid_precision(int p) {
@@ -434,30 +358,124 @@ static bool valid_precision(int p) {
 
 int qcdmrg_apply_heff(qcdmrg_ctx* ctx, int precision, const double* psi, double* sigma) {
   return guard(ctx, [&]() {
-    if (!ctx->have_env) throw Fail{QCDMRG_ESTATE, "build_env first"};
+    Engine& E = ctx->eng;
+    if (!E.have_env) throw Fail{QCDMRG_ESTATE, "build_env first"};
     if (!valid_precision(precision)) throw Fail{QCDMRG_EINVAL, "unknown precision"};
     if (!psi || !sigma) throw Fail{QCDMRG_EINVAL, "null argument"};
     Executor& ex = *ctx->be.ex;
-    ex.upload(ctx->dpsi, psi, ctx->lay.size);
+    ctx->staging(E.lay.size);
+    ex.upload(ctx->dpsi, psi, E.lay.size);
     auto t0 = std::chrono::steady_clock::now();
     void* st = ctx->be.pr->stream();
-    heff_dev(ctx, ctx->dpsi, ctx->dsig, st, precision);
+    E.heff(ctx->dpsi, ctx->dsig, st, precision);
     ctx->be.pr->sync(st);
-    if (ctx->be.pr->take_error()) throw Fail{QCDMRG_ETIMEOUT, "a tensor-core kernel wait gave up"};
     auto t1 = std::chrono::steady_clock::now();
+    if (ctx->be.pr->take_error()) throw Fail{QCDMRG_ETIMEOUT, "a tensor-core kernel wait gave up"};
     ctx->st.heff_seconds = std::chrono::duration<double>(t1 - t0).count();
-    ex.download(sigma, ctx->dsig, ctx->lay.size);
+    ex.download(sigma, ctx->dsig, E.lay.size);
     return QCDMRG_OK;
   });
 }
 
 int qcdmrg_apply_heff_dev(qcdmrg_ctx* ctx, int precision, const void* psi, void* sigma, void* stream) {
   return guard(ctx, [&]() {
-    if (!ctx->have_env) throw Fail{QCDMRG_ESTATE, "build_env first"};
+    if (!ctx->eng.have_env) throw Fail{QCDMRG_ESTATE, "build_env first"};
     if (!valid_precision(precision)) throw Fail{QCDMRG_EINVAL, "unknown precision"};
     if (!psi || !sigma || psi == sigma) throw Fail{QCDMRG_EINVAL, "psi and sigma must be distinct device arrays"};
-    heff_dev(ctx, (uint64_t)psi, (uint64_t)sigma, stream, precision);
+    ctx->eng.heff((uint64_t)psi, (uint64_t)sigma, stream, precision);
     return QCDMRG_OK;
+  });
+}
+
+static DavOpts dav_opts(const qcdmrg_dav_opts* o) {
+  DavOpts d;
+  if (!o) return d;
+  if (o->tol > 0) d.tol = o->tol;
+  if (o->max_iter > 0) d.max_iter = o->max_iter;
+  if (o->m_max > 0) d.m_max = o->m_max;
+  d.policy = o->policy;
+  d.precision = o->precision;
+  if (o->tau1 > 0) d.tau1 = o->tau1;
+  if (o->tau2 > 0) d.tau2 = o->tau2;
+  return d;
+}
+
+int qcdmrg_heff_diag(qcdmrg_ctx* ctx, double* out, size_t n) {
+  return guard(ctx, [&]() {
+    Engine& E = ctx->eng;
+    if (!E.have_env) throw Fail{QCDMRG_ESTATE, "build_env first"};
+    if (!out || n != (size_t)E.lay.size) throw Fail{QCDMRG_EINVAL, "output size differs from the wavefunction"};
+    ctx->be.ex->download(out, E.ddiag, E.lay.size);
+    return QCDMRG_OK;
+  });
+}
+
+int qcdmrg_davidson(qcdmrg_ctx* ctx, const qcdmrg_dav_opts* o, double* energy, double* resid, int* iters) {
+  return guard(ctx, [&]() {
+    Engine& E = ctx->eng;
+    if (!E.have_env) throw Fail{QCDMRG_ESTATE, "build_env first"};
+    if (o && (!valid_precision(o->precision) || o->policy < 0 || o->policy > 1))
+      throw Fail{QCDMRG_EINVAL, "bad Davidson options"};
+    DavResult r = E.davidson(dav_opts(o));
+    if (energy) *energy = r.energy;
+    if (resid) *resid = r.resid;
+    if (iters) *iters = r.iters;
+    return r.converged ? QCDMRG_OK : QCDMRG_ENOTCONV;
+  });
+}
+
+int qcdmrg_truncate(qcdmrg_ctx* ctx, int D, int dir, double* trunc_err) {
+  return guard(ctx, [&]() {
+    Engine& E = ctx->eng;
+    if (!E.have_env) throw Fail{QCDMRG_ESTATE, "build_env first"};
+    if (D < 1 || (dir != 1 && dir != -1)) throw Fail{QCDMRG_EINVAL, "D >= 1 and dir = +1 or -1"};
+    if ((dir > 0 && E.center + 2 >= E.L) || (dir < 0 && E.center == 0))
+      throw Fail{QCDMRG_EINVAL, "the centre cannot move further in that direction"};
+    double e = E.truncate_move(D, dir, 0.0);
+    if (trunc_err) *trunc_err = e;
+    return QCDMRG_OK;
+  });
+}
+
+int qcdmrg_move_center(qcdmrg_ctx* ctx, int target) {
+  return guard(ctx, [&]() {
+    Engine& E = ctx->eng;
+    if (!E.have_env) throw Fail{QCDMRG_ESTATE, "build_env first"};
+    if (target < 0 || target + 1 >= E.L) throw Fail{QCDMRG_EINVAL, "centre out of range"};
+    while (E.center > target) E.truncate_move(1 << 30, -1, 1e-28);
+    while (E.center < target) E.truncate_move(1 << 30, +1, 1e-28);
+    return QCDMRG_OK;
+  });
+}
+
+int qcdmrg_sweep(qcdmrg_ctx* ctx, const qcdmrg_sweep_opts* o, qcdmrg_sweep_report* rep) {
+  return guard(ctx, [&]() {
+    Engine& E = ctx->eng;
+    if (!E.have_env) throw Fail{QCDMRG_ESTATE, "build_env first"};
+    if (!o || o->D < 1) throw Fail{QCDMRG_EINVAL, "sweep options with D >= 1 required"};
+    if (E.L < 3) throw Fail{QCDMRG_EINVAL, "sweeps need L >= 3"};
+    auto t0 = std::chrono::steady_clock::now();
+    while (E.center > 0) E.truncate_move(1 << 30, -1, 1e-28);
+    DavOpts dop = dav_opts(&o->dav);
+    qcdmrg_sweep_report R{};
+    bool conv = true;
+    auto step = [&](int dir) {
+      DavResult r = E.davidson(dop);
+      conv = conv && r.converged;
+      for (int k = 0; k < 4; ++k) R.n_hpsi[k] += r.hpsi[k];
+      R.energy = r.energy;
+      R.energy_mixed = r.energy_mixed;
+      R.n_steps++;
+      double e = E.truncate_move(o->D, dir, 0.0);
+      R.max_trunc_err = std::max(R.max_trunc_err, e);
+    };
+    for (int l = 0; l < E.L - 2; ++l) step(+1);
+    for (int l = E.L - 2; l > 0; --l) step(-1);
+    R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (rep) *rep = R;
+    ctx->st.heff_flops = E.plan.flops;
+    ctx->st.psi_size = E.lay.size;
+    return conv ? QCDMRG_OK : QCDMRG_ENOTCONV;
   });
 }
 

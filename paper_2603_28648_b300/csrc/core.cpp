@@ -290,22 +290,10 @@ PsiLayout make_psi_layout(const ProdBasis& Lp, const ProdBasis& Rp, QN target) {
   return lay;
 }
 
-namespace {
-struct Term {
-  const OpView* L;
-  bool LT;
-  const OpView* R;
-  bool RT;
-  double coef;
-};
-}  // namespace
-
-HeffPlan plan_heff(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay,
-                   const Integrals& I, int64_t tmp_budget) {
-  HeffPlan plan;
+std::vector<CenterTerm> center_terms(const Enlarged& Lp, const Enlarged& Rp, const Integrals& I) {
   const int c = Lp.cut;  // L' = [0, c), R' = [c, L)
   const int L = I.L;
-  std::vector<Term> terms;
+  std::vector<CenterTerm> terms;
   auto get = [](const Enlarged& E, Key k) -> const OpView* {
     auto it = E.ops.find(k);
     if (it == E.ops.end() || it->second.empty()) return nullptr;
@@ -349,6 +337,13 @@ HeffPlan plan_heff(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay,
       if (!B || !Q) continue;
       terms.push_back({B, false, Q, false, 1.0});
     }
+  return terms;
+}
+
+HeffPlan plan_heff(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay,
+                   const Integrals& I, int64_t tmp_budget) {
+  HeffPlan plan;
+  std::vector<CenterTerm> terms = center_terms(Lp, Rp, I);
   plan.nterms = (int)terms.size();
 
   const ProdBasis& LB = Lp.pb;
@@ -375,7 +370,7 @@ HeffPlan plan_heff(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay,
     out.clear();
     tused = 0;
   };
-  for (const Term& t : terms) {
+  for (const CenterTerm& t : terms) {
     OpView Lv = t.LT ? transpose(*t.L) : *t.L;
     OpView Rv = t.RT ? transpose(*t.R) : *t.R;
     std::map<int, std::vector<const BRef*>> lby;  // col sub -> blocks
@@ -433,6 +428,53 @@ HeffPlan plan_heff(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay,
   }
   flush();
   return plan;
+}
+
+Launch plan_diag(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay, const Integrals& I,
+                 uint64_t ones) {
+  // diag H_eff[(x,i,j,y)][a][b] = sum_t c_t dL[a] dR[b] over terms whose left and
+  // right blocks are diagonal blocks: rank-1 segments (K = 1) with strided
+  // diagonals (leading dimension ld + 1) or a vector of ones for identities
+  std::vector<CenterTerm> terms = center_terms(Lp, Rp, I);
+  std::map<int, std::vector<Seg>> out;
+  const ProdBasis& LB = Lp.pb;
+  for (const CenterTerm& t : terms) {
+    OpView Lv = t.LT ? transpose(*t.L) : *t.L;
+    OpView Rv = t.RT ? transpose(*t.R) : *t.R;
+    std::map<int, std::vector<const BRef*>> ldiag, rdiag;
+    for (const BRef& b : Lv.blocks) if (b.r == b.c) ldiag[b.r].push_back(&b);
+    for (const BRef& b : Rv.blocks) if (b.r == b.c) rdiag[b.r].push_back(&b);
+    for (auto& lk : ldiag)
+      for (auto& rk : rdiag) {
+        auto it = lay.by_sub.find({lk.first, rk.first});
+        if (it == lay.by_sub.end()) continue;
+        int par = 1;
+        if (Rv.odd) par = (LB.prod.q[LB.subs[lk.first].prod].n & 1) ? -1 : 1;
+        for (const BRef* bl : lk.second)
+          for (const BRef* br : rk.second) {
+            Seg g;
+            g.k = 1;
+            if (bl->ident()) { g.a = ones; g.lda = 1; } else { g.a = bl->ptr; g.lda = bl->ld + 1; }
+            g.abuf = B_ABS; g.ta = 0;
+            if (br->ident()) { g.b = ones; g.ldb = 1; } else { g.b = br->ptr; g.ldb = br->ld + 1; }
+            g.bbuf = B_ABS; g.tb = 1;
+            g.sc = t.coef * bl->sc * br->sc * par;
+            out[it->second].push_back(g);
+          }
+      }
+  }
+  Launch l;
+  for (auto& kv : out) {
+    const auto& b = lay.blks[kv.first];
+    Prob p;
+    p.c = (uint64_t)b.off; p.cbuf = B_SIG;
+    p.m = b.rows; p.n = b.cols; p.ldc = b.cols; p.beta = 1;
+    p.seg0 = (int)l.segs.size(); p.nseg = (int)kv.second.size();
+    for (auto& g : kv.second) l.segs.push_back(g);
+    l.probs.push_back(p);
+  }
+  (void)I;
+  return l;
 }
 
 }  // namespace qd

@@ -229,6 +229,21 @@ struct PsiLayout {
 };
 PsiLayout make_psi_layout(const ProdBasis& Lp, const ProdBasis& Rp, QN target);
 
+// Operator-product terms of H at the centre cut: coef * L op (x) R op.
+struct CenterTerm {
+  const OpView* L;
+  bool LT;
+  const OpView* R;
+  bool RT;
+  double coef;
+};
+std::vector<CenterTerm> center_terms(const Enlarged& Lp, const Enlarged& Rp, const Integrals& I);
+
+// Diagonal of H_eff as rank-1 segments into the sigma buffer (ones: device
+// vector of 1.0 at least as long as the largest sector).
+Launch plan_diag(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay, const Integrals& I,
+                 uint64_t ones);
+
 // H_eff psi task lists (chunks of stage-1 / stage-2 launches).
 struct HeffPlan {
   std::vector<Launch> stage1, stage2;

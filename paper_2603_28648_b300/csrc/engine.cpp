@@ -1,0 +1,610 @@
+// Sweep engine: environment build, H_eff psi, Davidson with FP64 control and a
+// precision policy, density-matrix truncation, renormalization and the
+// two-site wavefunction transformation that moves the centre.
+#include "engine.hpp"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <stdexcept>
+#include <tuple>
+
+namespace qd {
+
+namespace {
+
+EnvBlock vacuum(bool left, int cut) {
+  EnvBlock b;
+  b.left = left;
+  b.cut = cut;
+  b.basis.add(QN{0, 0}, 1);
+  return b;
+}
+
+// Jacobi eigensolver for the small symmetric subspace matrix (n <= 64):
+// eigenvalues ascending in w, eigenvectors as columns of V (n x n, row-major).
+void small_eigh(const std::vector<double>& A0, int n, std::vector<double>& w, std::vector<double>& V) {
+  std::vector<double> A(A0);
+  V.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) off += A[(size_t)p * n + q] * A[(size_t)p * n + q];
+    if (off < 1e-30) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        double apq = A[(size_t)p * n + q];
+        if (std::fabs(apq) < 1e-300) continue;
+        double app = A[(size_t)p * n + p], aqq = A[(size_t)q * n + q];
+        double th = 0.5 * std::atan2(2 * apq, aqq - app);
+        double c = std::cos(th), s = std::sin(th);
+        for (int k = 0; k < n; ++k) {
+          double akp = A[(size_t)k * n + p], akq = A[(size_t)k * n + q];
+          A[(size_t)k * n + p] = c * akp - s * akq;
+          A[(size_t)k * n + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {
+          double apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
+          A[(size_t)p * n + k] = c * apk - s * aqk;
+          A[(size_t)q * n + k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          double vkp = V[(size_t)k * n + p], vkq = V[(size_t)k * n + q];
+          V[(size_t)k * n + p] = c * vkp - s * vkq;
+          V[(size_t)k * n + q] = s * vkp + c * vkq;
+        }
+      }
+  }
+  std::vector<int> ord(n);
+  for (int i = 0; i < n; ++i) ord[i] = i;
+  std::sort(ord.begin(), ord.end(), [&](int a, int b) { return A[(size_t)a * n + a] < A[(size_t)b * n + b]; });
+  w.resize(n);
+  std::vector<double> W((size_t)n * n);
+  for (int j = 0; j < n; ++j) {
+    w[j] = A[(size_t)ord[j] * n + ord[j]];
+    for (int k = 0; k < n; ++k) W[(size_t)k * n + j] = V[(size_t)k * n + ord[j]];
+  }
+  V.swap(W);
+}
+
+Prob copy_prob(uint64_t dst, int m, int n, int ldc, int seg0) {
+  Prob p;
+  p.c = dst; p.cbuf = B_ABS; p.m = m; p.n = n; p.ldc = ldc; p.beta = 0; p.seg0 = seg0; p.nseg = 1;
+  return p;
+}
+
+}  // namespace
+
+void Engine::free_block(EnvBlock& b) {
+  for (auto p : b.owned) ex->release(p);
+  b.owned.clear();
+  b.ops.clear();
+}
+
+void Engine::free_enlarged(Enlarged& e) {
+  for (auto p : e.owned) ex->release(p);
+  e.owned.clear();
+  e.ops.clear();
+}
+
+void Engine::clear_env() {
+  if (!ex) return;
+  for (auto& kv : lenv) free_block(kv.second);
+  for (auto& kv : renv) free_block(kv.second);
+  lenv.clear();
+  renv.clear();
+  free_enlarged(Lp);
+  free_enlarged(Rp);
+  if (pr) pr->drop_prepared();
+  prepared.clear();
+  if (ddiag) ex->release(ddiag);
+  ddiag = 0;
+  have_env = false;
+}
+
+void Engine::clear() {
+  if (!ex) return;
+  clear_env();
+  for (auto p : site)
+    if (p) ex->release(p);
+  site.clear();
+  if (dpsi) ex->release(dpsi);
+  dpsi = 0;
+  if (dones) ex->release(dones);
+  dones = 0;
+  ones_n = 0;
+  center = -1;
+}
+
+void Engine::set_psi_host(const std::vector<double>& h) {
+  if (dpsi) ex->release(dpsi);
+  dpsi = ex->alloc(std::max<size_t>(1, h.size()));
+  ex->upload(dpsi, h.data(), (int64_t)h.size());
+}
+
+std::vector<double> Engine::get_psi_host() {
+  ProdBasis a = make_prod(bonds[center], true), b = make_prod(bonds[center + 2], false);
+  PsiLayout l = make_psi_layout(a, b, QN{N, two_s});
+  std::vector<double> h(l.size);
+  if (l.size) ex->download(h.data(), dpsi, l.size);
+  return h;
+}
+
+void Engine::build_env() {
+  auto t0 = std::chrono::steady_clock::now();
+  clear_env();
+  double fl = 0;
+  lenv[0] = vacuum(true, 0);
+  for (int p = 0; p < center; ++p) {
+    Enlarged E;
+    enlarge(lenv[p], I, *ex, E, &fl);
+    EnvBlock nb;
+    nb.cut = p + 1;
+    renormalize(E, bonds[p + 1], site_nb[p], site[p], site_off[p], *ex, nb, tmp_budget, &fl);
+    free_enlarged(E);
+    lenv[p + 1] = nb;
+  }
+  renv[L] = vacuum(false, L);
+  for (int p = L - 1; p >= center + 2; --p) {
+    Enlarged E;
+    enlarge(renv[p + 1], I, *ex, E, &fl);
+    EnvBlock nb;
+    nb.cut = p;
+    renormalize(E, bonds[p], site_nb[p], site[p], site_off[p], *ex, nb, tmp_budget, &fl);
+    free_enlarged(E);
+    renv[p] = nb;
+  }
+  env_flops = fl;
+  prepare_center();
+  env_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+void Engine::prepare_center() {
+  free_enlarged(Lp);
+  free_enlarged(Rp);
+  if (pr) pr->drop_prepared();
+  prepared.clear();
+  double fl = 0;
+  enlarge(lenv.at(center), I, *ex, Lp, &fl);
+  enlarge(renv.at(center + 2), I, *ex, Rp, &fl);
+  lay = make_psi_layout(Lp.pb, Rp.pb, QN{N, two_s});
+  plan = plan_heff(Lp, Rp, lay, I, tmp_budget);
+  ex->tmp(std::max<int64_t>(1, plan.tmp_elems));
+  for (size_t k = 0; k < plan.stage1.size(); ++k)
+    prepared.emplace_back(pr->prepare(plan.stage1[k]), pr->prepare(plan.stage2[k]));
+  int64_t mx = 1;
+  for (int d : lenv.at(center).basis.dim) mx = std::max<int64_t>(mx, d);
+  for (int d : renv.at(center + 2).basis.dim) mx = std::max<int64_t>(mx, d);
+  if (mx > ones_n) {
+    if (dones) ex->release(dones);
+    std::vector<double> one(mx, 1.0);
+    dones = ex->alloc(mx);
+    ex->upload(dones, one.data(), mx);
+    ones_n = mx;
+  }
+  diag_launch = plan_diag(Lp, Rp, lay, I, dones);
+  if (ddiag) ex->release(ddiag);
+  ddiag = ex->alloc(std::max<int64_t>(1, lay.size));
+  ex->run(diag_launch, 0, ddiag);
+  have_env = true;
+}
+
+void Engine::heff(uint64_t psi, uint64_t sig, void* stream, int prec) {
+  pr->zero_async(sig, lay.size, stream);
+  for (auto& h : prepared) {
+    pr->run_prepared(h.first, psi, sig, stream, prec);
+    pr->run_prepared(h.second, psi, sig, stream, prec);
+  }
+}
+
+DavResult Engine::davidson(const DavOpts& o) {
+  DavResult R;
+  const int64_t n = lay.size;
+  if (n == 0) throw std::runtime_error("empty wavefunction");
+  const int mmax = std::max(2, std::min(o.m_max, 64));
+  void* st = pr->stream();
+  std::vector<uint64_t> V(mmax), W(mmax);
+  for (int k = 0; k < mmax; ++k) {
+    V[k] = ex->alloc(n);
+    W[k] = ex->alloc(n);
+  }
+  uint64_t x = ex->alloc(n), w = ex->alloc(n), r = ex->alloc(n), t = ex->alloc(n);
+  uint64_t xp = ex->alloc(n), wp = ex->alloc(n);   // previous Ritz pair (restart)
+  bool have_prev = false;
+  auto cleanup = [&]() {
+    for (int k = 0; k < mmax; ++k) {
+      ex->release(V[k]);
+      ex->release(W[k]);
+    }
+    ex->release(x); ex->release(w); ex->release(r); ex->release(t);
+    ex->release(xp); ex->release(wp);
+  };
+  try {
+    int prec = o.policy ? 2 : o.precision;   // policy 1 starts in BF16
+    auto apply = [&](uint64_t in, uint64_t out) {
+      heff(in, out, st, prec);
+      pr->sync(st);
+      if (pr->take_error()) throw std::runtime_error("tensor-core kernel wait gave up");
+      R.hpsi[prec]++;
+    };
+    ex->copy(V[0], dpsi, n);
+    double nrm = std::sqrt(ex->dot(V[0], V[0], n));
+    if (nrm == 0) throw std::runtime_error("zero initial vector");
+    ex->scale(V[0], 1.0 / nrm, n);
+    apply(V[0], W[0]);
+    int m = 1;
+    std::vector<double> Hs((size_t)mmax * mmax, 0.0);
+    Hs[0] = ex->dot(V[0], W[0], n);
+    double theta = Hs[0];
+    for (int it = 0; it < o.max_iter; ++it) {
+      R.iters = it + 1;
+      std::vector<double> hs((size_t)m * m), ev, vec;
+      for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) hs[(size_t)i * m + j] = 0.5 * (Hs[(size_t)i * mmax + j] + Hs[(size_t)j * mmax + i]);
+      small_eigh(hs, m, ev, vec);
+      theta = ev[0];
+      if (it > 0) {
+        ex->copy(xp, x, n);
+        ex->copy(wp, w, n);
+        have_prev = true;
+      }
+      ex->zero(x, n);
+      ex->zero(w, n);
+      for (int k = 0; k < m; ++k) {
+        double y = vec[(size_t)k * m + 0];
+        ex->axpby(x, y, V[k], 1.0, n);
+        ex->axpby(w, y, W[k], 1.0, n);
+      }
+      ex->copy(r, w, n);
+      ex->axpby(r, -theta, x, 1.0, n);
+      double rn = std::sqrt(ex->dot(r, r, n));
+      R.resid = rn;
+      R.energy = theta;
+      int nprec = prec;
+      if (o.policy) {
+        if (prec == 2 && rn < o.tau1) nprec = 3;
+        if (prec == 3 && rn < o.tau2) nprec = 0;
+        if (prec != 0 && rn < o.tol) nprec = 0;
+      }
+      if (nprec != prec) {  // restart from the Ritz vector with the new precision
+        if (prec == 3) R.energy_mixed = theta;
+        prec = nprec;
+        double xn = std::sqrt(ex->dot(x, x, n));
+        ex->copy(V[0], x, n);
+        ex->scale(V[0], 1.0 / xn, n);
+        apply(V[0], W[0]);
+        m = 1;
+        Hs[0] = ex->dot(V[0], W[0], n);
+        have_prev = false;
+        continue;
+      }
+      if (rn < o.tol && prec == (o.policy ? 0 : o.precision)) {
+        R.converged = true;
+        break;
+      }
+      // correction vector: preconditioned residual, orthogonalised twice
+      ex->precond(t, r, ddiag, theta, o.floor, n);
+      for (int pass = 0; pass < 2; ++pass)
+        for (int k = 0; k < m; ++k) {
+          double c = ex->dot(V[k], t, n);
+          ex->axpby(t, -c, V[k], 1.0, n);
+        }
+      double tn = std::sqrt(ex->dot(t, t, n));
+      if (!(tn > 1e-14)) {  // no new direction: take the residual itself
+        ex->copy(t, r, n);
+        for (int pass = 0; pass < 2; ++pass)
+          for (int k = 0; k < m; ++k) {
+            double c = ex->dot(V[k], t, n);
+            ex->axpby(t, -c, V[k], 1.0, n);
+          }
+        tn = std::sqrt(ex->dot(t, t, n));
+        if (!(tn > 1e-14)) { R.converged = rn < o.tol; break; }
+      }
+      if (m == mmax) {  // restart: keep the Ritz vector and the previous one
+        double xn = std::sqrt(ex->dot(x, x, n));
+        ex->copy(V[0], x, n);
+        ex->scale(V[0], 1.0 / xn, n);
+        ex->copy(W[0], w, n);
+        ex->scale(W[0], 1.0 / xn, n);
+        m = 1;
+        Hs[0] = ex->dot(V[0], W[0], n);
+        if (have_prev) {  // V1 = xp - (V0.xp) V0 normalised; W1 by the same combination
+          double c = ex->dot(V[0], xp, n);
+          ex->copy(V[1], xp, n);
+          ex->axpby(V[1], -c, V[0], 1.0, n);
+          ex->copy(W[1], wp, n);
+          ex->axpby(W[1], -c, W[0], 1.0, n);
+          double c2 = ex->dot(V[0], V[1], n);   // second pass
+          ex->axpby(V[1], -c2, V[0], 1.0, n);
+          ex->axpby(W[1], -c2, W[0], 1.0, n);
+          double vn = std::sqrt(ex->dot(V[1], V[1], n));
+          if (vn > 1e-3) {  // W1 by cancellation is only accurate when V1 is well conditioned
+            ex->scale(V[1], 1.0 / vn, n);
+            ex->scale(W[1], 1.0 / vn, n);
+            double h01 = ex->dot(V[0], W[1], n), h11 = ex->dot(V[1], W[1], n);
+            Hs[1] = h01;
+            Hs[(size_t)mmax] = h01;
+            Hs[(size_t)mmax + 1] = h11;
+            m = 2;
+          }
+        }
+        for (int pass = 0; pass < 2; ++pass)
+          for (int k = 0; k < m; ++k) {
+            double c = ex->dot(V[k], t, n);
+            ex->axpby(t, -c, V[k], 1.0, n);
+          }
+        tn = std::sqrt(ex->dot(t, t, n));
+      }
+      ex->copy(V[m], t, n);
+      ex->scale(V[m], 1.0 / tn, n);
+      apply(V[m], W[m]);
+      for (int i = 0; i <= m; ++i) {
+        double v = ex->dot(V[i], W[m], n);
+        Hs[(size_t)i * mmax + m] = v;
+        Hs[(size_t)m * mmax + i] = v;
+      }
+      ++m;
+    }
+    // store the normalised Ritz vector as the new wavefunction
+    double xn = std::sqrt(ex->dot(x, x, n));
+    ex->copy(dpsi, x, n);
+    ex->scale(dpsi, 1.0 / xn, n);
+  } catch (...) {
+    cleanup();
+    throw;
+  }
+  cleanup();
+  return R;
+}
+
+double Engine::truncate_move(int D, int dir, double drop_below) {
+  const QN target{N, two_s};
+  const ProdBasis& LB = Lp.pb;
+  const ProdBasis& RB = Rp.pb;
+  // sector matrices Psi_q [(x,i) rows of L' sector q, (j,y) cols of R' sector]
+  struct Sec { int lq, rq, rows, cols; int64_t off; int64_t roff; };
+  std::vector<Sec> secs;
+  std::vector<int> sec_of_l(LB.prod.nsec(), -1), sec_of_r(RB.prod.nsec(), -1);
+  int64_t tot = 0, rtot = 0;
+  for (int lq = 0; lq < LB.prod.nsec(); ++lq) {
+    int rq = RB.prod.find(target - LB.prod.q[lq]);
+    if (rq < 0) continue;
+    Sec s{lq, rq, LB.prod.dim[lq], RB.prod.dim[rq], tot, rtot};
+    int ne = dir > 0 ? s.rows : s.cols;
+    tot += (int64_t)s.rows * s.cols;
+    rtot += (int64_t)ne * ne;
+    sec_of_l[lq] = (int)secs.size();
+    sec_of_r[rq] = (int)secs.size();
+    secs.push_back(s);
+  }
+  uint64_t Psi = ex->alloc(std::max<int64_t>(1, tot));
+  uint64_t Rho = ex->alloc(std::max<int64_t>(1, rtot));
+  {
+    Launch g;
+    for (const auto& b : lay.blks) {
+      const Sub& sl = LB.subs[b.lsub];
+      const Sub& sr = RB.subs[b.rsub];
+      const Sec& s = secs.at(sec_of_l[sl.prod]);
+      Seg e;
+      e.a = 0; e.b = dpsi + 8ull * b.off; e.ldb = b.cols; e.k = b.rows;
+      g.probs.push_back(copy_prob(Psi + 8ull * (s.off + (int64_t)sl.off * s.cols + sr.off), b.rows, b.cols, s.cols,
+                                  (int)g.segs.size()));
+      g.segs.push_back(e);
+    }
+    ex->run(g, 0, 0);
+    Launch h;
+    for (const auto& s : secs) {
+      Seg e;
+      uint64_t P = Psi + 8ull * s.off;
+      if (dir > 0) {  // rho = Psi Psi^T
+        e.a = P; e.lda = s.cols; e.ta = 0; e.b = P; e.ldb = s.cols; e.tb = 1; e.k = s.cols;
+        h.probs.push_back(copy_prob(Rho + 8ull * s.roff, s.rows, s.rows, s.rows, (int)h.segs.size()));
+      } else {        // rho = Psi^T Psi
+        e.a = P; e.lda = s.cols; e.ta = 1; e.b = P; e.ldb = s.cols; e.tb = 0; e.k = s.rows;
+        h.probs.push_back(copy_prob(Rho + 8ull * s.roff, s.cols, s.cols, s.cols, (int)h.segs.size()));
+      }
+      h.segs.push_back(e);
+    }
+    ex->run(h, 0, 0);
+  }
+  // eigen-decompositions and the global selection of the D largest weights
+  std::vector<std::vector<double>> lam(secs.size());
+  std::vector<std::tuple<double, QN, int, int>> cand;  // (-lambda, left label, index in sector (desc), sector)
+  for (size_t k = 0; k < secs.size(); ++k) {
+    int ne = dir > 0 ? secs[k].rows : secs[k].cols;
+    lam[k].resize(ne);
+    ex->eigh(Rho + 8ull * secs[k].roff, ne, lam[k].data());
+    for (int j = 0; j < ne; ++j) cand.emplace_back(-lam[k][ne - 1 - j], LB.prod.q[secs[k].lq], j, (int)k);
+  }
+  std::sort(cand.begin(), cand.end(), [](const auto& a, const auto& b) {
+    if (std::get<0>(a) != std::get<0>(b)) return std::get<0>(a) < std::get<0>(b);
+    if (std::get<1>(a) != std::get<1>(b)) return std::get<1>(a) < std::get<1>(b);
+    return std::get<2>(a) < std::get<2>(b);
+  });
+  std::vector<int> keep(secs.size(), 0);
+  double disc = 0;
+  int nk = 0;
+  for (auto& c : cand) {
+    double l = -std::get<0>(c);
+    if (nk < D && l > drop_below) {
+      keep[std::get<3>(c)]++;
+      ++nk;
+    } else {
+      disc += std::max(0.0, l);
+    }
+  }
+  if (nk == 0) throw std::runtime_error("truncation kept no state");
+  // new bond basis
+  Basis nb;
+  std::vector<int> nb_of_sec(secs.size(), -1);
+  {
+    std::vector<std::pair<QN, int>> lab;
+    for (size_t k = 0; k < secs.size(); ++k)
+      if (keep[k]) lab.push_back({dir > 0 ? LB.prod.q[secs[k].lq] : RB.prod.q[secs[k].rq], (int)k});
+    std::sort(lab.begin(), lab.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+    for (auto& x : lab) {
+      nb_of_sec[x.second] = nb.nsec();
+      nb.add(x.first, keep[x.second]);
+    }
+  }
+  // new site tensor
+  const ProdBasis& PB = dir > 0 ? LB : RB;
+  std::vector<int64_t> toff(PB.prod.nsec(), -1);
+  std::vector<int> tnb(PB.prod.nsec(), -1);
+  int64_t ttot = 0;
+  for (size_t k = 0; k < secs.size(); ++k) {
+    if (!keep[k]) continue;
+    int q = dir > 0 ? secs[k].lq : secs[k].rq;
+    int ne = dir > 0 ? secs[k].rows : secs[k].cols;
+    toff[q] = ttot;
+    tnb[q] = nb_of_sec[k];
+    ttot += (int64_t)ne * keep[k];
+  }
+  uint64_t T = ex->alloc(std::max<int64_t>(1, ttot));
+  {
+    Launch g;
+    for (size_t k = 0; k < secs.size(); ++k) {
+      if (!keep[k]) continue;
+      int q = dir > 0 ? secs[k].lq : secs[k].rq;
+      int ne = dir > 0 ? secs[k].rows : secs[k].cols;
+      int d = keep[k];
+      uint64_t ev = Rho + 8ull * (secs[k].roff + (int64_t)(ne - d) * ne);  // last d eigenvectors
+      Seg e;
+      e.a = 0; e.b = ev; e.ldb = ne; e.k = dir > 0 ? ne : d;
+      if (dir > 0) {  // U_q[r][k] = evec_k[r]: transpose of the column-major block
+        e.tb = 1;
+        g.probs.push_back(copy_prob(T + 8ull * toff[q], ne, d, d, (int)g.segs.size()));
+      } else {        // V_q[k][c] = evec_k[c]: same memory order
+        e.tb = 0;
+        g.probs.push_back(copy_prob(T + 8ull * toff[q], d, ne, ne, (int)g.segs.size()));
+      }
+      g.segs.push_back(e);
+    }
+    ex->run(g, 0, 0);
+  }
+  double fl = 0;
+  // C = U^T Psi (right move) or Psi V^T (left move)
+  std::vector<int64_t> coff(secs.size(), -1);
+  int64_t ctot = 0;
+  for (size_t k = 0; k < secs.size(); ++k) {
+    if (!keep[k]) continue;
+    coff[k] = ctot;
+    ctot += (int64_t)keep[k] * (dir > 0 ? secs[k].cols : secs[k].rows);
+  }
+  uint64_t Cb = ex->alloc(std::max<int64_t>(1, ctot));
+  {
+    Launch g;
+    for (size_t k = 0; k < secs.size(); ++k) {
+      if (!keep[k]) continue;
+      const Sec& s = secs[k];
+      int q = dir > 0 ? s.lq : s.rq;
+      int d = keep[k];
+      Seg e;
+      uint64_t P = Psi + 8ull * s.off, U = T + 8ull * toff[q];
+      if (dir > 0) {
+        e.a = U; e.lda = d; e.ta = 1; e.b = P; e.ldb = s.cols; e.tb = 0; e.k = s.rows;
+        g.probs.push_back(copy_prob(Cb + 8ull * coff[k], d, s.cols, s.cols, (int)g.segs.size()));
+      } else {
+        e.a = P; e.lda = s.cols; e.ta = 0; e.b = U; e.ldb = s.cols; e.tb = 1; e.k = s.cols;
+        g.probs.push_back(copy_prob(Cb + 8ull * coff[k], s.rows, d, d, (int)g.segs.size()));
+      }
+      g.segs.push_back(e);
+    }
+    ex->run(g, 0, 0);
+  }
+  const int c = center;
+  // new block and new centre
+  if (dir > 0) {
+    EnvBlock blk;
+    blk.cut = c + 1;
+    renormalize(Lp, nb, tnb, T, toff, *ex, blk, tmp_budget, &fl);
+    site[c] = T;
+    site_off[c] = toff;
+    site_nb[c] = tnb;
+    bonds[c + 1] = nb;
+    lenv[c + 1] = blk;
+    // psi'(x', i', j', y') = C[x' rows, (i', y) cols] V_{c+2}[y, (j', y')]
+    ProdBasis nL = make_prod(bonds[c + 1], true), nR = make_prod(bonds[c + 3], false);
+    PsiLayout nl = make_psi_layout(nL, nR, target);
+    ProdBasis R3 = make_prod(bonds[c + 3], false);
+    uint64_t np = ex->alloc(std::max<int64_t>(1, nl.size));
+    Launch g;
+    for (const auto& b : nl.blks) {
+      QN ylab = SITE_QN[b.j] + bonds[c + 3].q[b.y];
+      int y = bonds[c + 2].find(ylab);
+      if (y < 0) continue;
+      int sR = RB.find(y, b.i);                       // old R' sub (i', y)
+      int k = sec_of_r[RB.subs[sR].prod];
+      if (k < 0 || !keep[k]) continue;
+      const Sec& s = secs[k];
+      int r = R3.find(b.y, b.j);                      // product sub (j', y') of site c+2
+      int rp = R3.subs[r].prod;
+      Seg e;
+      e.a = Cb + 8ull * (coff[k] + RB.subs[sR].off); e.lda = s.cols; e.ta = 0;
+      e.b = site[c + 2] + 8ull * (site_off[c + 2][rp] + R3.subs[r].off); e.ldb = R3.prod.dim[rp]; e.tb = 0;
+      e.k = bonds[c + 2].dim[y];
+      g.probs.push_back(copy_prob(np + 8ull * b.off, b.rows, b.cols, b.cols, (int)g.segs.size()));
+      g.segs.push_back(e);
+    }
+    ex->run(g, 0, 0);
+    ex->release(site[c + 2]);
+    site[c + 2] = 0;
+    free_block(renv.at(c + 2));
+    renv.erase(c + 2);
+    bonds[c + 2] = Basis();
+    ex->release(dpsi);
+    dpsi = np;
+    center = c + 1;
+  } else {
+    EnvBlock blk;
+    blk.cut = c + 1;
+    renormalize(Rp, nb, tnb, T, toff, *ex, blk, tmp_budget, &fl);
+    site[c + 1] = T;
+    site_off[c + 1] = toff;
+    site_nb[c + 1] = tnb;
+    bonds[c + 1] = nb;
+    renv[c + 1] = blk;
+    // psi'(x', i', j', y') = U_{c-1}[(x', i') rows -> x] C[(x, j') rows, y' cols]
+    ProdBasis nL = make_prod(bonds[c - 1], true), nR = make_prod(bonds[c + 1], false);
+    PsiLayout nl = make_psi_layout(nL, nR, target);
+    ProdBasis L1 = make_prod(bonds[c - 1], true);
+    uint64_t np = ex->alloc(std::max<int64_t>(1, nl.size));
+    Launch g;
+    for (const auto& b : nl.blks) {
+      QN xlab = bonds[c - 1].q[b.x] + SITE_QN[b.i];
+      int x = bonds[c].find(xlab);
+      if (x < 0) continue;
+      int sL = LB.find(x, b.j);                       // old L' sub (x, j')
+      int k = sec_of_l[LB.subs[sL].prod];
+      if (k < 0 || !keep[k]) continue;
+      int d = keep[k];
+      int u = L1.find(b.x, b.i);                      // product sub (x', i') of site c-1
+      int up = L1.subs[u].prod;
+      Seg e;
+      e.a = site[c - 1] + 8ull * (site_off[c - 1][up] + (int64_t)L1.subs[u].off * bonds[c].dim[x]);
+      e.lda = bonds[c].dim[x]; e.ta = 0;
+      e.b = Cb + 8ull * (coff[k] + (int64_t)LB.subs[sL].off * d); e.ldb = d; e.tb = 0;
+      e.k = bonds[c].dim[x];
+      g.probs.push_back(copy_prob(np + 8ull * b.off, b.rows, b.cols, b.cols, (int)g.segs.size()));
+      g.segs.push_back(e);
+    }
+    ex->run(g, 0, 0);
+    ex->release(site[c - 1]);
+    site[c - 1] = 0;
+    free_block(lenv.at(c));
+    lenv.erase(c);
+    bonds[c] = Basis();
+    ex->release(dpsi);
+    dpsi = np;
+    center = c - 1;
+  }
+  ex->release(Psi);
+  ex->release(Rho);
+  ex->release(Cb);
+  env_flops += fl;
+  prepare_center();
+  return disc;
+}
+
+}  // namespace qd

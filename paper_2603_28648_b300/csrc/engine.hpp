@@ -1,0 +1,72 @@
+// Sweep engine: MPS, renormalized blocks, H_eff plan, Davidson, truncation.
+#pragma once
+#include <map>
+#include <vector>
+
+#include "core.hpp"
+#include "kernels.hpp"
+
+namespace qd {
+
+struct DavOpts {
+  double tol = 1e-6;        // residual 2-norm (normalised vector), Numerical procedure section
+  int max_iter = 300;
+  int m_max = 32;           // subspace size before restart
+  int policy = 0;           // 0: fixed precision, 1: BF16 -> BF16x3 -> FP64 correction
+  int precision = 0;        // fixed precision (policy 0)
+  double tau1 = 1e-2, tau2 = 1e-5;
+  double floor = 1e-8;      // |diag - theta| floor of the preconditioner
+};
+
+struct DavResult {
+  double energy = 0, resid = 0;
+  double energy_mixed = 0;  // last Ritz value before the FP64 correction (policy 1)
+  int iters = 0;
+  int hpsi[4] = {0, 0, 0, 0};  // H psi products per precision
+  bool converged = false;
+};
+
+struct Engine {
+  Executor* ex = nullptr;
+  PreparedRunner* pr = nullptr;
+  Integrals I;
+  int N = 0, two_s = 0, L = 0, center = -1;
+  int64_t tmp_budget = 0;
+  // MPS: bonds (left labels for b <= center, right labels for b >= center+2),
+  // site tensors (product-sector matrices) for every site except the centre pair
+  std::vector<Basis> bonds;
+  std::vector<uint64_t> site;
+  std::vector<std::vector<int64_t>> site_off;
+  std::vector<std::vector<int>> site_nb;
+  // renormalized blocks by cut
+  std::map<int, EnvBlock> lenv, renv;
+  // centre
+  bool have_env = false;
+  Enlarged Lp, Rp;
+  PsiLayout lay;
+  HeffPlan plan;
+  std::vector<std::pair<int, int>> prepared;
+  Launch diag_launch;
+  uint64_t dpsi = 0, ddiag = 0, dones = 0;
+  int64_t ones_n = 0;
+  double env_flops = 0, env_seconds = 0;
+
+  ~Engine() { clear(); }
+  void clear();
+  void clear_env();
+  void free_block(EnvBlock& b);
+  void free_enlarged(Enlarged& e);
+  void set_psi_host(const std::vector<double>& h);
+  std::vector<double> get_psi_host();
+
+  // blocks [0, center) and [center+2, L), then the centre plan
+  void build_env();
+  void prepare_center();
+  void heff(uint64_t psi, uint64_t sig, void* stream, int prec);
+  DavResult davidson(const DavOpts& o);
+  // truncate the centre to D states (drop weights <= drop_below), renormalize
+  // and move the centre by dir (+1 right, -1 left); returns the discarded weight
+  double truncate_move(int D, int dir, double drop_below);
+};
+
+}  // namespace qd
