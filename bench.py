@@ -35,7 +35,8 @@ def parse():
     ap.add_argument("--D", type=int, default=1024)
     ap.add_argument("--L", type=int, default=36)
     ap.add_argument("--N", type=int, default=54)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "tf32", "bf16", "bf16x3"])
+    ap.add_argument("--precision", default="bf16", choices=["fp64", "tf32", "bf16", "bf16x3"],
+                    help="form whose throughput is the headline value (all forms are timed)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="bracket the timed region with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
@@ -88,6 +89,16 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def measured_peaks():
+    """Measured peaks of this machine (MEASURED_PEAKS.json), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {"bf16": float(d["bf16_tflops"]), "hbm": float(d["hbm_gbs"]), "source": "measured"}
+    except Exception:
+        return {"bf16": 1800.0, "hbm": 6400.0, "source": "fallback"}
 
 
 def fp64_peak_tflops(torch):
@@ -208,34 +219,53 @@ def run_ours(args, rank, world, local):
     sig = torch.empty_like(psi)
     stream = torch.cuda.current_stream()
 
-    prec = qd.PRECISIONS[args.precision]
+    head = qd.PRECISIONS[args.precision]
 
-    def step():
+    def step(prec):
         ctx.apply_heff_dev(psi.data_ptr(), sig.data_ptr(), stream.cuda_stream, prec)
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    clocks = Clocks(local)
-    clocks.start()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if args.profile:
-        torch.cuda.profiler.start()
-    ev0.record(stream)
-    for _ in range(args.steps):
-        step()
-    ev1.record(stream)
-    if args.profile:
+    def timed(prec, steps, clocks=None, profile=False):
+        for _ in range(args.warmup):
+            step(prec)
         torch.cuda.synchronize()
-        torch.cuda.profiler.stop()
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    elapsed = ev0.elapsed_time(ev1) / 1e3
+        if clocks:
+            clocks.start()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if profile:
+            torch.cuda.profiler.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            step(prec)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if profile:
+            torch.cuda.profiler.stop()
+        if dist:
+            dist.barrier()
+        ctx.check_device()
+        return e0.elapsed_time(e1) / 1e3
+
+    forms = {}
+    energies = {}
+    for name, prec in qd.PRECISIONS.items():
+        if name == args.precision:
+            continue
+        t = timed(prec, max(2, args.steps // 2))
+        energies[name] = float(torch.dot(psi, sig).item())
+        forms[name] = {"tflops": flops / (t / max(2, args.steps // 2)) / 1e12,
+                       "ms_per_step": t / max(2, args.steps // 2) * 1e3}
+    clocks = Clocks(local)
+    elapsed = timed(head, args.steps, clocks, args.profile)
     clk = clocks.stop()
+    energies[args.precision] = float(torch.dot(psi, sig).item())
+    forms[args.precision] = {"tflops": flops / (elapsed / args.steps) / 1e12,
+                             "ms_per_step": elapsed / args.steps * 1e3}
+    for name in forms:
+        forms[name]["energy_minus_fp64"] = energies[name] - energies["fp64"]
+        forms[name]["speedup_vs_fp64"] = forms["fp64"]["ms_per_step"] / forms[name]["ms_per_step"]
     # end to end through the public API: pinned host psi -> device, H psi, sigma -> host
     hpsi = psi.cpu().pin_memory()
     hsig = torch.empty_like(hpsi).pin_memory()
@@ -244,13 +274,12 @@ def run_ours(args, rank, world, local):
     e0.record(stream)
     for _ in range(args.steps):
         psi.copy_(hpsi, non_blocking=True)
-        step()
+        step(head)
         hsig.copy_(sig, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_t = e0.elapsed_time(e1) / 1e3
-    # check: sigma is finite and <psi|H|psi> is real
-    energy = float(torch.dot(psi, sig).item())
+    energy = energies[args.precision]
     if dist:
         tt = torch.tensor([elapsed, e2e_t], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -272,6 +301,18 @@ def run_ours(args, rank, world, local):
                "sample": "U(1) L=10 N=10 D=64 centre-bond H_eff psi, oracle dense FP64 "
                          "(environment build excluded), 3 timed repetitions"}
     achieved = flops / per_step / 1e12
+    pk = measured_peaks()
+    if args.precision == "fp64":
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "measured cuBLAS DGEMM 4096^3 on this GPU (FP64 FMA)"}
+    else:
+        ratio = {"bf16": 1.0, "tf32": 1.1 / 2.25, "bf16x3": 1.0 / 6.0}[args.precision]
+        p = pk["bf16"] * ratio
+        roof = {"bound": "tensor", "achieved": achieved, "peak": p, "unit": "TFLOP/s",
+                "frac": achieved / p, "traffic": None,
+                "peak_source": f"{pk['source']} BF16 dense burst {pk['bf16']} TFLOP/s x {ratio:.4f} "
+                               "(TF32: nominal 1.1/2.25 ratio; BF16x3: six BF16 products per useful product)"}
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
@@ -283,15 +324,16 @@ def run_ours(args, rank, world, local):
                    "heff_gflop": flops / 1e9, "env_build_s": env_s,
                    "env_build_tflops": st["env_flops"] / env_s / 1e12,
                    "l2": "operator blocks read per step exceed L2 (no flush needed)",
-                   "device_bytes": st["device_bytes"], "energy_check": energy,
+                   "device_bytes": st["device_bytes"], "energy_psi_h_psi": energy,
+                   "forms": forms, "fp64_peak_tflops_measured": peak,
                    "parallelism": f"replicas{world}"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "peak_source": "measured cuBLAS DGEMM 4096^3 on this GPU (FP64)"},
+        "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": "TFLOP/s", "h2d_bytes_per_step": int(psi.numel() * 8),
                 "d2h_bytes_per_step": int(sig.numel() * 8)},
         "gpu_launches": int(st["nlaunch"]) * args.steps,
+        "gpu_launches_note": "per step: 2 launches of the grouped GEMM kernel per task-list chunk "
+                             "(plus one cudaMemsetAsync of sigma)",
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)

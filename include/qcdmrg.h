@@ -241,6 +241,26 @@ int qcdmrg_sweep(qcdmrg_ctx* ctx, const qcdmrg_sweep_opts* opts, qcdmrg_sweep_re
  * _dev calls (synchronous). Errors: ETIMEOUT if a bounded wait gave up. */
 int qcdmrg_check_device(qcdmrg_ctx* ctx);
 
+/*
+ * Batched H_eff psi in one CUDA graph (the batching pattern of the task: all
+ * quantum-number blocks of one or several independent H_eff psi products in
+ * one replay). The H_eff psi of each context (memset of sigma plus its
+ * grouped-GEMM launches) is captured once, contexts as parallel branches,
+ * with psi[i] and sigma[i] (device arrays of each context's psi size) baked
+ * into the graph; qcdmrg_graph_launch replays it on a stream. The contexts'
+ * environments must stay unchanged while the graph is used (build_env,
+ * truncate or sweep invalidate it). All contexts on one device. Errors:
+ * EINVAL, ESTATE (a context without environment), ECUDA (message in the first
+ * context).
+ */
+typedef struct qcdmrg_graph qcdmrg_graph;
+int qcdmrg_graph_create(qcdmrg_ctx* const* ctxs, int n, int precision, const void* const* psi,
+                        void* const* sigma, qcdmrg_graph** out);
+int qcdmrg_graph_launch(qcdmrg_graph* graph, void* stream);
+/* Algorithmic flops of one replay and number of graph nodes. */
+int qcdmrg_graph_info(const qcdmrg_graph* graph, double* flops, int* nodes);
+int qcdmrg_graph_destroy(qcdmrg_graph* graph);
+
 /* Counters of the last calls. */
 int qcdmrg_stats(const qcdmrg_ctx* ctx, qcdmrg_stats_t* out);
 

@@ -69,6 +69,8 @@ EXPORTS = [
     "qcdmrg_apply_heff", "qcdmrg_apply_heff_dev", "qcdmrg_stats", "qcdmrg_init_mps",
     "qcdmrg_get_bond", "qcdmrg_get_psi", "qcdmrg_check_device", "qcdmrg_davidson",
     "qcdmrg_truncate", "qcdmrg_move_center", "qcdmrg_sweep", "qcdmrg_heff_diag",
+    "qcdmrg_graph_create", "qcdmrg_graph_launch",
+    "qcdmrg_graph_info", "qcdmrg_graph_destroy",
 ]
 
 _lib = None
@@ -106,6 +108,11 @@ def load(path=None):
     lib.qcdmrg_truncate.argtypes = [P, ctypes.c_int, ctypes.c_int, dp]
     lib.qcdmrg_move_center.argtypes = [P, ctypes.c_int]
     lib.qcdmrg_heff_diag.argtypes = [P, dp, ctypes.c_size_t]
+    lib.qcdmrg_graph_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P)]
+    lib.qcdmrg_graph_launch.argtypes = [P, P]
+    lib.qcdmrg_graph_info.argtypes = [P, dp, ctypes.POINTER(ctypes.c_int)]
+    lib.qcdmrg_graph_destroy.argtypes = [P]
     lib.qcdmrg_sweep.argtypes = [P, ctypes.POINTER(SweepOpts), ctypes.POINTER(SweepReport)]
     for f in EXPORTS:
         getattr(lib, f).restype = getattr(lib, f).restype or ctypes.c_int
@@ -242,3 +249,41 @@ class Context:
         s = Stats()
         self._check(self.lib.qcdmrg_stats(self.h, ctypes.byref(s)))
         return {f: getattr(s, f) for f, _ in Stats._fields_}
+
+
+class HeffGraph:
+    """H_eff psi of one or several contexts captured in one CUDA graph."""
+
+    def __init__(self, contexts, psi_ptrs, sigma_ptrs, precision=FP64):
+        self.lib = contexts[0].lib
+        n = len(contexts)
+        P = ctypes.c_void_p
+        ctxs = (P * n)(*[c.h.value for c in contexts])
+        ps = (P * n)(*psi_ptrs)
+        ss = (P * n)(*sigma_ptrs)
+        self.h = P()
+        rc = self.lib.qcdmrg_graph_create(ctxs, n, precision, ps, ss, ctypes.byref(self.h))
+        if rc != QCDMRG_OK:
+            raise QcdmrgError(rc, self.lib.qcdmrg_last_error(contexts[0].h).decode())
+        self._ctx = contexts
+
+    def launch(self, stream=0):
+        rc = self.lib.qcdmrg_graph_launch(self.h, ctypes.c_void_p(stream))
+        if rc != QCDMRG_OK:
+            raise QcdmrgError(rc, "graph launch failed")
+
+    def info(self):
+        f, n = ctypes.c_double(), ctypes.c_int()
+        self.lib.qcdmrg_graph_info(self.h, ctypes.byref(f), ctypes.byref(n))
+        return f.value, n.value
+
+    def close(self):
+        if self.h:
+            self.lib.qcdmrg_graph_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

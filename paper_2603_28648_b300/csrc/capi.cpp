@@ -12,6 +12,7 @@
 #include "core.hpp"
 #include "engine.hpp"
 #include "kernels.hpp"
+#include "graph.hpp"
 
 using namespace qd;
 
@@ -59,6 +60,9 @@ int guard(qcdmrg_ctx* c, F&& f) {
   } catch (const Fail& e) {
     c->err = e.msg;
     return e.code;
+  } catch (const StateError& e) {
+    c->err = e.what();
+    return QCDMRG_ESTATE;
   } catch (const std::bad_alloc&) {
     c->err = "host allocation failed";
     return QCDMRG_ENOMEM;
@@ -86,6 +90,9 @@ int qcdmrg_create(qcdmrg_ctx** out, const qcdmrg_config* cfg) {
     c->eng.ex = c->be.ex;
     c->eng.pr = c->be.pr;
     c->eng.tmp_budget = (int64_t)(gb * 1e9 / 8);
+  } catch (const std::invalid_argument&) {
+    delete c;
+    return QCDMRG_EINVAL;
   } catch (const std::exception& e) {
     delete c;
     return QCDMRG_ECUDA;
@@ -484,6 +491,60 @@ int qcdmrg_check_device(qcdmrg_ctx* ctx) {
     if (ctx->be.pr->take_error()) throw Fail{QCDMRG_ETIMEOUT, "a tensor-core kernel wait gave up"};
     return QCDMRG_OK;
   });
+}
+
+struct qcdmrg_graph {
+  HeffGraph* g = nullptr;
+};
+
+int qcdmrg_graph_create(qcdmrg_ctx* const* ctxs, int n, int precision, const void* const* psi,
+                        void* const* sigma, qcdmrg_graph** out) {
+  if (!ctxs || n < 1 || !psi || !sigma || !out) return QCDMRG_EINVAL;
+  *out = nullptr;
+  if (!valid_precision(precision)) return QCDMRG_EINVAL;
+  std::vector<Engine*> eng;
+  std::vector<uint64_t> ps, ss;
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i] || !psi[i] || !sigma[i] || psi[i] == sigma[i]) return QCDMRG_EINVAL;
+    if (!ctxs[i]->eng.have_env) return QCDMRG_ESTATE;
+    if (ctxs[i]->device != ctxs[0]->device) return QCDMRG_EINVAL;
+    eng.push_back(&ctxs[i]->eng);
+    ps.push_back((uint64_t)psi[i]);
+    ss.push_back((uint64_t)sigma[i]);
+  }
+  try {
+    auto* g = new qcdmrg_graph();
+    g->g = graph_create(eng, ps, ss, precision);
+    *out = g;
+  } catch (const std::exception& e) {
+    ctxs[0]->err = e.what();
+    return QCDMRG_ECUDA;
+  }
+  return QCDMRG_OK;
+}
+
+int qcdmrg_graph_launch(qcdmrg_graph* g, void* stream) {
+  if (!g || !g->g) return QCDMRG_EINVAL;
+  try {
+    graph_launch(g->g, stream);
+  } catch (const std::exception&) {
+    return QCDMRG_ECUDA;
+  }
+  return QCDMRG_OK;
+}
+
+int qcdmrg_graph_info(const qcdmrg_graph* g, double* flops, int* nodes) {
+  if (!g || !g->g) return QCDMRG_EINVAL;
+  if (flops) *flops = graph_flops(g->g);
+  if (nodes) *nodes = graph_nodes(g->g);
+  return QCDMRG_OK;
+}
+
+int qcdmrg_graph_destroy(qcdmrg_graph* g) {
+  if (!g) return QCDMRG_EINVAL;
+  graph_destroy(g->g);
+  delete g;
+  return QCDMRG_OK;
 }
 
 int qcdmrg_stats(const qcdmrg_ctx* ctx, qcdmrg_stats_t* out) {

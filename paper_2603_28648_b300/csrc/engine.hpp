@@ -1,12 +1,18 @@
 // Sweep engine: MPS, renormalized blocks, H_eff plan, Davidson, truncation.
 #pragma once
 #include <map>
+#include <stdexcept>
 #include <vector>
 
 #include "core.hpp"
 #include "kernels.hpp"
 
 namespace qd {
+
+// A call made in a state that does not allow it (maps to QCDMRG_ESTATE).
+struct StateError : std::runtime_error {
+  using std::runtime_error::runtime_error;
+};
 
 struct DavOpts {
   double tol = 1e-6;        // residual 2-norm (normalised vector), Numerical procedure section

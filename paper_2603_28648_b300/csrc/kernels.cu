@@ -264,6 +264,8 @@ class CudaExec : public Executor, public PreparedRunner {
   explicit CudaExec(int device) : dev_(device) {
     CK(cudaSetDevice(dev_));
     CK(cudaStreamCreateWithFlags(&st_, cudaStreamNonBlocking));
+    CK(cudaMalloc(&err_, sizeof(int)));
+    CK(cudaMemset(err_, 0, sizeof(int)));
   }
   ~CudaExec() override {
     cudaSetDevice(dev_);

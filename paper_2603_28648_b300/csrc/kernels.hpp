@@ -1,5 +1,7 @@
 // Backend interface shared by the C ABI and the CUDA executor.
 #pragma once
+#include <cuda_runtime.h>
+
 #include "core.hpp"
 
 namespace qd {

@@ -19,6 +19,7 @@
 //     + 2 sum_{i<j in L} (A_ij P_ij + A_ij^+ P_ij^+) + sum_{il in L} B_il Q_il.
 // A product O_X O_s on X (x) site acts as (O_X P_X^{p(O_s)}) (x) O_s; a
 // product O_s O_Y on site (x) Y as (O_s P_s^{p(O_Y)}) (x) O_Y.
+#include <algorithm>
 #include <cmath>
 #include <map>
 #include <stdexcept>
@@ -429,6 +430,7 @@ void enlarge(const EnvBlock& B, const Integrals& I, Executor& ex, Enlarged& E, d
   } else {
     const int c = B.cut - 1;      // site p = c, Y = [c+1, L)
     E.cut = c;
+    const int mc = 2 * c;                     // complementary operators for modes < 2c
     const int sm[2] = {2 * c, 2 * c + 1};
     const int y0 = 2 * (c + 1);
     x.view(Key(F_I), {C_(nullptr, false, I4, 1.0, false)}, false);
@@ -436,8 +438,8 @@ void enlarge(const EnvBlock& B, const Integrals& I, Executor& ex, Enlarged& E, d
     for (int k = y0; k < 2 * L; ++k)
       if (auto C = x.get(Key(F_C, k))) x.view(Key(F_C, k), {C_(C, false, I4, 1.0, true)}, true);
     // P'_ij, i < j < 2c
-    for (int i = 0; i < 2 * c; ++i)
-      for (int j = i + 1; j < 2 * c; ++j) {
+    for (int i = 0; i < mc; ++i)
+      for (int j = i + 1; j < mc; ++j) {
         std::vector<Contrib> cs;
         if (auto P = x.get(Key(F_P, i, j))) cs.push_back(C_(P, false, I4, 1.0, false));
         for (int s = 0; s < 2; ++s)
@@ -454,8 +456,8 @@ void enlarge(const EnvBlock& B, const Integrals& I, Executor& ex, Enlarged& E, d
         x.materialize(Key(F_P, i, j), cs, false);
       }
     // Q'_il, i, l < 2c
-    for (int i = 0; i < 2 * c; ++i)
-      for (int l = 0; l < 2 * c; ++l) {
+    for (int i = 0; i < mc; ++i)
+      for (int l = 0; l < mc; ++l) {
         std::vector<Contrib> cs;
         if (auto Q = x.get(Key(F_Q, i, l))) cs.push_back(C_(Q, false, I4, 1.0, false));
         for (int s = 0; s < 2; ++s)
@@ -474,7 +476,7 @@ void enlarge(const EnvBlock& B, const Integrals& I, Executor& ex, Enlarged& E, d
         x.materialize(Key(F_Q, i, l), cs, false);
       }
     // S'_m, m < 2c
-    for (int m = 0; m < 2 * c; ++m) {
+    for (int m = 0; m < mc; ++m) {
       std::vector<Contrib> cs;
       if (auto S = x.get(Key(F_S, m))) cs.push_back(C_(S, false, I4, 1.0, true));
       Mat4 t1;

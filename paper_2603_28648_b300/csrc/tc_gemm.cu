@@ -119,7 +119,11 @@ __device__ __forceinline__ uint32_t tile_off(int r, int k) {
 template <int MODE>
 __device__ __forceinline__ void put(unsigned char* base, uint32_t off, size_t split_stride, double v) {
   if constexpr (MODE == TC_TF32) {
-    *reinterpret_cast<float*>(base + off) = (float)v;
+    // round to nearest TF32 (the tensor core would otherwise drop the low
+    // mantissa bits, a biased truncation)
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"((float)v));
+    *reinterpret_cast<uint32_t*>(base + off) = r;
   } else if constexpr (MODE == TC_BF16) {
     *reinterpret_cast<__nv_bfloat16*>(base + off) = __float2bfloat16_rn((float)v);
   } else {
