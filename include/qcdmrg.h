@@ -199,6 +199,25 @@ int qcdmrg_apply_heff(qcdmrg_ctx* ctx, int precision, const double* psi, double*
 int qcdmrg_apply_heff_dev(qcdmrg_ctx* ctx, int precision, const void* psi, void* sigma,
                           void* stream);
 
+/*
+ * No counterpart in the paper: an H_eff psi that allocates nothing, for
+ * callers that cannot allocate device memory when they need the product
+ * (work being captured into a CUDA graph, a GPU whose free memory is held by
+ * another framework's caching allocator, solvers with a fixed memory budget).
+ * FP64 form only. The stage-1 intermediates go to a fixed 32 MiB device array
+ * (QCDMRG_NOALLOC_SCRATCH_DOUBLES doubles) compiled into the library, which
+ * every GPU that loads the library holds until exit; a problem whose
+ * intermediates need more is rejected with QCDMRG_EINVAL (a smaller
+ * tmp_budget_gb at qcdmrg_create makes the chunks fit). The first call on a
+ * device looks up the array's address with that device current; make that
+ * first call before any stream capture. All calls share the array and it
+ * keeps the last call's contents: calls whose work overlaps on the GPU race.
+ * psi, sigma: device arrays of psi_size doubles; stream: cudaStream_t (NULL is
+ * the legacy default stream). Errors: ESTATE, EINVAL, ECUDA.
+ */
+#define QCDMRG_NOALLOC_SCRATCH_DOUBLES (4 * 1024 * 1024)
+int qcdmrg_apply_heff_noalloc(qcdmrg_ctx* ctx, const void* psi, void* sigma, void* stream);
+
 /* Diagonal of H_eff at the centre (psi layout, n = psi size), as used by the
  * Davidson preconditioner: sum over terms of c_t diag(O_L) (x) diag(O_R)
  * restricted to diagonal quantum-number blocks. */

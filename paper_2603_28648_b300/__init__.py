@@ -69,7 +69,7 @@ EXPORTS = [
     "qcdmrg_apply_heff", "qcdmrg_apply_heff_dev", "qcdmrg_stats", "qcdmrg_init_mps",
     "qcdmrg_get_bond", "qcdmrg_get_psi", "qcdmrg_check_device", "qcdmrg_davidson",
     "qcdmrg_truncate", "qcdmrg_move_center", "qcdmrg_sweep", "qcdmrg_heff_diag",
-    "qcdmrg_graph_create", "qcdmrg_graph_launch",
+    "qcdmrg_apply_heff_noalloc", "qcdmrg_graph_create", "qcdmrg_graph_launch",
     "qcdmrg_graph_info", "qcdmrg_graph_destroy",
 ]
 
@@ -108,6 +108,7 @@ def load(path=None):
     lib.qcdmrg_truncate.argtypes = [P, ctypes.c_int, ctypes.c_int, dp]
     lib.qcdmrg_move_center.argtypes = [P, ctypes.c_int]
     lib.qcdmrg_heff_diag.argtypes = [P, dp, ctypes.c_size_t]
+    lib.qcdmrg_apply_heff_noalloc.argtypes = [P, P, P, P]
     lib.qcdmrg_graph_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, ctypes.c_int,
                                         ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P)]
     lib.qcdmrg_graph_launch.argtypes = [P, P]
@@ -219,6 +220,13 @@ class Context:
         if not (allow_notconv and rc == -5):
             self._check(rc)
         return e.value, r.value, it.value
+
+    def apply_heff_noalloc(self, psi_ptr, sigma_ptr, stream=0):
+        """FP64 H_eff psi on device arrays without any allocation in the call
+        (stage-1 intermediates in the library's fixed 32 MiB device array)."""
+        self._check(self.lib.qcdmrg_apply_heff_noalloc(self.h, ctypes.c_void_p(psi_ptr),
+                                                       ctypes.c_void_p(sigma_ptr),
+                                                       ctypes.c_void_p(stream)))
 
     def heff_diag(self):
         out = np.empty(self.psi_size())

@@ -12,6 +12,7 @@
 #include "core.hpp"
 #include "engine.hpp"
 #include "kernels.hpp"
+#include "noalloc.hpp"
 #include "graph.hpp"
 
 using namespace qd;
@@ -390,6 +391,21 @@ int qcdmrg_apply_heff_dev(qcdmrg_ctx* ctx, int precision, const void* psi, void*
     if (!valid_precision(precision)) throw Fail{QCDMRG_EINVAL, "unknown precision"};
     if (!psi || !sigma || psi == sigma) throw Fail{QCDMRG_EINVAL, "psi and sigma must be distinct device arrays"};
     ctx->eng.heff((uint64_t)psi, (uint64_t)sigma, stream, precision);
+    return QCDMRG_OK;
+  });
+}
+
+int qcdmrg_apply_heff_noalloc(qcdmrg_ctx* ctx, const void* psi, void* sigma, void* stream) {
+  return guard(ctx, [&]() {
+    Engine& E = ctx->eng;
+    if (!E.have_env) throw Fail{QCDMRG_ESTATE, "build_env first"};
+    if (!psi || !sigma || psi == sigma) throw Fail{QCDMRG_EINVAL, "psi and sigma must be distinct device arrays"};
+    if (E.plan.tmp_elems > NOALLOC_SCRATCH_DOUBLES)
+      throw Fail{QCDMRG_EINVAL, "this H_eff needs " + std::to_string(E.plan.tmp_elems) +
+                                    " doubles of scratch; the fixed array holds " +
+                                    std::to_string(NOALLOC_SCRATCH_DOUBLES) +
+                                    " (use qcdmrg_apply_heff_dev, or a smaller tmp_budget_gb)"};
+    heff_noalloc(E, ctx->device, (uint64_t)psi, (uint64_t)sigma, stream);
     return QCDMRG_OK;
   });
 }

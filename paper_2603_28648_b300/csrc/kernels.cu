@@ -484,6 +484,7 @@ class CudaExec : public Executor, public PreparedRunner {
     if (h) CK(cudaMemset(err_, 0, sizeof(int)));
     return h;
   }
+  const void* prepared_handle(int h) const override { return &prepared_.at(h); }
   void* stream() override { return st_; }
   void sync(void* stream) override { CK(cudaStreamSynchronize((cudaStream_t)stream)); }
   void zero_async(uint64_t p, int64_t n, void* stream) override {
@@ -538,6 +539,19 @@ class CudaExec : public Executor, public PreparedRunner {
   void* part_ = nullptr;
   size_t part_cap_ = 0;
 };
+
+cudaError_t launch_f64_prepared(const void* handle, uint64_t psi, uint64_t sig, uint64_t scratch,
+                                cudaStream_t st) {
+  const DevLaunch* d = static_cast<const DevLaunch*>(handle);
+  if (!d || !d->ntiles) return cudaSuccess;
+  Bases B;
+  B.b[0] = 0;
+  B.b[1] = psi;
+  B.b[2] = sig;
+  B.b[3] = scratch;
+  seg_gemm_f64<<<d->ntiles, 256, 0, st>>>(d->p, d->s, d->t, d->ntiles, B);
+  return cudaGetLastError();
+}
 
 Backend make_backend(int device) {
   auto* e = new CudaExec(device);

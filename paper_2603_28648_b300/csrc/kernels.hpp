@@ -15,6 +15,8 @@ struct PreparedRunner {
   virtual void run_prepared(int handle, uint64_t psi, uint64_t sig, void* stream, int precision) = 0;
   // returns and clears the device error flag of the tensor-core kernels
   virtual int take_error() = 0;
+  // opaque device task list of a prepared launch (for the no-allocation path)
+  virtual const void* prepared_handle(int handle) const = 0;
   virtual void* stream() = 0;
   virtual void sync(void* stream) = 0;
   virtual void zero_async(uint64_t p, int64_t n, void* stream) = 0;
@@ -28,5 +30,9 @@ struct Backend {
 
 // Creates the CUDA backend on a device (throws std::runtime_error on failure).
 Backend make_backend(int device);
+
+// Runs one prepared launch with the FP64 kernel, scratch base given by the caller.
+cudaError_t launch_f64_prepared(const void* handle, uint64_t psi, uint64_t sig, uint64_t scratch,
+                                cudaStream_t st);
 
 }  // namespace qd
