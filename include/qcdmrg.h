@@ -109,7 +109,8 @@ typedef struct {
   int m_max;      /* subspace size before a restart [32] */
   int policy;     /* 0: every H psi in `precision`; 1: BF16 while the residual is above tau1,
                      BF16x3 while above tau2, then FP64 H psi until converged (the final
-                     residual and energy are always from the FP64 form) */
+                     residual and energy are always from the FP64 form); a reduced-precision
+                     phase also ends when its residual has not halved in 6 iterations */
   int precision;  /* QCDMRG_FP64 / _TF32 / _BF16 / _BF16X3 for policy 0 */
   double tau1;    /* [1e-2] */
   double tau2;    /* [1e-5] */
@@ -174,6 +175,9 @@ int qcdmrg_get_bond(const qcdmrg_ctx* ctx, int bond, int* nsec, int* sec, int ca
 /* Copy the current two-site wavefunction (n = its size). */
 int qcdmrg_get_psi(const qcdmrg_ctx* ctx, double* out, size_t n);
 
+/* Replace the current two-site wavefunction (n = its size, host array). */
+int qcdmrg_set_psi(qcdmrg_ctx* ctx, const double* psi, size_t n);
+
 /*
  * Renormalize the left block up to the centre and the right block down to
  * it (the operator renormalization of every truncation step, replayed for
@@ -217,6 +221,17 @@ int qcdmrg_apply_heff_dev(qcdmrg_ctx* ctx, int precision, const void* psi, void*
  */
 #define QCDMRG_NOALLOC_SCRATCH_DOUBLES (4 * 1024 * 1024)
 int qcdmrg_apply_heff_noalloc(qcdmrg_ctx* ctx, const void* psi, void* sigma, void* stream);
+
+/*
+ * Spin-summed one-particle density matrix gamma_pq = <Psi|E_pq|Psi>/<Psi|Psi>
+ * (L*L row-major) of the current MPS state, which is the gradient dE/dh_pq of
+ * the energy at fixed wavefunction (the 1-RDM CASSCF orbital optimisation
+ * needs, DMRG-SCF of the paper's New benchmark system section). Measured with
+ * the stored operators at the centre (L-2, L-1), where the left enlarged
+ * block holds a+_k a_l for every orbital but the last: move the centre there
+ * first (qcdmrg_move_center(ctx, L-2)). Errors: ESTATE.
+ */
+int qcdmrg_rdm1(qcdmrg_ctx* ctx, double* gamma);
 
 /* Diagonal of H_eff at the centre (psi layout, n = psi size), as used by the
  * Davidson preconditioner: sum over terms of c_t diag(O_L) (x) diag(O_R)

@@ -70,7 +70,7 @@ EXPORTS = [
     "qcdmrg_get_bond", "qcdmrg_get_psi", "qcdmrg_check_device", "qcdmrg_davidson",
     "qcdmrg_truncate", "qcdmrg_move_center", "qcdmrg_sweep", "qcdmrg_heff_diag",
     "qcdmrg_apply_heff_noalloc", "qcdmrg_graph_create", "qcdmrg_graph_launch",
-    "qcdmrg_graph_info", "qcdmrg_graph_destroy",
+    "qcdmrg_graph_info", "qcdmrg_graph_destroy", "qcdmrg_rdm1", "qcdmrg_set_psi",
 ]
 
 _lib = None
@@ -114,6 +114,8 @@ def load(path=None):
     lib.qcdmrg_graph_launch.argtypes = [P, P]
     lib.qcdmrg_graph_info.argtypes = [P, dp, ctypes.POINTER(ctypes.c_int)]
     lib.qcdmrg_graph_destroy.argtypes = [P]
+    lib.qcdmrg_rdm1.argtypes = [P, dp]
+    lib.qcdmrg_set_psi.argtypes = [P, dp, ctypes.c_size_t]
     lib.qcdmrg_sweep.argtypes = [P, ctypes.POINTER(SweepOpts), ctypes.POINTER(SweepReport)]
     for f in EXPORTS:
         getattr(lib, f).restype = getattr(lib, f).restype or ctypes.c_int
@@ -188,6 +190,10 @@ class Context:
         self._check(self.lib.qcdmrg_get_psi(self.h, _dptr(out), n))
         return out
 
+    def set_psi(self, psi):
+        psi = np.ascontiguousarray(psi, dtype=np.float64)
+        self._check(self.lib.qcdmrg_set_psi(self.h, _dptr(psi), psi.size))
+
     def build_env(self):
         self._check(self.lib.qcdmrg_build_env(self.h))
 
@@ -227,6 +233,11 @@ class Context:
         self._check(self.lib.qcdmrg_apply_heff_noalloc(self.h, ctypes.c_void_p(psi_ptr),
                                                        ctypes.c_void_p(sigma_ptr),
                                                        ctypes.c_void_p(stream)))
+
+    def rdm1(self, L):
+        g = np.empty((L, L))
+        self._check(self.lib.qcdmrg_rdm1(self.h, _dptr(g)))
+        return g
 
     def heff_diag(self):
         out = np.empty(self.psi_size())

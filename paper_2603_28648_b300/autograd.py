@@ -1,0 +1,47 @@
+"""Energy of the two-site wavefunction as a torch.autograd.Function.
+
+E(psi, h, V) = <psi| H_eff(h, V) |psi> / <psi|psi> at the context's centre.
+Backward: dE/dpsi = 2 (H_eff psi - E psi) / <psi|psi> (one H_eff psi in the
+library), dE/dh_pq = gamma_pq, the spin-summed one-particle density matrix
+of the state (qcdmrg_rdm1), the quantity CASSCF orbital gradients are built
+from. The 2-RDM (dE/dV) is not provided by this version of the library.
+"""
+
+import torch
+
+from . import FP64
+
+
+class DMRGEnergy(torch.autograd.Function):
+    """apply(psi, h, V, context, precision=FP64).
+
+    psi: CUDA float64 tensor of the context's psi size; h, V: the integrals the
+    context's environment was built from (tensors; only their gradient slots
+    are used). Gradients w.r.t. h need the context's centre at (L-2, L-1) and
+    its stored wavefunction equal to psi (context.set_psi).
+    """
+
+    @staticmethod
+    def forward(fctx, psi, h, V, context, precision=FP64):
+        sig = torch.empty_like(psi)
+        stream = torch.cuda.current_stream()
+        context.apply_heff_dev(psi.data_ptr(), sig.data_ptr(), stream.cuda_stream, precision)
+        nn = torch.dot(psi, psi)
+        E = torch.dot(psi, sig) / nn
+        fctx.save_for_backward(psi, sig, E, nn)
+        fctx.context = context
+        fctx.L = h.shape[0]
+        return E
+
+    @staticmethod
+    def backward(fctx, gE):
+        psi, sig, E, nn = fctx.saved_tensors
+        dpsi = dh = None
+        if fctx.needs_input_grad[0]:
+            dpsi = 2.0 * (sig - E * psi) / nn * gE
+        if fctx.needs_input_grad[1]:
+            g = fctx.context.rdm1(fctx.L)
+            dh = torch.as_tensor(g, dtype=torch.float64) * gE.detach().cpu()
+        if fctx.needs_input_grad[2]:
+            raise NotImplementedError("dE/dV (the 2-RDM) is not provided by this version")
+        return dpsi, dh, None, None, None

@@ -336,6 +336,18 @@ int qcdmrg_get_psi(const qcdmrg_ctx* cctx, double* out, size_t n) {
   });
 }
 
+int qcdmrg_set_psi(qcdmrg_ctx* ctx, const double* psi, size_t n) {
+  return guard(ctx, [&]() {
+    Engine& E = ctx->eng;
+    if (E.center < 0) throw Fail{QCDMRG_ESTATE, "no MPS"};
+    ProdBasis a = make_prod(E.bonds[E.center], true), b = make_prod(E.bonds[E.center + 2], false);
+    int64_t sz = make_psi_layout(a, b, QN{E.N, E.two_s}).size;
+    if (!psi || (int64_t)n != sz) throw Fail{QCDMRG_EINVAL, "input size differs from the wavefunction"};
+    ctx->be.ex->upload(E.dpsi, psi, sz);
+    return QCDMRG_OK;
+  });
+}
+
 int qcdmrg_build_env(qcdmrg_ctx* ctx) {
   return guard(ctx, [&]() {
     Engine& E = ctx->eng;
@@ -421,6 +433,17 @@ static DavOpts dav_opts(const qcdmrg_dav_opts* o) {
   if (o->tau1 > 0) d.tau1 = o->tau1;
   if (o->tau2 > 0) d.tau2 = o->tau2;
   return d;
+}
+
+int qcdmrg_rdm1(qcdmrg_ctx* ctx, double* gamma) {
+  return guard(ctx, [&]() {
+    Engine& E = ctx->eng;
+    if (!E.have_env) throw Fail{QCDMRG_ESTATE, "build_env first"};
+    if (!gamma) throw Fail{QCDMRG_EINVAL, "null argument"};
+    std::vector<double> g = E.rdm1();
+    std::copy(g.begin(), g.end(), gamma);
+    return QCDMRG_OK;
+  });
 }
 
 int qcdmrg_heff_diag(qcdmrg_ctx* ctx, double* out, size_t n) {

@@ -342,8 +342,33 @@ std::vector<CenterTerm> center_terms(const Enlarged& Lp, const Enlarged& Rp, con
 
 HeffPlan plan_heff(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay,
                    const Integrals& I, int64_t tmp_budget) {
+  return plan_terms(Lp, Rp, lay, center_terms(Lp, Rp, I), tmp_budget);
+}
+
+OpView site_op_view(const Enlarged& E, const Mat4& o, bool par) {
+  OpView v;
+  const Basis& B = *E.pb.blk;
+  for (int x = 0; x < B.nsec(); ++x)
+    for (int i = 0; i < NSITE; ++i)
+      for (int j = 0; j < NSITE; ++j) {
+        double val = o(i, j);
+        if (val == 0.0) continue;
+        BRef r;
+        r.r = E.pb.find(x, i);
+        r.c = E.pb.find(x, j);
+        r.ptr = 0;
+        r.rows = r.cols = r.ld = B.dim[x];
+        double sg = 1.0;
+        if (par) sg = E.left ? ((B.q[x].n & 1) ? -1.0 : 1.0) : ((SITE_QN[j].n & 1) ? -1.0 : 1.0);
+        r.sc = val * sg;
+        v.blocks.push_back(r);
+      }
+  return v;
+}
+
+HeffPlan plan_terms(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay,
+                    const std::vector<CenterTerm>& terms, int64_t tmp_budget) {
   HeffPlan plan;
-  std::vector<CenterTerm> terms = center_terms(Lp, Rp, I);
   plan.nterms = (int)terms.size();
 
   const ProdBasis& LB = Lp.pb;

@@ -253,5 +253,11 @@ struct HeffPlan {
 };
 HeffPlan plan_heff(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay,
                    const Integrals& I, int64_t tmp_budget);
+// Same for an arbitrary list of operator-product terms (expectation values).
+HeffPlan plan_terms(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay,
+                    const std::vector<CenterTerm>& terms, int64_t tmp_budget);
+// identity of the block part (x) a single-site operator, on an enlarged basis;
+// par applies the fermion parity of the block (left) or site (right) ket part
+OpView site_op_view(const Enlarged& E, const Mat4& o, bool par);
 
 }  // namespace qd

@@ -237,6 +237,7 @@ DavResult Engine::davidson(const DavOpts& o) {
     std::vector<double> Hs((size_t)mmax * mmax, 0.0);
     Hs[0] = ex->dot(V[0], W[0], n);
     double theta = Hs[0];
+    std::vector<double> phase_res;   // residuals of the current precision phase
     for (int it = 0; it < o.max_iter; ++it) {
       R.iters = it + 1;
       std::vector<double> hs((size_t)m * m), ev, vec;
@@ -262,14 +263,20 @@ DavResult Engine::davidson(const DavOpts& o) {
       R.resid = rn;
       R.energy = theta;
       int nprec = prec;
+      phase_res.push_back(rn);
       if (o.policy) {
-        if (prec == 2 && rn < o.tau1) nprec = 3;
-        if (prec == 3 && rn < o.tau2) nprec = 0;
+        // a reduced-precision phase ends at its threshold, or when its
+        // residual stops falling (the rounding of its H psi sets a floor)
+        const size_t np = phase_res.size();
+        const bool stalled = np > 6 && rn > 0.5 * phase_res[np - 7];
+        if (prec == 2 && (rn < o.tau1 || stalled)) nprec = 3;
+        if (prec == 3 && (rn < o.tau2 || stalled)) nprec = 0;
         if (prec != 0 && rn < o.tol) nprec = 0;
       }
       if (nprec != prec) {  // restart from the Ritz vector with the new precision
         if (prec == 3) R.energy_mixed = theta;
         prec = nprec;
+        phase_res.clear();
         double xn = std::sqrt(ex->dot(x, x, n));
         ex->copy(V[0], x, n);
         ex->scale(V[0], 1.0 / xn, n);
@@ -605,6 +612,66 @@ double Engine::truncate_move(int D, int dir, double drop_below) {
   env_flops += fl;
   prepare_center();
   return disc;
+}
+
+double Engine::expect(const std::vector<CenterTerm>& terms) {
+  HeffPlan pl = plan_terms(Lp, Rp, lay, terms, tmp_budget);
+  ex->tmp(std::max<int64_t>(1, pl.tmp_elems));
+  uint64_t tau = ex->alloc(std::max<int64_t>(1, lay.size));
+  for (size_t k = 0; k < pl.stage1.size(); ++k) {
+    ex->run(pl.stage1[k], dpsi, tau);
+    ex->run(pl.stage2[k], dpsi, tau);
+  }
+  double v = ex->dot(dpsi, tau, lay.size);
+  ex->release(tau);
+  return v;
+}
+
+std::vector<double> Engine::rdm1() {
+  // At the centre (L-2, L-1) the left enlarged block L' holds the normal
+  // operators a+_k a_l of every spin-orbital of sites 0..L-2, and the right
+  // enlarged block is the last site alone, so every E_pq is a product of
+  // stored operators:
+  //   p, q < L-1 : B_{p s, q s} (x) 1
+  //   p < L-1 = q: (a+_p)_L' (a_q)_R'
+  //   q < L-1 = p: a+_p a_q = -(a_q)_L' (a+_p)_R'
+  //   p = q = L-1: 1 (x) a+_p a_p on the last site
+  if (center != L - 2) throw StateError("the one-particle density matrix needs the centre at (L-2, L-1)");
+  const double nrm = ex->dot(dpsi, dpsi, lay.size);
+  auto get = [](const Enlarged& E, Key k) -> const OpView* {
+    auto it = E.ops.find(k);
+    if (it == E.ops.end() || it->second.empty()) return nullptr;
+    return &it->second;
+  };
+  const OpView* IL = get(Lp, Key(F_I));
+  const OpView* IR = get(Rp, Key(F_I));
+  const int last = L - 1;
+  std::vector<double> g((size_t)L * L, 0.0);
+  std::vector<OpView> site_ops;
+  site_ops.reserve(2);
+  for (int s = 0; s < 2; ++s) site_ops.push_back(site_op_view(Rp, cre(s) * ann(s), false));
+  for (int p = 0; p < L; ++p)
+    for (int q = 0; q < L; ++q) {
+      std::vector<CenterTerm> t;
+      for (int s = 0; s < 2; ++s) {
+        const int kp = 2 * p + s, kq = 2 * q + s;
+        if (p < last && q < last) {
+          if (auto B = get(Lp, Key(F_B, kp, kq))) t.push_back({B, false, IR, false, 1.0});
+        } else if (p < last) {
+          auto C = get(Lp, Key(F_C, kp));
+          auto Cr = get(Rp, Key(F_C, kq));
+          if (C && Cr) t.push_back({C, false, Cr, true, 1.0});
+        } else if (q < last) {
+          auto C = get(Lp, Key(F_C, kq));
+          auto Cr = get(Rp, Key(F_C, kp));
+          if (C && Cr) t.push_back({C, true, Cr, false, -1.0});
+        } else {
+          t.push_back({IL, false, &site_ops[s], false, 1.0});
+        }
+      }
+      if (!t.empty()) g[(size_t)p * L + q] = expect(t) / nrm;
+    }
+  return g;
 }
 
 }  // namespace qd

@@ -73,6 +73,11 @@ struct Engine {
   // truncate the centre to D states (drop weights <= drop_below), renormalize
   // and move the centre by dir (+1 right, -1 left); returns the discarded weight
   double truncate_move(int D, int dir, double drop_below);
+  // <psi| sum_t c_t O_L (x) O_R |psi> for a list of centre terms
+  double expect(const std::vector<CenterTerm>& terms);
+  // spin-summed one-particle density matrix gamma_pq = <E_pq> of the
+  // normalised state; needs the centre at (L-2, L-1)
+  std::vector<double> rdm1();
 };
 
 }  // namespace qd
