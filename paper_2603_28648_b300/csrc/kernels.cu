@@ -40,7 +40,8 @@ __device__ __forceinline__ const double* res(unsigned long long v, int buf, cons
                   : reinterpret_cast<const double*>(B.b[buf] + v * 8ull);
 }
 
-__global__ void __launch_bounds__(256) seg_gemm_f64(const GProb* __restrict__ probs,
+template <int T>
+__global__ void __launch_bounds__(T * T / 16) seg_gemm_f64_t(const GProb* __restrict__ probs,
                                                     const GSeg* __restrict__ segs,
                                                     const GTile* __restrict__ tiles, int ntiles,
                                                     Bases bases) {
@@ -48,10 +49,12 @@ __global__ void __launch_bounds__(256) seg_gemm_f64(const GProb* __restrict__ pr
   if (t >= ntiles) return;
   const GTile tl = tiles[t];
   const GProb p = probs[tl.prob];
-  __shared__ double As[TK][TM + 1];
-  __shared__ double Bs[TK][TN + 1];
+  constexpr int NT = T * T / 16;   // threads; each computes 4 x 4 outputs
+  constexpr int TD = T / 4;        // threads per tile dimension
+  __shared__ double As[TK][T + 1];
+  __shared__ double Bs[TK][T + 1];
   const int tid = threadIdx.x;
-  const int tx = tid & 15, ty = tid >> 4;
+  const int tx = tid % TD, ty = tid / TD;
   double acc[4][4];
 #pragma unroll
   for (int r = 0; r < 4; ++r)
@@ -68,16 +71,16 @@ __global__ void __launch_bounds__(256) seg_gemm_f64(const GProb* __restrict__ pr
         for (int r = 0; r < 4; ++r)
 #pragma unroll
           for (int c = 0; c < 4; ++c)
-            if (m0 + ty + 16 * r == n0 + tx + 16 * c) acc[r][c] += g.sc;
+            if (m0 + ty + TD * r == n0 + tx + TD * c) acc[r][c] += g.sc;
       } else {
         const double* Bp = res(g.b, g.bbuf, bases);
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-          const int row = m0 + ty + 16 * r;
+          const int row = m0 + ty + TD * r;
           if (row >= p.m) continue;
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
-            const int col = n0 + tx + 16 * c;
+            const int col = n0 + tx + TD * c;
             if (col >= p.n) continue;
             const double v = g.tb ? Bp[(size_t)col * g.ldb + row] : Bp[(size_t)row * g.ldb + col];
             acc[r][c] += g.sc * v;
@@ -90,11 +93,11 @@ __global__ void __launch_bounds__(256) seg_gemm_f64(const GProb* __restrict__ pr
     const double* Bp = res(g.b, g.bbuf, bases);
     for (int k0 = 0; k0 < g.k; k0 += TK) {
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int idx = tid + 256 * e;
+      for (int e = 0; e < T * TK / NT; ++e) {
+        const int idx = tid + NT * e;
         int row, kk;
-        if (g.ta) { kk = idx >> 6; row = idx & 63; }
-        else { row = idx >> 4; kk = idx & 15; }
+        if (g.ta) { kk = idx / T; row = idx % T; }
+        else { row = idx / TK; kk = idx % TK; }
         const int gr = m0 + row, gk = k0 + kk;
         double v = 0.0;
         if (gr < p.m && gk < g.k)
@@ -102,11 +105,11 @@ __global__ void __launch_bounds__(256) seg_gemm_f64(const GProb* __restrict__ pr
         As[kk][row] = v * g.sc;
       }
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int idx = tid + 256 * e;
+      for (int e = 0; e < T * TK / NT; ++e) {
+        const int idx = tid + NT * e;
         int col, kk;
-        if (g.tb) { col = idx >> 4; kk = idx & 15; }
-        else { kk = idx >> 6; col = idx & 63; }
+        if (g.tb) { col = idx / TK; kk = idx % TK; }
+        else { kk = idx / T; col = idx % T; }
         const int gc = n0 + col, gk = k0 + kk;
         double v = 0.0;
         if (gc < p.n && gk < g.k)
@@ -118,9 +121,9 @@ __global__ void __launch_bounds__(256) seg_gemm_f64(const GProb* __restrict__ pr
       for (int kk = 0; kk < TK; ++kk) {
         double a[4], b[4];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) a[r] = As[kk][ty + 16 * r];
+        for (int r = 0; r < 4; ++r) a[r] = As[kk][ty + TD * r];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + 16 * c];
+        for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + TD * c];
 #pragma unroll
         for (int r = 0; r < 4; ++r)
 #pragma unroll
@@ -132,11 +135,11 @@ __global__ void __launch_bounds__(256) seg_gemm_f64(const GProb* __restrict__ pr
   double* Cp = const_cast<double*>(res(p.c, p.cbuf, bases));
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
-    const int row = m0 + ty + 16 * r;
+    const int row = m0 + ty + TD * r;
     if (row >= p.m) continue;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      const int col = n0 + tx + 16 * c;
+      const int col = n0 + tx + TD * c;
       if (col >= p.n) continue;
       double* dst = Cp + (size_t)row * p.ldc + col;
       if (tl.split) atomicAdd(dst, acc[r][c]);
@@ -206,7 +209,9 @@ __global__ void precond_kernel(double* t, const double* r, const double* d, doub
 struct DevLaunch {
   GProb* p = nullptr;
   GSeg* s = nullptr;
-  GTile* t = nullptr;    // 64x64 tiles (FP64 kernel)
+  GTile* t = nullptr;    // 64x64 tiles (FP64 kernel), problems larger than 32 x 32
+  GTile* ts = nullptr;   // 32x32 tiles (FP64 kernel), problems that fit in 32 x 32
+  int ntiles_s = 0;
   GTile* t2 = nullptr;   // 128x128 tiles (tcgen05 kernel)
   int ntiles = 0, ntiles2 = 0;
   double flops = 0;
@@ -214,10 +219,13 @@ struct DevLaunch {
 
 // Work items: every tile of every problem, with the problem's segments cut into
 // ranges whose summed K stays below kmax (split-K over segments).
-static void make_tiles(const Launch& l, int tile, int kmax, std::vector<GTile>& T) {
+// sel: 0 all problems, 1 problems that fit in 32 x 32, 2 the others
+static void make_tiles(const Launch& l, int tile, int kmax, std::vector<GTile>& T, int sel = 0) {
   T.clear();
   for (size_t i = 0; i < l.probs.size(); ++i) {
     const Prob& q = l.probs[i];
+    const bool small = q.m <= 32 && q.n <= 32;
+    if ((sel == 1 && !small) || (sel == 2 && small)) continue;
     std::vector<std::pair<int, int>> ranges;
     int s0 = 0, ksum = 0;
     for (int s = 0; s < q.nseg; ++s) {
@@ -238,18 +246,15 @@ static void make_tiles(const Launch& l, int tile, int kmax, std::vector<GTile>& 
   }
 }
 
-static void build_host(const Launch& l, std::vector<GProb>& P, std::vector<GSeg>& S,
-                       std::vector<GTile>& T, int tile = TM) {
+static void build_host(const Launch& l, std::vector<GProb>& P, std::vector<GSeg>& S) {
   P.resize(l.probs.size());
   S.resize(l.segs.size());
-  T.clear();
   for (size_t i = 0; i < l.probs.size(); ++i) {
     const Prob& q = l.probs[i];
     GProb& g = P[i];
     g.c = q.c; g.m = q.m; g.n = q.n; g.ldc = q.ldc; g.beta = q.beta;
     g.seg0 = q.seg0; g.nseg = q.nseg; g.cbuf = q.cbuf; g.pad = 0;
   }
-  make_tiles(l, tile, KMAX_F64, T);
   for (size_t i = 0; i < l.segs.size(); ++i) {
     const Seg& q = l.segs[i];
     GSeg& g = S[i];
@@ -257,6 +262,13 @@ static void build_host(const Launch& l, std::vector<GProb>& P, std::vector<GSeg>
     g.abuf = (unsigned char)q.abuf; g.bbuf = (unsigned char)q.bbuf;
     g.ta = (unsigned char)q.ta; g.tb = (unsigned char)q.tb; g.sc = q.sc;
   }
+}
+
+// FP64 kernel launches over both size classes
+static void launch_f64(const GProb* P, const GSeg* S, const GTile* T64, int n64, const GTile* T32, int n32,
+                       const Bases& B, cudaStream_t st) {
+  if (n64) seg_gemm_f64_t<64><<<n64, 256, 0, st>>>(P, S, T64, n64, B);
+  if (n32) seg_gemm_f64_t<32><<<n32, 64, 0, st>>>(P, S, T32, n32, B);
 }
 
 class CudaExec : public Executor, public PreparedRunner {
@@ -311,16 +323,23 @@ class CudaExec : public Executor, public PreparedRunner {
     if (l.empty()) return;
     std::vector<GProb> P;
     std::vector<GSeg> S;
-    std::vector<GTile> T;
-    build_host(l, P, S, T);
+    std::vector<GTile> T, Ts;
+    build_host(l, P, S);
+    make_tiles(l, TM, KMAX_F64, T, 2);
+    make_tiles(l, 32, KMAX_F64, Ts, 1);
+    const size_t nt = T.size();
+    T.insert(T.end(), Ts.begin(), Ts.end());
     CK(cudaStreamSynchronize(st_));
     grow(&sp_, &spcap_, P.size() * sizeof(GProb));
-    grow(&ss_, &sscap_, S.size() * sizeof(GSeg));
-    grow(&stt_, &stcap_, T.size() * sizeof(GTile));
+    grow(&ss_, &sscap_, std::max<size_t>(1, S.size()) * sizeof(GSeg));
+    grow(&stt_, &stcap_, std::max<size_t>(1, T.size()) * sizeof(GTile));
     CK(cudaMemcpyAsync(sp_, P.data(), P.size() * sizeof(GProb), cudaMemcpyHostToDevice, st_));
-    CK(cudaMemcpyAsync(ss_, S.data(), S.size() * sizeof(GSeg), cudaMemcpyHostToDevice, st_));
-    CK(cudaMemcpyAsync(stt_, T.data(), T.size() * sizeof(GTile), cudaMemcpyHostToDevice, st_));
-    launch((GProb*)sp_, (GSeg*)ss_, (GTile*)stt_, (int)T.size(), psi, sig, st_);
+    if (!S.empty()) CK(cudaMemcpyAsync(ss_, S.data(), S.size() * sizeof(GSeg), cudaMemcpyHostToDevice, st_));
+    if (!T.empty()) CK(cudaMemcpyAsync(stt_, T.data(), T.size() * sizeof(GTile), cudaMemcpyHostToDevice, st_));
+    Bases B;
+    B.b[0] = 0; B.b[1] = psi; B.b[2] = sig; B.b[3] = tmp_;
+    launch_f64((GProb*)sp_, (GSeg*)ss_, (GTile*)stt_, (int)nt, (GTile*)stt_ + nt, (int)Ts.size(), B, st_);
+    CK(cudaGetLastError());
     CK(cudaStreamSynchronize(st_));
   }
   void upload(uint64_t dst, const double* h, int64_t n) override {
@@ -436,22 +455,25 @@ class CudaExec : public Executor, public PreparedRunner {
     DevLaunch d;
     std::vector<GProb> P;
     std::vector<GSeg> S;
-    std::vector<GTile> T;
-    build_host(l, P, S, T);
+    std::vector<GTile> T, Ts, T2;
+    build_host(l, P, S);
+    make_tiles(l, TM, KMAX_F64, T, 2);
+    make_tiles(l, 32, KMAX_F64, Ts, 1);
+    make_tiles(l, TC_TILE, KMAX_TC, T2, 0);
     d.ntiles = (int)T.size();
-    d.flops = l.flops;
-    std::vector<GTile> T2;
-    make_tiles(l, TC_TILE, KMAX_TC, T2);
+    d.ntiles_s = (int)Ts.size();
     d.ntiles2 = (int)T2.size();
-    if (d.ntiles) {
-      CK(cudaMalloc(&d.p, P.size() * sizeof(GProb)));
-      CK(cudaMalloc(&d.s, std::max<size_t>(1, S.size()) * sizeof(GSeg)));
-      CK(cudaMalloc(&d.t, T.size() * sizeof(GTile)));
-      CK(cudaMalloc(&d.t2, T2.size() * sizeof(GTile)));
-      CK(cudaMemcpy(d.p, P.data(), P.size() * sizeof(GProb), cudaMemcpyHostToDevice));
-      if (!S.empty()) CK(cudaMemcpy(d.s, S.data(), S.size() * sizeof(GSeg), cudaMemcpyHostToDevice));
-      CK(cudaMemcpy(d.t, T.data(), T.size() * sizeof(GTile), cudaMemcpyHostToDevice));
-      CK(cudaMemcpy(d.t2, T2.data(), T2.size() * sizeof(GTile), cudaMemcpyHostToDevice));
+    d.flops = l.flops;
+    auto up = [](void** dst, const void* src, size_t bytes) {
+      CK(cudaMalloc(dst, std::max<size_t>(bytes, 16)));
+      if (bytes) CK(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
+    };
+    if (!P.empty()) {
+      up((void**)&d.p, P.data(), P.size() * sizeof(GProb));
+      up((void**)&d.s, S.data(), S.size() * sizeof(GSeg));
+      up((void**)&d.t, T.data(), T.size() * sizeof(GTile));
+      up((void**)&d.ts, Ts.data(), Ts.size() * sizeof(GTile));
+      up((void**)&d.t2, T2.data(), T2.size() * sizeof(GTile));
     }
     prepared_.push_back(d);
     return (int)prepared_.size() - 1;
@@ -463,9 +485,12 @@ class CudaExec : public Executor, public PreparedRunner {
   }
   void run_prepared(int h, uint64_t psi, uint64_t sig, void* stream, int precision) override {
     const DevLaunch& d = prepared_.at(h);
-    if (!d.ntiles) return;
+    if (!d.ntiles && !d.ntiles_s) return;
     if (precision == 0) {
-      launch(d.p, d.s, d.t, d.ntiles, psi, sig, (cudaStream_t)stream);
+      Bases B;
+      B.b[0] = 0; B.b[1] = psi; B.b[2] = sig; B.b[3] = tmp_;
+      launch_f64(d.p, d.s, d.t, d.ntiles, d.ts, d.ntiles_s, B, (cudaStream_t)stream);
+      CK(cudaGetLastError());
       return;
     }
     if (!err_) {
@@ -500,15 +525,6 @@ class CudaExec : public Executor, public PreparedRunner {
       CK(cudaMalloc(&info_, sizeof(int)));
     }
   }
-  void launch(GProb* P, GSeg* S, GTile* T, int nt, uint64_t psi, uint64_t sig, cudaStream_t s) {
-    Bases B;
-    B.b[0] = 0;
-    B.b[1] = psi;
-    B.b[2] = sig;
-    B.b[3] = tmp_;
-    seg_gemm_f64<<<nt, 256, 0, s>>>(P, S, T, nt, B);
-    CK(cudaGetLastError());
-  }
   void grow(void** p, size_t* cap, size_t need) {
     if (need <= *cap) return;
     if (*p) CK(cudaFree(*p));
@@ -520,7 +536,8 @@ class CudaExec : public Executor, public PreparedRunner {
     if (d.s) cudaFree(d.s);
     if (d.t) cudaFree(d.t);
     if (d.t2) cudaFree(d.t2);
-    d.p = nullptr; d.s = nullptr; d.t = nullptr; d.t2 = nullptr;
+    if (d.ts) cudaFree(d.ts);
+    d.p = nullptr; d.s = nullptr; d.t = nullptr; d.t2 = nullptr; d.ts = nullptr;
   }
   int dev_;
   cudaStream_t st_ = nullptr;
@@ -543,13 +560,13 @@ class CudaExec : public Executor, public PreparedRunner {
 cudaError_t launch_f64_prepared(const void* handle, uint64_t psi, uint64_t sig, uint64_t scratch,
                                 cudaStream_t st) {
   const DevLaunch* d = static_cast<const DevLaunch*>(handle);
-  if (!d || !d->ntiles) return cudaSuccess;
+  if (!d || (!d->ntiles && !d->ntiles_s)) return cudaSuccess;
   Bases B;
   B.b[0] = 0;
   B.b[1] = psi;
   B.b[2] = sig;
   B.b[3] = scratch;
-  seg_gemm_f64<<<d->ntiles, 256, 0, st>>>(d->p, d->s, d->t, d->ntiles, B);
+  launch_f64(d->p, d->s, d->t, d->ntiles, d->ts, d->ntiles_s, B, st);
   return cudaGetLastError();
 }
 

@@ -116,18 +116,46 @@ __device__ __forceinline__ uint32_t tile_off(int r, int k) {
   return (uint32_t)((((r >> 3) * KB + kb) << 7) + ((r & 7) << 4) + ((k * ES) & 15));
 }
 
+// FP64 -> FP32 with round-to-nearest-even using integer operations only (the
+// FP64 pipe of this GPU is narrow and a hardware conversion per operand
+// element would be the bottleneck of the producer). Values below the FP32
+// normal range flush to zero; the operands here are far from both limits.
+__device__ __forceinline__ float f64_to_f32(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned int sign = (unsigned int)(b >> 63) << 31;
+  const int e = (int)((b >> 52) & 0x7FF) - 1023 + 127;
+  if (e <= 0) return __uint_as_float(sign);
+  if (e >= 255) return __uint_as_float(sign | 0x7F800000u);
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  unsigned int m23 = (unsigned int)(m >> 29);
+  const unsigned long long rem = m & 0x1FFFFFFFull;
+  const unsigned long long half = 0x10000000ull;
+  unsigned int bits = sign | ((unsigned int)e << 23);
+  if (rem > half || (rem == half && (m23 & 1u))) ++m23;  // carry into the exponent is exact
+  return __uint_as_float(bits + m23);
+}
+
+// FP32 -> FP64, exact, integer operations only (zero and normal numbers)
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned int b = __float_as_uint(f);
+  const unsigned long long sign = (unsigned long long)(b >> 31) << 63;
+  const unsigned int e = (b >> 23) & 0xFF;
+  if (e == 0) return __longlong_as_double((long long)sign);
+  const unsigned long long m = (unsigned long long)(b & 0x7FFFFF) << 29;
+  return __longlong_as_double((long long)(sign | ((unsigned long long)(e - 127 + 1023) << 52) | m));
+}
+
 template <int MODE>
-__device__ __forceinline__ void put(unsigned char* base, uint32_t off, size_t split_stride, double v) {
+__device__ __forceinline__ void put(unsigned char* base, uint32_t off, size_t split_stride, float x) {
   if constexpr (MODE == TC_TF32) {
     // round to nearest TF32 (the tensor core would otherwise drop the low
     // mantissa bits, a biased truncation)
     uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"((float)v));
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
     *reinterpret_cast<uint32_t*>(base + off) = r;
   } else if constexpr (MODE == TC_BF16) {
-    *reinterpret_cast<__nv_bfloat16*>(base + off) = __float2bfloat16_rn((float)v);
+    *reinterpret_cast<__nv_bfloat16*>(base + off) = __float2bfloat16_rn(x);
   } else {
-    float x = (float)v;
     __nv_bfloat16 h0 = __float2bfloat16_rn(x);
     float r1 = x - __bfloat162float(h0);
     __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
@@ -172,6 +200,13 @@ __global__ void __launch_bounds__(128, 1)
     mbar_init(&mbar[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  // padding rows of both stages stay zero for the whole work item: zero once
+  {
+    uint4* z = reinterpret_cast<uint4*>(smem);
+    const uint4 zero = make_uint4(0, 0, 0, 0);
+    for (uint32_t i = tid; i < 2 * STAGE / 16; i += 128) z[i] = zero;
+  }
+  const int mv = min(TCM, p.m - m0), nv = min(TCN, p.n - n0);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -194,29 +229,40 @@ __global__ void __launch_bounds__(128, 1)
       }
       unsigned char* sA = smem + st * STAGE;
       unsigned char* sB = sA + NS * TILE;
-      // A tile: rows m0.., k0..
-#pragma unroll 4
-      for (int e = 0; e < KC; ++e) {
-        const int idx = tid + 128 * e;
-        int r, k;
-        if (g.ta) { k = idx >> 7; r = idx & 127; }
-        else { r = idx / KC; k = idx % KC; }
-        const int gr = m0 + r, gk = k0 + k;
-        double v = 0.0;
-        if (gr < p.m && gk < g.k) v = sc * (g.ta ? Ap[(size_t)gk * g.lda + gr] : Ap[(size_t)gr * g.lda + gk]);
-        put<MODE>(sA, tile_off<ES, KC>(r, k), TILE, v);
+      // A tile: valid rows m0 .. m0+mv-1 only (padding rows are zero), K
+      // positions past the segment's end written as zero
+      const int kv = min(KC, g.k - k0);
+      const float scf = (float)sc;
+      if (g.ta) {
+        for (int idx = tid; idx < KC * mv; idx += 128) {
+          const int k = idx / mv, r = idx - k * mv;
+          float v = 0.f;
+          if (k < kv) v = scf * f64_to_f32(Ap[(size_t)(k0 + k) * g.lda + m0 + r]);
+          put<MODE>(sA, tile_off<ES, KC>(r, k), TILE, v);
+        }
+      } else {
+        for (int idx = tid; idx < KC * mv; idx += 128) {
+          const int r = idx / KC, k = idx - r * KC;
+          float v = 0.f;
+          if (k < kv) v = scf * f64_to_f32(Ap[(size_t)(m0 + r) * g.lda + k0 + k]);
+          put<MODE>(sA, tile_off<ES, KC>(r, k), TILE, v);
+        }
       }
-      // B tile stored N x K (K-major): element (k, n) of op(B)
-#pragma unroll 4
-      for (int e = 0; e < KC; ++e) {
-        const int idx = tid + 128 * e;
-        int n, k;
-        if (g.tb) { n = idx / KC; k = idx % KC; }
-        else { k = idx >> 7; n = idx & 127; }
-        const int gn = n0 + n, gk = k0 + k;
-        double v = 0.0;
-        if (gn < p.n && gk < g.k) v = g.tb ? Bp[(size_t)gn * g.ldb + gk] : Bp[(size_t)gk * g.ldb + gn];
-        put<MODE>(sB, tile_off<ES, KC>(n, k), TILE, v);
+      // B tile stored N x K (K-major): element (k, n) of op(B), valid columns only
+      if (g.tb) {
+        for (int idx = tid; idx < KC * nv; idx += 128) {
+          const int n = idx / KC, k = idx - n * KC;
+          float v = 0.f;
+          if (k < kv) v = f64_to_f32(Bp[(size_t)(n0 + n) * g.ldb + k0 + k]);
+          put<MODE>(sB, tile_off<ES, KC>(n, k), TILE, v);
+        }
+      } else {
+        for (int idx = tid; idx < KC * nv; idx += 128) {
+          const int k = idx / nv, n = idx - k * nv;
+          float v = 0.f;
+          if (k < kv) v = f64_to_f32(Bp[(size_t)(k0 + k) * g.ldb + n0 + n]);
+          put<MODE>(sB, tile_off<ES, KC>(n, k), TILE, v);
+        }
       }
       fence_async_smem();
       __syncthreads();
@@ -297,7 +343,7 @@ __global__ void __launch_bounds__(128, 1)
     if (row < p.m && n0 + c0 < p.n) {
       double out[16];
 #pragma unroll
-      for (int j = 0; j < 16; ++j) out[j] = (double)acc[j];
+      for (int j = 0; j < 16; ++j) out[j] = f32_to_f64(acc[j]);
       for (int s = tl.s0; s < tl.s1; ++s) {  // identity segments
         const TcSeg g = segs[p.seg0 + s];
         if (!(g.a == 0ull && g.abuf == 0)) continue;
