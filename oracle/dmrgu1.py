@@ -376,8 +376,23 @@ def svd_sectors(x, Ln, Ls, Rn, Rs, N, two_sz):
     return blocks
 
 
-def select_kept(blocks, D, drop_below=0.0):
-    """Keep the D largest weights sv^2; ties by label ascending, then index.
+TIE_REL = 1e-8
+# Weights at or below this are rounding noise of the density-matrix eigenvalues
+# (absolute error ~1e-16 of the unit trace) and are always discarded, so that
+# zero-weight states never enter a basis.
+WEIGHT_FLOOR = 1e-14
+
+
+def select_kept(blocks, D, drop_below=WEIGHT_FLOOR):
+    """Keep the D largest weights sv^2 above drop_below; ties by label
+    ascending, then index.
+
+    Weights that are equal up to rounding (within TIE_REL relative of the D-th
+    weight) are kept or discarded together: when such a group straddles the
+    cut it is discarded as a whole, so fewer than D states are kept. Exact
+    ties arise from the spin-flip symmetry of Sz = 0 states (sectors Sz and
+    -Sz carry equal weights), and a cut through them would otherwise be
+    decided by rounding.
 
     Returns ({qL: [k...]}, discarded weight).
     """
@@ -386,8 +401,14 @@ def select_kept(blocks, D, drop_below=0.0):
         for k, x in enumerate(sv):
             cand.append((-x * x, qn, k))
     cand.sort()
-    keep = [c for c in cand[:D] if -c[0] > drop_below]
-    disc = sum(-c[0] for c in cand if c not in keep)
+    keep = cand[:D]
+    if len(cand) > D:
+        lam_cut = -cand[D - 1][0]
+        if -cand[D][0] >= lam_cut - TIE_REL * lam_cut:
+            keep = [c for c in keep if -c[0] > lam_cut + TIE_REL * lam_cut]
+    keep = [c for c in keep if -c[0] > drop_below]
+    kept_set = set(keep)
+    disc = sum(-c[0] for c in cand if c not in kept_set)
     kept = {}
     for _, qn, k in keep:
         kept.setdefault(qn, []).append(k)
@@ -475,7 +496,7 @@ class DMRGU1:
             Rn = (SITE_N[:, None] + rb[l + 2].n[None, :]).reshape(-1)
             Rs = (SITE_S[:, None] + rb[l + 2].s[None, :]).reshape(-1)
             blocks = svd_sectors(to_mat(psi), Ln, Ls, Rn, Rs, self.N, self.two_sz)
-            kept, _ = select_kept(blocks, 10 ** 9, drop_below=1e-28)
+            kept, _ = select_kept(blocks, 10 ** 9)
             bnew, Vt, US = right_factor(blocks, kept, len(Ln), len(Rn), self.N, self.two_sz)
             R[l + 1] = Vt.reshape(bnew.dim, 4, DY)
             rb[l + 1] = bnew
