@@ -59,6 +59,11 @@ typedef struct {
   int symmetry;         /* QCDMRG_U1 */
   int device;           /* CUDA device ordinal */
   double tmp_budget_gb; /* scratch for stage-1 intermediates (0: 2 GB) */
+  double hbm_budget_gb; /* device memory for renormalized blocks before the ones away from the
+                           centre move to pinned host memory (0: unlimited); the block the next
+                           move needs is copied back on a second stream during the current
+                           step (the host-device transfer of the paper's Unexploited power
+                           section) */
 } qcdmrg_config;
 
 /*
@@ -96,9 +101,16 @@ typedef struct {
   double env_flops;      /* flops of the last environment build */
   double env_seconds;    /* wall time of the last environment build */
   int64_t psi_size;      /* elements of the two-site wavefunction */
-  int64_t device_bytes;  /* bytes allocated on the device by the context */
+  int64_t device_bytes;  /* peak bytes allocated on the device by the context */
+  int64_t live_bytes;    /* bytes allocated on the device by the context now */
   int nterms;            /* operator-product terms of H_eff */
   int nlaunch;           /* kernel launches per H_eff psi */
+  int64_t h2d_bytes;     /* out-of-core store: bytes copied back to the device */
+  int64_t d2h_bytes;     /* bytes moved to pinned host memory */
+  int evictions, restores;
+  double copy_wait_seconds; /* host time the compute stream waited for copies */
+  double heff_bytes;     /* algorithmic minimum traffic of one H_eff psi: every operator block
+                            it references read once, psi read once, sigma written once (FP64) */
 } qcdmrg_stats_t;
 
 /* Davidson options (zero fields take the defaults in brackets). */
@@ -253,14 +265,16 @@ int qcdmrg_davidson(qcdmrg_ctx* ctx, const qcdmrg_dav_opts* opts, double* energy
  * Truncation step of the sweep: density matrix of the two-site wavefunction
  * per quantum-number sector (rho = Psi Psi^T for dir = +1, Psi^T Psi for
  * dir = -1), FP64 eigendecomposition, the D states of largest weight kept
- * across sectors (ties: weight, then label, then in-sector order), new site
+ * across sectors (ties: weight, then label, then in-sector order; weights
+ * equal to 1e-8 relative that straddle the cut are dropped together, and
+ * weights <= 1e-14, rounding noise of the eigenvalues, are always dropped), new site
  * tensor, renormalization of every operator of the grown block, and the
  * transformed wavefunction as the guess at the moved centre. trunc_err gets
  * the discarded weight. Errors: ESTATE, EINVAL.
  */
 int qcdmrg_truncate(qcdmrg_ctx* ctx, int D, int dir, double* trunc_err);
 
-/* Move the centre without truncation (only weights below 1e-28 dropped). */
+/* Move the centre without truncation (only weights <= 1e-14, rounding noise, dropped). */
 int qcdmrg_move_center(qcdmrg_ctx* ctx, int target);
 
 /*

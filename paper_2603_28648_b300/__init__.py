@@ -31,7 +31,7 @@ class QcdmrgError(RuntimeError):
 
 class Config(ctypes.Structure):
     _fields_ = [("symmetry", ctypes.c_int), ("device", ctypes.c_int),
-                ("tmp_budget_gb", ctypes.c_double)]
+                ("tmp_budget_gb", ctypes.c_double), ("hbm_budget_gb", ctypes.c_double)]
 
 
 class MpsDesc(ctypes.Structure):
@@ -60,7 +60,11 @@ class Stats(ctypes.Structure):
     _fields_ = [("heff_flops", ctypes.c_double), ("heff_seconds", ctypes.c_double),
                 ("env_flops", ctypes.c_double), ("env_seconds", ctypes.c_double),
                 ("psi_size", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
-                ("nterms", ctypes.c_int), ("nlaunch", ctypes.c_int)]
+                ("live_bytes", ctypes.c_int64),
+                ("nterms", ctypes.c_int), ("nlaunch", ctypes.c_int),
+                ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64),
+                ("evictions", ctypes.c_int), ("restores", ctypes.c_int),
+                ("copy_wait_seconds", ctypes.c_double), ("heff_bytes", ctypes.c_double)]
 
 
 EXPORTS = [
@@ -132,10 +136,10 @@ def _dptr(a):
 class Context:
     """One qcdmrg context (one device, one problem)."""
 
-    def __init__(self, device=0, symmetry=U1, tmp_budget_gb=0.0, lib=None):
+    def __init__(self, device=0, symmetry=U1, tmp_budget_gb=0.0, hbm_budget_gb=0.0, lib=None):
         self.lib = lib or load()
         self.h = ctypes.c_void_p()
-        cfg = Config(symmetry, device, tmp_budget_gb)
+        cfg = Config(symmetry, device, tmp_budget_gb, hbm_budget_gb)
         rc = self.lib.qcdmrg_create(ctypes.byref(self.h), ctypes.byref(cfg))
         if rc != QCDMRG_OK:
             raise QcdmrgError(rc, "context creation failed (no usable CUDA device?)")

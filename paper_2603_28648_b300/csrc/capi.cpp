@@ -91,6 +91,8 @@ int qcdmrg_create(qcdmrg_ctx** out, const qcdmrg_config* cfg) {
     c->eng.ex = c->be.ex;
     c->eng.pr = c->be.pr;
     c->eng.tmp_budget = (int64_t)(gb * 1e9 / 8);
+    if (cfg->hbm_budget_gb < 0) throw std::invalid_argument("hbm_budget_gb");
+    c->eng.hbm_budget = (int64_t)(cfg->hbm_budget_gb * 1e9);
   } catch (const std::invalid_argument&) {
     delete c;
     return QCDMRG_EINVAL;
@@ -356,6 +358,7 @@ int qcdmrg_build_env(qcdmrg_ctx* ctx) {
     ctx->st.env_flops = E.env_flops;
     ctx->st.env_seconds = E.env_seconds;
     ctx->st.heff_flops = E.plan.flops;
+    ctx->st.heff_bytes = E.plan.bytes;
     ctx->st.psi_size = E.lay.size;
     ctx->st.nterms = E.plan.nterms;
     ctx->st.nlaunch = 2 * (int)E.plan.stage1.size();
@@ -520,6 +523,7 @@ int qcdmrg_sweep(qcdmrg_ctx* ctx, const qcdmrg_sweep_opts* o, qcdmrg_sweep_repor
     R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (rep) *rep = R;
     ctx->st.heff_flops = E.plan.flops;
+    ctx->st.heff_bytes = E.plan.bytes;
     ctx->st.psi_size = E.lay.size;
     return conv ? QCDMRG_OK : QCDMRG_ENOTCONV;
   });
@@ -590,6 +594,12 @@ int qcdmrg_stats(const qcdmrg_ctx* ctx, qcdmrg_stats_t* out) {
   if (!ctx || !out) return QCDMRG_EINVAL;
   *out = ctx->st;
   out->device_bytes = ctx->be.pr ? ctx->be.pr->bytes_allocated() : 0;
+  out->live_bytes = ctx->be.ex ? ctx->be.ex->live_bytes() : 0;
+  out->h2d_bytes = ctx->eng.h2d_bytes;
+  out->d2h_bytes = ctx->eng.d2h_bytes;
+  out->evictions = ctx->eng.evictions;
+  out->restores = ctx->eng.restores;
+  out->copy_wait_seconds = ctx->be.ex ? ctx->be.ex->copies_wait_seconds() : 0.0;
   return QCDMRG_OK;
 }
 

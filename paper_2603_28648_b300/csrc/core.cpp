@@ -5,6 +5,7 @@
 #include <cmath>
 #include <stdexcept>
 #include <tuple>
+#include <unordered_map>
 
 namespace qd {
 
@@ -174,7 +175,10 @@ void renormalize(const Enlarged& E, const Basis& nb, const std::vector<int>& nb_
     }
   }
   uint64_t store = total ? ex.alloc(total) : 0;
-  if (store) out.owned.push_back(store);
+  if (store) {
+    out.owned.push_back(store);
+    out.owned_n.push_back(total);
+  }
   auto sub_ptr = [&](int s) -> uint64_t {
     const Sub& S = pb.subs[s];
     int nq = nb_of_prod[S.prod];
@@ -374,6 +378,12 @@ HeffPlan plan_terms(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay
   const ProdBasis& LB = Lp.pb;
   Launch s1, s2;
   std::map<int, std::vector<Seg>> out;  // psi block -> segments
+  std::unordered_map<uint64_t, int64_t> blocks_read;  // storage address -> elements
+  auto note = [&](const BRef& b) {
+    if (b.ident()) return;
+    int64_t& e = blocks_read[b.ptr];
+    e = std::max<int64_t>(e, (int64_t)b.rows * b.cols);
+  };
   int64_t tused = 0;
   auto flush = [&]() {
     if (out.empty() && s1.empty()) return;
@@ -414,6 +424,7 @@ HeffPlan plan_terms(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay
         int cL = kv.first;
         auto it = lay.by_sub.find({cL, bR.c});
         if (it == lay.by_sub.end()) continue;
+        note(bR);
         const auto& pin = lay.blks[it->second];
         uint64_t Tb;
         int Tbuf, ldT = bR.rows;
@@ -439,6 +450,7 @@ HeffPlan plan_terms(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay
         for (const BRef* bL : kv.second) {
           auto ot = lay.by_sub.find({bL->r, bR.r});
           if (ot == lay.by_sub.end()) continue;
+          note(*bL);
           Seg g;
           if (bL->ident()) { g.a = 0; g.abuf = B_ABS; g.lda = 0; g.ta = 0; }
           else { g.a = bL->ptr; g.abuf = B_ABS; g.lda = bL->ld; g.ta = bL->tr ? 1 : 0; }
@@ -452,6 +464,9 @@ HeffPlan plan_terms(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay
     }
   }
   flush();
+  double e = 2.0 * (double)lay.size;
+  for (auto& kv : blocks_read) e += (double)kv.second;
+  plan.bytes = 8.0 * e;
   return plan;
 }
 

@@ -147,6 +147,14 @@ struct Executor {
   // w (host) -> ascending eigenvalues
   virtual void eigh(uint64_t A, int n, double* w) = 0;
   virtual void copy(uint64_t dst, uint64_t src, int64_t n) = 0;
+  // out-of-core store: pinned host buffers and copies on a second stream
+  virtual uint64_t host_alloc(int64_t nelem) = 0;
+  virtual void host_free(uint64_t h) = 0;
+  virtual void d2h(uint64_t h, uint64_t d, int64_t n) = 0;        // synchronous
+  virtual void h2d_async(uint64_t d, uint64_t h, int64_t n) = 0;  // on the copy stream
+  virtual void copies_join() = 0;      // compute stream waits for the copy stream
+  virtual double copies_wait_seconds() = 0;  // host time spent waiting in copies_join so far
+  virtual int64_t live_bytes() const = 0;
 };
 
 // Integrals; spin-orbital form t_kl, w_ijkl with k = 2p + sigma.
@@ -201,7 +209,10 @@ struct EnvBlock {
   int cut = 0;
   Basis basis;
   std::map<Key, OpView> ops;
-  std::vector<uint64_t> owned;
+  std::vector<uint64_t> owned;     // device storage (released when evicted)
+  std::vector<int64_t> owned_n;    // elements of each owned allocation
+  std::vector<uint64_t> host;      // pinned host copies while evicted
+  bool evicted = false;
 };
 
 // Sector rule of the initial MPS (left labels, bonds 0..L).
@@ -248,6 +259,9 @@ Launch plan_diag(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay, c
 struct HeffPlan {
   std::vector<Launch> stage1, stage2;
   double flops = 0;
+  // algorithmic minimum traffic of one product: every operator block the terms
+  // reference read once, psi read once, sigma written once (FP64 elements)
+  double bytes = 0;
   int64_t tmp_elems = 0;
   int nterms = 0;
 };

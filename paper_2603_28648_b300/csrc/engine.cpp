@@ -13,6 +13,11 @@ namespace qd {
 
 namespace {
 
+constexpr double TIE_REL = 1e-8;  // relative width of a group of equal weights at the cut
+// density-matrix eigenvalues at or below this are rounding noise (absolute
+// error ~1e-16 of the unit trace) and are always discarded
+constexpr double WEIGHT_FLOOR = 1e-14;
+
 EnvBlock vacuum(bool left, int cut) {
   EnvBlock b;
   b.left = left;
@@ -77,9 +82,96 @@ Prob copy_prob(uint64_t dst, int m, int n, int ldc, int seg0) {
 }  // namespace
 
 void Engine::free_block(EnvBlock& b) {
-  for (auto p : b.owned) ex->release(p);
+  if (!b.evicted)
+    for (auto p : b.owned) ex->release(p);
+  for (auto h : b.host) ex->host_free(h);
   b.owned.clear();
+  b.owned_n.clear();
+  b.host.clear();
+  b.evicted = false;
   b.ops.clear();
+}
+
+void Engine::evict(EnvBlock& b) {
+  if (b.evicted || b.owned.empty()) return;
+  ex->copies_join();   // no copy of this block may be in flight
+  for (auto h : b.host) ex->host_free(h);
+  b.host.clear();
+  for (size_t k = 0; k < b.owned.size(); ++k) {
+    uint64_t h = ex->host_alloc(b.owned_n[k]);
+    ex->d2h(h, b.owned[k], b.owned_n[k]);
+    d2h_bytes += 8 * b.owned_n[k];
+    ex->release(b.owned[k]);
+    b.host.push_back(h);
+  }
+  b.evicted = true;
+  ++evictions;
+}
+
+void Engine::restore_async(EnvBlock& b) {
+  if (!b.evicted) return;
+  for (size_t k = 0; k < b.owned.size(); ++k) {
+    const uint64_t old = b.owned[k], n = (uint64_t)b.owned_n[k];
+    const uint64_t nw = ex->alloc(b.owned_n[k]);
+    ex->h2d_async(nw, b.host[k], b.owned_n[k]);
+    h2d_bytes += 8 * b.owned_n[k];
+    for (auto& kv : b.ops)
+      for (BRef& r : kv.second.blocks)
+        if (r.ptr >= old && r.ptr < old + 8 * n) r.ptr = nw + (r.ptr - old);
+    b.owned[k] = nw;
+  }
+  b.evicted = false;
+  ++restores;
+  // host copies are freed once the copies are joined (ensure_resident)
+}
+
+void Engine::ensure_resident(EnvBlock& b) {
+  if (b.evicted) restore_async(b);
+  ex->copies_join();
+  for (auto h : b.host) ex->host_free(h);
+  b.host.clear();
+}
+
+void Engine::enforce_budget_build(int cut, bool left) {
+  if (hbm_budget <= 0) return;
+  // during the environment build only the newest block of each side is needed
+  while (ex->live_bytes() > hbm_budget) {
+    EnvBlock* far = nullptr;
+    if (left) {
+      for (auto& kv : lenv)
+        if (kv.first < cut && !kv.second.evicted && !kv.second.owned.empty()) { far = &kv.second; break; }
+    } else {
+      for (auto it = renv.rbegin(); it != renv.rend(); ++it)
+        if (it->first > cut && !it->second.evicted && !it->second.owned.empty()) { far = &it->second; break; }
+    }
+    if (!far) break;
+    evict(*far);
+  }
+}
+
+void Engine::enforce_budget() {
+  if (hbm_budget <= 0) return;
+  // candidates: blocks not needed by the centre or the next move, farthest first
+  while (ex->live_bytes() > hbm_budget) {
+    EnvBlock* far = nullptr;
+    int dist = -1;
+    for (auto& kv : lenv) {
+      int d = center - kv.first;
+      if (kv.first < center - 1 && !kv.second.evicted && !kv.second.owned.empty() && d > dist) {
+        dist = d;
+        far = &kv.second;
+      }
+    }
+    for (auto& kv : renv) {
+      int d = kv.first - (center + 2);
+      if (kv.first > center + 3 && !kv.second.evicted && !kv.second.owned.empty() && d > dist) {
+        dist = d;
+        far = &kv.second;
+      }
+    }
+    if (!far) break;
+    evict(*far);
+  }
 }
 
 void Engine::free_enlarged(Enlarged& e) {
@@ -144,6 +236,7 @@ void Engine::build_env() {
     renormalize(E, bonds[p + 1], site_nb[p], site[p], site_off[p], *ex, nb, tmp_budget, &fl);
     free_enlarged(E);
     lenv[p + 1] = nb;
+    enforce_budget_build(p + 1, true);
   }
   renv[L] = vacuum(false, L);
   for (int p = L - 1; p >= center + 2; --p) {
@@ -154,6 +247,7 @@ void Engine::build_env() {
     renormalize(E, bonds[p], site_nb[p], site[p], site_off[p], *ex, nb, tmp_budget, &fl);
     free_enlarged(E);
     renv[p] = nb;
+    enforce_budget_build(p, false);
   }
   env_flops = fl;
   prepare_center();
@@ -166,6 +260,8 @@ void Engine::prepare_center() {
   if (pr) pr->drop_prepared();
   prepared.clear();
   double fl = 0;
+  ensure_resident(lenv.at(center));
+  ensure_resident(renv.at(center + 2));
   enlarge(lenv.at(center), I, *ex, Lp, &fl);
   enlarge(renv.at(center + 2), I, *ex, Rp, &fl);
   lay = make_psi_layout(Lp.pb, Rp.pb, QN{N, two_s});
@@ -366,6 +462,7 @@ DavResult Engine::davidson(const DavOpts& o) {
 }
 
 double Engine::truncate_move(int D, int dir, double drop_below) {
+  drop_below = std::max(drop_below, WEIGHT_FLOOR);
   const QN target{N, two_s};
   const ProdBasis& LB = Lp.pb;
   const ProdBasis& RB = Rp.pb;
@@ -429,12 +526,20 @@ double Engine::truncate_move(int D, int dir, double drop_below) {
     if (std::get<1>(a) != std::get<1>(b)) return std::get<1>(a) < std::get<1>(b);
     return std::get<2>(a) < std::get<2>(b);
   });
+  // weights equal up to rounding (within TIE_REL of the D-th) are kept or
+  // dropped together: a group straddling the cut is dropped (spin-flip pairs
+  // of Sz = 0 states carry equal weights; rounding must not pick one)
+  double above = -1.0;
+  if ((int)cand.size() > D && D > 0) {
+    const double lc = -std::get<0>(cand[D - 1]), ln = -std::get<0>(cand[D]);
+    if (ln >= lc - TIE_REL * lc) above = lc + TIE_REL * lc;
+  }
   std::vector<int> keep(secs.size(), 0);
   double disc = 0;
   int nk = 0;
   for (auto& c : cand) {
     double l = -std::get<0>(c);
-    if (nk < D && l > drop_below) {
+    if (nk < D && l > drop_below && l > above) {
       keep[std::get<3>(c)]++;
       ++nk;
     } else {
@@ -611,6 +716,15 @@ double Engine::truncate_move(int D, int dir, double drop_below) {
   ex->release(Cb);
   env_flops += fl;
   prepare_center();
+  enforce_budget();
+  // prefetch the block the next move in this direction will need
+  if (dir > 0) {
+    auto it = renv.find(center + 3);
+    if (it != renv.end() && it->second.evicted) restore_async(it->second);
+  } else {
+    auto it = lenv.find(center - 1);
+    if (it != lenv.end() && it->second.evicted) restore_async(it->second);
+  }
   return disc;
 }
 

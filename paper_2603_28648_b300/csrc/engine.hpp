@@ -56,6 +56,16 @@ struct Engine {
   uint64_t dpsi = 0, ddiag = 0, dones = 0;
   int64_t ones_n = 0;
   double env_flops = 0, env_seconds = 0;
+  // out-of-core operator store: renormalized blocks away from the centre move
+  // to pinned host memory when the device footprint exceeds hbm_budget bytes
+  int64_t hbm_budget = 0;          // 0: unlimited
+  int64_t h2d_bytes = 0, d2h_bytes = 0;
+  int evictions = 0, restores = 0;
+  void evict(EnvBlock& b);
+  void restore_async(EnvBlock& b);  // H2D on the copy stream, references remapped
+  void ensure_resident(EnvBlock& b);
+  void enforce_budget();
+  void enforce_budget_build(int cut, bool left);
 
   ~Engine() { clear(); }
   void clear();

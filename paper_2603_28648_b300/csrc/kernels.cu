@@ -12,7 +12,9 @@
 
 #include <cstdio>
 #include <algorithm>
+#include <chrono>
 #include <cstring>
+#include <map>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -31,7 +33,7 @@ namespace qd {
                                " at " + __FILE__ + ":" + std::to_string(__LINE__)); \
   } while (0)
 
-constexpr int TM = 64, TN = 64, TK = 16;
+constexpr int TM = 64, TK = 16;   // FP64 kernel: square TM x TM output tiles
 constexpr int KMAX_F64 = 1024;   // summed K per work item before splitting (FP64 kernel)
 constexpr int KMAX_TC = 4096;    // same for the tensor-core kernel
 
@@ -292,6 +294,8 @@ class CudaExec : public Executor, public PreparedRunner {
     if (info_) cudaFree(info_);
     if (sol_) cusolverDnDestroy(sol_);
     if (err_) cudaFree(err_);
+    if (cp_) cudaStreamDestroy(cp_);
+    if (cpev_) cudaEventDestroy(cpev_);
     cudaStreamDestroy(st_);
   }
   uint64_t alloc(int64_t n) override {
@@ -300,14 +304,53 @@ class CudaExec : public Executor, public PreparedRunner {
     CK(cudaMalloc(&p, (size_t)n * 8));
     CK(cudaMemsetAsync(p, 0, (size_t)n * 8, st_));
     bytes_ += n * 8;
+    live_ += n * 8;
+    peak_ = std::max(peak_, live_);
+    sizes_[reinterpret_cast<uint64_t>(p)] = n * 8;
     return reinterpret_cast<uint64_t>(p);
   }
   void release(uint64_t p) override {
     if (p) {
       CK(cudaStreamSynchronize(st_));
       CK(cudaFree(reinterpret_cast<void*>(p)));
+      auto it = sizes_.find(p);
+      if (it != sizes_.end()) {
+        live_ -= it->second;
+        sizes_.erase(it);
+      }
     }
   }
+  uint64_t host_alloc(int64_t n) override {
+    void* p = nullptr;
+    CK(cudaHostAlloc(&p, (size_t)std::max<int64_t>(1, n) * 8, cudaHostAllocDefault));
+    return reinterpret_cast<uint64_t>(p);
+  }
+  void host_free(uint64_t h) override {
+    if (h) CK(cudaFreeHost(reinterpret_cast<void*>(h)));
+  }
+  void d2h(uint64_t h, uint64_t d, int64_t n) override {
+    CK(cudaStreamSynchronize(st_));
+    CK(cudaMemcpy(reinterpret_cast<void*>(h), reinterpret_cast<void*>(d), (size_t)n * 8, cudaMemcpyDeviceToHost));
+  }
+  void h2d_async(uint64_t d, uint64_t h, int64_t n) override {
+    if (!cp_) {
+      CK(cudaStreamCreateWithFlags(&cp_, cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&cpev_, cudaEventDisableTiming));
+    }
+    // the destination was allocated (and zeroed) on the compute stream
+    CK(cudaEventRecord(cpev_, st_));
+    CK(cudaStreamWaitEvent(cp_, cpev_, 0));
+    CK(cudaMemcpyAsync(reinterpret_cast<void*>(d), reinterpret_cast<void*>(h), (size_t)n * 8,
+                       cudaMemcpyHostToDevice, cp_));
+  }
+  void copies_join() override {
+    if (!cp_) return;
+    auto t0 = std::chrono::steady_clock::now();
+    CK(cudaStreamSynchronize(cp_));
+    wait_s_ += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  double copies_wait_seconds() override { return wait_s_; }
+  int64_t live_bytes() const override { return live_; }
   uint64_t tmp(int64_t n) override {
     if (n > tmpcap_) {
       CK(cudaStreamSynchronize(st_));
@@ -515,7 +558,7 @@ class CudaExec : public Executor, public PreparedRunner {
   void zero_async(uint64_t p, int64_t n, void* stream) override {
     CK(cudaMemsetAsync(reinterpret_cast<void*>(p), 0, (size_t)n * 8, (cudaStream_t)stream));
   }
-  int64_t bytes_allocated() const override { return bytes_; }
+  int64_t bytes_allocated() const override { return peak_; }
 
  private:
   void solver() {
@@ -546,7 +589,11 @@ class CudaExec : public Executor, public PreparedRunner {
   void *sp_ = nullptr, *ss_ = nullptr, *stt_ = nullptr;
   size_t spcap_ = 0, sscap_ = 0, stcap_ = 0;
   std::vector<DevLaunch> prepared_;
-  int64_t bytes_ = 0;
+  int64_t bytes_ = 0, live_ = 0, peak_ = 0;
+  std::map<uint64_t, int64_t> sizes_;
+  cudaStream_t cp_ = nullptr;
+  cudaEvent_t cpev_ = nullptr;
+  double wait_s_ = 0;
   int* err_ = nullptr;
   cusolverDnHandle_t sol_ = nullptr;
   int* info_ = nullptr;
