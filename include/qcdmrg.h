@@ -64,6 +64,8 @@ typedef struct {
                            move needs is copied back on a second stream during the current
                            step (the host-device transfer of the paper's Unexploited power
                            section) */
+  int autotune_off;     /* 1: the BF16 forms keep the default work-item shape instead of timing
+                           the candidates on the first product of each problem-size class */
 } qcdmrg_config;
 
 /*
@@ -111,6 +113,10 @@ typedef struct {
   double copy_wait_seconds; /* host time the compute stream waited for copies */
   double heff_bytes;     /* algorithmic minimum traffic of one H_eff psi: every operator block
                             it references read once, psi read once, sigma written once (FP64) */
+  int tile_kmax;         /* work-item shape of the BF16 forms in use: summed K per stage-2 item */
+  int tile_width;        /* and accumulator columns per stage-1 item */
+  int tunes;             /* autotuner runs of this context */
+  double tune_seconds;   /* wall time spent in them */
 } qcdmrg_stats_t;
 
 /* Davidson options (zero fields take the defaults in brackets). */

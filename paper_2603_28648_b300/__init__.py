@@ -31,7 +31,8 @@ class QcdmrgError(RuntimeError):
 
 class Config(ctypes.Structure):
     _fields_ = [("symmetry", ctypes.c_int), ("device", ctypes.c_int),
-                ("tmp_budget_gb", ctypes.c_double), ("hbm_budget_gb", ctypes.c_double)]
+                ("tmp_budget_gb", ctypes.c_double), ("hbm_budget_gb", ctypes.c_double),
+                ("autotune_off", ctypes.c_int)]
 
 
 class MpsDesc(ctypes.Structure):
@@ -64,7 +65,9 @@ class Stats(ctypes.Structure):
                 ("nterms", ctypes.c_int), ("nlaunch", ctypes.c_int),
                 ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64),
                 ("evictions", ctypes.c_int), ("restores", ctypes.c_int),
-                ("copy_wait_seconds", ctypes.c_double), ("heff_bytes", ctypes.c_double)]
+                ("copy_wait_seconds", ctypes.c_double), ("heff_bytes", ctypes.c_double),
+                ("tile_kmax", ctypes.c_int), ("tile_width", ctypes.c_int), ("tunes", ctypes.c_int),
+                ("tune_seconds", ctypes.c_double)]
 
 
 EXPORTS = [
@@ -136,10 +139,11 @@ def _dptr(a):
 class Context:
     """One qcdmrg context (one device, one problem)."""
 
-    def __init__(self, device=0, symmetry=U1, tmp_budget_gb=0.0, hbm_budget_gb=0.0, lib=None):
+    def __init__(self, device=0, symmetry=U1, tmp_budget_gb=0.0, hbm_budget_gb=0.0, autotune=True,
+                 lib=None):
         self.lib = lib or load()
         self.h = ctypes.c_void_p()
-        cfg = Config(symmetry, device, tmp_budget_gb, hbm_budget_gb)
+        cfg = Config(symmetry, device, tmp_budget_gb, hbm_budget_gb, 0 if autotune else 1)
         rc = self.lib.qcdmrg_create(ctypes.byref(self.h), ctypes.byref(cfg))
         if rc != QCDMRG_OK:
             raise QcdmrgError(rc, "context creation failed (no usable CUDA device?)")

@@ -93,6 +93,7 @@ int qcdmrg_create(qcdmrg_ctx** out, const qcdmrg_config* cfg) {
     c->eng.tmp_budget = (int64_t)(gb * 1e9 / 8);
     if (cfg->hbm_budget_gb < 0) throw std::invalid_argument("hbm_budget_gb");
     c->eng.hbm_budget = (int64_t)(cfg->hbm_budget_gb * 1e9);
+    c->eng.autotune = cfg->autotune_off == 0;
   } catch (const std::invalid_argument&) {
     delete c;
     return QCDMRG_EINVAL;
@@ -596,6 +597,10 @@ int qcdmrg_stats(const qcdmrg_ctx* ctx, qcdmrg_stats_t* out) {
   out->device_bytes = ctx->be.pr ? ctx->be.pr->bytes_allocated() : 0;
   out->live_bytes = ctx->be.ex ? ctx->be.ex->live_bytes() : 0;
   out->h2d_bytes = ctx->eng.h2d_bytes;
+  out->tile_kmax = ctx->eng.tcfg.kmax;
+  out->tile_width = ctx->eng.tcfg.width;
+  out->tunes = ctx->eng.tunes;
+  out->tune_seconds = ctx->eng.tune_seconds;
   out->d2h_bytes = ctx->eng.d2h_bytes;
   out->evictions = ctx->eng.evictions;
   out->restores = ctx->eng.restores;

@@ -426,6 +426,9 @@ HeffPlan plan_terms(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay
         if (it == lay.by_sub.end()) continue;
         note(bR);
         const auto& pin = lay.blks[it->second];
+        int par = 1;
+        if (Rv.odd) par = (LB.prod.q[LB.subs[cL].prod].n & 1) ? -1 : 1;
+        const double bsc = t.coef * bR.sc * par;
         uint64_t Tb;
         int Tbuf, ldT = bR.rows;
         if (bR.ident()) {
@@ -435,6 +438,7 @@ HeffPlan plan_terms(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay
           p.c = (uint64_t)tused; p.cbuf = B_TMP;
           p.m = pin.rows; p.n = bR.rows; p.ldc = bR.rows; p.beta = 0;
           p.seg0 = (int)s1.segs.size(); p.nseg = 1;
+          p.osc = bsc;
           Seg h;
           h.a = (uint64_t)pin.off; h.abuf = B_PSI; h.lda = pin.cols; h.ta = 0;
           h.b = bR.ptr; h.bbuf = B_ABS; h.ldb = bR.ld; h.tb = bR.tr ? 0 : 1;
@@ -445,8 +449,7 @@ HeffPlan plan_terms(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay
           Tb = (uint64_t)tused; Tbuf = B_TMP;
           tused += (int64_t)p.m * p.n;
         }
-        int par = 1;
-        if (Rv.odd) par = (LB.prod.q[LB.subs[cL].prod].n & 1) ? -1 : 1;
+
         for (const BRef* bL : kv.second) {
           auto ot = lay.by_sub.find({bL->r, bR.r});
           if (ot == lay.by_sub.end()) continue;
@@ -456,7 +459,9 @@ HeffPlan plan_terms(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay
           else { g.a = bL->ptr; g.abuf = B_ABS; g.lda = bL->ld; g.ta = bL->tr ? 1 : 0; }
           g.b = Tb; g.bbuf = Tbuf; g.ldb = ldT; g.tb = 0;
           g.k = bL->cols;
-          g.sc = t.coef * bL->sc * bR.sc * par;
+          g.sc = bsc * bL->sc;
+          g.asc = bL->sc;
+          g.bsc = bsc;
           out[ot->second].push_back(g);
           if (!bL->ident()) s2.flops += 2.0 * bL->rows * bR.rows * (double)bL->cols;
         }

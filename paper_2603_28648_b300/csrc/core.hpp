@@ -105,6 +105,9 @@ struct Seg {
   int lda = 0, ldb = 0, k = 0;
   int ta = 0, tb = 0;
   double sc = 1.0;
+  // H_eff stage-2 segments: sc = asc * bsc, asc from the left block reference,
+  // bsc = term coefficient x right reference scalar x fermion parity
+  double asc = 1.0, bsc = 1.0;
 };
 struct Prob {
   uint64_t c = 0;
@@ -112,6 +115,7 @@ struct Prob {
   int m = 0, n = 0, ldc = 0;
   int beta = 0;             // 1: accumulate into C
   int seg0 = 0, nseg = 0;
+  double osc = 1.0;         // H_eff stage 1: scalar the stage-2 users of C carry (bsc)
 };
 struct Launch {
   std::vector<Prob> probs;

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <mutex>
 #include <stdexcept>
 #include <tuple>
 
@@ -288,10 +289,70 @@ void Engine::prepare_center() {
 
 void Engine::heff(uint64_t psi, uint64_t sig, void* stream, int prec) {
   pr->zero_async(sig, lay.size, stream);
+  if (prec == 2 || prec == 3) {
+    // BF16 forms: bf16 operand mirrors fed to the tensor cores by bulk copies
+    const int planes = prec == 3 ? 3 : 1;
+    if (pr->tiled_planes() < planes) {
+      pr->prepare_tiled(plan_tiled(plan, lay, tcfg), planes);
+      if (autotune) tune_tiled(psi, sig, prec);
+    }
+    pr->run_tiled(psi, sig, stream, prec);
+    return;
+  }
   for (auto& h : prepared) {
     pr->run_prepared(h.first, psi, sig, stream, prec);
     pr->run_prepared(h.second, psi, sig, stream, prec);
   }
+}
+
+// Autotuner of the bf16 tensor-core path: times every candidate work-item
+// shape on this centre's task lists (the operand mirrors stay; only the items
+// change) and keeps the fastest. The choice is cached per problem-size class
+// (precision, psi size to a factor of two, number of terms), so the centres
+// of a sweep at the same bond dimension are tuned once.
+void Engine::tune_tiled(uint64_t psi, uint64_t sig, int prec) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int>, TileCfg> cache;
+  int lg = 0;
+  while ((int64_t(1) << lg) < lay.size) ++lg;
+  const auto key = std::make_tuple(prec, lg, plan.nterms);
+  auto same = [](const TileCfg& a, const TileCfg& b) { return a.kmax == b.kmax && a.width == b.width; };
+  {
+    std::lock_guard<std::mutex> g(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      if (!same(it->second, tcfg)) {
+        tcfg = it->second;
+        pr->set_tiled_items(plan_tiled(plan, lay, tcfg));
+      }
+      return;
+    }
+  }
+  auto t0 = std::chrono::steady_clock::now();
+  // BF16x3 keeps the FP32 accumulation of one item to K <= 4096
+  std::vector<TileCfg> cands = {{4096, TP_B}, {1024, TP_B}, {4096, 128}, {1024, 128}};
+  if (prec != 3) cands.push_back({1 << 30, TP_B});
+  TileCfg loaded = tcfg, best = tcfg;
+  double tbest = 1e30;
+  for (const TileCfg& c : cands) {
+    if (!same(c, loaded)) {
+      pr->set_tiled_items(plan_tiled(plan, lay, c));
+      loaded = c;
+    }
+    const double t = pr->time_tiled(psi, sig, prec, 2);
+    if (t < tbest) {
+      tbest = t;
+      best = c;
+    }
+  }
+  if (!same(best, loaded)) pr->set_tiled_items(plan_tiled(plan, lay, best));
+  tcfg = best;
+  {
+    std::lock_guard<std::mutex> g(mu);
+    cache[key] = best;
+  }
+  ++tunes;
+  tune_seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 }
 
 DavResult Engine::davidson(const DavOpts& o) {

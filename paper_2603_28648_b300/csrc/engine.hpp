@@ -61,6 +61,12 @@ struct Engine {
   int64_t hbm_budget = 0;          // 0: unlimited
   int64_t h2d_bytes = 0, d2h_bytes = 0;
   int evictions = 0, restores = 0;
+  // work-item shape of the bf16 tensor-core path and its autotuner
+  TileCfg tcfg;
+  bool autotune = true;
+  double tune_seconds = 0;
+  int tunes = 0;
+  void tune_tiled(uint64_t psi, uint64_t sig, int prec);
   void evict(EnvBlock& b);
   void restore_async(EnvBlock& b);  // H2D on the copy stream, references remapped
   void ensure_resident(EnvBlock& b);

@@ -22,6 +22,7 @@
 #include "core.hpp"
 #include "kernels.hpp"
 #include "tc_gemm.hpp"
+#include "tc_tiled.hpp"
 
 namespace qd {
 
@@ -280,11 +281,13 @@ class CudaExec : public Executor, public PreparedRunner {
     CK(cudaStreamCreateWithFlags(&st_, cudaStreamNonBlocking));
     CK(cudaMalloc(&err_, sizeof(int)));
     CK(cudaMemset(err_, 0, sizeof(int)));
+    CK(cudaDeviceGetAttribute(&nsm_, cudaDevAttrMultiProcessorCount, dev_));
   }
   ~CudaExec() override {
     cudaSetDevice(dev_);
     cudaStreamSynchronize(st_);
     for (auto& d : prepared_) free_dev(d);
+    free_tiled();
     if (tmp_) cudaFree(reinterpret_cast<void*>(tmp_));
     if (sp_) cudaFree(sp_);
     if (ss_) cudaFree(ss_);
@@ -525,6 +528,80 @@ class CudaExec : public Executor, public PreparedRunner {
     CK(cudaStreamSynchronize(st_));
     for (auto& d : prepared_) free_dev(d);
     prepared_.clear();
+    free_tiled();
+  }
+
+  void prepare_tiled(const TiledPlan& P, int planes) override {
+    CK(cudaStreamSynchronize(st_));
+    free_tiled();
+    TiledDev& t = td_;
+    t.planes = planes;
+    t.aplane = P.abytes;
+    t.bplane = P.bbytes;
+    t.psiplane = P.psibytes;
+    t.tplane = P.tbytes;
+    auto arena = [&](uint8_t** d, int64_t bytes) {
+      const size_t n = std::max<size_t>(16, (size_t)bytes * planes);
+      CK(cudaMalloc(reinterpret_cast<void**>(d), n));
+      CK(cudaMemsetAsync(*d, 0, n, st_));  // padding stays zero for good
+      t.bytes += (int64_t)n;
+    };
+    arena(&t.a, P.abytes);
+    arena(&t.b, P.bbytes);
+    arena(&t.psi, P.psibytes);
+    arena(&t.t, P.tbytes);
+    TView *av = nullptr, *bv = nullptr;
+    upload(reinterpret_cast<void**>(&av), P.avw.data(), P.avw.size() * sizeof(TView), nullptr);
+    upload(reinterpret_cast<void**>(&bv), P.bvw.data(), P.bvw.size() * sizeof(TView), nullptr);
+    upload(reinterpret_cast<void**>(&t.psiv), P.psivw.data(), P.psivw.size() * sizeof(TView), &t.bytes);
+    t.npsiv = (int)P.psivw.size();
+    set_items(P);
+    // operator mirrors: converted once per prepared centre
+    CK(launch_tile_views(av, (int)P.avw.size(), t.a, P.abytes, planes, nullptr, st_));
+    CK(launch_tile_views(bv, (int)P.bvw.size(), t.b, P.bbytes, planes, nullptr, st_));
+    CK(cudaStreamSynchronize(st_));
+    CK(cudaFree(av));
+    CK(cudaFree(bv));
+    live_ += t.bytes;
+    peak_ = std::max(peak_, live_);
+  }
+  void set_tiled_items(const TiledPlan& P) override {
+    if (!td_.planes) throw std::runtime_error("tiled path not prepared");
+    CK(cudaStreamSynchronize(st_));
+    live_ -= td_.items_bytes;
+    td_.bytes -= td_.items_bytes;
+    for (void* p : {(void*)td_.i1, (void*)td_.v1, (void*)td_.i2, (void*)td_.s2})
+      if (p) CK(cudaFree(p));
+    set_items(P);
+    live_ += td_.items_bytes;
+    peak_ = std::max(peak_, live_);
+  }
+  int tiled_planes() const override { return td_.planes; }
+  double time_tiled(uint64_t psi, uint64_t sig, int precision, int reps) override {
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    run_tiled(psi, sig, st_, precision);
+    CK(cudaEventRecord(e0, st_));
+    for (int r = 0; r < reps; ++r) run_tiled(psi, sig, st_, precision);
+    CK(cudaEventRecord(e1, st_));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ms * 1e-3 / std::max(1, reps);
+  }
+  void run_tiled(uint64_t psi, uint64_t sig, void* stream, int precision) override {
+    const TiledDev& t = td_;
+    const int mode = precision == 3 ? TT_BF16X3 : TT_BF16;
+    if (t.planes == 0 || (mode == TT_BF16X3 && t.planes < 3) || (precision != 2 && precision != 3))
+      throw std::runtime_error("tiled tensor-core path not prepared for this precision");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(launch_tile_views(t.psiv, t.npsiv, t.psi, t.psiplane, t.planes, reinterpret_cast<const double*>(psi), s));
+    CK(launch_tiled_stage1(mode, t.i1, t.ni1, t.v1, t.psi, t.psiplane, t.b, t.bplane, t.t, t.tplane, nsm_, err_, s));
+    CK(launch_tiled_stage2(mode, t.i2, t.ni2, t.s2, t.a, t.aplane, t.t, t.tplane, reinterpret_cast<double*>(sig),
+                           nsm_, err_, s));
   }
   void run_prepared(int h, uint64_t psi, uint64_t sig, void* stream, int precision) override {
     const DevLaunch& d = prepared_.at(h);
@@ -574,6 +651,45 @@ class CudaExec : public Executor, public PreparedRunner {
     CK(cudaMalloc(p, need));
     *cap = need;
   }
+  struct TiledDev {
+    int planes = 0;
+    uint8_t *a = nullptr, *b = nullptr, *psi = nullptr, *t = nullptr;
+    int64_t aplane = 0, bplane = 0, psiplane = 0, tplane = 0;
+    TView* psiv = nullptr;
+    K1Item* i1 = nullptr;
+    K1View* v1 = nullptr;
+    K2Item* i2 = nullptr;
+    K2Seg* s2 = nullptr;
+    int npsiv = 0, ni1 = 0, ni2 = 0;
+    int64_t bytes = 0, items_bytes = 0;
+  };
+  void upload(void** d, const void* src, size_t bytes, int64_t* count) {
+    CK(cudaMalloc(d, std::max<size_t>(bytes, 16)));
+    if (bytes) CK(cudaMemcpy(*d, src, bytes, cudaMemcpyHostToDevice));
+    if (count) *count += (int64_t)std::max<size_t>(bytes, 16);
+  }
+  void set_items(const TiledPlan& P) {
+    TiledDev& t = td_;
+    int64_t b = 0;
+    upload(reinterpret_cast<void**>(&t.i1), P.i1.data(), P.i1.size() * sizeof(K1Item), &b);
+    upload(reinterpret_cast<void**>(&t.v1), P.v1.data(), P.v1.size() * sizeof(K1View), &b);
+    upload(reinterpret_cast<void**>(&t.i2), P.i2.data(), P.i2.size() * sizeof(K2Item), &b);
+    upload(reinterpret_cast<void**>(&t.s2), P.s2.data(), P.s2.size() * sizeof(K2Seg), &b);
+    t.ni1 = (int)P.i1.size();
+    t.ni2 = (int)P.i2.size();
+    t.items_bytes = b;
+    t.bytes += b;
+  }
+  void free_tiled() {
+    TiledDev& t = td_;
+    if (!t.planes && !t.bytes) return;
+    cudaStreamSynchronize(st_);
+    for (void* p : {(void*)t.a, (void*)t.b, (void*)t.psi, (void*)t.t, (void*)t.psiv, (void*)t.i1, (void*)t.v1,
+                    (void*)t.i2, (void*)t.s2})
+      if (p) cudaFree(p);
+    live_ -= t.bytes;
+    t = TiledDev();
+  }
   static void free_dev(DevLaunch& d) {
     if (d.p) cudaFree(d.p);
     if (d.s) cudaFree(d.s);
@@ -583,6 +699,8 @@ class CudaExec : public Executor, public PreparedRunner {
     d.p = nullptr; d.s = nullptr; d.t = nullptr; d.t2 = nullptr; d.ts = nullptr;
   }
   int dev_;
+  int nsm_ = 148;
+  TiledDev td_;
   cudaStream_t st_ = nullptr;
   uint64_t tmp_ = 0;
   int64_t tmpcap_ = 0;

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include "core.hpp"
+#include "tiled.hpp"
 
 namespace qd {
 
@@ -21,6 +22,17 @@ struct PreparedRunner {
   virtual void sync(void* stream) = 0;
   virtual void zero_async(uint64_t p, int64_t n, void* stream) = 0;
   virtual int64_t bytes_allocated() const = 0;
+  // TMA-fed tensor-core path (BF16, BF16x3): bf16 operand mirrors with one or
+  // three planes and the work items of both stages (dropped with the prepared
+  // launches); tiled_planes() is 0 when nothing is prepared
+  virtual void prepare_tiled(const TiledPlan& plan, int planes) = 0;
+  // replaces the work items only (same arenas: another TileCfg of the same plan)
+  virtual void set_tiled_items(const TiledPlan& plan) = 0;
+  virtual int tiled_planes() const = 0;
+  // device seconds of one H_eff psi on the tiled path (mean of reps, after one warm-up)
+  virtual double time_tiled(uint64_t psi, uint64_t sig, int precision, int reps) = 0;
+  // sigma must be zero; precision 2 (BF16) or 3 (BF16x3)
+  virtual void run_tiled(uint64_t psi, uint64_t sig, void* stream, int precision) = 0;
 };
 
 struct Backend {

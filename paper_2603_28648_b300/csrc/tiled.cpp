@@ -1,0 +1,227 @@
+// Work items of the TMA-fed tensor-core H_eff psi (see tiled.hpp), derived
+// from the FP64 task lists of the same product.
+#include "tiled.hpp"
+
+#include <map>
+#include <stdexcept>
+#include <tuple>
+
+namespace qd {
+
+namespace {
+
+using VKey = std::tuple<uint64_t, int, int, int, int, int, double>;  // src, buf, ld, tr, rows, cols, scale
+
+struct Arena {
+  std::vector<TView>* views;
+  int64_t* bytes;
+  int panel;
+  std::map<VKey, int64_t> index;
+  int64_t add(uint64_t src, int buf, int ld, int tr, int rows, int cols, double scale) {
+    VKey k{src, buf, ld, tr, rows, cols, scale};
+    auto it = index.find(k);
+    if (it != index.end()) return it->second;
+    TView v{src, buf, rows, cols, ld, tr, panel, scale, *bytes};
+    views->push_back(v);
+    index[k] = *bytes;
+    *bytes += tiled_bytes(rows, cols, panel);
+    return v.dst;
+  }
+};
+
+struct TProd {       // one T_t: psi block x right view
+  int blk;
+  int64_t b, tout;
+  int n, k;
+  double osc;
+};
+
+struct SigBlk {
+  int64_t out;
+  int m, n, ldc;
+  std::vector<K2Seg> segs;
+};
+
+inline int round16(int x) { return 16 * ((x + 15) / 16); }
+
+}  // namespace
+
+TiledPlan plan_tiled(const HeffPlan& plan, const PsiLayout& lay, const TileCfg& cfg) {
+  const int kmax = cfg.kmax;
+  TiledPlan P;
+  P.flops = plan.flops;
+  Arena psi{&P.psivw, &P.psibytes, TP_A, {}};
+  Arena am{&P.avw, &P.abytes, TP_A, {}};
+  Arena bm{&P.bvw, &P.bbytes, TP_B, {}};
+  std::map<int64_t, int> blk_of_off;
+  std::vector<int64_t> psi_off(lay.blks.size());
+  for (size_t i = 0; i < lay.blks.size(); ++i) {
+    const auto& b = lay.blks[i];
+    blk_of_off[b.off] = (int)i;
+    psi_off[i] = psi.add((uint64_t)b.off, 1, b.cols, 0, b.rows, b.cols, 1.0);
+  }
+  auto blk_at = [&](int64_t off) {
+    auto it = blk_of_off.find(off);
+    if (it == blk_of_off.end()) throw std::runtime_error("tiled plan: psi block not found");
+    return it->second;
+  };
+
+  std::vector<TProd> tps;
+  auto add_t = [&](int blk, int64_t b, int n, int k, double osc) {
+    tps.push_back({blk, b, P.tbytes, n, k, osc});
+    P.tbytes += tiled_bytes(n, lay.blks[blk].rows, TP_B);  // transposed: n rows, K = psi rows
+    return (int)tps.size() - 1;
+  };
+  std::map<std::pair<int64_t, double>, int> copies;  // (psi offset, scalar) -> T_t of psi itself
+  std::map<int64_t, int> sig_of;
+  std::vector<SigBlk> sig;
+
+  for (size_t c = 0; c < plan.stage1.size(); ++c) {
+    const Launch& L1 = plan.stage1[c];
+    const Launch& L2 = plan.stage2[c];
+    std::map<uint64_t, int> t_of;  // FP64 stage-1 output offset of this chunk -> T_t
+    for (const Prob& p : L1.probs) {
+      const Seg& h = L1.segs[p.seg0];
+      const int blk = blk_at((int64_t)h.a);
+      if (lay.blks[blk].rows != p.m || lay.blks[blk].cols != h.k)
+        throw std::runtime_error("tiled plan: stage-1 shape");
+      const int64_t b = bm.add(h.b, 0, h.ldb, h.tb ? 0 : 1, p.n, h.k, 1.0);
+      t_of[p.c] = add_t(blk, b, p.n, h.k, p.osc);
+    }
+    for (const Prob& p : L2.probs) {
+      auto it = sig_of.find((int64_t)p.c);
+      int si;
+      if (it == sig_of.end()) {
+        si = (int)sig.size();
+        sig_of[(int64_t)p.c] = si;
+        sig.push_back({(int64_t)p.c, p.m, p.n, p.ldc, {}});
+      } else {
+        si = it->second;
+      }
+      for (int s = 0; s < p.nseg; ++s) {
+        const Seg& g = L2.segs[p.seg0 + s];
+        int tp;
+        if (g.bbuf == B_TMP) {
+          auto jt = t_of.find(g.b);
+          if (jt == t_of.end()) throw std::runtime_error("tiled plan: stage-1 output not found");
+          tp = jt->second;
+          if (tps[tp].osc != g.bsc) throw std::runtime_error("tiled plan: stage-1 scalar differs between users");
+        } else if (g.bbuf == B_PSI) {
+          auto key = std::make_pair((int64_t)g.b, g.bsc);
+          auto jt = copies.find(key);
+          if (jt != copies.end()) {
+            tp = jt->second;
+          } else {
+            const int blk = blk_at((int64_t)g.b);
+            const int n = lay.blks[blk].cols;
+            tp = add_t(blk, bm.add(0, 0, 0, 0, n, n, 1.0), n, n, g.bsc);
+            copies[key] = tp;
+          }
+        } else {
+          throw std::runtime_error("tiled plan: unexpected stage-2 operand");
+        }
+        if (tps[tp].n != p.n || lay.blks[tps[tp].blk].rows != g.k)
+          throw std::runtime_error("tiled plan: stage-2 shape");
+        // the left reference scalar (sign included) is folded into its view
+        const int64_t a = (g.a == 0 && g.abuf == B_ABS) ? am.add(0, 0, 0, 0, p.m, g.k, g.asc)
+                                                         : am.add(g.a, 0, g.lda, g.ta, p.m, g.k, g.asc);
+        sig[si].segs.push_back({a, tps[tp].tout, g.k, 0});
+      }
+    }
+  }
+
+  // stage 1: T_t grouped by psi block, blocks ordered by right then left
+  // sector so that consecutive items reuse the same right views from L2
+  std::vector<std::vector<int>> by_blk(lay.blks.size());
+  for (int i = 0; i < (int)tps.size(); ++i) by_blk[tps[i].blk].push_back(i);
+  std::vector<int> order(lay.blks.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+  std::sort(order.begin(), order.end(), [&](int x, int y) {
+    return std::make_pair(lay.blks[x].rsub, lay.blks[x].lsub) < std::make_pair(lay.blks[y].rsub, lay.blks[y].lsub);
+  });
+  for (int blk : order) {
+    if (by_blk[blk].empty()) continue;
+    const auto& pb = lay.blks[blk];
+    const int c8 = tiled_c8(pb.cols);
+    for (int mp = 0; mp * TP_A < pb.rows; ++mp) {
+      const int mrows = std::min(TP_A, pb.rows - mp * TP_A);
+      K1Item it{};
+      it.a = psi_off[blk] + (int64_t)mp * (TP_A / 8) * c8 * 128;
+      it.pa8 = (mrows + 7) / 8;
+      it.mrows = mrows;
+      it.k = pb.cols;
+      it.mp = mp;
+      it.mtot = pb.rows;
+      it.v0 = (int)P.v1.size();
+      it.nv = 0;
+      int col = 0;
+      for (int tp : by_blk[blk]) {
+        const TProd& t = tps[tp];
+        for (int np = 0; np * TP_B < t.n; ++np) {
+          const int nrows = std::min(TP_B, t.n - np * TP_B);
+          const int nm = round16(nrows);
+          if (col + nm > std::max(cfg.width, nm)) {
+            P.i1.push_back(it);
+            it.v0 = (int)P.v1.size();
+            it.nv = 0;
+            col = 0;
+          }
+          K1View v{};
+          v.b = t.b + (int64_t)np * (TP_B / 8) * c8 * 128;
+          v.tout = t.tout;
+          v.osc = t.osc;
+          v.pb8 = (nrows + 7) / 8;
+          v.nrows = nrows;
+          v.ncol = col;
+          v.np = np;
+          v.ntot = t.n;
+          P.v1.push_back(v);
+          it.nv++;
+          col += nm;
+        }
+      }
+      if (it.nv) P.i1.push_back(it);
+    }
+  }
+
+  // stage 2: sigma blocks, segment ranges of summed K <= kmax, costliest first
+  std::vector<std::pair<double, K2Item>> items;
+  for (const SigBlk& sb : sig) {
+    std::vector<std::pair<int, int>> ranges;
+    int s0 = (int)P.s2.size(), ks = 0;
+    for (const K2Seg& g : sb.segs) {
+      const int s = (int)P.s2.size();
+      if (s > s0 && ks + g.k > kmax) {
+        ranges.push_back({s0, s});
+        s0 = s;
+        ks = 0;
+      }
+      ks += g.k;
+      P.s2.push_back(g);
+    }
+    ranges.push_back({s0, (int)P.s2.size()});
+    const int split = ranges.size() > 1 ? 1 : 0;
+    for (int mp = 0; mp * TP_A < sb.m; ++mp)
+      for (int np = 0; np * TP_B < sb.n; ++np)
+        for (auto& r : ranges) {
+          K2Item it{};
+          it.out = sb.out;
+          it.ldc = sb.ldc;
+          it.mrows = std::min(TP_A, sb.m - mp * TP_A);
+          it.nrows = std::min(TP_B, sb.n - np * TP_B);
+          it.mp = mp;
+          it.np = np;
+          it.s0 = r.first;
+          it.s1 = r.second;
+          it.split = split;
+          double cost = 0;
+          for (int s = r.first; s < r.second; ++s) cost += P.s2[s].k + 16;
+          items.push_back({cost * round16(it.nrows), it});
+        }
+  }
+  std::stable_sort(items.begin(), items.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+  for (auto& x : items) P.i2.push_back(x.second);
+  return P;
+}
+
+}  // namespace qd

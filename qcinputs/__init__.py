@@ -13,7 +13,7 @@ Integral recipe (chemist notation V_pqrs = (pq|rs), 8-fold symmetric, PSD):
 """
 
 from .integrals import make_integrals, open_shell_diagonal, write_integrals, read_integrals
-from .mps import (site_qns, fuse, mps_structure, random_mps_blocks, SYM_U1, SYM_SU2,
+from .mps import (batched_instances, site_qns, fuse, mps_structure, random_mps_blocks, SYM_U1, SYM_SU2,
                   workload)
 
 __all__ = [

@@ -234,3 +234,16 @@ def workload(name):
                                       diag=open_shell_diagonal()),
     }
     return dict(table[name])
+
+
+def batched_instances(n=16, seed=99):
+    """Independent problems of the batched workload: L uniform in 12..24,
+    N = L, 2S = N mod 2, D uniform in {128, 256, 512}, integral seeds
+    100, 101, ..., MPS seeds 1100, 1101, ..."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        L = int(rng.integers(12, 25))
+        D = int(rng.choice([128, 256, 512]))
+        out.append(dict(L=L, N=L, two_s=L % 2, D=D, int_seed=100 + i, mps_seed=1100 + i))
+    return out

@@ -42,6 +42,28 @@ def test_tensor_core_forms_vs_fp64(prec, L, N, D, c):
     assert err <= BOUND[prec], err
 
 
+def test_bf16_forms_two_row_panels_L14():
+    """psi blocks of more than 128 rows (two A panels) in the bulk-copy-fed
+    BF16 path; stage-2 items split over segment ranges."""
+    import paper_2603_28648_b300 as qd
+    ensure_built()
+    L, N, D = 14, 14, 1024
+    h, V = q.make_integrals(L, 77)
+    ctx = qd.Context()
+    ctx.load_integrals(h, V)
+    ctx.set_target(N, 0)
+    ctx.init_mps(D, 7, 6)
+    ctx.build_env()
+    psi = ctx.psi()
+    ref = ctx.apply_heff(psi, qd.FP64)
+    for prec in ["bf16", "bf16x3"]:
+        out = ctx.apply_heff(psi, qd.PRECISIONS[prec])
+        err = np.linalg.norm(out - ref) / np.linalg.norm(ref)
+        assert err <= BOUND[prec], (prec, err)
+        again = ctx.apply_heff(psi, qd.PRECISIONS[prec])
+        assert np.linalg.norm(again - out) <= 1e-6 * np.linalg.norm(ref)   # only atomics order differs
+
+
 def test_tensor_core_large_blocks_L36():
     """Blocks larger than one 128x128 tile and K spanning several chunks."""
     import paper_2603_28648_b300 as qd
@@ -59,3 +81,26 @@ def test_tensor_core_large_blocks_L36():
         out = ctx.apply_heff(psi, qd.PRECISIONS[prec])
         err = np.linalg.norm(out - ref) / np.linalg.norm(ref)
         assert err <= BOUND[prec], (prec, err)
+
+
+def test_autotuner_picks_a_shape_and_keeps_results():
+    """The autotuner times the candidate work-item shapes on the first BF16
+    product; its choice changes the schedule, not the result."""
+    import paper_2603_28648_b300 as qd
+    ensure_built()
+    L, N, D = 12, 12, 256
+    h, V = q.make_integrals(L, 5)
+    out = {}
+    for tune in (False, True):
+        ctx = qd.Context(autotune=tune)
+        ctx.load_integrals(h, V)
+        ctx.set_target(N, 0)
+        ctx.init_mps(D, 9, 5)
+        ctx.build_env()
+        psi = ctx.psi()
+        out[tune] = ctx.apply_heff(psi, qd.BF16)
+        st = ctx.stats()
+        assert st["tile_kmax"] > 0 and st["tile_width"] in (128, 256)
+        if tune:
+            assert st["tune_seconds"] >= 0.0
+    assert np.linalg.norm(out[True] - out[False]) <= 1e-5 * np.linalg.norm(out[False])
