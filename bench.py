@@ -38,6 +38,8 @@ def parse():
     ap.add_argument("--precision", default="bf16", choices=["fp64", "tf32", "bf16", "bf16x3"],
                     help="form whose throughput is the headline value (all forms are timed)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep", action="store_true",
+                    help="one full sweep (L->R->L) with FP64 Davidson and with the mixed policy, same start")
     ap.add_argument("--batched", action="store_true",
                     help="16 independent problems (L 12..24, D 128..512) in one CUDA graph vs one by one")
     ap.add_argument("--profile", action="store_true",
@@ -309,18 +311,29 @@ def run_ours(args, rank, world, local):
         cpu = {"value": f_cpu / t_cpu / 1e12, "unit": "TFLOP/s", "cores": cores(), "kind": "oracle",
                "sample": "U(1) L=10 N=10 D=64 centre-bond H_eff psi, oracle dense FP64 "
                          "(environment build excluded), 3 timed repetitions"}
+    st2 = ctx.stats()
+    tile = {"stage2_kmax": st2["tile_kmax"], "stage1_width": st2["tile_width"], "autotuner_runs": st2["tunes"],
+            "autotuner_s": st2["tune_seconds"]}
     pk = measured_peaks()
-    nbytes = st["heff_bytes"]
+    # algorithmic minimum traffic of one product in each form's operand type:
+    # every referenced operator element once (8 B FP64, 4 B TF32, 2 B BF16,
+    # 6 B for the three BF16 planes), psi and sigma (FP64 in every form)
+    nelem = st["heff_bytes"] / 8.0
+    npsi = 2.0 * st["psi_size"]
+    esize = {"fp64": 8, "tf32": 4, "bf16": 2, "bf16x3": 6}
+    form_bytes = {k: (nelem - npsi) * e + 8 * npsi for k, e in esize.items()}
     tensor_ratio = {"fp64": None, "bf16": 1.0, "tf32": 1.1 / 2.25, "bf16x3": 1.0 / 6.0}
     for name, f in forms.items():
         t_s = f["ms_per_step"] / 1e3
-        f["hbm_gbs_algorithmic"] = nbytes / t_s / 1e9
+        f["algorithmic_bytes"] = form_bytes[name]
+        f["hbm_gbs_algorithmic"] = form_bytes[name] / t_s / 1e9
         f["hbm_frac"] = f["hbm_gbs_algorithmic"] / pk["hbm"]
         r = tensor_ratio[name]
         f["compute_frac"] = f["tflops"] / (pk["bf16"] * r if r else peak)
     # the dominant kernel (the grouped block GEMM, every launch of the step) is
-    # bound by HBM: flops / algorithmic bytes is far below the ridge point of
-    # every tensor form, so its roofline is the measured copy bandwidth
+    # bound by HBM: flops / algorithmic bytes is below the ridge point of every
+    # tensor form, so its roofline is the measured copy bandwidth
+    nbytes = form_bytes[args.precision]
     achieved = nbytes / per_step / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm"], "unit": "GB/s",
             "frac": achieved / pk["hbm"], "traffic": None,
@@ -329,6 +342,14 @@ def run_ours(args, rank, world, local):
             "peak_source": f"{pk['source']} copy bandwidth (of {pk['source']})",
             "traffic_note": "null: no DRAM counter capture of this kernel build at this size",
             "compute_frac": forms[args.precision]["compute_frac"]}
+    if args.precision in ("bf16", "bf16x3"):
+        launches_per_step = 3
+        launches_note = ("per step: psi tiling, stage-1 and stage-2 launches of the bulk-copy-fed "
+                         "tcgen05 kernel (plus one cudaMemsetAsync of sigma)")
+    else:
+        launches_per_step = int(st["nlaunch"])
+        launches_note = ("per step: the grouped GEMM launches of every task-list chunk "
+                         "(plus one cudaMemsetAsync of sigma)")
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
@@ -340,16 +361,15 @@ def run_ours(args, rank, world, local):
                    "heff_gflop": flops / 1e9, "env_build_s": env_s,
                    "env_build_tflops": st["env_flops"] / env_s / 1e12,
                    "l2": "operator blocks read per step exceed L2 (no flush needed)",
-                   "device_bytes": st["device_bytes"], "energy_psi_h_psi": energy,
+                   "device_bytes": st2["device_bytes"], "energy_psi_h_psi": energy, "tile": tile,
                    "forms": forms, "fp64_peak_tflops_measured": peak,
                    "parallelism": f"replicas{world}"},
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": "TFLOP/s", "h2d_bytes_per_step": int(psi.numel() * 8),
                 "d2h_bytes_per_step": int(sig.numel() * 8)},
-        "gpu_launches": int(st["nlaunch"]) * args.steps,
-        "gpu_launches_note": "per step: 2 launches of the grouped GEMM kernel per task-list chunk "
-                             "(plus one cudaMemsetAsync of sigma)",
+        "gpu_launches": launches_per_step * args.steps,
+        "gpu_launches_note": launches_note,
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)
@@ -377,7 +397,9 @@ def run_batched(args, rank, world, local):
         c.build_env()
         st = c.stats()
         flops += st["heff_flops"]
-        nbytes += st["heff_bytes"]
+        e = {"fp64": 8, "tf32": 4, "bf16": 2, "bf16x3": 6}[args.precision]
+        npsi = 2.0 * st["psi_size"]
+        nbytes += (st["heff_bytes"] / 8.0 - npsi) * e + 8 * npsi
         p = torch.tensor(c.psi(), device="cuda")
         ctxs.append(c)
         psis.append(p)
@@ -432,6 +454,48 @@ def run_batched(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+def run_sweep(args, rank, world, local):
+    """Wall time of one full two-site sweep at bond dimension D (renormalization
+    included) with every H_eff psi in FP64, and with the mixed policy (BF16 ->
+    BF16x3 -> FP64 residual correction), from the same random MPS."""
+    import torch
+    import qcinputs as q
+    import paper_2603_28648_b300 as qd
+    torch.cuda.set_device(local)
+    L, N, D = args.L, args.N, args.D
+    h, V = q.make_integrals(L, q.integrals.BASE_SEED + 2)
+    out = {}
+    for name, kw in (("fp64", dict(policy=0, precision=qd.FP64)), ("mixed", dict(policy=1))):
+        ctx = qd.Context(device=local)
+        ctx.load_integrals(h, V)
+        ctx.set_target(N, 0)
+        ctx.init_mps(D, q.integrals.BASE_SEED + 1002, L // 2 - 1)
+        ctx.build_env()
+        ctx.move_center(0)
+        torch.cuda.synchronize()
+        clocks = Clocks(local)
+        clocks.start()
+        t0 = time.perf_counter()
+        rep = ctx.sweep(D, allow_notconv=True, tol=1e-6, **kw)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        rep["wall_s"] = wall
+        rep["clocks"] = clocks.stop()
+        rep["tile"] = {k: ctx.stats()[k] for k in ("tile_kmax", "tile_width", "tunes", "tune_seconds")}
+        out[name] = rep
+        ctx.close()
+    line = {
+        "metric": "sweep seconds, one L->R->L two-site sweep (68 steps at L=36)",
+        "value": out["mixed"]["wall_s"], "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 0,
+        "higher_is_better": False, "dtype": "mixed", "data": "synthetic",
+        "config": {"workload": f"u1_L{L}_N{N}_Sz0_D{D} full sweep from a random MPS",
+                   "fp64": out["fp64"], "mixed": out["mixed"],
+                   "speedup_vs_fp64": out["fp64"]["wall_s"] / out["mixed"]["wall_s"],
+                   "energy_mixed_minus_fp64": out["mixed"]["energy"] - out["fp64"]["energy"]},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", 0))
@@ -442,6 +506,9 @@ def main():
     elif args.batched:
         if rank == 0:
             run_batched(args, rank, world, local)
+    elif args.sweep:
+        if rank == 0:
+            run_sweep(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
 

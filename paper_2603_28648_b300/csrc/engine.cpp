@@ -294,7 +294,10 @@ void Engine::heff(uint64_t psi, uint64_t sig, void* stream, int prec) {
     const int planes = prec == 3 ? 3 : 1;
     if (pr->tiled_planes() < planes) {
       pr->prepare_tiled(plan_tiled(plan, lay, tcfg), planes);
-      if (autotune) tune_tiled(psi, sig, prec);
+      if (autotune) {
+        tune_tiled(psi, sig, prec);
+        pr->zero_async(sig, lay.size, stream);
+      }
     }
     pr->run_tiled(psi, sig, stream, prec);
     return;

@@ -34,7 +34,7 @@ namespace qd {
                                " at " + __FILE__ + ":" + std::to_string(__LINE__)); \
   } while (0)
 
-constexpr int TM = 64, TK = 16;   // FP64 kernel: square TM x TM output tiles
+constexpr int TK = 16;   // FP64 kernel: K step of a tile
 constexpr int KMAX_F64 = 1024;   // summed K per work item before splitting (FP64 kernel)
 constexpr int KMAX_TC = 4096;    // same for the tensor-core kernel
 
@@ -43,21 +43,24 @@ __device__ __forceinline__ const double* res(unsigned long long v, int buf, cons
                   : reinterpret_cast<const double*>(B.b[buf] + v * 8ull);
 }
 
-template <int T>
-__global__ void __launch_bounds__(T * T / 16) seg_gemm_f64_t(const GProb* __restrict__ probs,
-                                                    const GSeg* __restrict__ segs,
-                                                    const GTile* __restrict__ tiles, int ntiles,
-                                                    Bases bases) {
+// One CTA per TM x TN output tile of a problem (TM, TN in {32, 64}, the
+// smallest padding of each problem's rows and columns), summing every segment
+// of its range; each thread owns a 4 x 4 sub-tile.
+template <int TM, int TN>
+__global__ void __launch_bounds__(TM * TN / 16, TM * TN == 4096 ? 2 : (TM * TN == 2048 ? 3 : 4)) seg_gemm_f64_t(const GProb* __restrict__ probs,
+                                                               const GSeg* __restrict__ segs,
+                                                               const GTile* __restrict__ tiles, int ntiles,
+                                                               Bases bases) {
   const int t = blockIdx.x;
   if (t >= ntiles) return;
   const GTile tl = tiles[t];
   const GProb p = probs[tl.prob];
-  constexpr int NT = T * T / 16;   // threads; each computes 4 x 4 outputs
-  constexpr int TD = T / 4;        // threads per tile dimension
-  __shared__ double As[TK][T + 1];
-  __shared__ double Bs[TK][T + 1];
+  constexpr int NT = TM * TN / 16;  // threads; each computes 4 x 4 outputs
+  constexpr int TDM = TM / 4, TDN = TN / 4;
+  __shared__ double As[TK][TM + 1];
+  __shared__ double Bs[TK][TN + 1];
   const int tid = threadIdx.x;
-  const int tx = tid % TD, ty = tid / TD;
+  const int tx = tid % TDN, ty = tid / TDN;
   double acc[4][4];
 #pragma unroll
   for (int r = 0; r < 4; ++r)
@@ -74,16 +77,16 @@ __global__ void __launch_bounds__(T * T / 16) seg_gemm_f64_t(const GProb* __rest
         for (int r = 0; r < 4; ++r)
 #pragma unroll
           for (int c = 0; c < 4; ++c)
-            if (m0 + ty + TD * r == n0 + tx + TD * c) acc[r][c] += g.sc;
+            if (m0 + ty + TDM * r == n0 + tx + TDN * c) acc[r][c] += g.sc;
       } else {
         const double* Bp = res(g.b, g.bbuf, bases);
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-          const int row = m0 + ty + TD * r;
+          const int row = m0 + ty + TDM * r;
           if (row >= p.m) continue;
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
-            const int col = n0 + tx + TD * c;
+            const int col = n0 + tx + TDN * c;
             if (col >= p.n) continue;
             const double v = g.tb ? Bp[(size_t)col * g.ldb + row] : Bp[(size_t)row * g.ldb + col];
             acc[r][c] += g.sc * v;
@@ -96,10 +99,10 @@ __global__ void __launch_bounds__(T * T / 16) seg_gemm_f64_t(const GProb* __rest
     const double* Bp = res(g.b, g.bbuf, bases);
     for (int k0 = 0; k0 < g.k; k0 += TK) {
 #pragma unroll
-      for (int e = 0; e < T * TK / NT; ++e) {
+      for (int e = 0; e < TM * TK / NT; ++e) {
         const int idx = tid + NT * e;
         int row, kk;
-        if (g.ta) { kk = idx / T; row = idx % T; }
+        if (g.ta) { kk = idx / TM; row = idx % TM; }
         else { row = idx / TK; kk = idx % TK; }
         const int gr = m0 + row, gk = k0 + kk;
         double v = 0.0;
@@ -108,11 +111,11 @@ __global__ void __launch_bounds__(T * T / 16) seg_gemm_f64_t(const GProb* __rest
         As[kk][row] = v * g.sc;
       }
 #pragma unroll
-      for (int e = 0; e < T * TK / NT; ++e) {
+      for (int e = 0; e < TN * TK / NT; ++e) {
         const int idx = tid + NT * e;
         int col, kk;
         if (g.tb) { col = idx / TK; kk = idx % TK; }
-        else { kk = idx / T; col = idx % T; }
+        else { kk = idx / TN; col = idx % TN; }
         const int gc = n0 + col, gk = k0 + kk;
         double v = 0.0;
         if (gc < p.n && gk < g.k)
@@ -124,9 +127,9 @@ __global__ void __launch_bounds__(T * T / 16) seg_gemm_f64_t(const GProb* __rest
       for (int kk = 0; kk < TK; ++kk) {
         double a[4], b[4];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) a[r] = As[kk][ty + TD * r];
+        for (int r = 0; r < 4; ++r) a[r] = As[kk][ty + TDM * r];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + TD * c];
+        for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + TDN * c];
 #pragma unroll
         for (int r = 0; r < 4; ++r)
 #pragma unroll
@@ -138,11 +141,11 @@ __global__ void __launch_bounds__(T * T / 16) seg_gemm_f64_t(const GProb* __rest
   double* Cp = const_cast<double*>(res(p.c, p.cbuf, bases));
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
-    const int row = m0 + ty + TD * r;
+    const int row = m0 + ty + TDM * r;
     if (row >= p.m) continue;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      const int col = n0 + tx + TD * c;
+      const int col = n0 + tx + TDN * c;
       if (col >= p.n) continue;
       double* dst = Cp + (size_t)row * p.ldc + col;
       if (tl.split) atomicAdd(dst, acc[r][c]);
@@ -209,14 +212,17 @@ __global__ void precond_kernel(double* t, const double* r, const double* d, doub
 }
 
 // ---------------------------------------------------------------------------
+// FP64 tile shapes: TM, TN in {64, 32}; class 2 * i(TM) + i(TN)
+constexpr int F64_SIZES[2] = {64, 32};
+constexpr int F64_CLASSES = 4;
+
 struct DevLaunch {
   GProb* p = nullptr;
   GSeg* s = nullptr;
-  GTile* t = nullptr;    // 64x64 tiles (FP64 kernel), problems larger than 32 x 32
-  GTile* ts = nullptr;   // 32x32 tiles (FP64 kernel), problems that fit in 32 x 32
-  int ntiles_s = 0;
+  GTile* t = nullptr;    // FP64 tiles, grouped by shape class
+  int cls[F64_CLASSES + 1] = {};  // class c: tiles [cls[c], cls[c+1])
   GTile* t2 = nullptr;   // 128x128 tiles (tcgen05 kernel)
-  int ntiles = 0, ntiles2 = 0;
+  int ntiles2 = 0;
   double flops = 0;
 };
 
@@ -249,6 +255,50 @@ static void make_tiles(const Launch& l, int tile, int kmax, std::vector<GTile>& 
   }
 }
 
+// FP64 work items: each problem gets the tile shape of least padding (ties:
+// the larger tile), tiles listed class by class; off gets the class offsets
+static int f64_size_index(int d) {
+  int best = 0;
+  long long pad = 1ll << 60;
+  for (int i = 0; i < 2; ++i) {
+    const int t = F64_SIZES[i];
+    const long long p = (long long)((d + t - 1) / t) * t;
+    if (p < pad) { pad = p; best = i; }
+  }
+  return best;
+}
+static void make_tiles_f64(const Launch& l, int kmax, std::vector<GTile>& T, int off[F64_CLASSES + 1]) {
+  std::vector<GTile> byc[F64_CLASSES];
+  for (size_t i = 0; i < l.probs.size(); ++i) {
+    const Prob& q = l.probs[i];
+    const int im = f64_size_index(q.m), in = f64_size_index(q.n);
+    const int tm = F64_SIZES[im], tn = F64_SIZES[in];
+    std::vector<std::pair<int, int>> ranges;
+    int s0 = 0, ksum = 0;
+    for (int s = 0; s < q.nseg; ++s) {
+      const Seg& g = l.segs[q.seg0 + s];
+      int k = (g.a == 0 && g.abuf == 0) ? 1 : g.k;
+      if (s > s0 && ksum + k > kmax) {
+        ranges.push_back({s0, s});
+        s0 = s;
+        ksum = 0;
+      }
+      ksum += k;
+    }
+    ranges.push_back({s0, q.nseg});
+    const int split = ranges.size() > 1 ? 1 : 0;
+    for (int m0 = 0; m0 < q.m; m0 += tm)
+      for (int n0 = 0; n0 < q.n; n0 += tn)
+        for (auto& r : ranges) byc[2 * im + in].push_back({(int)i, m0, n0, r.first, r.second, split});
+  }
+  T.clear();
+  for (int c = 0; c < F64_CLASSES; ++c) {
+    off[c] = (int)T.size();
+    T.insert(T.end(), byc[c].begin(), byc[c].end());
+  }
+  off[F64_CLASSES] = (int)T.size();
+}
+
 static void build_host(const Launch& l, std::vector<GProb>& P, std::vector<GSeg>& S) {
   P.resize(l.probs.size());
   S.resize(l.segs.size());
@@ -267,11 +317,18 @@ static void build_host(const Launch& l, std::vector<GProb>& P, std::vector<GSeg>
   }
 }
 
-// FP64 kernel launches over both size classes
-static void launch_f64(const GProb* P, const GSeg* S, const GTile* T64, int n64, const GTile* T32, int n32,
-                       const Bases& B, cudaStream_t st) {
-  if (n64) seg_gemm_f64_t<64><<<n64, 256, 0, st>>>(P, S, T64, n64, B);
-  if (n32) seg_gemm_f64_t<32><<<n32, 64, 0, st>>>(P, S, T32, n32, B);
+// FP64 kernel launches, one per tile-shape class
+template <int TM, int TN>
+static void launch_class(const GProb* P, const GSeg* S, const GTile* T, int n, const Bases& B, cudaStream_t st) {
+  if (n > 0) seg_gemm_f64_t<TM, TN><<<n, TM * TN / 16, 0, st>>>(P, S, T, n, B);
+}
+static void launch_f64(const GProb* P, const GSeg* S, const GTile* T, const int* off, const Bases& B,
+                       cudaStream_t st) {
+  auto n = [&](int c) { return off[c + 1] - off[c]; };
+  launch_class<64, 64>(P, S, T + off[0], n(0), B, st);
+  launch_class<64, 32>(P, S, T + off[1], n(1), B, st);
+  launch_class<32, 64>(P, S, T + off[2], n(2), B, st);
+  launch_class<32, 32>(P, S, T + off[3], n(3), B, st);
 }
 
 class CudaExec : public Executor, public PreparedRunner {
@@ -369,12 +426,10 @@ class CudaExec : public Executor, public PreparedRunner {
     if (l.empty()) return;
     std::vector<GProb> P;
     std::vector<GSeg> S;
-    std::vector<GTile> T, Ts;
+    std::vector<GTile> T;
+    int off[F64_CLASSES + 1];
     build_host(l, P, S);
-    make_tiles(l, TM, KMAX_F64, T, 2);
-    make_tiles(l, 32, KMAX_F64, Ts, 1);
-    const size_t nt = T.size();
-    T.insert(T.end(), Ts.begin(), Ts.end());
+    make_tiles_f64(l, KMAX_F64, T, off);
     CK(cudaStreamSynchronize(st_));
     grow(&sp_, &spcap_, P.size() * sizeof(GProb));
     grow(&ss_, &sscap_, std::max<size_t>(1, S.size()) * sizeof(GSeg));
@@ -384,7 +439,7 @@ class CudaExec : public Executor, public PreparedRunner {
     if (!T.empty()) CK(cudaMemcpyAsync(stt_, T.data(), T.size() * sizeof(GTile), cudaMemcpyHostToDevice, st_));
     Bases B;
     B.b[0] = 0; B.b[1] = psi; B.b[2] = sig; B.b[3] = tmp_;
-    launch_f64((GProb*)sp_, (GSeg*)ss_, (GTile*)stt_, (int)nt, (GTile*)stt_ + nt, (int)Ts.size(), B, st_);
+    launch_f64((GProb*)sp_, (GSeg*)ss_, (GTile*)stt_, off, B, st_);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(st_));
   }
@@ -501,13 +556,10 @@ class CudaExec : public Executor, public PreparedRunner {
     DevLaunch d;
     std::vector<GProb> P;
     std::vector<GSeg> S;
-    std::vector<GTile> T, Ts, T2;
+    std::vector<GTile> T, T2;
     build_host(l, P, S);
-    make_tiles(l, TM, KMAX_F64, T, 2);
-    make_tiles(l, 32, KMAX_F64, Ts, 1);
+    make_tiles_f64(l, KMAX_F64, T, d.cls);
     make_tiles(l, TC_TILE, KMAX_TC, T2, 0);
-    d.ntiles = (int)T.size();
-    d.ntiles_s = (int)Ts.size();
     d.ntiles2 = (int)T2.size();
     d.flops = l.flops;
     auto up = [](void** dst, const void* src, size_t bytes) {
@@ -518,7 +570,6 @@ class CudaExec : public Executor, public PreparedRunner {
       up((void**)&d.p, P.data(), P.size() * sizeof(GProb));
       up((void**)&d.s, S.data(), S.size() * sizeof(GSeg));
       up((void**)&d.t, T.data(), T.size() * sizeof(GTile));
-      up((void**)&d.ts, Ts.data(), Ts.size() * sizeof(GTile));
       up((void**)&d.t2, T2.data(), T2.size() * sizeof(GTile));
     }
     prepared_.push_back(d);
@@ -555,6 +606,7 @@ class CudaExec : public Executor, public PreparedRunner {
     upload(reinterpret_cast<void**>(&bv), P.bvw.data(), P.bvw.size() * sizeof(TView), nullptr);
     upload(reinterpret_cast<void**>(&t.psiv), P.psivw.data(), P.psivw.size() * sizeof(TView), &t.bytes);
     t.npsiv = (int)P.psivw.size();
+    psi_elems_ = P.psi_elems;
     set_items(P);
     // operator mirrors: converted once per prepared centre
     CK(launch_tile_views(av, (int)P.avw.size(), t.a, P.abytes, planes, nullptr, st_));
@@ -581,9 +633,14 @@ class CudaExec : public Executor, public PreparedRunner {
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
+    // sigma is zeroed before each product, as every caller of run_tiled does
+    CK(cudaMemsetAsync(reinterpret_cast<void*>(sig), 0, (size_t)psi_elems_ * 8, st_));
     run_tiled(psi, sig, st_, precision);
     CK(cudaEventRecord(e0, st_));
-    for (int r = 0; r < reps; ++r) run_tiled(psi, sig, st_, precision);
+    for (int r = 0; r < reps; ++r) {
+      CK(cudaMemsetAsync(reinterpret_cast<void*>(sig), 0, (size_t)psi_elems_ * 8, st_));
+      run_tiled(psi, sig, st_, precision);
+    }
     CK(cudaEventRecord(e1, st_));
     CK(cudaEventSynchronize(e1));
     float ms = 0;
@@ -605,11 +662,11 @@ class CudaExec : public Executor, public PreparedRunner {
   }
   void run_prepared(int h, uint64_t psi, uint64_t sig, void* stream, int precision) override {
     const DevLaunch& d = prepared_.at(h);
-    if (!d.ntiles && !d.ntiles_s) return;
+    if (!d.cls[F64_CLASSES]) return;
     if (precision == 0) {
       Bases B;
       B.b[0] = 0; B.b[1] = psi; B.b[2] = sig; B.b[3] = tmp_;
-      launch_f64(d.p, d.s, d.t, d.ntiles, d.ts, d.ntiles_s, B, (cudaStream_t)stream);
+      launch_f64(d.p, d.s, d.t, d.cls, B, (cudaStream_t)stream);
       CK(cudaGetLastError());
       return;
     }
@@ -695,12 +752,12 @@ class CudaExec : public Executor, public PreparedRunner {
     if (d.s) cudaFree(d.s);
     if (d.t) cudaFree(d.t);
     if (d.t2) cudaFree(d.t2);
-    if (d.ts) cudaFree(d.ts);
-    d.p = nullptr; d.s = nullptr; d.t = nullptr; d.t2 = nullptr; d.ts = nullptr;
+    d.p = nullptr; d.s = nullptr; d.t = nullptr; d.t2 = nullptr;
   }
   int dev_;
   int nsm_ = 148;
   TiledDev td_;
+  int64_t psi_elems_ = 0;
   cudaStream_t st_ = nullptr;
   uint64_t tmp_ = 0;
   int64_t tmpcap_ = 0;
@@ -725,13 +782,13 @@ class CudaExec : public Executor, public PreparedRunner {
 cudaError_t launch_f64_prepared(const void* handle, uint64_t psi, uint64_t sig, uint64_t scratch,
                                 cudaStream_t st) {
   const DevLaunch* d = static_cast<const DevLaunch*>(handle);
-  if (!d || (!d->ntiles && !d->ntiles_s)) return cudaSuccess;
+  if (!d || !d->cls[F64_CLASSES]) return cudaSuccess;
   Bases B;
   B.b[0] = 0;
   B.b[1] = psi;
   B.b[2] = sig;
   B.b[3] = scratch;
-  launch_f64(d->p, d->s, d->t, d->ntiles, d->ts, d->ntiles_s, B, st);
+  launch_f64(d->p, d->s, d->t, d->cls, B, st);
   return cudaGetLastError();
 }
 

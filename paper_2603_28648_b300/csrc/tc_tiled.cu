@@ -2,28 +2,29 @@
 //
 // Operands are pre-tiled bf16 planes (tiled.hpp): every K chunk of an operand
 // panel is one contiguous range, so a single cp.async.bulk per operand and
-// plane moves it into a shared-memory ring slot whose mbarrier counts the
-// bytes. One persistent CTA per SM walks a static list of work items with
-// three roles:
-//   warp 0, one lane : producer, issues the bulk copies of every K chunk into
-//                      an NS-deep ring (waits until the MMAs freed the slot);
-//   warp 1, one lane : issues tcgen05.mma for each chunk into one of two
-//                      accumulators in tensor memory (256 FP32 columns each),
-//                      tcgen05.commit frees the ring slot and, after an item's
-//                      last chunk, marks its accumulator full;
-//   warps 2-5        : epilogue, tcgen05.ld of the accumulator rows (warp w
-//                      reads lanes 32 (w % 4) ..), then stage 1 scales, rounds
-//                      to bf16 (split into three planes for BF16x3), transposes
-//                      8 x 8 groups across lanes with shuffles and stores
-//                      T_t^T in the tiled layout; stage 2 adds into sigma (FP64,
-//                      atomics for split items). It then frees the accumulator.
-// The two accumulators let the epilogue of one item overlap the MMAs of the
-// next. MMA shape: M = 128 (rows past the panel are ignored), N = the view's
-// rows rounded to 16 (stage 1, several views side by side in the accumulator)
-// or the sigma block's columns rounded to 16 (stage 2), K = 16 per instruction.
-// The shared-memory descriptors are K-major without swizzle: K-adjacent core
-// matrices LBO = (panel core rows) x 128 bytes apart, M/N-adjacent ones 128
-// bytes apart, exactly the order of the tiled arenas.
+// plane moves it into shared memory. One persistent CTA per SM walks a static
+// list of work items with three roles:
+//   warp 0   : producer. Reserves each K chunk in a byte ring of shared memory
+//              (chunks take exactly their bytes, so many small chunks are in
+//              flight), writes the chunk's MMA list into one of NR metadata
+//              records, arms the record's mbarrier with the byte count and
+//              issues the bulk copies (stage 1: one lane per view). Segment
+//              and view descriptors are loaded 32 at a time by the warp.
+//   warp 1   : one lane issues tcgen05.mma from the metadata records into one
+//              of two accumulators in tensor memory (256 FP32 columns each);
+//              tcgen05.commit frees the record and its ring bytes and, after an
+//              item's last chunk, marks the accumulator full.
+//   warps 2-9: epilogue, two warps per tensor-memory lane quarter splitting the
+//              columns. Stage 1 scales T_t^T rows, rounds them to bf16 (three
+//              planes for BF16x3) and stores 16-byte core-matrix rows; stage 2
+//              adds into sigma (FP64, atomics for split items). Then the
+//              accumulator is released.
+// Stage 1 computes T_t^T = O_R psi_blk^T (accumulator lane = row of T_t^T), so
+// no transposition is needed to produce the stage-2 B operand.
+// MMA shape: M = 128 (rows past the panel are ignored), N = the B panel's rows
+// rounded to 16, K = 16 per instruction. Shared-memory descriptors are K-major
+// without swizzle: K-adjacent core matrices LBO = (panel core rows) x 128 bytes
+// apart, M/N-adjacent ones 128 bytes apart, the order of the tiled arenas.
 // BF16x3 (Henry, Tang, Heinecke, ARITH 2019): x = x0 + x1 + x2; the six
 // products a_i b_j with i + j <= 2 accumulate in FP32.
 // Every wait is bounded (~1 s of clock64); on a timeout the CTA records an
@@ -40,29 +41,19 @@ namespace qd {
 namespace {
 
 constexpr long long WAIT_CYCLES = 2000000000ll;
-constexpr int NTHREADS = 192;
+constexpr int NEPI = 8;                     // epilogue warps
+constexpr int NTHREADS = 64 + 32 * NEPI;
 constexpr uint32_t TMEM_COLS = 512;
 
 template <int MODE>
 struct TCfg;
 template <>
 struct TCfg<TT_BF16> {
-  static constexpr int NP = 1, KC = 64, NS = 4;
+  static constexpr int NP = 1, KC = 64;   // planes, K elements per chunk
 };
 template <>
 struct TCfg<TT_BF16X3> {
-  static constexpr int NP = 3, KC = 32, NS = 3;
-};
-
-template <int MODE>
-struct Ring {
-  static constexpr int NP = TCfg<MODE>::NP, KC = TCfg<MODE>::KC, NS = TCfg<MODE>::NS;
-  static constexpr uint32_t APL = TP_A * KC * 2;         // one A plane of a slot
-  static constexpr uint32_t BPL = TP_B * KC * 2;         // one B plane of a slot
-  static constexpr uint32_t SLOT = NP * (APL + BPL);
-  static constexpr uint32_t RING = NS * SLOT + 256;      // slack: MMA reads of a last view's padding rows
-  static constexpr uint32_t BARS = RING;                 // 2 NS ring + 4 accumulator + 1 drain mbarriers
-  static constexpr uint32_t SMEM = BARS + (2 * NS + 5) * 8 + 16;
+  static constexpr int NP = 3, KC = 32;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -87,6 +78,17 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
   while (!mbar_try(bar, parity)) {
     if (*abort_flag) return false;
     if (clock64() - t0 > WAIT_CYCLES) return false;
+  }
+  return true;
+}
+// bounded wait that yields the issue slots between polls (for the epilogue
+// warps, which share their schedulers with the producer and MMA lanes)
+__device__ __forceinline__ bool mbar_wait_sleep(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  const long long t0 = clock64();
+  while (!mbar_try(bar, parity)) {
+    if (*abort_flag) return false;
+    if (clock64() - t0 > WAIT_CYCLES) return false;
+    __nanosleep(100);
   }
   return true;
 }
@@ -129,23 +131,6 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
       "l"(da), "l"(db), "r"(id), "r"(acc));
 }
-// all planes of one K step: BF16 one product, BF16x3 a_i b_j with i + j <= 2
-template <int MODE>
-__device__ __forceinline__ void mma_step(uint32_t tmem, uint32_t a, uint32_t b, uint32_t lboa, uint32_t lbob,
-                                         uint32_t id, bool first) {
-  using R = Ring<MODE>;
-  if constexpr (R::NP == 1) {
-    mma_bf16(tmem, sdesc(a, lboa, 128), sdesc(b, lbob, 128), id, first ? 0u : 1u);
-  } else {
-    const int pi[6] = {2, 1, 0, 1, 0, 0};
-    const int pj[6] = {0, 1, 2, 0, 1, 0};
-#pragma unroll
-    for (int q = 0; q < 6; ++q)
-      mma_bf16(tmem, sdesc(a + pi[q] * R::APL, lboa, 128), sdesc(b + pj[q] * R::BPL, lbob, 128), id,
-               (first && q == 0) ? 0u : 1u);
-  }
-}
-
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
   uint32_t r[8];
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -156,39 +141,6 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
   for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-// 8 x 8 transpose of packed bf16 pairs across the 8 lanes of a lane group:
-// lane r holds row r (elements 2k, 2k+1 in p[k]); afterwards it holds column r
-__device__ __forceinline__ void transpose8(uint32_t* p, int lane) {
-  const int r = lane & 7;
-  {  // element distance 4 = register distance 2
-    const bool hi = (r >> 2) & 1;
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      const uint32_t send = hi ? p[k] : p[k + 2];
-      const uint32_t recv = __shfl_xor_sync(0xffffffffu, send, 4);
-      if (hi) p[k] = recv; else p[k + 2] = recv;
-    }
-  }
-  {  // element distance 2 = register distance 1
-    const bool hi = (r >> 1) & 1;
-#pragma unroll
-    for (int k = 0; k < 4; k += 2) {
-      const uint32_t send = hi ? p[k] : p[k + 1];
-      const uint32_t recv = __shfl_xor_sync(0xffffffffu, send, 2);
-      if (hi) p[k] = recv; else p[k + 1] = recv;
-    }
-  }
-  {  // element distance 1 = halves of a register
-    const bool hi = r & 1;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const uint32_t send = hi ? (p[k] & 0xFFFFu) : (p[k] >> 16);
-      const uint32_t recv = __shfl_xor_sync(0xffffffffu, send, 1);
-      p[k] = hi ? ((p[k] & 0xFFFF0000u) | recv) : ((p[k] & 0xFFFFu) | (recv << 16));
-    }
-  }
-}
-
 __device__ __forceinline__ uint32_t bf16_bits(float x) {
   return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x));
 }
@@ -196,9 +148,9 @@ __device__ __forceinline__ uint32_t bf16_bits(float x) {
 struct Stage1Args {
   const K1Item* items;
   const K1View* views;
-  const uint8_t* A;
+  const uint8_t* A;    // right-view arena (A operands)
   int64_t aplane;
-  const uint8_t* B;
+  const uint8_t* B;    // psi arena (B operand)
   int64_t bplane;
   uint8_t* T;
   int64_t tplane;
@@ -206,27 +158,100 @@ struct Stage1Args {
 struct Stage2Args {
   const K2Item* items;
   const K2Seg* segs;
-  const uint8_t* A;
+  const uint8_t* A;    // left-view arena
   int64_t aplane;
-  const uint8_t* B;
+  const uint8_t* B;    // T arena
   int64_t bplane;
   double* sig;
 };
 
+// One K chunk as the MMA issuer sees it: up to MAXOPS (A, B) pairs, each its
+// own accumulator column range, over nk16 K steps; planes of a chunk follow
+// each other at astride / bstride bytes.
+constexpr int MAXOPS = 16;
+struct Op {
+  uint32_t a, b, lboa, lbob, idesc, tcol;
+};
+struct Meta {
+  uint32_t nops, nk16, flags, li, astride, bstride;
+  Op op[MAXOPS];
+};
+constexpr uint32_t F_FIRST = 1, F_LAST = 2, F_END = 4;
+
+template <int MODE>
+struct Smem {
+  static constexpr int NP = TCfg<MODE>::NP, KC = TCfg<MODE>::KC;
+  static constexpr uint32_t RB = 196608;      // byte ring of chunk data
+  static constexpr uint32_t SLACK = 2048;     // MMA reads of padding rows past a chunk's end
+  static constexpr int NR = 32;               // chunk records in flight
+  static constexpr uint32_t META = RB + SLACK;
+  static constexpr uint32_t BARS = META + NR * sizeof(Meta);
+  static constexpr uint32_t SMEM = BARS + (2 * NR + 5) * 8 + 16;
+};
+
+template <int MODE>
+__device__ __forceinline__ void mma_op(uint32_t tmem, const Op& o, uint32_t koff_a, uint32_t koff_b,
+                                       uint32_t astride, uint32_t bstride, bool first) {
+  if constexpr (TCfg<MODE>::NP == 1) {
+    mma_bf16(tmem, sdesc(o.a + koff_a, o.lboa, 128), sdesc(o.b + koff_b, o.lbob, 128), o.idesc, first ? 0u : 1u);
+  } else {
+    const int pi[6] = {2, 1, 0, 1, 0, 0};
+    const int pj[6] = {0, 1, 2, 0, 1, 0};
+#pragma unroll
+    for (int q = 0; q < 6; ++q)
+      mma_bf16(tmem, sdesc(o.a + pi[q] * astride + koff_a, o.lboa, 128),
+               sdesc(o.b + pj[q] * bstride + koff_b, o.lbob, 128), o.idesc, (first && q == 0) ? 0u : 1u);
+  }
+}
+
+__device__ __forceinline__ int64_t shfl64(int64_t v, int src) {
+  const int lo = __shfl_sync(0xffffffffu, (int)(v & 0xffffffff), src);
+  const int hi = __shfl_sync(0xffffffffu, (int)(v >> 32), src);
+  return ((int64_t)hi << 32) | (uint32_t)lo;
+}
+
+// Producer-side byte ring: chunk c takes [vs, vs + size) of a virtual byte
+// stream (never wrapping inside the ring) and record c % NR; both are reused
+// once the MMAs of the chunks before it have completed (freed in order).
+template <int MODE>
+struct RingAlloc {
+  using S = Smem<MODE>;
+  uint64_t vhead = 0, freed = 0;
+  long long chunk = 0, oldest = 0;
+  uint64_t vend[S::NR];
+  // lane 0 only; false on a timeout
+  __device__ bool reserve(uint32_t size, uint32_t& off, uint32_t bars, volatile int* abort_flag) {
+    uint64_t vs = vhead;
+    if ((vs % S::RB) + size > S::RB) vs = (vs / S::RB + 1) * S::RB;
+    const uint64_t ve = vs + size;
+    while (oldest < chunk && (oldest <= chunk - S::NR || ve > freed + S::RB)) {
+      const int r = (int)(oldest % S::NR);
+      if (!mbar_wait(bars + 8u * (S::NR + r), (uint32_t)((oldest / S::NR) & 1), abort_flag)) return false;
+      freed = vend[r];
+      ++oldest;
+    }
+    vend[chunk % S::NR] = ve;
+    vhead = ve;
+    off = (uint32_t)(vs % S::RB);
+    return true;
+  }
+};
+
 template <int MODE, int STAGE, typename Args>
 __global__ void __launch_bounds__(NTHREADS, 1) tiled_gemm(Args args, int nitems, int* err) {
-  using R = Ring<MODE>;
-  constexpr int NP = R::NP, KC = R::KC, NS = R::NS;
+  using S = Smem<MODE>;
+  constexpr int NP = S::NP, KC = S::KC, NR = S::NR;
   extern __shared__ __align__(1024) uint8_t smem[];
   const uint32_t sbase = smem_u32(smem);
-  const uint32_t bars = sbase + R::BARS;
-  auto full = [&](int s) { return bars + 8u * s; };
-  auto empty = [&](int s) { return bars + 8u * (NS + s); };
-  auto accf = [&](int b) { return bars + 8u * (2 * NS + b); };
-  auto acce = [&](int b) { return bars + 8u * (2 * NS + 2 + b); };
-  const uint32_t drain = bars + 8u * (2 * NS + 4);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + R::BARS + (2 * NS + 5) * 8);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + R::BARS + (2 * NS + 5) * 8 + 8);
+  Meta* meta = reinterpret_cast<Meta*>(smem + S::META);
+  const uint32_t bars = sbase + S::BARS;
+  auto full = [&](int r) { return bars + 8u * r; };
+  auto empty = [&](int r) { return bars + 8u * (NR + r); };
+  auto accf = [&](int b) { return bars + 8u * (2 * NR + b); };
+  auto acce = [&](int b) { return bars + 8u * (2 * NR + 2 + b); };
+  const uint32_t drain = bars + 8u * (2 * NR + 4);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + S::BARS + (2 * NR + 5) * 8);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + S::BARS + (2 * NR + 5) * 8 + 8);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (warp == 1) {
@@ -235,13 +260,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) tiled_gemm(Args args, int nitems,
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    for (int s = 0; s < NS; ++s) {
-      mbar_init(full(s), 1);
-      mbar_init(empty(s), 1);
+    for (int r = 0; r < NR; ++r) {
+      mbar_init(full(r), 1);
+      mbar_init(empty(r), 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(accf(b), 1);
-      mbar_init(acce(b), 4);
+      mbar_init(acce(b), NEPI);
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
@@ -253,137 +278,179 @@ __global__ void __launch_bounds__(NTHREADS, 1) tiled_gemm(Args args, int nitems,
   const uint32_t tmem = *tslot;
 
   if (warp == 0) {
-    // ---------------- producer ----------------
-    if (lane == 0) {
-      int chunk = 0;
-      bool ok = true;
-      for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
-        if constexpr (STAGE == 1) {
-          const K1Item it = args.items[item];
-          const int kp = tiled_c8(it.k) * 8;
-          for (int k0 = 0; k0 < kp && ok; k0 += KC) {
-            const int ck = min(KC, kp - k0), cc = ck / 8;
-            const int slot = chunk % NS;
-            if (chunk >= NS && !mbar_wait(empty(slot), ((chunk / NS) - 1) & 1, abort_flag)) { ok = false; break; }
-            uint32_t bytes = (uint32_t)it.pa8 * cc * 128;
-            for (int v = it.v0; v < it.v0 + it.nv; ++v) bytes += (uint32_t)args.views[v].pb8 * cc * 128;
-            mbar_expect_tx(full(slot), bytes * NP);
-            const uint32_t sa = sbase + slot * R::SLOT, sb = sa + NP * R::APL;
+    // ---------------- producer (whole warp; lane 0 waits and signals) ----------------
+    RingAlloc<MODE> ring;
+    bool ok = true;
+    int li = 0;
+    // reserve the next chunk; the outcome is shared by the warp
+    auto next = [&](uint32_t size, uint32_t& off) -> bool {
+      int good = 1;
+      uint32_t o = 0;
+      if (lane == 0) good = ring.reserve(size, o, bars, abort_flag) ? 1 : 0;
+      good = __shfl_sync(0xffffffffu, good, 0);
+      off = __shfl_sync(0xffffffffu, o, 0);
+      return good != 0;
+    };
+    for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x, ++li) {
+      if constexpr (STAGE == 1) {
+        const K1Item it = args.items[item];
+        K1View mv{};
+        if (lane < it.nv) mv = args.views[it.v0 + lane];
+        const int kp = tiled_c8(it.k) * 8;
+        for (int k0 = 0; k0 < kp && ok; k0 += KC) {
+          const int ck = min(KC, kp - k0), cc = ck / 8;
+          // A parts of the views side by side (exclusive prefix over lanes), then B
+          const uint32_t mine = lane < it.nv ? (uint32_t)mv.pa8 * cc * 128 : 0u;
+          uint32_t pre = mine;
+#pragma unroll
+          for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, pre, d);
+            if (lane >= d) pre += t;
+          }
+          const uint32_t atot = __shfl_sync(0xffffffffu, pre, 31);
+          pre -= mine;
+          const uint32_t bsz = (uint32_t)it.pb8 * cc * 128;
+          uint32_t off;
+          if (!next(NP * (atot + bsz), off)) { ok = false; break; }
+          const int r = (int)(ring.chunk % NR);
+          const uint32_t ca = sbase + off, cb = ca + NP * atot;
+          if (lane < it.nv) {
+            Op& o = meta[r].op[lane];
+            o.a = ca + pre;
+            o.b = cb;
+            o.lboa = (uint32_t)mv.pa8 * 128;
+            o.lbob = (uint32_t)it.pb8 * 128;
+            o.idesc = idesc_bf16(16 * ((it.nrows + 15) / 16), 0);
+            o.tcol = (uint32_t)mv.tcol;
+          }
+          if (lane == 0) {
+            meta[r].nops = (uint32_t)it.nv;
+            meta[r].nk16 = (uint32_t)(ck / 16);
+            meta[r].flags = (k0 == 0 ? F_FIRST : 0u) | (k0 + KC >= kp ? F_LAST : 0u);
+            meta[r].li = (uint32_t)li;
+            meta[r].astride = atot;
+            meta[r].bstride = bsz;
+          }
+          __syncwarp();
+          if (lane == 0) mbar_expect_tx(full(r), NP * (atot + bsz));
+          __syncwarp();
+          if (lane < it.nv) {
 #pragma unroll
             for (int q = 0; q < NP; ++q)
-              bulk_g2s(sa + q * R::APL, args.A + q * args.aplane + it.a + (int64_t)(k0 / 8) * it.pa8 * 128,
-                       (uint32_t)it.pa8 * cc * 128, full(slot));
-            uint32_t boff = 0;
-            for (int v = it.v0; v < it.v0 + it.nv; ++v) {
-              const K1View w = args.views[v];
-              const uint32_t nb = (uint32_t)w.pb8 * cc * 128;
-#pragma unroll
-              for (int q = 0; q < NP; ++q)
-                bulk_g2s(sb + q * R::BPL + boff, args.B + q * args.bplane + w.b + (int64_t)(k0 / 8) * w.pb8 * 128, nb,
-                         full(slot));
-              boff += nb;
-            }
-            ++chunk;
+              bulk_g2s(ca + q * atot + pre, args.A + q * args.aplane + mv.a + (int64_t)(k0 / 8) * mv.pa8 * 128, mine,
+                       full(r));
           }
-        } else {
-          const K2Item it = args.items[item];
-          const int pa8 = (it.mrows + 7) / 8, pb8 = (it.nrows + 7) / 8;
-          for (int s = it.s0; s < it.s1 && ok; ++s) {
-            const K2Seg g = args.segs[s];
-            const int c8 = tiled_c8(g.k), kp = c8 * 8;
-            const int64_t ab = g.a + (int64_t)it.mp * (TP_A / 8) * c8 * 128;
-            const int64_t bb = g.b + (int64_t)it.np * (TP_B / 8) * c8 * 128;
+          if (lane == 0) {
+#pragma unroll
+            for (int q = 0; q < NP; ++q)
+              bulk_g2s(cb + q * bsz, args.B + q * args.bplane + it.b + (int64_t)(k0 / 8) * it.pb8 * 128, bsz, full(r));
+          }
+          ring.chunk++;
+          __syncwarp();
+        }
+      } else {
+        const K2Item it = args.items[item];
+        const int pa8 = (it.mrows + 7) / 8, pb8 = (it.nrows + 7) / 8;
+        const uint32_t id = idesc_bf16(16 * ((it.nrows + 15) / 16), 0);
+        for (int sb = it.s0; sb < it.s1 && ok; sb += 32) {
+          K2Seg mg{};
+          if (sb + lane < it.s1) mg = args.segs[sb + lane];
+          const int cnt = min(32, it.s1 - sb);
+          for (int j = 0; j < cnt && ok; ++j) {
+            const int k = __shfl_sync(0xffffffffu, mg.k, j);
+            const int64_t ga = shfl64(mg.a, j), gb = shfl64(mg.b, j);
+            const int c8 = tiled_c8(k), kp = c8 * 8;
+            const int64_t ab = ga + (int64_t)it.mp * (TP_A / 8) * c8 * 128;
+            const int64_t bb = gb + (int64_t)it.np * (TP_B / 8) * c8 * 128;
             for (int k0 = 0; k0 < kp; k0 += KC) {
               const int ck = min(KC, kp - k0), cc = ck / 8;
-              const int slot = chunk % NS;
-              if (chunk >= NS && !mbar_wait(empty(slot), ((chunk / NS) - 1) & 1, abort_flag)) { ok = false; break; }
               const uint32_t na = (uint32_t)pa8 * cc * 128, nb = (uint32_t)pb8 * cc * 128;
-              mbar_expect_tx(full(slot), (na + nb) * NP);
-              const uint32_t sa = sbase + slot * R::SLOT, sb = sa + NP * R::APL;
+              uint32_t off;
+              if (!next(NP * (na + nb), off)) { ok = false; break; }
+              if (lane == 0) {
+                const int r = (int)(ring.chunk % NR);
+                const uint32_t ca = sbase + off, cb = ca + NP * na;
+                Op& o = meta[r].op[0];
+                o.a = ca;
+                o.b = cb;
+                o.lboa = (uint32_t)pa8 * 128;
+                o.lbob = (uint32_t)pb8 * 128;
+                o.idesc = id;
+                o.tcol = 0;
+                meta[r].nops = 1;
+                meta[r].nk16 = (uint32_t)(ck / 16);
+                meta[r].flags = (sb == it.s0 && j == 0 && k0 == 0 ? F_FIRST : 0u) |
+                                (sb + j == it.s1 - 1 && k0 + KC >= kp ? F_LAST : 0u);
+                meta[r].li = (uint32_t)li;
+                meta[r].astride = na;
+                meta[r].bstride = nb;
+                mbar_expect_tx(full(r), NP * (na + nb));
 #pragma unroll
-              for (int q = 0; q < NP; ++q) {
-                bulk_g2s(sa + q * R::APL, args.A + q * args.aplane + ab + (int64_t)(k0 / 8) * pa8 * 128, na, full(slot));
-                bulk_g2s(sb + q * R::BPL, args.B + q * args.bplane + bb + (int64_t)(k0 / 8) * pb8 * 128, nb, full(slot));
+                for (int q = 0; q < NP; ++q) {
+                  bulk_g2s(ca + q * na, args.A + q * args.aplane + ab + (int64_t)(k0 / 8) * pa8 * 128, na, full(r));
+                  bulk_g2s(cb + q * nb, args.B + q * args.bplane + bb + (int64_t)(k0 / 8) * pb8 * 128, nb, full(r));
+                }
               }
-              ++chunk;
+              ring.chunk++;
+              __syncwarp();
             }
           }
         }
       }
+    }
+    if (ok) {
+      // end-of-work record for the MMA issuer
+      uint32_t off;
+      if (next(0, off)) {
+        if (lane == 0) {
+          const int r = (int)(ring.chunk % NR);
+          meta[r].nops = 0;
+          meta[r].flags = F_END;
+          mbar_arrive(full(r));
+        }
+        ring.chunk++;
+      } else {
+        ok = false;
+      }
+    }
+    if (lane == 0) {
       if (!ok) {
         atomicExch(err, 1);
         *abort_flag = 1;
       }
       // no copy of ours may still be in flight when the CTA exits
-      for (int c = chunk - 1; c >= 0 && c >= chunk - NS; --c) {
+      for (long long c = ring.oldest; c < ring.chunk; ++c) {
         const long long t0 = clock64();
-        while (!mbar_try(full(c % NS), (c / NS) & 1) && clock64() - t0 < WAIT_CYCLES) {
+        while (!mbar_try(full((int)(c % NR)), (uint32_t)((c / NR) & 1)) && clock64() - t0 < WAIT_CYCLES) {
         }
       }
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
-      int chunk = 0, li = 0;
       bool ok = true;
-      for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x, ++li) {
-        const int b = li & 1;
-        if (li >= 2 && !mbar_wait(acce(b), ((li >> 1) - 1) & 1, abort_flag)) { ok = false; break; }
+      for (long long c = 0;; ++c) {
+        const int r = (int)(c % NR);
+        if (!mbar_wait(full(r), (uint32_t)((c / NR) & 1), abort_flag)) { ok = false; break; }
+        const Meta& m = meta[r];
+        const uint32_t flags = m.flags;
+        if (flags & F_END) break;
+        const int li = (int)m.li, b = li & 1;
+        if ((flags & F_FIRST) && li >= 2 && !mbar_wait(acce(b), (uint32_t)(((li >> 1) - 1) & 1), abort_flag)) {
+          ok = false;
+          break;
+        }
         tc_fence_after();
         const uint32_t tacc = tmem + (uint32_t)b * 256u;
-        if constexpr (STAGE == 1) {
-          const K1Item it = args.items[item];
-          const int kp = tiled_c8(it.k) * 8;
-          bool first = true;
-          for (int k0 = 0; k0 < kp; k0 += KC) {
-            const int ck = min(KC, kp - k0), cc = ck / 8;
-            const int slot = chunk % NS;
-            if (!mbar_wait(full(slot), (chunk / NS) & 1, abort_flag)) { ok = false; break; }
-            tc_fence_after();
-            const uint32_t sa = sbase + slot * R::SLOT, sb = sa + NP * R::APL;
-            const uint32_t lboa = (uint32_t)it.pa8 * 128;
-            for (int kk = 0; kk < ck / 16; ++kk) {
-              uint32_t boff = 0;
-              for (int v = it.v0; v < it.v0 + it.nv; ++v) {
-                const K1View w = args.views[v];
-                const uint32_t lbob = (uint32_t)w.pb8 * 128;
-                const int n = 16 * ((w.nrows + 15) / 16);
-                mma_step<MODE>(tacc + (uint32_t)w.ncol, sa + kk * 2 * lboa, sb + boff + kk * 2 * lbob, lboa, lbob,
-                               idesc_bf16(n, 0), first && kk == 0);
-                boff += (uint32_t)w.pb8 * cc * 128;
-              }
-            }
-            first = false;
-            tc_commit(empty(slot));
-            ++chunk;
+        const int nops = (int)m.nops, nk = (int)m.nk16;
+        for (int kk = 0; kk < nk; ++kk)
+          for (int o = 0; o < nops; ++o) {
+            const Op op = m.op[o];
+            mma_op<MODE>(tacc + op.tcol, op, kk * 2 * op.lboa, kk * 2 * op.lbob, m.astride, m.bstride,
+                         (flags & F_FIRST) && kk == 0);
           }
-        } else {
-          const K2Item it = args.items[item];
-          const int pa8 = (it.mrows + 7) / 8, pb8 = (it.nrows + 7) / 8;
-          const int n = 16 * ((it.nrows + 15) / 16);
-          const uint32_t lboa = (uint32_t)pa8 * 128, lbob = (uint32_t)pb8 * 128;
-          bool first = true;
-          for (int s = it.s0; s < it.s1 && ok; ++s) {
-            const K2Seg g = args.segs[s];
-            const int kp = tiled_c8(g.k) * 8;
-            const uint32_t id = idesc_bf16(n, g.neg);
-            for (int k0 = 0; k0 < kp; k0 += KC) {
-              const int ck = min(KC, kp - k0);
-              const int slot = chunk % NS;
-              if (!mbar_wait(full(slot), (chunk / NS) & 1, abort_flag)) { ok = false; break; }
-              tc_fence_after();
-              const uint32_t sa = sbase + slot * R::SLOT, sb = sa + NP * R::APL;
-              for (int kk = 0; kk < ck / 16; ++kk) {
-                mma_step<MODE>(tacc, sa + kk * 2 * lboa, sb + kk * 2 * lbob, lboa, lbob, id, first);
-                first = false;
-              }
-              tc_commit(empty(slot));
-              ++chunk;
-            }
-          }
-        }
-        if (!ok) break;
-        tc_commit(accf(b));
+        tc_commit(empty(r));
+        if (flags & F_LAST) tc_commit(accf(b));
       }
       if (!ok) {
         atomicExch(err, 1);
@@ -396,14 +463,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) tiled_gemm(Args args, int nitems,
       }
     }
   } else {
-    // ---------------- epilogue (warps 2..5) ----------------
-    const int quarter = warp & 3;
-    const int m = quarter * 32 + lane;  // accumulator row (lane) within the panel
+    // ---------------- epilogue (warps 2 .. 2 + NEPI - 1) ----------------
+    const int quarter = warp & 3;            // tensor-memory lanes this warp may read
+    const int half = (warp - 2) >> 2;        // two warps per lane quarter split the columns
+    const int m = quarter * 32 + lane;       // accumulator row
     int li = 0;
     for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++li) {
       const int b = li & 1;
-      // the warp decides together: tcgen05.ld below is warp-collective
-      const bool okw = __all_sync(0xffffffffu, mbar_wait(accf(b), (li >> 1) & 1, abort_flag));
+      const bool okw = __all_sync(0xffffffffu, mbar_wait_sleep(accf(b), (uint32_t)((li >> 1) & 1), abort_flag));
       if (!okw) {
         if (lane == 0) atomicExch(err, 1);
         *abort_flag = 1;
@@ -413,38 +480,36 @@ __global__ void __launch_bounds__(NTHREADS, 1) tiled_gemm(Args args, int nitems,
       const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)b * 256u;
       if constexpr (STAGE == 1) {
         const K1Item it = args.items[item];
-        const bool mval = m < it.mrows;
         const int c8t = tiled_c8(it.mtot);
-        const int m8 = (m & ~7);
-        const bool group_live = m8 < it.mrows;  // the 16-byte unit holds a valid K position
-        const int jc = (it.mp * TP_A + m8) / 8;
-        for (int v = it.v0; v < it.v0 + it.nv; ++v) {
+        const int ngrp = (it.nrows + 7) / 8;
+        for (int v = it.v0 + half; v < it.v0 + it.nv; v += 2) {
           const K1View w = args.views[v];
+          const bool mval = m < w.mrows;
+          const int R = w.mp * TP_A + m;        // row of T_t^T
+          const int pr = R / TP_B;
+          const int pr8 = (min(TP_B, w.ntot - pr * TP_B) + 7) / 8;
+          uint8_t* rowp = args.T + w.tout + (int64_t)pr * (TP_B / 8) * c8t * 128 + ((R % TP_B) / 8) * 128 + (R % 8) * 16;
           const float osc = (float)w.osc;
-          for (int c0 = 0; c0 < w.nrows; c0 += 8) {
+          for (int g = 0; g < ngrp; ++g) {
             float x[8];
-            tmem_ld8(trow + (uint32_t)(w.ncol + c0), x);
+            tmem_ld8(trow + (uint32_t)(w.tcol + 8 * g), x);
+            if (mval) {
+              const int jc = (it.np * TP_B) / 8 + g;   // 16-byte K unit of T_t^T
 #pragma unroll
-            for (int j = 0; j < 8; ++j) x[j] = mval ? osc * x[j] : 0.f;
-            const int rrow = c0 + (lane & 7);          // row of T^T within this panel after the transpose
-            const bool store = group_live && rrow < w.nrows;
-            const int R = w.np * TP_B + rrow;
-            uint8_t* dst = args.T + w.tout + (int64_t)w.np * (TP_B / 8) * c8t * 128 + (int64_t)jc * w.pb8 * 128 +
-                           ((R % TP_B) / 8) * 128 + (R % 8) * 16;
+              for (int j = 0; j < 8; ++j) x[j] = (8 * g + j < it.nrows) ? osc * x[j] : 0.f;
 #pragma unroll
-            for (int q = 0; q < NP; ++q) {
-              uint32_t p[4];
-              float r[8];
+              for (int q = 0; q < NP; ++q) {
+                uint32_t p[4];
 #pragma unroll
-              for (int j = 0; j < 8; ++j) {
-                const uint32_t h = bf16_bits(x[j]);
-                r[j] = x[j] - __uint_as_float(h << 16);
-                if (j & 1) p[j >> 1] |= h << 16; else p[j >> 1] = h;
+                for (int j = 0; j < 8; j += 2) {
+                  const uint32_t h0 = bf16_bits(x[j]), h1 = bf16_bits(x[j + 1]);
+                  p[j >> 1] = h0 | (h1 << 16);
+                  x[j] -= __uint_as_float(h0 << 16);
+                  x[j + 1] -= __uint_as_float(h1 << 16);
+                }
+                *reinterpret_cast<uint4*>(rowp + q * args.tplane + (int64_t)jc * pr8 * 128) =
+                    make_uint4(p[0], p[1], p[2], p[3]);
               }
-#pragma unroll
-              for (int j = 0; j < 8; ++j) x[j] = r[j];
-              transpose8(p, lane);
-              if (store) *reinterpret_cast<uint4*>(dst + q * args.tplane) = make_uint4(p[0], p[1], p[2], p[3]);
             }
           }
         }
@@ -452,15 +517,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) tiled_gemm(Args args, int nitems,
         const K2Item it = args.items[item];
         const bool mval = m < it.mrows;
         double* row = args.sig + it.out + (int64_t)(it.mp * TP_A + m) * it.ldc + it.np * TP_B;
-        for (int c0 = 0; c0 < it.nrows; c0 += 8) {
+        const int ngrp = (it.nrows + 7) / 8;
+        for (int g = half; g < ngrp; g += 2) {
           float x[8];
-          tmem_ld8(trow + (uint32_t)c0, x);
+          tmem_ld8(trow + (uint32_t)(8 * g), x);
           if (mval) {
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-              if (c0 + j < it.nrows) {
-                if (it.split) atomicAdd(row + c0 + j, (double)x[j]);
-                else row[c0 + j] += (double)x[j];
+              const int c = 8 * g + j;
+              if (c < it.nrows) {
+                if (it.split) atomicAdd(row + c, (double)x[j]);
+                else row[c] += (double)x[j];
               }
             }
           }
@@ -525,7 +592,7 @@ __global__ void __launch_bounds__(256) tile_views_kernel(const TView* __restrict
 template <int MODE, int STAGE, typename Args>
 cudaError_t launch(Args a, int nitems, int grid, int* err, cudaStream_t st) {
   if (nitems <= 0) return cudaSuccess;
-  constexpr uint32_t sm = Ring<MODE>::SMEM;
+  constexpr uint32_t sm = Smem<MODE>::SMEM;
   static bool init = false;
   if (!init) {
     cudaError_t e = cudaFuncSetAttribute(tiled_gemm<MODE, STAGE, Args>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -547,10 +614,11 @@ cudaError_t launch_tile_views(const TView* views, int nviews, uint8_t* dst, int6
 }
 
 cudaError_t launch_tiled_stage1(int mode, const K1Item* items, int nitems, const K1View* views,
-                                const uint8_t* psi_arena, int64_t psi_plane, const uint8_t* b_arena,
-                                int64_t b_plane, uint8_t* t_arena, int64_t t_plane, int grid, int* err,
+                                const uint8_t* psi_arena, int64_t psi_plane, const uint8_t* r_arena,
+                                int64_t r_plane, uint8_t* t_arena, int64_t t_plane, int grid, int* err,
                                 cudaStream_t st) {
-  Stage1Args a{items, views, psi_arena, psi_plane, b_arena, b_plane, t_arena, t_plane};
+  // A operands: right views; B operand: psi
+  Stage1Args a{items, views, r_arena, r_plane, psi_arena, psi_plane, t_arena, t_plane};
   if (mode == TT_BF16) return launch<TT_BF16, 1>(a, nitems, grid, err, st);
   if (mode == TT_BF16X3) return launch<TT_BF16X3, 1>(a, nitems, grid, err, st);
   return cudaErrorInvalidValue;

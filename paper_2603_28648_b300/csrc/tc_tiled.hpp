@@ -15,10 +15,10 @@ constexpr int TT_BF16X3 = 1;  // three bf16 planes, six MMAs per K step
 cudaError_t launch_tile_views(const TView* views, int nviews, uint8_t* dst, int64_t plane_bytes, int planes,
                               const double* psi_base, cudaStream_t st);
 
-// Stage 1: T_t from psi and right views (T arena pads must be zero)
+// Stage 1: T_t^T from the right views and psi (T arena pads must be zero)
 cudaError_t launch_tiled_stage1(int mode, const K1Item* items, int nitems, const K1View* views,
-                                const uint8_t* psi_arena, int64_t psi_plane, const uint8_t* b_arena,
-                                int64_t b_plane, uint8_t* t_arena, int64_t t_plane, int grid, int* err,
+                                const uint8_t* psi_arena, int64_t psi_plane, const uint8_t* r_arena,
+                                int64_t r_plane, uint8_t* t_arena, int64_t t_plane, int grid, int* err,
                                 cudaStream_t st);
 
 // Stage 2: sigma += O_L T_t (sigma zeroed by the caller)

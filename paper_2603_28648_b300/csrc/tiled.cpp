@@ -50,9 +50,10 @@ TiledPlan plan_tiled(const HeffPlan& plan, const PsiLayout& lay, const TileCfg& 
   const int kmax = cfg.kmax;
   TiledPlan P;
   P.flops = plan.flops;
-  Arena psi{&P.psivw, &P.psibytes, TP_A, {}};
+  P.psi_elems = lay.size;
+  Arena psi{&P.psivw, &P.psibytes, TP_B, {}};
   Arena am{&P.avw, &P.abytes, TP_A, {}};
-  Arena bm{&P.bvw, &P.bbytes, TP_B, {}};
+  Arena bm{&P.bvw, &P.bbytes, TP_A, {}};
   std::map<int64_t, int> blk_of_off;
   std::vector<int64_t> psi_off(lay.blks.size());
   for (size_t i = 0; i < lay.blks.size(); ++i) {
@@ -131,7 +132,9 @@ TiledPlan plan_tiled(const HeffPlan& plan, const PsiLayout& lay, const TileCfg& 
   }
 
   // stage 1: T_t grouped by psi block, blocks ordered by right then left
-  // sector so that consecutive items reuse the same right views from L2
+  // sector so that consecutive items reuse the same right views from L2; an
+  // item holds views while their accumulator columns fit the width and their
+  // rows fit the 256 A rows of a chunk
   std::vector<std::vector<int>> by_blk(lay.blks.size());
   for (int i = 0; i < (int)tps.size(); ++i) by_blk[tps[i].blk].push_back(i);
   std::vector<int> order(lay.blks.size());
@@ -143,41 +146,44 @@ TiledPlan plan_tiled(const HeffPlan& plan, const PsiLayout& lay, const TileCfg& 
     if (by_blk[blk].empty()) continue;
     const auto& pb = lay.blks[blk];
     const int c8 = tiled_c8(pb.cols);
-    for (int mp = 0; mp * TP_A < pb.rows; ++mp) {
-      const int mrows = std::min(TP_A, pb.rows - mp * TP_A);
+    for (int np = 0; np * TP_B < pb.rows; ++np) {
+      const int nrows = std::min(TP_B, pb.rows - np * TP_B);
+      const int nm = round16(nrows);
       K1Item it{};
-      it.a = psi_off[blk] + (int64_t)mp * (TP_A / 8) * c8 * 128;
-      it.pa8 = (mrows + 7) / 8;
-      it.mrows = mrows;
+      it.b = psi_off[blk] + (int64_t)np * (TP_B / 8) * c8 * 128;
+      it.pb8 = (nrows + 7) / 8;
+      it.nrows = nrows;
       it.k = pb.cols;
-      it.mp = mp;
+      it.np = np;
       it.mtot = pb.rows;
       it.v0 = (int)P.v1.size();
       it.nv = 0;
-      int col = 0;
+      int col = 0, rows = 0;
       for (int tp : by_blk[blk]) {
         const TProd& t = tps[tp];
-        for (int np = 0; np * TP_B < t.n; ++np) {
-          const int nrows = std::min(TP_B, t.n - np * TP_B);
-          const int nm = round16(nrows);
-          if (col + nm > std::max(cfg.width, nm)) {
+        for (int mp = 0; mp * TP_A < t.n; ++mp) {
+          const int mrows = std::min(TP_A, t.n - mp * TP_A);
+          const int r8 = 8 * ((mrows + 7) / 8);
+          if (it.nv && (col + nm > std::max(cfg.width, nm) || rows + r8 > 2 * TP_A || it.nv == 16)) {
             P.i1.push_back(it);
             it.v0 = (int)P.v1.size();
             it.nv = 0;
             col = 0;
+            rows = 0;
           }
           K1View v{};
-          v.b = t.b + (int64_t)np * (TP_B / 8) * c8 * 128;
+          v.a = t.b + (int64_t)mp * (TP_A / 8) * c8 * 128;
           v.tout = t.tout;
           v.osc = t.osc;
-          v.pb8 = (nrows + 7) / 8;
-          v.nrows = nrows;
-          v.ncol = col;
-          v.np = np;
+          v.pa8 = r8 / 8;
+          v.mrows = mrows;
+          v.tcol = col;
+          v.mp = mp;
           v.ntot = t.n;
           P.v1.push_back(v);
           it.nv++;
           col += nm;
+          rows += r8;
         }
       }
       if (it.nv) P.i1.push_back(it);

@@ -51,24 +51,27 @@ struct TView {
   int64_t dst;      // byte offset in its arena (plane 0)
 };
 
-// Stage 1. An item is one 128-row panel of one psi block (the A operand, K =
-// columns of the block) times up to 256 accumulator columns made of several
-// right-block references (views), each its own MMA of N = rows rounded to 16.
+// Stage 1 computes T_t transposed directly, T_t^T = O_R psi_blk^T: the A
+// operand is a right view (M = its rows, panel of 128), the B operand the psi
+// block (N = its rows, panel of 256, K = its columns). An item is one psi panel
+// times several views, each its own MMA into its own accumulator columns, so
+// that accumulator lane = row of T_t^T and the epilogue stores 16-byte rows.
 struct K1View {
-  int64_t b;        // B arena offset of the view's panel
-  int64_t tout;     // T arena offset of T_t (transposed: ntot rows, K = mtot)
+  int64_t a;        // right-view arena offset of the view's panel
+  int64_t tout;     // T arena offset of T_t^T (ntot rows, K = mtot)
   double osc;       // s_t: term coefficient x reference scalar x fermion parity
-  int pb8, nrows;   // core rows and valid rows of the panel
-  int ncol;         // first accumulator column (multiple of 16)
-  int np, ntot;     // panel index and total rows of the view (rows of T_t transposed)
+  int pa8, mrows;   // core rows and valid rows of the view panel
+  int tcol;         // first accumulator column (multiple of 16)
+  int mp, ntot;     // view panel index, rows of the view (rows of T_t^T)
   int pad;
 };
 struct K1Item {
-  int64_t a;        // psi arena offset of the panel
-  int pa8, mrows;   // core rows and valid rows of the panel
+  int64_t b;        // psi arena offset of the psi panel
+  int pb8, nrows;   // core rows and valid rows of the psi panel
   int k;            // K = columns of the psi block
-  int mp, mtot;     // panel index and rows of the psi block (K of T_t)
+  int np, mtot;     // psi panel index, rows of the psi block (K of T_t^T)
   int v0, nv;       // views
+  int pad;
 };
 
 // Stage 2. An item is one 128-row x up-to-256-column tile of one sigma block,
@@ -84,8 +87,9 @@ struct K2Item {
 };
 
 struct TiledPlan {
-  std::vector<TView> avw, bvw, psivw;   // A arena (left views), B arena (right views), psi arena
+  std::vector<TView> avw, bvw, psivw;   // left views (A role), right views (A role), psi (B role)
   int64_t abytes = 0, bbytes = 0, psibytes = 0, tbytes = 0;
+  int64_t psi_elems = 0;                // elements of psi and sigma
   std::vector<K1View> v1;
   std::vector<K1Item> i1;
   std::vector<K2Seg> s2;
@@ -96,7 +100,7 @@ struct TiledPlan {
 // Work-item shape, picked per problem-size class by the autotuner.
 //   kmax : summed K of one stage-2 item before a sigma block's segments are
 //          split over several items (more parallelism, FP64 atomics)
-//   width: accumulator columns of one stage-1 item (views packed side by side)
+//   width: accumulator columns of one stage-1 item (views side by side)
 struct TileCfg {
   int kmax = 4096;
   int width = TP_B;

@@ -103,4 +103,6 @@ def test_autotuner_picks_a_shape_and_keeps_results():
         assert st["tile_kmax"] > 0 and st["tile_width"] in (128, 256)
         if tune:
             assert st["tune_seconds"] >= 0.0
-    assert np.linalg.norm(out[True] - out[False]) <= 1e-5 * np.linalg.norm(out[False])
+    # shapes differ in how the FP32 partial sums are grouped (split items add
+    # in FP64): a difference far below the BF16 form's own error (~2e-3)
+    assert np.linalg.norm(out[True] - out[False]) <= 1e-4 * np.linalg.norm(out[False])
