@@ -42,6 +42,11 @@ def parse():
                     help="one full sweep (L->R->L) with FP64 Davidson and with the mixed policy, same start")
     ap.add_argument("--batched", action="store_true",
                     help="16 independent problems (L 12..24, D 128..512) in one CUDA graph vs one by one")
+    ap.add_argument("--max-iter", type=int, default=300,
+                    help="Davidson iteration cap per two-site step of --sweep (a step that hits it is kept)")
+    ap.add_argument("--hbm-budget", type=float, default=0.0,
+                    help="device GB for renormalized operator blocks (0: unlimited); blocks beyond it "
+                         "live in pinned host memory, so only the centre's blocks stay on the device")
     ap.add_argument("--profile", action="store_true",
                     help="bracket the timed region with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     return ap.parse_args()
@@ -207,7 +212,7 @@ def run_ours(args, rank, world, local):
 
     L, N, D = args.L, args.N, args.D
     h, V = q.make_integrals(L, q.integrals.BASE_SEED + 2)
-    ctx = qd.Context(device=local)
+    ctx = qd.Context(device=local, hbm_budget_gb=args.hbm_budget)
     ctx.load_integrals(h, V)
     ctx.set_target(N, 0)
     center = L // 2 - 1
@@ -476,7 +481,7 @@ def run_sweep(args, rank, world, local):
         clocks = Clocks(local)
         clocks.start()
         t0 = time.perf_counter()
-        rep = ctx.sweep(D, allow_notconv=True, tol=1e-6, **kw)
+        rep = ctx.sweep(D, allow_notconv=True, tol=1e-6, max_iter=args.max_iter, **kw)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         rep["wall_s"] = wall

@@ -34,6 +34,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "tc_tiled.hpp"
 
 namespace qd {
@@ -141,6 +143,18 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
   for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
 __device__ __forceinline__ uint32_t bf16_bits(float x) {
   return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x));
 }
@@ -165,15 +179,19 @@ struct Stage2Args {
   double* sig;
 };
 
-// One K chunk as the MMA issuer sees it: up to MAXOPS (A, B) pairs, each its
-// own accumulator column range, over nk16 K steps; planes of a chunk follow
-// each other at astride / bstride bytes.
+// One chunk as the MMA issuer sees it: up to MAXOPS (A, B) pairs, each over
+// its own nk16 K steps into accumulator columns from tcol (stage 1: one
+// column range per view; stage 2: all ops of an item add into the same
+// columns, several short segments packed into one chunk). The planes of an
+// operand follow each other at astride / bstride bytes; zero: the op's first
+// K step overwrites the accumulator instead of adding.
 constexpr int MAXOPS = 16;
 struct Op {
   uint32_t a, b, lboa, lbob, idesc, tcol;
+  uint32_t nk16, astride, bstride, zero;
 };
 struct Meta {
-  uint32_t nops, nk16, flags, li, astride, bstride;
+  uint32_t nops, flags, li, pad;
   Op op[MAXOPS];
 };
 constexpr uint32_t F_FIRST = 1, F_LAST = 2, F_END = 4;
@@ -184,14 +202,16 @@ struct Smem {
   static constexpr uint32_t RB = 196608;      // byte ring of chunk data
   static constexpr uint32_t SLACK = 2048;     // MMA reads of padding rows past a chunk's end
   static constexpr int NR = 32;               // chunk records in flight
+  static constexpr uint32_t PACK = 32768;     // bytes of one chunk of packed stage-2 segments
   static constexpr uint32_t META = RB + SLACK;
   static constexpr uint32_t BARS = META + NR * sizeof(Meta);
-  static constexpr uint32_t SMEM = BARS + (2 * NR + 5) * 8 + 16;
+  static constexpr uint32_t VEND = BARS + (2 * NR + 5) * 8 + 16;  // ring ends of the records in flight
+  static constexpr uint32_t SMEM = VEND + NR * 8;
 };
 
 template <int MODE>
-__device__ __forceinline__ void mma_op(uint32_t tmem, const Op& o, uint32_t koff_a, uint32_t koff_b,
-                                       uint32_t astride, uint32_t bstride, bool first) {
+__device__ __forceinline__ void mma_op(uint32_t tmem, const Op& o, uint32_t koff_a, uint32_t koff_b, bool first) {
+  const uint32_t astride = o.astride, bstride = o.bstride;
   if constexpr (TCfg<MODE>::NP == 1) {
     mma_bf16(tmem, sdesc(o.a + koff_a, o.lboa, 128), sdesc(o.b + koff_b, o.lbob, 128), o.idesc, first ? 0u : 1u);
   } else {
@@ -218,7 +238,7 @@ struct RingAlloc {
   using S = Smem<MODE>;
   uint64_t vhead = 0, freed = 0;
   long long chunk = 0, oldest = 0;
-  uint64_t vend[S::NR];
+  uint64_t* vend;  // NR entries in shared memory
   // lane 0 only; false on a timeout
   __device__ bool reserve(uint32_t size, uint32_t& off, uint32_t bars, volatile int* abort_flag) {
     uint64_t vs = vhead;
@@ -280,6 +300,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tiled_gemm(Args args, int nitems,
   if (warp == 0) {
     // ---------------- producer (whole warp; lane 0 waits and signals) ----------------
     RingAlloc<MODE> ring;
+    ring.vend = reinterpret_cast<uint64_t*>(smem + S::VEND);
     bool ok = true;
     int li = 0;
     // reserve the next chunk; the outcome is shared by the warp
@@ -322,14 +343,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) tiled_gemm(Args args, int nitems,
             o.lbob = (uint32_t)it.pb8 * 128;
             o.idesc = idesc_bf16(16 * ((it.nrows + 15) / 16), 0);
             o.tcol = (uint32_t)mv.tcol;
+            o.nk16 = (uint32_t)(ck / 16);
+            o.astride = atot;
+            o.bstride = bsz;
+            o.zero = k0 == 0 ? 1u : 0u;
           }
           if (lane == 0) {
             meta[r].nops = (uint32_t)it.nv;
-            meta[r].nk16 = (uint32_t)(ck / 16);
             meta[r].flags = (k0 == 0 ? F_FIRST : 0u) | (k0 + KC >= kp ? F_LAST : 0u);
             meta[r].li = (uint32_t)li;
-            meta[r].astride = atot;
-            meta[r].bstride = bsz;
           }
           __syncwarp();
           if (lane == 0) mbar_expect_tx(full(r), NP * (atot + bsz));
@@ -352,48 +374,124 @@ __global__ void __launch_bounds__(NTHREADS, 1) tiled_gemm(Args args, int nitems,
         const K2Item it = args.items[item];
         const int pa8 = (it.mrows + 7) / 8, pb8 = (it.nrows + 7) / 8;
         const uint32_t id = idesc_bf16(16 * ((it.nrows + 15) / 16), 0);
+        bool first = true;  // no chunk of this item issued yet
         for (int sb = it.s0; sb < it.s1 && ok; sb += 32) {
-          K2Seg mg{};
-          if (sb + lane < it.s1) mg = args.segs[sb + lane];
           const int cnt = min(32, it.s1 - sb);
-          for (int j = 0; j < cnt && ok; ++j) {
+          K2Seg mg{};
+          if (lane < cnt) mg = args.segs[sb + lane];
+          // this lane's segment as one piece of a packed chunk (0: K longer
+          // than one chunk, or no segment)
+          const int mkp = tiled_c8(mg.k) * 8;
+          const uint32_t mna = (uint32_t)pa8 * (mkp / 8) * 128, mnb = (uint32_t)pb8 * (mkp / 8) * 128;
+          const uint32_t msz = (lane < cnt && mkp > 0 && mkp <= KC) ? NP * (mna + mnb) : 0u;
+          int j = 0;
+          while (j < cnt && ok) {
             const int k = __shfl_sync(0xffffffffu, mg.k, j);
-            const int64_t ga = shfl64(mg.a, j), gb = shfl64(mg.b, j);
-            const int c8 = tiled_c8(k), kp = c8 * 8;
-            const int64_t ab = ga + (int64_t)it.mp * (TP_A / 8) * c8 * 128;
-            const int64_t bb = gb + (int64_t)it.np * (TP_B / 8) * c8 * 128;
-            for (int k0 = 0; k0 < kp; k0 += KC) {
-              const int ck = min(KC, kp - k0), cc = ck / 8;
-              const uint32_t na = (uint32_t)pa8 * cc * 128, nb = (uint32_t)pb8 * cc * 128;
-              uint32_t off;
-              if (!next(NP * (na + nb), off)) { ok = false; break; }
-              if (lane == 0) {
-                const int r = (int)(ring.chunk % NR);
-                const uint32_t ca = sbase + off, cb = ca + NP * na;
-                Op& o = meta[r].op[0];
-                o.a = ca;
-                o.b = cb;
-                o.lboa = (uint32_t)pa8 * 128;
-                o.lbob = (uint32_t)pb8 * 128;
-                o.idesc = id;
-                o.tcol = 0;
-                meta[r].nops = 1;
-                meta[r].nk16 = (uint32_t)(ck / 16);
-                meta[r].flags = (sb == it.s0 && j == 0 && k0 == 0 ? F_FIRST : 0u) |
-                                (sb + j == it.s1 - 1 && k0 + KC >= kp ? F_LAST : 0u);
-                meta[r].li = (uint32_t)li;
-                meta[r].astride = na;
-                meta[r].bstride = nb;
-                mbar_expect_tx(full(r), NP * (na + nb));
-#pragma unroll
-                for (int q = 0; q < NP; ++q) {
-                  bulk_g2s(ca + q * na, args.A + q * args.aplane + ab + (int64_t)(k0 / 8) * pa8 * 128, na, full(r));
-                  bulk_g2s(cb + q * nb, args.B + q * args.bplane + bb + (int64_t)(k0 / 8) * pb8 * 128, nb, full(r));
-                }
-              }
-              ring.chunk++;
-              __syncwarp();
+            const int kp = tiled_c8(k) * 8;
+            if (kp == 0) {
+              ++j;
+              continue;
             }
+            if (kp > KC) {
+              // a long segment: chunks of KC along K, one op each
+              const int64_t ga = shfl64(mg.a, j), gb = shfl64(mg.b, j);
+              const int c8 = kp / 8;
+              const int64_t ab = ga + (int64_t)it.mp * (TP_A / 8) * c8 * 128;
+              const int64_t bb = gb + (int64_t)it.np * (TP_B / 8) * c8 * 128;
+              for (int k0 = 0; k0 < kp; k0 += KC) {
+                const int ck = min(KC, kp - k0), cc = ck / 8;
+                const uint32_t na = (uint32_t)pa8 * cc * 128, nb = (uint32_t)pb8 * cc * 128;
+                uint32_t off;
+                if (!next(NP * (na + nb), off)) { ok = false; break; }
+                if (lane == 0) {
+                  const int r = (int)(ring.chunk % NR);
+                  const uint32_t ca = sbase + off, cb = ca + NP * na;
+                  Op& o = meta[r].op[0];
+                  o.a = ca;
+                  o.b = cb;
+                  o.lboa = (uint32_t)pa8 * 128;
+                  o.lbob = (uint32_t)pb8 * 128;
+                  o.idesc = id;
+                  o.tcol = 0;
+                  o.nk16 = (uint32_t)(ck / 16);
+                  o.astride = na;
+                  o.bstride = nb;
+                  o.zero = first ? 1u : 0u;
+                  meta[r].nops = 1;
+                  meta[r].flags = (first ? F_FIRST : 0u) | (sb + j == it.s1 - 1 && k0 + KC >= kp ? F_LAST : 0u);
+                  meta[r].li = (uint32_t)li;
+                  mbar_expect_tx(full(r), NP * (na + nb));
+#pragma unroll
+                  for (int q = 0; q < NP; ++q) {
+                    bulk_g2s(ca + q * na, args.A + q * args.aplane + ab + (int64_t)(k0 / 8) * pa8 * 128, na, full(r));
+                    bulk_g2s(cb + q * nb, args.B + q * args.bplane + bb + (int64_t)(k0 / 8) * pb8 * 128, nb, full(r));
+                  }
+                }
+                first = false;
+                ring.chunk++;
+                __syncwarp();
+              }
+              ++j;
+              continue;
+            }
+            // short segments j .. j2-1 packed into one chunk, one op each,
+            // copied by their own lanes
+            int j2 = j;
+            uint32_t tot = 0;
+            while (j2 < cnt && j2 - j < MAXOPS) {
+              const uint32_t sz = __shfl_sync(0xffffffffu, msz, j2);
+              if (sz == 0 || (j2 > j && tot + sz > S::PACK)) break;
+              tot += sz;
+              ++j2;
+            }
+            const bool in = lane >= j && lane < j2;
+            const uint32_t mine = in ? msz : 0u;
+            uint32_t pre = mine;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+              const uint32_t t = __shfl_up_sync(0xffffffffu, pre, d);
+              if (lane >= d) pre += t;
+            }
+            pre -= mine;
+            uint32_t off;
+            if (!next(tot, off)) { ok = false; break; }
+            const int r = (int)(ring.chunk % NR);
+            const uint32_t ca = sbase + off + pre, cb = ca + NP * mna;
+            if (in) {
+              Op& o = meta[r].op[lane - j];
+              o.a = ca;
+              o.b = cb;
+              o.lboa = (uint32_t)pa8 * 128;
+              o.lbob = (uint32_t)pb8 * 128;
+              o.idesc = id;
+              o.tcol = 0;
+              o.nk16 = (uint32_t)(mkp / 16);
+              o.astride = mna;
+              o.bstride = mnb;
+              o.zero = (first && lane == j) ? 1u : 0u;
+            }
+            if (lane == 0) {
+              meta[r].nops = (uint32_t)(j2 - j);
+              meta[r].flags = (first ? F_FIRST : 0u) | (sb + j2 == it.s1 ? F_LAST : 0u);
+              meta[r].li = (uint32_t)li;
+            }
+            __syncwarp();
+            if (lane == 0) mbar_expect_tx(full(r), tot);
+            __syncwarp();
+            if (in) {
+              const int c8 = mkp / 8;
+              const int64_t ab = mg.a + (int64_t)it.mp * (TP_A / 8) * c8 * 128;
+              const int64_t bb = mg.b + (int64_t)it.np * (TP_B / 8) * c8 * 128;
+#pragma unroll
+              for (int q = 0; q < NP; ++q) {
+                bulk_g2s(ca + q * mna, args.A + q * args.aplane + ab, mna, full(r));
+                bulk_g2s(cb + q * mnb, args.B + q * args.bplane + bb, mnb, full(r));
+              }
+            }
+            first = false;
+            ring.chunk++;
+            __syncwarp();
+            j = j2;
           }
         }
       }
@@ -442,13 +540,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) tiled_gemm(Args args, int nitems,
         }
         tc_fence_after();
         const uint32_t tacc = tmem + (uint32_t)b * 256u;
-        const int nops = (int)m.nops, nk = (int)m.nk16;
-        for (int kk = 0; kk < nk; ++kk)
-          for (int o = 0; o < nops; ++o) {
-            const Op op = m.op[o];
-            mma_op<MODE>(tacc + op.tcol, op, kk * 2 * op.lboa, kk * 2 * op.lbob, m.astride, m.bstride,
-                         (flags & F_FIRST) && kk == 0);
-          }
+        const int nops = (int)m.nops;
+        for (int o = 0; o < nops; ++o) {
+          const Op op = m.op[o];
+          for (int kk = 0; kk < (int)op.nk16; ++kk)
+            mma_op<MODE>(tacc + op.tcol, op, kk * 2 * op.lboa, kk * 2 * op.lbob, op.zero && kk == 0);
+        }
         tc_commit(empty(r));
         if (flags & F_LAST) tc_commit(accf(b));
       }
@@ -470,6 +567,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) tiled_gemm(Args args, int nitems,
     int li = 0;
     for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++li) {
       const int b = li & 1;
+      // descriptors are fetched before the wait, so their latency overlaps it
+      // (stage 1: lane j holds view j of the item)
+      using Item = typename std::conditional<STAGE == 1, K1Item, K2Item>::type;
+      const Item it = args.items[item];
+      K1View mv{};
+      if constexpr (STAGE == 1) {
+        if (lane < it.nv) mv = args.views[it.v0 + lane];
+      }
       const bool okw = __all_sync(0xffffffffu, mbar_wait_sleep(accf(b), (uint32_t)((li >> 1) & 1), abort_flag));
       if (!okw) {
         if (lane == 0) atomicExch(err, 1);
@@ -479,42 +584,50 @@ __global__ void __launch_bounds__(NTHREADS, 1) tiled_gemm(Args args, int nitems,
       tc_fence_after();
       const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)b * 256u;
       if constexpr (STAGE == 1) {
-        const K1Item it = args.items[item];
         const int c8t = tiled_c8(it.mtot);
-        const int ngrp = (it.nrows + 7) / 8;
-        for (int v = it.v0 + half; v < it.v0 + it.nv; v += 2) {
-          const K1View w = args.views[v];
-          const bool mval = m < w.mrows;
-          const int R = w.mp * TP_A + m;        // row of T_t^T
+        const int ng16 = (it.nrows + 15) / 16;   // 16-column groups (within the view's accumulator columns)
+        for (int vi = half; vi < it.nv; vi += 2) {
+          const int64_t tout = shfl64(mv.tout, vi);
+          const float osc = (float)__shfl_sync(0xffffffffu, mv.osc, vi);
+          const int mrows = __shfl_sync(0xffffffffu, mv.mrows, vi);
+          const int tcol = __shfl_sync(0xffffffffu, mv.tcol, vi);
+          const int mp = __shfl_sync(0xffffffffu, mv.mp, vi);
+          const int ntot = __shfl_sync(0xffffffffu, mv.ntot, vi);
+          const bool mval = m < mrows;
+          const int R = mp * TP_A + m;          // row of T_t^T
           const int pr = R / TP_B;
-          const int pr8 = (min(TP_B, w.ntot - pr * TP_B) + 7) / 8;
-          uint8_t* rowp = args.T + w.tout + (int64_t)pr * (TP_B / 8) * c8t * 128 + ((R % TP_B) / 8) * 128 + (R % 8) * 16;
-          const float osc = (float)w.osc;
-          for (int g = 0; g < ngrp; ++g) {
-            float x[8];
-            tmem_ld8(trow + (uint32_t)(w.tcol + 8 * g), x);
+          const int pr8 = (min(TP_B, ntot - pr * TP_B) + 7) / 8;
+          uint8_t* rowp = args.T + tout + (int64_t)pr * (TP_B / 8) * c8t * 128 + ((R % TP_B) / 8) * 128 + (R % 8) * 16;
+          for (int g2 = 0; g2 < ng16; ++g2) {
+            float x[16];
+            tmem_ld16(trow + (uint32_t)(tcol + 16 * g2), x);
             if (mval) {
-              const int jc = (it.np * TP_B) / 8 + g;   // 16-byte K unit of T_t^T
 #pragma unroll
-              for (int j = 0; j < 8; ++j) x[j] = (8 * g + j < it.nrows) ? osc * x[j] : 0.f;
+              for (int h = 0; h < 2; ++h) {
+                const int g = 2 * g2 + h;
+                if (8 * g >= it.nrows) break;
+                float* y = x + 8 * h;
+                const int jc = (it.np * TP_B) / 8 + g;   // 16-byte K unit of T_t^T
 #pragma unroll
-              for (int q = 0; q < NP; ++q) {
-                uint32_t p[4];
+                for (int j = 0; j < 8; ++j) y[j] = (8 * g + j < it.nrows) ? osc * y[j] : 0.f;
 #pragma unroll
-                for (int j = 0; j < 8; j += 2) {
-                  const uint32_t h0 = bf16_bits(x[j]), h1 = bf16_bits(x[j + 1]);
-                  p[j >> 1] = h0 | (h1 << 16);
-                  x[j] -= __uint_as_float(h0 << 16);
-                  x[j + 1] -= __uint_as_float(h1 << 16);
+                for (int q = 0; q < NP; ++q) {
+                  uint32_t p[4];
+#pragma unroll
+                  for (int j = 0; j < 8; j += 2) {
+                    const uint32_t h0 = bf16_bits(y[j]), h1 = bf16_bits(y[j + 1]);
+                    p[j >> 1] = h0 | (h1 << 16);
+                    y[j] -= __uint_as_float(h0 << 16);
+                    y[j + 1] -= __uint_as_float(h1 << 16);
+                  }
+                  *reinterpret_cast<uint4*>(rowp + q * args.tplane + (int64_t)jc * pr8 * 128) =
+                      make_uint4(p[0], p[1], p[2], p[3]);
                 }
-                *reinterpret_cast<uint4*>(rowp + q * args.tplane + (int64_t)jc * pr8 * 128) =
-                    make_uint4(p[0], p[1], p[2], p[3]);
               }
             }
           }
         }
       } else {
-        const K2Item it = args.items[item];
         const bool mval = m < it.mrows;
         double* row = args.sig + it.out + (int64_t)(it.mp * TP_A + m) * it.ldc + it.np * TP_B;
         const int ngrp = (it.nrows + 7) / 8;

@@ -58,6 +58,9 @@ TiledPlan plan_tiled(const HeffPlan& plan, const PsiLayout& lay, const TileCfg& 
   std::vector<int64_t> psi_off(lay.blks.size());
   for (size_t i = 0; i < lay.blks.size(); ++i) {
     const auto& b = lay.blks[i];
+    // every work item of the kernels needs at least one K step: an empty
+    // block would leave an accumulator that no MMA completes
+    if (b.rows <= 0 || b.cols <= 0) throw std::runtime_error("tiled plan: empty psi block");
     blk_of_off[b.off] = (int)i;
     psi_off[i] = psi.add((uint64_t)b.off, 1, b.cols, 0, b.rows, b.cols, 1.0);
   }
@@ -126,6 +129,7 @@ TiledPlan plan_tiled(const HeffPlan& plan, const PsiLayout& lay, const TileCfg& 
         // the left reference scalar (sign included) is folded into its view
         const int64_t a = (g.a == 0 && g.abuf == B_ABS) ? am.add(0, 0, 0, 0, p.m, g.k, g.asc)
                                                          : am.add(g.a, 0, g.lda, g.ta, p.m, g.k, g.asc);
+        if (g.k <= 0) throw std::runtime_error("tiled plan: stage-2 segment without K");
         sig[si].segs.push_back({a, tps[tp].tout, g.k, 0});
       }
     }
@@ -193,6 +197,7 @@ TiledPlan plan_tiled(const HeffPlan& plan, const PsiLayout& lay, const TileCfg& 
   // stage 2: sigma blocks, segment ranges of summed K <= kmax, costliest first
   std::vector<std::pair<double, K2Item>> items;
   for (const SigBlk& sb : sig) {
+    if (sb.segs.empty()) continue;
     std::vector<std::pair<int, int>> ranges;
     int s0 = (int)P.s2.size(), ks = 0;
     for (const K2Seg& g : sb.segs) {
