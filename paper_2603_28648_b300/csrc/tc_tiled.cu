@@ -184,17 +184,24 @@ struct Stage2Args {
 // column range per view; stage 2: all ops of an item add into the same
 // columns, several short segments packed into one chunk). The planes of an
 // operand follow each other at astride / bstride bytes; zero: the op's first
-// K step overwrites the accumulator instead of adding.
+// K step overwrites the accumulator instead of adding. The producer stores
+// ready shared-memory descriptors and their increments (16-byte units) per
+// K step and per plane, so that the issuing thread only adds and issues.
 constexpr int MAXOPS = 16;
 struct Op {
-  uint32_t a, b, lboa, lbob, idesc, tcol;
-  uint32_t nk16, astride, bstride, zero;
+  uint64_t da, db;          // descriptors of the first K step, plane 0
+  uint32_t idesc, tcol, nk16, zero;
+  uint32_t ka, kb;          // descriptor increment per K step
+  uint32_t pa, pb;          // descriptor increment per plane
 };
 struct Meta {
   uint32_t nops, flags, li, pad;
   Op op[MAXOPS];
 };
-constexpr uint32_t F_FIRST = 1, F_LAST = 2, F_END = 4;
+// F_COMMIT: the MMA issuer commits the chunk's record to its empty barrier
+// (every 4th chunk and every record without data; one commit releases the
+// ring bytes of all chunks before it)
+constexpr uint32_t F_FIRST = 1, F_LAST = 2, F_END = 4, F_COMMIT = 8;
 
 template <int MODE>
 struct Smem {
@@ -206,21 +213,36 @@ struct Smem {
   static constexpr uint32_t META = RB + SLACK;
   static constexpr uint32_t BARS = META + NR * sizeof(Meta);
   static constexpr uint32_t VEND = BARS + (2 * NR + 5) * 8 + 16;  // ring ends of the records in flight
-  static constexpr uint32_t SMEM = VEND + NR * 8;
+  static constexpr uint32_t ECNT = VEND + NR * 8;                  // commits consumed per record
+  static constexpr uint32_t VCM = ECNT + NR * 4;                   // record holds a commit point
+  static constexpr uint32_t SMEM = VCM + NR;
 };
 
+__device__ __forceinline__ void set_op(Op& o, uint32_t a, uint32_t b, uint32_t lboa, uint32_t lbob, uint32_t idesc,
+                                       uint32_t tcol, uint32_t nk16, uint32_t astride, uint32_t bstride, uint32_t zero) {
+  o.da = sdesc(a, lboa, 128);
+  o.db = sdesc(b, lbob, 128);
+  o.idesc = idesc;
+  o.tcol = tcol;
+  o.nk16 = nk16;
+  o.zero = zero;
+  o.ka = (2 * lboa) >> 4;
+  o.kb = (2 * lbob) >> 4;
+  o.pa = astride >> 4;
+  o.pb = bstride >> 4;
+}
+
+// one K step of an op (all planes of the split form)
 template <int MODE>
-__device__ __forceinline__ void mma_op(uint32_t tmem, const Op& o, uint32_t koff_a, uint32_t koff_b, bool first) {
-  const uint32_t astride = o.astride, bstride = o.bstride;
+__device__ __forceinline__ void mma_step(uint32_t tmem, uint64_t da, uint64_t db, const Op& o, bool first) {
   if constexpr (TCfg<MODE>::NP == 1) {
-    mma_bf16(tmem, sdesc(o.a + koff_a, o.lboa, 128), sdesc(o.b + koff_b, o.lbob, 128), o.idesc, first ? 0u : 1u);
+    mma_bf16(tmem, da, db, o.idesc, first ? 0u : 1u);
   } else {
-    const int pi[6] = {2, 1, 0, 1, 0, 0};
-    const int pj[6] = {0, 1, 2, 0, 1, 0};
+    const uint32_t pi[6] = {2, 1, 0, 1, 0, 0};
+    const uint32_t pj[6] = {0, 1, 2, 0, 1, 0};
 #pragma unroll
     for (int q = 0; q < 6; ++q)
-      mma_bf16(tmem, sdesc(o.a + pi[q] * astride + koff_a, o.lboa, 128),
-               sdesc(o.b + pj[q] * bstride + koff_b, o.lbob, 128), o.idesc, (first && q == 0) ? 0u : 1u);
+      mma_bf16(tmem, da + pi[q] * o.pa, db + pj[q] * o.pb, o.idesc, (first && q == 0) ? 0u : 1u);
   }
 }
 
@@ -233,24 +255,47 @@ __device__ __forceinline__ int64_t shfl64(int64_t v, int src) {
 // Producer-side byte ring: chunk c takes [vs, vs + size) of a virtual byte
 // stream (never wrapping inside the ring) and record c % NR; both are reused
 // once the MMAs of the chunks before it have completed (freed in order).
+// Completion is known at commit points only (every 4th chunk); when the
+// producer must wait and none of its chunks in flight is a commit point, it
+// inserts a record without data that only commits.
 template <int MODE>
 struct RingAlloc {
   using S = Smem<MODE>;
   uint64_t vhead = 0, freed = 0;
   long long chunk = 0, oldest = 0;
-  uint64_t* vend;  // NR entries in shared memory
+  uint64_t* vend;   // NR entries in shared memory
+  uint32_t* ecnt;   // commits consumed per record
+  uint8_t* vcm;     // record's chunk is a commit point
+  static __device__ __forceinline__ bool commit_point(long long c) { return (c & 3) == 3; }
   // lane 0 only; false on a timeout
-  __device__ bool reserve(uint32_t size, uint32_t& off, uint32_t bars, volatile int* abort_flag) {
+  __device__ bool reserve(uint32_t size, uint32_t& off, uint32_t bars, volatile int* abort_flag, Meta* meta,
+                          uint32_t li) {
     uint64_t vs = vhead;
     if ((vs % S::RB) + size > S::RB) vs = (vs / S::RB + 1) * S::RB;
     const uint64_t ve = vs + size;
     while (oldest < chunk && (oldest <= chunk - S::NR || ve > freed + S::RB)) {
-      const int r = (int)(oldest % S::NR);
-      if (!mbar_wait(bars + 8u * (S::NR + r), (uint32_t)((oldest / S::NR) & 1), abort_flag)) return false;
+      long long c = oldest;
+      while (c < chunk && !vcm[c % S::NR]) ++c;
+      if (c == chunk) {
+        // fewer than 4 chunks in flight and none commits: a commit-only record
+        const int r = (int)(chunk % S::NR);
+        meta[r].nops = 0;
+        meta[r].flags = F_COMMIT;
+        meta[r].li = li;
+        vend[r] = vhead;
+        vcm[r] = 1;
+        mbar_arrive(bars + 8u * r);
+        ++chunk;
+        continue;
+      }
+      const int r = (int)(c % S::NR);
+      if (!mbar_wait(bars + 8u * (S::NR + r), ecnt[r] & 1u, abort_flag)) return false;
+      ++ecnt[r];
       freed = vend[r];
-      ++oldest;
+      oldest = c + 1;
     }
     vend[chunk % S::NR] = ve;
+    vcm[chunk % S::NR] = commit_point(chunk) ? 1 : 0;
     vhead = ve;
     off = (uint32_t)(vs % S::RB);
     return true;
@@ -301,15 +346,20 @@ __global__ void __launch_bounds__(NTHREADS, 1) tiled_gemm(Args args, int nitems,
     // ---------------- producer (whole warp; lane 0 waits and signals) ----------------
     RingAlloc<MODE> ring;
     ring.vend = reinterpret_cast<uint64_t*>(smem + S::VEND);
+    ring.ecnt = reinterpret_cast<uint32_t*>(smem + S::ECNT);
+    ring.vcm = smem + S::VCM;
+    if (lane < NR) ring.ecnt[lane] = 0;
+    __syncwarp();
     bool ok = true;
     int li = 0;
     // reserve the next chunk; the outcome is shared by the warp
     auto next = [&](uint32_t size, uint32_t& off) -> bool {
       int good = 1;
       uint32_t o = 0;
-      if (lane == 0) good = ring.reserve(size, o, bars, abort_flag) ? 1 : 0;
+      if (lane == 0) good = ring.reserve(size, o, bars, abort_flag, meta, (uint32_t)li) ? 1 : 0;
       good = __shfl_sync(0xffffffffu, good, 0);
       off = __shfl_sync(0xffffffffu, o, 0);
+      ring.chunk = shfl64(ring.chunk, 0);  // lane 0 may have inserted commit-only records
       return good != 0;
     };
     for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x, ++li) {
@@ -337,20 +387,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) tiled_gemm(Args args, int nitems,
           const uint32_t ca = sbase + off, cb = ca + NP * atot;
           if (lane < it.nv) {
             Op& o = meta[r].op[lane];
-            o.a = ca + pre;
-            o.b = cb;
-            o.lboa = (uint32_t)mv.pa8 * 128;
-            o.lbob = (uint32_t)it.pb8 * 128;
-            o.idesc = idesc_bf16(16 * ((it.nrows + 15) / 16), 0);
-            o.tcol = (uint32_t)mv.tcol;
-            o.nk16 = (uint32_t)(ck / 16);
-            o.astride = atot;
-            o.bstride = bsz;
-            o.zero = k0 == 0 ? 1u : 0u;
+            set_op(o, ca + pre, cb, (uint32_t)mv.pa8 * 128, (uint32_t)it.pb8 * 128,
+                   idesc_bf16(16 * ((it.nrows + 15) / 16), 0), (uint32_t)mv.tcol, (uint32_t)(ck / 16), atot, bsz,
+                   k0 == 0 ? 1u : 0u);
           }
           if (lane == 0) {
             meta[r].nops = (uint32_t)it.nv;
-            meta[r].flags = (k0 == 0 ? F_FIRST : 0u) | (k0 + KC >= kp ? F_LAST : 0u);
+            meta[r].flags = (k0 == 0 ? F_FIRST : 0u) | (k0 + KC >= kp ? F_LAST : 0u) |
+                            (RingAlloc<MODE>::commit_point(ring.chunk) ? F_COMMIT : 0u);
             meta[r].li = (uint32_t)li;
           }
           __syncwarp();
@@ -362,10 +406,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) tiled_gemm(Args args, int nitems,
               bulk_g2s(ca + q * atot + pre, args.A + q * args.aplane + mv.a + (int64_t)(k0 / 8) * mv.pa8 * 128, mine,
                        full(r));
           }
-          if (lane == 0) {
-#pragma unroll
-            for (int q = 0; q < NP; ++q)
-              bulk_g2s(cb + q * bsz, args.B + q * args.bplane + it.b + (int64_t)(k0 / 8) * it.pb8 * 128, bsz, full(r));
+          // the psi panel's planes by lanes 16.. (views use lanes < 16), so that
+          // the copies issue in parallel
+          if (lane >= 16 && lane < 16 + NP) {
+            const int q = lane - 16;
+            bulk_g2s(cb + q * bsz, args.B + q * args.bplane + it.b + (int64_t)(k0 / 8) * it.pb8 * 128, bsz, full(r));
           }
           ring.chunk++;
           __syncwarp();
@@ -384,6 +429,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) tiled_gemm(Args args, int nitems,
           const int mkp = tiled_c8(mg.k) * 8;
           const uint32_t mna = (uint32_t)pa8 * (mkp / 8) * 128, mnb = (uint32_t)pb8 * (mkp / 8) * 128;
           const uint32_t msz = (lane < cnt && mkp > 0 && mkp <= KC) ? NP * (mna + mnb) : 0u;
+          // inclusive prefix sum of the piece sizes over the lanes
+          uint32_t cum = msz;
+#pragma unroll
+          for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, cum, d);
+            if (lane >= d) cum += t;
+          }
           int j = 0;
           while (j < cnt && ok) {
             const int k = __shfl_sync(0xffffffffu, mg.k, j);
@@ -403,29 +455,28 @@ __global__ void __launch_bounds__(NTHREADS, 1) tiled_gemm(Args args, int nitems,
                 const uint32_t na = (uint32_t)pa8 * cc * 128, nb = (uint32_t)pb8 * cc * 128;
                 uint32_t off;
                 if (!next(NP * (na + nb), off)) { ok = false; break; }
+                const int r0 = (int)(ring.chunk % NR);
                 if (lane == 0) {
-                  const int r = (int)(ring.chunk % NR);
+                  const int r = r0;
                   const uint32_t ca = sbase + off, cb = ca + NP * na;
                   Op& o = meta[r].op[0];
-                  o.a = ca;
-                  o.b = cb;
-                  o.lboa = (uint32_t)pa8 * 128;
-                  o.lbob = (uint32_t)pb8 * 128;
-                  o.idesc = id;
-                  o.tcol = 0;
-                  o.nk16 = (uint32_t)(ck / 16);
-                  o.astride = na;
-                  o.bstride = nb;
-                  o.zero = first ? 1u : 0u;
+                  set_op(o, ca, cb, (uint32_t)pa8 * 128, (uint32_t)pb8 * 128, id, 0u, (uint32_t)(ck / 16), na, nb,
+                         first ? 1u : 0u);
                   meta[r].nops = 1;
-                  meta[r].flags = (first ? F_FIRST : 0u) | (sb + j == it.s1 - 1 && k0 + KC >= kp ? F_LAST : 0u);
+                  meta[r].flags = (first ? F_FIRST : 0u) | (sb + j == it.s1 - 1 && k0 + KC >= kp ? F_LAST : 0u) |
+                                  (RingAlloc<MODE>::commit_point(ring.chunk) ? F_COMMIT : 0u);
                   meta[r].li = (uint32_t)li;
                   mbar_expect_tx(full(r), NP * (na + nb));
-#pragma unroll
-                  for (int q = 0; q < NP; ++q) {
-                    bulk_g2s(ca + q * na, args.A + q * args.aplane + ab + (int64_t)(k0 / 8) * pa8 * 128, na, full(r));
-                    bulk_g2s(cb + q * nb, args.B + q * args.bplane + bb + (int64_t)(k0 / 8) * pb8 * 128, nb, full(r));
-                  }
+                }
+                __syncwarp();
+                // plane q of A by lane q, of B by lane NP + q
+                if (lane < 2 * NP) {
+                  const int q = lane % NP;
+                  const uint32_t ca = sbase + off, cb = ca + NP * na;
+                  if (lane < NP)
+                    bulk_g2s(ca + q * na, args.A + q * args.aplane + ab + (int64_t)(k0 / 8) * pa8 * 128, na, full(r0));
+                  else
+                    bulk_g2s(cb + q * nb, args.B + q * args.bplane + bb + (int64_t)(k0 / 8) * pb8 * 128, nb, full(r0));
                 }
                 first = false;
                 ring.chunk++;
@@ -434,58 +485,51 @@ __global__ void __launch_bounds__(NTHREADS, 1) tiled_gemm(Args args, int nitems,
               ++j;
               continue;
             }
-            // short segments j .. j2-1 packed into one chunk, one op each,
-            // copied by their own lanes
-            int j2 = j;
-            uint32_t tot = 0;
-            while (j2 < cnt && j2 - j < MAXOPS) {
-              const uint32_t sz = __shfl_sync(0xffffffffu, msz, j2);
-              if (sz == 0 || (j2 > j && tot + sz > S::PACK)) break;
-              tot += sz;
-              ++j2;
-            }
+            // short segments j .. j2-1 packed into one chunk, one op each: the
+            // group ends before the first lane whose piece is not short, would
+            // overflow PACK bytes, or is the (MAXOPS+1)-th
+            const uint32_t base = __shfl_sync(0xffffffffu, cum - msz, j);
+            const unsigned stop = __ballot_sync(0xffffffffu, lane > j && (msz == 0 || cum - base > S::PACK ||
+                                                                         lane - j >= MAXOPS));
+            const int j2 = min(cnt, stop ? __ffs(stop) - 1 : 32);
+            const uint32_t tot = __shfl_sync(0xffffffffu, cum, j2 - 1) - base;
             const bool in = lane >= j && lane < j2;
-            const uint32_t mine = in ? msz : 0u;
-            uint32_t pre = mine;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-              const uint32_t t = __shfl_up_sync(0xffffffffu, pre, d);
-              if (lane >= d) pre += t;
-            }
-            pre -= mine;
             uint32_t off;
             if (!next(tot, off)) { ok = false; break; }
             const int r = (int)(ring.chunk % NR);
-            const uint32_t ca = sbase + off + pre, cb = ca + NP * mna;
+            const uint32_t ca = sbase + off + (cum - msz - base), cb = ca + NP * mna;
             if (in) {
               Op& o = meta[r].op[lane - j];
-              o.a = ca;
-              o.b = cb;
-              o.lboa = (uint32_t)pa8 * 128;
-              o.lbob = (uint32_t)pb8 * 128;
-              o.idesc = id;
-              o.tcol = 0;
-              o.nk16 = (uint32_t)(mkp / 16);
-              o.astride = mna;
-              o.bstride = mnb;
-              o.zero = (first && lane == j) ? 1u : 0u;
+              set_op(o, ca, cb, (uint32_t)pa8 * 128, (uint32_t)pb8 * 128, id, 0u, (uint32_t)(mkp / 16), mna, mnb,
+                     (first && lane == j) ? 1u : 0u);
             }
             if (lane == 0) {
               meta[r].nops = (uint32_t)(j2 - j);
-              meta[r].flags = (first ? F_FIRST : 0u) | (sb + j2 == it.s1 ? F_LAST : 0u);
+              meta[r].flags = (first ? F_FIRST : 0u) | (sb + j2 == it.s1 ? F_LAST : 0u) |
+                              (RingAlloc<MODE>::commit_point(ring.chunk) ? F_COMMIT : 0u);
               meta[r].li = (uint32_t)li;
             }
             __syncwarp();
             if (lane == 0) mbar_expect_tx(full(r), tot);
             __syncwarp();
-            if (in) {
+            {
+              // A pieces by their own lanes, B pieces by the partner lane
+              // (lane ^ 16: a group spans at most 16 lanes, so no lane issues
+              // both), so that every lane issues at most one piece
               const int c8 = mkp / 8;
               const int64_t ab = mg.a + (int64_t)it.mp * (TP_A / 8) * c8 * 128;
               const int64_t bb = mg.b + (int64_t)it.np * (TP_B / 8) * c8 * 128;
+              const int64_t pbb = shfl64(bb, lane ^ 16);
+              const uint32_t pcb = __shfl_sync(0xffffffffu, cb, lane ^ 16);
+              const uint32_t pnb = __shfl_sync(0xffffffffu, mnb, lane ^ 16);
+              const bool pin = __shfl_sync(0xffffffffu, in ? 1 : 0, lane ^ 16) != 0;
+              if (in) {
 #pragma unroll
-              for (int q = 0; q < NP; ++q) {
-                bulk_g2s(ca + q * mna, args.A + q * args.aplane + ab, mna, full(r));
-                bulk_g2s(cb + q * mnb, args.B + q * args.bplane + bb, mnb, full(r));
+                for (int q = 0; q < NP; ++q) bulk_g2s(ca + q * mna, args.A + q * args.aplane + ab, mna, full(r));
+              }
+              if (pin) {
+#pragma unroll
+                for (int q = 0; q < NP; ++q) bulk_g2s(pcb + q * pnb, args.B + q * args.bplane + pbb, pnb, full(r));
               }
             }
             first = false;
@@ -525,30 +569,47 @@ __global__ void __launch_bounds__(NTHREADS, 1) tiled_gemm(Args args, int nitems,
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
-    if (lane == 0) {
-      bool ok = true;
-      for (long long c = 0;; ++c) {
-        const int r = (int)(c % NR);
-        if (!mbar_wait(full(r), (uint32_t)((c / NR) & 1), abort_flag)) { ok = false; break; }
-        const Meta& m = meta[r];
-        const uint32_t flags = m.flags;
-        if (flags & F_END) break;
-        const int li = (int)m.li, b = li & 1;
-        if ((flags & F_FIRST) && li >= 2 && !mbar_wait(acce(b), (uint32_t)(((li >> 1) - 1) & 1), abort_flag)) {
-          ok = false;
-          break;
-        }
-        tc_fence_after();
+    // The whole warp runs the loop and lane 0 issues: a tcgen05.mma issues in
+    // about half the time when the warp-mates of the issuing lane wait at a
+    // nearby __syncwarp rather than at the CTA barrier. Every lane waits on
+    // the barriers itself (its own acquire of the chunk record), and the warp
+    // agrees on the outcome.
+    bool ok = true;
+    for (long long c = 0;; ++c) {
+      const int r = (int)(c % NR);
+      if (!__all_sync(0xffffffffu, mbar_wait(full(r), (uint32_t)((c / NR) & 1), abort_flag))) {
+        ok = false;
+        break;
+      }
+      const uint32_t flags = meta[r].flags;
+      if (flags & F_END) break;
+      const int li = (int)meta[r].li, b = li & 1;
+      if ((flags & F_FIRST) && li >= 2 &&
+          !__all_sync(0xffffffffu, mbar_wait(acce(b), (uint32_t)(((li >> 1) - 1) & 1), abort_flag))) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      // lane 0 issues the chunk's MMAs back to back (no warp barrier between
+      // them); the warp meets again after the commits
+      if (lane == 0) {
         const uint32_t tacc = tmem + (uint32_t)b * 256u;
-        const int nops = (int)m.nops;
+        const int nops = (int)meta[r].nops;
         for (int o = 0; o < nops; ++o) {
-          const Op op = m.op[o];
-          for (int kk = 0; kk < (int)op.nk16; ++kk)
-            mma_op<MODE>(tacc + op.tcol, op, kk * 2 * op.lboa, kk * 2 * op.lbob, op.zero && kk == 0);
+          const Op op = meta[r].op[o];
+          uint64_t da = op.da, db = op.db;
+          for (int kk = 0; kk < (int)op.nk16; ++kk) {
+            mma_step<MODE>(tacc + op.tcol, da, db, op, op.zero && kk == 0);
+            da += op.ka;
+            db += op.kb;
+          }
         }
-        tc_commit(empty(r));
+        if (flags & F_COMMIT) tc_commit(empty(r));
         if (flags & F_LAST) tc_commit(accf(b));
       }
+      __syncwarp();
+    }
+    if (lane == 0) {
       if (!ok) {
         atomicExch(err, 1);
         *abort_flag = 1;
@@ -559,6 +620,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tiled_gemm(Args args, int nitems,
       while (!mbar_try(drain, 0) && clock64() - t0 < WAIT_CYCLES) {
       }
     }
+    __syncwarp();
   } else {
     // ---------------- epilogue (warps 2 .. 2 + NEPI - 1) ----------------
     const int quarter = warp & 3;            // tensor-memory lanes this warp may read
