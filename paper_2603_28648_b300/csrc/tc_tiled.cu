@@ -362,11 +362,36 @@ __global__ void __launch_bounds__(NTHREADS, 1) tiled_gemm(Args args, int nitems,
       ring.chunk = shfl64(ring.chunk, 0);  // lane 0 may have inserted commit-only records
       return good != 0;
     };
-    for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x, ++li) {
+    // Descriptor prefetch: work-item descriptors two items ahead, the views
+    // (stage 1) or the first 32 segments (stage 2) of the next item one item
+    // ahead, so that no item starts with two dependent global loads.
+    using Item = typename std::conditional<STAGE == 1, K1Item, K2Item>::type;
+    using Sub = typename std::conditional<STAGE == 1, K1View, K2Seg>::type;
+    auto load_item = [&](int i) {
+      Item x{};
+      if (i < nitems) x = args.items[i];
+      return x;
+    };
+    auto load_sub = [&](const Item& x) {
+      Sub y{};
       if constexpr (STAGE == 1) {
-        const K1Item it = args.items[item];
-        K1View mv{};
-        if (lane < it.nv) mv = args.views[it.v0 + lane];
+        if (lane < x.nv) y = args.views[x.v0 + lane];
+      } else {
+        if (lane < x.s1 - x.s0) y = args.segs[x.s0 + lane];
+      }
+      return y;
+    };
+    Item it_n = load_item(blockIdx.x);
+    Sub sub_n = load_sub(it_n);
+    Item it_n2 = load_item(blockIdx.x + gridDim.x);
+    for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x, ++li) {
+      const Item it = it_n;
+      const Sub sub0 = sub_n;
+      it_n = it_n2;
+      sub_n = load_sub(it_n);
+      it_n2 = load_item(item + 2 * gridDim.x);
+      if constexpr (STAGE == 1) {
+        const K1View mv = sub0;
         const int kp = tiled_c8(it.k) * 8;
         for (int k0 = 0; k0 < kp && ok; k0 += KC) {
           const int ck = min(KC, kp - k0), cc = ck / 8;
@@ -416,14 +441,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) tiled_gemm(Args args, int nitems,
           __syncwarp();
         }
       } else {
-        const K2Item it = args.items[item];
         const int pa8 = (it.mrows + 7) / 8, pb8 = (it.nrows + 7) / 8;
         const uint32_t id = idesc_bf16(16 * ((it.nrows + 15) / 16), 0);
         bool first = true;  // no chunk of this item issued yet
+        K2Seg mg_n = sub0;  // segments of the next batch (loaded one batch ahead)
         for (int sb = it.s0; sb < it.s1 && ok; sb += 32) {
           const int cnt = min(32, it.s1 - sb);
-          K2Seg mg{};
-          if (lane < cnt) mg = args.segs[sb + lane];
+          const K2Seg mg = mg_n;
+          mg_n = K2Seg{};
+          if (sb + 32 + lane < it.s1) mg_n = args.segs[sb + 32 + lane];
           // this lane's segment as one piece of a packed chunk (0: K longer
           // than one chunk, or no segment)
           const int mkp = tiled_c8(mg.k) * 8;
