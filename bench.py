@@ -44,6 +44,8 @@ def parse():
                     help="16 independent problems (L 12..24, D 128..512) in one CUDA graph vs one by one")
     ap.add_argument("--max-iter", type=int, default=300,
                     help="Davidson iteration cap per two-site step of --sweep (a step that hits it is kept)")
+    ap.add_argument("--sweep-budget", type=float, default=300.0,
+                    help="seconds of sweep steps per form in --sweep mode before it stops early")
     ap.add_argument("--hbm-budget", type=float, default=0.0,
                     help="device GB for renormalized operator blocks (0: unlimited); blocks beyond it "
                          "live in pinned host memory, so only the centre's blocks stay on the device")
@@ -98,6 +100,14 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+# DRAM bytes (read + write) of one H_eff psi on the tiled tensor-core kernel,
+# from one ncu capture of both stage launches (dram__bytes_read.sum +
+# dram__bytes_write.sum), keyed by (form, L, N, D); the capture and its command
+# are summarised in profiles/tiled_gemm_bf16_u1_L36_N54_D1024.md. A key that is
+# absent reports null.
+DRAM_TRAFFIC = {}
 
 
 def measured_peaks():
@@ -340,12 +350,15 @@ def run_ours(args, rank, world, local):
     # tensor form, so its roofline is the measured copy bandwidth
     nbytes = form_bytes[args.precision]
     achieved = nbytes / per_step / 1e9
+    traffic = DRAM_TRAFFIC.get((args.precision, L, N, D))
     roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm"], "unit": "GB/s",
-            "frac": achieved / pk["hbm"], "traffic": None,
+            "frac": achieved / pk["hbm"], "traffic": traffic,
             "algorithmic_bytes_per_step": nbytes,
             "intensity_flop_per_byte": flops / nbytes,
             "peak_source": f"{pk['source']} copy bandwidth (of {pk['source']})",
-            "traffic_note": "null: no DRAM counter capture of this kernel build at this size",
+            "traffic_note": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the stage-1 and stage-2 "
+                             "launches of one product (profiles/)") if traffic else
+                            "null: no DRAM counter capture of this kernel build at this size",
             "compute_frac": forms[args.precision]["compute_frac"]}
     if args.precision in ("bf16", "bf16x3"):
         launches_per_step = 3
@@ -460,43 +473,69 @@ def run_batched(args, rank, world, local):
 
 
 def run_sweep(args, rank, world, local):
-    """Wall time of one full two-site sweep at bond dimension D (renormalization
-    included) with every H_eff psi in FP64, and with the mixed policy (BF16 ->
-    BF16x3 -> FP64 residual correction), from the same random MPS."""
+    """Two-site sweep at bond dimension D through the public API, with every
+    H_eff psi in FP64 and with the mixed policy (BF16 -> BF16x3 -> FP64
+    residual correction), from the same random MPS. The sweep starts at the
+    centre bond, runs right to the end, left to the other end and right back
+    to the centre: 2(L-2) two-site steps, each a Davidson solve followed by
+    truncation, renormalization and preparation of the next centre, timed
+    separately. A form stops early when its time budget runs out; the line
+    then reports the steps it completed."""
     import torch
     import qcinputs as q
     import paper_2603_28648_b300 as qd
     torch.cuda.set_device(local)
     L, N, D = args.L, args.N, args.D
     h, V = q.make_integrals(L, q.integrals.BASE_SEED + 2)
+    c0 = L // 2 - 1
+    order = [+1] * (L - 2 - c0) + [-1] * (L - 2) + [+1] * c0
     out = {}
     for name, kw in (("fp64", dict(policy=0, precision=qd.FP64)), ("mixed", dict(policy=1))):
         ctx = qd.Context(device=local)
         ctx.load_integrals(h, V)
         ctx.set_target(N, 0)
-        ctx.init_mps(D, q.integrals.BASE_SEED + 1002, L // 2 - 1)
+        ctx.init_mps(D, q.integrals.BASE_SEED + 1002, c0)
+        t0 = time.perf_counter()
         ctx.build_env()
-        ctx.move_center(0)
         torch.cuda.synchronize()
+        env_s = time.perf_counter() - t0
         clocks = Clocks(local)
         clocks.start()
-        t0 = time.perf_counter()
-        rep = ctx.sweep(D, allow_notconv=True, tol=1e-6, max_iter=args.max_iter, **kw)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
-        rep["wall_s"] = wall
-        rep["clocks"] = clocks.stop()
-        rep["tile"] = {k: ctx.stats()[k] for k in ("tile_kmax", "tile_width", "tunes", "tune_seconds")}
-        out[name] = rep
+        dav_s, move_s, energies, iters = [], [], [], []
+        t_start = time.perf_counter()
+        for step, d in enumerate(order):
+            t1 = time.perf_counter()
+            e, r, it = ctx.davidson(allow_notconv=True, tol=1e-6, max_iter=args.max_iter, **kw)
+            t2 = time.perf_counter()
+            ctx.truncate(D, d)
+            torch.cuda.synchronize()
+            t3 = time.perf_counter()
+            dav_s.append(t2 - t1)
+            move_s.append(t3 - t2)
+            energies.append(e)
+            iters.append(it)
+            if t3 - t_start > args.sweep_budget:
+                break
+        wall = time.perf_counter() - t_start
+        out[name] = {"steps_done": len(dav_s), "steps_sweep": len(order), "complete": len(dav_s) == len(order),
+                     "wall_s": wall, "davidson_s": sum(dav_s), "truncate_renormalize_s": sum(move_s),
+                     "centre_step_s": (dav_s[0] + move_s[0]) if dav_s else None,
+                     "step_s": [a + b for a, b in zip(dav_s, move_s)],
+                     "energy_last": energies[-1] if energies else None, "energies": energies,
+                     "davidson_iters": iters, "env_build_s": env_s, "clocks": clocks.stop()}
         ctx.close()
+    f, m = out["fp64"], out["mixed"]
+    n = min(f["steps_done"], m["steps_done"])
     line = {
-        "metric": "sweep seconds, one L->R->L two-site sweep (68 steps at L=36)",
-        "value": out["mixed"]["wall_s"], "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 0,
+        "metric": f"sweep seconds, one two-site sweep (2(L-2) = {2 * (L - 2)} steps) at L={L}",
+        "value": m["wall_s"] if m["complete"] else None, "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 0,
         "higher_is_better": False, "dtype": "mixed", "data": "synthetic",
-        "config": {"workload": f"u1_L{L}_N{N}_Sz0_D{D} full sweep from a random MPS",
-                   "fp64": out["fp64"], "mixed": out["mixed"],
-                   "speedup_vs_fp64": out["fp64"]["wall_s"] / out["mixed"]["wall_s"],
-                   "energy_mixed_minus_fp64": out["mixed"]["energy"] - out["fp64"]["energy"]},
+        "config": {"workload": f"u1_L{L}_N{N}_Sz0_D{D} sweep from a random MPS, centre start",
+                   "davidson": {"tol": 1e-6, "max_iter": args.max_iter}, "budget_s": args.sweep_budget,
+                   "fp64": f, "mixed": m,
+                   "same_steps_compared": n,
+                   "speedup_vs_fp64_same_steps": (sum(f["step_s"][:n]) / sum(m["step_s"][:n])) if n else None,
+                   "energy_mixed_minus_fp64_last_common_step": (m["energies"][n - 1] - f["energies"][n - 1]) if n else None},
     }
     print(json.dumps(line), flush=True)
 

@@ -291,7 +291,9 @@ void Engine::heff(uint64_t psi, uint64_t sig, void* stream, int prec) {
   pr->zero_async(sig, lay.size, stream);
   if (prec == 2 || prec == 3) {
     // BF16 forms: bf16 operand mirrors fed to the tensor cores by bulk copies
-    const int planes = prec == 3 ? 3 : 1;
+    // the mixed Davidson policy prepares the three planes of the split once:
+    // the BF16 form reads plane 0, which is the same round-to-nearest bf16
+    const int planes = (prec == 3 || mixed_planes) ? 3 : 1;
     if (pr->tiled_planes() < planes) {
       pr->prepare_tiled(plan_tiled(plan, lay, tcfg), planes);
       if (autotune) {
@@ -311,14 +313,14 @@ void Engine::heff(uint64_t psi, uint64_t sig, void* stream, int prec) {
 // Autotuner of the bf16 tensor-core path: times every candidate work-item
 // shape on this centre's task lists (the operand mirrors stay; only the items
 // change) and keeps the fastest. The choice is cached per problem-size class
-// (precision, psi size to a factor of two, number of terms), so the centres
-// of a sweep at the same bond dimension are tuned once.
+// (precision, psi size to a factor of two), so the centres of a sweep at the
+// same bond dimension are tuned once or twice, not at every step.
 void Engine::tune_tiled(uint64_t psi, uint64_t sig, int prec) {
   static std::mutex mu;
-  static std::map<std::tuple<int, int, int>, TileCfg> cache;
+  static std::map<std::pair<int, int>, TileCfg> cache;
   int lg = 0;
   while ((int64_t(1) << lg) < lay.size) ++lg;
-  const auto key = std::make_tuple(prec, lg, plan.nterms);
+  const auto key = std::make_pair(prec, lg);
   auto same = [](const TileCfg& a, const TileCfg& b) { return a.kmax == b.kmax && a.width == b.width; };
   {
     std::lock_guard<std::mutex> g(mu);
@@ -382,6 +384,7 @@ DavResult Engine::davidson(const DavOpts& o) {
   };
   try {
     int prec = o.policy ? 2 : o.precision;   // policy 1 starts in BF16
+    mixed_planes = o.policy != 0;
     auto apply = [&](uint64_t in, uint64_t out) {
       heff(in, out, st, prec);
       pr->sync(st);

@@ -64,6 +64,7 @@ struct Engine {
   // work-item shape of the bf16 tensor-core path and its autotuner
   TileCfg tcfg;
   bool autotune = true;
+  bool mixed_planes = false;       // prepare the three bf16 planes even for the BF16 form
   double tune_seconds = 0;
   int tunes = 0;
   void tune_tiled(uint64_t psi, uint64_t sig, int prec);
