@@ -274,6 +274,9 @@ PsiLayout make_psi_layout(const ProdBasis& Lp, const ProdBasis& Rp, QN target) {
   PsiLayout lay;
   const Basis& X = *Lp.blk;
   const Basis& Y = *Rp.blk;
+  lay.nl = Lp.nsub();
+  lay.nr = Rp.nsub();
+  lay.by_sub.assign((size_t)lay.nl * lay.nr, -1);
   for (int x = 0; x < X.nsec(); ++x)
     for (int i = 0; i < NSITE; ++i)
       for (int j = 0; j < NSITE; ++j)
@@ -288,7 +291,7 @@ PsiLayout make_psi_layout(const ProdBasis& Lp, const ProdBasis& Rp, QN target) {
           b.cols = Y.dim[y];
           b.off = lay.size;
           lay.size += (int64_t)b.rows * b.cols;
-          lay.by_sub[{b.lsub, b.rsub}] = (int)lay.blks.size();
+          lay.by_sub[(size_t)b.lsub * lay.nr + b.rsub] = (int)lay.blks.size();
           lay.blks.push_back(b);
         }
   return lay;
@@ -377,7 +380,10 @@ HeffPlan plan_terms(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay
 
   const ProdBasis& LB = Lp.pb;
   Launch s1, s2;
-  std::map<int, std::vector<Seg>> out;  // psi block -> segments
+  // psi block -> segments of the current chunk (vectors keep their capacity
+  // across chunks; blocks are emitted in index order)
+  std::vector<std::vector<Seg>> out(lay.blks.size());
+  bool any_out = false;
   std::unordered_map<uint64_t, int64_t> blocks_read;  // storage address -> elements
   auto note = [&](const BRef& b) {
     if (b.ident()) return;
@@ -386,14 +392,15 @@ HeffPlan plan_terms(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay
   };
   int64_t tused = 0;
   auto flush = [&]() {
-    if (out.empty() && s1.empty()) return;
-    for (auto& kv : out) {
-      const auto& pbk = lay.blks[kv.first];
+    if (!any_out && s1.empty()) return;
+    for (size_t bi = 0; bi < out.size(); ++bi) {
+      if (out[bi].empty()) continue;
+      const auto& pbk = lay.blks[bi];
       Prob p;
       p.c = (uint64_t)pbk.off; p.cbuf = B_SIG;
       p.m = pbk.rows; p.n = pbk.cols; p.ldc = pbk.cols; p.beta = 1;
-      p.seg0 = (int)s2.segs.size(); p.nseg = (int)kv.second.size();
-      for (auto& g : kv.second) s2.segs.push_back(g);
+      p.seg0 = (int)s2.segs.size(); p.nseg = (int)out[bi].size();
+      for (auto& g : out[bi]) s2.segs.push_back(g);
       s2.probs.push_back(p);
     }
     plan.flops += s1.flops + s2.flops;
@@ -402,7 +409,8 @@ HeffPlan plan_terms(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay
     plan.tmp_elems = std::max(plan.tmp_elems, tused);
     s1.clear();
     s2.clear();
-    out.clear();
+    for (auto& v : out) v.clear();
+    any_out = false;
     tused = 0;
   };
   for (const CenterTerm& t : terms) {
@@ -414,18 +422,18 @@ HeffPlan plan_terms(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay
     for (const BRef& bR : Rv.blocks) {
       if (bR.ident()) continue;
       for (auto& kv : lby) {
-        auto it = lay.by_sub.find({kv.first, bR.c});
-        if (it != lay.by_sub.end()) need += (int64_t)lay.blks[it->second].rows * bR.rows;
+        const int it = lay.find(kv.first, bR.c);
+        if (it >= 0) need += (int64_t)lay.blks[it].rows * bR.rows;
       }
     }
     if (tused && tused + need > tmp_budget) flush();
     for (const BRef& bR : Rv.blocks) {
       for (auto& kv : lby) {
         int cL = kv.first;
-        auto it = lay.by_sub.find({cL, bR.c});
-        if (it == lay.by_sub.end()) continue;
+        const int it = lay.find(cL, bR.c);
+        if (it < 0) continue;
         note(bR);
-        const auto& pin = lay.blks[it->second];
+        const auto& pin = lay.blks[it];
         int par = 1;
         if (Rv.odd) par = (LB.prod.q[LB.subs[cL].prod].n & 1) ? -1 : 1;
         const double bsc = t.coef * bR.sc * par;
@@ -451,8 +459,8 @@ HeffPlan plan_terms(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay
         }
 
         for (const BRef* bL : kv.second) {
-          auto ot = lay.by_sub.find({bL->r, bR.r});
-          if (ot == lay.by_sub.end()) continue;
+          const int ot = lay.find(bL->r, bR.r);
+          if (ot < 0) continue;
           note(*bL);
           Seg g;
           if (bL->ident()) { g.a = 0; g.abuf = B_ABS; g.lda = 0; g.ta = 0; }
@@ -462,7 +470,8 @@ HeffPlan plan_terms(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay
           g.sc = bsc * bL->sc;
           g.asc = bL->sc;
           g.bsc = bsc;
-          out[ot->second].push_back(g);
+          out[ot].push_back(g);
+          any_out = true;
           if (!bL->ident()) s2.flops += 2.0 * bL->rows * bR.rows * (double)bL->cols;
         }
       }
@@ -491,8 +500,8 @@ Launch plan_diag(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay, c
     for (const BRef& b : Rv.blocks) if (b.r == b.c) rdiag[b.r].push_back(&b);
     for (auto& lk : ldiag)
       for (auto& rk : rdiag) {
-        auto it = lay.by_sub.find({lk.first, rk.first});
-        if (it == lay.by_sub.end()) continue;
+        const int it = lay.find(lk.first, rk.first);
+        if (it < 0) continue;
         int par = 1;
         if (Rv.odd) par = (LB.prod.q[LB.subs[lk.first].prod].n & 1) ? -1 : 1;
         for (const BRef* bl : lk.second)
@@ -504,7 +513,7 @@ Launch plan_diag(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay, c
             if (br->ident()) { g.b = ones; g.ldb = 1; } else { g.b = br->ptr; g.ldb = br->ld + 1; }
             g.bbuf = B_ABS; g.tb = 1;
             g.sc = t.coef * bl->sc * br->sc * par;
-            out[it->second].push_back(g);
+            out[it].push_back(g);
           }
       }
   }

@@ -239,8 +239,13 @@ void renormalize(const Enlarged& E, const Basis& nb, const std::vector<int>& nb_
 struct PsiLayout {
   struct Blk { int x, i, j, y, lsub, rsub; int64_t off; int rows, cols; };
   std::vector<Blk> blks;
-  std::map<std::pair<int, int>, int> by_sub;   // (lsub, rsub) -> index
+  int nl = 0, nr = 0;            // sub-blocks of the left and right enlarged bases
+  std::vector<int> by_sub;       // lsub * nr + rsub -> block index, -1: no block
   int64_t size = 0;
+  int find(int lsub, int rsub) const {
+    if (lsub < 0 || rsub < 0 || lsub >= nl || rsub >= nr) return -1;
+    return by_sub[(size_t)lsub * nr + rsub];
+  }
 };
 PsiLayout make_psi_layout(const ProdBasis& Lp, const ProdBasis& Rp, QN target);
 

@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <cmath>
 #include <map>
+#include <unordered_map>
 #include <stdexcept>
 
 #include "core.hpp"
@@ -176,31 +177,37 @@ struct Ctx {
     struct Plan { std::vector<Group> groups; };
     std::vector<Plan> plans(pending.size());
     for (size_t n = 0; n < pending.size(); ++n) {
-      std::map<std::pair<int, int>, int> gi;   // (monomial or -1-identity-slot, par) -> group
+      int gi[16][2];                             // (monomial, par) -> group
+      for (auto& row : gi) row[0] = row[1] = -1;
+      std::vector<std::unordered_map<uintptr_t, int>> where;  // per group: (source, transposed) -> item
       auto& G = plans[n].groups;
       for (const Contrib& c : pending[n].cs) {
         if (c.coef == 0.0 || c.o.zero()) continue;
         double x[16];
         M.split(c.o, x);
+        const uintptr_t id = reinterpret_cast<uintptr_t>(c.src) * 2 + (c.srcT ? 1 : 0);
         for (int k = 0; k < 16; ++k) {
           if (x[k] == 0.0) continue;
-          auto key = std::make_pair(k, (int)c.par);
-          auto it = gi.find(key);
-          int g;
-          if (it == gi.end()) {
+          int& g = gi[k][c.par ? 1 : 0];
+          if (g < 0) {
             g = (int)G.size();
-            gi[key] = g;
             G.push_back({M.m[k], c.par, {}});
-          } else {
-            g = it->second;
+            where.emplace_back();
           }
-          bool merged = false;
-          for (auto& itm : G[g].items)
-            if (itm.src == c.src && itm.T == c.srcT) { itm.coef += c.coef * x[k]; merged = true; break; }
-          if (!merged) G[g].items.push_back({c.src, c.srcT, c.coef * x[k]});
+          auto ins = where[g].emplace(id, (int)G[g].items.size());
+          if (ins.second) G[g].items.push_back({c.src, c.srcT, c.coef * x[k]});
+          else G[g].items[ins.first->second].coef += c.coef * x[k];
         }
       }
     }
+    // block lists of the sources (transposes built once)
+    std::unordered_map<uintptr_t, std::vector<BRef>> blocks_of;
+    auto blocks = [&](const OpView* src, bool T) -> const std::vector<BRef>& {
+      const uintptr_t id = reinterpret_cast<uintptr_t>(src) * 2 + (T ? 1 : 0);
+      auto it = blocks_of.find(id);
+      if (it != blocks_of.end()) return it->second;
+      return blocks_of.emplace(id, src_blocks(src, T)).first->second;
+    };
     // storage for summed groups
     int64_t total = 0;
     struct Mat { size_t n, g; std::map<std::pair<int, int>, std::pair<int64_t, std::pair<int, int>>> blk; };
@@ -211,7 +218,7 @@ struct Ctx {
         if (grp.items.size() < 2) continue;
         Mat mt{n, g, {}};
         for (auto& itm : grp.items)
-          for (const BRef& b : src_blocks(itm.src, itm.T)) {
+          for (const BRef& b : blocks(itm.src, itm.T)) {
             auto key = std::make_pair(b.r, b.c);
             if (!mt.blk.count(key)) {
               mt.blk[key] = {total, {b.rows, b.cols}};
@@ -226,24 +233,27 @@ struct Ctx {
     std::map<std::pair<size_t, size_t>, std::vector<BRef>> summed;
     for (auto& mt : mats) {
       auto& grp = plans[mt.n].groups[mt.g];
-      std::map<std::pair<int, int>, std::vector<Seg>> segs;
+      // segments grouped by destination block, in item order within a block
+      std::vector<std::pair<std::pair<int, int>, Seg>> segs;
       for (auto& itm : grp.items)
-        for (const BRef& b : src_blocks(itm.src, itm.T)) {
+        for (const BRef& b : blocks(itm.src, itm.T)) {
           Seg s;
           s.a = 0; s.abuf = B_ABS; s.k = b.rows; s.sc = itm.coef * b.sc;
           if (b.ident()) { s.b = 0; s.bbuf = B_ABS; }
           else { s.b = b.ptr; s.bbuf = B_ABS; s.ldb = b.ld; s.tb = b.tr ? 1 : 0; }
-          segs[{b.r, b.c}].push_back(s);
+          segs.push_back({{b.r, b.c}, s});
         }
+      std::stable_sort(segs.begin(), segs.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
       std::vector<BRef> refs;
+      size_t si = 0;
       for (auto& kv : mt.blk) {
         Prob p;
         p.c = store + 8ull * kv.second.first; p.cbuf = B_ABS;
         p.m = kv.second.second.first; p.n = kv.second.second.second; p.ldc = p.n; p.beta = 0;
         p.seg0 = (int)l.segs.size();
-        auto& sv = segs[kv.first];
-        p.nseg = (int)sv.size();
-        for (auto& s : sv) l.segs.push_back(s);
+        const size_t s0 = si;
+        while (si < segs.size() && segs[si].first == kv.first) l.segs.push_back(segs[si++].second);
+        p.nseg = (int)(si - s0);
         l.probs.push_back(p);
         BRef r;
         r.r = kv.first.first; r.c = kv.first.second; r.ptr = p.c;
@@ -262,7 +272,7 @@ struct Ctx {
           expand(summed[{n, g}], grp.o, 1.0, grp.par, v.blocks);
         } else if (grp.items.size() == 1) {
           auto& itm = grp.items[0];
-          expand(src_blocks(itm.src, itm.T), grp.o, itm.coef, grp.par, v.blocks);
+          expand(blocks(itm.src, itm.T), grp.o, itm.coef, grp.par, v.blocks);
         }
       }
       if (!v.blocks.empty()) E.ops[pending[n].key] = v;
