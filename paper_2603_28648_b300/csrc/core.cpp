@@ -186,8 +186,18 @@ void renormalize(const Enlarged& E, const Basis& nb, const std::vector<int>& nb_
     return tensor + 8ull * (toff[S.prod] + S.off);
   };
   Launch s1, s2;
+  {
+    // one segment per stored block reference at most, in either stage
+    size_t nseg = 0;
+    for (auto& kv : E.ops)
+      if (kv.first.f != F_I) nseg += kv.second.blocks.size();
+    s1.segs.reserve(nseg);
+    s1.probs.reserve(nseg);
+    s2.segs.reserve(nseg);
+  }
   int64_t tused = 0;
   double fl = 0;
+  std::vector<std::pair<std::pair<int, int>, Seg>> segs;
   auto flush = [&]() {
     if (s1.empty() && s2.empty()) return;
     if (tused) ex.tmp(tused);
@@ -212,7 +222,9 @@ void renormalize(const Enlarged& E, const Basis& nb, const std::vector<int>& nb_
       need += (int64_t)b.rows * nb.dim[nq2];
     }
     if (tused && tused + need > tmp_budget) flush();
-    std::map<std::pair<int, int>, std::vector<Seg>> segs;
+    // (output block, segment) pairs, grouped by output block below in the
+    // order they were produced
+    segs.clear();
     for (const BRef& b : op.blocks) {
       const Sub& Sr = pb.subs[b.r];
       const Sub& Sc = pb.subs[b.c];
@@ -246,16 +258,19 @@ void renormalize(const Enlarged& E, const Basis& nb, const std::vector<int>& nb_
         g.b = (uint64_t)tused; g.bbuf = B_TMP; g.ldb = dq2; g.tb = 0;
         tused += (int64_t)b.rows * dq2;
       }
-      segs[{nq, nq2}].push_back(g);
+      segs.push_back({{nq, nq2}, g});
       s2.flops += 2.0 * dq * dq2 * g.k;
     }
-    for (auto& sv : segs) {
-      int nq = sv.first.first, nq2 = sv.first.second;
+    std::stable_sort(segs.begin(), segs.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+    for (size_t si = 0; si < segs.size();) {
+      const std::pair<int, int> key = segs[si].first;
+      int nq = key.first, nq2 = key.second;
       Prob p;
-      p.c = store + 8ull * lay[sv.first]; p.cbuf = B_ABS;
+      p.c = store + 8ull * lay[key]; p.cbuf = B_ABS;
       p.m = nb.dim[nq]; p.n = nb.dim[nq2]; p.ldc = p.n; p.beta = 0;
-      p.seg0 = (int)s2.segs.size(); p.nseg = (int)sv.second.size();
-      for (auto& g : sv.second) s2.segs.push_back(g);
+      p.seg0 = (int)s2.segs.size();
+      while (si < segs.size() && segs[si].first == key) s2.segs.push_back(segs[si++].second);
+      p.nseg = (int)s2.segs.size() - p.seg0;
       s2.probs.push_back(p);
       BRef r;
       r.r = nq; r.c = nq2; r.ptr = p.c; r.rows = p.m; r.cols = p.n; r.ld = p.n; r.tr = false; r.sc = 1.0;
