@@ -395,10 +395,11 @@ HeffPlan plan_terms(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay
 
   const ProdBasis& LB = Lp.pb;
   Launch s1, s2;
-  // psi block -> segments of the current chunk (vectors keep their capacity
-  // across chunks; blocks are emitted in index order)
-  std::vector<std::vector<Seg>> out(lay.blks.size());
-  bool any_out = false;
+  // (psi block, segment) pairs of the current chunk, emitted grouped by
+  // block in index order (a counting sort keeps the order within a block)
+  std::vector<std::pair<int, Seg>> out;
+  std::vector<int> cnt(lay.blks.size() + 1);
+  std::vector<Seg> sorted;
   std::unordered_map<uint64_t, int64_t> blocks_read;  // storage address -> elements
   auto note = [&](const BRef& b) {
     if (b.ident()) return;
@@ -407,15 +408,25 @@ HeffPlan plan_terms(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay
   };
   int64_t tused = 0;
   auto flush = [&]() {
-    if (!any_out && s1.empty()) return;
-    for (size_t bi = 0; bi < out.size(); ++bi) {
-      if (out[bi].empty()) continue;
+    if (out.empty() && s1.empty()) return;
+    std::fill(cnt.begin(), cnt.end(), 0);
+    for (auto& e : out) cnt[e.first + 1]++;
+    for (size_t bi = 0; bi < lay.blks.size(); ++bi) cnt[bi + 1] += cnt[bi];
+    sorted.resize(out.size());
+    {
+      std::vector<int> pos(cnt.begin(), cnt.end() - 1);
+      for (auto& e : out) sorted[pos[e.first]++] = e.second;
+    }
+    s2.segs.reserve(s2.segs.size() + sorted.size());
+    for (size_t bi = 0; bi < lay.blks.size(); ++bi) {
+      const int n = cnt[bi + 1] - cnt[bi];
+      if (n == 0) continue;
       const auto& pbk = lay.blks[bi];
       Prob p;
       p.c = (uint64_t)pbk.off; p.cbuf = B_SIG;
       p.m = pbk.rows; p.n = pbk.cols; p.ldc = pbk.cols; p.beta = 1;
-      p.seg0 = (int)s2.segs.size(); p.nseg = (int)out[bi].size();
-      for (auto& g : out[bi]) s2.segs.push_back(g);
+      p.seg0 = (int)s2.segs.size(); p.nseg = n;
+      s2.segs.insert(s2.segs.end(), sorted.begin() + cnt[bi], sorted.begin() + cnt[bi + 1]);
       s2.probs.push_back(p);
     }
     plan.flops += s1.flops + s2.flops;
@@ -424,8 +435,7 @@ HeffPlan plan_terms(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay
     plan.tmp_elems = std::max(plan.tmp_elems, tused);
     s1.clear();
     s2.clear();
-    for (auto& v : out) v.clear();
-    any_out = false;
+    out.clear();
     tused = 0;
   };
   for (const CenterTerm& t : terms) {
@@ -485,8 +495,7 @@ HeffPlan plan_terms(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay
           g.sc = bsc * bL->sc;
           g.asc = bL->sc;
           g.bsc = bsc;
-          out[ot].push_back(g);
-          any_out = true;
+          out.push_back({ot, g});
           if (!bL->ident()) s2.flops += 2.0 * bL->rows * bR.rows * (double)bL->cols;
         }
       }
@@ -505,7 +514,7 @@ Launch plan_diag(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay, c
   // right blocks are diagonal blocks: rank-1 segments (K = 1) with strided
   // diagonals (leading dimension ld + 1) or a vector of ones for identities
   std::vector<CenterTerm> terms = center_terms(Lp, Rp, I);
-  std::map<int, std::vector<Seg>> out;
+  std::vector<std::pair<int, Seg>> out;  // (psi block, segment), grouped by block below
   const ProdBasis& LB = Lp.pb;
   for (const CenterTerm& t : terms) {
     OpView Lv = t.LT ? transpose(*t.L) : *t.L;
@@ -528,18 +537,22 @@ Launch plan_diag(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay, c
             if (br->ident()) { g.b = ones; g.ldb = 1; } else { g.b = br->ptr; g.ldb = br->ld + 1; }
             g.bbuf = B_ABS; g.tb = 1;
             g.sc = t.coef * bl->sc * br->sc * par;
-            out[it].push_back(g);
+            out.push_back({it, g});
           }
       }
   }
   Launch l;
-  for (auto& kv : out) {
-    const auto& b = lay.blks[kv.first];
+  std::stable_sort(out.begin(), out.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+  l.segs.reserve(out.size());
+  for (size_t i = 0; i < out.size();) {
+    const int bi = out[i].first;
+    const auto& b = lay.blks[bi];
     Prob p;
     p.c = (uint64_t)b.off; p.cbuf = B_SIG;
     p.m = b.rows; p.n = b.cols; p.ldc = b.cols; p.beta = 1;
-    p.seg0 = (int)l.segs.size(); p.nseg = (int)kv.second.size();
-    for (auto& g : kv.second) l.segs.push_back(g);
+    p.seg0 = (int)l.segs.size();
+    while (i < out.size() && out[i].first == bi) l.segs.push_back(out[i++].second);
+    p.nseg = (int)l.segs.size() - p.seg0;
     l.probs.push_back(p);
   }
   (void)I;
