@@ -1,0 +1,285 @@
+// Host-side check of the library's task lists, without a GPU.
+//
+// Builds the environment of a random-structure MPS with a recording executor
+// (device addresses are handed out by a bump allocator and every allocation is
+// remembered; nothing is computed), then checks that every FP64 segment, every
+// tiled work item, view and segment of the tensor-core path stays inside the
+// buffer it addresses, that no work item is empty, and that the algorithmic
+// flop counts of the FP64 and tiled plans agree. An out-of-range offset in a
+// plan would be an out-of-bounds access on the GPU.
+//
+// usage: planner_check L N D   (2Sz = N mod 2, centre bond L/2 - 1)
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <string>
+
+#include "engine.hpp"
+#include "tiled.hpp"
+
+using namespace qd;
+
+namespace {
+
+int fails = 0;
+void fail(const std::string& m) {
+  if (fails < 20) std::fprintf(stderr, "FAIL: %s\n", m.c_str());
+  ++fails;
+}
+
+struct RecEx : Executor {
+  uint64_t next = 1ull << 40;
+  std::map<uint64_t, int64_t> alloc_bytes;  // base -> bytes
+  uint64_t tmp_base = 0;
+  int64_t tmp_n = 0;
+  int64_t live = 0;
+  uint64_t alloc(int64_t n) override {
+    const uint64_t p = next;
+    const int64_t b = std::max<int64_t>(8, n * 8);
+    next += ((b + 255) / 256) * 256 + 256;
+    alloc_bytes[p] = b;
+    live += b;
+    return p;
+  }
+  void release(uint64_t) override {}
+  uint64_t tmp(int64_t n) override {
+    if (n > tmp_n) {
+      tmp_base = alloc(n);
+      tmp_n = n;
+    }
+    return tmp_base;
+  }
+  // [addr, addr + bytes) inside one recorded allocation
+  bool inside(uint64_t addr, int64_t bytes) const {
+    auto it = alloc_bytes.upper_bound(addr);
+    if (it == alloc_bytes.begin()) return false;
+    --it;
+    return addr >= it->first && addr + (uint64_t)bytes <= it->first + (uint64_t)it->second;
+  }
+  void run(const Launch&, uint64_t, uint64_t) override {}
+  void upload(uint64_t, const double*, int64_t) override {}
+  void download(double* h, uint64_t, int64_t n) override { std::fill(h, h + n, 0.0); }
+  void zero(uint64_t, int64_t) override {}
+  void randn(uint64_t, int64_t, uint64_t) override {}
+  void orthonormal_cols(uint64_t, int, int) override {}
+  double dot(uint64_t, uint64_t, int64_t) override { return 1.0; }
+  void scale(uint64_t, double, int64_t) override {}
+  void axpby(uint64_t, double, uint64_t, double, int64_t) override {}
+  void precond(uint64_t, uint64_t, uint64_t, double, double, int64_t) override {}
+  void eigh(uint64_t, int, double*) override {}
+  void copy(uint64_t, uint64_t, int64_t) override {}
+  uint64_t host_alloc(int64_t) override { return 0; }
+  void host_free(uint64_t) override {}
+  void d2h(uint64_t, uint64_t, int64_t) override {}
+  void h2d_async(uint64_t, uint64_t, int64_t) override {}
+  void copies_join() override {}
+  double copies_wait_seconds() override { return 0.0; }
+  int64_t live_bytes() const override { return live; }
+};
+
+struct NullRunner : PreparedRunner {
+  int n = 0;
+  int prepare(const Launch&) override { return n++; }
+  void drop_prepared() override {}
+  void run_prepared(int, uint64_t, uint64_t, void*, int) override {}
+  int take_error() override { return 0; }
+  const void* prepared_handle(int) const override { return nullptr; }
+  void* stream() override { return nullptr; }
+  void sync(void*) override {}
+  void zero_async(uint64_t, int64_t, void*) override {}
+  int64_t bytes_allocated() const override { return 0; }
+  void prepare_tiled(const TiledPlan&, int) override {}
+  void set_tiled_items(const TiledPlan&) override {}
+  int tiled_planes() const override { return 0; }
+  double time_tiled(uint64_t, uint64_t, int, int) override { return 0.0; }
+  void run_tiled(uint64_t, uint64_t, void*, int) override {}
+};
+
+// extent in elements of a rows x cols operand with leading dimension ld,
+// stored transposed when tr
+int64_t extent(int rows, int cols, int ld, int tr) {
+  if (rows <= 0 || cols <= 0) return 0;
+  return tr ? (int64_t)(cols - 1) * ld + rows : (int64_t)(rows - 1) * ld + cols;
+}
+
+void check_fp64(const HeffPlan& P, const PsiLayout& lay, const RecEx& ex) {
+  auto buf_ok = [&](uint64_t a, int buf, int64_t elems, const char* what) {
+    if (elems <= 0) return;
+    bool ok = false;
+    if (buf == B_ABS) ok = ex.inside(a, elems * 8);
+    else if (buf == B_PSI || buf == B_SIG) ok = (int64_t)a + elems <= lay.size;
+    else if (buf == B_TMP) ok = (int64_t)a + elems <= P.tmp_elems;
+    if (!ok) fail(std::string("fp64 plan: ") + what + " out of its buffer");
+  };
+  for (size_t c = 0; c < P.stage1.size(); ++c)
+    for (const Launch* L : {&P.stage1[c], &P.stage2[c]}) {
+      for (const Prob& p : L->probs) {
+        if (p.nseg <= 0) fail("fp64 plan: problem without segments");
+        if (p.seg0 < 0 || p.seg0 + p.nseg > (int)L->segs.size()) fail("fp64 plan: segment range");
+        buf_ok(p.c, p.cbuf, extent(p.m, p.n, p.ldc, 0), "output");
+        for (int s = p.seg0; s < p.seg0 + p.nseg && s < (int)L->segs.size(); ++s) {
+          const Seg& g = L->segs[s];
+          if (g.k <= 0) fail("fp64 plan: segment without K");
+          if (!(g.a == 0 && g.abuf == B_ABS)) buf_ok(g.a, g.abuf, extent(p.m, g.k, g.lda, g.ta), "A operand");
+          if (!(g.b == 0 && g.bbuf == B_ABS)) buf_ok(g.b, g.bbuf, extent(g.k, p.n, g.ldb, g.tb), "B operand");
+        }
+      }
+    }
+}
+
+void check_tiled(const HeffPlan& P, const PsiLayout& lay, const RecEx& ex, const TileCfg& cfg) {
+  const TiledPlan T = plan_tiled(P, lay, cfg);
+  if (T.flops != P.flops) fail("tiled plan: flop count differs from the FP64 plan");
+  // conversion views
+  auto views_ok = [&](const std::vector<TView>& vs, int64_t arena, const char* what) {
+    for (const TView& v : vs) {
+      if (v.rows <= 0 || v.cols <= 0) fail(std::string("tiled view without rows or columns: ") + what);
+      if (v.dst < 0 || v.dst + tiled_bytes(v.rows, v.cols, v.panel) > arena)
+        fail(std::string("tiled view past its arena: ") + what);
+      if (v.src == 0 && v.buf == 0) continue;  // scaled identity
+      const int64_t e = extent(v.rows, v.cols, v.ld, v.tr);
+      if (v.buf == 1 ? (int64_t)v.src + e > lay.size : !ex.inside(v.src, e * 8))
+        fail(std::string("tiled view source out of its buffer: ") + what);
+    }
+  };
+  views_ok(T.avw, T.abytes, "left");
+  views_ok(T.bvw, T.bbytes, "right");
+  views_ok(T.psivw, T.psibytes, "psi");
+  // stage 1
+  int64_t nviews = 0;
+  for (const K1Item& it : T.i1) {
+    if (it.nv <= 0 || it.nv > 16) fail("stage-1 item with 0 or more than 16 views");
+    if (it.k <= 0 || it.nrows <= 0 || it.nrows > TP_B) fail("stage-1 item shape");
+    const int c8 = tiled_c8(it.k);
+    if (it.pb8 != (it.nrows + 7) / 8) fail("stage-1 psi panel core rows");
+    if (it.b + (int64_t)it.pb8 * c8 * 128 > T.psibytes) fail("stage-1 psi panel past the psi arena");
+    int cols = 0;
+    for (int v = it.v0; v < it.v0 + it.nv; ++v) {
+      if (v < 0 || v >= (int)T.v1.size()) {
+        fail("stage-1 view index");
+        continue;
+      }
+      const K1View& w = T.v1[v];
+      ++nviews;
+      if (w.mrows <= 0 || w.mrows > TP_A || w.pa8 != (w.mrows + 7) / 8) fail("stage-1 view rows");
+      if (w.a + (int64_t)w.pa8 * c8 * 128 > T.bbytes) fail("stage-1 view panel past the right arena");
+      if (w.tcol % 16 || w.tcol != cols) fail("stage-1 accumulator columns not packed in order");
+      cols = w.tcol + 16 * ((it.nrows + 15) / 16);
+      if (cols > 256) fail("stage-1 accumulator columns beyond 256");
+      if (w.mp * TP_A + w.mrows > w.ntot) fail("stage-1 view rows beyond T rows");
+      if (w.tout < 0 || w.tout + tiled_bytes(w.ntot, it.mtot, TP_B) > T.tbytes) fail("stage-1 T tile past the T arena");
+      if (it.np * TP_B + it.nrows > it.mtot) fail("stage-1 psi panel beyond the psi block rows");
+    }
+  }
+  if (nviews != (int64_t)T.v1.size()) fail("stage-1 views not covered exactly once");
+  // stage 2
+  std::vector<int> seen(T.s2.size(), 0);
+  for (const K2Item& it : T.i2) {
+    if (it.s1 <= it.s0) fail("stage-2 item without segments");
+    if (it.mrows <= 0 || it.mrows > TP_A || it.nrows <= 0 || it.nrows > TP_B) fail("stage-2 tile shape");
+    const int64_t last = it.out + (int64_t)(it.mp * TP_A + it.mrows - 1) * it.ldc + it.np * TP_B + it.nrows;
+    if (it.out < 0 || last > lay.size) fail("stage-2 tile past sigma");
+    const int pa8 = (it.mrows + 7) / 8, pb8 = (it.nrows + 7) / 8;
+    for (int s = it.s0; s < it.s1; ++s) {
+      if (s < 0 || s >= (int)T.s2.size()) {
+        fail("stage-2 segment index");
+        continue;
+      }
+      seen[s]++;
+      const K2Seg& g = T.s2[s];
+      if (g.k <= 0) fail("stage-2 segment without K");
+      const int c8 = tiled_c8(g.k);
+      if (g.a + (int64_t)it.mp * (TP_A / 8) * c8 * 128 + (int64_t)pa8 * c8 * 128 > T.abytes)
+        fail("stage-2 left view panel past the left arena");
+      if (g.b + (int64_t)it.np * (TP_B / 8) * c8 * 128 + (int64_t)pb8 * c8 * 128 > T.tbytes)
+        fail("stage-2 T panel past the T arena");
+    }
+  }
+  // every segment is used by the tiles of its sigma block: same count for all
+  // segments of a block, at least once
+  for (size_t s = 0; s < seen.size(); ++s)
+    if (seen[s] < 1) fail("stage-2 segment never used");
+}
+
+}  // namespace
+
+int main(int argc, char** argv) {
+  if (argc < 4) {
+    std::fprintf(stderr, "usage: planner_check L N D\n");
+    return 2;
+  }
+  const int L = std::atoi(argv[1]), N = std::atoi(argv[2]), D = std::atoi(argv[3]);
+  const int two_s = N % 2;
+  RecEx ex;
+  NullRunner pr;
+  Engine E;
+  E.ex = &ex;
+  E.pr = &pr;
+  E.N = N;
+  E.two_s = two_s;
+  E.L = L;
+  E.tmp_budget = (int64_t)(2e9 / 8);
+  E.I.L = L;
+  E.I.h.assign((size_t)L * L, 0.0);
+  E.I.V.assign((size_t)L * L * L * L, 0.0);
+  // generic symmetric integrals (every coupling present)
+  for (int p = 0; p < L; ++p)
+    for (int q = 0; q < L; ++q) E.I.h[(size_t)p * L + q] = 0.1 + 0.01 * ((p + q) % 7);
+  for (int p = 0; p < L; ++p)
+    for (int q = 0; q < L; ++q)
+      for (int r = 0; r < L; ++r)
+        for (int s = 0; s < L; ++s) {
+          const int a = std::min(p, q) * L + std::max(p, q), b = std::min(r, s) * L + std::max(r, s);
+          E.I.V[(((size_t)p * L + q) * L + r) * L + s] = 0.01 + 1e-3 * ((std::min(a, b) * 31 + std::max(a, b) * 17) % 97);
+        }
+  const int center = L / 2 - 1;
+  auto st = mps_structure(L, N, two_s, D);
+  std::vector<Basis> bonds(L + 1);
+  for (int b = 0; b <= center; ++b)
+    for (auto& kv : st[b]) bonds[b].add(kv.first, kv.second);
+  for (int b = center + 2; b <= L; ++b)
+    for (auto& kv : st[L - b]) bonds[b].add(kv.first, kv.second);
+  E.site.assign(L, 0);
+  E.site_off.assign(L, {});
+  E.site_nb.assign(L, {});
+  for (int p = 0; p < L; ++p) {
+    if (p == center || p == center + 1) continue;
+    const bool left = p < center;
+    const Basis& from = left ? bonds[p] : bonds[p + 1];
+    const Basis& to = left ? bonds[p + 1] : bonds[p];
+    ProdBasis pb = make_prod(from, left);
+    std::vector<int64_t> so(pb.prod.nsec(), -1);
+    std::vector<int> nb(pb.prod.nsec(), -1);
+    int64_t tot = 0;
+    for (int q = 0; q < pb.prod.nsec(); ++q) {
+      const int t = to.find(pb.prod.q[q]);
+      if (t < 0) continue;
+      so[q] = tot;
+      nb[q] = t;
+      tot += (int64_t)pb.prod.dim[q] * to.dim[t];
+    }
+    E.site[p] = ex.alloc(std::max<int64_t>(1, tot));
+    E.site_off[p] = so;
+    E.site_nb[p] = nb;
+  }
+  E.bonds = bonds;
+  E.center = center;
+  {
+    ProdBasis a = make_prod(bonds[center], true), b = make_prod(bonds[center + 2], false);
+    PsiLayout l = make_psi_layout(a, b, QN{N, two_s});
+    E.dpsi = ex.alloc(std::max<int64_t>(1, l.size));
+  }
+  E.build_env();
+  check_fp64(E.plan, E.lay, ex);
+  for (int kmax : {1024, 4096, 1 << 30})
+    for (int width : {128, 256}) {
+      TileCfg cfg;
+      cfg.kmax = kmax;
+      cfg.width = width;
+      check_tiled(E.plan, E.lay, ex, cfg);
+    }
+  std::printf("L=%d N=%d D=%d psi=%lld terms=%d gflop=%.4f fails=%d\n", L, N, D, (long long)E.lay.size,
+              E.plan.nterms, E.plan.flops / 1e9, fails);
+  return fails ? 1 : 0;
+}

@@ -1,0 +1,36 @@
+"""Host logic without a GPU: the task lists the library plans for H_eff psi
+(FP64 segments and the tiled tensor-core work items) stay inside the buffers
+they address, no work item is empty, and both plans count the same
+algorithmic flops. The library's host sources are compiled with g++ together
+with tests/planner_check.cpp, which records allocations instead of computing."""
+import os
+import shutil
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2603_28648_b300", "csrc")
+HOST_SOURCES = ["core.cpp", "rules.cpp", "init.cpp", "engine.cpp", "tiled.cpp"]
+
+
+@pytest.fixture(scope="module")
+def checker(tmp_path_factory):
+    if shutil.which("g++") is None:
+        pytest.skip("g++ not available")
+    out = str(tmp_path_factory.mktemp("planner") / "planner_check")
+    inc = ["-I", CSRC]
+    cuda_inc = "/usr/local/cuda/include"
+    if os.path.isdir(cuda_inc):
+        inc += ["-I", cuda_inc]
+    cmd = (["g++", "-O2", "-std=c++17"] + inc + [os.path.join(ROOT, "tests", "planner_check.cpp")] +
+           [os.path.join(CSRC, s) for s in HOST_SOURCES] + ["-o", out])
+    subprocess.run(cmd, check=True)
+    return out
+
+
+@pytest.mark.parametrize("L,N,D", [(6, 6, 16), (7, 5, 16), (12, 12, 32), (36, 54, 64)])
+def test_plans_stay_in_bounds(checker, L, N, D):
+    r = subprocess.run([checker, str(L), str(N), str(D)], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "fails=0" in r.stdout
