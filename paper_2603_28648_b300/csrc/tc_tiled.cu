@@ -1,19 +1,25 @@
-// TMA-fed tcgen05 grouped GEMM of H_eff psi (BF16 and three-term BF16) for sm_103a.
+// Bulk-copy-fed tcgen05 grouped GEMM of H_eff psi (BF16 and three-term BF16) for sm_103a.
 //
 // Operands are pre-tiled bf16 planes (tiled.hpp): every K chunk of an operand
 // panel is one contiguous range, so a single cp.async.bulk per operand and
 // plane moves it into shared memory. One persistent CTA per SM walks a static
 // list of work items with three roles:
-//   warp 0   : producer. Reserves each K chunk in a byte ring of shared memory
+//   warp 0   : producer. Reserves each chunk in a byte ring of shared memory
 //              (chunks take exactly their bytes, so many small chunks are in
-//              flight), writes the chunk's MMA list into one of NR metadata
-//              records, arms the record's mbarrier with the byte count and
-//              issues the bulk copies (stage 1: one lane per view). Segment
-//              and view descriptors are loaded 32 at a time by the warp.
-//   warp 1   : one lane issues tcgen05.mma from the metadata records into one
-//              of two accumulators in tensor memory (256 FP32 columns each);
-//              tcgen05.commit frees the record and its ring bytes and, after an
-//              item's last chunk, marks the accumulator full.
+//              flight), writes the chunk's MMA list (ready shared-memory
+//              descriptors) into one of NR records, arms the record's mbarrier
+//              with the byte count and issues the bulk copies from several
+//              lanes at once (stage 1: one lane per view, the psi panel by
+//              lanes 16..; stage 2: up to 16 short segments packed into one
+//              chunk, A pieces by their own lanes, B pieces by lane ^ 16).
+//              Work-item descriptors are prefetched two items ahead, views and
+//              segment batches one step ahead.
+//   warp 1   : lane 0 of the converged warp issues tcgen05.mma from the
+//              records into one of two accumulators in tensor memory (256 FP32
+//              columns each); every fourth chunk (and every record without
+//              data) commits to its record's mbarrier, which frees the ring
+//              bytes of all chunks before it; after an item's last chunk a
+//              commit marks the accumulator full.
 //   warps 2-9: epilogue, two warps per tensor-memory lane quarter splitting the
 //              columns. Stage 1 scales T_t^T rows, rounds them to bf16 (three
 //              planes for BF16x3) and stores 16-byte core-matrix rows; stage 2
