@@ -201,7 +201,9 @@ def run_reference(args, rank, world):
         "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "u1_L10_N10_D64 centre-bond H_eff psi (oracle sample)",
-                   "note": "oracle: dense FP64 numpy, H_eff psi with environments built"},
+                   "note": "oracle: dense FP64 numpy, H_eff psi with environments built",
+                   "flops": "algorithmic count of the library's task list for the same product "
+                            "(qcdmrg_stats.heff_flops, planned outside the timed region)"},
         "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": cores(), "kind": "oracle",
                          "sample": "U(1) L=10 N=10 D=64 centre-bond H_eff psi (environment excluded)"},
         "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
