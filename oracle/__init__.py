@@ -12,7 +12,9 @@ Modules
              renormalized operators (dense blocks), Lanczos, SVD truncation
   mpssu2     SU(2) spin-adapted two-site tangent space (multiplets coupled with
              Clebsch-Gordan coefficients, expanded to determinants) and the
-             plain definition H_eff = P^T H_FCI P in that space
+             plain definition H_eff = P^T H_FCI P in that space; the same space
+             written as a U(1) MPS with the Clebsch-Gordan map of the
+             two-site coefficients
 
 Conventions (the paper states none; fixed here and used by both sides):
   H = sum_pq h_pq E_pq + 1/2 sum_pqrs (pq|rs) (E_pq E_rs - delta_qr E_ps) + e_core,

@@ -132,11 +132,15 @@ class TangentSU2:
         self.L, self.N, self.two_s, self.l = L, N, two_s, l
         rng = np.random.default_rng(seed)
         left = vacuum()
+        self.lefts = [left]            # left blocks of 0, 1, ..., l sites
         for _ in range(l):
             left = grow(left, True, rng, None if cap is None else _caps(left, cap, True))
+            self.lefts.append(left)
         right = vacuum()
+        self.rights = [right]          # right blocks of the last 0, 1, ..., L-l-2 sites
         for _ in range(L - l - 2):
             right = grow(right, False, rng, None if cap is None else _caps(right, cap, False))
+            self.rights.append(right)
         self.left, self.right = left, right
         a = coupled_candidates(left, site_mults())     # (left block x site l)
         b = coupled_candidates(site_mults(), right)    # (site l+1 x right block)
@@ -161,6 +165,7 @@ class TangentSU2:
                 cols.append(self._to_dets(v))
                 labels.append((la, lb))
         self.labels = labels
+        self.cand_a, self.cand_b = a, b
         self.P = np.stack(cols, axis=1) if cols else np.zeros((self.space.dim, 0))
 
     def _to_dets(self, v):
@@ -197,3 +202,75 @@ def _caps(block, cap, left):
     cands = coupled_candidates(block, site_mults()) if left else coupled_candidates(site_mults(), block)
     keys = {(m.n, m.s) for _, m in cands}
     return {k: cap for k in keys}
+
+
+def _states(block):
+    """All components of a block's multiplets as U(1) states: labels (N, 2M) and Fock vectors,
+    sorted by label (stable within a label)."""
+    st = []
+    for m in block:
+        for i in range(m.s + 1):
+            st.append(((m.n, m.s - 2 * i), m.vec[i]))
+    st.sort(key=lambda t: t[0])
+    return st
+
+
+def to_u1(t):
+    """The same state space as a U(1)xU(1) MPS: bond states are all M components of the
+    multiplets. Returns (mps, C) with mps an oracle.mpsu1.MPSU1 (left- and right-canonical
+    tensors, psi = 0) and C[flat U(1) psi index, SU(2) column] the Clebsch-Gordan map of the
+    reduced two-site wavefunction onto the U(1) one (orthonormal columns)."""
+    from .mpsu1 import MPSU1, Bond
+    L, l = t.L, t.l
+    lst = [_states(b) for b in t.lefts]            # bond b = 0..l
+    rst = [_states(b) for b in t.rights]           # right block of k sites -> bond L - k
+
+    def bond(states):
+        d = {}
+        for lab, _ in states:
+            d[lab] = d.get(lab, 0) + 1
+        return Bond(d)
+
+    lbonds = {b: bond(lst[b]) for b in range(l + 1)}
+    rbonds = {L - k: bond(rst[k]) for k in range(L - l - 1)}
+    A, R = {}, {}
+    for p in range(l):
+        old, new = lst[p], lst[p + 1]
+        n_old = 4 ** p
+        T = np.zeros((len(old), 4, len(new)))
+        Vo = np.stack([v for _, v in old])                    # (D_p, 4^p)
+        for c, (_, v) in enumerate(new):
+            T[:, :, c] = Vo @ v.reshape(4, n_old).T            # site p is the slowest digit
+        A[p] = T
+    for k in range(1, L - l - 1):
+        p = L - k                                              # site of this step
+        new, old = rst[k], rst[k - 1]
+        Vo = np.stack([v for _, v in old])                    # (D_{p+1}, 4^(k-1))
+        T = np.zeros((len(new), 4, len(old)))
+        for r, (_, v) in enumerate(new):
+            T[r] = (Vo @ v.reshape(-1, 4)).T                   # site p is the fastest digit
+        R[p] = T
+    mps = MPSU1(L, t.N, t.two_s, l, lbonds, rbonds, A, R,
+                np.zeros((lbonds[l].dim, 4, 4, rbonds[l + 2].dim)))
+    VX = np.stack([v for _, v in lst[l]])                     # (D_X, 4^l)
+    VY = np.stack([v for _, v in rst[L - l - 2]])             # (D_Y, 4^(L-l-2))
+    nX = 4 ** l
+    cols = []
+    for (la, lb) in t.labels:
+        ma = dict(t.cand_a)[la]
+        mb = dict(t.cand_b)[lb]
+        psi = np.zeros((VX.shape[0], 4, 4, VY.shape[0]))
+        for ia in range(ma.s + 1):
+            two_ma = ma.s - 2 * ia
+            two_mb = t.two_s - two_ma
+            if abs(two_mb) > mb.s or (mb.s - two_mb) % 2:
+                continue
+            c = cg(ma.s, two_ma, mb.s, two_mb, t.two_s, t.two_s)
+            if not c:
+                continue
+            alpha = VX @ ma.vec[ia].reshape(4, nX).T          # (D_X, 4): <x i | a, m_a>
+            beta = (VY @ mb.vec[(mb.s - two_mb) // 2].reshape(-1, 4)).T   # (4, D_Y): <j y | b, m_b>
+            psi += c * np.einsum("xi,jy->xijy", alpha, beta)
+        cols.append(mps.psi_to_flat(psi))
+    C = np.stack(cols, axis=1) if cols else np.zeros((len(mps.psi_to_flat()), 0))
+    return mps, C

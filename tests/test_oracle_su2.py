@@ -68,3 +68,27 @@ def test_truncated_tangent_space(L, N, two_s, l, cap):
     # H_eff psi by the definition equals the matrix on a random vector
     psi = np.random.default_rng(2).normal(size=P.shape[1])
     assert np.abs(t.heff(f, psi) - Heff @ psi).max() < 1e-10
+
+
+@pytest.mark.parametrize("L,N,two_s,l,cap", [(6, 6, 0, 2, 2), (7, 7, 1, 2, 2), (7, 5, 1, 3, 2)])
+def test_su2_space_as_u1_mps_matches_operator_oracle(L, N, two_s, l, cap):
+    """The SU(2) space written as a U(1) MPS (bond states = all M components): the
+    Clebsch-Gordan map C is an isometry, the U(1) expansion of every SU(2) basis state is
+    its determinant vector, and sigma of the plain SU(2) definition equals C^T applied to
+    the operator-based U(1) oracle's sigma (a separately written code path)."""
+    from oracle.dmrgu1 import DMRGU1
+    from oracle.mpssu2 import to_u1
+    from oracle.mpsu1 import Projector
+    t = TangentSU2(L, N, two_s, l, cap=cap, seed=5)
+    mps, C = to_u1(t)
+    assert np.abs(C.T @ C - np.eye(C.shape[1])).max() < 1e-13
+    pr = Projector(mps, t.space)
+    for k in range(C.shape[1]):
+        assert np.abs(pr.apply(mps.psi_from_flat(C[:, k])) - t.P[:, k]).max() < 1e-13
+    h, V = q.make_integrals(L, 11)
+    f = FCI(h, V, N, two_s)
+    psi = np.random.default_rng(3).normal(size=C.shape[1])
+    s_su2 = t.heff(f, psi)
+    s_u1 = DMRGU1(h, V, N, two_s).sigma(mps, mps.psi_from_flat(C @ psi))
+    s_via = C.T @ mps.psi_to_flat(s_u1)
+    assert np.linalg.norm(s_su2 - s_via) <= 1e-12 * np.linalg.norm(s_su2)
