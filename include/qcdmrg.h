@@ -251,6 +251,23 @@ int qcdmrg_apply_heff_noalloc(qcdmrg_ctx* ctx, const void* psi, void* sigma, voi
  */
 int qcdmrg_rdm1(qcdmrg_ctx* ctx, double* gamma);
 
+/*
+ * Spin-summed two-particle density matrix of the current MPS state,
+ *   Gamma_pqrs = <Psi|E_pq E_rs - delta_qr E_ps|Psi> / <Psi|Psi>
+ * (L^4 row-major, caller-allocated), averaged over the 8 index permutations
+ * that leave a chemist-notation integral (pq|rs) invariant. With the
+ * Hamiltonian's 1/2 sum V_pqrs (E_pq E_rs - delta_qr E_ps), 1/2 Gamma is the
+ * gradient dE/dV at fixed wavefunction for an 8-fold symmetric V, the 2-RDM
+ * CASSCF orbital optimisation needs (DMRG-SCF of the paper's New benchmark
+ * system section). Computed by exact linearity in V: for each permutation
+ * orbit the environment is rebuilt with h = 0 and unit integrals on that
+ * orbit, and <H_eff> at the centre gives half the orbit's sum of Gamma; that
+ * is L^4/8 environment builds, meant for small active spaces. Any centre.
+ * The context's integrals and environment are restored before returning.
+ * Errors: ESTATE (no environment), EINVAL, ENOMEM, ECUDA.
+ */
+int qcdmrg_rdm2(qcdmrg_ctx* ctx, double* gamma2);
+
 /* Diagonal of H_eff at the centre (psi layout, n = psi size), as used by the
  * Davidson preconditioner: sum over terms of c_t diag(O_L) (x) diag(O_R)
  * restricted to diagonal quantum-number blocks. */

@@ -77,7 +77,7 @@ EXPORTS = [
     "qcdmrg_get_bond", "qcdmrg_get_psi", "qcdmrg_check_device", "qcdmrg_davidson",
     "qcdmrg_truncate", "qcdmrg_move_center", "qcdmrg_sweep", "qcdmrg_heff_diag",
     "qcdmrg_apply_heff_noalloc", "qcdmrg_graph_create", "qcdmrg_graph_launch",
-    "qcdmrg_graph_info", "qcdmrg_graph_destroy", "qcdmrg_rdm1", "qcdmrg_set_psi",
+    "qcdmrg_graph_info", "qcdmrg_graph_destroy", "qcdmrg_rdm1", "qcdmrg_rdm2", "qcdmrg_set_psi",
 ]
 
 _lib = None
@@ -122,6 +122,7 @@ def load(path=None):
     lib.qcdmrg_graph_info.argtypes = [P, dp, ctypes.POINTER(ctypes.c_int)]
     lib.qcdmrg_graph_destroy.argtypes = [P]
     lib.qcdmrg_rdm1.argtypes = [P, dp]
+    lib.qcdmrg_rdm2.argtypes = [P, dp]
     lib.qcdmrg_set_psi.argtypes = [P, dp, ctypes.c_size_t]
     lib.qcdmrg_sweep.argtypes = [P, ctypes.POINTER(SweepOpts), ctypes.POINTER(SweepReport)]
     for f in EXPORTS:
@@ -245,6 +246,13 @@ class Context:
     def rdm1(self, L):
         g = np.empty((L, L))
         self._check(self.lib.qcdmrg_rdm1(self.h, _dptr(g)))
+        return g
+
+    def rdm2(self, L):
+        """Spin-summed 2-RDM, averaged over the 8-fold permutations of (pq|rs)
+        (L^4/8 environment builds: small active spaces)."""
+        g = np.empty((L, L, L, L))
+        self._check(self.lib.qcdmrg_rdm2(self.h, _dptr(g)))
         return g
 
     def heff_diag(self):

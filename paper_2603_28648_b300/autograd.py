@@ -3,8 +3,10 @@
 E(psi, h, V) = <psi| H_eff(h, V) |psi> / <psi|psi> at the context's centre.
 Backward: dE/dpsi = 2 (H_eff psi - E psi) / <psi|psi> (one H_eff psi in the
 library), dE/dh_pq = gamma_pq, the spin-summed one-particle density matrix
-of the state (qcdmrg_rdm1), the quantity CASSCF orbital gradients are built
-from. The 2-RDM (dE/dV) is not provided by this version of the library.
+of the state (qcdmrg_rdm1), and dE/dV_pqrs = 1/2 Gamma_pqrs, the spin-summed
+2-RDM averaged over the 8 permutations of (pq|rs) (qcdmrg_rdm2, the gradient
+for an 8-fold symmetric V) -- the quantities CASSCF orbital gradients are
+built from.
 """
 
 import torch
@@ -36,12 +38,13 @@ class DMRGEnergy(torch.autograd.Function):
     @staticmethod
     def backward(fctx, gE):
         psi, sig, E, nn = fctx.saved_tensors
-        dpsi = dh = None
+        dpsi = dh = dV = None
         if fctx.needs_input_grad[0]:
             dpsi = 2.0 * (sig - E * psi) / nn * gE
         if fctx.needs_input_grad[1]:
             g = fctx.context.rdm1(fctx.L)
             dh = torch.as_tensor(g, dtype=torch.float64) * gE.detach().cpu()
         if fctx.needs_input_grad[2]:
-            raise NotImplementedError("dE/dV (the 2-RDM) is not provided by this version")
-        return dpsi, dh, None, None, None
+            G = fctx.context.rdm2(fctx.L)
+            dV = 0.5 * torch.as_tensor(G, dtype=torch.float64) * gE.detach().cpu()
+        return dpsi, dh, dV, None, None

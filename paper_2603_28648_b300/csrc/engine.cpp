@@ -8,6 +8,7 @@
 #include <cmath>
 #include <mutex>
 #include <stdexcept>
+#include <array>
 #include <tuple>
 
 namespace qd {
@@ -853,6 +854,52 @@ std::vector<double> Engine::rdm1() {
       if (!t.empty()) g[(size_t)p * L + q] = expect(t) / nrm;
     }
   return g;
+}
+
+std::vector<double> Engine::rdm2() {
+  // At fixed MPS the energy is linear in V: with h = 0, e_core = 0 and V the
+  // unit tensor on one permutation orbit {pqrs, qprs, pqsr, qpsr, rspq, srpq,
+  // rsqp, srqp}, <H_eff> = 1/2 sum over the orbit's distinct elements of
+  // Gamma. Each element of the orbit receives the orbit average.
+  if (!have_env) throw StateError("build_env first");
+  const int64_t n = lay.size;
+  const double nrm = ex->dot(dpsi, dpsi, n);
+  if (!(nrm > 0)) throw std::runtime_error("zero wavefunction");
+  const Integrals saved = I;
+  const size_t L4 = (size_t)L * L * L * L;
+  auto at = [&](int p, int q, int r, int s) { return (((size_t)p * L + q) * L + r) * L + s; };
+  std::vector<double> G(L4, 0.0);
+  uint64_t sig = ex->alloc(std::max<int64_t>(1, n));
+  try {
+    I.h.assign((size_t)L * L, 0.0);
+    I.ecore = 0.0;
+    for (int p = 0; p < L; ++p)
+      for (int q = 0; q < L; ++q)
+        for (int r = 0; r < L; ++r)
+          for (int s = 0; s < L; ++s) {
+            const std::array<std::array<int, 4>, 8> perm = {{{p, q, r, s}, {q, p, r, s}, {p, q, s, r}, {q, p, s, r},
+                                                             {r, s, p, q}, {s, r, p, q}, {r, s, q, p}, {s, r, q, p}}};
+            std::vector<std::array<int, 4>> orbit(perm.begin(), perm.end());
+            std::sort(orbit.begin(), orbit.end());
+            orbit.erase(std::unique(orbit.begin(), orbit.end()), orbit.end());
+            if (orbit.front() != perm[0]) continue;  // not the orbit's smallest member
+            I.V.assign(L4, 0.0);
+            for (auto& e : orbit) I.V[at(e[0], e[1], e[2], e[3])] = 1.0;
+            build_env();
+            heff(dpsi, sig, pr->stream(), 0);
+            const double e = ex->dot(dpsi, sig, n) / nrm;
+            for (auto& x : orbit) G[at(x[0], x[1], x[2], x[3])] = 2.0 * e / (double)orbit.size();
+          }
+  } catch (...) {
+    I = saved;
+    ex->release(sig);
+    build_env();
+    throw;
+  }
+  I = saved;
+  ex->release(sig);
+  build_env();
+  return G;
 }
 
 }  // namespace qd
