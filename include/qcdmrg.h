@@ -186,6 +186,33 @@ int qcdmrg_import_mps(qcdmrg_ctx* ctx, const qcdmrg_mps_desc* desc, const double
  */
 int qcdmrg_init_mps(qcdmrg_ctx* ctx, int D, uint64_t seed, int center);
 
+/*
+ * Copy the current MPS out in the layout qcdmrg_import_mps reads (after sweeps
+ * and centre moves too): *L, *center, bond_nsec (L+1 ints; bond center+1 has
+ * no sectors), bond_sec ((n, two_sz, dim) triples, *n_sec of them), data (the
+ * left site tensors U_q [(x, i) rows, kept states], the right site tensors V_q
+ * [kept states, (j, y) columns], each site's product sectors in label order,
+ * then the two-site wavefunction; *n_data doubles). Every output pointer may
+ * be NULL; call once with bond_sec and data NULL to learn *n_sec and *n_data.
+ * The MPS of the paper's Method section (Eq. (mps)) around its two-site
+ * centre; no counterpart of the file format in the paper. Errors: ESTATE (no
+ * MPS), EINVAL (a buffer shorter than needed: sec_cap ints, cap doubles).
+ */
+int qcdmrg_export_mps(qcdmrg_ctx* ctx, int* L, int* center, int* bond_nsec, int* bond_sec, int sec_cap,
+                      double* data, size_t cap, int* n_sec, size_t* n_data);
+
+/*
+ * Checkpoint: write the integrals, the target and the MPS (export layout) to
+ * a binary file (magic "QCDMRGC1", seven int64 sizes, e_core, h, V, bond
+ * sector counts and triples, data; native byte order). Restore: read such a
+ * file into a context, replacing its integrals, target and MPS; call
+ * qcdmrg_build_env afterwards. Errors: EIO (open, short read or write, not a
+ * checkpoint), ESTATE (checkpoint without integrals or target), and those of
+ * qcdmrg_load_integrals / qcdmrg_import_mps on restore.
+ */
+int qcdmrg_checkpoint(qcdmrg_ctx* ctx, const char* path);
+int qcdmrg_restore(qcdmrg_ctx* ctx, const char* path);
+
 /* Sectors of bond b of the current MPS as (n, two_sz, dim) triples; sec may be
  * NULL to query *nsec only; cap is the length of sec in ints. */
 int qcdmrg_get_bond(const qcdmrg_ctx* ctx, int bond, int* nsec, int* sec, int cap);

@@ -78,6 +78,7 @@ EXPORTS = [
     "qcdmrg_truncate", "qcdmrg_move_center", "qcdmrg_sweep", "qcdmrg_heff_diag",
     "qcdmrg_apply_heff_noalloc", "qcdmrg_graph_create", "qcdmrg_graph_launch",
     "qcdmrg_graph_info", "qcdmrg_graph_destroy", "qcdmrg_rdm1", "qcdmrg_rdm2", "qcdmrg_set_psi",
+    "qcdmrg_export_mps", "qcdmrg_checkpoint", "qcdmrg_restore",
 ]
 
 _lib = None
@@ -123,6 +124,10 @@ def load(path=None):
     lib.qcdmrg_graph_destroy.argtypes = [P]
     lib.qcdmrg_rdm1.argtypes = [P, dp]
     lib.qcdmrg_rdm2.argtypes = [P, dp]
+    lib.qcdmrg_export_mps.argtypes = [P, ip, ip, ip, ip, ctypes.c_int, dp, ctypes.c_size_t, ip,
+                                      ctypes.POINTER(ctypes.c_size_t)]
+    lib.qcdmrg_checkpoint.argtypes = [P, ctypes.c_char_p]
+    lib.qcdmrg_restore.argtypes = [P, ctypes.c_char_p]
     lib.qcdmrg_set_psi.argtypes = [P, dp, ctypes.c_size_t]
     lib.qcdmrg_sweep.argtypes = [P, ctypes.POINTER(SweepOpts), ctypes.POINTER(SweepReport)]
     for f in EXPORTS:
@@ -247,6 +252,26 @@ class Context:
         g = np.empty((L, L))
         self._check(self.lib.qcdmrg_rdm1(self.h, _dptr(g)))
         return g
+
+    def export_mps(self):
+        """(L, center, bond_nsec, bond_sec, data) in the layout import_mps reads."""
+        L, c, ns, nd = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
+        self._check(self.lib.qcdmrg_export_mps(self.h, ctypes.byref(L), ctypes.byref(c), None, None, 0, None, 0,
+                                               ctypes.byref(ns), ctypes.byref(nd)))
+        nsec = np.zeros(L.value + 1, dtype=np.int32)
+        sec = np.zeros(max(1, 3 * ns.value), dtype=np.int32)
+        data = np.zeros(nd.value)
+        ipt = ctypes.POINTER(ctypes.c_int)
+        self._check(self.lib.qcdmrg_export_mps(self.h, ctypes.byref(L), ctypes.byref(c),
+                                               nsec.ctypes.data_as(ipt), sec.ctypes.data_as(ipt), sec.size,
+                                               _dptr(data), data.size, ctypes.byref(ns), ctypes.byref(nd)))
+        return L.value, c.value, nsec, sec[:3 * ns.value], data
+
+    def checkpoint(self, path):
+        self._check(self.lib.qcdmrg_checkpoint(self.h, os.fsencode(path)))
+
+    def restore(self, path):
+        self._check(self.lib.qcdmrg_restore(self.h, os.fsencode(path)))
 
     def rdm2(self, L):
         """Spin-summed 2-RDM, averaged over the 8-fold permutations of (pq|rs)

@@ -2,6 +2,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <memory>
 #include <stdexcept>
@@ -217,6 +218,149 @@ int qcdmrg_import_mps(qcdmrg_ctx* ctx, const qcdmrg_mps_desc* d, const double* d
     E.set_psi_host(std::vector<double>(data + off, data + off + lay.size));
     return QCDMRG_OK;
   });
+}
+
+namespace {
+
+// The current MPS in the layout qcdmrg_import_mps reads: sector triples of
+// bonds 0..center and center+2..L (bond center+1 has none), the left site
+// tensors U_q, the right site tensors V_q (product-sector order), then psi.
+struct HostMps {
+  int L = 0, center = -1;
+  std::vector<int> nsec, sec;
+  std::vector<double> data;
+};
+
+HostMps export_host(qcdmrg_ctx* ctx) {
+  Engine& E = ctx->eng;
+  if (E.center < 0) throw Fail{QCDMRG_ESTATE, "no MPS"};
+  HostMps M;
+  M.L = E.L;
+  M.center = E.center;
+  const int L = E.L, c = E.center;
+  for (int b = 0; b <= L; ++b) {
+    const bool have = b <= c || b >= c + 2;
+    const Basis& B = E.bonds[b];
+    M.nsec.push_back(have ? B.nsec() : 0);
+    if (!have) continue;
+    for (int i = 0; i < B.nsec(); ++i) {
+      M.sec.push_back(B.q[i].n);
+      M.sec.push_back(B.q[i].s);
+      M.sec.push_back(B.dim[i]);
+    }
+  }
+  auto put_site = [&](int p, const Basis& from, bool left, const Basis& to) {
+    ProdBasis pb = make_prod(from, left);
+    for (int q = 0; q < pb.prod.nsec(); ++q) {
+      const int t = to.find(pb.prod.q[q]);
+      if (t < 0) continue;
+      if (q >= (int)E.site_off[p].size() || E.site_off[p][q] < 0)
+        throw Fail{QCDMRG_ESTATE, "site tensor without a stored sector"};
+      const int64_t cnt = (int64_t)pb.prod.dim[q] * to.dim[t];
+      const size_t at = M.data.size();
+      M.data.resize(at + (size_t)cnt);
+      ctx->be.ex->download(M.data.data() + at, E.site[p] + 8ull * (uint64_t)E.site_off[p][q], cnt);
+    }
+  };
+  for (int p = 0; p < c; ++p) put_site(p, E.bonds[p], true, E.bonds[p + 1]);
+  for (int p = c + 2; p < L; ++p) put_site(p, E.bonds[p + 1], false, E.bonds[p]);
+  std::vector<double> psi = E.get_psi_host();
+  M.data.insert(M.data.end(), psi.begin(), psi.end());
+  return M;
+}
+
+}  // namespace
+
+int qcdmrg_export_mps(qcdmrg_ctx* ctx, int* L, int* center, int* bond_nsec, int* bond_sec, int sec_cap,
+                      double* data, size_t cap, int* n_sec, size_t* n_data) {
+  return guard(ctx, [&]() {
+    HostMps M = export_host(ctx);
+    if (L) *L = M.L;
+    if (center) *center = M.center;
+    if (n_sec) *n_sec = (int)(M.sec.size() / 3);
+    if (n_data) *n_data = M.data.size();
+    if (bond_nsec) std::copy(M.nsec.begin(), M.nsec.end(), bond_nsec);
+    if (bond_sec) {
+      if (sec_cap < (int)M.sec.size()) throw Fail{QCDMRG_EINVAL, "sector buffer too small"};
+      std::copy(M.sec.begin(), M.sec.end(), bond_sec);
+    }
+    if (data) {
+      if (cap < M.data.size()) throw Fail{QCDMRG_EINVAL, "data buffer too small"};
+      std::copy(M.data.begin(), M.data.end(), data);
+    }
+    return QCDMRG_OK;
+  });
+}
+
+int qcdmrg_checkpoint(qcdmrg_ctx* ctx, const char* path) {
+  return guard(ctx, [&]() {
+    if (!path) throw Fail{QCDMRG_EINVAL, "null path"};
+    if (!ctx->have_int || !ctx->have_target) throw Fail{QCDMRG_ESTATE, "no integrals or target"};
+    HostMps M = export_host(ctx);
+    const Engine& E = ctx->eng;
+    FILE* f = std::fopen(path, "wb");
+    if (!f) throw Fail{QCDMRG_EIO, std::string("cannot open ") + path};
+    const char magic[8] = {'Q', 'C', 'D', 'M', 'R', 'G', 'C', '1'};
+    const int64_t hdr[7] = {E.I.L, E.N, E.two_s, M.center, (int64_t)M.nsec.size(), (int64_t)M.sec.size(),
+                            (int64_t)M.data.size()};
+    bool ok = std::fwrite(magic, 1, 8, f) == 8 && std::fwrite(hdr, sizeof(int64_t), 7, f) == 7 &&
+              std::fwrite(&E.I.ecore, sizeof(double), 1, f) == 1 &&
+              std::fwrite(E.I.h.data(), sizeof(double), E.I.h.size(), f) == E.I.h.size() &&
+              std::fwrite(E.I.V.data(), sizeof(double), E.I.V.size(), f) == E.I.V.size() &&
+              std::fwrite(M.nsec.data(), sizeof(int), M.nsec.size(), f) == M.nsec.size() &&
+              std::fwrite(M.sec.data(), sizeof(int), M.sec.size(), f) == M.sec.size() &&
+              std::fwrite(M.data.data(), sizeof(double), M.data.size(), f) == M.data.size();
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) throw Fail{QCDMRG_EIO, std::string("write failed: ") + path};
+    return QCDMRG_OK;
+  });
+}
+
+int qcdmrg_restore(qcdmrg_ctx* ctx, const char* path) {
+  if (!ctx) return QCDMRG_EINVAL;
+  int rc = guard(ctx, [&]() {
+    if (!path) throw Fail{QCDMRG_EINVAL, "null path"};
+    return QCDMRG_OK;
+  });
+  if (rc != QCDMRG_OK) return rc;
+  std::vector<double> h, V, data;
+  std::vector<int> nsec, sec;
+  int64_t hdr[7] = {0, 0, 0, 0, 0, 0, 0};
+  double ecore = 0.0;
+  rc = guard(ctx, [&]() {
+    FILE* f = std::fopen(path, "rb");
+    if (!f) throw Fail{QCDMRG_EIO, std::string("cannot open ") + path};
+    char magic[8];
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "QCDMRGC1", 8) == 0 &&
+              std::fread(hdr, sizeof(int64_t), 7, f) == 7;
+    const int64_t L = hdr[0];
+    ok = ok && L >= 2 && L <= 512 && hdr[4] == L + 1 && hdr[5] >= 0 && hdr[5] % 3 == 0 && hdr[5] <= (int64_t)1 << 30 &&
+         hdr[6] >= 0 && hdr[6] <= (int64_t)1 << 40;
+    if (ok) {
+      h.resize((size_t)(L * L));
+      V.resize((size_t)(L * L * L * L));
+      nsec.resize((size_t)hdr[4]);
+      sec.resize((size_t)hdr[5]);
+      data.resize((size_t)hdr[6]);
+      ok = std::fread(&ecore, sizeof(double), 1, f) == 1 &&
+           std::fread(h.data(), sizeof(double), h.size(), f) == h.size() &&
+           std::fread(V.data(), sizeof(double), V.size(), f) == V.size() &&
+           std::fread(nsec.data(), sizeof(int), nsec.size(), f) == nsec.size() &&
+           std::fread(sec.data(), sizeof(int), sec.size(), f) == sec.size() &&
+           std::fread(data.data(), sizeof(double), data.size(), f) == data.size();
+    }
+    std::fclose(f);
+    if (!ok) throw Fail{QCDMRG_EIO, std::string("not a qcdmrg checkpoint or truncated: ") + path};
+    return QCDMRG_OK;
+  });
+  if (rc != QCDMRG_OK) return rc;
+  rc = qcdmrg_load_integrals(ctx, (int)hdr[0], h.data(), V.data(), ecore);
+  if (rc == QCDMRG_OK) rc = qcdmrg_set_target(ctx, (int)hdr[1], (int)hdr[2]);
+  if (rc == QCDMRG_OK) {
+    qcdmrg_mps_desc d{(int)hdr[0], (int)hdr[3], nsec.data(), sec.data()};
+    rc = qcdmrg_import_mps(ctx, &d, data.data(), data.size());
+  }
+  return rc;
 }
 
 int qcdmrg_init_mps(qcdmrg_ctx* ctx, int D, uint64_t seed, int center) {
