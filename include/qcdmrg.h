@@ -235,6 +235,27 @@ int qcdmrg_build_env(qcdmrg_ctx* ctx);
 int qcdmrg_psi_size(const qcdmrg_ctx* ctx, size_t* n);
 
 /*
+ * Block layout of the two-site wavefunction psi[x, i, j, y] (the flat order of
+ * every psi and sigma array of this interface): for each sub-block, in order,
+ * 8 ints (x n, x two_sz, i, j, y n, y two_sz, rows = dim x, cols = dim y);
+ * sub-blocks follow each other, each rows x cols row-major. blocks may be NULL
+ * to query *nblocks and *nelem only; cap is its length in ints. The centre of
+ * the MPS of the paper's Method section (Eq. (mps)). Errors: ESTATE, EINVAL.
+ */
+int qcdmrg_psi_layout(const qcdmrg_ctx* ctx, int* blocks, int cap, int* nblocks, size_t* nelem);
+
+/*
+ * Energy of the current two-site wavefunction at fixed MPS and its gradients
+ * (host arrays, any of them NULL to skip): E = <psi|H_eff|psi>/<psi|psi> (FP64
+ * product), dpsi = dE/dpsi = 2 (H_eff psi - E psi)/<psi|psi> (psi size),
+ * gamma1 = dE/dh (L*L, as qcdmrg_rdm1: needs the centre at (L-2, L-1)),
+ * gamma2 = 2 dE/dV for 8-fold symmetric V (L^4, as qcdmrg_rdm2: L^4/8
+ * environment builds). The derivatives the paper's DMRG-SCF needs (New
+ * benchmark system section). Errors: ESTATE, EINVAL, ENOMEM, ECUDA.
+ */
+int qcdmrg_energy_grad(qcdmrg_ctx* ctx, double* energy, double* dpsi, double* gamma1, double* gamma2);
+
+/*
  * sigma = H_eff psi on host arrays of psi_size elements (layout above).
  * precision: one of QCDMRG_FP64, _TF32, _BF16, _BF16X3. Errors: ESTATE (no
  * environment), EINVAL, ETIMEOUT (a bounded wait of a tensor-core kernel gave

@@ -78,7 +78,8 @@ EXPORTS = [
     "qcdmrg_truncate", "qcdmrg_move_center", "qcdmrg_sweep", "qcdmrg_heff_diag",
     "qcdmrg_apply_heff_noalloc", "qcdmrg_graph_create", "qcdmrg_graph_launch",
     "qcdmrg_graph_info", "qcdmrg_graph_destroy", "qcdmrg_rdm1", "qcdmrg_rdm2", "qcdmrg_set_psi",
-    "qcdmrg_export_mps", "qcdmrg_checkpoint", "qcdmrg_restore",
+    "qcdmrg_export_mps", "qcdmrg_checkpoint", "qcdmrg_restore", "qcdmrg_psi_layout",
+    "qcdmrg_energy_grad",
 ]
 
 _lib = None
@@ -127,6 +128,8 @@ def load(path=None):
     lib.qcdmrg_export_mps.argtypes = [P, ip, ip, ip, ip, ctypes.c_int, dp, ctypes.c_size_t, ip,
                                       ctypes.POINTER(ctypes.c_size_t)]
     lib.qcdmrg_checkpoint.argtypes = [P, ctypes.c_char_p]
+    lib.qcdmrg_psi_layout.argtypes = [P, ip, ctypes.c_int, ip, ctypes.POINTER(ctypes.c_size_t)]
+    lib.qcdmrg_energy_grad.argtypes = [P, dp, dp, dp, dp]
     lib.qcdmrg_restore.argtypes = [P, ctypes.c_char_p]
     lib.qcdmrg_set_psi.argtypes = [P, dp, ctypes.c_size_t]
     lib.qcdmrg_sweep.argtypes = [P, ctypes.POINTER(SweepOpts), ctypes.POINTER(SweepReport)]
@@ -266,6 +269,25 @@ class Context:
                                                nsec.ctypes.data_as(ipt), sec.ctypes.data_as(ipt), sec.size,
                                                _dptr(data), data.size, ctypes.byref(ns), ctypes.byref(nd)))
         return L.value, c.value, nsec, sec[:3 * ns.value], data
+
+    def psi_layout(self):
+        """Sub-blocks of psi in flat order: rows of (x n, x 2Sz, i, j, y n, y 2Sz, rows, cols)."""
+        nb, ne = ctypes.c_int(), ctypes.c_size_t()
+        self._check(self.lib.qcdmrg_psi_layout(self.h, None, 0, ctypes.byref(nb), ctypes.byref(ne)))
+        out = np.zeros((max(1, nb.value), 8), dtype=np.int32)
+        self._check(self.lib.qcdmrg_psi_layout(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), out.size,
+                                               ctypes.byref(nb), ctypes.byref(ne)))
+        return out[:nb.value]
+
+    def energy_grad(self, L, dpsi=True, gamma1=False, gamma2=False):
+        """(E, dE/dpsi or None, gamma (L x L) or None, Gamma (L^4) or None) of the current state."""
+        e = ctypes.c_double()
+        d = np.empty(self.psi_size()) if dpsi else None
+        g1 = np.empty((L, L)) if gamma1 else None
+        g2 = np.empty((L, L, L, L)) if gamma2 else None
+        ptr = lambda a: _dptr(a) if a is not None else None
+        self._check(self.lib.qcdmrg_energy_grad(self.h, ctypes.byref(e), ptr(d), ptr(g1), ptr(g2)))
+        return e.value, d, g1, g2
 
     def checkpoint(self, path):
         self._check(self.lib.qcdmrg_checkpoint(self.h, os.fsencode(path)))

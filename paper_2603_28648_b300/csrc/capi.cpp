@@ -520,6 +520,74 @@ int qcdmrg_psi_size(const qcdmrg_ctx* ctx, size_t* n) {
   return QCDMRG_OK;
 }
 
+int qcdmrg_psi_layout(const qcdmrg_ctx* cctx, int* blocks, int cap, int* nblocks, size_t* nelem) {
+  qcdmrg_ctx* ctx = const_cast<qcdmrg_ctx*>(cctx);
+  return guard(ctx, [&]() {
+    const Engine& E = ctx->eng;
+    if (E.center < 0) throw Fail{QCDMRG_ESTATE, "no MPS"};
+    const Basis& X = E.bonds[E.center];
+    const Basis& Y = E.bonds[E.center + 2];
+    ProdBasis a = make_prod(X, true), b = make_prod(Y, false);
+    PsiLayout lay = make_psi_layout(a, b, QN{E.N, E.two_s});
+    if (nblocks) *nblocks = (int)lay.blks.size();
+    if (nelem) *nelem = (size_t)lay.size;
+    if (blocks) {
+      if (cap < 8 * (int)lay.blks.size()) throw Fail{QCDMRG_EINVAL, "block buffer too small"};
+      int k = 0;
+      for (const auto& bk : lay.blks) {
+        blocks[k++] = X.q[bk.x].n;
+        blocks[k++] = X.q[bk.x].s;
+        blocks[k++] = bk.i;
+        blocks[k++] = bk.j;
+        blocks[k++] = Y.q[bk.y].n;
+        blocks[k++] = Y.q[bk.y].s;
+        blocks[k++] = bk.rows;
+        blocks[k++] = bk.cols;
+      }
+    }
+    return QCDMRG_OK;
+  });
+}
+
+int qcdmrg_energy_grad(qcdmrg_ctx* ctx, double* energy, double* dpsi, double* gamma1, double* gamma2) {
+  return guard(ctx, [&]() {
+    Engine& E = ctx->eng;
+    if (!E.have_env) throw Fail{QCDMRG_ESTATE, "build_env first"};
+    if (gamma1 && E.center != E.L - 2)
+      throw Fail{QCDMRG_ESTATE, "the one-particle density matrix needs the centre at (L-2, L-1)"};
+    Executor& ex = *ctx->be.ex;
+    const int64_t n = E.lay.size;
+    uint64_t sig = ex.alloc(std::max<int64_t>(1, n));
+    double e = 0.0;
+    try {
+      E.heff(E.dpsi, sig, ctx->be.pr->stream(), 0);
+      const double nn = ex.dot(E.dpsi, E.dpsi, n);
+      if (!(nn > 0)) throw Fail{QCDMRG_EINVAL, "zero wavefunction"};
+      e = ex.dot(E.dpsi, sig, n) / nn;
+      if (dpsi) {
+        // dE/dpsi = 2 (H psi - E psi) / <psi|psi>
+        ex.axpby(sig, -e, E.dpsi, 1.0, n);
+        ex.scale(sig, 2.0 / nn, n);
+        ex.download(dpsi, sig, n);
+      }
+    } catch (...) {
+      ex.release(sig);
+      throw;
+    }
+    ex.release(sig);
+    if (energy) *energy = e;
+    if (gamma1) {
+      std::vector<double> g = E.rdm1();
+      std::copy(g.begin(), g.end(), gamma1);
+    }
+    if (gamma2) {
+      std::vector<double> g = E.rdm2();
+      std::copy(g.begin(), g.end(), gamma2);
+    }
+    return QCDMRG_OK;
+  });
+}
+
 static bool valid_precision(int p) {
   return p == QCDMRG_FP64 || p == QCDMRG_TF32 || p == QCDMRG_BF16 || p == QCDMRG_BF16X3;
 }
