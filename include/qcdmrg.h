@@ -362,9 +362,8 @@ int qcdmrg_check_device(qcdmrg_ctx* ctx);
 
 /*
  * Batched H_eff psi in one CUDA graph: all quantum-number blocks of one or
- * several independent H_eff psi products in one replay (the many-problem
- * workloads of the paper's Numerical procedure section run one after another
- * otherwise). The H_eff psi of each context (memset of sigma plus its
+ * several independent H_eff psi products in one replay, instead of one
+ * product after another. The H_eff psi of each context (memset of sigma plus its
  * grouped-GEMM launches) is captured once, contexts as parallel branches,
  * with psi[i] and sigma[i] (device arrays of each context's psi size) baked
  * into the graph; qcdmrg_graph_launch replays it on a stream. The contexts'
