@@ -191,6 +191,21 @@ def sample_flops(m, h, V):
     return f
 
 
+def max_over_ranks(values, dist, device):
+    """Element-wise maximum over the ranks of per-rank seconds (the slowest replica
+    sets the job's time)."""
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def replica_throughput(flops_per_step, seconds_per_step, world):
+    """Whole-job TFLOP/s of `world` independent replicas, each doing flops_per_step in
+    at most seconds_per_step (the maximum over ranks)."""
+    return world * flops_per_step / seconds_per_step / 1e12
+
+
 def cores():
     return len(os.sched_getaffinity(0))
 
@@ -320,13 +335,11 @@ def run_ours(args, rank, world, local):
     e2e_t = e0.elapsed_time(e1) / 1e3
     energy = energies[args.precision]
     if dist:
-        tt = torch.tensor([elapsed, e2e_t], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed, e2e_t = tt.tolist()
+        elapsed, e2e_t = max_over_ranks([elapsed, e2e_t], dist, "cuda")
     peak = fp64_peak_tflops(torch)
     per_step = elapsed / args.steps
-    value = world * flops / per_step / 1e12
-    e2e_val = world * flops / (e2e_t / args.steps) / 1e12
+    value = replica_throughput(flops, per_step, world)
+    e2e_val = replica_throughput(flops, e2e_t / args.steps, world)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
