@@ -1,7 +1,7 @@
 """MPS export and checkpoint/restore through the C ABI: an imported MPS comes back
 bit for bit; after a sweep (moved centre, truncated bonds) the exported MPS imported
 into a new context, and a checkpoint restored into a new context, give the same
-H_eff psi as the original context."""
+H_eff psi as the original context; missing, truncated and foreign files are file errors."""
 import numpy as np
 import pytest
 
@@ -61,7 +61,17 @@ def test_export_and_checkpoint_after_a_sweep(tmp_path):
     ctx3.build_env()
     assert np.array_equal(ctx3.psi(), psi)
     assert np.linalg.norm(ctx3.apply_heff(psi) - ref) <= 1e-13 * np.linalg.norm(ref)
-    with pytest.raises(qd.QcdmrgError):
+    with pytest.raises(qd.QcdmrgError) as e:
         ctx3.restore(str(tmp_path / "missing.qcdmrg"))
+    assert e.value.code == -7
+    # a truncated checkpoint and a file that is not one are file errors, not crashes
+    raw = open(path, "rb").read()
+    for name, blob in (("short.qcdmrg", raw[: len(raw) // 2]), ("other.qcdmrg", b"NOTACHECKPOINT" + raw[14:])):
+        bad = str(tmp_path / name)
+        with open(bad, "wb") as f:
+            f.write(blob)
+        with pytest.raises(qd.QcdmrgError) as e:
+            ctx3.restore(bad)
+        assert e.value.code == -7
     for c in (ctx, ctx2, ctx3):
         c.close()
