@@ -1,0 +1,299 @@
+// Test-only host execution of the library's H_eff task lists, without a GPU.
+//
+// The library's host planner (rules, renormalization, H_eff task lists, tiled
+// work items) runs unchanged with an executor that keeps every buffer in host
+// memory and executes each segmented-GEMM task list with plain loops. The
+// driver imports an MPS (the C-ABI import layout), builds the environment,
+// applies the FP64 task lists to psi, and separately evaluates the tiled work
+// items of the tensor-core path in FP64 (views, panels, term scalars, T tiles,
+// no bf16 rounding), so that both plans can be compared with the oracle.
+//
+// usage: host_exec in.bin out.bin
+//   in : int64 L, N, two_sz, center, nsec_len (= L+1), sec_len, data_len;
+//        h (L*L), V (L^4) doubles; bond_nsec, bond_sec int32; data doubles
+//   out: sigma of the FP64 task lists, then sigma of the tiled work items
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <stdexcept>
+#include <vector>
+
+#include "engine.hpp"
+#include "tiled.hpp"
+
+using namespace qd;
+
+namespace {
+
+struct HostEx : Executor {
+  std::map<uint64_t, std::vector<double>> bufs;  // base address -> storage
+  uint64_t tmp_base = 0;
+  int64_t tmp_n = 0, live = 0;
+  uint64_t alloc(int64_t n) override {
+    std::vector<double> v((size_t)std::max<int64_t>(1, n), 0.0);
+    const uint64_t p = reinterpret_cast<uint64_t>(v.data());
+    live += (int64_t)v.size() * 8;
+    bufs[p] = std::move(v);
+    return p;
+  }
+  void release(uint64_t p) override {
+    auto it = bufs.find(p);
+    if (it != bufs.end()) {
+      live -= (int64_t)it->second.size() * 8;
+      bufs.erase(it);
+    }
+  }
+  uint64_t tmp(int64_t n) override {
+    if (n > tmp_n) {
+      if (tmp_base) release(tmp_base);
+      tmp_base = alloc(n);
+      tmp_n = n;
+    }
+    return tmp_base;
+  }
+  static double* ptr(uint64_t p) { return reinterpret_cast<double*>(p); }
+  void exec(const Launch& l, uint64_t psi, uint64_t sig) {
+    const uint64_t base[4] = {0, psi, sig, tmp_base};
+    auto res = [&](uint64_t v, int buf) { return buf == 0 ? ptr(v) : ptr(base[buf] + v * 8); };
+    for (const Prob& p : l.probs) {
+      std::vector<double> acc((size_t)p.m * p.n, 0.0);
+      for (int s = p.seg0; s < p.seg0 + p.nseg; ++s) {
+        const Seg& g = l.segs[s];
+        const bool aid = g.a == 0 && g.abuf == 0, bid = g.b == 0 && g.bbuf == 0;
+        if (aid) {
+          if (bid) {
+            for (int r = 0; r < std::min(p.m, p.n); ++r) acc[(size_t)r * p.n + r] += g.sc;
+          } else {
+            const double* B = res(g.b, g.bbuf);
+            for (int r = 0; r < p.m; ++r)
+              for (int c = 0; c < p.n; ++c)
+                acc[(size_t)r * p.n + c] += g.sc * (g.tb ? B[(size_t)c * g.ldb + r] : B[(size_t)r * g.ldb + c]);
+          }
+          continue;
+        }
+        if (bid) throw std::runtime_error("task list: identity B with a stored A");
+        const double* A = res(g.a, g.abuf);
+        const double* B = res(g.b, g.bbuf);
+        for (int r = 0; r < p.m; ++r)
+          for (int k = 0; k < g.k; ++k) {
+            const double a = g.sc * (g.ta ? A[(size_t)k * g.lda + r] : A[(size_t)r * g.lda + k]);
+            if (a == 0.0) continue;
+            for (int c = 0; c < p.n; ++c)
+              acc[(size_t)r * p.n + c] += a * (g.tb ? B[(size_t)c * g.ldb + k] : B[(size_t)k * g.ldb + c]);
+          }
+      }
+      double* C = res(p.c, p.cbuf);
+      for (int r = 0; r < p.m; ++r)
+        for (int c = 0; c < p.n; ++c) {
+          double& d = C[(size_t)r * p.ldc + c];
+          d = p.beta ? d + acc[(size_t)r * p.n + c] : acc[(size_t)r * p.n + c];
+        }
+    }
+  }
+  void run(const Launch& l, uint64_t psi, uint64_t sig) override { exec(l, psi, sig); }
+  void upload(uint64_t dst, const double* h, int64_t n) override { std::memcpy(ptr(dst), h, (size_t)n * 8); }
+  void download(double* h, uint64_t src, int64_t n) override { std::memcpy(h, ptr(src), (size_t)n * 8); }
+  void zero(uint64_t p, int64_t n) override { std::fill(ptr(p), ptr(p) + n, 0.0); }
+  void randn(uint64_t, int64_t, uint64_t) override { throw std::runtime_error("not needed"); }
+  void orthonormal_cols(uint64_t, int, int) override { throw std::runtime_error("not needed"); }
+  double dot(uint64_t x, uint64_t y, int64_t n) override {
+    double s = 0;
+    for (int64_t i = 0; i < n; ++i) s += ptr(x)[i] * ptr(y)[i];
+    return s;
+  }
+  void scale(uint64_t x, double a, int64_t n) override {
+    for (int64_t i = 0; i < n; ++i) ptr(x)[i] *= a;
+  }
+  void axpby(uint64_t y, double a, uint64_t x, double b, int64_t n) override {
+    for (int64_t i = 0; i < n; ++i) ptr(y)[i] = a * ptr(x)[i] + b * ptr(y)[i];
+  }
+  void precond(uint64_t, uint64_t, uint64_t, double, double, int64_t) override { throw std::runtime_error("not needed"); }
+  void eigh(uint64_t, int, double*) override { throw std::runtime_error("not needed"); }
+  void copy(uint64_t d, uint64_t s, int64_t n) override { std::memcpy(ptr(d), ptr(s), (size_t)n * 8); }
+  uint64_t host_alloc(int64_t) override { throw std::runtime_error("not needed"); }
+  void host_free(uint64_t) override {}
+  void d2h(uint64_t, uint64_t, int64_t) override {}
+  void h2d_async(uint64_t, uint64_t, int64_t) override {}
+  void copies_join() override {}
+  double copies_wait_seconds() override { return 0.0; }
+  int64_t live_bytes() const override { return live; }
+};
+
+struct HostRunner : PreparedRunner {
+  HostEx* ex;
+  std::vector<Launch> prepared;
+  explicit HostRunner(HostEx* e) : ex(e) {}
+  int prepare(const Launch& l) override {
+    prepared.push_back(l);
+    return (int)prepared.size() - 1;
+  }
+  void drop_prepared() override { prepared.clear(); }
+  void run_prepared(int h, uint64_t psi, uint64_t sig, void*, int prec) override {
+    if (prec != 0) throw std::runtime_error("host execution runs the FP64 task lists only");
+    ex->exec(prepared.at(h), psi, sig);
+  }
+  int take_error() override { return 0; }
+  const void* prepared_handle(int) const override { return nullptr; }
+  void* stream() override { return nullptr; }
+  void sync(void*) override {}
+  void zero_async(uint64_t p, int64_t n, void*) override { ex->zero(p, n); }
+  int64_t bytes_allocated() const override { return ex->live; }
+  void prepare_tiled(const TiledPlan&, int) override {}
+  void set_tiled_items(const TiledPlan&) override {}
+  int tiled_planes() const override { return 0; }
+  double time_tiled(uint64_t, uint64_t, int, int) override { return 0.0; }
+  void run_tiled(uint64_t, uint64_t, void*, int) override { throw std::runtime_error("not here"); }
+};
+
+// value of element (r, c) of a view (scaled, possibly transposed, or a scaled identity)
+double view_at(const TView& v, int r, int c, const double* psi) {
+  if (r >= v.rows || c >= v.cols) return 0.0;
+  if (v.src == 0 && v.buf == 0) return r == c ? v.scale : 0.0;
+  const double* s = v.buf ? psi + v.src : reinterpret_cast<const double*>(v.src);
+  return v.scale * (v.tr ? s[(size_t)c * v.ld + r] : s[(size_t)r * v.ld + c]);
+}
+
+// sigma of the tiled work items evaluated in FP64
+std::vector<double> tiled_sigma(const HeffPlan& plan, const PsiLayout& lay, const double* psi, const TileCfg& cfg) {
+  const TiledPlan T = plan_tiled(plan, lay, cfg);
+  std::map<int64_t, const TView*> A, B, Ps;  // arena offset of a view -> view
+  for (auto& v : T.avw) A[v.dst] = &v;
+  for (auto& v : T.bvw) B[v.dst] = &v;
+  for (auto& v : T.psivw) Ps[v.dst] = &v;
+  std::map<int64_t, std::vector<double>> Tt;  // T arena offset -> T_t^T (ntot x mtot, row-major)
+  std::map<int64_t, int> Tcols;
+  for (const K1Item& it : T.i1) {
+    const int c8 = tiled_c8(it.k);
+    const TView* pv = Ps.at(it.b - (int64_t)it.np * (TP_B / 8) * c8 * 128);
+    for (int vi = it.v0; vi < it.v0 + it.nv; ++vi) {
+      const K1View& w = T.v1[vi];
+      const TView* rv = B.at(w.a - (int64_t)w.mp * (TP_A / 8) * c8 * 128);
+      auto& M = Tt[w.tout];
+      if (M.empty()) {
+        M.assign((size_t)w.ntot * it.mtot, 0.0);
+        Tcols[w.tout] = it.mtot;
+      }
+      for (int r = 0; r < w.mrows; ++r) {
+        const int R = w.mp * TP_A + r;
+        for (int x = 0; x < it.nrows; ++x) {
+          const int X = it.np * TP_B + x;
+          double s = 0;
+          for (int y = 0; y < it.k; ++y) s += view_at(*rv, R, y, psi) * view_at(*pv, X, y, psi);
+          M[(size_t)R * it.mtot + X] = w.osc * s;
+        }
+      }
+    }
+  }
+  std::vector<double> sig((size_t)lay.size, 0.0);
+  for (const K2Item& it : T.i2)
+    for (int s = it.s0; s < it.s1; ++s) {
+      const K2Seg& g = T.s2[s];
+      const TView* av = A.at(g.a);
+      const auto& M = Tt.at(g.b);
+      const int K = Tcols.at(g.b);
+      for (int r = 0; r < it.mrows; ++r)
+        for (int c = 0; c < it.nrows; ++c) {
+          const int R = it.mp * TP_A + r, C = it.np * TP_B + c;
+          double acc = 0;
+          for (int k = 0; k < g.k; ++k) acc += view_at(*av, R, k, psi) * M[(size_t)C * K + k];
+          sig[(size_t)it.out + (size_t)R * it.ldc + C] += acc;
+        }
+    }
+  return sig;
+}
+
+template <class T>
+void rd(FILE* f, T* p, size_t n) {
+  if (std::fread(p, sizeof(T), n, f) != n) throw std::runtime_error("short input");
+}
+
+}  // namespace
+
+int main(int argc, char** argv) {
+  if (argc < 3) return 2;
+  try {
+    FILE* f = std::fopen(argv[1], "rb");
+    if (!f) throw std::runtime_error("cannot open input");
+    int64_t hd[7];
+    rd(f, hd, 7);
+    const int L = (int)hd[0];
+    std::vector<double> h((size_t)L * L), V((size_t)L * L * L * L), data((size_t)hd[6]);
+    std::vector<int> nsec((size_t)hd[4]), sec((size_t)hd[5]);
+    rd(f, h.data(), h.size());
+    rd(f, V.data(), V.size());
+    rd(f, nsec.data(), nsec.size());
+    rd(f, sec.data(), sec.size());
+    rd(f, data.data(), data.size());
+    std::fclose(f);
+
+    HostEx ex;
+    HostRunner pr(&ex);
+    Engine E;
+    E.ex = &ex;
+    E.pr = &pr;
+    E.tmp_budget = (int64_t)(2e9 / 8);
+    E.I.L = L;
+    E.I.h = h;
+    E.I.V = V;
+    E.N = (int)hd[1];
+    E.two_s = (int)hd[2];
+    const int c = (int)hd[3];
+    // import, as the C ABI does: bond sectors, site tensors per product sector, psi
+    std::vector<Basis> bonds(L + 1);
+    int pos = 0;
+    for (int b = 0; b <= L; ++b)
+      for (int s = 0; s < nsec[b]; ++s, ++pos) bonds[b].add(QN{sec[3 * pos], sec[3 * pos + 1]}, sec[3 * pos + 2]);
+    size_t off = 0;
+    E.site.assign(L, 0);
+    E.site_off.assign(L, {});
+    E.site_nb.assign(L, {});
+    auto take_site = [&](int p, const Basis& from, bool left, const Basis& to) {
+      ProdBasis pb = make_prod(from, left);
+      std::vector<int64_t> so(pb.prod.nsec(), -1);
+      std::vector<int> nb(pb.prod.nsec(), -1);
+      int64_t tot = 0;
+      for (int q = 0; q < pb.prod.nsec(); ++q) {
+        const int t = to.find(pb.prod.q[q]);
+        if (t < 0) continue;
+        so[q] = tot;
+        nb[q] = t;
+        tot += (int64_t)pb.prod.dim[q] * to.dim[t];
+      }
+      const uint64_t dev = ex.alloc(tot);
+      ex.upload(dev, data.data() + off, tot);
+      off += (size_t)tot;
+      E.site[p] = dev;
+      E.site_off[p] = so;
+      E.site_nb[p] = nb;
+    };
+    for (int p = 0; p < c; ++p) take_site(p, bonds[p], true, bonds[p + 1]);
+    for (int p = c + 2; p < L; ++p) take_site(p, bonds[p + 1], false, bonds[p]);
+    E.bonds = bonds;
+    E.L = L;
+    E.center = c;
+    E.set_psi_host(std::vector<double>(data.begin() + (long)off, data.end()));
+    E.build_env();
+    const int64_t n = E.lay.size;
+    if ((size_t)n != data.size() - off) throw std::runtime_error("psi layout differs from the input");
+    const uint64_t sig = ex.alloc(n);
+    E.heff(E.dpsi, sig, nullptr, 0);
+    std::vector<double> s64((size_t)n);
+    ex.download(s64.data(), sig, n);
+    TileCfg cfg;
+    cfg.kmax = 8;  // small: many split stage-2 items
+    cfg.width = 128;
+    std::vector<double> st = tiled_sigma(E.plan, E.lay, reinterpret_cast<const double*>(E.dpsi), cfg);
+    FILE* o = std::fopen(argv[2], "wb");
+    if (!o) throw std::runtime_error("cannot open output");
+    std::fwrite(s64.data(), 8, s64.size(), o);
+    std::fwrite(st.data(), 8, st.size(), o);
+    std::fclose(o);
+  } catch (const std::exception& e) {
+    std::fprintf(stderr, "host_exec: %s\n", e.what());
+    return 1;
+  }
+  return 0;
+}
