@@ -8,10 +8,13 @@
 // items of the tensor-core path in FP64 (views, panels, term scalars, T tiles,
 // no bf16 rounding), so that both plans can be compared with the oracle.
 //
-// usage: host_exec in.bin out.bin
+// usage: host_exec in.bin out.bin                       (one H_eff psi, both plans)
+//        host_exec in.bin out.bin sweep D nsweeps tol     (full FP64 sweeps)
 //   in : int64 L, N, two_sz, center, nsec_len (= L+1), sec_len, data_len;
 //        h (L*L), V (L^4) doubles; bond_nsec, bond_sec int32; data doubles
-//   out: sigma of the FP64 task lists, then sigma of the tiled work items
+//   out: sigma of the FP64 task lists, then sigma of the tiled work items; or
+//        the energy of the last optimisation of each sweep (the sweeps start by
+//        moving the centre to bond 0, as qcdmrg_sweep does)
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -19,6 +22,7 @@
 #include <cstring>
 #include <map>
 #include <stdexcept>
+#include <string>
 #include <vector>
 
 #include "engine.hpp"
@@ -110,8 +114,63 @@ struct HostEx : Executor {
   void axpby(uint64_t y, double a, uint64_t x, double b, int64_t n) override {
     for (int64_t i = 0; i < n; ++i) ptr(y)[i] = a * ptr(x)[i] + b * ptr(y)[i];
   }
-  void precond(uint64_t, uint64_t, uint64_t, double, double, int64_t) override { throw std::runtime_error("not needed"); }
-  void eigh(uint64_t, int, double*) override { throw std::runtime_error("not needed"); }
+  void precond(uint64_t t, uint64_t r, uint64_t d, double theta, double fl, int64_t n) override {
+    for (int64_t i = 0; i < n; ++i) {
+      double den = ptr(d)[i] - theta;
+      if (std::fabs(den) < fl) den = den < 0 ? -fl : fl;
+      ptr(t)[i] = ptr(r)[i] / den;
+    }
+  }
+  // symmetric eigendecomposition by cyclic Jacobi rotations: A (n x n,
+  // column-major) becomes the eigenvectors, w the ascending eigenvalues
+  void eigh(uint64_t a, int n, double* w) override {
+    double* A = ptr(a);
+    std::vector<double> M((size_t)n * n), Vv((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) M[(size_t)i * n + j] = 0.5 * (A[(size_t)j * n + i] + A[(size_t)i * n + j]);
+    for (int i = 0; i < n; ++i) Vv[(size_t)i * n + i] = 1.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+      double off = 0, tot = 0;
+      for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+          const double x = M[(size_t)i * n + j] * M[(size_t)i * n + j];
+          tot += x;
+          if (i != j) off += x;
+        }
+      if (off <= 1e-30 * std::max(tot, 1e-300)) break;
+      for (int p = 0; p < n; ++p)
+        for (int q = p + 1; q < n; ++q) {
+          const double apq = M[(size_t)p * n + q];
+          if (apq == 0.0) continue;
+          const double app = M[(size_t)p * n + p], aqq = M[(size_t)q * n + q];
+          const double tau = (aqq - app) / (2.0 * apq);
+          const double t = (tau >= 0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1.0 + tau * tau));
+          const double c = 1.0 / std::sqrt(1.0 + t * t), s = t * c;
+          for (int k = 0; k < n; ++k) {  // rows p, q
+            const double mpk = M[(size_t)p * n + k], mqk = M[(size_t)q * n + k];
+            M[(size_t)p * n + k] = c * mpk - s * mqk;
+            M[(size_t)q * n + k] = s * mpk + c * mqk;
+          }
+          for (int k = 0; k < n; ++k) {  // columns p, q
+            const double mkp = M[(size_t)k * n + p], mkq = M[(size_t)k * n + q];
+            M[(size_t)k * n + p] = c * mkp - s * mkq;
+            M[(size_t)k * n + q] = s * mkp + c * mkq;
+          }
+          for (int k = 0; k < n; ++k) {
+            const double vkp = Vv[(size_t)k * n + p], vkq = Vv[(size_t)k * n + q];
+            Vv[(size_t)k * n + p] = c * vkp - s * vkq;
+            Vv[(size_t)k * n + q] = s * vkp + c * vkq;
+          }
+        }
+    }
+    std::vector<int> ord(n);
+    for (int i = 0; i < n; ++i) ord[i] = i;
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return M[(size_t)x * n + x] < M[(size_t)y * n + y]; });
+    for (int j = 0; j < n; ++j) {
+      w[j] = M[(size_t)ord[j] * n + ord[j]];
+      for (int i = 0; i < n; ++i) A[(size_t)j * n + i] = Vv[(size_t)i * n + ord[j]];
+    }
+  }
   void copy(uint64_t d, uint64_t s, int64_t n) override { std::memcpy(ptr(d), ptr(s), (size_t)n * 8); }
   uint64_t host_alloc(int64_t) override { throw std::runtime_error("not needed"); }
   void host_free(uint64_t) override {}
@@ -276,6 +335,30 @@ int main(int argc, char** argv) {
     E.center = c;
     E.set_psi_host(std::vector<double>(data.begin() + (long)off, data.end()));
     E.build_env();
+    if (argc >= 7 && std::string(argv[3]) == "sweep") {
+      const int D = std::atoi(argv[4]), nsw = std::atoi(argv[5]);
+      DavOpts o;
+      o.tol = std::atof(argv[6]);
+      while (E.center > 0) E.truncate_move(1 << 30, -1, 1e-28);
+      std::vector<double> energies;
+      for (int sw = 0; sw < nsw; ++sw) {
+        double e = 0.0;
+        for (int l = 0; l < L - 2; ++l) {
+          e = E.davidson(o).energy;
+          E.truncate_move(D, +1, 0.0);
+        }
+        for (int l = L - 2; l > 0; --l) {
+          e = E.davidson(o).energy;
+          E.truncate_move(D, -1, 0.0);
+        }
+        energies.push_back(e);
+      }
+      FILE* o2 = std::fopen(argv[2], "wb");
+      if (!o2) throw std::runtime_error("cannot open output");
+      std::fwrite(energies.data(), 8, energies.size(), o2);
+      std::fclose(o2);
+      return 0;
+    }
     const int64_t n = E.lay.size;
     if ((size_t)n != data.size() - off) throw std::runtime_error("psi layout differs from the input");
     const uint64_t sig = ex.alloc(n);

@@ -32,17 +32,21 @@ def host_exec(tmp_path_factory):
     return out
 
 
-def _run(exe, tmp, mps, h, V):
+def _write(path, mps, h, V):
     from oracle.mpsu1 import export_abi
     nsec, sec, data = export_abi(mps)
-    fin, fout = str(tmp / "in.bin"), str(tmp / "out.bin")
-    with open(fin, "wb") as f:
+    with open(path, "wb") as f:
         f.write(struct.pack("<7q", mps.L, mps.N, mps.two_sz, mps.center, len(nsec), len(sec), len(data)))
         f.write(np.ascontiguousarray(h, "<f8").tobytes())
         f.write(np.ascontiguousarray(V, "<f8").tobytes())
         f.write(np.asarray(nsec, "<i4").tobytes())
         f.write(np.asarray(sec, "<i4").tobytes())
         f.write(np.asarray(data, "<f8").tobytes())
+
+
+def _run(exe, tmp, mps, h, V):
+    fin, fout = str(tmp / "in.bin"), str(tmp / "out.bin")
+    _write(fin, mps, h, V)
     r = subprocess.run([exe, fin, fout], capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr
     out = np.fromfile(fout, "<f8")
@@ -75,3 +79,35 @@ def test_library_task_lists_on_an_su2_state(host_exec, tmp_path):
     ref = t.heff(FCI(h, V, 7, 1), psi)
     for s in (s64, st):
         assert np.linalg.norm(C.T @ s - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def _sweeps(exe, tmp, mps, h, V, D, nsweeps):
+    fin, fout = str(tmp / "sw_in.bin"), str(tmp / "sw_out.bin")
+    _write(fin, mps, h, V)
+    r = subprocess.run([exe, fin, fout, "sweep", str(D), str(nsweeps), "1e-10"], capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0, r.stderr
+    return np.fromfile(fout, "<f8")
+
+
+@pytest.mark.parametrize("L,N,D,c,mps_seed,int_seed", [(6, 6, 8, 2, 3, 4), (7, 5, 12, 3, 5, 6)])
+def test_engine_sweeps_match_the_oracle(host_exec, tmp_path, L, N, D, c, mps_seed, int_seed):
+    from oracle.dmrgu1 import DMRGU1
+    from oracle.mpsu1 import MPSU1
+    two = N % 2
+    m = MPSU1.from_raw(q.random_mps_blocks(L, N, two, D, q.SYM_U1, mps_seed, c))
+    h, V = q.make_integrals(L, int_seed)
+    E = _sweeps(host_exec, tmp_path, m, h, V, D, 2)
+    Eo, _, _ = DMRGU1(h, V, N, two).sweeps(m, D, 2, tol=1e-12)
+    assert np.abs(E - np.array(Eo)).max() <= 1e-9
+
+
+def test_engine_sweeps_at_exact_bond_dimension_give_fci(host_exec, tmp_path):
+    from oracle.fci import FCI
+    from oracle.mpsu1 import MPSU1
+    L, N, D = 6, 6, 64
+    m = MPSU1.from_raw(q.random_mps_blocks(L, N, 0, D, q.SYM_U1, 3, 2))
+    h, V = q.make_integrals(L, 11)
+    E = _sweeps(host_exec, tmp_path, m, h, V, D, 2)
+    e0, _ = FCI(h, V, N, 0).ground_state()
+    assert abs(E[-1] - e0) <= 1e-9
