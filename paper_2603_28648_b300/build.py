@@ -10,7 +10,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 def build(verbose=False):
     out = os.path.join(HERE, "libqcdmrg.so")
-    cmd = (["nvcc", "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-shared"] + ARCH +
+    cmd = (["nvcc", "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-pthread", "-shared"] + ARCH +
            ["-Xptxas", "-v" if verbose else "-O3"] + [os.path.join(HERE, s) for s in SRC] +
            ["-o", out, "-lcudart", "-lcusolver"])
     subprocess.run(cmd, check=True, cwd=HERE)

@@ -20,6 +20,11 @@
 // A product O_X O_s on X (x) site acts as (O_X P_X^{p(O_s)}) (x) O_s; a
 // product O_s O_Y on site (x) Y as (O_s P_s^{p(O_Y)}) (x) O_Y.
 #include <algorithm>
+#include <atomic>
+#include <exception>
+#include <functional>
+#include <mutex>
+#include <thread>
 #include <cmath>
 #include <map>
 #include <unordered_map>
@@ -102,6 +107,33 @@ const Monos& monos() {
   return M;
 }
 
+// f(0..n-1) on up to 16 host threads (items are independent and write only
+// their own results); the first exception of any item is rethrown
+void parallel_for(size_t n, const std::function<void(size_t)>& f) {
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const unsigned nt = (unsigned)std::min<size_t>(std::min(hw, 16u), n / 32);
+  if (nt <= 1) {
+    for (size_t i = 0; i < n; ++i) f(i);
+    return;
+  }
+  std::atomic<size_t> next{0};
+  std::exception_ptr err;
+  std::mutex mu;
+  std::vector<std::thread> ts;
+  for (unsigned t = 0; t < nt; ++t)
+    ts.emplace_back([&]() {
+      try {
+        for (size_t i; (i = next.fetch_add(1)) < n;) f(i);
+      } catch (...) {
+        std::lock_guard<std::mutex> g(mu);
+        if (!err) err = std::current_exception();
+        next = n;
+      }
+    });
+  for (auto& t : ts) t.join();
+  if (err) std::rethrow_exception(err);
+}
+
 struct Ctx {
   const EnvBlock& B;
   const Integrals& I;
@@ -113,7 +145,9 @@ struct Ctx {
     std::vector<Contrib> cs;
   };
   std::vector<Pending> pending;
-  Ctx(const EnvBlock& b, const Integrals& i, Enlarged& e) : B(b), I(i), E(e), pb(e.pb) {}
+  Ctx(const EnvBlock& b, const Integrals& i, Enlarged& e) : B(b), I(i), E(e), pb(e.pb) {
+    pending.reserve(16 + 8 * (size_t)i.L * i.L);  // complementary operators of one block
+  }
 
   const OpView* get(Key k) const {
     auto it = B.ops.find(k);
@@ -163,8 +197,8 @@ struct Ctx {
     if (!v.blocks.empty()) E.ops[k] = v;
   }
 
-  void materialize(Key k, const std::vector<Contrib>& cs, bool odd) {
-    pending.push_back({k, odd, cs});
+  void materialize(Key k, std::vector<Contrib>&& cs, bool odd) {
+    pending.push_back({k, odd, std::move(cs)});
   }
 
   // Group every pending operator's contributions by (site monomial, parity
@@ -176,7 +210,8 @@ struct Ctx {
     struct Group { Mat4 o; bool par; std::vector<Item> items; };
     struct Plan { std::vector<Group> groups; };
     std::vector<Plan> plans(pending.size());
-    for (size_t n = 0; n < pending.size(); ++n) {
+    // every pending operator is planned on its own (independent, any thread)
+    parallel_for(pending.size(), [&](size_t n) {
       int gi[16][2];                             // (monomial, par) -> group
       for (auto& row : gi) row[0] = row[1] = -1;
       std::vector<std::unordered_map<uintptr_t, int>> where;  // per group: (source, transposed) -> item
@@ -199,7 +234,7 @@ struct Ctx {
           else G[g].items[ins.first->second].coef += c.coef * x[k];
         }
       }
-    }
+    });
     // block lists of the sources (transposes built once)
     std::unordered_map<uintptr_t, std::vector<BRef>> blocks_of;
     auto blocks = [&](const OpView* src, bool T) -> const std::vector<BRef>& {
@@ -230,37 +265,77 @@ struct Ctx {
     uint64_t store = total ? ex.alloc(total) : 0;
     if (store) E.owned.push_back(store);
     Launch l;
-    std::map<std::pair<size_t, size_t>, std::vector<BRef>> summed;
-    for (auto& mt : mats) {
-      auto& grp = plans[mt.n].groups[mt.g];
-      // segments grouped by destination block, in item order within a block
-      std::vector<std::pair<std::pair<int, int>, Seg>> segs;
-      for (auto& itm : grp.items)
-        for (const BRef& b : blocks(itm.src, itm.T)) {
-          Seg s;
-          s.a = 0; s.abuf = B_ABS; s.k = b.rows; s.sc = itm.coef * b.sc;
-          if (b.ident()) { s.b = 0; s.bbuf = B_ABS; }
-          else { s.b = b.ptr; s.bbuf = B_ABS; s.ldb = b.ld; s.tb = b.tr ? 1 : 0; }
-          segs.push_back({{b.r, b.c}, s});
-        }
-      std::stable_sort(segs.begin(), segs.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
-      std::vector<BRef> refs;
-      size_t si = 0;
-      for (auto& kv : mt.blk) {
-        Prob p;
-        p.c = store + 8ull * kv.second.first; p.cbuf = B_ABS;
-        p.m = kv.second.second.first; p.n = kv.second.second.second; p.ldc = p.n; p.beta = 0;
-        p.seg0 = (int)l.segs.size();
-        const size_t s0 = si;
-        while (si < segs.size() && segs[si].first == kv.first) l.segs.push_back(segs[si++].second);
-        p.nseg = (int)(si - s0);
-        l.probs.push_back(p);
-        BRef r;
-        r.r = kv.first.first; r.c = kv.first.second; r.ptr = p.c;
-        r.rows = p.m; r.cols = p.n; r.ld = p.n; r.tr = false; r.sc = 1.0;
-        refs.push_back(r);
+    {
+      size_t nseg = 0, nprob = 0;
+      for (auto& mt : mats) {
+        nprob += mt.blk.size();
+        for (auto& itm : plans[mt.n].groups[mt.g].items) nseg += blocks(itm.src, itm.T).size();
       }
-      summed[{mt.n, mt.g}] = refs;
+      l.segs.reserve(nseg);
+      l.probs.reserve(nprob);
+    }
+    std::map<std::pair<size_t, size_t>, std::vector<BRef>> summed;
+    // block lists of every summed source, built here so that the parallel part
+    // below only reads the cache
+    for (auto& mt : mats)
+      for (auto& itm : plans[mt.n].groups[mt.g].items) blocks(itm.src, itm.T);
+    auto blocks_ro = [&](const OpView* src, bool T) -> const std::vector<BRef>& {
+      return blocks_of.at(reinterpret_cast<uintptr_t>(src) * 2 + (T ? 1 : 0));
+    };
+    // each summed group's problems, segments (grouped by destination block in
+    // key order, item order within a block) and block references, independently
+    struct Part {
+      std::vector<Seg> segs;
+      std::vector<Prob> probs;
+      std::vector<BRef> refs;
+    };
+    std::vector<Part> parts(mats.size());
+    parallel_for(mats.size(), [&](size_t mi) {
+      const Mat& mt = mats[mi];
+      const auto& grp = plans[mt.n].groups[mt.g];
+      Part& P = parts[mi];
+      std::map<std::pair<int, int>, int> kidx;
+      for (auto& kv : mt.blk) kidx.emplace(kv.first, (int)kidx.size());
+      std::vector<std::pair<int, Seg>> tmp;
+      for (auto& itm : grp.items)
+        for (const BRef& b : blocks_ro(itm.src, itm.T)) {
+          Seg sg;
+          sg.a = 0; sg.abuf = B_ABS; sg.k = b.rows; sg.sc = itm.coef * b.sc;
+          if (b.ident()) { sg.b = 0; sg.bbuf = B_ABS; }
+          else { sg.b = b.ptr; sg.bbuf = B_ABS; sg.ldb = b.ld; sg.tb = b.tr ? 1 : 0; }
+          tmp.push_back({kidx.at({b.r, b.c}), sg});
+        }
+      std::vector<int> start(kidx.size() + 1, 0);
+      for (auto& e : tmp) start[e.first + 1]++;
+      for (size_t i = 0; i < kidx.size(); ++i) start[i + 1] += start[i];
+      P.segs.resize(tmp.size());
+      {
+        std::vector<int> pos(start.begin(), start.end() - 1);
+        for (auto& e : tmp) P.segs[pos[e.first]++] = e.second;
+      }
+      int q = 0;
+      for (auto& kv : mt.blk) {
+        Prob pr;
+        pr.c = store + 8ull * kv.second.first; pr.cbuf = B_ABS;
+        pr.m = kv.second.second.first; pr.n = kv.second.second.second; pr.ldc = pr.n; pr.beta = 0;
+        pr.seg0 = start[q];   // relative to this part; shifted when the parts are joined
+        pr.nseg = start[q + 1] - start[q];
+        ++q;
+        P.probs.push_back(pr);
+        BRef r;
+        r.r = kv.first.first; r.c = kv.first.second; r.ptr = pr.c;
+        r.rows = pr.m; r.cols = pr.n; r.ld = pr.n; r.tr = false; r.sc = 1.0;
+        P.refs.push_back(r);
+      }
+    });
+    for (size_t mi = 0; mi < mats.size(); ++mi) {
+      const int base = (int)l.segs.size();
+      for (Prob pr : parts[mi].probs) {
+        pr.seg0 += base;
+        l.probs.push_back(pr);
+      }
+      l.segs.insert(l.segs.end(), parts[mi].segs.begin(), parts[mi].segs.end());
+      summed[{mats[mi].n, mats[mi].g}] = std::move(parts[mi].refs);
     }
     if (!l.empty()) ex.run(l, 0, 0);
     for (size_t n = 0; n < plans.size(); ++n) {
@@ -400,7 +475,7 @@ void enlarge(const EnvBlock& B, const Integrals& I, Executor& ex, Enlarged& E, d
           }
         }
       cs.push_back(C_(nullptr, false, site_three(I, m, sm), 1.0, true));
-      x.materialize(Key(F_S, m), cs, true);
+      x.materialize(Key(F_S, m), std::move(cs), true);
     }
     // H'
     {
@@ -435,7 +510,7 @@ void enlarge(const EnvBlock& B, const Integrals& I, Executor& ex, Enlarged& E, d
               for (int b = 0; b < 2; ++b) Q = Q + cre(a) * ann(b) * I.q(i, sm[a], sm[b], l);
             cs.push_back(C_(Bil, false, Q, 1.0, false));
           }
-      x.materialize(Key(F_H), cs, false);
+      x.materialize(Key(F_H), std::move(cs), false);
     }
   } else {
     const int c = B.cut - 1;      // site p = c, Y = [c+1, L)
@@ -463,7 +538,7 @@ void enlarge(const EnvBlock& B, const Integrals& I, Executor& ex, Enlarged& E, d
         for (int a = 0; a < 2; ++a)
           for (int b = 0; b < 2; ++b) P = P + ann(a) * ann(b) * (0.5 * I.w(i, j, sm[a], sm[b]));
         cs.push_back(C_(nullptr, false, P, 1.0, false));
-        x.materialize(Key(F_P, i, j), cs, false);
+        x.materialize(Key(F_P, i, j), std::move(cs), false);
       }
     // Q'_il, i, l < 2c
     for (int i = 0; i < mc; ++i)
@@ -483,7 +558,7 @@ void enlarge(const EnvBlock& B, const Integrals& I, Executor& ex, Enlarged& E, d
         for (int a = 0; a < 2; ++a)
           for (int b = 0; b < 2; ++b) Q = Q + cre(a) * ann(b) * I.q(i, sm[a], sm[b], l);
         cs.push_back(C_(nullptr, false, Q, 1.0, false));
-        x.materialize(Key(F_Q, i, l), cs, false);
+        x.materialize(Key(F_Q, i, l), std::move(cs), false);
       }
     // S'_m, m < 2c
     for (int m = 0; m < mc; ++m) {
@@ -509,7 +584,7 @@ void enlarge(const EnvBlock& B, const Integrals& I, Executor& ex, Enlarged& E, d
             if (w2 != 0.0) cs.push_back(C_(C, false, ann(a) * ann(b), w2, true));
           }
       cs.push_back(C_(nullptr, false, site_three(I, m, sm), 1.0, false));
-      x.materialize(Key(F_S, m), cs, true);
+      x.materialize(Key(F_S, m), std::move(cs), true);
     }
     // H'
     {
@@ -535,7 +610,7 @@ void enlarge(const EnvBlock& B, const Integrals& I, Executor& ex, Enlarged& E, d
       for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b)
           if (auto Q = x.get(Key(F_Q, sm[a], sm[b]))) cs.push_back(C_(Q, false, cre(a) * ann(b), 1.0, false));
-      x.materialize(Key(F_H), cs, false);
+      x.materialize(Key(F_H), std::move(cs), false);
     }
   }
   x.finish(ex);

@@ -27,7 +27,7 @@ def host_exec(tmp_path_factory):
     inc = ["-I", CSRC]
     if os.path.isdir("/usr/local/cuda/include"):
         inc += ["-I", "/usr/local/cuda/include"]
-    subprocess.run(["g++", "-O2", "-std=c++17"] + inc + [os.path.join(ROOT, "tests", "host_exec.cpp")] +
+    subprocess.run(["g++", "-O2", "-std=c++17", "-pthread"] + inc + [os.path.join(ROOT, "tests", "host_exec.cpp")] +
                    [os.path.join(CSRC, s) for s in HOST_SOURCES] + ["-o", out], check=True)
     return out
 

@@ -23,7 +23,7 @@ def checker(tmp_path_factory):
     cuda_inc = "/usr/local/cuda/include"
     if os.path.isdir(cuda_inc):
         inc += ["-I", cuda_inc]
-    cmd = (["g++", "-O2", "-std=c++17"] + inc + [os.path.join(ROOT, "tests", "planner_check.cpp")] +
+    cmd = (["g++", "-O2", "-std=c++17", "-pthread"] + inc + [os.path.join(ROOT, "tests", "planner_check.cpp")] +
            [os.path.join(CSRC, s) for s in HOST_SOURCES] + ["-o", out])
     subprocess.run(cmd, check=True)
     return out
