@@ -66,6 +66,13 @@ typedef struct {
                            section) */
   int autotune_off;     /* 1: the BF16 forms keep the default work-item shape instead of timing
                            the candidates on the first product of each problem-size class */
+  int pair_switch;      /* cut of the normal/complementary switch (0: off). Left blocks at cuts
+                           <= pair_switch and right blocks at cuts > pair_switch keep the normal
+                           pair operators A_kl, B_kl of their own modes; the others keep the
+                           complementary P_ij, Q_il of the modes across the cut. At L/2 this is
+                           the N/2 rule: the pairs are stored on the side with fewer modes,
+                           which halves the operator volume of a sweep environment. 0 keeps
+                           normal pairs on the left at every cut. Negative: QCDMRG_EINVAL */
 } qcdmrg_config;
 
 /*

@@ -95,6 +95,8 @@ int qcdmrg_create(qcdmrg_ctx** out, const qcdmrg_config* cfg) {
     if (cfg->hbm_budget_gb < 0) throw std::invalid_argument("hbm_budget_gb");
     c->eng.hbm_budget = (int64_t)(cfg->hbm_budget_gb * 1e9);
     c->eng.autotune = cfg->autotune_off == 0;
+    if (cfg->pair_switch < 0) throw std::invalid_argument("pair_switch");
+    c->eng.pair_switch = cfg->pair_switch;
   } catch (const std::invalid_argument&) {
     delete c;
     return QCDMRG_EINVAL;

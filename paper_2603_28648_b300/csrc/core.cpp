@@ -154,6 +154,7 @@ void renormalize(const Enlarged& E, const Basis& nb, const std::vector<int>& nb_
   const ProdBasis& pb = E.pb;
   const bool left = E.left;
   out.left = left;
+  out.normal = E.normal;
   out.basis = nb;
   out.ops.clear();
   // storage plan: every output block is allocated in one buffer
@@ -170,9 +171,14 @@ void renormalize(const Enlarged& E, const Basis& nb, const std::vector<int>& nb_
       auto key = std::make_pair(nq, nq2);
       if (!lay.count(key)) {
         lay[key] = total;
-        total += (int64_t)nb.dim[nq] * nb.dim[nq2];
+        if (!E.batched) total += (int64_t)nb.dim[nq] * nb.dim[nq2];
       }
     }
+    if (E.batched)  // sector order: operators with the same blocks get the same offsets
+      for (auto& e : lay) {
+        e.second = total;
+        total += (int64_t)nb.dim[e.first.first] * nb.dim[e.first.second];
+      }
   }
   uint64_t store = total ? ex.alloc(total) : 0;
   if (store) {
@@ -343,22 +349,45 @@ std::vector<CenterTerm> center_terms(const Enlarged& Lp, const Enlarged& Rp, con
     terms.push_back({S, false, C, false, -1.0});
     terms.push_back({S, true, C, true, 1.0});
   }
-  // 2 sum_{i<j} (A_ij P_ij + A_ij^+ P_ij^+) + sum_{il} B_il Q_il
-  for (int i = 0; i < 2 * c; ++i)
-    for (int j = i + 1; j < 2 * c; ++j) {
-      auto A = get(Lp, Key(F_A, i, j));
-      auto P = get(Rp, Key(F_P, i, j));
-      if (!A || !P) continue;
-      terms.push_back({A, false, P, false, 2.0});
-      terms.push_back({A, true, P, true, 2.0});
-    }
-  for (int i = 0; i < 2 * c; ++i)
-    for (int l = 0; l < 2 * c; ++l) {
-      auto B = get(Lp, Key(F_B, i, l));
-      auto Q = get(Rp, Key(F_Q, i, l));
-      if (!B || !Q) continue;
-      terms.push_back({B, false, Q, false, 1.0});
-    }
+  if (Lp.normal == Rp.normal)
+    throw std::logic_error("center_terms: exactly one enlarged block must hold normal pairs");
+  if (Lp.normal) {
+    // 2 sum_{i<j in L'} (A_ij P_ij + A_ij^+ P_ij^+) + sum_{il in L'} B_il Q_il
+    for (int i = 0; i < 2 * c; ++i)
+      for (int j = i + 1; j < 2 * c; ++j) {
+        auto A = get(Lp, Key(F_A, i, j));
+        auto P = get(Rp, Key(F_P, i, j));
+        if (!A || !P) continue;
+        terms.push_back({A, false, P, false, 2.0});
+        terms.push_back({A, true, P, true, 2.0});
+      }
+    for (int i = 0; i < 2 * c; ++i)
+      for (int l = 0; l < 2 * c; ++l) {
+        auto B = get(Lp, Key(F_B, i, l));
+        auto Q = get(Rp, Key(F_Q, i, l));
+        if (!B || !Q) continue;
+        terms.push_back({B, false, Q, false, 1.0});
+      }
+  } else {
+    // normal pairs on the right (both pair products are even, so the order of
+    // the factors is free): 2 sum_{i<j in R'} (P_ij A_ij + P_ij^+ A_ij^+)
+    // + sum_{jk in R'} Q_jk B_jk, with P, Q of L' indexed by modes of R'
+    for (int i = 2 * c; i < 2 * L; ++i)
+      for (int j = i + 1; j < 2 * L; ++j) {
+        auto P = get(Lp, Key(F_P, i, j));
+        auto A = get(Rp, Key(F_A, i, j));
+        if (!A || !P) continue;
+        terms.push_back({P, false, A, false, 2.0});
+        terms.push_back({P, true, A, true, 2.0});
+      }
+    for (int j = 2 * c; j < 2 * L; ++j)
+      for (int k = 2 * c; k < 2 * L; ++k) {
+        auto Q = get(Lp, Key(F_Q, j, k));
+        auto B = get(Rp, Key(F_B, j, k));
+        if (!B || !Q) continue;
+        terms.push_back({Q, false, B, false, 1.0});
+      }
+  }
   return terms;
 }
 

@@ -198,9 +198,23 @@ struct Contrib {
   bool par = false;
 };
 
+// Which side of a cut holds the two-index operators of its own modes. A block
+// with normal pairs keeps A_kl = a+_k a+_l and B_kl = a+_k a_l for k, l in the
+// block; a block with complementary pairs keeps P_ij and Q_il for i, j, l on
+// the other side of the cut. A left block at cut c has normal pairs while
+// c <= mid and a right block while c > mid, so that at every centre cut
+// exactly one of the two enlarged blocks holds normal pairs; mid = L keeps
+// them on the left everywhere, mid near L/2 puts them on the side with fewer
+// modes (the N/2 rule of the complementary-operator method).
+inline bool normal_pairs(bool left, int cut, int mid) { return left ? cut <= mid : cut > mid; }
+
 // Enlarged block: product basis and the views of its operators.
 struct Enlarged {
   bool left = true;
+  bool normal = true;       // pair operators: normal (A, B) or complementary (P, Q)
+  bool batched = false;     // set by the caller: wide sums of block operators run as GEMMs
+                            // over a coefficient matrix, and renormalized operators store
+                            // their blocks in sector order (equal strides across operators)
   int cut = 0;              // the enlarged block covers [0, cut) or [cut, L)
   ProdBasis pb;
   std::map<Key, OpView> ops;
@@ -210,6 +224,7 @@ struct Enlarged {
 // Renormalized block. Left block at cut c: sites [0, c); right: [c, L).
 struct EnvBlock {
   bool left = true;
+  bool normal = true;              // pair operators, as in Enlarged
   int cut = 0;
   Basis basis;
   std::map<Key, OpView> ops;
@@ -222,11 +237,14 @@ struct EnvBlock {
 // Sector rule of the initial MPS (left labels, bonds 0..L).
 std::vector<std::map<QN, int>> mps_structure(int L, int N, int two_s, int D);
 
-// Op-key list of a block at a cut (left-normal / right-complementary layout).
-std::vector<Key> block_keys(bool left, int cut, int L);
+// Op-key list of a block at a cut with normal or complementary pairs.
+std::vector<Key> block_keys(bool left, bool normal, int cut, int L);
 
-// Build the enlarged views from a renormalized block and one site.
-void enlarge(const EnvBlock& B, const Integrals& I, Executor& ex, Enlarged& out, double* flops);
+// Build the enlarged views from a renormalized block and one site. The
+// enlarged block holds normal pairs if `normal`; a block with normal pairs
+// can become complementary here (the switch), the reverse is not possible.
+void enlarge(const EnvBlock& B, const Integrals& I, Executor& ex, Enlarged& out, double* flops,
+             bool normal);
 
 // Renormalize enlarged operators with the new site tensor: for each product
 // sector that is kept, a dense matrix (left: [dim_prod x d_new], right:

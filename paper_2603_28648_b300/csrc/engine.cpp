@@ -230,9 +230,11 @@ void Engine::build_env() {
   clear_env();
   double fl = 0;
   lenv[0] = vacuum(true, 0);
+  lenv[0].normal = normal_at(true, 0);
   for (int p = 0; p < center; ++p) {
     Enlarged E;
-    enlarge(lenv[p], I, *ex, E, &fl);
+    E.batched = batched_sums();
+    enlarge(lenv[p], I, *ex, E, &fl, normal_at(true, p + 1));
     EnvBlock nb;
     nb.cut = p + 1;
     renormalize(E, bonds[p + 1], site_nb[p], site[p], site_off[p], *ex, nb, tmp_budget, &fl);
@@ -241,9 +243,11 @@ void Engine::build_env() {
     enforce_budget_build(p + 1, true);
   }
   renv[L] = vacuum(false, L);
+  renv[L].normal = normal_at(false, L);
   for (int p = L - 1; p >= center + 2; --p) {
     Enlarged E;
-    enlarge(renv[p + 1], I, *ex, E, &fl);
+    E.batched = batched_sums();
+    enlarge(renv[p + 1], I, *ex, E, &fl, normal_at(false, p));
     EnvBlock nb;
     nb.cut = p;
     renormalize(E, bonds[p], site_nb[p], site[p], site_off[p], *ex, nb, tmp_budget, &fl);
@@ -264,8 +268,9 @@ void Engine::prepare_center() {
   double fl = 0;
   ensure_resident(lenv.at(center));
   ensure_resident(renv.at(center + 2));
-  enlarge(lenv.at(center), I, *ex, Lp, &fl);
-  enlarge(renv.at(center + 2), I, *ex, Rp, &fl);
+  Lp.batched = Rp.batched = batched_sums();
+  enlarge(lenv.at(center), I, *ex, Lp, &fl, normal_at(true, center + 1));
+  enlarge(renv.at(center + 2), I, *ex, Rp, &fl, normal_at(false, center + 1));
   lay = make_psi_layout(Lp.pb, Rp.pb, QN{N, two_s});
   plan = plan_heff(Lp, Rp, lay, I, tmp_budget);
   ex->tmp(std::max<int64_t>(1, plan.tmp_elems));
@@ -819,6 +824,25 @@ std::vector<double> Engine::rdm1() {
   //   q < L-1 = p: a+_p a_q = -(a_q)_L' (a+_p)_R'
   //   p = q = L-1: 1 (x) a+_p a_p on the last site
   if (center != L - 2) throw StateError("the one-particle density matrix needs the centre at (L-2, L-1)");
+  if (!Lp.normal) {
+    // the blocks at this centre hold complementary pairs on the left: rebuild
+    // the environment with normal pairs on the left (the MPS is unchanged),
+    // take the density matrix there, and restore the switched environment
+    const int saved = pair_switch;
+    pair_switch = 0;
+    std::vector<double> g;
+    try {
+      build_env();
+      g = rdm1();
+    } catch (...) {
+      pair_switch = saved;
+      build_env();
+      throw;
+    }
+    pair_switch = saved;
+    build_env();
+    return g;
+  }
   const double nrm = ex->dot(dpsi, dpsi, lay.size);
   auto get = [](const Enlarged& E, Key k) -> const OpView* {
     auto it = E.ops.find(k);

@@ -38,6 +38,14 @@ struct Engine {
   Integrals I;
   int N = 0, two_s = 0, L = 0, center = -1;
   int64_t tmp_budget = 0;
+  // cut of the normal/complementary switch: left blocks at cuts <= pair_switch
+  // and right blocks at cuts > pair_switch hold normal pairs (0: normal pairs
+  // on the left at every cut)
+  int pair_switch = 0;
+  bool normal_at(bool left, int cut) const { return normal_pairs(left, cut, pair_switch > 0 ? pair_switch : L); }
+  // with the switch on, wide sums of stored operators run as GEMMs (the
+  // switching enlargement sums every pair operator of a block into each P', Q')
+  bool batched_sums() const { return pair_switch > 0; }
   // MPS: bonds (left labels for b <= center, right labels for b >= center+2),
   // site tensors (product-sector matrices) for every site except the centre pair
   std::vector<Basis> bonds;

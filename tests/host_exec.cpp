@@ -8,8 +8,12 @@
 // items of the tensor-core path in FP64 (views, panels, term scalars, T tiles,
 // no bf16 rounding), so that both plans can be compared with the oracle.
 //
+// Every launch is checked against the buffers it addresses. The environment
+// variable HOST_EXEC_PAIR_SWITCH sets the cut of the normal/complementary switch.
+//
 // usage: host_exec in.bin out.bin                       (one H_eff psi, both plans)
 //        host_exec in.bin out.bin sweep D nsweeps tol     (full FP64 sweeps)
+//        host_exec in.bin out.bin rdm1                    (1-RDM, centre at L-2)
 //   in : int64 L, N, two_sz, center, nsec_len (= L+1), sec_len, data_len;
 //        h (L*L), V (L^4) doubles; bond_nsec, bond_sec int32; data doubles
 //   out: sigma of the FP64 task lists, then sigma of the tiled work items; or
@@ -59,10 +63,23 @@ struct HostEx : Executor {
     return tmp_base;
   }
   static double* ptr(uint64_t p) { return reinterpret_cast<double*>(p); }
+  // the elements [q, q + last] must lie inside one live allocation
+  void inside(const double* q, int64_t last, const char* what) const {
+    const uint64_t a = reinterpret_cast<uint64_t>(q);
+    auto it = bufs.upper_bound(a);
+    if (last < 0 || it == bufs.begin()) throw std::runtime_error(std::string("task list: ") + what + " outside every buffer");
+    --it;
+    const int64_t first = (int64_t)(a - it->first);
+    if (first % 8 || first / 8 + last >= (int64_t)it->second.size())
+      throw std::runtime_error(std::string("task list: ") + what + " past the end of its buffer");
+  }
   void exec(const Launch& l, uint64_t psi, uint64_t sig) {
     const uint64_t base[4] = {0, psi, sig, tmp_base};
     auto res = [&](uint64_t v, int buf) { return buf == 0 ? ptr(v) : ptr(base[buf] + v * 8); };
     for (const Prob& p : l.probs) {
+      if (p.m <= 0 || p.n <= 0 || p.ldc < p.n) throw std::runtime_error("task list: empty or malformed problem");
+      if (p.seg0 < 0 || p.nseg < 0 || p.seg0 + p.nseg > (int)l.segs.size()) throw std::runtime_error("task list: segment range");
+      inside(res(p.c, p.cbuf), (int64_t)(p.m - 1) * p.ldc + p.n - 1, "C");
       std::vector<double> acc((size_t)p.m * p.n, 0.0);
       for (int s = p.seg0; s < p.seg0 + p.nseg; ++s) {
         const Seg& g = l.segs[s];
@@ -72,6 +89,7 @@ struct HostEx : Executor {
             for (int r = 0; r < std::min(p.m, p.n); ++r) acc[(size_t)r * p.n + r] += g.sc;
           } else {
             const double* B = res(g.b, g.bbuf);
+            inside(B, g.tb ? (int64_t)(p.n - 1) * g.ldb + p.m - 1 : (int64_t)(p.m - 1) * g.ldb + p.n - 1, "B of a gather");
             for (int r = 0; r < p.m; ++r)
               for (int c = 0; c < p.n; ++c)
                 acc[(size_t)r * p.n + c] += g.sc * (g.tb ? B[(size_t)c * g.ldb + r] : B[(size_t)r * g.ldb + c]);
@@ -81,6 +99,9 @@ struct HostEx : Executor {
         if (bid) throw std::runtime_error("task list: identity B with a stored A");
         const double* A = res(g.a, g.abuf);
         const double* B = res(g.b, g.bbuf);
+        if (g.k <= 0) throw std::runtime_error("task list: empty segment");
+        inside(A, g.ta ? (int64_t)(g.k - 1) * g.lda + p.m - 1 : (int64_t)(p.m - 1) * g.lda + g.k - 1, "A");
+        inside(B, g.tb ? (int64_t)(p.n - 1) * g.ldb + g.k - 1 : (int64_t)(g.k - 1) * g.ldb + p.n - 1, "B");
         for (int r = 0; r < p.m; ++r)
           for (int k = 0; k < g.k; ++k) {
             const double a = g.sc * (g.ta ? A[(size_t)k * g.lda + r] : A[(size_t)r * g.lda + k]);
@@ -294,6 +315,7 @@ int main(int argc, char** argv) {
     E.ex = &ex;
     E.pr = &pr;
     E.tmp_budget = (int64_t)(2e9 / 8);
+    if (const char* sw = std::getenv("HOST_EXEC_PAIR_SWITCH")) E.pair_switch = std::atoi(sw);
     E.I.L = L;
     E.I.h = h;
     E.I.V = V;
@@ -357,6 +379,14 @@ int main(int argc, char** argv) {
       if (!o2) throw std::runtime_error("cannot open output");
       std::fwrite(energies.data(), 8, energies.size(), o2);
       std::fclose(o2);
+      return 0;
+    }
+    if (argc >= 4 && std::string(argv[3]) == "rdm1") {
+      const std::vector<double> g = E.rdm1();
+      FILE* o3 = std::fopen(argv[2], "wb");
+      if (!o3) throw std::runtime_error("cannot open output");
+      std::fwrite(g.data(), 8, g.size(), o3);
+      std::fclose(o3);
       return 0;
     }
     const int64_t n = E.lay.size;

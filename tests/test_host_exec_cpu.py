@@ -2,7 +2,8 @@
 (complementary-operator rules, renormalization, centre plan) executed with plain loops,
 and the tiled work items of the tensor-core path evaluated in FP64 (views, panels, term
 scalars, T tiles, split stage-2 items), both against the oracle's sigma, on imported
-MPS of several shapes, edge centres included, and on the M-expansion of an SU(2) MPS.
+MPS of several shapes, edge centres included, and on the M-expansion of an SU(2) MPS; with
+the normal/complementary switch at several cuts as well. Every launch is bounds-checked.
 tests/host_exec.cpp holds the test-only host executor; the product path still needs CUDA."""
 import os
 import shutil
@@ -44,10 +45,14 @@ def _write(path, mps, h, V):
         f.write(np.asarray(data, "<f8").tobytes())
 
 
-def _run(exe, tmp, mps, h, V):
+def _env(switch):
+    return dict(os.environ, HOST_EXEC_PAIR_SWITCH=str(switch))
+
+
+def _run(exe, tmp, mps, h, V, switch=0):
     fin, fout = str(tmp / "in.bin"), str(tmp / "out.bin")
     _write(fin, mps, h, V)
-    r = subprocess.run([exe, fin, fout], capture_output=True, text=True, timeout=600)
+    r = subprocess.run([exe, fin, fout], capture_output=True, text=True, timeout=600, env=_env(switch))
     assert r.returncode == 0, r.stderr
     out = np.fromfile(fout, "<f8")
     n = len(out) // 2
@@ -81,11 +86,11 @@ def test_library_task_lists_on_an_su2_state(host_exec, tmp_path):
         assert np.linalg.norm(C.T @ s - ref) <= 1e-12 * np.linalg.norm(ref)
 
 
-def _sweeps(exe, tmp, mps, h, V, D, nsweeps):
+def _sweeps(exe, tmp, mps, h, V, D, nsweeps, switch=0):
     fin, fout = str(tmp / "sw_in.bin"), str(tmp / "sw_out.bin")
     _write(fin, mps, h, V)
     r = subprocess.run([exe, fin, fout, "sweep", str(D), str(nsweeps), "1e-10"], capture_output=True,
-                       text=True, timeout=600)
+                       text=True, timeout=600, env=_env(switch))
     assert r.returncode == 0, r.stderr
     return np.fromfile(fout, "<f8")
 
@@ -111,3 +116,59 @@ def test_engine_sweeps_at_exact_bond_dimension_give_fci(host_exec, tmp_path):
     E = _sweeps(host_exec, tmp_path, m, h, V, D, 2)
     e0, _ = FCI(h, V, N, 0).ground_state()
     assert abs(E[-1] - e0) <= 1e-9
+
+
+# Normal/complementary switch: left blocks at cuts <= switch and right blocks beyond it hold
+# the normal pairs. The cases put the switch left of, at, and right of the centre cut, so the
+# switching enlargement runs in the left chain, the right chain and at the centre, and the
+# centre uses either decomposition; edge centres included.
+@pytest.mark.parametrize("L,N,two_sz,D,c,seed,switch", [(6, 6, 0, 16, 2, 3, 1), (6, 6, 0, 16, 2, 3, 2),
+                                                         (6, 6, 0, 16, 2, 3, 3), (6, 6, 0, 16, 2, 3, 5),
+                                                         (7, 5, 1, 16, 2, 4, 2), (8, 8, 0, 32, 3, 7, 4),
+                                                         (8, 8, 0, 32, 3, 7, 6), (6, 6, 0, 16, 0, 3, 3),
+                                                         (7, 7, 1, 16, 5, 8, 3)])
+def test_switched_task_lists_match_the_oracle(host_exec, tmp_path, L, N, two_sz, D, c, seed, switch):
+    from oracle.dmrgu1 import DMRGU1
+    from oracle.mpsu1 import MPSU1
+    m = MPSU1.from_raw(q.random_mps_blocks(L, N, two_sz, D, q.SYM_U1, seed, c))
+    h, V = q.make_integrals(L, seed + 1)
+    s64, st = _run(host_exec, tmp_path, m, h, V, switch)
+    ref = m.psi_to_flat(DMRGU1(h, V, N, two_sz).sigma(m))
+    assert np.linalg.norm(s64 - ref) <= 1e-12 * np.linalg.norm(ref)
+    assert np.linalg.norm(st - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("L,N,D,c,mps_seed,int_seed,switch", [(6, 6, 8, 2, 3, 4, 2), (6, 6, 8, 2, 3, 4, 3),
+                                                               (7, 5, 12, 3, 5, 6, 3)])
+def test_switched_sweeps_match_the_oracle(host_exec, tmp_path, L, N, D, c, mps_seed, int_seed, switch):
+    """Sweeps move the centre across the switch in both directions: blocks are renormalized
+    as normal on one side and complementary on the other, and the switching enlargement is
+    rebuilt at every crossing."""
+    from oracle.dmrgu1 import DMRGU1
+    from oracle.mpsu1 import MPSU1
+    two = N % 2
+    m = MPSU1.from_raw(q.random_mps_blocks(L, N, two, D, q.SYM_U1, mps_seed, c))
+    h, V = q.make_integrals(L, int_seed)
+    E = _sweeps(host_exec, tmp_path, m, h, V, D, 2, switch)
+    Eo, _, _ = DMRGU1(h, V, N, two).sweeps(m, D, 2, tol=1e-12)
+    assert np.abs(E - np.array(Eo)).max() <= 1e-9
+
+
+def test_switched_rdm1_equals_unswitched(host_exec, tmp_path):
+    """With the switch on, the 1-RDM at the last centre is taken on an environment rebuilt with
+    normal pairs on the left (then the switched one is restored): same matrix, and its trace
+    is N."""
+    from oracle.mpsu1 import MPSU1
+    L, N = 6, 6
+    m = MPSU1.from_raw(q.random_mps_blocks(L, N, 0, 16, q.SYM_U1, 9, L - 2))
+    h, V = q.make_integrals(L, 10)
+    fin, fout = str(tmp_path / "r_in.bin"), str(tmp_path / "r_out.bin")
+    _write(fin, m, h, V)
+    g = []
+    for switch in (0, 3):
+        r = subprocess.run([host_exec, fin, fout, "rdm1"], capture_output=True, text=True, timeout=600,
+                           env=_env(switch))
+        assert r.returncode == 0, r.stderr
+        g.append(np.fromfile(fout, "<f8").reshape(L, L))
+    assert np.abs(g[1] - g[0]).max() <= 1e-12
+    assert abs(np.trace(g[0]) - N) <= 1e-10

@@ -29,8 +29,12 @@ def checker(tmp_path_factory):
     return out
 
 
-@pytest.mark.parametrize("L,N,D", [(6, 6, 16), (7, 5, 16), (12, 12, 32), (36, 54, 64)])
-def test_plans_stay_in_bounds(checker, L, N, D):
-    r = subprocess.run([checker, str(L), str(N), str(D)], capture_output=True, text=True, timeout=600)
+@pytest.mark.parametrize("L,N,D,switch", [(6, 6, 16, 0), (7, 5, 16, 0), (12, 12, 32, 0), (36, 54, 64, 0),
+                                           (12, 12, 32, 4), (12, 12, 32, 6), (36, 54, 64, 18)])
+def test_plans_stay_in_bounds(checker, L, N, D, switch):
+    """switch: cut of the normal/complementary switch (0: normal pairs on the left everywhere;
+    at the centre cut L/2 the right blocks switch; at L/2 - 2 the centre uses the mirrored
+    decomposition with normal pairs on the right)."""
+    r = subprocess.run([checker, str(L), str(N), str(D), str(switch)], capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "fails=0" in r.stdout
