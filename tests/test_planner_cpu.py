@@ -30,11 +30,13 @@ def checker(tmp_path_factory):
 
 
 @pytest.mark.parametrize("L,N,D,switch", [(6, 6, 16, 0), (7, 5, 16, 0), (12, 12, 32, 0), (36, 54, 64, 0),
-                                           (12, 12, 32, 4), (12, 12, 32, 6), (36, 54, 64, 18)])
+                                           (12, 12, 32, 4), (12, 12, 32, 6), (36, 54, 64, 18),
+                                           (36, 54, 4096, 18)])
 def test_plans_stay_in_bounds(checker, L, N, D, switch):
     """switch: cut of the normal/complementary switch (0: normal pairs on the left everywhere;
     at the centre cut L/2 the right blocks switch; at L/2 - 2 the centre uses the mirrored
-    decomposition with normal pairs on the right)."""
+    decomposition with normal pairs on the right). The D=4096 case is the full CAS(54,36)-shaped
+    size of the switched run (task lists only: about 15 s)."""
     r = subprocess.run([checker, str(L), str(N), str(D), str(switch)], capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "fails=0" in r.stdout
