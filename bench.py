@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--pair-switch", type=int, default=0,
                     help="cut of the normal/complementary switch (0: normal pairs on the left at every "
                          "cut; L/2: the N/2 rule, which the D=4096 environment needs to fit)")
+    ap.add_argument("--sum-gemm", type=int, default=0, choices=[-1, 0, 1],
+                    help="operator sums of the renormalization side as GEMMs (1), block by block (-1), "
+                         "or as GEMMs only with the switch (0)")
     ap.add_argument("--profile", action="store_true",
                     help="bracket the timed region with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     return ap.parse_args()
@@ -253,7 +256,8 @@ def run_ours(args, rank, world, local):
 
     L, N, D = args.L, args.N, args.D
     h, V = q.make_integrals(L, q.integrals.BASE_SEED + 2)
-    ctx = qd.Context(device=local, hbm_budget_gb=args.hbm_budget, pair_switch=args.pair_switch)
+    ctx = qd.Context(device=local, hbm_budget_gb=args.hbm_budget, pair_switch=args.pair_switch,
+                     sum_gemm=args.sum_gemm)
     ctx.load_integrals(h, V)
     ctx.set_target(N, 0)
     center = L // 2 - 1
@@ -411,7 +415,7 @@ def run_ours(args, rank, world, local):
                    "l2": "operator blocks read per step exceed L2 (no flush needed)",
                    "device_bytes": st2["device_bytes"], "energy_psi_h_psi": energy, "tile": tile,
                    "forms": forms, "fp64_peak_tflops_measured": peak,
-                   "pair_switch": args.pair_switch, "hbm_budget_gb": args.hbm_budget,
+                   "pair_switch": args.pair_switch, "sum_gemm": args.sum_gemm, "hbm_budget_gb": args.hbm_budget,
                    "parallelism": f"replicas{world}"},
         "roofline": roof,
         "cpu_baseline": cpu,
@@ -522,7 +526,8 @@ def run_sweep(args, rank, world, local):
     order = [+1] * (L - 2 - c0) + [-1] * (L - 2) + [+1] * c0
     out = {}
     for name, kw in (("fp64", dict(policy=0, precision=qd.FP64)), ("mixed", dict(policy=1))):
-        ctx = qd.Context(device=local, hbm_budget_gb=args.hbm_budget, pair_switch=args.pair_switch)
+        ctx = qd.Context(device=local, hbm_budget_gb=args.hbm_budget, pair_switch=args.pair_switch,
+                     sum_gemm=args.sum_gemm)
         ctx.load_integrals(h, V)
         ctx.set_target(N, 0)
         ctx.init_mps(D, q.integrals.BASE_SEED + 1002, c0)
@@ -563,7 +568,7 @@ def run_sweep(args, rank, world, local):
         "higher_is_better": False, "dtype": "mixed", "data": "synthetic",
         "config": {"workload": f"u1_L{L}_N{N}_Sz0_D{D} sweep from a random MPS, centre start",
                    "davidson": {"tol": 1e-6, "max_iter": args.max_iter}, "budget_s": args.sweep_budget,
-                   "pair_switch": args.pair_switch, "hbm_budget_gb": args.hbm_budget,
+                   "pair_switch": args.pair_switch, "sum_gemm": args.sum_gemm, "hbm_budget_gb": args.hbm_budget,
                    "fp64": f, "mixed": m,
                    "same_steps_compared": n,
                    "speedup_vs_fp64_same_steps": (sum(f["step_s"][:n]) / sum(m["step_s"][:n])) if n else None,

@@ -73,6 +73,10 @@ typedef struct {
                            the N/2 rule: the pairs are stored on the side with fewer modes,
                            which halves the operator volume of a sweep environment. 0 keeps
                            normal pairs on the left at every cut. Negative: QCDMRG_EINVAL */
+  int sum_gemm;         /* renormalization-side sums of many stored operators (the S', H', P',
+                           Q' of an enlarged block): 1 runs each group of at least 8 as a GEMM of
+                           a coefficient matrix with the operators' blocks, -1 sums them block
+                           by block, 0 (default) takes the GEMM form when pair_switch is set */
 } qcdmrg_config;
 
 /*

@@ -32,7 +32,7 @@ class QcdmrgError(RuntimeError):
 class Config(ctypes.Structure):
     _fields_ = [("symmetry", ctypes.c_int), ("device", ctypes.c_int),
                 ("tmp_budget_gb", ctypes.c_double), ("hbm_budget_gb", ctypes.c_double),
-                ("autotune_off", ctypes.c_int), ("pair_switch", ctypes.c_int)]
+                ("autotune_off", ctypes.c_int), ("pair_switch", ctypes.c_int), ("sum_gemm", ctypes.c_int)]
 
 
 class MpsDesc(ctypes.Structure):
@@ -149,10 +149,10 @@ class Context:
     """One qcdmrg context (one device, one problem)."""
 
     def __init__(self, device=0, symmetry=U1, tmp_budget_gb=0.0, hbm_budget_gb=0.0, autotune=True,
-                 pair_switch=0, lib=None):
+                 pair_switch=0, sum_gemm=0, lib=None):
         self.lib = lib or load()
         self.h = ctypes.c_void_p()
-        cfg = Config(symmetry, device, tmp_budget_gb, hbm_budget_gb, 0 if autotune else 1, pair_switch)
+        cfg = Config(symmetry, device, tmp_budget_gb, hbm_budget_gb, 0 if autotune else 1, pair_switch, sum_gemm)
         rc = self.lib.qcdmrg_create(ctypes.byref(self.h), ctypes.byref(cfg))
         if rc != QCDMRG_OK:
             raise QcdmrgError(rc, "context creation failed (no usable CUDA device?)")

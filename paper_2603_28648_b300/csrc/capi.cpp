@@ -97,6 +97,8 @@ int qcdmrg_create(qcdmrg_ctx** out, const qcdmrg_config* cfg) {
     c->eng.autotune = cfg->autotune_off == 0;
     if (cfg->pair_switch < 0) throw std::invalid_argument("pair_switch");
     c->eng.pair_switch = cfg->pair_switch;
+    if (cfg->sum_gemm < -1 || cfg->sum_gemm > 1) throw std::invalid_argument("sum_gemm");
+    c->eng.sum_gemm = cfg->sum_gemm;
   } catch (const std::invalid_argument&) {
     delete c;
     return QCDMRG_EINVAL;

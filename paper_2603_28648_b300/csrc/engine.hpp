@@ -43,9 +43,10 @@ struct Engine {
   // on the left at every cut)
   int pair_switch = 0;
   bool normal_at(bool left, int cut) const { return normal_pairs(left, cut, pair_switch > 0 ? pair_switch : L); }
-  // with the switch on, wide sums of stored operators run as GEMMs (the
-  // switching enlargement sums every pair operator of a block into each P', Q')
-  bool batched_sums() const { return pair_switch > 0; }
+  // wide sums of stored operators as GEMMs: 1 on, -1 off, 0 on with the switch
+  // (the switching enlargement sums every pair operator of a block into each P', Q')
+  int sum_gemm = 0;
+  bool batched_sums() const { return sum_gemm > 0 || (sum_gemm == 0 && pair_switch > 0); }
   // MPS: bonds (left labels for b <= center, right labels for b >= center+2),
   // site tensors (product-sector matrices) for every site except the centre pair
   std::vector<Basis> bonds;

@@ -9,7 +9,8 @@
 // no bf16 rounding), so that both plans can be compared with the oracle.
 //
 // Every launch is checked against the buffers it addresses. The environment
-// variable HOST_EXEC_PAIR_SWITCH sets the cut of the normal/complementary switch.
+// variable HOST_EXEC_PAIR_SWITCH sets the cut of the normal/complementary switch,
+// HOST_EXEC_SUM_GEMM the form of the operator sums (1 GEMM, -1 block by block).
 //
 // usage: host_exec in.bin out.bin                       (one H_eff psi, both plans)
 //        host_exec in.bin out.bin sweep D nsweeps tol     (full FP64 sweeps)
@@ -316,6 +317,7 @@ int main(int argc, char** argv) {
     E.pr = &pr;
     E.tmp_budget = (int64_t)(2e9 / 8);
     if (const char* sw = std::getenv("HOST_EXEC_PAIR_SWITCH")) E.pair_switch = std::atoi(sw);
+    if (const char* sg = std::getenv("HOST_EXEC_SUM_GEMM")) E.sum_gemm = std::atoi(sg);
     E.I.L = L;
     E.I.h = h;
     E.I.V = V;

@@ -77,3 +77,22 @@ def test_switched_rdm1_equals_unswitched():
     from oracle.dmrgu1 import DMRGU1
     ref = m.psi_to_flat(DMRGU1(h, V, N, 0).sigma(m))
     assert np.linalg.norm(ctx.apply_heff(psi) - ref) <= TOL_FP64 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("switch,sum_gemm", [(0, 1), (3, -1)])
+def test_operator_sum_forms_match_oracle(switch, sum_gemm):
+    """Operator sums as GEMMs without the switch, block by block with it."""
+    import paper_2603_28648_b300 as qd
+    from oracle.dmrgu1 import DMRGU1
+    from oracle.mpsu1 import MPSU1, export_abi
+    ensure_built()
+    L, N, D, c = 8, 8, 32, 3
+    m = MPSU1.from_raw(q.random_mps_blocks(L, N, 0, D, q.SYM_U1, 7, c))
+    h, V = q.make_integrals(L, 8)
+    ctx = qd.Context(pair_switch=switch, sum_gemm=sum_gemm)
+    ctx.load_integrals(h, V)
+    ctx.set_target(N, 0)
+    ctx.import_mps(L, c, *export_abi(m))
+    ctx.build_env()
+    ref = m.psi_to_flat(DMRGU1(h, V, N, 0).sigma(m))
+    assert np.linalg.norm(ctx.apply_heff(m.psi_to_flat()) - ref) <= TOL_FP64 * np.linalg.norm(ref)

@@ -45,14 +45,15 @@ def _write(path, mps, h, V):
         f.write(np.asarray(data, "<f8").tobytes())
 
 
-def _env(switch):
-    return dict(os.environ, HOST_EXEC_PAIR_SWITCH=str(switch))
+def _env(switch, sum_gemm=0):
+    return dict(os.environ, HOST_EXEC_PAIR_SWITCH=str(switch), HOST_EXEC_SUM_GEMM=str(sum_gemm))
 
 
-def _run(exe, tmp, mps, h, V, switch=0):
+def _run(exe, tmp, mps, h, V, switch=0, sum_gemm=0):
     fin, fout = str(tmp / "in.bin"), str(tmp / "out.bin")
     _write(fin, mps, h, V)
-    r = subprocess.run([exe, fin, fout], capture_output=True, text=True, timeout=600, env=_env(switch))
+    r = subprocess.run([exe, fin, fout], capture_output=True, text=True, timeout=600,
+                       env=_env(switch, sum_gemm))
     assert r.returncode == 0, r.stderr
     out = np.fromfile(fout, "<f8")
     n = len(out) // 2
@@ -86,11 +87,11 @@ def test_library_task_lists_on_an_su2_state(host_exec, tmp_path):
         assert np.linalg.norm(C.T @ s - ref) <= 1e-12 * np.linalg.norm(ref)
 
 
-def _sweeps(exe, tmp, mps, h, V, D, nsweeps, switch=0):
+def _sweeps(exe, tmp, mps, h, V, D, nsweeps, switch=0, sum_gemm=0):
     fin, fout = str(tmp / "sw_in.bin"), str(tmp / "sw_out.bin")
     _write(fin, mps, h, V)
     r = subprocess.run([exe, fin, fout, "sweep", str(D), str(nsweeps), "1e-10"], capture_output=True,
-                       text=True, timeout=600, env=_env(switch))
+                       text=True, timeout=600, env=_env(switch, sum_gemm))
     assert r.returncode == 0, r.stderr
     return np.fromfile(fout, "<f8")
 
@@ -172,3 +173,23 @@ def test_switched_rdm1_equals_unswitched(host_exec, tmp_path):
         g.append(np.fromfile(fout, "<f8").reshape(L, L))
     assert np.abs(g[1] - g[0]).max() <= 1e-12
     assert abs(np.trace(g[0]) - N) <= 1e-10
+
+
+@pytest.mark.parametrize("switch,sum_gemm", [(0, 1), (3, -1)])
+def test_operator_sum_forms_match_the_oracle(host_exec, tmp_path, switch, sum_gemm):
+    """The GEMM form of the operator sums without the switch, and the block-by-block form
+    with it: the same sigma and sweep energies as the oracle."""
+    from oracle.dmrgu1 import DMRGU1
+    from oracle.mpsu1 import MPSU1
+    L, N, D, c = 8, 8, 32, 3
+    m = MPSU1.from_raw(q.random_mps_blocks(L, N, 0, D, q.SYM_U1, 7, c))
+    h, V = q.make_integrals(L, 8)
+    s64, st = _run(host_exec, tmp_path, m, h, V, switch, sum_gemm)
+    ref = m.psi_to_flat(DMRGU1(h, V, N, 0).sigma(m))
+    assert np.linalg.norm(s64 - ref) <= 1e-12 * np.linalg.norm(ref)
+    assert np.linalg.norm(st - ref) <= 1e-12 * np.linalg.norm(ref)
+    m2 = MPSU1.from_raw(q.random_mps_blocks(6, 6, 0, 8, q.SYM_U1, 3, 2))
+    h2, V2 = q.make_integrals(6, 4)
+    E = _sweeps(host_exec, tmp_path, m2, h2, V2, 8, 2, switch, sum_gemm)
+    Eo, _, _ = DMRGU1(h2, V2, 6, 0).sweeps(m2, 8, 2, tol=1e-12)
+    assert np.abs(E - np.array(Eo)).max() <= 1e-9
