@@ -96,3 +96,29 @@ def test_operator_sum_forms_match_oracle(switch, sum_gemm):
     ctx.build_env()
     ref = m.psi_to_flat(DMRGU1(h, V, N, 0).sigma(m))
     assert np.linalg.norm(ctx.apply_heff(m.psi_to_flat()) - ref) <= TOL_FP64 * np.linalg.norm(ref)
+
+
+def test_switch_leaves_sigma_unchanged_L36():
+    """CAS(54,36)-shaped problem at D=512: the switch at the centre cut and two cuts left of it
+    gives the unswitched FP64 sigma (to summation order), and its BF16 forms stay within their
+    bounds of it."""
+    import paper_2603_28648_b300 as qd
+    ensure_built()
+    L, N, D = 36, 54, 512
+    h, V = q.make_integrals(L, q.integrals.BASE_SEED + 2)
+    out = {}
+    for switch in (0, 18, 16):
+        ctx = qd.Context(pair_switch=switch)
+        ctx.load_integrals(h, V)
+        ctx.set_target(N, 0)
+        ctx.init_mps(D, 5, 17)
+        ctx.build_env()
+        psi = ctx.psi()
+        out[switch] = ctx.apply_heff(psi, qd.FP64)
+        if switch:
+            ref = out[0]
+            assert np.linalg.norm(out[switch] - ref) <= 1e-12 * np.linalg.norm(ref)
+            for prec in ("bf16", "bf16x3"):
+                x = ctx.apply_heff(psi, qd.PRECISIONS[prec])
+                assert np.linalg.norm(x - ref) <= BOUND[prec] * np.linalg.norm(ref), prec
+        ctx.close()

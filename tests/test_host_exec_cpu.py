@@ -193,3 +193,19 @@ def test_operator_sum_forms_match_the_oracle(host_exec, tmp_path, switch, sum_ge
     E = _sweeps(host_exec, tmp_path, m2, h2, V2, 8, 2, switch, sum_gemm)
     Eo, _, _ = DMRGU1(h2, V2, 6, 0).sweeps(m2, 8, 2, tol=1e-12)
     assert np.abs(E - np.array(Eo)).max() <= 1e-9
+
+
+def test_switch_leaves_sigma_unchanged_at_the_cas54_36_shape(host_exec, tmp_path):
+    """At L=36, N=54 (D=64, centre 17) the switch changes which block stores the pair
+    operators, not H_eff: sigma with the switch at the centre cut and two cuts left of it
+    equals the unswitched sigma, and the tiled work items agree with the FP64 task lists."""
+    from oracle.mpsu1 import MPSU1
+    L, N, D, c = 36, 54, 64, 17
+    m = MPSU1.from_raw(q.random_mps_blocks(L, N, 0, D, q.SYM_U1, 3, c))
+    h, V = q.make_integrals(L, 4)
+    s0, t0 = _run(host_exec, tmp_path, m, h, V, 0)
+    assert np.linalg.norm(t0 - s0) <= 1e-13 * np.linalg.norm(s0)
+    for switch in (18, 16):
+        s1, t1 = _run(host_exec, tmp_path, m, h, V, switch)
+        assert np.linalg.norm(s1 - s0) <= 1e-13 * np.linalg.norm(s0)
+        assert np.linalg.norm(t1 - s0) <= 1e-13 * np.linalg.norm(s0)
