@@ -306,7 +306,11 @@ int qcdmrg_apply_heff_noalloc(qcdmrg_ctx* ctx, const void* psi, void* sigma, voi
  * needs, DMRG-SCF of the paper's New benchmark system section). Measured with
  * the stored operators at the centre (L-2, L-1), where the left enlarged
  * block holds a+_k a_l for every orbital but the last: move the centre there
- * first (qcdmrg_move_center(ctx, L-2)). Errors: ESTATE.
+ * first (qcdmrg_move_center(ctx, L-2)). With pair_switch set, the blocks at
+ * that centre hold complementary pairs on the left; the call then rebuilds the
+ * environment with normal pairs on the left, measures, and rebuilds the
+ * switched environment (two environment builds; the MPS is unchanged).
+ * Errors: ESTATE.
  */
 int qcdmrg_rdm1(qcdmrg_ctx* ctx, double* gamma);
 
