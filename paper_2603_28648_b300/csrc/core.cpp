@@ -2,6 +2,12 @@
 #include "core.hpp"
 
 #include <algorithm>
+#include <atomic>
+#include <exception>
+#include <functional>
+#include <mutex>
+#include <thread>
+#include <climits>
 #include <cmath>
 #include <stdexcept>
 #include <tuple>
@@ -148,6 +154,35 @@ Mat4 ann(int sigma) { return cre(sigma).T(); }
 // ---------------------------------------------------------------------------
 // Renormalization: O_new = U^T O U (left) or V O V^T (right), two stages.
 // ---------------------------------------------------------------------------
+namespace {
+// f(0..n-1) on up to 16 host threads (items independent, each writing only its
+// own results); the first exception of any item is rethrown
+void parallel_for_ops(size_t n, const std::function<void(size_t)>& f) {
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const unsigned nt = (unsigned)std::min<size_t>(std::min(hw, 16u), n / 16);
+  if (nt <= 1) {
+    for (size_t i = 0; i < n; ++i) f(i);
+    return;
+  }
+  std::atomic<size_t> next{0};
+  std::exception_ptr err;
+  std::mutex mu;
+  std::vector<std::thread> ts;
+  for (unsigned t = 0; t < nt; ++t)
+    ts.emplace_back([&]() {
+      try {
+        for (size_t i; (i = next.fetch_add(1)) < n;) f(i);
+      } catch (...) {
+        std::lock_guard<std::mutex> g(mu);
+        if (!err) err = std::current_exception();
+        next = n;
+      }
+    });
+  for (auto& t : ts) t.join();
+  if (err) std::rethrow_exception(err);
+}
+}  // namespace
+
 void renormalize(const Enlarged& E, const Basis& nb, const std::vector<int>& nb_of_prod,
                  uint64_t tensor, const std::vector<int64_t>& toff, Executor& ex,
                  EnvBlock& out, int64_t tmp_budget, double* flops) {
@@ -191,46 +226,59 @@ void renormalize(const Enlarged& E, const Basis& nb, const std::vector<int>& nb_
     if (left) return tensor + 8ull * (toff[S.prod] + (int64_t)S.off * nb.dim[nq]);
     return tensor + 8ull * (toff[S.prod] + S.off);
   };
-  Launch s1, s2;
-  {
-    // one segment per stored block reference at most, in either stage
-    size_t nseg = 0;
-    for (auto& kv : E.ops)
-      if (kv.first.f != F_I) nseg += kv.second.blocks.size();
-    s1.segs.reserve(nseg);
-    s1.probs.reserve(nseg);
-    s2.segs.reserve(nseg);
-  }
-  int64_t tused = 0;
-  double fl = 0;
-  std::vector<std::pair<std::pair<int, int>, Seg>> segs;
-  auto flush = [&]() {
-    if (s1.empty() && s2.empty()) return;
-    if (tused) ex.tmp(tused);
-    if (!s1.empty()) ex.run(s1, 0, 0);
-    if (!s2.empty()) ex.run(s2, 0, 0);
-    fl += s1.flops + s2.flops;
-    s1.clear();
-    s2.clear();
-    tused = 0;
-  };
-  for (auto& kv : E.ops) {
-    if (kv.first.f == F_I) continue;
-    const OpView& op = kv.second;
-    auto& lay = layout[kv.first];
+  // Every stored operator (key order) is O' = U^T O U per output block: stage
+  // 1 writes O U of each stored block reference to scratch, stage 2 sums U^T
+  // times those (or U^T U_c for identity references) into the output block.
+  // The operators are taken in chunks whose scratch fits the budget; each
+  // operator's segments are built independently, then joined in order.
+  struct OpPlan {
+    const Key* key;
+    const OpView* op;
+    int64_t tbase;            // scratch offset of the operator in its chunk
+    int chunk;
+    std::vector<Seg> s1segs, s2segs;
+    std::vector<Prob> s1probs, s2probs;   // seg0 relative to the operator's segments
+    double fl1 = 0, fl2 = 0;
     OpView nv;
-    nv.odd = op.odd;
-    // count scratch of this op
-    int64_t need = 0;
-    for (const BRef& b : op.blocks) {
-      int nq2 = nb_of_prod[pb.subs[b.c].prod];
-      if (nq2 < 0 || nb_of_prod[pb.subs[b.r].prod] < 0 || b.ident()) continue;
-      need += (int64_t)b.rows * nb.dim[nq2];
+  };
+  std::vector<OpPlan> ops;
+  std::vector<int64_t> chunk_tmp;
+  {
+    int64_t tused = 0;
+    int chunk = 0;
+    for (auto& kv : E.ops) {
+      if (kv.first.f == F_I) continue;
+      int64_t need = 0;
+      for (const BRef& b : kv.second.blocks) {
+        int nq2 = nb_of_prod[pb.subs[b.c].prod];
+        if (nq2 < 0 || nb_of_prod[pb.subs[b.r].prod] < 0 || b.ident()) continue;
+        need += (int64_t)b.rows * nb.dim[nq2];
+      }
+      if (tused && tused + need > tmp_budget) {
+        chunk_tmp.push_back(tused);
+        ++chunk;
+        tused = 0;
+      }
+      ops.emplace_back();
+      OpPlan& o = ops.back();
+      o.key = &kv.first;
+      o.op = &kv.second;
+      o.tbase = tused;
+      o.chunk = chunk;
+      tused += need;
     }
-    if (tused && tused + need > tmp_budget) flush();
+    chunk_tmp.push_back(tused);
+  }
+  parallel_for_ops(ops.size(), [&](size_t oi) {
+    OpPlan& o = ops[oi];
+    const OpView& op = *o.op;
+    const auto& lay = layout.at(*o.key);
+    o.nv.odd = op.odd;
+    int64_t tused = o.tbase;
     // (output block, segment) pairs, grouped by output block below in the
     // order they were produced
-    segs.clear();
+    std::vector<std::pair<std::pair<int, int>, Seg>> segs;
+    segs.reserve(op.blocks.size());
     for (const BRef& b : op.blocks) {
       const Sub& Sr = pb.subs[b.r];
       const Sub& Sc = pb.subs[b.c];
@@ -253,38 +301,88 @@ void renormalize(const Enlarged& E, const Basis& nb, const std::vector<int>& nb_
         Prob p;
         p.c = (uint64_t)tused; p.cbuf = B_TMP;
         p.m = b.rows; p.n = dq2; p.ldc = dq2; p.beta = 0;
-        p.seg0 = (int)s1.segs.size(); p.nseg = 1;
+        p.seg0 = (int)o.s1segs.size(); p.nseg = 1;
         Seg h;
         h.a = b.ptr; h.abuf = B_ABS; h.lda = b.ld; h.ta = b.tr ? 1 : 0;
         h.b = sub_ptr(b.c); h.bbuf = B_ABS; h.k = b.cols;
         if (left) { h.ldb = dq2; h.tb = 0; } else { h.ldb = pq2; h.tb = 1; }
-        s1.segs.push_back(h);
-        s1.probs.push_back(p);
-        s1.flops += 2.0 * p.m * p.n * h.k;
+        o.s1segs.push_back(h);
+        o.s1probs.push_back(p);
+        o.fl1 += 2.0 * p.m * p.n * h.k;
         g.b = (uint64_t)tused; g.bbuf = B_TMP; g.ldb = dq2; g.tb = 0;
         tused += (int64_t)b.rows * dq2;
       }
       segs.push_back({{nq, nq2}, g});
-      s2.flops += 2.0 * dq * dq2 * g.k;
+      o.fl2 += 2.0 * dq * dq2 * g.k;
     }
     std::stable_sort(segs.begin(), segs.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+    o.s2segs.reserve(segs.size());
     for (size_t si = 0; si < segs.size();) {
       const std::pair<int, int> key = segs[si].first;
       int nq = key.first, nq2 = key.second;
       Prob p;
-      p.c = store + 8ull * lay[key]; p.cbuf = B_ABS;
+      p.c = store + 8ull * lay.at(key); p.cbuf = B_ABS;
       p.m = nb.dim[nq]; p.n = nb.dim[nq2]; p.ldc = p.n; p.beta = 0;
-      p.seg0 = (int)s2.segs.size();
-      while (si < segs.size() && segs[si].first == key) s2.segs.push_back(segs[si++].second);
-      p.nseg = (int)s2.segs.size() - p.seg0;
-      s2.probs.push_back(p);
+      p.seg0 = (int)o.s2segs.size();
+      while (si < segs.size() && segs[si].first == key) o.s2segs.push_back(segs[si++].second);
+      p.nseg = (int)o.s2segs.size() - p.seg0;
+      o.s2probs.push_back(p);
       BRef r;
       r.r = nq; r.c = nq2; r.ptr = p.c; r.rows = p.m; r.cols = p.n; r.ld = p.n; r.tr = false; r.sc = 1.0;
-      nv.blocks.push_back(r);
+      o.nv.blocks.push_back(r);
     }
-    out.ops[kv.first] = nv;
+  });
+  // join each chunk in operator order (offsets by prefix sums, copies in
+  // parallel) and run it
+  double fl = 0;
+  Launch s1, s2;
+  struct Off { size_t s1s, s1p, s2s, s2p; };
+  std::vector<Off> off(ops.size());
+  for (size_t oi = 0; oi < ops.size();) {
+    const int chunk = ops[oi].chunk;
+    const size_t o0 = oi;
+    Off t{0, 0, 0, 0};
+    for (; oi < ops.size() && ops[oi].chunk == chunk; ++oi) {
+      const OpPlan& o = ops[oi];
+      off[oi] = t;
+      t.s1s += o.s1segs.size(); t.s1p += o.s1probs.size();
+      t.s2s += o.s2segs.size(); t.s2p += o.s2probs.size();
+    }
+    if (t.s1s > (size_t)INT32_MAX || t.s2s > (size_t)INT32_MAX)
+      throw std::runtime_error("renormalize: task list too long");
+    s1.clear();
+    s2.clear();
+    s1.segs.resize(t.s1s); s1.probs.resize(t.s1p);
+    s2.segs.resize(t.s2s); s2.probs.resize(t.s2p);
+    parallel_for_ops(oi - o0, [&](size_t j) {
+      OpPlan& o = ops[o0 + j];
+      const Off& f = off[o0 + j];
+      std::copy(o.s1segs.begin(), o.s1segs.end(), s1.segs.begin() + f.s1s);
+      std::copy(o.s2segs.begin(), o.s2segs.end(), s2.segs.begin() + f.s2s);
+      for (size_t k = 0; k < o.s1probs.size(); ++k) {
+        Prob p = o.s1probs[k];
+        p.seg0 += (int)f.s1s;
+        s1.probs[f.s1p + k] = p;
+      }
+      for (size_t k = 0; k < o.s2probs.size(); ++k) {
+        Prob p = o.s2probs[k];
+        p.seg0 += (int)f.s2s;
+        s2.probs[f.s2p + k] = p;
+      }
+      std::vector<Seg>().swap(o.s1segs);
+      std::vector<Seg>().swap(o.s2segs);
+    });
+    for (size_t j = o0; j < oi; ++j) {
+      s1.flops += ops[j].fl1;
+      s2.flops += ops[j].fl2;
+      out.ops[*ops[j].key] = std::move(ops[j].nv);
+    }
+    if (s1.empty() && s2.empty()) continue;
+    if (chunk_tmp[chunk]) ex.tmp(chunk_tmp[chunk]);
+    if (!s1.empty()) ex.run(s1, 0, 0);
+    if (!s2.empty()) ex.run(s2, 0, 0);
+    fl += s1.flops + s2.flops;
   }
-  flush();
   if (flops) *flops += fl;
 }
 

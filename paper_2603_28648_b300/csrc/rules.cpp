@@ -384,99 +384,102 @@ struct Ctx {
     Launch lb;
     std::set<std::pair<size_t, size_t>> in_batch;
     if (E.batched) batch_sums(plans, lb, in_batch, summed, ex);
-    // storage for summed groups
-    int64_t total = 0;
-    struct Mat { size_t n, g; std::map<std::pair<int, int>, std::pair<int64_t, std::pair<int, int>>> blk; };
-    std::vector<Mat> mats;
+    // block lists of every source that is summed or referenced below
+    // (transposes built once), filled here so that the parallel parts only
+    // read the cache
     for (size_t n = 0; n < plans.size(); ++n)
-      for (size_t g = 0; g < plans[n].groups.size(); ++g) {
-        auto& grp = plans[n].groups[g];
-        if (grp.items.size() < 2 || in_batch.count({n, g})) continue;
-        Mat mt{n, g, {}};
-        for (auto& itm : grp.items)
-          for (const BRef& b : blocks(itm.src, itm.T)) {
-            auto key = std::make_pair(b.r, b.c);
-            if (!mt.blk.count(key)) {
-              mt.blk[key] = {total, {b.rows, b.cols}};
-              total += (int64_t)b.rows * b.cols;
-            }
-          }
-        mats.push_back(mt);
-      }
-    uint64_t store = total ? ex.alloc(total) : 0;
-    if (store) E.owned.push_back(store);
-    Launch l;
-    {
-      size_t nseg = 0, nprob = 0;
-      for (auto& mt : mats) {
-        nprob += mt.blk.size();
-        for (auto& itm : plans[mt.n].groups[mt.g].items) nseg += blocks(itm.src, itm.T).size();
-      }
-      l.segs.reserve(nseg);
-      l.probs.reserve(nprob);
-    }
-    // block lists of every summed source, built here so that the parallel part
-    // below only reads the cache
-    for (auto& mt : mats)
-      for (auto& itm : plans[mt.n].groups[mt.g].items) blocks(itm.src, itm.T);
+      for (size_t g = 0; g < plans[n].groups.size(); ++g)
+        if (!in_batch.count({n, g}))
+          for (auto& itm : plans[n].groups[g].items) blocks(itm.src, itm.T);
     auto blocks_ro = [&](const OpView* src, bool T) -> const std::vector<BRef>& {
       return blocks_of.at(reinterpret_cast<uintptr_t>(src) * 2 + (T ? 1 : 0));
     };
-    // each summed group's problems, segments (grouped by destination block in
-    // key order, item order within a block) and block references, independently
-    struct Part {
-      std::vector<Seg> segs;
-      std::vector<Prob> probs;
-      std::vector<BRef> refs;
+    // summed groups: each group's destination blocks (offsets in order of first
+    // appearance, problems in block-key order), then the groups' storage,
+    // problems and segments laid out one group after the other
+    struct Mat {
+      size_t n, g;
+      std::map<std::pair<int, int>, std::pair<int64_t, std::pair<int, int>>> blk;  // key -> local offset, shape
+      int64_t size = 0, off = 0;
+      size_t nseg = 0, seg0 = 0, prob0 = 0;
     };
-    std::vector<Part> parts(mats.size());
+    std::vector<Mat> mats;
+    for (size_t n = 0; n < plans.size(); ++n)
+      for (size_t g = 0; g < plans[n].groups.size(); ++g)
+        if (plans[n].groups[g].items.size() >= 2 && !in_batch.count({n, g})) {
+          mats.emplace_back();
+          mats.back().n = n;
+          mats.back().g = g;
+        }
+    parallel_for(mats.size(), [&](size_t mi) {
+      Mat& mt = mats[mi];
+      for (auto& itm : plans[mt.n].groups[mt.g].items)
+        for (const BRef& b : blocks_ro(itm.src, itm.T)) {
+          auto ins = mt.blk.emplace(std::make_pair(b.r, b.c), std::make_pair(mt.size, std::make_pair(b.rows, b.cols)));
+          if (ins.second) mt.size += (int64_t)b.rows * b.cols;
+          ++mt.nseg;
+        }
+    });
+    int64_t total = 0;
+    size_t nseg = 0, nprob = 0;
+    for (auto& mt : mats) {
+      mt.off = total;
+      mt.seg0 = nseg;
+      mt.prob0 = nprob;
+      total += mt.size;
+      nseg += mt.nseg;
+      nprob += mt.blk.size();
+    }
+    if (nseg + lb.segs.size() > (size_t)INT32_MAX) throw std::runtime_error("enlarge: summation task list too long");
+    uint64_t store = total ? ex.alloc(total) : 0;
+    if (store) E.owned.push_back(store);
+    Launch l;
+    l.segs.resize(nseg);
+    l.probs.resize(nprob);
+    // each group's problems and segments (grouped by destination block in key
+    // order, item order within a block) and block references, in place
+    std::vector<std::vector<BRef>> refs(mats.size());
     parallel_for(mats.size(), [&](size_t mi) {
       const Mat& mt = mats[mi];
       const auto& grp = plans[mt.n].groups[mt.g];
-      Part& P = parts[mi];
       std::map<std::pair<int, int>, int> kidx;
       for (auto& kv : mt.blk) kidx.emplace(kv.first, (int)kidx.size());
-      std::vector<std::pair<int, Seg>> tmp;
+      std::vector<int> key_of;
+      key_of.reserve(mt.nseg);
+      std::vector<size_t> start(kidx.size() + 1, 0);
+      for (auto& itm : grp.items)
+        for (const BRef& b : blocks_ro(itm.src, itm.T)) {
+          key_of.push_back(kidx.at({b.r, b.c}));
+          start[key_of.back() + 1]++;
+        }
+      for (size_t i = 0; i < kidx.size(); ++i) start[i + 1] += start[i];
+      std::vector<size_t> pos(start.begin(), start.end() - 1);
+      size_t e = 0;
       for (auto& itm : grp.items)
         for (const BRef& b : blocks_ro(itm.src, itm.T)) {
           Seg sg;
           sg.a = 0; sg.abuf = B_ABS; sg.k = b.rows; sg.sc = itm.coef * b.sc;
           if (b.ident()) { sg.b = 0; sg.bbuf = B_ABS; }
           else { sg.b = b.ptr; sg.bbuf = B_ABS; sg.ldb = b.ld; sg.tb = b.tr ? 1 : 0; }
-          tmp.push_back({kidx.at({b.r, b.c}), sg});
+          l.segs[mt.seg0 + pos[key_of[e++]]++] = sg;
         }
-      std::vector<int> start(kidx.size() + 1, 0);
-      for (auto& e : tmp) start[e.first + 1]++;
-      for (size_t i = 0; i < kidx.size(); ++i) start[i + 1] += start[i];
-      P.segs.resize(tmp.size());
-      {
-        std::vector<int> pos(start.begin(), start.end() - 1);
-        for (auto& e : tmp) P.segs[pos[e.first]++] = e.second;
-      }
       int q = 0;
+      refs[mi].reserve(mt.blk.size());
       for (auto& kv : mt.blk) {
         Prob pr;
-        pr.c = store + 8ull * kv.second.first; pr.cbuf = B_ABS;
+        pr.c = store + 8ull * (mt.off + kv.second.first); pr.cbuf = B_ABS;
         pr.m = kv.second.second.first; pr.n = kv.second.second.second; pr.ldc = pr.n; pr.beta = 0;
-        pr.seg0 = start[q];   // relative to this part; shifted when the parts are joined
-        pr.nseg = start[q + 1] - start[q];
+        pr.seg0 = (int)(mt.seg0 + start[q]);
+        pr.nseg = (int)(start[q + 1] - start[q]);
+        l.probs[mt.prob0 + q] = pr;
         ++q;
-        P.probs.push_back(pr);
         BRef r;
         r.r = kv.first.first; r.c = kv.first.second; r.ptr = pr.c;
         r.rows = pr.m; r.cols = pr.n; r.ld = pr.n; r.tr = false; r.sc = 1.0;
-        P.refs.push_back(r);
+        refs[mi].push_back(r);
       }
     });
-    for (size_t mi = 0; mi < mats.size(); ++mi) {
-      const int base = (int)l.segs.size();
-      for (Prob pr : parts[mi].probs) {
-        pr.seg0 += base;
-        l.probs.push_back(pr);
-      }
-      l.segs.insert(l.segs.end(), parts[mi].segs.begin(), parts[mi].segs.end());
-      summed[{mats[mi].n, mats[mi].g}] = std::move(parts[mi].refs);
-    }
+    for (size_t mi = 0; mi < mats.size(); ++mi) summed[{mats[mi].n, mats[mi].g}] = std::move(refs[mi]);
     if (!lb.empty()) {  // the GEMM-batched sums join the same launch
       const int base = (int)l.segs.size();
       for (Prob pr : lb.probs) {
@@ -487,20 +490,23 @@ struct Ctx {
       l.flops += lb.flops;
     }
     if (!l.empty()) ex.run(l, 0, 0);
-    for (size_t n = 0; n < plans.size(); ++n) {
-      OpView v;
+    // the operators' views, independently; then stored in key order
+    std::vector<OpView> views(plans.size());
+    parallel_for(plans.size(), [&](size_t n) {
+      OpView& v = views[n];
       v.odd = pending[n].odd;
       for (size_t g = 0; g < plans[n].groups.size(); ++g) {
         auto& grp = plans[n].groups[g];
         if (grp.items.size() >= 2) {
-          expand(summed[{n, g}], grp.o, 1.0, grp.par, v.blocks);
+          expand(summed.at({n, g}), grp.o, 1.0, grp.par, v.blocks);
         } else if (grp.items.size() == 1) {
           auto& itm = grp.items[0];
-          expand(blocks(itm.src, itm.T), grp.o, itm.coef, grp.par, v.blocks);
+          expand(blocks_ro(itm.src, itm.T), grp.o, itm.coef, grp.par, v.blocks);
         }
       }
-      if (!v.blocks.empty()) E.ops[pending[n].key] = v;
-    }
+    });
+    for (size_t n = 0; n < plans.size(); ++n)
+      if (!views[n].blocks.empty()) E.ops[pending[n].key] = std::move(views[n]);
   }
 };
 
