@@ -159,7 +159,9 @@ typedef struct {
   int n_steps;           /* two-site optimisations (2L-4) */
 } qcdmrg_sweep_report;
 
-/* Create a context on cfg->device. Errors: EINVAL, ECUDA, ENOMEM. */
+/* Create a context on cfg->device. Errors: EINVAL (unknown symmetry, negative
+ * budgets, pair_switch < 0, sum_gemm outside -1..1; checked before any CUDA
+ * call), ECUDA, ENOMEM. */
 int qcdmrg_create(qcdmrg_ctx** out, const qcdmrg_config* cfg);
 int qcdmrg_destroy(qcdmrg_ctx* ctx);
 /* Message of the last failed call (empty if none); owned by the context. */

@@ -84,6 +84,10 @@ int qcdmrg_create(qcdmrg_ctx** out, const qcdmrg_config* cfg) {
   if (!out || !cfg) return QCDMRG_EINVAL;
   *out = nullptr;
   if (cfg->symmetry != QCDMRG_U1) return QCDMRG_EINVAL;
+  // the configuration is checked before any CUDA call
+  if (!(cfg->hbm_budget_gb >= 0) || !(cfg->tmp_budget_gb >= 0) || cfg->pair_switch < 0 || cfg->sum_gemm < -1 ||
+      cfg->sum_gemm > 1)
+    return QCDMRG_EINVAL;
   auto* c = new qcdmrg_ctx();
   try {
     c->device = cfg->device;
@@ -92,12 +96,9 @@ int qcdmrg_create(qcdmrg_ctx** out, const qcdmrg_config* cfg) {
     c->eng.ex = c->be.ex;
     c->eng.pr = c->be.pr;
     c->eng.tmp_budget = (int64_t)(gb * 1e9 / 8);
-    if (cfg->hbm_budget_gb < 0) throw std::invalid_argument("hbm_budget_gb");
     c->eng.hbm_budget = (int64_t)(cfg->hbm_budget_gb * 1e9);
     c->eng.autotune = cfg->autotune_off == 0;
-    if (cfg->pair_switch < 0) throw std::invalid_argument("pair_switch");
     c->eng.pair_switch = cfg->pair_switch;
-    if (cfg->sum_gemm < -1 || cfg->sum_gemm > 1) throw std::invalid_argument("sum_gemm");
     c->eng.sum_gemm = cfg->sum_gemm;
   } catch (const std::invalid_argument&) {
     delete c;

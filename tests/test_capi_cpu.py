@@ -35,3 +35,18 @@ def test_create_without_device_fails_cleanly():
 def test_header_compiles_as_c():
     r = subprocess.run(["gcc", "-fsyntax-only", "-x", "c", HEADER], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+@pytest.mark.parametrize("field,value", [("pair_switch", -1), ("sum_gemm", 2), ("sum_gemm", -2),
+                                         ("hbm_budget_gb", -1.0), ("tmp_budget_gb", -1.0), ("symmetry", 7)])
+def test_create_rejects_bad_configuration_before_cuda(field, value):
+    """Configuration errors are EINVAL whether or not a device is present (no CUDA call is
+    made for them)."""
+    import paper_2603_28648_b300 as qd
+    path = ensure_built()
+    lib = ctypes.CDLL(path)
+    cfg = qd.Config(qd.U1, 0, 0.0, 0.0, 0, 0, 0)
+    setattr(cfg, field, value)
+    h = ctypes.c_void_p()
+    assert lib.qcdmrg_create(ctypes.byref(h), ctypes.byref(cfg)) == -1
+    assert not h.value
