@@ -73,7 +73,8 @@ def test_library_task_lists_match_the_oracle(host_exec, tmp_path, L, N, two_sz, 
     assert np.linalg.norm(st - ref) <= 1e-12 * np.linalg.norm(ref)
 
 
-def test_library_task_lists_on_an_su2_state(host_exec, tmp_path):
+@pytest.mark.parametrize("switch", [0, 3])
+def test_library_task_lists_on_an_su2_state(host_exec, tmp_path, switch):
     from oracle.fci import FCI
     from oracle.mpssu2 import TangentSU2, to_u1
     t = TangentSU2(7, 7, 1, 2, cap=2, seed=9)
@@ -81,7 +82,7 @@ def test_library_task_lists_on_an_su2_state(host_exec, tmp_path):
     psi = np.random.default_rng(4).normal(size=C.shape[1])
     mps.psi = mps.psi_from_flat(C @ psi)
     h, V = q.make_integrals(7, 13)
-    s64, st = _run(host_exec, tmp_path, mps, h, V)
+    s64, st = _run(host_exec, tmp_path, mps, h, V, switch)
     ref = t.heff(FCI(h, V, 7, 1), psi)
     for s in (s64, st):
         assert np.linalg.norm(C.T @ s - ref) <= 1e-12 * np.linalg.norm(ref)
