@@ -333,6 +333,25 @@ int qcdmrg_rdm1(qcdmrg_ctx* ctx, double* gamma);
  */
 int qcdmrg_rdm2(qcdmrg_ctx* ctx, double* gamma2);
 
+/*
+ * The same two-particle density matrix element by element, without the
+ * permutation average: Gamma_pqrs = sum over spins s, t of
+ * <a+_{p,s} a+_{r,t} a_{s,t} a_{q,s}> / <Psi|Psi> (orbital indices p, q, r, s;
+ * L^4 row-major, caller-allocated). Each element is measured once, at the
+ * centre (o3 - 1, o3) for its sorted orbitals o1 <= o2 <= o3 <= o4 (o3 >= 1),
+ * where at most two of its operators fall on the left block (stored a+, A, B
+ * operators), any number on the two sites and at most one on the right block:
+ * O(L^4) single-term products at the centres instead of L^4/8 environment
+ * builds, so that active spaces of the paper's size are in reach. The centre
+ * walks the chain once by exact moves (every state above the rounding noise of
+ * its sector's density-matrix eigenvalues is kept) and returns to its bond;
+ * the state is unchanged, its gauge and bond dimensions may change. With
+ * pair_switch set, the environment is rebuilt with normal pairs on the left
+ * for the walk and the switched one restored afterwards.
+ * Errors: ESTATE (no environment), EINVAL, ENOMEM, ECUDA.
+ */
+int qcdmrg_rdm2_sweep(qcdmrg_ctx* ctx, double* gamma2);
+
 /* Diagonal of H_eff at the centre (psi layout, n = psi size), as used by the
  * Davidson preconditioner: sum over terms of c_t diag(O_L) (x) diag(O_R)
  * restricted to diagonal quantum-number blocks. */

@@ -77,7 +77,7 @@ EXPORTS = [
     "qcdmrg_get_bond", "qcdmrg_get_psi", "qcdmrg_check_device", "qcdmrg_davidson",
     "qcdmrg_truncate", "qcdmrg_move_center", "qcdmrg_sweep", "qcdmrg_heff_diag",
     "qcdmrg_apply_heff_noalloc", "qcdmrg_graph_create", "qcdmrg_graph_launch",
-    "qcdmrg_graph_info", "qcdmrg_graph_destroy", "qcdmrg_rdm1", "qcdmrg_rdm2", "qcdmrg_set_psi",
+    "qcdmrg_graph_info", "qcdmrg_graph_destroy", "qcdmrg_rdm1", "qcdmrg_rdm2", "qcdmrg_rdm2_sweep", "qcdmrg_set_psi",
     "qcdmrg_export_mps", "qcdmrg_checkpoint", "qcdmrg_restore", "qcdmrg_psi_layout",
     "qcdmrg_energy_grad",
 ]
@@ -125,6 +125,7 @@ def load(path=None):
     lib.qcdmrg_graph_destroy.argtypes = [P]
     lib.qcdmrg_rdm1.argtypes = [P, dp]
     lib.qcdmrg_rdm2.argtypes = [P, dp]
+    lib.qcdmrg_rdm2_sweep.argtypes = [P, dp]
     lib.qcdmrg_export_mps.argtypes = [P, ip, ip, ip, ip, ctypes.c_int, dp, ctypes.c_size_t, ip,
                                       ctypes.POINTER(ctypes.c_size_t)]
     lib.qcdmrg_checkpoint.argtypes = [P, ctypes.c_char_p]
@@ -300,6 +301,13 @@ class Context:
         (L^4/8 environment builds: small active spaces)."""
         g = np.empty((L, L, L, L))
         self._check(self.lib.qcdmrg_rdm2(self.h, _dptr(g)))
+        return g
+
+    def rdm2_sweep(self, L):
+        """Spin-summed 2-RDM element by element (no permutation average), measured while the
+        centre walks the chain once (O(L^4) small products; the centre returns to its bond)."""
+        g = np.empty((L, L, L, L))
+        self._check(self.lib.qcdmrg_rdm2_sweep(self.h, _dptr(g)))
         return g
 
     def heff_diag(self):

@@ -678,6 +678,17 @@ int qcdmrg_rdm2(qcdmrg_ctx* ctx, double* gamma2) {
   });
 }
 
+int qcdmrg_rdm2_sweep(qcdmrg_ctx* ctx, double* gamma2) {
+  return guard(ctx, [&]() {
+    Engine& E = ctx->eng;
+    if (!E.have_env) throw Fail{QCDMRG_ESTATE, "build_env first"};
+    if (!gamma2) throw Fail{QCDMRG_EINVAL, "null argument"};
+    std::vector<double> g = E.rdm2_sweep();
+    std::copy(g.begin(), g.end(), gamma2);
+    return QCDMRG_OK;
+  });
+}
+
 int qcdmrg_heff_diag(qcdmrg_ctx* ctx, double* out, size_t n) {
   return guard(ctx, [&]() {
     Engine& E = ctx->eng;

@@ -246,6 +246,11 @@ std::vector<Key> block_keys(bool left, bool normal, int cut, int L);
 void enlarge(const EnvBlock& B, const Integrals& I, Executor& ex, Enlarged& out, double* flops,
              bool normal);
 
+// An operator of the enlarged block E (built from B and one site) given as a
+// sum of block-operator (x) site-operator products, each in operator order
+// (left: O_B O_s; right: O_s O_B) as the enlargement rules write them.
+OpView product_view(const EnvBlock& B, const Integrals& I, Enlarged& E, const std::vector<Contrib>& cs, bool odd);
+
 // Renormalize enlarged operators with the new site tensor: for each product
 // sector that is kept, a dense matrix (left: [dim_prod x d_new], right:
 // [d_new x dim_prod]) at device address tensor + off[prod sector].

@@ -4,6 +4,7 @@
 #include "engine.hpp"
 
 #include <algorithm>
+#include <deque>
 #include <chrono>
 #include <cmath>
 #include <mutex>
@@ -535,7 +536,11 @@ DavResult Engine::davidson(const DavOpts& o) {
 }
 
 double Engine::truncate_move(int D, int dir, double drop_below) {
-  drop_below = std::max(drop_below, WEIGHT_FLOOR);
+  // a negative drop_below keeps every weight above the rounding noise of its
+  // own sector's eigenvalues (exact moves for measurements); otherwise weights
+  // at the global rounding floor are always dropped
+  const bool exact = drop_below < 0;
+  drop_below = exact ? 0.0 : std::max(drop_below, WEIGHT_FLOOR);
   const QN target{N, two_s};
   const ProdBasis& LB = Lp.pb;
   const ProdBasis& RB = Rp.pb;
@@ -610,9 +615,19 @@ double Engine::truncate_move(int D, int dir, double drop_below) {
   std::vector<int> keep(secs.size(), 0);
   double disc = 0;
   int nk = 0;
+  // exact moves: eigenvalues of a sector's density matrix carry an absolute
+  // rounding error of about n eps lambda_max(sector); anything below 8 times
+  // that is not distinguishable from zero and is dropped
+  std::vector<double> noise(secs.size(), 0.0);
+  if (exact)
+    for (size_t k = 0; k < secs.size(); ++k) {
+      double mx = 0.0;
+      for (double v : lam[k]) mx = std::max(mx, v);
+      noise[k] = 8.0 * (double)lam[k].size() * 2.220446049250313e-16 * mx;
+    }
   for (auto& c : cand) {
     double l = -std::get<0>(c);
-    if (nk < D && l > drop_below && l > above) {
+    if (nk < D && l > drop_below && l > noise[std::get<3>(c)] && l > above) {
       keep[std::get<3>(c)]++;
       ++nk;
     } else {
@@ -878,6 +893,155 @@ std::vector<double> Engine::rdm1() {
       if (!t.empty()) g[(size_t)p * L + q] = expect(t) / nrm;
     }
   return g;
+}
+
+std::vector<double> Engine::rdm2_sweep() {
+  // Gamma_pqrs = sum over spins sigma, tau of <a+_{p sigma} a+_{r tau} a_{s tau} a_{q sigma}>,
+  // each element measured at the one centre (s1, s2 = s1 + 1) where its four
+  // operators split into at most two on the left block (stored C, A, B), any
+  // number on each of the two sites (exact 4x4 products) and at most one on
+  // the right block (stored C): with o1 <= o2 <= o3 <= o4 the sorted orbitals,
+  // s2 = max(o3, 1). The centre walks the chain once by exact moves (every
+  // state of positive weight kept, so the state is not changed at first order
+  // as it would be by dropping weights at the rounding floor), then returns to
+  // its bond.
+  if (!have_env) throw StateError("build_env first");
+  if (pair_switch > 0) {
+    // the walk reads normal pairs from every left block
+    const int saved = pair_switch;
+    pair_switch = 0;
+    std::vector<double> g;
+    try {
+      build_env();
+      g = rdm2_sweep();
+    } catch (...) {
+      pair_switch = saved;
+      build_env();
+      throw;
+    }
+    pair_switch = saved;
+    build_env();
+    return g;
+  }
+  const size_t L4 = (size_t)L * L * L * L;
+  auto at = [&](int p, int q, int r, int s) { return (((size_t)p * L + q) * L + r) * L + s; };
+  // representatives of {pqrs, rspq, qpsr, srqp} (equal for a real state), by centre
+  std::vector<std::vector<std::array<int, 4>>> todo(L - 1);
+  for (int p = 0; p < L; ++p)
+    for (int q = 0; q < L; ++q)
+      for (int r = 0; r < L; ++r)
+        for (int s = 0; s < L; ++s) {
+          const std::array<int, 4> t{p, q, r, s};
+          if (std::array<int, 4>{r, s, p, q} < t || std::array<int, 4>{q, p, s, r} < t ||
+              std::array<int, 4>{s, r, q, p} < t)
+            continue;
+          std::array<int, 4> o = t;
+          std::sort(o.begin(), o.end());
+          todo[std::max(o[2], 1) - 1].push_back(t);
+        }
+  std::vector<double> G(L4, 0.0);
+  auto get = [](const EnvBlock& B, Key k) -> const OpView* {
+    auto it = B.ops.find(k);
+    if (it == B.ops.end() || it->second.empty()) return nullptr;
+    return &it->second;
+  };
+  const int c0 = center;
+  while (center > 0) truncate_move(1 << 30, -1, -1.0);
+  for (int s1 = 0; s1 <= L - 2; ++s1) {
+    if (s1 > 0) truncate_move(1 << 30, +1, -1.0);
+    const int s2 = s1 + 1;
+    const EnvBlock& LB = lenv.at(s1);
+    const EnvBlock& RB = renv.at(s2 + 1);
+    const int64_t n = lay.size;
+    const double nrm = ex->dot(dpsi, dpsi, n);
+    if (!(nrm > 0)) throw std::runtime_error("zero wavefunction");
+    uint64_t tau = ex->alloc(std::max<int64_t>(1, n));
+    try {
+      for (const auto& t : todo[s1]) {
+        std::deque<OpView> views;
+        std::vector<CenterTerm> terms;
+        for (int sg = 0; sg < 2; ++sg)
+          for (int tu = 0; tu < 2; ++tu) {
+            struct Op { bool cre; int mode, orb; };
+            const Op ops[4] = {{true, 2 * t[0] + sg, t[0]}, {true, 2 * t[2] + tu, t[2]},
+                               {false, 2 * t[3] + tu, t[3]}, {false, 2 * t[1] + sg, t[1]}};
+            if (ops[0].mode == ops[1].mode || ops[2].mode == ops[3].mode) continue;
+            int grp[4];
+            for (int i = 0; i < 4; ++i) grp[i] = ops[i].orb < s1 ? 0 : ops[i].orb == s1 ? 1 : ops[i].orb == s2 ? 2 : 3;
+            int inv = 0;
+            for (int i = 0; i < 4; ++i)
+              for (int j = i + 1; j < 4; ++j) inv += grp[i] > grp[j];
+            std::vector<Op> g[4];
+            for (int i = 0; i < 4; ++i) g[grp[i]].push_back(ops[i]);
+            if (g[3].size() > 1 || g[0].size() > 2) throw std::logic_error("rdm2_sweep: element at the wrong centre");
+            Mat4 m1 = Mat4::id(), m2 = Mat4::id();
+            for (const Op& o : g[1]) m1 = m1 * (o.cre ? cre(o.mode & 1) : ann(o.mode & 1));
+            for (const Op& o : g[2]) m2 = m2 * (o.cre ? cre(o.mode & 1) : ann(o.mode & 1));
+            // left block: identity, C_k / C_k^T, or a pair in operator order
+            std::vector<Contrib> xl;
+            const bool par1 = g[1].size() & 1;
+            auto add = [&](const OpView* src, bool T, double c) {
+              Contrib x;
+              x.src = src; x.srcT = T; x.o = m1; x.coef = c; x.par = par1;
+              xl.push_back(x);
+            };
+            if (g[0].empty()) {
+              add(nullptr, false, 1.0);
+            } else if (g[0].size() == 1) {
+              if (auto C = get(LB, Key(F_C, g[0][0].mode))) add(C, !g[0][0].cre, 1.0);
+            } else {
+              const Op a = g[0][0], b = g[0][1];
+              const int k1 = a.mode, k2 = b.mode;
+              if (a.cre && b.cre) {          // a+_k1 a+_k2
+                if (auto A = get(LB, Key(F_A, std::min(k1, k2), std::max(k1, k2)))) add(A, false, k1 < k2 ? 1.0 : -1.0);
+              } else if (!a.cre && !b.cre) { // a_k1 a_k2 = (a+_k2 a+_k1)^T
+                if (auto A = get(LB, Key(F_A, std::min(k1, k2), std::max(k1, k2)))) add(A, true, k2 < k1 ? 1.0 : -1.0);
+              } else if (a.cre) {            // a+_k1 a_k2
+                if (auto B = get(LB, Key(F_B, k1, k2))) add(B, false, 1.0);
+              } else {                       // a_k1 a+_k2 = d_k1k2 - a+_k2 a_k1
+                if (auto B = get(LB, Key(F_B, k2, k1))) add(B, false, -1.0);
+                if (k1 == k2) add(nullptr, false, 1.0);
+              }
+            }
+            if (xl.empty()) continue;
+            const OpView* rsrc = nullptr;
+            bool rT = false;
+            if (g[3].size() == 1) {
+              rsrc = get(RB, Key(F_C, g[3][0].mode));
+              if (!rsrc) continue;
+              rT = !g[3][0].cre;
+            }
+            Contrib yr;
+            yr.src = rsrc; yr.srcT = rT; yr.o = m2; yr.coef = 1.0; yr.par = g[3].size() & 1;
+            views.push_back(product_view(LB, I, Lp, xl, (g[0].size() + g[1].size()) & 1));
+            const OpView* X = &views.back();
+            views.push_back(product_view(RB, I, Rp, {yr}, (g[2].size() + g[3].size()) & 1));
+            const OpView* Y = &views.back();
+            if (X->empty() || Y->empty()) continue;
+            terms.push_back({X, false, Y, false, (inv & 1) ? -1.0 : 1.0});
+          }
+        double v = 0.0;
+        if (!terms.empty()) {
+          HeffPlan pl = plan_terms(Lp, Rp, lay, terms, tmp_budget);
+          ex->tmp(std::max<int64_t>(1, pl.tmp_elems));
+          ex->zero(tau, n);
+          for (size_t k = 0; k < pl.stage1.size(); ++k) {
+            ex->run(pl.stage1[k], dpsi, tau);
+            ex->run(pl.stage2[k], dpsi, tau);
+          }
+          v = ex->dot(dpsi, tau, n) / nrm;
+        }
+        const int p = t[0], q = t[1], r = t[2], s = t[3];
+        G[at(p, q, r, s)] = G[at(r, s, p, q)] = G[at(q, p, s, r)] = G[at(s, r, q, p)] = v;
+      }
+    } catch (...) {
+      ex->release(tau);
+      throw;
+    }
+    ex->release(tau);
+  }
+  while (center > c0) truncate_move(1 << 30, -1, -1.0);
+  return G;
 }
 
 std::vector<double> Engine::rdm2() {

@@ -96,8 +96,10 @@ struct Engine {
   void prepare_center();
   void heff(uint64_t psi, uint64_t sig, void* stream, int prec);
   DavResult davidson(const DavOpts& o);
-  // truncate the centre to D states (drop weights <= drop_below), renormalize
-  // and move the centre by dir (+1 right, -1 left); returns the discarded weight
+  // truncate the centre to D states (drop weights <= drop_below, at least the
+  // rounding floor 1e-14; a negative drop_below keeps every positive weight),
+  // renormalize and move the centre by dir (+1 right, -1 left); returns the
+  // discarded weight
   double truncate_move(int D, int dir, double drop_below);
   // <psi| sum_t c_t O_L (x) O_R |psi> for a list of centre terms
   double expect(const std::vector<CenterTerm>& terms);
@@ -109,6 +111,11 @@ struct Engine {
   // invariant; by exact linearity in V (one environment build per permutation
   // orbit, L^4/8 of them); the integrals and the environment are restored
   std::vector<double> rdm2();
+  // the same matrix without the permutation average, every element measured
+  // once while the centre walks the chain (O(L^4) single-term products at the
+  // centres instead of L^4/8 environment builds); the centre returns to its
+  // bond, the MPS re-gauged by exact moves
+  std::vector<double> rdm2_sweep();
 };
 
 }  // namespace qd

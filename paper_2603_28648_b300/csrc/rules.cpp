@@ -554,6 +554,14 @@ Contrib C_(const OpView* src, bool T, const Mat4& o, double coef, bool par) {
 
 }  // namespace
 
+OpView product_view(const EnvBlock& B, const Integrals& I, Enlarged& E, const std::vector<Contrib>& cs, bool odd) {
+  Ctx x(B, I, E);
+  OpView v;
+  v.odd = odd;
+  for (const Contrib& c : cs) x.expand(x.src_blocks(c.src, c.srcT), c.o, c.coef, c.par, v.blocks);
+  return v;
+}
+
 void enlarge(const EnvBlock& B, const Integrals& I, Executor& ex, Enlarged& E, double* flops, bool normal) {
   if (normal && !B.normal) throw std::logic_error("enlarge: complementary pair operators cannot become normal");
   const int L = I.L;

@@ -15,6 +15,8 @@
 // usage: host_exec in.bin out.bin                       (one H_eff psi, both plans)
 //        host_exec in.bin out.bin sweep D nsweeps tol     (full FP64 sweeps)
 //        host_exec in.bin out.bin rdm1                    (1-RDM, centre at L-2)
+//        host_exec in.bin out.bin rdm2sweep               (2-RDM by the centre walk, then
+//                                                          psi and sigma at the centre)
 //   in : int64 L, N, two_sz, center, nsec_len (= L+1), sec_len, data_len;
 //        h (L*L), V (L^4) doubles; bond_nsec, bond_sec int32; data doubles
 //   out: sigma of the FP64 task lists, then sigma of the tiled work items; or
@@ -381,6 +383,23 @@ int main(int argc, char** argv) {
       if (!o2) throw std::runtime_error("cannot open output");
       std::fwrite(energies.data(), 8, energies.size(), o2);
       std::fclose(o2);
+      return 0;
+    }
+    if (argc >= 4 && std::string(argv[3]) == "rdm2sweep") {
+      const std::vector<double> g = E.rdm2_sweep();
+      FILE* o4 = std::fopen(argv[2], "wb");
+      if (!o4) throw std::runtime_error("cannot open output");
+      std::fwrite(g.data(), 8, g.size(), o4);
+      // then sigma at the centre the walk returned to, to check that the state is unchanged
+      const int64_t n2 = E.lay.size;
+      const uint64_t sg2 = ex.alloc(n2);
+      E.heff(E.dpsi, sg2, nullptr, 0);
+      std::vector<double> ps((size_t)n2), sv((size_t)n2);
+      ex.download(ps.data(), E.dpsi, n2);
+      ex.download(sv.data(), sg2, n2);
+      std::fwrite(ps.data(), 8, ps.size(), o4);
+      std::fwrite(sv.data(), 8, sv.size(), o4);
+      std::fclose(o4);
       return 0;
     }
     if (argc >= 4 && std::string(argv[3]) == "rdm1") {

@@ -122,3 +122,35 @@ def test_switch_leaves_sigma_unchanged_L36():
                 x = ctx.apply_heff(psi, qd.PRECISIONS[prec])
                 assert np.linalg.norm(x - ref) <= BOUND[prec] * np.linalg.norm(ref), prec
         ctx.close()
+
+
+def test_rdm2_by_centre_walk_matches_brute_force():
+    """qcdmrg_rdm2_sweep (every element at its centre, exact moves) against the 2-RDM of the
+    expanded MPS vector, its permutation average against qcdmrg_rdm2, and the state after the
+    walk unchanged (same sigma at the original centre, up to the re-gauging)."""
+    import paper_2603_28648_b300 as qd
+    from oracle.fci import FCI
+    from oracle.mpsu1 import MPSU1, Projector, export_abi
+    ensure_built()
+    L, N, D, c = 6, 5, 16, 2
+    m = MPSU1.from_raw(q.random_mps_blocks(L, N, 1, D, q.SYM_U1, 6, c))
+    h, V = q.make_integrals(L, 7)
+    ctx = qd.Context()
+    ctx.load_integrals(h, V)
+    ctx.set_target(N, 1)
+    ctx.import_mps(L, c, *export_abi(m))
+    ctx.build_env()
+    psi0 = m.psi_to_flat()
+    e0 = psi0 @ ctx.apply_heff(psi0) / (psi0 @ psi0)
+    G = ctx.rdm2_sweep(L)
+    f = FCI(h, V, N, 1)
+    v = Projector(m, f.space).apply(m.psi)
+    g1, Gf = f.rdm12(v / np.linalg.norm(v))
+    assert np.abs(G - Gf).max() <= 1e-10
+    axes = [(0, 1, 2, 3), (1, 0, 2, 3), (0, 1, 3, 2), (1, 0, 3, 2),
+            (2, 3, 0, 1), (3, 2, 0, 1), (2, 3, 1, 0), (3, 2, 1, 0)]
+    Gs = sum(G.transpose(a) for a in axes) / 8.0
+    assert np.abs(Gs - ctx.rdm2(L)).max() <= 1e-10
+    psi1 = ctx.psi()
+    e1 = psi1 @ ctx.apply_heff(psi1) / (psi1 @ psi1)
+    assert abs(e1 - e0) <= 1e-10 * abs(e0)
