@@ -344,8 +344,9 @@ int qcdmrg_rdm2(qcdmrg_ctx* ctx, double* gamma2);
  * O(L^4) single-term products at the centres instead of L^4/8 environment
  * builds, so that active spaces of the paper's size are in reach. The centre
  * walks the chain once by exact moves (every state above the rounding noise of
- * its sector's density-matrix eigenvalues is kept) and returns to its bond;
- * the state is unchanged, its gauge and bond dimensions may change. With
+ * its sector's density-matrix eigenvalues is kept); afterwards the MPS (site
+ * tensors, bonds, psi at its centre) is restored as it was and the environment
+ * rebuilt once. With
  * pair_switch set, the environment is rebuilt with normal pairs on the left
  * for the walk and the switched one restored afterwards.
  * Errors: ESTATE (no environment), EINVAL, ENOMEM, ECUDA.

@@ -305,7 +305,7 @@ class Context:
 
     def rdm2_sweep(self, L):
         """Spin-summed 2-RDM element by element (no permutation average), measured while the
-        centre walks the chain once (O(L^4) small products; the centre returns to its bond)."""
+        centre walks the chain once (O(L^4) small products; the MPS is restored afterwards)."""
         g = np.empty((L, L, L, L))
         self._check(self.lib.qcdmrg_rdm2_sweep(self.h, _dptr(g)))
         return g

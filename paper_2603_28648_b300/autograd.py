@@ -4,14 +4,19 @@ E(psi, h, V) = <psi| H_eff(h, V) |psi> / <psi|psi> at the context's centre.
 Backward: dE/dpsi = 2 (H_eff psi - E psi) / <psi|psi> (one H_eff psi in the
 library), dE/dh_pq = gamma_pq, the spin-summed one-particle density matrix
 of the state (qcdmrg_rdm1), and dE/dV_pqrs = 1/2 Gamma_pqrs, the spin-summed
-2-RDM averaged over the 8 permutations of (pq|rs) (qcdmrg_rdm2, the gradient
-for an 8-fold symmetric V) -- the quantities CASSCF orbital gradients are
-built from.
+2-RDM averaged over the 8 permutations of (pq|rs) (the gradient for an 8-fold
+symmetric V) -- the quantities CASSCF orbital gradients are built from. Gamma
+comes from qcdmrg_rdm2 (one environment build per permutation orbit) up to
+PROBE_MAX_L orbitals and from the centre walk of qcdmrg_rdm2_sweep beyond.
 """
 
 import torch
 
 from . import FP64
+
+PROBE_MAX_L = 10
+_AXES = [(0, 1, 2, 3), (1, 0, 2, 3), (0, 1, 3, 2), (1, 0, 3, 2),
+         (2, 3, 0, 1), (3, 2, 0, 1), (2, 3, 1, 0), (3, 2, 1, 0)]
 
 
 class DMRGEnergy(torch.autograd.Function):
@@ -45,6 +50,10 @@ class DMRGEnergy(torch.autograd.Function):
             g = fctx.context.rdm1(fctx.L)
             dh = torch.as_tensor(g, dtype=torch.float64) * gE.detach().cpu()
         if fctx.needs_input_grad[2]:
-            G = fctx.context.rdm2(fctx.L)
+            if fctx.L <= PROBE_MAX_L:
+                G = fctx.context.rdm2(fctx.L)
+            else:
+                G1 = fctx.context.rdm2_sweep(fctx.L)
+                G = sum(G1.transpose(a) for a in _AXES) / 8.0
             dV = 0.5 * torch.as_tensor(G, dtype=torch.float64) * gE.detach().cpu()
         return dpsi, dh, dV, None, None

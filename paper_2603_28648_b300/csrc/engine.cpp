@@ -902,9 +902,9 @@ std::vector<double> Engine::rdm2_sweep() {
   // number on each of the two sites (exact 4x4 products) and at most one on
   // the right block (stored C): with o1 <= o2 <= o3 <= o4 the sorted orbitals,
   // s2 = max(o3, 1). The centre walks the chain once by exact moves (every
-  // state of positive weight kept, so the state is not changed at first order
-  // as it would be by dropping weights at the rounding floor), then returns to
-  // its bond.
+  // weight above its sector's rounding noise kept, so the state is not
+  // changed at first order as it would be by dropping weights at the global
+  // floor); afterwards the MPS and its environment are restored as they were.
   if (!have_env) throw StateError("build_env first");
   if (pair_switch > 0) {
     // the walk reads normal pairs from every left block
@@ -945,7 +945,45 @@ std::vector<double> Engine::rdm2_sweep() {
     if (it == B.ops.end() || it->second.empty()) return nullptr;
     return &it->second;
   };
-  const int c0 = center;
+  // the MPS before the walk, restored exactly afterwards (the walk re-gauges it)
+  struct Snap {
+    int center;
+    std::vector<Basis> bonds;
+    std::vector<std::vector<int64_t>> off;
+    std::vector<std::vector<int>> nb;
+    std::vector<std::vector<double>> site;
+    std::vector<double> psi;
+  } snap{center, bonds, site_off, site_nb, {}, get_psi_host()};
+  snap.site.resize(L);
+  for (int p = 0; p < L; ++p) {
+    if (!site[p]) continue;
+    const bool left = p < center;
+    const ProdBasis pb = make_prod(left ? bonds[p] : bonds[p + 1], left);
+    const Basis& to = left ? bonds[p + 1] : bonds[p];
+    int64_t n = 0;
+    for (int q = 0; q < pb.prod.nsec(); ++q)
+      if (site_off[p][q] >= 0) n = std::max<int64_t>(n, site_off[p][q] + (int64_t)pb.prod.dim[q] * to.dim[site_nb[p][q]]);
+    snap.site[p].resize((size_t)n);
+    if (n) ex->download(snap.site[p].data(), site[p], n);
+  }
+  auto restore = [&]() {
+    clear_env();
+    for (auto& t : site)
+      if (t) ex->release(t);
+    site.assign(L, 0);
+    for (int p = 0; p < L; ++p) {
+      if (snap.site[p].empty()) continue;
+      site[p] = ex->alloc((int64_t)snap.site[p].size());
+      ex->upload(site[p], snap.site[p].data(), (int64_t)snap.site[p].size());
+    }
+    bonds = snap.bonds;
+    site_off = snap.off;
+    site_nb = snap.nb;
+    center = snap.center;
+    set_psi_host(snap.psi);
+    build_env();
+  };
+  try {
   while (center > 0) truncate_move(1 << 30, -1, -1.0);
   for (int s1 = 0; s1 <= L - 2; ++s1) {
     if (s1 > 0) truncate_move(1 << 30, +1, -1.0);
@@ -1040,7 +1078,11 @@ std::vector<double> Engine::rdm2_sweep() {
     }
     ex->release(tau);
   }
-  while (center > c0) truncate_move(1 << 30, -1, -1.0);
+  } catch (...) {
+    restore();
+    throw;
+  }
+  restore();
   return G;
 }
 

@@ -113,8 +113,8 @@ struct Engine {
   std::vector<double> rdm2();
   // the same matrix without the permutation average, every element measured
   // once while the centre walks the chain (O(L^4) single-term products at the
-  // centres instead of L^4/8 environment builds); the centre returns to its
-  // bond, the MPS re-gauged by exact moves
+  // centres instead of L^4/8 environment builds); the MPS is restored
+  // afterwards and its environment rebuilt
   std::vector<double> rdm2_sweep();
 };
 

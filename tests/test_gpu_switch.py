@@ -126,8 +126,8 @@ def test_switch_leaves_sigma_unchanged_L36():
 
 def test_rdm2_by_centre_walk_matches_brute_force():
     """qcdmrg_rdm2_sweep (every element at its centre, exact moves) against the 2-RDM of the
-    expanded MPS vector, its permutation average against qcdmrg_rdm2, and the state after the
-    walk unchanged (same sigma at the original centre, up to the re-gauging)."""
+    expanded MPS vector, its permutation average against qcdmrg_rdm2, and the MPS restored
+    after the walk (same psi, same H_eff psi)."""
     import paper_2603_28648_b300 as qd
     from oracle.fci import FCI
     from oracle.mpsu1 import MPSU1, Projector, export_abi
@@ -151,6 +151,6 @@ def test_rdm2_by_centre_walk_matches_brute_force():
             (2, 3, 0, 1), (3, 2, 0, 1), (2, 3, 1, 0), (3, 2, 1, 0)]
     Gs = sum(G.transpose(a) for a in axes) / 8.0
     assert np.abs(Gs - ctx.rdm2(L)).max() <= 1e-10
-    psi1 = ctx.psi()
-    e1 = psi1 @ ctx.apply_heff(psi1) / (psi1 @ psi1)
-    assert abs(e1 - e0) <= 1e-10 * abs(e0)
+    assert np.array_equal(ctx.psi(), psi0)      # the MPS is restored after the walk
+    e1 = psi0 @ ctx.apply_heff(psi0) / (psi0 @ psi0)
+    assert abs(e1 - e0) <= 1e-13 * abs(e0)

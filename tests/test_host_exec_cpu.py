@@ -217,8 +217,9 @@ def test_switch_leaves_sigma_unchanged_at_the_cas54_36_shape(host_exec, tmp_path
                                                          (7, 7, 1, 16, 5, 8, 3)])
 def test_rdm2_by_centre_walk_matches_brute_force(host_exec, tmp_path, L, N, two_sz, D, c, seed, switch):
     """The library's centre-walk 2-RDM (every element measured once at its centre, exact
-    moves) against the 2-RDM of the expanded MPS vector, element by element; the state after
-    the walk gives the same energy as the density matrices (E = sum h gamma + 1/2 sum V Gamma)."""
+    moves) against the 2-RDM of the expanded MPS vector, element by element; afterwards the
+    MPS is the one imported (same psi at the same centre) and its energy equals
+    sum h gamma + 1/2 sum V Gamma."""
     from oracle.fci import FCI
     from oracle.mpsu1 import MPSU1, Projector
     m = MPSU1.from_raw(q.random_mps_blocks(L, N, two_sz, D, q.SYM_U1, seed, c))
@@ -237,5 +238,6 @@ def test_rdm2_by_centre_walk_matches_brute_force(host_exec, tmp_path, L, N, two_
     rest = out[L ** 4:]
     n = rest.size // 2
     psi, sig = rest[:n], rest[n:]
+    assert np.array_equal(psi, m.psi_to_flat())        # the MPS is restored after the walk
     E = psi @ sig / (psi @ psi)
     assert abs(np.sum(h * g1) + 0.5 * np.sum(V * G) - E) <= 1e-10 * abs(E)
