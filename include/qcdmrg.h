@@ -263,7 +263,8 @@ int qcdmrg_psi_layout(const qcdmrg_ctx* ctx, int* blocks, int cap, int* nblocks,
  * product), dpsi = dE/dpsi = 2 (H_eff psi - E psi)/<psi|psi> (psi size),
  * gamma1 = dE/dh (L*L, as qcdmrg_rdm1: needs the centre at (L-2, L-1)),
  * gamma2 = 2 dE/dV for 8-fold symmetric V (L^4, as qcdmrg_rdm2: L^4/8
- * environment builds). The derivatives the paper's DMRG-SCF needs (New
+ * environment builds, for L <= 10; beyond, the permutation average of
+ * qcdmrg_rdm2_sweep). The derivatives the paper's DMRG-SCF needs (New
  * benchmark system section). Errors: ESTATE, EINVAL, ENOMEM, ECUDA.
  */
 int qcdmrg_energy_grad(qcdmrg_ctx* ctx, double* energy, double* dpsi, double* gamma1, double* gamma2);

@@ -554,6 +554,20 @@ int qcdmrg_psi_layout(const qcdmrg_ctx* cctx, int* blocks, int cap, int* nblocks
   });
 }
 
+// Gamma averaged over the 8 index permutations that leave (pq|rs) invariant
+static std::vector<double> permutation_average(const std::vector<double>& G, int L) {
+  auto at = [L](int p, int q, int r, int s) { return (((size_t)p * L + q) * L + r) * L + s; };
+  std::vector<double> A(G.size());
+  for (int p = 0; p < L; ++p)
+    for (int q = 0; q < L; ++q)
+      for (int r = 0; r < L; ++r)
+        for (int s = 0; s < L; ++s)
+          A[at(p, q, r, s)] = (G[at(p, q, r, s)] + G[at(q, p, r, s)] + G[at(p, q, s, r)] + G[at(q, p, s, r)] +
+                               G[at(r, s, p, q)] + G[at(s, r, p, q)] + G[at(r, s, q, p)] + G[at(s, r, q, p)]) /
+                              8.0;
+  return A;
+}
+
 int qcdmrg_energy_grad(qcdmrg_ctx* ctx, double* energy, double* dpsi, double* gamma1, double* gamma2) {
   return guard(ctx, [&]() {
     Engine& E = ctx->eng;
@@ -586,7 +600,9 @@ int qcdmrg_energy_grad(qcdmrg_ctx* ctx, double* energy, double* dpsi, double* ga
       std::copy(g.begin(), g.end(), gamma1);
     }
     if (gamma2) {
-      std::vector<double> g = E.rdm2();
+      // environment-build probes while they are affordable, the centre walk
+      // (averaged over the 8 permutations of (pq|rs)) beyond
+      std::vector<double> g = E.L <= 10 ? E.rdm2() : permutation_average(E.rdm2_sweep(), E.L);
       std::copy(g.begin(), g.end(), gamma2);
     }
     return QCDMRG_OK;
