@@ -241,3 +241,29 @@ def test_rdm2_by_centre_walk_matches_brute_force(host_exec, tmp_path, L, N, two_
     assert np.array_equal(psi, m.psi_to_flat())        # the MPS is restored after the walk
     E = psi @ sig / (psi @ psi)
     assert abs(np.sum(h * g1) + 0.5 * np.sum(V * G) - E) <= 1e-10 * abs(E)
+
+
+def test_rdm2_by_centre_walk_identities_at_L12(host_exec, tmp_path):
+    """Beyond brute-force sizes (L=12, N=12, D=32): properties of any 2-RDM of the state —
+    sum_pr Gamma_pprr = N(N-1), the symmetries Gamma_pqrs = Gamma_rspq = Gamma_qpsr, and the
+    energy of the MPS (from H_eff psi after the walk) equal to sum h gamma + 1/2 sum V Gamma
+    with gamma_pq = sum_r Gamma_pqrr / (N-1); the last weighs every element by V."""
+    from oracle.mpsu1 import MPSU1
+    L, N, D, c = 12, 12, 32, 5
+    m = MPSU1.from_raw(q.random_mps_blocks(L, N, 0, D, q.SYM_U1, 5, c))
+    h, V = q.make_integrals(L, 6)
+    fin, fout = str(tmp_path / "w_in.bin"), str(tmp_path / "w_out.bin")
+    _write(fin, m, h, V)
+    r = subprocess.run([host_exec, fin, fout, "rdm2sweep"], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr
+    out = np.fromfile(fout, "<f8")
+    G = out[:L ** 4].reshape(L, L, L, L)
+    assert abs(np.einsum("pprr->", G) - N * (N - 1)) <= 1e-10
+    assert np.abs(G - G.transpose(2, 3, 0, 1)).max() <= 1e-13
+    assert np.abs(G - G.transpose(1, 0, 3, 2)).max() <= 1e-13
+    g = np.einsum("pqrr->pq", G) / (N - 1)
+    rest = out[L ** 4:]
+    n = rest.size // 2
+    psi, sig = rest[:n], rest[n:]
+    E = psi @ sig / (psi @ psi)
+    assert abs(np.sum(h * g) + 0.5 * np.sum(V * G) - E) <= 1e-11 * abs(E)
