@@ -154,3 +154,25 @@ def test_rdm2_by_centre_walk_matches_brute_force():
     assert np.array_equal(ctx.psi(), psi0)      # the MPS is restored after the walk
     e1 = psi0 @ ctx.apply_heff(psi0) / (psi0 @ psi0)
     assert abs(e1 - e0) <= 1e-13 * abs(e0)
+
+
+def test_rdm2_by_centre_walk_identities_L16():
+    """Beyond brute-force sizes (L=16, N=16, D=128, GPU-initialised MPS): the traces, the
+    symmetries and the energy identity E = sum h gamma + 1/2 sum V Gamma with gamma from the
+    contraction of Gamma."""
+    import paper_2603_28648_b300 as qd
+    ensure_built()
+    L, N, D = 16, 16, 128
+    h, V = q.make_integrals(L, 21)
+    ctx = qd.Context()
+    ctx.load_integrals(h, V)
+    ctx.set_target(N, 0)
+    ctx.init_mps(D, 3, 7)
+    ctx.build_env()
+    psi = ctx.psi()
+    E = psi @ ctx.apply_heff(psi) / (psi @ psi)
+    G = ctx.rdm2_sweep(L)
+    assert abs(np.einsum("pprr->", G) - N * (N - 1)) <= 1e-9
+    assert np.abs(G - G.transpose(2, 3, 0, 1)).max() <= 1e-12
+    g = np.einsum("pqrr->pq", G) / (N - 1)
+    assert abs(np.sum(h * g) + 0.5 * np.sum(V * G) - E) <= 1e-10 * abs(E)
