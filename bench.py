@@ -42,6 +42,8 @@ def parse():
                     help="one full sweep (L->R->L) with FP64 Davidson and with the mixed policy, same start")
     ap.add_argument("--batched", action="store_true",
                     help="16 independent problems (L 12..24, D 128..512) in one CUDA graph vs one by one")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="time the backward of E(psi, h, V): dE/dpsi, gamma and the centre-walk 2-RDM")
     ap.add_argument("--max-iter", type=int, default=300,
                     help="Davidson iteration cap per two-site step of --sweep (a step that hits it is kept)")
     ap.add_argument("--sweep-budget", type=float, default=300.0,
@@ -577,6 +579,48 @@ def run_sweep(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+def run_adjoint(args, rank, world, local):
+    """Backward of E(psi, h, V) through the public API at the last centre (L-2, L-1):
+    dE/dpsi (one FP64 H_eff psi), gamma = dE/dh from the stored operators, and the spin-summed
+    2-RDM element by element by the walk of the centre (qcdmrg_rdm2_sweep, O(L^4) single-term
+    products), each timed; checks E = sum h gamma + 1/2 sum V Gamma and the trace of Gamma."""
+    import numpy as np
+    import torch
+    import qcinputs as q
+    import paper_2603_28648_b300 as qd
+    torch.cuda.set_device(local)
+    L, N, D = args.L, args.N, args.D
+    h, V = q.make_integrals(L, q.integrals.BASE_SEED + 2)
+    ctx = qd.Context(device=local, hbm_budget_gb=args.hbm_budget, pair_switch=args.pair_switch,
+                     sum_gemm=args.sum_gemm)
+    ctx.load_integrals(h, V)
+    ctx.set_target(N, 0)
+    ctx.init_mps(D, q.integrals.BASE_SEED + 1002, L - 2)
+    ctx.build_env()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    E, dpsi, g1, _ = ctx.energy_grad(L, dpsi=True, gamma1=True, gamma2=False)
+    t1 = time.perf_counter()
+    G = ctx.rdm2_sweep(L)
+    t2 = time.perf_counter()
+    st = ctx.stats()
+    ident = float(np.sum(h * g1) + 0.5 * np.sum(V * G) - E)
+    line = {
+        "metric": f"adjoint seconds: dE/dpsi, gamma and the 2-RDM (centre walk) at L={L}",
+        "value": t2 - t0, "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 0,
+        "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"u1_L{L}_N{N}_Sz0_D{D} random MPS, centre (L-2, L-1)",
+                   "dpsi_gamma_s": t1 - t0, "rdm2_walk_s": t2 - t1,
+                   "rdm2_elements_measured": (L ** 4 + 3 * L ** 2) // 4,
+                   "energy": E, "energy_identity_residual": ident,
+                   "trace_gamma2_minus_N(N-1)": float(np.einsum("pprr->", G) - N * (N - 1)),
+                   "device_bytes_peak": st["device_bytes"],
+                   "pair_switch": args.pair_switch, "hbm_budget_gb": args.hbm_budget},
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", 0))
@@ -590,6 +634,9 @@ def main():
     elif args.sweep:
         if rank == 0:
             run_sweep(args, rank, world, local)
+    elif args.adjoint:
+        if rank == 0:
+            run_adjoint(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
 
