@@ -557,11 +557,11 @@ HeffPlan plan_terms(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay
       s2.probs.push_back(p);
     }
     plan.flops += s1.flops + s2.flops;
-    plan.stage1.push_back(s1);
-    plan.stage2.push_back(s2);
+    plan.stage1.push_back(std::move(s1));
+    plan.stage2.push_back(std::move(s2));
     plan.tmp_elems = std::max(plan.tmp_elems, tused);
-    s1.clear();
-    s2.clear();
+    s1 = Launch();
+    s2 = Launch();
     out.clear();
     tused = 0;
   };

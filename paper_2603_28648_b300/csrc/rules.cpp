@@ -152,8 +152,8 @@ struct Ctx {
     std::vector<Contrib> cs;
   };
   std::vector<Pending> pending;
-  Ctx(const EnvBlock& b, const Integrals& i, Enlarged& e) : B(b), I(i), E(e), pb(e.pb) {
-    pending.reserve(16 + 8 * (size_t)i.L * i.L);  // complementary operators of one block
+  Ctx(const EnvBlock& b, const Integrals& i, Enlarged& e, bool for_enlarge = true) : B(b), I(i), E(e), pb(e.pb) {
+    if (for_enlarge) pending.reserve(16 + 8 * (size_t)i.L * i.L);  // complementary operators of one block
   }
 
   const OpView* get(Key k) const {
@@ -555,7 +555,7 @@ Contrib C_(const OpView* src, bool T, const Mat4& o, double coef, bool par) {
 }  // namespace
 
 OpView product_view(const EnvBlock& B, const Integrals& I, Enlarged& E, const std::vector<Contrib>& cs, bool odd) {
-  Ctx x(B, I, E);
+  Ctx x(B, I, E, false);
   OpView v;
   v.odd = odd;
   for (const Contrib& c : cs) x.expand(x.src_blocks(c.src, c.srcT), c.o, c.coef, c.par, v.blocks);
