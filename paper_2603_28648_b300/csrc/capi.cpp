@@ -76,6 +76,20 @@ int guard(qcdmrg_ctx* c, F&& f) {
   }
 }
 
+// Gamma averaged over the 8 index permutations that leave (pq|rs) invariant
+std::vector<double> permutation_average(const std::vector<double>& G, int L) {
+  auto at = [L](int p, int q, int r, int s) { return (((size_t)p * L + q) * L + r) * L + s; };
+  std::vector<double> A(G.size());
+  for (int p = 0; p < L; ++p)
+    for (int q = 0; q < L; ++q)
+      for (int r = 0; r < L; ++r)
+        for (int s = 0; s < L; ++s)
+          A[at(p, q, r, s)] = (G[at(p, q, r, s)] + G[at(q, p, r, s)] + G[at(p, q, s, r)] + G[at(q, p, s, r)] +
+                               G[at(r, s, p, q)] + G[at(s, r, p, q)] + G[at(r, s, q, p)] + G[at(s, r, q, p)]) /
+                              8.0;
+  return A;
+}
+
 }  // namespace
 
 extern "C" {
@@ -552,20 +566,6 @@ int qcdmrg_psi_layout(const qcdmrg_ctx* cctx, int* blocks, int cap, int* nblocks
     }
     return QCDMRG_OK;
   });
-}
-
-// Gamma averaged over the 8 index permutations that leave (pq|rs) invariant
-static std::vector<double> permutation_average(const std::vector<double>& G, int L) {
-  auto at = [L](int p, int q, int r, int s) { return (((size_t)p * L + q) * L + r) * L + s; };
-  std::vector<double> A(G.size());
-  for (int p = 0; p < L; ++p)
-    for (int q = 0; q < L; ++q)
-      for (int r = 0; r < L; ++r)
-        for (int s = 0; s < L; ++s)
-          A[at(p, q, r, s)] = (G[at(p, q, r, s)] + G[at(q, p, r, s)] + G[at(p, q, s, r)] + G[at(q, p, s, r)] +
-                               G[at(r, s, p, q)] + G[at(s, r, p, q)] + G[at(r, s, q, p)] + G[at(s, r, q, p)]) /
-                              8.0;
-  return A;
 }
 
 int qcdmrg_energy_grad(qcdmrg_ctx* ctx, double* energy, double* dpsi, double* gamma1, double* gamma2) {
