@@ -57,7 +57,40 @@ struct RecEx : Executor {
     --it;
     return addr >= it->first && addr + (uint64_t)bytes <= it->first + (uint64_t)it->second;
   }
-  void run(const Launch&, uint64_t, uint64_t) override {}
+  // every launch the host planner hands over (renormalization, enlargement
+  // sums, the GEMM-form sums): each problem's C and each segment's A and B
+  // must lie inside one allocation (psi and sigma buffers, scratch or stored)
+  int64_t launches_checked = 0;
+  void run(const Launch& l, uint64_t psi, uint64_t sig) override {
+    ++launches_checked;
+    const uint64_t base[4] = {0, psi, sig, tmp_base};
+    auto addr = [&](uint64_t v, int buf) { return buf == 0 ? v : base[buf] + v * 8; };
+    for (size_t pi = 0; pi < l.probs.size(); ++pi) {
+      const Prob& p = l.probs[pi];
+      if (p.m <= 0 || p.n <= 0 || p.ldc < p.n || p.seg0 < 0 || p.nseg < 0 ||
+          (size_t)p.seg0 + p.nseg > l.segs.size()) {
+        fail("launch problem " + std::to_string(pi) + " malformed");
+        continue;
+      }
+      if (!inside(addr(p.c, p.cbuf), 8 * ((int64_t)(p.m - 1) * p.ldc + p.n))) fail("launch C out of bounds");
+      for (int si = p.seg0; si < p.seg0 + p.nseg; ++si) {
+        const Seg& g = l.segs[si];
+        const bool aid = g.a == 0 && g.abuf == 0, bid = g.b == 0 && g.bbuf == 0;
+        if (aid) {
+          if (!bid) {
+            const int64_t last = g.tb ? (int64_t)(p.n - 1) * g.ldb + p.m - 1 : (int64_t)(p.m - 1) * g.ldb + p.n - 1;
+            if (!inside(addr(g.b, g.bbuf), 8 * (last + 1))) fail("launch gathered B out of bounds");
+          }
+          continue;
+        }
+        if (bid || g.k <= 0) { fail("launch segment malformed"); continue; }
+        const int64_t la = g.ta ? (int64_t)(g.k - 1) * g.lda + p.m - 1 : (int64_t)(p.m - 1) * g.lda + g.k - 1;
+        const int64_t lb = g.tb ? (int64_t)(p.n - 1) * g.ldb + g.k - 1 : (int64_t)(g.k - 1) * g.ldb + p.n - 1;
+        if (!inside(addr(g.a, g.abuf), 8 * (la + 1))) fail("launch A out of bounds");
+        if (!inside(addr(g.b, g.bbuf), 8 * (lb + 1))) fail("launch B out of bounds");
+      }
+    }
+  }
   void upload(uint64_t, const double*, int64_t) override {}
   void download(double* h, uint64_t, int64_t n) override { std::fill(h, h + n, 0.0); }
   void zero(uint64_t, int64_t) override {}
@@ -280,7 +313,7 @@ int main(int argc, char** argv) {
       cfg.width = width;
       check_tiled(E.plan, E.lay, ex, cfg);
     }
-  std::printf("L=%d N=%d D=%d psi=%lld terms=%d gflop=%.4f fails=%d\n", L, N, D, (long long)E.lay.size,
-              E.plan.nterms, E.plan.flops / 1e9, fails);
+  std::printf("L=%d N=%d D=%d psi=%lld terms=%d gflop=%.4f launches=%lld fails=%d\n", L, N, D, (long long)E.lay.size,
+              E.plan.nterms, E.plan.flops / 1e9, (long long)ex.launches_checked, fails);
   return fails ? 1 : 0;
 }

@@ -1,8 +1,9 @@
-"""Host logic without a GPU: the task lists the library plans for H_eff psi
-(FP64 segments and the tiled tensor-core work items) stay inside the buffers
-they address, no work item is empty, and both plans count the same
-algorithmic flops. The library's host sources are compiled with g++ together
-with tests/planner_check.cpp, which records allocations instead of computing."""
+"""Host logic without a GPU: the task lists the library plans — every launch of the
+environment build (renormalization, enlargement sums, their GEMM form), the H_eff psi
+FP64 segments and the tiled tensor-core work items — stay inside the buffers they
+address, no work item is empty, and both H_eff plans count the same algorithmic flops.
+The library's host sources are compiled with g++ together with tests/planner_check.cpp,
+which records allocations instead of computing."""
 import os
 import shutil
 import subprocess
