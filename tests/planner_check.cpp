@@ -239,7 +239,7 @@ void check_tiled(const HeffPlan& P, const PsiLayout& lay, const RecEx& ex, const
 
 int main(int argc, char** argv) {
   if (argc < 4) {
-    std::fprintf(stderr, "usage: planner_check L N D [pair_switch]\n");
+    std::fprintf(stderr, "usage: planner_check L N D [pair_switch [sum_gemm]]\n");
     return 2;
   }
   const int L = std::atoi(argv[1]), N = std::atoi(argv[2]), D = std::atoi(argv[3]);
@@ -254,6 +254,7 @@ int main(int argc, char** argv) {
   E.L = L;
   E.tmp_budget = (int64_t)(2e9 / 8);
   if (argc > 4) E.pair_switch = std::atoi(argv[4]);
+  if (argc > 5) E.sum_gemm = std::atoi(argv[5]);
   E.I.L = L;
   E.I.h.assign((size_t)L * L, 0.0);
   E.I.V.assign((size_t)L * L * L * L, 0.0);

@@ -30,14 +30,17 @@ def checker(tmp_path_factory):
     return out
 
 
-@pytest.mark.parametrize("L,N,D,switch", [(6, 6, 16, 0), (7, 5, 16, 0), (12, 12, 32, 0), (36, 54, 64, 0),
-                                           (12, 12, 32, 4), (12, 12, 32, 6), (36, 54, 64, 18),
-                                           (36, 54, 4096, 18)])
-def test_plans_stay_in_bounds(checker, L, N, D, switch):
+@pytest.mark.parametrize("L,N,D,switch,sum_gemm", [(6, 6, 16, 0, 0), (7, 5, 16, 0, 0), (12, 12, 32, 0, 0),
+                                                    (36, 54, 64, 0, 0), (12, 12, 32, 4, 0), (12, 12, 32, 6, 0),
+                                                    (36, 54, 64, 18, 0), (36, 54, 4096, 18, 0),
+                                                    (36, 54, 1024, 0, 1)])
+def test_plans_stay_in_bounds(checker, L, N, D, switch, sum_gemm):
     """switch: cut of the normal/complementary switch (0: normal pairs on the left everywhere;
     at the centre cut L/2 the right blocks switch; at L/2 - 2 the centre uses the mirrored
     decomposition with normal pairs on the right). The D=4096 case is the full CAS(54,36)-shaped
-    size of the switched run (task lists only: about 15 s)."""
-    r = subprocess.run([checker, str(L), str(N), str(D), str(switch)], capture_output=True, text=True, timeout=600)
+    size of the switched run (task lists only: about 15 s); sum_gemm 1 takes the GEMM form of the
+    operator sums without the switch."""
+    r = subprocess.run([checker, str(L), str(N), str(D), str(switch), str(sum_gemm)], capture_output=True,
+                       text=True, timeout=600)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "fails=0" in r.stdout
