@@ -128,6 +128,10 @@ typedef struct {
   int tile_width;        /* and accumulator columns per stage-1 item */
   int tunes;             /* autotuner runs of this context */
   double tune_seconds;   /* wall time spent in them */
+  int64_t f64_tiles[4];  /* FP64 form of H_eff psi: work items (tiles) per tile shape 64x64, 64x32,
+                            32x64, 32x32 over the prepared task lists of the current centre */
+  int64_t f64_split_tiles; /* of those, tiles of problems whose summed K exceeds one work item
+                            (split over several tiles that add with FP64 atomics) */
 } qcdmrg_stats_t;
 
 /* Davidson options (zero fields take the defaults in brackets). */
@@ -297,7 +301,11 @@ int qcdmrg_apply_heff_dev(qcdmrg_ctx* ctx, int precision, const void* psi, void*
  * first call before any stream capture. All calls share the array and it
  * keeps the last call's contents: calls whose work overlaps on the GPU race.
  * psi, sigma: device arrays of psi_size doubles; stream: cudaStream_t (NULL is
- * the legacy default stream). Errors: ESTATE, EINVAL, ECUDA.
+ * the legacy default stream). The call makes the context's device current
+ * while it enqueues and restores the caller's current device before it
+ * returns; a launch error left pending by earlier work on the calling thread
+ * is cleared first, so that ECUDA always reports this call's own launches.
+ * Errors: ESTATE, EINVAL, ECUDA.
  */
 #define QCDMRG_NOALLOC_SCRATCH_DOUBLES (4 * 1024 * 1024)
 int qcdmrg_apply_heff_noalloc(qcdmrg_ctx* ctx, const void* psi, void* sigma, void* stream);

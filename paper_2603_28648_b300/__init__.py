@@ -67,7 +67,8 @@ class Stats(ctypes.Structure):
                 ("evictions", ctypes.c_int), ("restores", ctypes.c_int),
                 ("copy_wait_seconds", ctypes.c_double), ("heff_bytes", ctypes.c_double),
                 ("tile_kmax", ctypes.c_int), ("tile_width", ctypes.c_int), ("tunes", ctypes.c_int),
-                ("tune_seconds", ctypes.c_double)]
+                ("tune_seconds", ctypes.c_double), ("f64_tiles", ctypes.c_int64 * 4),
+                ("f64_split_tiles", ctypes.c_int64)]
 
 
 EXPORTS = [
@@ -338,7 +339,8 @@ class Context:
     def stats(self):
         s = Stats()
         self._check(self.lib.qcdmrg_stats(self.h, ctypes.byref(s)))
-        return {f: getattr(s, f) for f, _ in Stats._fields_}
+        out = {f: getattr(s, f) for f, _ in Stats._fields_}
+        return {f: (list(v) if isinstance(v, ctypes.Array) else v) for f, v in out.items()}
 
 
 class HeffGraph:

@@ -860,6 +860,16 @@ int qcdmrg_stats(const qcdmrg_ctx* ctx, qcdmrg_stats_t* out) {
   out->evictions = ctx->eng.evictions;
   out->restores = ctx->eng.restores;
   out->copy_wait_seconds = ctx->be.ex ? ctx->be.ex->copies_wait_seconds() : 0.0;
+  for (int c = 0; c < 4; ++c) out->f64_tiles[c] = 0;
+  out->f64_split_tiles = 0;
+  if (ctx->be.pr && ctx->eng.have_env)
+    for (auto& h : ctx->eng.prepared)
+      for (int hh : {h.first, h.second}) {
+        int64_t c[5];
+        ctx->be.pr->tile_counts(hh, c);
+        for (int k = 0; k < 4; ++k) out->f64_tiles[k] += c[k];
+        out->f64_split_tiles += c[4];
+      }
   return QCDMRG_OK;
 }
 

@@ -223,6 +223,7 @@ struct DevLaunch {
   int cls[F64_CLASSES + 1] = {};  // class c: tiles [cls[c], cls[c+1])
   GTile* t2 = nullptr;   // 128x128 tiles (tcgen05 kernel)
   int ntiles2 = 0;
+  int nsplit = 0;        // FP64 tiles of split problems
   double flops = 0;
 };
 
@@ -561,6 +562,7 @@ class CudaExec : public Executor, public PreparedRunner {
     make_tiles_f64(l, KMAX_F64, T, d.cls);
     make_tiles(l, TC_TILE, KMAX_TC, T2, 0);
     d.ntiles2 = (int)T2.size();
+    for (const GTile& g : T) d.nsplit += g.split ? 1 : 0;
     d.flops = l.flops;
     auto up = [](void** dst, const void* src, size_t bytes) {
       CK(cudaMalloc(dst, std::max<size_t>(bytes, 16)));
@@ -676,7 +678,10 @@ class CudaExec : public Executor, public PreparedRunner {
     }
     Bases B;
     B.b[0] = 0; B.b[1] = psi; B.b[2] = sig; B.b[3] = tmp_;
-    int mode = precision == 1 ? TC_TF32 : precision == 2 ? TC_BF16 : TC_BF16X3;
+    // the BF16 forms run on the tiled kernel (run_tiled); prepared task lists
+    // reach the tensor cores in the TF32 form only
+    if (precision != 1) throw std::runtime_error("run_prepared: BF16 forms use the tiled kernel");
+    int mode = TC_TF32;
     CK(launch_tc(mode, d.p, d.s, d.t2, d.ntiles2, B, err_, (cudaStream_t)stream));
   }
   int take_error() override {
@@ -687,6 +692,11 @@ class CudaExec : public Executor, public PreparedRunner {
     return h;
   }
   const void* prepared_handle(int h) const override { return &prepared_.at(h); }
+  void tile_counts(int h, int64_t counts[5]) const override {
+    const DevLaunch& d = prepared_.at(h);
+    for (int c = 0; c < F64_CLASSES; ++c) counts[c] = d.cls[c + 1] - d.cls[c];
+    counts[4] = d.nsplit;
+  }
   void* stream() override { return st_; }
   void sync(void* stream) override { CK(cudaStreamSynchronize((cudaStream_t)stream)); }
   void zero_async(uint64_t p, int64_t n, void* stream) override {

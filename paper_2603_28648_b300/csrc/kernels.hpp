@@ -18,11 +18,14 @@ struct PreparedRunner {
   virtual int take_error() = 0;
   // opaque device task list of a prepared launch (for the no-allocation path)
   virtual const void* prepared_handle(int handle) const = 0;
+  // FP64 work items of a prepared launch: tiles per shape class (64x64, 64x32,
+  // 32x64, 32x32) in counts[0..3], split-K tiles (FP64 atomics) in counts[4]
+  virtual void tile_counts(int handle, int64_t counts[5]) const = 0;
   virtual void* stream() = 0;
   virtual void sync(void* stream) = 0;
   virtual void zero_async(uint64_t p, int64_t n, void* stream) = 0;
   virtual int64_t bytes_allocated() const = 0;
-  // TMA-fed tensor-core path (BF16, BF16x3): bf16 operand mirrors with one or
+  // bulk-copy-fed tensor-core path (BF16, BF16x3): bf16 operand mirrors with one or
   // three planes and the work items of both stages (dropped with the prepared
   // launches); tiled_planes() is 0 when nothing is prepared
   virtual void prepare_tiled(const TiledPlan& plan, int planes) = 0;

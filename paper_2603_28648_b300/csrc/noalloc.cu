@@ -55,10 +55,29 @@ uint64_t noalloc_scratch_address() {
 
 namespace qd {
 
+namespace {
+// makes `device` current for the call and gives the caller's current device
+// back on every exit path
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int device) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) throw std::runtime_error(std::string("CUDA: ") + cudaGetErrorString(e));
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+}  // namespace
+
 void heff_noalloc(Engine& E, int device, uint64_t psi, uint64_t sig, void* stream) {
-  cudaError_t e = cudaSetDevice(device);
-  if (e != cudaSuccess) throw std::runtime_error(std::string("CUDA: ") + cudaGetErrorString(e));
+  DeviceGuard guard(device);
+  // a launch error left pending by earlier, unrelated work on this thread is
+  // cleared here, so that the status of this call reports its own launches
+  (void)cudaGetLastError();
   const uint64_t scratch = noalloc_scratch_address();
+  cudaError_t e;
   cudaStream_t st = (cudaStream_t)stream;
   e = cudaMemsetAsync(reinterpret_cast<void*>(sig), 0, (size_t)E.lay.size * 8, st);
   if (e != cudaSuccess) throw std::runtime_error(std::string("CUDA: ") + cudaGetErrorString(e));

@@ -1,22 +1,18 @@
-// tcgen05 segmented grouped GEMM (BF16, BF16x3 split, TF32) for sm_103a.
+// tcgen05 segmented grouped GEMM of the TF32 form for sm_103a.
 //
 // Same task lists as the FP64 kernel: one CTA owns a 128x128 output tile of a
 // problem and accumulates sum_s sc_s op(A_s) op(B_s) over all its segments in
 // one FP32 accumulator in tensor memory. Operand tiles are loaded from HBM by
 // all 128 threads (coalesced along the contiguous dimension of each operand),
-// scaled by the segment scalar, rounded to the MMA input type and stored in
-// shared memory in the K-major no-swizzle core-matrix layout; one thread then
-// issues tcgen05.mma for the chunk and tcgen05.commit signals an mbarrier when
-// the tensor core has consumed the stage (two stages in flight).
-//   BF16   : one bf16 MMA per K step.
-//   BF16x3 : x = x0 + x1 + x2 (bf16 each, x1 = bf16(x - x0), ...); six MMAs
-//            a_i b_j with i + j <= 2 per K step, FP32 accumulation
-//            (Henry, Tang, Heinecke, ARITH 2019).
-//   TF32   : FP32 operands, kind::tf32 MMA.
+// scaled by the segment scalar, rounded to TF32 (round to nearest) and stored
+// in shared memory in the K-major no-swizzle core-matrix layout; one thread
+// then issues tcgen05.mma (kind::tf32) for the chunk and tcgen05.commit
+// signals an mbarrier when the tensor core has consumed the stage (two stages
+// in flight). The BF16 and three-term BF16 forms run on the tiled kernel of
+// tc_tiled.cu, whose operands are converted once per prepared centre.
 // Every mbarrier wait is bounded (about one second of clock64 cycles); on a
 // timeout the kernel records an error code, waits once more (bounded) for its
 // own MMAs, frees its tensor memory and returns.
-#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -88,16 +84,6 @@ __host__ __device__ constexpr uint32_t idesc(uint32_t ab_format) {
 template <int MODE>
 struct Cfg;
 template <>
-struct Cfg<TC_BF16> {
-  static constexpr int ES = 2, KC = 64, KS = 16, NSPLIT = 1;
-  static constexpr uint32_t FMT = 1;
-};
-template <>
-struct Cfg<TC_BF16X3> {
-  static constexpr int ES = 2, KC = 64, KS = 16, NSPLIT = 3;
-  static constexpr uint32_t FMT = 1;
-};
-template <>
 struct Cfg<TC_TF32> {
   static constexpr int ES = 4, KC = 32, KS = 8, NSPLIT = 1;
   static constexpr uint32_t FMT = 2;
@@ -146,25 +132,13 @@ __device__ __forceinline__ double f32_to_f64(float f) {
 }
 
 template <int MODE>
-__device__ __forceinline__ void put(unsigned char* base, uint32_t off, size_t split_stride, float x) {
-  if constexpr (MODE == TC_TF32) {
-    // round to nearest TF32 (the tensor core would otherwise drop the low
-    // mantissa bits, a biased truncation)
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    *reinterpret_cast<uint32_t*>(base + off) = r;
-  } else if constexpr (MODE == TC_BF16) {
-    *reinterpret_cast<__nv_bfloat16*>(base + off) = __float2bfloat16_rn(x);
-  } else {
-    __nv_bfloat16 h0 = __float2bfloat16_rn(x);
-    float r1 = x - __bfloat162float(h0);
-    __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
-    float r2 = r1 - __bfloat162float(h1);
-    __nv_bfloat16 h2 = __float2bfloat16_rn(r2);
-    *reinterpret_cast<__nv_bfloat16*>(base + off) = h0;
-    *reinterpret_cast<__nv_bfloat16*>(base + split_stride + off) = h1;
-    *reinterpret_cast<__nv_bfloat16*>(base + 2 * split_stride + off) = h2;
-  }
+__device__ __forceinline__ void put(unsigned char* base, uint32_t off, size_t, float x) {
+  static_assert(MODE == TC_TF32, "TF32 only");
+  // round to nearest TF32 (the tensor core would otherwise drop the low
+  // mantissa bits, a biased truncation)
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  *reinterpret_cast<uint32_t*>(base + off) = r;
 }
 
 template <int MODE>
@@ -272,35 +246,12 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
         for (int kk = 0; kk < KC / KS; ++kk) {
           const uint32_t koff = kk * 2 * 128;  // two core matrices per K step
-          if constexpr (NS == 1) {
-            uint64_t da = sdesc(a0 + koff, LBO, SBO), db = sdesc(b0 + koff, LBO, SBO);
-            uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
-            if constexpr (MODE == TC_TF32) {
-              asm volatile(
-                  "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-                  " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                  "l"(da), "l"(db), "r"(idesc(C::FMT)), "r"(acc));
-            } else {
-              asm volatile(
-                  "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                  "l"(da), "l"(db), "r"(idesc(C::FMT)), "r"(acc));
-            }
-          } else {
-            // (i, j) pairs with i + j <= 2, smallest terms first
-            const int pi[6] = {2, 1, 0, 1, 0, 0};
-            const int pj[6] = {0, 1, 2, 0, 1, 0};
-#pragma unroll
-            for (int q = 0; q < 6; ++q) {
-              uint64_t da = sdesc(a0 + pi[q] * TILE + koff, LBO, SBO);
-              uint64_t db = sdesc(b0 + pj[q] * TILE + koff, LBO, SBO);
-              uint32_t acc = (kt > 0 || kk > 0 || q > 0) ? 1u : 0u;
-              asm volatile(
-                  "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                  "l"(da), "l"(db), "r"(idesc(C::FMT)), "r"(acc));
-            }
-          }
+          uint64_t da = sdesc(a0 + koff, LBO, SBO), db = sdesc(b0 + koff, LBO, SBO);
+          uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+              "l"(da), "l"(db), "r"(idesc(C::FMT)), "r"(acc));
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                          smem_u32(&mbar[st]))
@@ -405,8 +356,6 @@ cudaError_t launch_tc(int mode, const TcProb* P, const TcSeg* S, const TcTile* T
                       cudaStream_t st) {
   if (nt <= 0) return cudaSuccess;
   switch (mode) {
-    case TC_BF16: return launch_mode<TC_BF16>(P, S, T, nt, B, err, st);
-    case TC_BF16X3: return launch_mode<TC_BF16X3>(P, S, T, nt, B, err, st);
     case TC_TF32: return launch_mode<TC_TF32>(P, S, T, nt, B, err, st);
     default: return cudaErrorInvalidValue;
   }

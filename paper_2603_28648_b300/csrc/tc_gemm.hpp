@@ -28,10 +28,10 @@ using TcProb = GProb;
 using TcTile = GTile;
 using TcBases = Bases;
 
-enum TcMode : int { TC_BF16 = 1, TC_BF16X3 = 2, TC_TF32 = 3 };
+enum TcMode : int { TC_TF32 = 3 };
 constexpr int TC_TILE = 128;
 
-// Launch the tcgen05 kernel of the given mode over 128x128 tiles. err (device
+// Launch the tcgen05 kernel of the given mode (TF32) over 128x128 tiles. err (device
 // int) is set to 1 if a bounded wait gave up.
 cudaError_t launch_tc(int mode, const TcProb* P, const TcSeg* S, const TcTile* T, int nt, TcBases B,
                       int* err, cudaStream_t st);

@@ -1,4 +1,4 @@
-// Launchers of the TMA-fed tensor-core H_eff psi kernels (tc_tiled.cu).
+// Launchers of the bulk-copy-fed tensor-core H_eff psi kernels (tc_tiled.cu).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>

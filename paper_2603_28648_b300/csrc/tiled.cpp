@@ -1,4 +1,4 @@
-// Work items of the TMA-fed tensor-core H_eff psi (see tiled.hpp), derived
+// Work items of the bulk-copy-fed tensor-core H_eff psi (see tiled.hpp), derived
 // from the FP64 task lists of the same product.
 #include "tiled.hpp"
 

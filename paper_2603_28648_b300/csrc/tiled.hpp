@@ -1,4 +1,4 @@
-// Tiled BF16 operands and work items of the TMA-fed tensor-core H_eff psi.
+// Tiled BF16 operands and work items of the bulk-copy-fed tensor-core H_eff psi.
 //
 // H_eff psi runs in two stages, both summed over the operator-product terms t:
 //   stage 1: T_t = s_t psi_blk O_R^T   (one per term, right block reference, psi block)

@@ -9,8 +9,8 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA device and the built library")
     config.addinivalue_line("markers", "slow: longer CPU test")
-    config.addinivalue_line("markers", "run_last: GPU tests of a path not yet run on a device; collected "
-                                       "after the others so that a failure under -x does not hide them")
+    config.addinivalue_line("markers", "run_last: GPU tests of a newly added path; collected after the "
+                                       "others so that a failure under -x does not hide them")
 
 
 def pytest_collection_modifyitems(session, config, items):

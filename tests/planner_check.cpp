@@ -118,6 +118,7 @@ struct NullRunner : PreparedRunner {
   void run_prepared(int, uint64_t, uint64_t, void*, int) override {}
   int take_error() override { return 0; }
   const void* prepared_handle(int) const override { return nullptr; }
+  void tile_counts(int, int64_t c[5]) const override { for (int i = 0; i < 5; ++i) c[i] = 0; }
   void* stream() override { return nullptr; }
   void sync(void*) override {}
   void zero_async(uint64_t, int64_t, void*) override {}

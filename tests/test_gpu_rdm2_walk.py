@@ -1,14 +1,14 @@
 """GPU tests of the 2-RDM by a walk of the centre (qcdmrg_rdm2_sweep), through the C ABI:
 element by element against the 2-RDM of the expanded MPS vector, its permutation average
 against qcdmrg_rdm2, the MPS restored after the walk, and at L=16 the identities every 2-RDM
-of the state satisfies. Not yet run on a device: collected last."""
+of the state satisfies."""
 import numpy as np
 import pytest
 
 import qcinputs as q
 from tests._lib import ensure_built
 
-pytestmark = [pytest.mark.gpu, pytest.mark.run_last]
+pytestmark = pytest.mark.gpu
 
 
 def test_rdm2_by_centre_walk_matches_brute_force():

@@ -12,7 +12,7 @@ import pytest
 import qcinputs as q
 from tests._lib import ensure_built
 
-pytestmark = [pytest.mark.gpu, pytest.mark.run_last]
+pytestmark = pytest.mark.gpu
 
 TOL_FP64 = 1e-10
 BOUND = {"tf32": 8 * 2.0 ** -11, "bf16": 8 * 2.0 ** -9, "bf16x3": 2.0 ** -14}
