@@ -44,7 +44,11 @@ extern "C" {
 #define QCDMRG_EIO (-7)      /* file error */
 
 /* symmetry */
-#define QCDMRG_U1 0 /* U(1)xU(1): sector labels (N, 2Sz) */
+#define QCDMRG_U1 0  /* U(1)xU(1): sector labels (N, 2Sz), bond dimensions count states */
+#define QCDMRG_SU2 1 /* SU(2) spin adaptation (the paper's spin-adapted DMRG, Method section;
+                        bond dimensions D_SU(2) count multiplets, Numerical procedure section):
+                        sector labels (N, 2S), operators stored as reduced matrix elements
+                        between multiplets, the target's two_s is 2S; needs pair_switch = 0 */
 
 /* precision of the block contractions (all accumulate sigma in FP64 across
  * problems; inside one output tile the tensor-core forms accumulate in FP32) */

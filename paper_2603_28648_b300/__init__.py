@@ -15,7 +15,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libqcdmrg.so")
 
 QCDMRG_OK = 0
-U1 = 0
+U1, SU2 = 0, 1
 FP64, TF32, BF16, BF16X3 = 0, 1, 2, 3
 PRECISIONS = {"fp64": FP64, "tf32": TF32, "bf16": BF16, "bf16x3": BF16X3}
 

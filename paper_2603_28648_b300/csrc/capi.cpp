@@ -97,7 +97,9 @@ extern "C" {
 int qcdmrg_create(qcdmrg_ctx** out, const qcdmrg_config* cfg) {
   if (!out || !cfg) return QCDMRG_EINVAL;
   *out = nullptr;
-  if (cfg->symmetry != QCDMRG_U1) return QCDMRG_EINVAL;
+  if (cfg->symmetry != QCDMRG_U1 && cfg->symmetry != QCDMRG_SU2) return QCDMRG_EINVAL;
+  // the spin-adapted rules keep normal pairs on the left at every cut
+  if (cfg->symmetry == QCDMRG_SU2 && cfg->pair_switch != 0) return QCDMRG_EINVAL;
   // the configuration is checked before any CUDA call
   if (!(cfg->hbm_budget_gb >= 0) || !(cfg->tmp_budget_gb >= 0) || cfg->pair_switch < 0 || cfg->sum_gemm < -1 ||
       cfg->sum_gemm > 1)
@@ -113,6 +115,7 @@ int qcdmrg_create(qcdmrg_ctx** out, const qcdmrg_config* cfg) {
     c->eng.hbm_budget = (int64_t)(cfg->hbm_budget_gb * 1e9);
     c->eng.autotune = cfg->autotune_off == 0;
     c->eng.pair_switch = cfg->pair_switch;
+    c->eng.su2 = cfg->symmetry == QCDMRG_SU2;
     c->eng.sum_gemm = cfg->sum_gemm;
   } catch (const std::invalid_argument&) {
     delete c;
@@ -159,6 +162,7 @@ int qcdmrg_load_integrals(qcdmrg_ctx* ctx, int L, const double* h, const double*
 int qcdmrg_set_target(qcdmrg_ctx* ctx, int N, int two_s) {
   return guard(ctx, [&]() {
     if (N < 0 || ((N + two_s) & 1)) throw Fail{QCDMRG_EINVAL, "N and 2Sz must have equal parity"};
+    if (ctx->eng.su2 && two_s < 0) throw Fail{QCDMRG_EINVAL, "2S must not be negative"};
     if (ctx->have_int && (N > 2 * ctx->eng.I.L || std::abs(two_s) > N))
       throw Fail{QCDMRG_EINVAL, "target outside the Fock space"};
     ctx->eng.clear();
@@ -179,6 +183,7 @@ int qcdmrg_import_mps(qcdmrg_ctx* ctx, const qcdmrg_mps_desc* d, const double* d
     if (d->center < 0 || d->center + 1 >= L) throw Fail{QCDMRG_EINVAL, "centre out of range"};
     E.clear();
     std::vector<Basis> bonds(L + 1);
+    for (auto& b : bonds) b.su2 = E.su2;
     int pos = 0;
     for (int b = 0; b <= L; ++b) {
       int ns = d->bond_nsec[b];
@@ -390,10 +395,11 @@ int qcdmrg_init_mps(qcdmrg_ctx* ctx, int D, uint64_t seed, int center) {
     if (D < 1) throw Fail{QCDMRG_EINVAL, "D must be positive"};
     if (center < 0 || center + 1 >= L) throw Fail{QCDMRG_EINVAL, "centre out of range"};
     E.clear();
-    auto st = mps_structure(L, E.N, E.two_s, D);
+    auto st = mps_structure(L, E.N, E.two_s, D, E.su2);
     for (int b = 1; b < L; ++b)
       if (st[b].empty()) throw Fail{QCDMRG_EINVAL, "target not reachable: empty bond"};
     std::vector<Basis> bonds(L + 1);
+    for (auto& b : bonds) b.su2 = E.su2;
     for (int b = 0; b <= center; ++b)
       for (auto& kv : st[b]) bonds[b].add(kv.first, kv.second);
     for (int b = center + 2; b <= L; ++b)

@@ -1,5 +1,6 @@
 // Layout, operator views, renormalization and H_eff task lists.
 #include "core.hpp"
+#include "su2.hpp"
 
 #include <algorithm>
 #include <atomic>
@@ -38,10 +39,12 @@ ProdBasis make_prod(const Basis& blk, bool left) {
   ProdBasis pb;
   pb.left = left;
   pb.blk = &blk;
+  pb.prod.su2 = blk.su2;
   std::vector<std::tuple<QN, int, int, int>> items;  // label, first, second, (blk, st)
   for (int b = 0; b < blk.nsec(); ++b)
     for (int st = 0; st < NSITE; ++st) {
       QN q = blk.q[b] + SITE_QN[st];
+      if (blk.su2 && q.s < 0) continue;   // a doublet couples a singlet to spin 1/2 only
       if (left) items.emplace_back(q, b, st, 0);
       else items.emplace_back(q, st, b, 0);
     }
@@ -274,6 +277,7 @@ void renormalize(const Enlarged& E, const Basis& nb, const std::vector<int>& nb_
     const OpView& op = *o.op;
     const auto& lay = layout.at(*o.key);
     o.nv.odd = op.odd;
+    o.nv.k2 = op.k2;
     int64_t tused = o.tbase;
     // (output block, segment) pairs, grouped by output block below in the
     // order they were produced
@@ -393,6 +397,8 @@ PsiLayout make_psi_layout(const ProdBasis& Lp, const ProdBasis& Rp, QN target) {
   PsiLayout lay;
   const Basis& X = *Lp.blk;
   const Basis& Y = *Rp.blk;
+  lay.su2 = X.su2;
+  lay.target = target;
   lay.nl = Lp.nsub();
   lay.nr = Rp.nsub();
   lay.by_sub.assign((size_t)lay.nl * lay.nr, -1);
@@ -400,8 +406,16 @@ PsiLayout make_psi_layout(const ProdBasis& Lp, const ProdBasis& Rp, QN target) {
     for (int i = 0; i < NSITE; ++i)
       for (int j = 0; j < NSITE; ++j)
         for (int y = 0; y < Y.nsec(); ++y) {
-          QN t = X.q[x] + SITE_QN[i] + SITE_QN[j] + Y.q[y];
-          if (t != target) continue;
+          if (lay.su2) {
+            // SU(2): the multiplets (x i) J_a and (j y) J_b couple to the target spin
+            const int ls = Lp.find(x, i), rs = Rp.find(y, j);
+            if (ls < 0 || rs < 0) continue;
+            const QN a = Lp.sub_qn(ls), b = Rp.sub_qn(rs);
+            if (a.n + b.n != target.n || std::abs(a.s - b.s) > target.s || a.s + b.s < target.s) continue;
+          } else {
+            QN t = X.q[x] + SITE_QN[i] + SITE_QN[j] + Y.q[y];
+            if (t != target) continue;
+          }
           PsiLayout::Blk b;
           b.x = x; b.i = i; b.j = j; b.y = y;
           b.lsub = Lp.find(x, i);
@@ -491,8 +505,19 @@ std::vector<CenterTerm> center_terms(const Enlarged& Lp, const Enlarged& Rp, con
 
 HeffPlan plan_heff(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay,
                    const Integrals& I, int64_t tmp_budget) {
-  return plan_terms(Lp, Rp, lay, center_terms(Lp, Rp, I), tmp_budget);
+  return plan_terms(Lp, Rp, lay, lay.su2 ? center_terms_su2(Lp, Rp, I) : center_terms(Lp, Rp, I), tmp_budget);
 }
+
+namespace {
+// SU(2): reduced-element factor of the scalar coupling [O_L^k x O_R^k]^0 between
+// the two-site multiplets (a b) S and (a' b') S (1 in U(1))
+double pair_factor(const PsiLayout& lay, const ProdBasis& LB, const ProdBasis& RB, int k2, int la, int lap, int rb,
+                   int rbp) {
+  if (!lay.su2) return 1.0;
+  return su2::coupled(LB.sub_qn(la).s, RB.sub_qn(rb).s, lay.target.s, LB.sub_qn(lap).s, RB.sub_qn(rbp).s,
+                      lay.target.s, k2, k2, 0);
+}
+}  // namespace
 
 OpView site_op_view(const Enlarged& E, const Mat4& o, bool par) {
   OpView v;
@@ -565,9 +590,10 @@ HeffPlan plan_terms(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay
     out.clear();
     tused = 0;
   };
+  const ProdBasis& RB = Rp.pb;
   for (const CenterTerm& t : terms) {
-    OpView Lv = t.LT ? transpose(*t.L) : *t.L;
-    OpView Rv = t.RT ? transpose(*t.R) : *t.R;
+    OpView Lv = t.LT ? (lay.su2 ? adjoint_su2(*t.L, &LB, nullptr) : transpose(*t.L)) : *t.L;
+    OpView Rv = t.RT ? (lay.su2 ? adjoint_su2(*t.R, &RB, nullptr) : transpose(*t.R)) : *t.R;
     std::map<int, std::vector<const BRef*>> lby;  // col sub -> blocks
     for (const BRef& b : Lv.blocks) lby[b.c].push_back(&b);
     int64_t need = 0;
@@ -619,9 +645,12 @@ HeffPlan plan_terms(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay
           else { g.a = bL->ptr; g.abuf = B_ABS; g.lda = bL->ld; g.ta = bL->tr ? 1 : 0; }
           g.b = Tb; g.bbuf = Tbuf; g.ldb = ldT; g.tb = 0;
           g.k = bL->cols;
-          g.sc = bsc * bL->sc;
-          g.asc = bL->sc;
+          // the SU(2) coupling factor goes with the left reference (for S = 0 it
+          // depends on the left reference alone, so the left views are not duplicated)
+          g.asc = bL->sc * pair_factor(lay, LB, RB, t.k2, bL->r, bL->c, bR.r, bR.c);
+          g.sc = bsc * g.asc;
           g.bsc = bsc;
+          if (g.asc == 0.0) continue;
           out.push_back({ot, g});
           if (!bL->ident()) s2.flops += 2.0 * bL->rows * bR.rows * (double)bL->cols;
         }
@@ -640,12 +669,13 @@ Launch plan_diag(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay, c
   // diag H_eff[(x,i,j,y)][a][b] = sum_t c_t dL[a] dR[b] over terms whose left and
   // right blocks are diagonal blocks: rank-1 segments (K = 1) with strided
   // diagonals (leading dimension ld + 1) or a vector of ones for identities
-  std::vector<CenterTerm> terms = center_terms(Lp, Rp, I);
+  std::vector<CenterTerm> terms = lay.su2 ? center_terms_su2(Lp, Rp, I) : center_terms(Lp, Rp, I);
   std::vector<std::pair<int, Seg>> out;  // (psi block, segment), grouped by block below
   const ProdBasis& LB = Lp.pb;
+  const ProdBasis& RB = Rp.pb;
   for (const CenterTerm& t : terms) {
-    OpView Lv = t.LT ? transpose(*t.L) : *t.L;
-    OpView Rv = t.RT ? transpose(*t.R) : *t.R;
+    OpView Lv = t.LT ? (lay.su2 ? adjoint_su2(*t.L, &LB, nullptr) : transpose(*t.L)) : *t.L;
+    OpView Rv = t.RT ? (lay.su2 ? adjoint_su2(*t.R, &RB, nullptr) : transpose(*t.R)) : *t.R;
     std::map<int, std::vector<const BRef*>> ldiag, rdiag;
     for (const BRef& b : Lv.blocks) if (b.r == b.c) ldiag[b.r].push_back(&b);
     for (const BRef& b : Rv.blocks) if (b.r == b.c) rdiag[b.r].push_back(&b);
@@ -663,7 +693,8 @@ Launch plan_diag(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay, c
             g.abuf = B_ABS; g.ta = 0;
             if (br->ident()) { g.b = ones; g.ldb = 1; } else { g.b = br->ptr; g.ldb = br->ld + 1; }
             g.bbuf = B_ABS; g.tb = 1;
-            g.sc = t.coef * bl->sc * br->sc * par;
+            g.sc = t.coef * bl->sc * br->sc * par * pair_factor(lay, LB, RB, t.k2, lk.first, lk.first, rk.first, rk.first);
+            if (g.sc == 0.0) continue;
             out.push_back({it, g});
           }
       }

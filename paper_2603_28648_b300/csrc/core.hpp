@@ -16,7 +16,7 @@
 namespace qd {
 
 struct QN {
-  int n = 0, s = 0;  // particle number, 2Sz
+  int n = 0, s = 0;  // particle number, 2Sz (U(1)) or 2S (SU(2))
   bool operator<(const QN& o) const { return n != o.n ? n < o.n : s < o.s; }
   bool operator==(const QN& o) const { return n == o.n && s == o.s; }
   bool operator!=(const QN& o) const { return !(*this == o); }
@@ -25,11 +25,16 @@ struct QN {
 };
 
 // Site basis: 0 = |0>, 1 = a+_up|0>, 2 = a+_dn|0>, 3 = a+_up a+_dn|0>.
+// In SU(2) mode the four indices are coupling channels of a block multiplet
+// with a site multiplet: 0 = |0>, 1 = the doublet coupled to S + 1/2, 2 = the
+// doublet coupled to S - 1/2, 3 = a+_up a+_dn|0>; their label shifts (n, 2S)
+// are the same four as the U(1) shifts (n, 2Sz).
 constexpr int NSITE = 4;
 extern const QN SITE_QN[NSITE];
 
 // Sectors of a block basis, sorted by label.
 struct Basis {
+  bool su2 = false;          // labels are (n, 2S) of SU(2) multiplets
   std::vector<QN> q;
   std::vector<int> dim;
   std::map<QN, int> idx;
@@ -78,6 +83,7 @@ struct BRef {
 };
 struct OpView {
   bool odd = false;
+  int k2 = 0;               // SU(2): twice the rank of the tensor operator
   std::vector<BRef> blocks;
   bool empty() const { return blocks.empty(); }
 };
@@ -86,12 +92,13 @@ OpView transpose(const OpView& o);
 // Operator keys.
 enum Fam : int { F_I = 0, F_C, F_A, F_B, F_S, F_P, F_Q, F_H };
 struct Key {
-  int f, a, b;
-  Key(int f_ = 0, int a_ = -1, int b_ = -1) : f(f_), a(a_), b(b_) {}
+  int f, a, b, k;   // family, indices, twice the SU(2) rank (0 in U(1))
+  Key(int f_ = 0, int a_ = -1, int b_ = -1, int k_ = 0) : f(f_), a(a_), b(b_), k(k_) {}
   bool operator<(const Key& o) const {
     if (f != o.f) return f < o.f;
     if (a != o.a) return a < o.a;
-    return b < o.b;
+    if (b != o.b) return b < o.b;
+    return k < o.k;
   }
 };
 
@@ -235,7 +242,7 @@ struct EnvBlock {
 };
 
 // Sector rule of the initial MPS (left labels, bonds 0..L).
-std::vector<std::map<QN, int>> mps_structure(int L, int N, int two_s, int D);
+std::vector<std::map<QN, int>> mps_structure(int L, int N, int two_s, int D, bool su2 = false);
 
 // Op-key list of a block at a cut with normal or complementary pairs.
 std::vector<Key> block_keys(bool left, bool normal, int cut, int L);
@@ -261,6 +268,8 @@ void renormalize(const Enlarged& E, const Basis& nb, const std::vector<int>& nb_
 // Two-site wavefunction layout: sub-blocks (x, i, j, y), sorted, row-major.
 struct PsiLayout {
   struct Blk { int x, i, j, y, lsub, rsub; int64_t off; int rows, cols; };
+  bool su2 = false;              // blocks couple L' and R' multiplets to total spin target.s / 2
+  QN target;
   std::vector<Blk> blks;
   int nl = 0, nr = 0;            // sub-blocks of the left and right enlarged bases
   std::vector<int> by_sub;       // lsub * nr + rsub -> block index, -1: no block
@@ -273,12 +282,15 @@ struct PsiLayout {
 PsiLayout make_psi_layout(const ProdBasis& Lp, const ProdBasis& Rp, QN target);
 
 // Operator-product terms of H at the centre cut: coef * L op (x) R op.
+// SU(2): LT / RT select the adjoint tensor, and the pair is the scalar
+// coupling [L^k x R^k]^0 of two rank-k operators (k2 = 2k).
 struct CenterTerm {
   const OpView* L;
   bool LT;
   const OpView* R;
   bool RT;
   double coef;
+  int k2 = 0;
 };
 std::vector<CenterTerm> center_terms(const Enlarged& Lp, const Enlarged& Rp, const Integrals& I);
 
@@ -302,6 +314,17 @@ HeffPlan plan_heff(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay,
 // Same for an arbitrary list of operator-product terms (expectation values).
 HeffPlan plan_terms(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay,
                     const std::vector<CenterTerm>& terms, int64_t tmp_budget);
+// SU(2) spin-adapted rules (rules_su2.cpp). Left blocks keep the normal
+// operators c_p, A^k_pq, B^k_pq (p <= q) of their orbitals, right blocks the
+// complementary T_m, P^k_pq, Q^k_pq (p <= q) of the orbitals to their left;
+// both keep c_p of their own orbitals and their Hamiltonian.
+void enlarge_su2(const EnvBlock& B, const Integrals& I, Executor& ex, Enlarged& out);
+std::vector<CenterTerm> center_terms_su2(const Enlarged& Lp, const Enlarged& Rp, const Integrals& I);
+// SU(2) adjoint tensor of a view whose references index sub-blocks of pb
+// (enlarged) or sectors of basis (renormalized): transposed references with
+// the reduced-element factor of the adjoint
+OpView adjoint_su2(const OpView& o, const ProdBasis* pb, const Basis* basis);
+
 // identity of the block part (x) a single-site operator, on an enlarged basis;
 // par applies the fermion parity of the block (left) or site (right) ket part
 OpView site_op_view(const Enlarged& E, const Mat4& o, bool par);

@@ -2,6 +2,7 @@
 // precision policy, density-matrix truncation, renormalization and the
 // two-site wavefunction transformation that moves the centre.
 #include "engine.hpp"
+#include "su2.hpp"
 
 #include <algorithm>
 #include <deque>
@@ -21,10 +22,11 @@ constexpr double TIE_REL = 1e-8;  // relative width of a group of equal weights 
 // error ~1e-16 of the unit trace) and are always discarded
 constexpr double WEIGHT_FLOOR = 1e-14;
 
-EnvBlock vacuum(bool left, int cut) {
+EnvBlock vacuum(bool left, int cut, bool su2) {
   EnvBlock b;
   b.left = left;
   b.cut = cut;
+  b.basis.su2 = su2;
   b.basis.add(QN{0, 0}, 1);
   return b;
 }
@@ -75,6 +77,10 @@ void small_eigh(const std::vector<double>& A0, int n, std::vector<double>& w, st
   }
   V.swap(W);
 }
+
+// site multiplet of a coupling channel (SU(2)): 0 |0>, 1 the doublet, 2 |updn>
+inline int site_mult(int ch) { return ch == 0 ? 0 : (ch == 3 ? 2 : 1); }
+const int SITE_MULT_S[3] = {0, 1, 0};
 
 Prob copy_prob(uint64_t dst, int m, int n, int ldc, int seg0) {
   Prob p;
@@ -230,12 +236,13 @@ void Engine::build_env() {
   auto t0 = std::chrono::steady_clock::now();
   clear_env();
   double fl = 0;
-  lenv[0] = vacuum(true, 0);
+  lenv[0] = vacuum(true, 0, su2);
   lenv[0].normal = normal_at(true, 0);
   for (int p = 0; p < center; ++p) {
     Enlarged E;
     E.batched = batched_sums();
-    enlarge(lenv[p], I, *ex, E, &fl, normal_at(true, p + 1));
+    if (su2) enlarge_su2(lenv[p], I, *ex, E);
+    else enlarge(lenv[p], I, *ex, E, &fl, normal_at(true, p + 1));
     EnvBlock nb;
     nb.cut = p + 1;
     renormalize(E, bonds[p + 1], site_nb[p], site[p], site_off[p], *ex, nb, tmp_budget, &fl);
@@ -243,12 +250,13 @@ void Engine::build_env() {
     lenv[p + 1] = nb;
     enforce_budget_build(p + 1, true);
   }
-  renv[L] = vacuum(false, L);
+  renv[L] = vacuum(false, L, su2);
   renv[L].normal = normal_at(false, L);
   for (int p = L - 1; p >= center + 2; --p) {
     Enlarged E;
     E.batched = batched_sums();
-    enlarge(renv[p + 1], I, *ex, E, &fl, normal_at(false, p));
+    if (su2) enlarge_su2(renv[p + 1], I, *ex, E);
+    else enlarge(renv[p + 1], I, *ex, E, &fl, normal_at(false, p));
     EnvBlock nb;
     nb.cut = p;
     renormalize(E, bonds[p], site_nb[p], site[p], site_off[p], *ex, nb, tmp_budget, &fl);
@@ -270,8 +278,13 @@ void Engine::prepare_center() {
   ensure_resident(lenv.at(center));
   ensure_resident(renv.at(center + 2));
   Lp.batched = Rp.batched = batched_sums();
-  enlarge(lenv.at(center), I, *ex, Lp, &fl, normal_at(true, center + 1));
-  enlarge(renv.at(center + 2), I, *ex, Rp, &fl, normal_at(false, center + 1));
+  if (su2) {
+    enlarge_su2(lenv.at(center), I, *ex, Lp);
+    enlarge_su2(renv.at(center + 2), I, *ex, Rp);
+  } else {
+    enlarge(lenv.at(center), I, *ex, Lp, &fl, normal_at(true, center + 1));
+    enlarge(renv.at(center + 2), I, *ex, Rp, &fl, normal_at(false, center + 1));
+  }
   lay = make_psi_layout(Lp.pb, Rp.pb, QN{N, two_s});
   plan = plan_heff(Lp, Rp, lay, I, tmp_budget);
   ex->tmp(std::max<int64_t>(1, plan.tmp_elems));
@@ -544,20 +557,41 @@ double Engine::truncate_move(int D, int dir, double drop_below) {
   const QN target{N, two_s};
   const ProdBasis& LB = Lp.pb;
   const ProdBasis& RB = Rp.pb;
-  // sector matrices Psi_q [(x,i) rows of L' sector q, (j,y) cols of R' sector]
-  struct Sec { int lq, rq, rows, cols; int64_t off; int64_t roff; };
+  // sector matrices: moving right, Psi_q [rows of L' sector q, columns of every
+  // R' sector coupled with q to the target]; moving left, Psi_r [rows of every
+  // L' sector coupled with r, columns of R' sector r]. In U(1) each sector has
+  // one partner; in SU(2) an L' multiplet of spin S_a couples with R'
+  // multiplets of every spin |S_a - S| .. S_a + S, and the density matrix of
+  // the multiplets of a sector, Psi_q Psi_q^T, sums over all of them (the
+  // weight of a multiplet is that of all its M components).
+  auto couples = [&](QN a, QN b) {
+    if (!su2) return a + b == target;
+    return a.n + b.n == target.n && std::abs(a.s - b.s) <= target.s && a.s + b.s >= target.s;
+  };
+  struct Sec { int key; int rows, cols; int64_t off, roff; std::map<int, int> poff; };
   std::vector<Sec> secs;
-  std::vector<int> sec_of_l(LB.prod.nsec(), -1), sec_of_r(RB.prod.nsec(), -1);
+  const ProdBasis& KB = dir > 0 ? LB : RB;   // the side that is truncated
+  const ProdBasis& OB = dir > 0 ? RB : LB;   // its partners
+  std::vector<int> sec_of(KB.prod.nsec(), -1);
   int64_t tot = 0, rtot = 0;
-  for (int lq = 0; lq < LB.prod.nsec(); ++lq) {
-    int rq = RB.prod.find(target - LB.prod.q[lq]);
-    if (rq < 0) continue;
-    Sec s{lq, rq, LB.prod.dim[lq], RB.prod.dim[rq], tot, rtot};
-    int ne = dir > 0 ? s.rows : s.cols;
+  for (int kq = 0; kq < KB.prod.nsec(); ++kq) {
+    Sec s;
+    s.key = kq;
+    int pdim = 0;
+    for (int oq = 0; oq < OB.prod.nsec(); ++oq)
+      if (dir > 0 ? couples(KB.prod.q[kq], OB.prod.q[oq]) : couples(OB.prod.q[oq], KB.prod.q[kq])) {
+        s.poff[oq] = pdim;
+        pdim += OB.prod.dim[oq];
+      }
+    if (s.poff.empty()) continue;
+    s.rows = dir > 0 ? KB.prod.dim[kq] : pdim;
+    s.cols = dir > 0 ? pdim : KB.prod.dim[kq];
+    s.off = tot;
+    s.roff = rtot;
+    const int ne = KB.prod.dim[kq];
     tot += (int64_t)s.rows * s.cols;
     rtot += (int64_t)ne * ne;
-    sec_of_l[lq] = (int)secs.size();
-    sec_of_r[rq] = (int)secs.size();
+    sec_of[kq] = (int)secs.size();
     secs.push_back(s);
   }
   uint64_t Psi = ex->alloc(std::max<int64_t>(1, tot));
@@ -567,11 +601,12 @@ double Engine::truncate_move(int D, int dir, double drop_below) {
     for (const auto& b : lay.blks) {
       const Sub& sl = LB.subs[b.lsub];
       const Sub& sr = RB.subs[b.rsub];
-      const Sec& s = secs.at(sec_of_l[sl.prod]);
+      const Sec& s = secs.at(sec_of[dir > 0 ? sl.prod : sr.prod]);
+      const int64_t r0 = dir > 0 ? sl.off : s.poff.at(sl.prod) + sl.off;
+      const int64_t c0 = dir > 0 ? s.poff.at(sr.prod) + sr.off : sr.off;
       Seg e;
       e.a = 0; e.b = dpsi + 8ull * b.off; e.ldb = b.cols; e.k = b.rows;
-      g.probs.push_back(copy_prob(Psi + 8ull * (s.off + (int64_t)sl.off * s.cols + sr.off), b.rows, b.cols, s.cols,
-                                  (int)g.segs.size()));
+      g.probs.push_back(copy_prob(Psi + 8ull * (s.off + r0 * s.cols + c0), b.rows, b.cols, s.cols, (int)g.segs.size()));
       g.segs.push_back(e);
     }
     ex->run(g, 0, 0);
@@ -597,7 +632,9 @@ double Engine::truncate_move(int D, int dir, double drop_below) {
     int ne = dir > 0 ? secs[k].rows : secs[k].cols;
     lam[k].resize(ne);
     ex->eigh(Rho + 8ull * secs[k].roff, ne, lam[k].data());
-    for (int j = 0; j < ne; ++j) cand.emplace_back(-lam[k][ne - 1 - j], LB.prod.q[secs[k].lq], j, (int)k);
+    // ties are ordered by the left label (the truncated side's partner label in U(1))
+    const QN lab = dir > 0 || su2 ? KB.prod.q[secs[k].key] : target - KB.prod.q[secs[k].key];
+    for (int j = 0; j < ne; ++j) cand.emplace_back(-lam[k][ne - 1 - j], lab, j, (int)k);
   }
   std::sort(cand.begin(), cand.end(), [](const auto& a, const auto& b) {
     if (std::get<0>(a) != std::get<0>(b)) return std::get<0>(a) < std::get<0>(b);
@@ -637,11 +674,12 @@ double Engine::truncate_move(int D, int dir, double drop_below) {
   if (nk == 0) throw std::runtime_error("truncation kept no state");
   // new bond basis
   Basis nb;
+  nb.su2 = su2;
   std::vector<int> nb_of_sec(secs.size(), -1);
   {
     std::vector<std::pair<QN, int>> lab;
     for (size_t k = 0; k < secs.size(); ++k)
-      if (keep[k]) lab.push_back({dir > 0 ? LB.prod.q[secs[k].lq] : RB.prod.q[secs[k].rq], (int)k});
+      if (keep[k]) lab.push_back({KB.prod.q[secs[k].key], (int)k});
     std::sort(lab.begin(), lab.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
     for (auto& x : lab) {
       nb_of_sec[x.second] = nb.nsec();
@@ -655,7 +693,7 @@ double Engine::truncate_move(int D, int dir, double drop_below) {
   int64_t ttot = 0;
   for (size_t k = 0; k < secs.size(); ++k) {
     if (!keep[k]) continue;
-    int q = dir > 0 ? secs[k].lq : secs[k].rq;
+    int q = secs[k].key;
     int ne = dir > 0 ? secs[k].rows : secs[k].cols;
     toff[q] = ttot;
     tnb[q] = nb_of_sec[k];
@@ -666,7 +704,7 @@ double Engine::truncate_move(int D, int dir, double drop_below) {
     Launch g;
     for (size_t k = 0; k < secs.size(); ++k) {
       if (!keep[k]) continue;
-      int q = dir > 0 ? secs[k].lq : secs[k].rq;
+      int q = secs[k].key;
       int ne = dir > 0 ? secs[k].rows : secs[k].cols;
       int d = keep[k];
       uint64_t ev = Rho + 8ull * (secs[k].roff + (int64_t)(ne - d) * ne);  // last d eigenvectors
@@ -698,7 +736,7 @@ double Engine::truncate_move(int D, int dir, double drop_below) {
     for (size_t k = 0; k < secs.size(); ++k) {
       if (!keep[k]) continue;
       const Sec& s = secs[k];
-      int q = dir > 0 ? s.lq : s.rq;
+      int q = s.key;
       int d = keep[k];
       Seg e;
       uint64_t P = Psi + 8ull * s.off, U = T + 8ull * toff[q];
@@ -724,29 +762,49 @@ double Engine::truncate_move(int D, int dir, double drop_below) {
     site_nb[c] = tnb;
     bonds[c + 1] = nb;
     lenv[c + 1] = blk;
-    // psi'(x', i', j', y') = C[x' rows, (i', y) cols] V_{c+2}[y, (j', y')]
+    // psi'(x', i', j', y') = C[x' rows, (i', y) cols] V_{c+2}[y, (j', y')]; in SU(2) the
+    // sum runs over the channels of the old R' sub-block (s, y) whose site multiplet is
+    // that of i', each recoupled from |x', (s y) J_old; S> to |(x' s) J_a, y; S>
     ProdBasis nL = make_prod(bonds[c + 1], true), nR = make_prod(bonds[c + 3], false);
     PsiLayout nl = make_psi_layout(nL, nR, target);
     ProdBasis R3 = make_prod(bonds[c + 3], false);
     uint64_t np = ex->alloc(std::max<int64_t>(1, nl.size));
+    std::vector<int> sec_of_nb(nb.nsec(), -1);
+    for (size_t k = 0; k < secs.size(); ++k)
+      if (nb_of_sec[k] >= 0) sec_of_nb[nb_of_sec[k]] = (int)k;
     Launch g;
     for (const auto& b : nl.blks) {
-      QN ylab = SITE_QN[b.j] + bonds[c + 3].q[b.y];
-      int y = bonds[c + 2].find(ylab);
+      const int r = R3.find(b.y, b.j);                // product sub (j', y') of site c+2
+      const int rp = R3.subs[r].prod;
+      const int y = bonds[c + 2].find(R3.prod.q[rp]);
       if (y < 0) continue;
-      int sR = RB.find(y, b.i);                       // old R' sub (i', y)
-      int k = sec_of_r[RB.subs[sR].prod];
-      if (k < 0 || !keep[k]) continue;
-      const Sec& s = secs[k];
-      int r = R3.find(b.y, b.j);                      // product sub (j', y') of site c+2
-      int rp = R3.subs[r].prod;
-      Seg e;
-      e.a = Cb + 8ull * (coff[k] + RB.subs[sR].off); e.lda = s.cols; e.ta = 0;
-      e.b = site[c + 2] + 8ull * (site_off[c + 2][rp] + R3.subs[r].off); e.ldb = R3.prod.dim[rp]; e.tb = 0;
-      e.k = bonds[c + 2].dim[y];
-      g.probs.push_back(copy_prob(np + 8ull * b.off, b.rows, b.cols, b.cols, (int)g.segs.size()));
-      g.segs.push_back(e);
+      const int k = sec_of_nb[b.x];
+      const Sec& s = secs.at(k);
+      Prob p = copy_prob(np + 8ull * b.off, b.rows, b.cols, b.cols, (int)g.segs.size());
+      p.nseg = 0;
+      for (int ch = 0; ch < NSITE; ++ch) {
+        if (su2 ? site_mult(ch) != site_mult(b.i) : ch != b.i) continue;
+        const int sR = RB.find(y, ch);                  // old R' sub (s, y)
+        if (sR < 0) continue;
+        auto po = s.poff.find(RB.subs[sR].prod);
+        if (po == s.poff.end()) continue;
+        double w = 1.0;
+        if (su2) {
+          const int Ja = nL.sub_qn(nL.find(b.x, b.i)).s, Jold = RB.sub_qn(sR).s;
+          w = su2::assoc(nb.q[b.x].s, SITE_MULT_S[site_mult(ch)], bonds[c + 2].q[y].s, Ja, Jold, target.s);
+          if (w == 0.0) continue;
+        }
+        Seg e;
+        e.a = Cb + 8ull * (coff[k] + po->second + RB.subs[sR].off); e.lda = s.cols; e.ta = 0;
+        e.b = site[c + 2] + 8ull * (site_off[c + 2][rp] + R3.subs[r].off); e.ldb = R3.prod.dim[rp]; e.tb = 0;
+        e.k = bonds[c + 2].dim[y];
+        e.sc = w;
+        g.segs.push_back(e);
+        ++p.nseg;
+      }
+      if (p.nseg) g.probs.push_back(p);
     }
+    ex->zero(np, std::max<int64_t>(1, nl.size));
     ex->run(g, 0, 0);
     ex->release(site[c + 2]);
     site[c + 2] = 0;
@@ -765,30 +823,51 @@ double Engine::truncate_move(int D, int dir, double drop_below) {
     site_nb[c + 1] = tnb;
     bonds[c + 1] = nb;
     renv[c + 1] = blk;
-    // psi'(x', i', j', y') = U_{c-1}[(x', i') rows -> x] C[(x, j') rows, y' cols]
+    // psi'(x', i', j', y') = U_{c-1}[(x', i') rows -> x] C[(x, j') rows, y' cols]; in SU(2)
+    // over the channels of the old L' sub-block (x, s) whose site multiplet is that of
+    // j', each recoupled from |(x s) J_old, y'; S> to |x, (s y') J_b; S>
     ProdBasis nL = make_prod(bonds[c - 1], true), nR = make_prod(bonds[c + 1], false);
     PsiLayout nl = make_psi_layout(nL, nR, target);
     ProdBasis L1 = make_prod(bonds[c - 1], true);
     uint64_t np = ex->alloc(std::max<int64_t>(1, nl.size));
+    std::vector<int> sec_of_nb(nb.nsec(), -1);
+    for (size_t k = 0; k < secs.size(); ++k)
+      if (nb_of_sec[k] >= 0) sec_of_nb[nb_of_sec[k]] = (int)k;
     Launch g;
     for (const auto& b : nl.blks) {
-      QN xlab = bonds[c - 1].q[b.x] + SITE_QN[b.i];
-      int x = bonds[c].find(xlab);
+      const int u = L1.find(b.x, b.i);                // product sub (x', i') of site c-1
+      const int up = L1.subs[u].prod;
+      const int x = bonds[c].find(L1.prod.q[up]);
       if (x < 0) continue;
-      int sL = LB.find(x, b.j);                       // old L' sub (x, j')
-      int k = sec_of_l[LB.subs[sL].prod];
-      if (k < 0 || !keep[k]) continue;
-      int d = keep[k];
-      int u = L1.find(b.x, b.i);                      // product sub (x', i') of site c-1
-      int up = L1.subs[u].prod;
-      Seg e;
-      e.a = site[c - 1] + 8ull * (site_off[c - 1][up] + (int64_t)L1.subs[u].off * bonds[c].dim[x]);
-      e.lda = bonds[c].dim[x]; e.ta = 0;
-      e.b = Cb + 8ull * (coff[k] + (int64_t)LB.subs[sL].off * d); e.ldb = d; e.tb = 0;
-      e.k = bonds[c].dim[x];
-      g.probs.push_back(copy_prob(np + 8ull * b.off, b.rows, b.cols, b.cols, (int)g.segs.size()));
-      g.segs.push_back(e);
+      const int k = sec_of_nb[b.y];
+      const Sec& s = secs.at(k);
+      const int d = keep[k];
+      Prob p = copy_prob(np + 8ull * b.off, b.rows, b.cols, b.cols, (int)g.segs.size());
+      p.nseg = 0;
+      for (int ch = 0; ch < NSITE; ++ch) {
+        if (su2 ? site_mult(ch) != site_mult(b.j) : ch != b.j) continue;
+        const int sL = LB.find(x, ch);                  // old L' sub (x, s)
+        if (sL < 0) continue;
+        auto po = s.poff.find(LB.subs[sL].prod);
+        if (po == s.poff.end()) continue;
+        double w = 1.0;
+        if (su2) {
+          const int Jb = nR.sub_qn(nR.find(b.y, b.j)).s, Jold = LB.sub_qn(sL).s;
+          w = su2::assoc(bonds[c].q[x].s, SITE_MULT_S[site_mult(ch)], nb.q[b.y].s, Jold, Jb, target.s);
+          if (w == 0.0) continue;
+        }
+        Seg e;
+        e.a = site[c - 1] + 8ull * (site_off[c - 1][up] + (int64_t)L1.subs[u].off * bonds[c].dim[x]);
+        e.lda = bonds[c].dim[x]; e.ta = 0;
+        e.b = Cb + 8ull * (coff[k] + (po->second + (int64_t)LB.subs[sL].off) * d); e.ldb = d; e.tb = 0;
+        e.k = bonds[c].dim[x];
+        e.sc = w;
+        g.segs.push_back(e);
+        ++p.nseg;
+      }
+      if (p.nseg) g.probs.push_back(p);
     }
+    ex->zero(np, std::max<int64_t>(1, nl.size));
     ex->run(g, 0, 0);
     ex->release(site[c - 1]);
     site[c - 1] = 0;
@@ -830,6 +909,7 @@ double Engine::expect(const std::vector<CenterTerm>& terms) {
 }
 
 std::vector<double> Engine::rdm1() {
+  if (su2) throw StateError("density matrices are measured with the U(1) operators; not available with SU(2)");
   // At the centre (L-2, L-1) the left enlarged block L' holds the normal
   // operators a+_k a_l of every spin-orbital of sites 0..L-2, and the right
   // enlarged block is the last site alone, so every E_pq is a product of
@@ -896,6 +976,7 @@ std::vector<double> Engine::rdm1() {
 }
 
 std::vector<double> Engine::rdm2_sweep() {
+  if (su2) throw StateError("density matrices are measured with the U(1) operators; not available with SU(2)");
   // Gamma_pqrs = sum over spins sigma, tau of <a+_{p sigma} a+_{r tau} a_{s tau} a_{q sigma}>,
   // each element measured at the one centre (s1, s2 = s1 + 1) where its four
   // operators split into at most two on the left block (stored C, A, B), any
@@ -1087,6 +1168,7 @@ std::vector<double> Engine::rdm2_sweep() {
 }
 
 std::vector<double> Engine::rdm2() {
+  if (su2) throw StateError("density matrices are measured with the U(1) operators; not available with SU(2)");
   // At fixed MPS the energy is linear in V: with h = 0, e_core = 0 and V the
   // unit tensor on one permutation orbit {pqrs, qprs, pqsr, qpsr, rspq, srpq,
   // rsqp, srqp}, <H_eff> = 1/2 sum over the orbit's distinct elements of

@@ -37,6 +37,9 @@ struct Engine {
   PreparedRunner* pr = nullptr;
   Integrals I;
   int N = 0, two_s = 0, L = 0, center = -1;
+  // SU(2) spin adaptation: bond labels (n, 2S) of multiplets, reduced
+  // operators (rules_su2.cpp); two_s is then twice the total spin
+  bool su2 = false;
   int64_t tmp_budget = 0;
   // cut of the normal/complementary switch: left blocks at cuts <= pair_switch
   // and right blocks at cuts > pair_switch hold normal pairs (0: normal pairs

@@ -17,12 +17,19 @@
 
 namespace qd {
 
-static std::map<QN, double> counts(int nsites) {
+// Exact number of block states (U(1)) or multiplets (SU(2)) per label. In
+// SU(2) the four label shifts are the coupling channels of a site multiplet,
+// and a doublet coupled to a singlet gives spin 1/2 only (no negative 2S).
+static std::map<QN, double> counts(int nsites, bool su2) {
   std::map<QN, double> cur{{QN{0, 0}, 1.0}};
   for (int k = 0; k < nsites; ++k) {
     std::map<QN, double> nxt;
     for (auto& kv : cur)
-      for (int s = 0; s < NSITE; ++s) nxt[kv.first + SITE_QN[s]] += kv.second;
+      for (int s = 0; s < NSITE; ++s) {
+        const QN q = kv.first + SITE_QN[s];
+        if (su2 && q.s < 0) continue;
+        nxt[q] += kv.second;
+      }
     cur.swap(nxt);
   }
   return cur;
@@ -84,23 +91,35 @@ static std::map<QN, int> allocate(int D, const std::map<QN, long long>& caps,
   return out;
 }
 
-std::vector<std::map<QN, int>> mps_structure(int L, int N, int two_s, int D) {
+std::vector<std::map<QN, int>> mps_structure(int L, int N, int two_s, int D, bool su2) {
   std::vector<std::map<QN, int>> bonds(L + 1);
   bonds[0][QN{0, 0}] = 1;
   bonds[L][QN{N, two_s}] = 1;
   std::vector<std::map<QN, double>> cnt(L + 1);
-  for (int b = 0; b <= L; ++b) cnt[b] = counts(b);
+  for (int b = 0; b <= L; ++b) cnt[b] = counts(b, su2);
   const QN target{N, two_s};
   for (int b = 1; b < L; ++b) {
     std::map<QN, long long> prod;
     for (auto& kv : bonds[b - 1])
-      for (int s = 0; s < NSITE; ++s) prod[kv.first + SITE_QN[s]] += kv.second;
+      for (int s = 0; s < NSITE; ++s) {
+        const QN q = kv.first + SITE_QN[s];
+        if (su2 && q.s < 0) continue;
+        prod[q] += kv.second;
+      }
     std::map<QN, long long> caps;
     std::map<QN, double> w;
     for (auto& kv : cnt[b]) {
       const QN q = kv.first;
-      auto it = cnt[L - b].find(target - q);
-      double comp = it == cnt[L - b].end() ? 0.0 : it->second;
+      double comp = 0.0;
+      if (su2) {
+        // multiplets of the other L-b sites that couple with q to the target spin
+        for (auto& r : cnt[L - b])
+          if (r.first.n == N - q.n && std::abs(q.s - r.first.s) <= two_s && q.s + r.first.s >= two_s)
+            comp += r.second;
+      } else {
+        auto it = cnt[L - b].find(target - q);
+        comp = it == cnt[L - b].end() ? 0.0 : it->second;
+      }
       double c = std::min(kv.second, comp);
       auto pit = prod.find(q);
       double pc = pit == prod.end() ? 0.0 : (double)pit->second;

@@ -327,8 +327,10 @@ int main(int argc, char** argv) {
     E.N = (int)hd[1];
     E.two_s = (int)hd[2];
     const int c = (int)hd[3];
+    if (const char* s2 = std::getenv("HOST_EXEC_SU2")) E.su2 = std::atoi(s2) != 0;
     // import, as the C ABI does: bond sectors, site tensors per product sector, psi
     std::vector<Basis> bonds(L + 1);
+    for (auto& b : bonds) b.su2 = E.su2;
     int pos = 0;
     for (int b = 0; b <= L; ++b)
       for (int s = 0; s < nsec[b]; ++s, ++pos) bonds[b].add(QN{sec[3 * pos], sec[3 * pos + 1]}, sec[3 * pos + 2]);

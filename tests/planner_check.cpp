@@ -34,15 +34,25 @@ struct RecEx : Executor {
   uint64_t tmp_base = 0;
   int64_t tmp_n = 0;
   int64_t live = 0;
+  std::map<uint64_t, int64_t> cur;  // allocations not yet released
+  int64_t cur_live = 0, peak = 0;
   uint64_t alloc(int64_t n) override {
     const uint64_t p = next;
     const int64_t b = std::max<int64_t>(8, n * 8);
     next += ((b + 255) / 256) * 256 + 256;
     alloc_bytes[p] = b;
     live += b;
+    cur[p] = b;
+    cur_live += b;
+    peak = std::max(peak, cur_live);
     return p;
   }
-  void release(uint64_t) override {}
+  void release(uint64_t p) override {
+    auto it = cur.find(p);
+    if (it == cur.end()) return;
+    cur_live -= it->second;
+    cur.erase(it);
+  }
   uint64_t tmp(int64_t n) override {
     if (n > tmp_n) {
       tmp_base = alloc(n);
@@ -240,11 +250,12 @@ void check_tiled(const HeffPlan& P, const PsiLayout& lay, const RecEx& ex, const
 
 int main(int argc, char** argv) {
   if (argc < 4) {
-    std::fprintf(stderr, "usage: planner_check L N D [pair_switch [sum_gemm]]\n");
+    std::fprintf(stderr, "usage: planner_check L N D [pair_switch [sum_gemm [su2]]]\n");
     return 2;
   }
   const int L = std::atoi(argv[1]), N = std::atoi(argv[2]), D = std::atoi(argv[3]);
-  const int two_s = N % 2;
+  const bool su2 = argc > 6 && std::atoi(argv[6]) != 0;
+  const int two_s = su2 ? 0 : N % 2;
   RecEx ex;
   NullRunner pr;
   Engine E;
@@ -253,6 +264,7 @@ int main(int argc, char** argv) {
   E.N = N;
   E.two_s = two_s;
   E.L = L;
+  E.su2 = su2;
   E.tmp_budget = (int64_t)(2e9 / 8);
   if (argc > 4) E.pair_switch = std::atoi(argv[4]);
   if (argc > 5) E.sum_gemm = std::atoi(argv[5]);
@@ -270,8 +282,9 @@ int main(int argc, char** argv) {
           E.I.V[(((size_t)p * L + q) * L + r) * L + s] = 0.01 + 1e-3 * ((std::min(a, b) * 31 + std::max(a, b) * 17) % 97);
         }
   const int center = L / 2 - 1;
-  auto st = mps_structure(L, N, two_s, D);
+  auto st = mps_structure(L, N, two_s, D, su2);
   std::vector<Basis> bonds(L + 1);
+  for (auto& b : bonds) b.su2 = su2;
   for (int b = 0; b <= center; ++b)
     for (auto& kv : st[b]) bonds[b].add(kv.first, kv.second);
   for (int b = center + 2; b <= L; ++b)
@@ -315,7 +328,18 @@ int main(int argc, char** argv) {
       cfg.width = width;
       check_tiled(E.plan, E.lay, ex, cfg);
     }
-  std::printf("L=%d N=%d D=%d psi=%lld terms=%d gflop=%.4f launches=%lld fails=%d\n", L, N, D, (long long)E.lay.size,
-              E.plan.nterms, E.plan.flops / 1e9, (long long)ex.launches_checked, fails);
+  int64_t lp = 0, rp = 0;
+  for (uint64_t a : E.Lp.owned) lp += ex.alloc_bytes.at(a);
+  for (uint64_t a : E.Rp.owned) rp += ex.alloc_bytes.at(a);
+  std::printf("centre enlarged blocks: left %.2f GB (%zu ops), right %.2f GB (%zu ops)\n", lp / 1e9, E.Lp.ops.size(),
+              rp / 1e9, E.Rp.ops.size());
+  int64_t env = 0;
+  for (auto& kv : E.lenv)
+    for (int64_t n : kv.second.owned_n) env += 8 * n;
+  for (auto& kv : E.renv)
+    for (int64_t n : kv.second.owned_n) env += 8 * n;
+  std::printf("L=%d N=%d D=%d psi=%lld terms=%d gflop=%.4f launches=%lld fails=%d peak_gb=%.2f live_gb=%.2f env_gb=%.2f "
+              "heff_gb=%.3f\n", L, N, D, (long long)E.lay.size, E.plan.nterms, E.plan.flops / 1e9,
+              (long long)ex.launches_checked, fails, ex.peak / 1e9, ex.cur_live / 1e9, env / 1e9, E.plan.bytes / 1e9);
   return fails ? 1 : 0;
 }

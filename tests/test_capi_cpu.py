@@ -50,3 +50,14 @@ def test_create_rejects_bad_configuration_before_cuda(field, value):
     h = ctypes.c_void_p()
     assert lib.qcdmrg_create(ctypes.byref(h), ctypes.byref(cfg)) == -1
     assert not h.value
+
+
+def test_su2_needs_normal_pairs_on_the_left():
+    """The spin-adapted rules keep normal pairs on the left at every cut: an SU(2) context
+    with the normal/complementary switch is rejected before any CUDA call."""
+    import paper_2603_28648_b300 as qd
+    path = ensure_built()
+    lib = ctypes.CDLL(path)
+    cfg = qd.Config(qd.SU2, 0, 0.0, 0.0, 0, 3, 0)
+    h = ctypes.c_void_p()
+    assert lib.qcdmrg_create(ctypes.byref(h), ctypes.byref(cfg)) == -1

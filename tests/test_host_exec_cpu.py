@@ -17,7 +17,7 @@ import qcinputs as q
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_2603_28648_b300", "csrc")
-HOST_SOURCES = ["core.cpp", "rules.cpp", "init.cpp", "engine.cpp", "tiled.cpp"]
+HOST_SOURCES = ["core.cpp", "rules.cpp", "rules_su2.cpp", "su2.cpp", "init.cpp", "engine.cpp", "tiled.cpp"]
 
 
 @pytest.fixture(scope="module")
@@ -267,3 +267,57 @@ def test_rdm2_by_centre_walk_identities_at_L12(host_exec, tmp_path):
     psi, sig = rest[:n], rest[n:]
     E = psi @ sig / (psi @ psi)
     assert abs(np.sum(h * g) + 0.5 * np.sum(V * G) - E) <= 1e-11 * abs(E)
+
+
+# SU(2) spin adaptation: the library's reduced-operator task lists (rules_su2.cpp) and its
+# SU(2) truncation and centre moves against the operator-based SU(2) oracle.
+def _write_su2(path, mps, h, V):
+    from oracle.dmrgsu2 import export_abi_su2
+    nsec, sec, data = export_abi_su2(mps)
+    with open(path, "wb") as f:
+        f.write(struct.pack("<7q", mps.L, mps.N, mps.two_s, mps.center, len(nsec), len(sec), len(data)))
+        f.write(np.ascontiguousarray(h, "<f8").tobytes())
+        f.write(np.ascontiguousarray(V, "<f8").tobytes())
+        f.write(np.asarray(nsec, "<i4").tobytes())
+        f.write(np.asarray(sec, "<i4").tobytes())
+        f.write(np.asarray(data, "<f8").tobytes())
+
+
+def _run_su2(exe, tmp, mps, h, V, extra=()):
+    fin, fout = str(tmp / "su2_in.bin"), str(tmp / "su2_out.bin")
+    _write_su2(fin, mps, h, V)
+    r = subprocess.run([exe, fin, fout] + list(extra), capture_output=True, text=True, timeout=900,
+                       env=dict(os.environ, HOST_EXEC_SU2="1"))
+    assert r.returncode == 0, r.stderr
+    return np.fromfile(fout, "<f8")
+
+
+@pytest.mark.parametrize("L,N,two_s,D,c", [(4, 4, 0, 16, 1), (5, 5, 1, 8, 1), (5, 4, 2, 8, 2), (6, 6, 0, 6, 0),
+                                           (6, 5, 1, 6, 4), (6, 6, 2, 5, 2), (8, 8, 0, 20, 3)])
+def test_su2_task_lists_match_the_oracle(host_exec, tmp_path, L, N, two_s, D, c):
+    from oracle.dmrgsu2 import DMRGSU2, MPSSU2
+    mps = MPSSU2.from_raw(q.random_mps_blocks(L, N, two_s, D, q.SYM_SU2, 5, c))
+    h, V = q.make_integrals(L, 11)
+    out = _run_su2(host_exec, tmp_path, mps, h, V)
+    n = len(out) // 2
+    ref = mps.psi_to_flat(DMRGSU2(h, V, N, two_s).sigma(mps))
+    assert n == len(ref)
+    for s in (out[:n], out[n:]):
+        assert np.linalg.norm(s - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("L,N,two_s,D,c", [(6, 6, 0, 400, 2), (6, 5, 1, 8, 2), (6, 6, 2, 10, 1)])
+def test_su2_engine_sweeps_match_the_oracle(host_exec, tmp_path, L, N, two_s, D, c):
+    """Davidson, SU(2) truncation (multiplet weights of sectors coupled to several
+    partner spins) and the 6j recoupling of the two-site guess at every centre move,
+    two sweeps; at the exact bond dimension (first case) the spin-filtered FCI energy."""
+    from oracle.dmrgsu2 import DMRGSU2, MPSSU2
+    from oracle.fci import FCI
+    mps = MPSSU2.from_raw(q.random_mps_blocks(L, N, two_s, D, q.SYM_SU2, 2, c))
+    h, V = q.make_integrals(L, 13)
+    E = _run_su2(host_exec, tmp_path, mps, h, V, ["sweep", str(D), "2", "1e-10"])
+    Eo, _, _ = DMRGSU2(h, V, N, two_s).sweeps(mps, D, nsweeps=2, tol=1e-12)
+    assert np.abs(E - np.array(Eo)).max() <= 1e-9
+    if D == 400:
+        e_fci, _ = FCI(h, V, N, two_s).ground_state(two_s=two_s)
+        assert abs(E[-1] - e_fci) <= 1e-9

@@ -12,7 +12,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_2603_28648_b300", "csrc")
-HOST_SOURCES = ["core.cpp", "rules.cpp", "init.cpp", "engine.cpp", "tiled.cpp"]
+HOST_SOURCES = ["core.cpp", "rules.cpp", "rules_su2.cpp", "su2.cpp", "init.cpp", "engine.cpp", "tiled.cpp"]
 
 
 @pytest.fixture(scope="module")
@@ -42,5 +42,15 @@ def test_plans_stay_in_bounds(checker, L, N, D, switch, sum_gemm):
     operator sums without the switch."""
     r = subprocess.run([checker, str(L), str(N), str(D), str(switch), str(sum_gemm)], capture_output=True,
                        text=True, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "fails=0" in r.stdout
+
+
+@pytest.mark.parametrize("L,N,D", [(6, 6, 16), (12, 12, 64), (36, 54, 256)])
+def test_su2_plans_stay_in_bounds(checker, L, N, D):
+    """The SU(2) reduced-operator task lists (environment build, enlargement sums, centre
+    FP64 segments and tiled work items) at the CAS(54,36) shape and smaller."""
+    r = subprocess.run([checker, str(L), str(N), str(D), "0", "0", "1"], capture_output=True, text=True,
+                       timeout=600)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "fails=0" in r.stdout
