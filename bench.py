@@ -33,6 +33,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--D", type=int, default=1024)
+    ap.add_argument("--symmetry", default="su2", choices=["su2", "u1"],
+                    help="su2: spin-adapted (D counts SU(2) multiplets, the paper's D_SU(2)); u1: U(1)xU(1)")
     ap.add_argument("--L", type=int, default=36)
     ap.add_argument("--N", type=int, default=54)
     ap.add_argument("--precision", default="bf16", choices=["fp64", "tf32", "bf16", "bf16x3"],
@@ -258,7 +260,8 @@ def run_ours(args, rank, world, local):
 
     L, N, D = args.L, args.N, args.D
     h, V = q.make_integrals(L, q.integrals.BASE_SEED + 2)
-    ctx = qd.Context(device=local, hbm_budget_gb=args.hbm_budget, pair_switch=args.pair_switch,
+    sym = qd.SU2 if args.symmetry == "su2" else qd.U1
+    ctx = qd.Context(device=local, symmetry=sym, hbm_budget_gb=args.hbm_budget, pair_switch=args.pair_switch,
                      sum_gemm=args.sum_gemm)
     ctx.load_integrals(h, V)
     ctx.set_target(N, 0)
@@ -409,8 +412,10 @@ def run_ours(args, rank, world, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": args.precision.replace("fp", "f"), "data": "synthetic",
-        "config": {"workload": f"u1_L{L}_N{N}_Sz0_D{D} centre-bond H_eff psi",
-                   "symmetry": "U(1)xU(1)", "precision": args.precision, "L": L, "N": N, "D": D,
+        "config": {"workload": (f"su2_L{L}_N{N}_S0_D{D} centre-bond H_eff psi" if args.symmetry == "su2"
+                                else f"u1_L{L}_N{N}_Sz0_D{D} centre-bond H_eff psi"),
+                   "symmetry": "SU(2)" if args.symmetry == "su2" else "U(1)xU(1)",
+                   "precision": args.precision, "L": L, "N": N, "D": D,
                    "psi_size": st["psi_size"], "terms": st["nterms"],
                    "heff_gflop": flops / 1e9, "env_build_s": env_s,
                    "env_build_tflops": st["env_flops"] / env_s / 1e12,

@@ -136,6 +136,10 @@ typedef struct {
                             32x64, 32x32 over the prepared task lists of the current centre */
   int64_t f64_split_tiles; /* of those, tiles of problems whose summed K exceeds one work item
                             (split over several tiles that add with FP64 atomics) */
+  int dav_hpsi[4];       /* last qcdmrg_davidson call: H psi products per precision (FP64, TF32,
+                            BF16, BF16x3) */
+  double dav_seconds;    /* its wall time */
+  double dav_energy_mixed; /* its last Ritz value before the FP64 correction (policy 1) */
 } qcdmrg_stats_t;
 
 /* Davidson options (zero fields take the defaults in brackets). */
@@ -144,10 +148,16 @@ typedef struct {
                      residual, Numerical procedure section] */
   int max_iter;   /* [300] */
   int m_max;      /* subspace size before a restart [32] */
-  int policy;     /* 0: every H psi in `precision`; 1: BF16 while the residual is above tau1,
-                     BF16x3 while above tau2, then FP64 H psi until converged (the final
-                     residual and energy are always from the FP64 form); a reduced-precision
-                     phase also ends when its residual has not halved in 6 iterations */
+  int policy;     /* 0: every H psi in `precision`; 1: mixed precision with FP64 residual
+                     correction: BF16 H psi while the residual is above tau1, BF16x3 while
+                     above tau2 (a phase also ends at its rounding floor, 2^-6 |E| for BF16
+                     and 2^-14 |E| for BF16x3, or when its residual has not fallen by 10 % in
+                     8 iterations), then outer checks: one FP64 H psi of the normalised Ritz
+                     vector gives the energy and the residual; if the residual is above tol,
+                     that exact pair restarts the subspace and BF16x3 products expand it
+                     until the residual has fallen 30-fold (or m_max - 2 products), then the
+                     next check. The final energy and residual are always from an FP64
+                     product */
   int precision;  /* QCDMRG_FP64 / _TF32 / _BF16 / _BF16X3 for policy 0 */
   double tau1;    /* [1e-2] */
   double tau2;    /* [1e-5] */

@@ -652,6 +652,7 @@ class Heff:
         pa, pb = Lp.prod, Rp.prod
         na, sa = Lp.n, Lp.s
         nb, sb = Rp.n, Rp.s
+        self.mask_n = N
         self.mask = (na[:, None] + nb[None, :] == N) & \
             (np.abs(sa[:, None] - sb[None, :]) <= two_s) & (sa[:, None] + sb[None, :] >= two_s)
         self.sign = np.where(na % 2 == 0, 1.0, -1.0)
@@ -686,6 +687,41 @@ class Heff:
                             if odd:
                                 t = t * self.sign[Iap][:, None]
                             sig[np.ix_(Iap, Ibp)] += t
+
+    def algorithmic_flops(self):
+        """Flops of one H_eff psi counted per quantum-number sector: for every term
+        and every pair of nonzero (n, 2S) sector blocks of O_L and O_R that meet a
+        psi block, 2 d_a' d_b' d_b (psi O_R^T) + 2 d_a d_a' d_b (O_L times that);
+        the Hermitian conjugates and the block Hamiltonians counted the same way."""
+        def sectors(n, s):
+            labs = sorted(set(zip(n.tolist(), s.tolist())))
+            ind = np.zeros((len(labs), len(n)))
+            for k, lab in enumerate(labs):
+                ind[k, (n == lab[0]) & (s == lab[1])] = 1.0
+            return labs, ind, ind.sum(axis=1)
+        la, Ia, da = sectors(self.Lp.n, self.Lp.s)
+        lb, Ib, db = sectors(self.Rp.n, self.Rp.s)
+        allow = np.array([[1.0 if (a[0] + b[0] == self.mask_n and allowed(a[1], b[1], self.two_s)) else 0.0
+                           for b in lb] for a in la])
+
+        def nz(O, ind):
+            return (ind @ (np.abs(O) > 0) @ ind.T) > 0
+
+        def count(nzl, nzr):
+            # stage 1: X[a', b] = sum_b' allow[a', b'] nzr[b, b'] d_b' d_b
+            X = (allow * db[None, :]) @ (nzr.T * db[None, :])
+            s1 = float(np.sum((nzl * da[None, :]) @ X * allow))
+            # stage 2: sum over (a, a', b) of 2 d_a d_a' d_b where the stage-1 output exists
+            Y = allow @ nzr.T                       # [a', b]: some b' reaches b
+            s2 = float(np.sum(((nzl * (da[:, None] * da[None, :])) @ ((Y > 0) * db[None, :])) * allow))
+            return 2.0 * (s1 + s2)
+        tot = 0.0
+        idL, idR = np.eye(len(la)) > 0, np.eye(len(lb)) > 0
+        tot += count(nz(self.Lp.H, Ia), idR) + count(idL, nz(self.Rp.H, Ib))
+        for OL, OR, k, coef, odd, hc in self.terms:
+            f = count(nz(OL, Ia), nz(OR, Ib))
+            tot += 2 * f if hc else f
+        return tot
 
     def apply_mat(self, x):
         x = x * self.mask

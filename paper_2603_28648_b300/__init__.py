@@ -68,7 +68,8 @@ class Stats(ctypes.Structure):
                 ("copy_wait_seconds", ctypes.c_double), ("heff_bytes", ctypes.c_double),
                 ("tile_kmax", ctypes.c_int), ("tile_width", ctypes.c_int), ("tunes", ctypes.c_int),
                 ("tune_seconds", ctypes.c_double), ("f64_tiles", ctypes.c_int64 * 4),
-                ("f64_split_tiles", ctypes.c_int64)]
+                ("f64_split_tiles", ctypes.c_int64), ("dav_hpsi", ctypes.c_int * 4),
+                ("dav_seconds", ctypes.c_double), ("dav_energy_mixed", ctypes.c_double)]
 
 
 EXPORTS = [

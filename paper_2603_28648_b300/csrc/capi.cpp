@@ -727,7 +727,11 @@ int qcdmrg_davidson(qcdmrg_ctx* ctx, const qcdmrg_dav_opts* o, double* energy, d
     if (!E.have_env) throw Fail{QCDMRG_ESTATE, "build_env first"};
     if (o && (!valid_precision(o->precision) || o->policy < 0 || o->policy > 1))
       throw Fail{QCDMRG_EINVAL, "bad Davidson options"};
+    const auto t0 = std::chrono::steady_clock::now();
     DavResult r = E.davidson(dav_opts(o));
+    ctx->st.dav_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    for (int k = 0; k < 4; ++k) ctx->st.dav_hpsi[k] = r.hpsi[k];
+    ctx->st.dav_energy_mixed = r.energy_mixed;
     if (energy) *energy = r.energy;
     if (resid) *resid = r.resid;
     if (iters) *iters = r.iters;

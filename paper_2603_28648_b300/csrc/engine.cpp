@@ -8,6 +8,8 @@
 #include <deque>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <mutex>
 #include <stdexcept>
 #include <array>
@@ -288,8 +290,12 @@ void Engine::prepare_center() {
   lay = make_psi_layout(Lp.pb, Rp.pb, QN{N, two_s});
   plan = plan_heff(Lp, Rp, lay, I, tmp_budget);
   ex->tmp(std::max<int64_t>(1, plan.tmp_elems));
-  for (size_t k = 0; k < plan.stage1.size(); ++k)
-    prepared.emplace_back(pr->prepare(plan.stage1[k]), pr->prepare(plan.stage2[k]));
+  for (size_t k = 0; k < plan.stage1.size(); ++k) {
+    // stage 1 of a chunk is prepared before its stage 2 (runners may replay in handle order)
+    const int h1 = pr->prepare(plan.stage1[k]);
+    const int h2 = pr->prepare(plan.stage2[k]);
+    prepared.emplace_back(h1, h2);
+  }
   int64_t mx = 1;
   for (int d : lenv.at(center).basis.dim) mx = std::max<int64_t>(mx, d);
   for (int d : renv.at(center + 2).basis.dim) mx = std::max<int64_t>(mx, d);
@@ -381,6 +387,8 @@ void Engine::tune_tiled(uint64_t psi, uint64_t sig, int prec) {
 }
 
 DavResult Engine::davidson(const DavOpts& o) {
+  // QCDMRG_DAV_TRACE=1 prints every iteration to stderr
+  static const bool trace = std::getenv("QCDMRG_DAV_TRACE") && std::atoi(std::getenv("QCDMRG_DAV_TRACE")) != 0;
   DavResult R;
   const int64_t n = lay.size;
   if (n == 0) throw std::runtime_error("empty wavefunction");
@@ -405,6 +413,24 @@ DavResult Engine::davidson(const DavOpts& o) {
   try {
     int prec = o.policy ? 2 : o.precision;   // policy 1 starts in BF16
     mixed_planes = o.policy != 0;
+    // policy 1 after the BF16x3 phase: FP64 residual correction. Each outer
+    // check applies H once in FP64 to the normalised Ritz vector (energy and
+    // residual from that product); if the residual is above tol, the FP64 pair
+    // (x, H x) restarts the subspace and BF16x3 products expand it (inner
+    // iterations) until the mixed residual has fallen by REFINE_DROP, stalls, or
+    // REFINE_MAX inner products were spent; then the next FP64 check. The
+    // mixed products only have to resolve the correction, so their rounding
+    // error enters relative to the residual, not to H psi.
+    bool refine = false, w0_exact = false;
+    double outer_rn = 0.0;
+    int inner = 0;
+    constexpr double REFINE_DROP = 0.03;
+    const int REFINE_MAX = mmax - 2;   // inner products between checks (no restart in between)
+    // rounding floors of the residual: the reduced forms compute H psi to a
+    // relative accuracy of about 2^-9 (BF16) and 2^-17 (three-term split, its
+    // FP32 accumulation included), so their residuals cannot fall much below
+    // that fraction of |theta|
+    const double FLOOR_BF16 = 8.0 * std::ldexp(1.0, -9), FLOOR_X3 = 8.0 * std::ldexp(1.0, -17);
     auto apply = [&](uint64_t in, uint64_t out) {
       heff(in, out, st, prec);
       pr->sync(st);
@@ -447,18 +473,60 @@ DavResult Engine::davidson(const DavOpts& o) {
       R.energy = theta;
       int nprec = prec;
       phase_res.push_back(rn);
+      if (trace) std::fprintf(stderr, "davidson it %d prec %d refine %d m %d theta %.12f resid %.3e\n", it, prec,
+                              (int)refine, m, theta, rn);
+      bool check = false;   // FP64 outer check of the refinement
       if (o.policy) {
-        // a reduced-precision phase ends at its threshold, or when its
-        // residual stops falling (the rounding of its H psi sets a floor)
+        // a reduced-precision phase ends at its threshold, at its rounding
+        // floor, or when its residual has stopped falling (no 10 % drop in 8
+        // iterations)
         const size_t np = phase_res.size();
-        const bool stalled = np > 6 && rn > 0.5 * phase_res[np - 7];
-        if (prec == 2 && (rn < o.tau1 || stalled)) nprec = 3;
-        if (prec == 3 && (rn < o.tau2 || stalled)) nprec = 0;
-        if (prec != 0 && rn < o.tol) nprec = 0;
+        const bool stalled = np > 8 && rn > 0.9 * phase_res[np - 9];
+        const double at = std::fabs(theta);
+        if (!refine) {
+          if (prec == 2 && (rn < o.tau1 || rn < FLOOR_BF16 * at || stalled)) nprec = 3;
+          if (prec == 3 && (rn < o.tau2 || rn < FLOOR_X3 * at || stalled || rn < o.tol)) check = true;
+          if (prec == 2 && rn < o.tol) check = true;
+        } else if (inner > 0 && (rn < REFINE_DROP * outer_rn || rn < o.tol || stalled || inner >= REFINE_MAX)) {
+          check = true;
+        }
       }
+      if (check) {
+        if (!refine) R.energy_mixed = theta;
+        refine = true;
+        prec = 3;
+        phase_res.clear();
+        inner = 0;
+        double xn = std::sqrt(ex->dot(x, x, n));
+        ex->copy(V[0], x, n);
+        ex->scale(V[0], 1.0 / xn, n);
+        {
+          const int keep = prec;
+          prec = 0;
+          apply(V[0], W[0]);       // the FP64 product of the check
+          prec = keep;
+        }
+        m = 1;
+        Hs[0] = ex->dot(V[0], W[0], n);
+        w0_exact = true;
+        outer_rn = -1.0;           // set from the exact residual at the top of the loop
+        have_prev = false;
+        continue;
+      }
+      if (refine && outer_rn < 0.0) {
+        // first pass after a check: x = V0 and w = W0 = H x in FP64, so theta and
+        // rn are the exact Rayleigh quotient and residual
+        outer_rn = rn;
+        if (rn < o.tol) {
+          R.converged = true;
+          break;
+        }
+      }
+      if (refine) ++inner;
       if (nprec != prec) {  // restart from the Ritz vector with the new precision
         if (prec == 3) R.energy_mixed = theta;
         prec = nprec;
+        w0_exact = false;
         phase_res.clear();
         double xn = std::sqrt(ex->dot(x, x, n));
         ex->copy(V[0], x, n);
@@ -469,7 +537,7 @@ DavResult Engine::davidson(const DavOpts& o) {
         have_prev = false;
         continue;
       }
-      if (rn < o.tol && prec == (o.policy ? 0 : o.precision)) {
+      if (!o.policy && rn < o.tol) {
         R.converged = true;
         break;
       }
@@ -492,6 +560,7 @@ DavResult Engine::davidson(const DavOpts& o) {
         if (!(tn > 1e-14)) { R.converged = rn < o.tol; break; }
       }
       if (m == mmax) {  // restart: keep the Ritz vector and the previous one
+        w0_exact = false;
         double xn = std::sqrt(ex->dot(x, x, n));
         ex->copy(V[0], x, n);
         ex->scale(V[0], 1.0 / xn, n);
@@ -530,7 +599,10 @@ DavResult Engine::davidson(const DavOpts& o) {
       ex->scale(V[m], 1.0 / tn, n);
       apply(V[m], W[m]);
       for (int i = 0; i <= m; ++i) {
-        double v = ex->dot(V[i], W[m], n);
+        // after an FP64 check W0 = H V0 is exact: the coupling of V0 with a new
+        // direction is taken as V_m . (H V0) (H symmetric), whose error does not
+        // swamp the small true coupling the way V0 . (H V_m) in BF16x3 would
+        double v = (i == 0 && w0_exact) ? ex->dot(V[m], W[0], n) : ex->dot(V[i], W[m], n);
         Hs[(size_t)i * mmax + m] = v;
         Hs[(size_t)m * mmax + i] = v;
       }

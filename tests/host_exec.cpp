@@ -57,6 +57,10 @@ struct HostEx : Executor {
       bufs.erase(it);
     }
   }
+  int64_t size_of(uint64_t p) const {
+    auto it = bufs.find(p);
+    return it == bufs.end() ? 0 : (int64_t)it->second.size();
+  }
   uint64_t tmp(int64_t n) override {
     if (n > tmp_n) {
       if (tmp_base) release(tmp_base);
@@ -225,11 +229,31 @@ struct HostRunner : PreparedRunner {
   void sync(void*) override {}
   void zero_async(uint64_t p, int64_t n, void*) override { ex->zero(p, n); }
   int64_t bytes_allocated() const override { return ex->live; }
-  void prepare_tiled(const TiledPlan&, int) override {}
+  // The BF16 forms are emulated for the Davidson policy tests: the FP64 task
+  // lists of the centre (prepared in stage order), then every element of sigma perturbed by a relative
+  // amount uniform in [-u, u] (u = 2^-9 for BF16, 2^-18 for the split form),
+  // from a counter-based hash of the element and of the call.
+  int planes = 0;
+  uint64_t calls = 0;
+  void prepare_tiled(const TiledPlan&, int p) override { planes = p; }
   void set_tiled_items(const TiledPlan&) override {}
-  int tiled_planes() const override { return 0; }
+  int tiled_planes() const override { return planes; }
   double time_tiled(uint64_t, uint64_t, int, int) override { return 0.0; }
-  void run_tiled(uint64_t, uint64_t, void*, int) override { throw std::runtime_error("not here"); }
+  void run_tiled(uint64_t psi, uint64_t sig, void*, int prec) override {
+    for (const Launch& l : prepared) ex->exec(l, psi, sig);
+    const double u = prec == 2 ? std::ldexp(1.0, -9) : std::ldexp(1.0, -18);
+    double* s = reinterpret_cast<double*>(sig);
+    const int64_t n = ex->size_of(sig);
+    ++calls;
+    for (int64_t i = 0; i < n; ++i) {
+      uint64_t z = (uint64_t)i * 0x9E3779B97F4A7C15ull ^ (calls * 0xBF58476D1CE4E5B9ull);
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      z ^= z >> 31;
+      const double r = (double)(z >> 11) * (1.0 / 9007199254740992.0);   // [0, 1)
+      s[i] *= 1.0 + u * (2.0 * r - 1.0);
+    }
+  }
 };
 
 // value of element (r, c) of a view (scaled, possibly transposed, or a scaled identity)
@@ -388,6 +412,33 @@ int main(int argc, char** argv) {
       std::fclose(o2);
       return 0;
     }
+    if (argc >= 4 && std::string(argv[3]) == "davidson") {
+      // FP64 Davidson and the mixed policy (emulated BF16 forms) from the same start
+      const std::vector<double> psi0 = E.get_psi_host();
+      DavOpts o;
+      o.tol = 1e-8;
+      DavResult r0, r1;
+      if (std::getenv("HOST_EXEC_MIXED_FIRST")) {
+        o.policy = 1;
+        r1 = E.davidson(o);
+        E.set_psi_host(psi0);
+        o.policy = 0;
+        r0 = E.davidson(o);
+      } else {
+        r0 = E.davidson(o);
+        E.set_psi_host(psi0);
+        o.policy = 1;
+        r1 = E.davidson(o);
+      }
+      std::vector<double> out = {r0.energy, r1.energy, r0.resid, r1.resid, (double)r0.converged,
+                                 (double)r1.converged, (double)r0.hpsi[0], (double)r1.hpsi[0], (double)r1.hpsi[2],
+                                 (double)r1.hpsi[3], r1.energy_mixed};
+      FILE* o5 = std::fopen(argv[2], "wb");
+      if (!o5) throw std::runtime_error("cannot open output");
+      std::fwrite(out.data(), 8, out.size(), o5);
+      std::fclose(o5);
+      return 0;
+    }
     if (argc >= 4 && std::string(argv[3]) == "rdm2sweep") {
       const std::vector<double> g = E.rdm2_sweep();
       FILE* o4 = std::fopen(argv[2], "wb");
@@ -423,6 +474,7 @@ int main(int argc, char** argv) {
     cfg.kmax = 8;  // small: many split stage-2 items
     cfg.width = 128;
     std::vector<double> st = tiled_sigma(E.plan, E.lay, reinterpret_cast<const double*>(E.dpsi), cfg);
+    std::fprintf(stderr, "heff_flops=%.0f\n", E.plan.flops);
     FILE* o = std::fopen(argv[2], "wb");
     if (!o) throw std::runtime_error("cannot open output");
     std::fwrite(s64.data(), 8, s64.size(), o);

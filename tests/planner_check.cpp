@@ -339,7 +339,8 @@ int main(int argc, char** argv) {
   for (auto& kv : E.renv)
     for (int64_t n : kv.second.owned_n) env += 8 * n;
   std::printf("L=%d N=%d D=%d psi=%lld terms=%d gflop=%.4f launches=%lld fails=%d peak_gb=%.2f live_gb=%.2f env_gb=%.2f "
-              "heff_gb=%.3f\n", L, N, D, (long long)E.lay.size, E.plan.nterms, E.plan.flops / 1e9,
-              (long long)ex.launches_checked, fails, ex.peak / 1e9, ex.cur_live / 1e9, env / 1e9, E.plan.bytes / 1e9);
+              "heff_gb=%.3f env_tflop=%.2f\n", L, N, D, (long long)E.lay.size, E.plan.nterms, E.plan.flops / 1e9,
+              (long long)ex.launches_checked, fails, ex.peak / 1e9, ex.cur_live / 1e9, env / 1e9, E.plan.bytes / 1e9,
+              E.env_flops / 1e12);
   return fails ? 1 : 0;
 }

@@ -321,3 +321,24 @@ def test_su2_engine_sweeps_match_the_oracle(host_exec, tmp_path, L, N, two_s, D,
     if D == 400:
         e_fci, _ = FCI(h, V, N, two_s).ground_state(two_s=two_s)
         assert abs(E[-1] - e_fci) <= 1e-9
+
+
+@pytest.mark.parametrize("L,N,two_s,D,c", [(8, 8, 0, 20, 3), (12, 5, 1, 100, 5)])
+def test_mixed_davidson_policy_reaches_the_fp64_energy_with_few_fp64_products(host_exec, tmp_path, L, N, two_s,
+                                                                               D, c):
+    """The mixed policy (BF16 -> BF16x3 -> FP64 residual correction) against the FP64
+    Davidson from the same start, with the BF16 forms emulated on the host as the FP64
+    product plus a deterministic relative perturbation of each sigma element of their
+    rounding size (2^-9, 2^-18). Both converge to the residual 1e-8; the energies agree to
+    1e-10 and the mixed solve spends at most 8 FP64 products (one per outer check of the
+    refinement) where the FP64 solve spends all of its."""
+    from oracle.dmrgsu2 import MPSSU2
+    mps = MPSSU2.from_raw(q.random_mps_blocks(L, N, two_s, D, q.SYM_SU2, 5, c))
+    h, V = q.make_integrals(L, 11)
+    o = _run_su2(host_exec, tmp_path, mps, h, V, ["davidson"])
+    e64, emix, r64, rmix, c64, cmix, n64, nmix64, nbf16, nx3 = o[:10]
+    assert c64 == 1.0 and cmix == 1.0
+    assert r64 < 1e-8 and rmix < 1e-8
+    assert abs(emix - e64) < 1e-10
+    assert nmix64 <= 8 and n64 > 4 * nmix64
+    assert nbf16 + nx3 > 0
