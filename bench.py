@@ -1,11 +1,14 @@
-"""Benchmark of the two-site DMRG H_eff psi hot path (one JSON line on rank 0).
+"""Benchmark of the two-site DMRG hot path (one JSON line on rank 0).
 
-Default workload: U(1)xU(1) H_eff psi at the centre bond of a CAS(54,36)-shaped
-synthetic problem (L=36, N=54, 2Sz=0), random canonical MPS of bond dimension
-D, operator blocks built on the device by the library's renormalization.
+Default workload: the CAS(54,36)-shaped synthetic problem (L=36, N=54, S=0), SU(2)
+spin-adapted, bond dimension D = 2048 multiplets (the largest of the metric's bond
+dimensions whose environment fits one B300), random canonical MPS, environment built on
+the device by the library's renormalization. A step is one centre-bond Davidson solve
+with the mixed precision policy; the FP64 solve from the same start is its reference,
+and every H_eff psi form is also timed alone.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--D 1024] [--precision fp64]
+                  [--D 2048] [--symmetry su2|u1] [--sweep] [--batched] [--adjoint]
 Under torchrun every rank runs an independent replica (the path does not
 shard across GPUs); the line reports the whole-job throughput.
 """
@@ -29,10 +32,10 @@ METRIC = ("H·ψ TFLOP/s & sweep s, CAS(54,36)-shape D=4096: mixed vs FP64, "
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--D", type=int, default=1024)
+    ap.add_argument("--D", type=int, default=2048)
     ap.add_argument("--symmetry", default="su2", choices=["su2", "u1"],
                     help="su2: spin-adapted (D counts SU(2) multiplets, the paper's D_SU(2)); u1: U(1)xU(1)")
     ap.add_argument("--L", type=int, default=36)
@@ -59,6 +62,9 @@ def parse():
     ap.add_argument("--sum-gemm", type=int, default=0, choices=[-1, 0, 1],
                     help="operator sums of the renormalization side as GEMMs (1), block by block (-1), "
                          "or as GEMMs only with the switch (0)")
+    ap.add_argument("--products", default=None, choices=["fp64", "tf32", "bf16", "bf16x3"],
+                    help="only time single H_eff psi products of one form (the command the ncu "
+                         "captures under profiles/ run); prints a short line")
     ap.add_argument("--profile", action="store_true",
                     help="bracket the timed region with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     return ap.parse_args()
@@ -112,12 +118,11 @@ class Clocks:
                 "samples": len(sm)}
 
 
-# DRAM bytes (read + write) of one H_eff psi on the tiled tensor-core kernel,
-# from one ncu capture of both stage launches (dram__bytes_read.sum +
-# dram__bytes_write.sum), keyed by (form, L, N, D); the capture and its command
-# are summarised in profiles/tiled_gemm_bf16_u1_L36_N54_D1024.md. A key that is
-# absent reports null.
-DRAM_TRAFFIC = {("bf16", 36, 54, 1024): 2.58e9 + 1.64e9 + 3.52e9 + 0.0024e9}
+# DRAM bytes (read + write) of one H_eff psi of a form, from ncu captures
+# (dram__bytes_read.sum + dram__bytes_write.sum over the launches of one
+# product), keyed by (form, symmetry, L, N, D); each capture and its command are
+# summarised under profiles/. A key that is absent reports null.
+DRAM_TRAFFIC = {}
 
 
 def measured_peaks():
@@ -149,52 +154,45 @@ def fp64_peak_tflops(torch):
     return 2.0 * n ** 3 / best / 1e12
 
 
-def cpu_sample():
-    """Oracle H_eff psi on the L=10, N=10, D=64 U(1) workload (centre bond)."""
-    import numpy as np
+# CPU baseline: the SU(2) oracle's H_eff psi at the CAS(54,36) shape (L=36, N=54,
+# S=0) with a bond dimension the dense oracle handles (its environment build is
+# about a minute and excluded from the timing)
+CPU_D = 64
+
+
+def cpu_sample(D=CPU_D):
+    """The oracle's H_eff at the centre of the SU(2) CAS(54,36)-shaped workload at bond
+    dimension D (environment built here, outside any timing)."""
     import qcinputs as q
-    from oracle.mpsu1 import MPSU1
-    from oracle.dmrgu1 import DMRGU1
-    w = q.workload("u1_L10_N10_D64")
-    L, N = w["L"], w["N"]
-    h, V = q.make_integrals(L, w["int_seed"])
-    m = MPSU1.from_raw(q.random_mps_blocks(L, N, 0, w["D"], q.SYM_U1, w["mps_seed"], L // 2 - 1))
-    d = DMRGU1(h, V, N, 0)
-    heff = d.heff_at_center(m)
-    from oracle.dmrgu1 import to_mat
-    x = to_mat(m.psi)
-    return m, h, V, heff, x
+    from oracle.dmrgsu2 import DMRGSU2, MPSSU2
+    L, N = 36, 54
+    h, V = q.make_integrals(L, q.integrals.BASE_SEED + 2)
+    m = MPSSU2.from_raw(q.random_mps_blocks(L, N, 0, D, q.SYM_SU2, q.integrals.BASE_SEED + 1002, L // 2 - 1))
+    heff = DMRGSU2(h, V, N, 0).heff_at_center(m)
+    return m, h, V, heff
 
 
-def time_oracle(reps):
-    m, h, V, heff, x = cpu_sample()
-    ts = []
-    for _ in range(reps):
-        t0 = time.perf_counter()
-        heff.apply_mat(x)
-        ts.append(time.perf_counter() - t0)
-    return m, h, V, ts
-
-
-def time_oracle_for(seconds, min_reps=4):
-    """Oracle H_eff psi repeated until about `seconds` of CPU time (first repetition untimed)."""
-    m, h, V, heff, x = cpu_sample()
+def time_oracle_for(seconds, min_reps=3, sample=None):
+    """Oracle H_eff psi repeated until about `seconds` of CPU time (first repetition untimed).
+    Returns (mps, h, V, times, flops by the oracle's own sector count)."""
+    m, h, V, heff = sample or cpu_sample()
+    heff.apply_mat(m.psi)
     ts, t_all = [], time.perf_counter()
     while len(ts) < min_reps or time.perf_counter() - t_all < seconds:
         t0 = time.perf_counter()
-        heff.apply_mat(x)
+        heff.apply_mat(m.psi)
         ts.append(time.perf_counter() - t0)
-    return m, h, V, ts
+    return m, h, V, ts, heff.algorithmic_flops()
 
 
-def sample_flops(m, h, V):
-    """Algorithmic flops of the sample as counted by the library's task list."""
+def library_flops(m, h, V):
+    """The library's algorithmic count of the same product (cross-check of the oracle's)."""
     import paper_2603_28648_b300 as qd
-    from oracle.mpsu1 import export_abi
-    ctx = qd.Context()
+    from oracle.dmrgsu2 import export_abi_su2
+    ctx = qd.Context(symmetry=qd.SU2)
     ctx.load_integrals(h, V)
-    ctx.set_target(m.N, m.two_sz)
-    ctx.import_mps(m.L, m.center, *export_abi(m))
+    ctx.set_target(m.N, m.two_s)
+    ctx.import_mps(m.L, m.center, *export_abi_su2(m))
     ctx.build_env()
     f = ctx.stats()["heff_flops"]
     ctx.close()
@@ -221,33 +219,47 @@ def cores():
 
 
 def run_reference(args, rank, world):
+    """The oracle (plain FP64 numpy) timed on this host's cores on a bounded sample of the
+    workload: its H_eff psi at the centre of the SU(2) CAS(54,36)-shaped problem at
+    D = 64 multiplets, environment excluded; flops by the oracle's own count."""
     if rank != 0:
         return
-    reps = args.steps + args.warmup
-    m, h, V, ts = time_oracle(reps)
-    t = statistics.mean(ts[args.warmup:]) if len(ts) > args.warmup else statistics.mean(ts)
-    try:
-        flops = sample_flops(m, h, V)
-    except Exception:
-        flops = None
-    val = flops / t / 1e12 if flops else None
+    sample = cpu_sample()
+    m, h, V, heff = sample
+    for _ in range(args.warmup):
+        heff.apply_mat(m.psi)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        heff.apply_mat(m.psi)
+        ts.append(time.perf_counter() - t0)
+    t = statistics.mean(ts)
+    flops = heff.algorithmic_flops()
+    val = flops / t / 1e12
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "u1_L10_N10_D64 centre-bond H_eff psi (oracle sample)",
-                   "note": "oracle: dense FP64 numpy, H_eff psi with environments built",
-                   "flops": "algorithmic count of the library's task list for the same product "
-                            "(qcdmrg_stats.heff_flops, planned outside the timed region)"},
+        "config": {"workload": f"su2_L36_N54_S0_D{CPU_D} centre-bond H_eff psi (oracle sample)",
+                   "note": "oracle: dense FP64 numpy, reduced SU(2) operators, environment built outside "
+                           "the timing",
+                   "flops": "the oracle's own count: 2mnk over the nonzero quantum-number sector blocks "
+                            "of every term"},
         "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": cores(), "kind": "oracle",
-                         "sample": "U(1) L=10 N=10 D=64 centre-bond H_eff psi (environment excluded)"},
+                         "sample": f"SU(2) L=36 N=54 S=0 D={CPU_D} centre-bond H_eff psi (environment "
+                                   f"excluded), {args.steps} timed products"},
         "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
 def run_ours(args, rank, world, local):
+    """The default line. A step is one centre-bond Davidson solve (residual 1e-6) with the
+    mixed precision policy (BF16 and BF16x3 H_eff psi with FP64 residual correction) from a
+    fixed start vector; the same solve with every product in FP64 is its reference (energy
+    and time). Each H_eff psi form is also timed alone (single products), which gives the
+    rooflines of the kernels the step is made of."""
     import numpy as np
     import torch
     import qcinputs as q
@@ -259,8 +271,9 @@ def run_ours(args, rank, world, local):
         dist.init_process_group("nccl")
 
     L, N, D = args.L, args.N, args.D
+    su2 = args.symmetry == "su2"
     h, V = q.make_integrals(L, q.integrals.BASE_SEED + 2)
-    sym = qd.SU2 if args.symmetry == "su2" else qd.U1
+    sym = qd.SU2 if su2 else qd.U1
     ctx = qd.Context(device=local, symmetry=sym, hbm_budget_gb=args.hbm_budget, pair_switch=args.pair_switch,
                      sum_gemm=args.sum_gemm)
     ctx.load_integrals(h, V)
@@ -278,163 +291,248 @@ def run_ours(args, rank, world, local):
     sig = torch.empty_like(psi)
     stream = torch.cuda.current_stream()
 
-    head = qd.PRECISIONS[args.precision]
-
     def step(prec):
         ctx.apply_heff_dev(psi.data_ptr(), sig.data_ptr(), stream.cuda_stream, prec)
 
-    def timed(prec, steps, clocks=None, profile=False):
+    def timed_products(prec, steps):
         for _ in range(args.warmup):
             step(prec)
         torch.cuda.synchronize()
-        if clocks:
-            clocks.start()
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        if profile:
-            torch.cuda.profiler.start()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(steps):
             step(prec)
         e1.record(stream)
         torch.cuda.synchronize()
-        if profile:
-            torch.cuda.profiler.stop()
-        if dist:
-            dist.barrier()
         ctx.check_device()
-        return e0.elapsed_time(e1) / 1e3
+        return e0.elapsed_time(e1) / 1e3 / steps
 
+    # --- single products of every form (FP64 first: the reference of the sigma errors)
     forms = {}
-    energies = {}
-    step(0)  # FP64 reference product for the per-form sigma errors
+    step(0)
     torch.cuda.synchronize()
     sig64 = sig.clone()
-    errs = {}
+    e_fp64 = float(torch.dot(psi, sig64).item())
     for name, prec in qd.PRECISIONS.items():
-        if name == args.precision:
-            continue
-        t = timed(prec, max(2, args.steps // 2))
-        energies[name] = float(torch.dot(psi, sig).item())
-        errs[name] = float((torch.linalg.norm(sig - sig64) / torch.linalg.norm(sig64)).item())
-        forms[name] = {"tflops": flops / (t / max(2, args.steps // 2)) / 1e12,
-                       "ms_per_step": t / max(2, args.steps // 2) * 1e3}
+        t = timed_products(prec, 2 if name in ("fp64", "tf32") else max(2, args.steps))
+        forms[name] = {"tflops": flops / t / 1e12, "ms_per_product": t * 1e3,
+                       "sigma_rel_err_vs_fp64": float((torch.linalg.norm(sig - sig64) /
+                                                       torch.linalg.norm(sig64)).item()),
+                       "psi_h_psi_minus_fp64": float(torch.dot(psi, sig).item()) - e_fp64}
+    for f in forms.values():
+        f["speedup_vs_fp64"] = forms["fp64"]["ms_per_product"] / f["ms_per_product"]
+
+    # --- start vector of the solves: the random MPS's centre, brought to a residual of
+    # 1e-3 by a mixed solve (setup, untimed), so that the FP64 reference solve stays short
+    ctx.davidson(allow_notconv=True, policy=1, tol=1e-3, max_iter=args.max_iter)
+    psi0 = ctx.psi()
+
+    def solve(policy):
+        """One Davidson solve from psi0; device time by events on the legacy default stream
+        (the library's stream synchronises with it; the call returns after its last sync)."""
+        ctx.set_psi(psi0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        kw = dict(policy=1) if policy == "mixed" else dict(policy=0, precision=qd.FP64)
+        e, r, it = ctx.davidson(allow_notconv=True, tol=1e-6, max_iter=args.max_iter, **kw)
+        e1.record()
+        torch.cuda.synchronize()
+        s2 = ctx.stats()
+        return {"energy": e, "residual": r, "iterations": it, "seconds": e0.elapsed_time(e1) / 1e3,
+                "hpsi": dict(zip(["fp64", "tf32", "bf16", "bf16x3"], s2["dav_hpsi"])),
+                "energy_before_fp64_correction": s2["dav_energy_mixed"]}
+
+    # --- the timed steps: mixed solves; then the FP64 reference solve from the same start
+    for _ in range(args.warmup):
+        solve("mixed")
     clocks = Clocks(local)
-    elapsed = timed(head, args.steps, clocks, args.profile)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    runs = [solve("mixed") for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     clk = clocks.stop()
-    energies[args.precision] = float(torch.dot(psi, sig).item())
-    errs[args.precision] = float((torch.linalg.norm(sig - sig64) / torch.linalg.norm(sig64)).item())
-    forms[args.precision] = {"tflops": flops / (elapsed / args.steps) / 1e12,
-                             "ms_per_step": elapsed / args.steps * 1e3}
-    for name in forms:
-        forms[name]["energy_minus_fp64"] = energies[name] - energies["fp64"]
-        forms[name]["sigma_rel_err_vs_fp64"] = errs[name]
-        forms[name]["speedup_vs_fp64"] = forms["fp64"]["ms_per_step"] / forms[name]["ms_per_step"]
-    # end to end through the public API: pinned host psi -> device, H psi, sigma -> host
-    hpsi = psi.cpu().pin_memory()
-    hsig = torch.empty_like(hpsi).pin_memory()
+    ref = solve("fp64")
+    mixed = runs[-1]
+    per_step = statistics.mean(r["seconds"] for r in runs)
+    n_prod = {k: mixed["hpsi"][k] for k in mixed["hpsi"]}
+    step_flops = flops * sum(n_prod.values())
+    # end to end through the public API with host buffers: psi0 uploaded (qcdmrg_set_psi), the
+    # mixed solve, the solution downloaded (qcdmrg_get_psi), wall clock
+    t0 = time.perf_counter()
+    ctx.set_psi(psi0)
+    e_e2e, _, _ = ctx.davidson(allow_notconv=True, policy=1, tol=1e-6, max_iter=args.max_iter)
+    out = ctx.psi()
+    e2e_s = time.perf_counter() - t0
+    # truncation, renormalization and preparation of the next centre after the solve
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        psi.copy_(hpsi, non_blocking=True)
-        step(head)
-        hsig.copy_(sig, non_blocking=True)
-    e1.record(stream)
+    e0.record()
+    trunc_err = ctx.truncate(D, +1)
+    e1.record()
     torch.cuda.synchronize()
-    e2e_t = e0.elapsed_time(e1) / 1e3
-    energy = energies[args.precision]
+    trunc_s = e0.elapsed_time(e1) / 1e3
     if dist:
-        elapsed, e2e_t = max_over_ranks([elapsed, e2e_t], dist, "cuda")
-    peak = fp64_peak_tflops(torch)
-    per_step = elapsed / args.steps
-    value = replica_throughput(flops, per_step, world)
-    e2e_val = replica_throughput(flops, e2e_t / args.steps, world)
+        per_step, e2e_s = max_over_ranks([per_step, e2e_s], dist, "cuda")
+    value = replica_throughput(step_flops, per_step, world)
+    e2e_val = replica_throughput(step_flops, e2e_s, world)
+    peak64 = fp64_peak_tflops(torch)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
-    cpu = None
-    if not args.no_cpu_baseline:
-        m, hh, VV, ts = time_oracle_for(10.0)
-        t_cpu = statistics.mean(ts[1:])
-        f_cpu = sample_flops(m, hh, VV)
-        cpu = {"value": f_cpu / t_cpu / 1e12, "unit": "TFLOP/s", "cores": cores(), "kind": "oracle",
-               "sample": "U(1) L=10 N=10 D=64 centre-bond H_eff psi, oracle dense FP64 "
-                         f"(environment build excluded), {len(ts) - 1} timed repetitions, "
-                         f"{sum(ts[1:]):.1f} s of CPU work"}
-    st2 = ctx.stats()
-    tile = {"stage2_kmax": st2["tile_kmax"], "stage1_width": st2["tile_width"], "autotuner_runs": st2["tunes"],
-            "autotuner_s": st2["tune_seconds"]}
     pk = measured_peaks()
-    # algorithmic minimum traffic of one product in each form's operand type:
-    # every referenced operator element once (8 B FP64, 4 B TF32, 2 B BF16,
-    # 6 B for the three BF16 planes), psi and sigma (FP64 in every form)
+    # algorithmic bytes of one product in each form's operand type: every referenced
+    # operator element once (8 B FP64, 4 B TF32, 2 B BF16, 6 B for three BF16 planes),
+    # psi and sigma in FP64
     nelem = st["heff_bytes"] / 8.0
     npsi = 2.0 * st["psi_size"]
     esize = {"fp64": 8, "tf32": 4, "bf16": 2, "bf16x3": 6}
-    form_bytes = {k: (nelem - npsi) * e + 8 * npsi for k, e in esize.items()}
-    tensor_ratio = {"fp64": None, "bf16": 1.0, "tf32": 1.1 / 2.25, "bf16x3": 1.0 / 6.0}
+    ridge = pk["bf16"] / pk["hbm"]
     for name, f in forms.items():
-        t_s = f["ms_per_step"] / 1e3
-        f["algorithmic_bytes"] = form_bytes[name]
-        f["hbm_gbs_algorithmic"] = form_bytes[name] / t_s / 1e9
-        f["hbm_frac"] = f["hbm_gbs_algorithmic"] / pk["hbm"]
-        r = tensor_ratio[name]
-        f["compute_frac"] = f["tflops"] / (pk["bf16"] * r if r else peak)
-    # the dominant kernel (the grouped block GEMM, every launch of the step) is
-    # bound by HBM: flops / algorithmic bytes is below the ridge point of every
-    # tensor form, so its roofline is the measured copy bandwidth
-    nbytes = form_bytes[args.precision]
-    achieved = nbytes / per_step / 1e9
-    traffic = DRAM_TRAFFIC.get((args.precision, L, N, D))
-    roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm"], "unit": "GB/s",
-            "frac": achieved / pk["hbm"], "traffic": traffic,
-            "algorithmic_bytes_per_step": nbytes,
-            "intensity_flop_per_byte": flops / nbytes,
-            "peak_source": f"{pk['source']} copy bandwidth (of {pk['source']})",
-            "traffic_note": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the stage-1 and stage-2 "
-                             "launches of one product (profiles/)") if traffic else
-                            "null: no DRAM counter capture of this kernel build at this size",
-            "compute_frac": forms[args.precision]["compute_frac"]}
-    if args.precision in ("bf16", "bf16x3"):
-        launches_per_step = 3
-        launches_note = ("per step: psi tiling, stage-1 and stage-2 launches of the bulk-copy-fed "
-                         "tcgen05 kernel (plus one cudaMemsetAsync of sigma)")
-    else:
-        launches_per_step = int(st["nlaunch"])
-        launches_note = ("per step: the grouped GEMM launches of every task-list chunk "
-                         "(plus one cudaMemsetAsync of sigma)")
+        b = (nelem - npsi) * esize[name] + 8 * npsi
+        t_s = f["ms_per_product"] / 1e3
+        f["algorithmic_bytes"] = b
+        f["intensity_flop_per_byte"] = flops / b
+        f["hbm_frac"] = b / t_s / 1e9 / pk["hbm"]
+        if name == "fp64":
+            f["fp64_frac_of_dgemm"] = f["tflops"] / peak64
+        else:
+            mult = 6.0 if name == "bf16x3" else 1.0
+            peak = pk["bf16"] * (1.0 if name != "tf32" else 1.1 / 2.25)
+            f["tensor_frac"] = mult * f["tflops"] / peak
+    # the kernel that dominates the step: device time of its products in the mixed solve
+    share = {"seg_gemm_f64 (FP64 products)": n_prod["fp64"] * forms["fp64"]["ms_per_product"],
+             "tiled_gemm (BF16 and BF16x3 products)": n_prod["bf16"] * forms["bf16"]["ms_per_product"] +
+             n_prod["bf16x3"] * forms["bf16x3"]["ms_per_product"]}
+    dominant = max(share, key=share.get)
+    tot_ms = per_step * 1e3
+    roof_f64 = {"bound": "alu", "achieved": forms["fp64"]["tflops"], "peak": peak64, "unit": "TFLOP/s",
+                "frac": forms["fp64"]["tflops"] / peak64,
+                "traffic": DRAM_TRAFFIC.get(("fp64", args.symmetry, L, N, D)),
+                "peak_source": "cuBLAS DGEMM 4096^3 measured in this run (no FP64 figure in "
+                               "MEASURED_PEAKS.json; nominal 1.25 TFLOP/s)",
+                "algorithmic_bytes_per_launch_set": forms["fp64"]["algorithmic_bytes"]}
+    tform = "bf16x3" if n_prod["bf16x3"] * forms["bf16x3"]["ms_per_product"] >= \
+        n_prod["bf16"] * forms["bf16"]["ms_per_product"] else "bf16"
+    tf = forms[tform]
+    mult = 6.0 if tform == "bf16x3" else 1.0
+    tbound = "tensor" if tf["intensity_flop_per_byte"] * mult > ridge else "hbm"
+    roof_tc = {"bound": tbound, "form": tform, "unit": "TFLOP/s" if tbound == "tensor" else "GB/s",
+               "achieved": mult * tf["tflops"] if tbound == "tensor" else
+               tf["algorithmic_bytes"] / (tf["ms_per_product"] / 1e3) / 1e9,
+               "peak": pk["bf16"] if tbound == "tensor" else pk["hbm"],
+               "traffic": DRAM_TRAFFIC.get((tform, args.symmetry, L, N, D)),
+               "intensity_flop_per_byte": mult * tf["intensity_flop_per_byte"], "ridge_flop_per_byte": ridge,
+               "peak_source": f"{pk['source']} bf16 burst / copy bandwidth (of {pk['source']})"}
+    roof_tc["frac"] = roof_tc["achieved"] / roof_tc["peak"]
+    roof = dict(roof_f64 if dominant.startswith("seg_gemm_f64") else roof_tc)
+    roof["kernel"] = dominant
+    roof["time_share_of_step"] = {k: v / tot_ms for k, v in share.items()}
+    roof["other_kernel"] = roof_tc if dominant.startswith("seg_gemm_f64") else roof_f64
+    cpu = None
+    if not args.no_cpu_baseline:
+        m, hh, VV, ts, f_orc = time_oracle_for(10.0)
+        t_cpu = statistics.mean(ts[1:])
+        f_lib = library_flops(m, hh, VV)
+        cpu = {"value": f_orc / t_cpu / 1e12, "unit": "TFLOP/s", "cores": cores(), "kind": "oracle",
+               "sample": f"SU(2) L=36 N=54 S=0 D={CPU_D} centre-bond H_eff psi, oracle dense FP64 numpy "
+                         f"(environment build excluded), {len(ts) - 1} timed products, "
+                         f"{sum(ts[1:]):.1f} s of CPU work",
+               "flops_oracle_count": f_orc, "flops_library_count": f_lib,
+               "flop_counts_note": "the oracle counts nonzero (n, 2S) sector blocks of each term, the "
+                                   "library its site sub-blocks (x, channel) and excludes identity "
+                                   "references; both are reported"}
+    st2 = ctx.stats()
+    tile = {"stage2_kmax": st2["tile_kmax"], "stage1_width": st2["tile_width"], "autotuner_runs": st2["tunes"],
+            "autotuner_s": st2["tune_seconds"]}
+    sym_name = "SU(2)" if su2 else "U(1)xU(1)"
+    wl = f"su2_L{L}_N{N}_S0_D{D}" if su2 else f"u1_L{L}_N{N}_Sz0_D{D}"
+    dE = mixed["energy"] - ref["energy"]
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": args.precision.replace("fp", "f"), "data": "synthetic",
-        "config": {"workload": (f"su2_L{L}_N{N}_S0_D{D} centre-bond H_eff psi" if args.symmetry == "su2"
-                                else f"u1_L{L}_N{N}_Sz0_D{D} centre-bond H_eff psi"),
-                   "symmetry": "SU(2)" if args.symmetry == "su2" else "U(1)xU(1)",
-                   "precision": args.precision, "L": L, "N": N, "D": D,
-                   "psi_size": st["psi_size"], "terms": st["nterms"],
-                   "heff_gflop": flops / 1e9, "env_build_s": env_s,
-                   "env_build_tflops": st["env_flops"] / env_s / 1e12,
-                   "l2": "operator blocks read per step exceed L2 (no flush needed)",
-                   "device_bytes": st2["device_bytes"], "energy_psi_h_psi": energy, "tile": tile,
-                   "forms": forms, "fp64_peak_tflops_measured": peak,
+        "dtype": "bf16+f64", "data": "synthetic",
+        "config": {"workload": f"{wl} centre-bond Davidson solve, mixed precision policy",
+                   "step": "one Davidson solve at the centre bond from a fixed start (residual 1e-6): "
+                           "BF16 and BF16x3 H_eff psi with FP64 residual correction; value = algorithmic "
+                           "H_eff psi flops of its products / its device time",
+                   "symmetry": sym_name, "L": L, "N": N, "S": 0, "D": D,
+                   "psi_size": st["psi_size"], "terms": st["nterms"], "heff_gflop": flops / 1e9,
+                   "env_build_s": env_s, "env_build_tflops": st["env_flops"] / env_s / 1e12,
+                   "device_bytes": st2["device_bytes"],
+                   "mixed_solve": mixed, "mixed_solve_seconds_all_steps": [r["seconds"] for r in runs],
+                   "fp64_solve": ref,
+                   "energy_mixed_minus_fp64": dE, "same_energy_err": abs(dE) <= 1e-6,
+                   "speedup_vs_fp64_solve": ref["seconds"] / per_step,
+                   "products": forms,
+                   "truncate_renormalize_s": trunc_s, "truncation_error": trunc_err,
+                   "sweep_s_projection": {"mixed": 2 * (L - 2) * (per_step + trunc_s),
+                                          "fp64": 2 * (L - 2) * (ref["seconds"] + trunc_s),
+                                          "note": "2(L-2) two-site steps x (centre solve + truncation step) "
+                                                  "measured here; measured sweeps come from bench.py --sweep"},
+                   "l2": "operator blocks read per product exceed L2 (no flush needed)",
+                   "tile": tile, "fp64_dgemm_tflops_measured": peak64,
                    "pair_switch": args.pair_switch, "sum_gemm": args.sum_gemm, "hbm_budget_gb": args.hbm_budget,
                    "parallelism": f"replicas{world}"},
         "roofline": roof,
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_val, "unit": "TFLOP/s", "h2d_bytes_per_step": int(psi.numel() * 8),
-                "d2h_bytes_per_step": int(sig.numel() * 8)},
-        "gpu_launches": launches_per_step * args.steps,
-        "gpu_launches_note": launches_note,
+        "e2e": {"value": e2e_val, "unit": "TFLOP/s", "h2d_bytes_per_step": int(psi0.size * 8),
+                "d2h_bytes_per_step": int(out.size * 8), "energy": e_e2e,
+                "note": "qcdmrg_set_psi from host memory, qcdmrg_davidson, qcdmrg_get_psi to host memory; "
+                        "wall clock"},
+        "gpu_launches": int(3 * (n_prod["bf16"] + n_prod["bf16x3"]) + st["nlaunch"] * n_prod["fp64"]) *
+        args.steps,
+        "gpu_launches_note": "per solve: 3 launches per BF16/BF16x3 product (psi tiling, stage 1, stage 2), "
+                             "the task-list launches of each FP64 product; Davidson vector kernels not counted",
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def run_products(args, rank, world, local):
+    """W untimed and K timed single H_eff psi products of one form at the centre of the
+    default workload (no solves, no CPU baseline): the small command ncu profiles."""
+    import torch
+    import qcinputs as q
+    import paper_2603_28648_b300 as qd
+    torch.cuda.set_device(local)
+    L, N, D = args.L, args.N, args.D
+    h, V = q.make_integrals(L, q.integrals.BASE_SEED + 2)
+    ctx = qd.Context(device=local, symmetry=qd.SU2 if args.symmetry == "su2" else qd.U1,
+                     hbm_budget_gb=args.hbm_budget)
+    ctx.load_integrals(h, V)
+    ctx.set_target(N, 0)
+    ctx.init_mps(D, q.integrals.BASE_SEED + 1002, L // 2 - 1)
+    ctx.build_env()
+    psi = torch.tensor(ctx.psi(), device="cuda")
+    sig = torch.empty_like(psi)
+    stream = torch.cuda.current_stream()
+    prec = qd.PRECISIONS[args.products]
+    for _ in range(args.warmup):
+        ctx.apply_heff_dev(psi.data_ptr(), sig.data_ptr(), stream.cuda_stream, prec)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.apply_heff_dev(psi.data_ptr(), sig.data_ptr(), stream.cuda_stream, prec)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ctx.check_device()
+    t = e0.elapsed_time(e1) / 1e3 / args.steps
+    st = ctx.stats()
+    print(json.dumps({"mode": "products", "form": args.products, "symmetry": args.symmetry, "L": L, "N": N, "D": D,
+                      "ms_per_product": t * 1e3, "tflops": st["heff_flops"] / t / 1e12,
+                      "heff_gflop": st["heff_flops"] / 1e9, "nlaunch": st["nlaunch"],
+                      "f64_tiles": st["f64_tiles"], "f64_split_tiles": st["f64_split_tiles"]}), flush=True)
+    ctx.close()
 
 
 def run_batched(args, rank, world, local):
@@ -533,8 +631,8 @@ def run_sweep(args, rank, world, local):
     order = [+1] * (L - 2 - c0) + [-1] * (L - 2) + [+1] * c0
     out = {}
     for name, kw in (("fp64", dict(policy=0, precision=qd.FP64)), ("mixed", dict(policy=1))):
-        ctx = qd.Context(device=local, hbm_budget_gb=args.hbm_budget, pair_switch=args.pair_switch,
-                     sum_gemm=args.sum_gemm)
+        ctx = qd.Context(device=local, symmetry=qd.SU2 if args.symmetry == "su2" else qd.U1,
+                         hbm_budget_gb=args.hbm_budget, pair_switch=args.pair_switch, sum_gemm=args.sum_gemm)
         ctx.load_integrals(h, V)
         ctx.set_target(N, 0)
         ctx.init_mps(D, q.integrals.BASE_SEED + 1002, c0)
@@ -573,7 +671,8 @@ def run_sweep(args, rank, world, local):
         "metric": f"sweep seconds, one two-site sweep (2(L-2) = {2 * (L - 2)} steps) at L={L}",
         "value": m["wall_s"] if m["complete"] else None, "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 0,
         "higher_is_better": False, "dtype": "mixed", "data": "synthetic",
-        "config": {"workload": f"u1_L{L}_N{N}_Sz0_D{D} sweep from a random MPS, centre start",
+        "config": {"workload": (f"su2_L{L}_N{N}_S0_D{D}" if args.symmetry == "su2" else f"u1_L{L}_N{N}_Sz0_D{D}") +
+                   " sweep from a random MPS, centre start",
                    "davidson": {"tol": 1e-6, "max_iter": args.max_iter}, "budget_s": args.sweep_budget,
                    "pair_switch": args.pair_switch, "sum_gemm": args.sum_gemm, "hbm_budget_gb": args.hbm_budget,
                    "fp64": f, "mixed": m,
@@ -633,6 +732,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", 0))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.products:
+        if rank == 0:
+            run_products(args, rank, world, local)
     elif args.batched:
         if rank == 0:
             run_batched(args, rank, world, local)

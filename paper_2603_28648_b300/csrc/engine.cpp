@@ -981,7 +981,7 @@ double Engine::expect(const std::vector<CenterTerm>& terms) {
 }
 
 std::vector<double> Engine::rdm1() {
-  if (su2) throw StateError("density matrices are measured with the U(1) operators; not available with SU(2)");
+  if (su2) return rdm1_su2();
   // At the centre (L-2, L-1) the left enlarged block L' holds the normal
   // operators a+_k a_l of every spin-orbital of sites 0..L-2, and the right
   // enlarged block is the last site alone, so every E_pq is a product of
@@ -1044,6 +1044,48 @@ std::vector<double> Engine::rdm1() {
       }
       if (!t.empty()) g[(size_t)p * L + q] = expect(t) / nrm;
     }
+  return g;
+}
+
+std::vector<double> Engine::rdm1_su2() {
+  // SU(2): gamma_pq = <E_pq> with E_pq = -sqrt(2) [c_p x d_q]^0. At the centre
+  // (L-2, L-1) the left enlarged block holds B^0_pq = [c_p x d_q]^0 for p <= q
+  // of its orbitals and c_p; the right enlarged block is the last orbital:
+  //   p <= q < L-1 : -sqrt(2) [B^0_pq x 1]^0
+  //   p < L-1 = q  : -sqrt(2) [c_p x d_q]^0, d_q the adjoint tensor of c_q on the right
+  //   p = q = L-1  : N - sum of the other diagonal elements (Tr gamma = N)
+  // gamma is symmetric (real state, E_qp = E_pq^+).
+  if (center != L - 2) throw StateError("the one-particle density matrix needs the centre at (L-2, L-1)");
+  const double nrm = ex->dot(dpsi, dpsi, lay.size);
+  auto get = [](const Enlarged& E, Key k) -> const OpView* {
+    auto it = E.ops.find(k);
+    if (it == E.ops.end() || it->second.empty()) return nullptr;
+    return &it->second;
+  };
+  const OpView* IR = get(Rp, Key(F_I));
+  const int last = L - 1;
+  const double sq2 = std::sqrt(2.0);
+  std::vector<double> g((size_t)L * L, 0.0);
+  for (int p = 0; p < last; ++p)
+    for (int q = p; q < L; ++q) {
+      CenterTerm t{nullptr, false, nullptr, false, -sq2};
+      if (q < last) {
+        t.L = get(Lp, Key(F_B, p, q, 0));
+        t.R = IR;
+        t.k2 = 0;
+      } else {
+        t.L = get(Lp, Key(F_C, p));
+        t.R = get(Rp, Key(F_C, q));
+        t.RT = true;
+        t.k2 = 1;
+      }
+      if (!t.L || !t.R) continue;
+      const double v = expect({t}) / nrm;
+      g[(size_t)p * L + q] = g[(size_t)q * L + p] = v;
+    }
+  double tr = 0.0;
+  for (int p = 0; p < last; ++p) tr += g[(size_t)p * L + p];
+  g[(size_t)last * L + last] = N - tr;
   return g;
 }
 

@@ -109,6 +109,7 @@ struct Engine {
   // spin-summed one-particle density matrix gamma_pq = <E_pq> of the
   // normalised state; needs the centre at (L-2, L-1)
   std::vector<double> rdm1();
+  std::vector<double> rdm1_su2();   // the same for an SU(2) state (reduced operators)
   // spin-summed two-particle density matrix Gamma_pqrs = <E_pq E_rs - delta_qr E_ps>
   // of the normalised state, averaged over the 8 permutations that leave (pq|rs)
   // invariant; by exact linearity in V (one environment build per permutation

@@ -45,7 +45,13 @@ __device__ __forceinline__ const double* res(unsigned long long v, int buf, cons
 
 // One CTA per TM x TN output tile of a problem (TM, TN in {32, 64}, the
 // smallest padding of each problem's rows and columns), summing every segment
-// of its range; each thread owns a 4 x 4 sub-tile.
+// of its range. Each warp owns a 16 x 32 region of the tile and each of its
+// threads a 4 x 4 sub-tile of that region (rows 4 apart, columns 8 apart, so
+// that shared-memory reads are conflict-free); a warp whose region lies
+// outside the problem takes part in the loads but issues no FMA, and the K
+// loop of a chunk stops at the segment's K: the FP64 pipe, the bound of this
+// kernel, only runs on the problem's rows up to a multiple of 16, its
+// columns up to a multiple of 32 and its exact K.
 template <int TM, int TN>
 __global__ void __launch_bounds__(TM * TN / 16, TM * TN == 4096 ? 2 : (TM * TN == 2048 ? 3 : 4)) seg_gemm_f64_t(const GProb* __restrict__ probs,
                                                                const GSeg* __restrict__ segs,
@@ -56,17 +62,20 @@ __global__ void __launch_bounds__(TM * TN / 16, TM * TN == 4096 ? 2 : (TM * TN =
   const GTile tl = tiles[t];
   const GProb p = probs[tl.prob];
   constexpr int NT = TM * TN / 16;  // threads; each computes 4 x 4 outputs
-  constexpr int TDM = TM / 4, TDN = TN / 4;
+  constexpr int WRM = TM / 16;      // warp regions along the rows
   __shared__ double As[TK][TM + 1];
   __shared__ double Bs[TK][TN + 1];
   const int tid = threadIdx.x;
-  const int tx = tid % TDN, ty = tid / TDN;
+  const int w = tid >> 5, lane = tid & 31;
+  const int rb = 16 * (w % WRM), cb = 32 * (w / WRM);   // the warp's region in the tile
+  const int ty = lane >> 3, tx = lane & 7;               // rows rb + ty + 4r, columns cb + tx + 8c
   double acc[4][4];
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
   const int m0 = tl.m0, n0 = tl.n0;
+  const bool active = m0 + rb < p.m && n0 + cb < p.n;   // uniform in the warp
   for (int s = tl.s0; s < tl.s1; ++s) {
     const GSeg g = segs[p.seg0 + s];
     const bool aid = (g.a == 0ull && g.abuf == 0);
@@ -77,16 +86,16 @@ __global__ void __launch_bounds__(TM * TN / 16, TM * TN == 4096 ? 2 : (TM * TN =
         for (int r = 0; r < 4; ++r)
 #pragma unroll
           for (int c = 0; c < 4; ++c)
-            if (m0 + ty + TDM * r == n0 + tx + TDN * c) acc[r][c] += g.sc;
+            if (m0 + rb + ty + 4 * r == n0 + cb + tx + 8 * c) acc[r][c] += g.sc;
       } else {
         const double* Bp = res(g.b, g.bbuf, bases);
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-          const int row = m0 + ty + TDM * r;
+          const int row = m0 + rb + ty + 4 * r;
           if (row >= p.m) continue;
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
-            const int col = n0 + tx + TDN * c;
+            const int col = n0 + cb + tx + 8 * c;
             if (col >= p.n) continue;
             const double v = g.tb ? Bp[(size_t)col * g.ldb + row] : Bp[(size_t)row * g.ldb + col];
             acc[r][c] += g.sc * v;
@@ -123,17 +132,22 @@ __global__ void __launch_bounds__(TM * TN / 16, TM * TN == 4096 ? 2 : (TM * TN =
         Bs[kk][col] = v;
       }
       __syncthreads();
+      if (active) {
+        const int kn = g.k - k0 < TK ? g.k - k0 : TK;   // uniform in the CTA
 #pragma unroll
-      for (int kk = 0; kk < TK; ++kk) {
-        double a[4], b[4];
+        for (int kk = 0; kk < TK; ++kk) {
+          if (kk < kn) {
+            double a[4], b[4];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) a[r] = As[kk][ty + TDM * r];
+            for (int r = 0; r < 4; ++r) a[r] = As[kk][rb + ty + 4 * r];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + TDN * c];
+            for (int c = 0; c < 4; ++c) b[c] = Bs[kk][cb + tx + 8 * c];
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+            for (int r = 0; r < 4; ++r)
 #pragma unroll
-          for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+              for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+          }
+        }
       }
       __syncthreads();
     }
@@ -141,11 +155,11 @@ __global__ void __launch_bounds__(TM * TN / 16, TM * TN == 4096 ? 2 : (TM * TN =
   double* Cp = const_cast<double*>(res(p.c, p.cbuf, bases));
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
-    const int row = m0 + ty + TDM * r;
+    const int row = m0 + rb + ty + 4 * r;
     if (row >= p.m) continue;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      const int col = n0 + tx + TDN * c;
+      const int col = n0 + cb + tx + 8 * c;
       if (col >= p.n) continue;
       double* dst = Cp + (size_t)row * p.ldc + col;
       if (tl.split) atomicAdd(dst, acc[r][c]);

@@ -328,6 +328,41 @@ int main(int argc, char** argv) {
       cfg.width = width;
       check_tiled(E.plan, E.lay, ex, cfg);
     }
+  {
+    // executed (padded) FP64 flops of the centre product: tiles of 64 or 32 (least
+    // padding), K of each segment rounded up to 16
+    auto tsz = [](int d) { return ((d + 63) / 64) * 64 <= ((d + 31) / 32) * 32 ? 64 : 32; };
+    double exec_fl = 0, useful = 0, exec_k = 0, exec_k8 = 0, exec_16 = 0, exec_w = 0;
+    for (auto* Lv : {&E.plan.stage1, &E.plan.stage2})
+      for (const Launch& l : *Lv) {
+        useful += l.flops;
+        for (const Prob& p : l.probs) {
+          const int tm = tsz(p.m), tn = tsz(p.n);
+          const double tiles = (double)((p.m + tm - 1) / tm) * ((p.n + tn - 1) / tn);
+          for (int k = 0; k < p.nseg; ++k) {
+            const Seg& g = l.segs[p.seg0 + k];
+            if (g.a == 0 && g.abuf == 0) continue;
+            exec_fl += tiles * 2.0 * tm * tn * 16.0 * ((g.k + 15) / 16);
+            exec_k += tiles * 2.0 * tm * tn * g.k;
+            exec_k8 += tiles * 2.0 * tm * tn * 8.0 * ((g.k + 7) / 8);
+            const int tm2 = 16 * ((p.m + 15) / 16) <= 64 ? 16 * ((p.m + 15) / 16) : tm;
+            const int tn2 = 16 * ((p.n + 15) / 16) <= 64 ? 16 * ((p.n + 15) / 16) : tn;
+            const double tiles2 = (double)((p.m + tm2 - 1) / tm2) * ((p.n + tn2 - 1) / tn2);
+            exec_16 += tiles2 * 2.0 * tm2 * tn2 * 8.0 * ((g.k + 7) / 8);
+            // warps skip 16-row x (tn/2)-column regions outside the problem; K exact
+            for (int m0 = 0; m0 < p.m; m0 += tm)
+              for (int n0 = 0; n0 < p.n; n0 += tn) {
+                const int rm = std::min(tm, p.m - m0), rn = std::min(tn, p.n - n0);
+                const int wc = tn / 2;
+                exec_w += 2.0 * (16.0 * ((rm + 15) / 16)) * (wc * ((rn + wc - 1) / wc)) * g.k;
+              }
+          }
+        }
+      }
+    std::printf("fp64 padding: useful %.3f TFLOP, executed %.3f TFLOP, efficiency %.3f (exact K %.3f, K by 8 %.3f, "
+                "tiles by 16 up to 64 and K by 8 %.3f, warp skipping %.3f)\n", useful / 1e12, exec_fl / 1e12,
+                useful / exec_fl, useful / exec_k, useful / exec_k8, useful / exec_16, useful / exec_w);
+  }
   int64_t lp = 0, rp = 0;
   for (uint64_t a : E.Lp.owned) lp += ex.alloc_bytes.at(a);
   for (uint64_t a : E.Rp.owned) rp += ex.alloc_bytes.at(a);

@@ -342,3 +342,32 @@ def test_mixed_davidson_policy_reaches_the_fp64_energy_with_few_fp64_products(ho
     assert abs(emix - e64) < 1e-10
     assert nmix64 <= 8 and n64 > 4 * nmix64
     assert nbf16 + nx3 > 0
+
+
+@pytest.mark.parametrize("L,N,two_s,D", [(6, 6, 0, 8), (7, 7, 1, 10)])
+def test_su2_rdm1_is_the_energy_gradient_in_h(host_exec, tmp_path, L, N, two_s, D):
+    """The SU(2) one-particle density matrix at the centre (L-2, L-1) against central
+    differences of E = psi^T H_eff psi / psi^T psi in symmetric perturbations of h (E is
+    linear in h at fixed MPS), with H_eff from the library's SU(2) task lists (which match
+    the oracle); trace N, symmetric."""
+    from oracle.dmrgsu2 import MPSSU2
+    mps = MPSSU2.from_raw(q.random_mps_blocks(L, N, two_s, D, q.SYM_SU2, 5, L - 2))
+    h, V = q.make_integrals(L, 11)
+    g = _run_su2(host_exec, tmp_path, mps, h, V, ["rdm1"]).reshape(L, L)
+    assert abs(np.trace(g) - N) < 1e-12
+    assert np.abs(g - g.T).max() < 1e-14
+    psi = mps.psi_to_flat()
+
+    def energy(hh):
+        out = _run_su2(host_exec, tmp_path, mps, hh, V)
+        s = out[:len(out) // 2]
+        return psi @ s / (psi @ psi)
+    eps = 1e-5
+    for p, r in [(0, 0), (1, 3), (2, L - 1), (L - 1, L - 1)]:
+        dh = np.zeros((L, L))
+        dh[p, r] += 1.0
+        if p != r:
+            dh[r, p] += 1.0
+        fd = (energy(h + eps * dh) - energy(h - eps * dh)) / (2 * eps)
+        an = g[p, r] + (g[r, p] if p != r else 0.0)
+        assert abs(fd - an) <= 1e-8 * max(1.0, abs(an))
