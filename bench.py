@@ -351,8 +351,12 @@ def run_ours(args, rank, world, local):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    if args.profile:
+        torch.cuda.profiler.start()
     runs = [solve("mixed") for _ in range(args.steps)]
     torch.cuda.synchronize()
+    if args.profile:
+        torch.cuda.profiler.stop()
     if dist:
         dist.barrier()
     clk = clocks.stop()
@@ -392,7 +396,7 @@ def run_ours(args, rank, world, local):
     nelem = st["heff_bytes"] / 8.0
     npsi = 2.0 * st["psi_size"]
     esize = {"fp64": 8, "tf32": 4, "bf16": 2, "bf16x3": 6}
-    ridge = pk["bf16"] / pk["hbm"]
+    ridge = pk["bf16"] * 1e3 / pk["hbm"]          # flop per byte: TFLOP/s over GB/s
     for name, f in forms.items():
         b = (nelem - npsi) * esize[name] + 8 * npsi
         t_s = f["ms_per_product"] / 1e3
@@ -519,12 +523,16 @@ def run_products(args, rank, world, local):
     for _ in range(args.warmup):
         ctx.apply_heff_dev(psi.data_ptr(), sig.data_ptr(), stream.cuda_stream, prec)
     torch.cuda.synchronize()
+    if args.profile:
+        torch.cuda.profiler.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
         ctx.apply_heff_dev(psi.data_ptr(), sig.data_ptr(), stream.cuda_stream, prec)
     e1.record(stream)
     torch.cuda.synchronize()
+    if args.profile:
+        torch.cuda.profiler.stop()
     ctx.check_device()
     t = e0.elapsed_time(e1) / 1e3 / args.steps
     st = ctx.stats()
@@ -546,9 +554,10 @@ def run_batched(args, rank, world, local):
     ctxs, psis, sigs, shapes = [], [], [], []
     flops = nbytes = 0.0
     t0 = time.perf_counter()
+    sym = qd.SU2 if args.symmetry == "su2" else qd.U1
     for w in q.batched_instances():
         h, V = q.make_integrals(w["L"], w["int_seed"])
-        c = qd.Context(device=local)
+        c = qd.Context(device=local, symmetry=sym)
         c.load_integrals(h, V)
         c.set_target(w["N"], w["two_s"])
         c.init_mps(w["D"], w["mps_seed"], w["L"] // 2 - 1)
@@ -593,22 +602,49 @@ def run_batched(args, rank, world, local):
         c.check_device()
     diff = max(float((torch.linalg.norm(a - b) / torch.linalg.norm(b)).item()) for a, b in zip(sigs, ref))
     gflops, nodes = g.info()
+    g.close()
+    for c in ctxs:
+        c.close()
+    # part (i): the CAS(54,36)-shaped product at D = 2048 alone, in one graph and eagerly
+    single = None
+    if args.D > 0:
+        L1, N1 = args.L, args.N
+        h, V = q.make_integrals(L1, q.integrals.BASE_SEED + 2)
+        c1 = qd.Context(device=local, symmetry=sym)
+        c1.load_integrals(h, V)
+        c1.set_target(N1, 0)
+        c1.init_mps(args.D, q.integrals.BASE_SEED + 1002, L1 // 2 - 1)
+        c1.build_env()
+        p1 = torch.tensor(c1.psi(), device="cuda")
+        s1 = torch.empty_like(p1)
+        f1 = c1.stats()["heff_flops"]
+        t_eager = timed(lambda: c1.apply_heff_dev(p1.data_ptr(), s1.data_ptr(), stream.cuda_stream, prec))
+        r1 = s1.clone()
+        g1 = qd.HeffGraph([c1], [p1.data_ptr()], [s1.data_ptr()], prec)
+        t_g1 = timed(lambda: g1.launch(stream.cuda_stream))
+        single = {"workload": f"L{L1} N{N1} D{args.D} centre product", "gflop": f1 / 1e9,
+                  "eager_ms": t_eager * 1e3, "graph_ms": t_g1 * 1e3, "graph_speedup": t_eager / t_g1,
+                  "graph_tflops": f1 / t_g1 / 1e12,
+                  "graph_vs_eager_rel_diff": float((torch.linalg.norm(s1 - r1) / torch.linalg.norm(r1)).item())}
+        g1.close()
+        c1.close()
     pk = measured_peaks()
     line = {
         "metric": "batched H_eff psi TFLOP/s, 16 independent problems in one CUDA graph",
         "value": flops / t_graph / 1e12, "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_graph * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.precision.replace("fp", "f"), "data": "synthetic",
-        "config": {"workload": "16 U(1) problems, L uniform 12..24, N = L, D in {128, 256, 512} (seed 99)",
+        "config": {"workload": f"16 {args.symmetry.upper()} problems, L uniform 12..24, N = L, D in {{128, 256, 512}} "
+                               "(seed 99)",
                    "instances": shapes, "gflop_per_step": flops / 1e9, "graph_nodes": nodes,
                    "one_by_one_ms": t_seq * 1e3, "graph_speedup": t_seq / t_graph,
                    "graph_vs_one_by_one_max_rel_diff": diff, "env_build_s": build_s,
+                   "symmetry": args.symmetry, "single_problem_in_graph": single,
                    "l2": "all operators of the 16 problems stay resident; replays are L2-warm"},
         "roofline": {"bound": "hbm", "achieved": nbytes / t_graph / 1e9, "peak": pk["hbm"], "unit": "GB/s",
                      "frac": nbytes / t_graph / 1e9 / pk["hbm"], "traffic": None},
         "clocks": clk,
     }
-    g.close()
     print(json.dumps(line), flush=True)
 
 

@@ -174,6 +174,28 @@ void check_fp64(const HeffPlan& P, const PsiLayout& lay, const RecEx& ex) {
 
 void check_tiled(const HeffPlan& P, const PsiLayout& lay, const RecEx& ex, const TileCfg& cfg) {
   const TiledPlan T = plan_tiled(P, lay, cfg);
+  if (std::getenv("PLANNER_TILED_STATS") && cfg.kmax == 4096 && cfg.width == 256) {
+    // MMA work of both stages (M = 128 rows per A panel, N = the B panel rows rounded to 16,
+    // K rounded to 16) against the algorithmic flops; chunks of 64 K per MMA group
+    double mma1 = 0, mma2 = 0, kch1 = 0, kch2 = 0;
+    for (const K1Item& it : T.i1)
+      for (int v = it.v0; v < it.v0 + it.nv; ++v) {
+        const int nm = 16 * ((it.nrows + 15) / 16), kk = 16 * ((it.k + 15) / 16);
+        mma1 += 2.0 * 128 * nm * kk;
+        kch1 += (kk + 63) / 64;
+      }
+    for (const K2Item& it : T.i2)
+      for (int sg = it.s0; sg < it.s1; ++sg) {
+        const int nm = 16 * ((it.nrows + 15) / 16), kk = 16 * ((T.s2[sg].k + 15) / 16);
+        mma2 += 2.0 * 128 * nm * kk;
+        kch2 += (kk + 63) / 64;
+      }
+    std::printf("tiled: stage1 items %zu views %zu, stage2 items %zu segs %zu; MMA flops %.3f + %.3f TFLOP for %.3f "
+                "useful (padding %.2fx); K chunks of 64: %.0f + %.0f; arenas A %.2f B %.2f psi %.3f T %.2f GB/plane\n",
+                T.i1.size(), T.v1.size(), T.i2.size(), T.s2.size(), mma1 / 1e12, mma2 / 1e12, T.flops / 1e12,
+                (mma1 + mma2) / T.flops, kch1, kch2, T.abytes / 1e9, T.bbytes / 1e9, T.psibytes / 1e9,
+                T.tbytes / 1e9);
+  }
   if (T.flops != P.flops) fail("tiled plan: flop count differs from the FP64 plan");
   // conversion views
   auto views_ok = [&](const std::vector<TView>& vs, int64_t arena, const char* what) {
