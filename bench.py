@@ -452,7 +452,8 @@ def run_ours(args, rank, world, local):
                                    "library its site sub-blocks (x, channel) and excludes identity "
                                    "references; both are reported"}
     st2 = ctx.stats()
-    tile = {"stage2_kmax": st2["tile_kmax"], "stage1_width": st2["tile_width"], "autotuner_runs": st2["tunes"],
+    tile = {"stage2_kmax": st2["tile_kmax"], "stage1_width": st2["tile_width"], "chunk_bytes": st2["tile_chunk"],
+            "autotuner_runs": st2["tunes"],
             "autotuner_s": st2["tune_seconds"]}
     sym_name = "SU(2)" if su2 else "U(1)xU(1)"
     wl = f"su2_L{L}_N{N}_S0_D{D}" if su2 else f"u1_L{L}_N{N}_Sz0_D{D}"

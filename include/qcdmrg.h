@@ -81,6 +81,9 @@ typedef struct {
                            Q' of an enlarged block): 1 runs each group of at least 8 as a GEMM of
                            a coefficient matrix with the operators' blocks, -1 sums them block
                            by block, 0 (default) takes the GEMM form when pair_switch is set */
+  int tile_chunk;       /* with autotune_off = 1: chunk byte target of the BF16 forms (0: a fixed
+                           K depth per chunk; 1..65536: chunks of small operand panels deepened
+                           to about that many bytes). Outside 0..65536: QCDMRG_EINVAL */
 } qcdmrg_config;
 
 /*
@@ -140,6 +143,7 @@ typedef struct {
                             BF16, BF16x3) */
   double dav_seconds;    /* its wall time */
   double dav_energy_mixed; /* its last Ritz value before the FP64 correction (policy 1) */
+  int tile_chunk;        /* chunk byte target of the BF16 forms in use (0: fixed K depth) */
 } qcdmrg_stats_t;
 
 /* Davidson options (zero fields take the defaults in brackets). */

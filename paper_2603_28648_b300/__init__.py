@@ -32,7 +32,8 @@ class QcdmrgError(RuntimeError):
 class Config(ctypes.Structure):
     _fields_ = [("symmetry", ctypes.c_int), ("device", ctypes.c_int),
                 ("tmp_budget_gb", ctypes.c_double), ("hbm_budget_gb", ctypes.c_double),
-                ("autotune_off", ctypes.c_int), ("pair_switch", ctypes.c_int), ("sum_gemm", ctypes.c_int)]
+                ("autotune_off", ctypes.c_int), ("pair_switch", ctypes.c_int), ("sum_gemm", ctypes.c_int),
+                ("tile_chunk", ctypes.c_int)]
 
 
 class MpsDesc(ctypes.Structure):
@@ -69,7 +70,8 @@ class Stats(ctypes.Structure):
                 ("tile_kmax", ctypes.c_int), ("tile_width", ctypes.c_int), ("tunes", ctypes.c_int),
                 ("tune_seconds", ctypes.c_double), ("f64_tiles", ctypes.c_int64 * 4),
                 ("f64_split_tiles", ctypes.c_int64), ("dav_hpsi", ctypes.c_int * 4),
-                ("dav_seconds", ctypes.c_double), ("dav_energy_mixed", ctypes.c_double)]
+                ("dav_seconds", ctypes.c_double), ("dav_energy_mixed", ctypes.c_double),
+                ("tile_chunk", ctypes.c_int)]
 
 
 EXPORTS = [
@@ -152,10 +154,11 @@ class Context:
     """One qcdmrg context (one device, one problem)."""
 
     def __init__(self, device=0, symmetry=U1, tmp_budget_gb=0.0, hbm_budget_gb=0.0, autotune=True,
-                 pair_switch=0, sum_gemm=0, lib=None):
+                 pair_switch=0, sum_gemm=0, tile_chunk=0, lib=None):
         self.lib = lib or load()
         self.h = ctypes.c_void_p()
-        cfg = Config(symmetry, device, tmp_budget_gb, hbm_budget_gb, 0 if autotune else 1, pair_switch, sum_gemm)
+        cfg = Config(symmetry, device, tmp_budget_gb, hbm_budget_gb, 0 if autotune else 1, pair_switch, sum_gemm,
+                     tile_chunk)
         rc = self.lib.qcdmrg_create(ctypes.byref(self.h), ctypes.byref(cfg))
         if rc != QCDMRG_OK:
             raise QcdmrgError(rc, "context creation failed (no usable CUDA device?)")

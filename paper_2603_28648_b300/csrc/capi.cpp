@@ -102,7 +102,7 @@ int qcdmrg_create(qcdmrg_ctx** out, const qcdmrg_config* cfg) {
   if (cfg->symmetry == QCDMRG_SU2 && cfg->pair_switch != 0) return QCDMRG_EINVAL;
   // the configuration is checked before any CUDA call
   if (!(cfg->hbm_budget_gb >= 0) || !(cfg->tmp_budget_gb >= 0) || cfg->pair_switch < 0 || cfg->sum_gemm < -1 ||
-      cfg->sum_gemm > 1)
+      cfg->sum_gemm > 1 || cfg->tile_chunk < 0 || cfg->tile_chunk > 65536)
     return QCDMRG_EINVAL;
   auto* c = new qcdmrg_ctx();
   try {
@@ -116,7 +116,9 @@ int qcdmrg_create(qcdmrg_ctx** out, const qcdmrg_config* cfg) {
     c->eng.autotune = cfg->autotune_off == 0;
     c->eng.pair_switch = cfg->pair_switch;
     c->eng.su2 = cfg->symmetry == QCDMRG_SU2;
+    c->eng.device = cfg->device;
     c->eng.sum_gemm = cfg->sum_gemm;
+    c->eng.tcfg.chunk = cfg->tile_chunk;
   } catch (const std::invalid_argument&) {
     delete c;
     return QCDMRG_EINVAL;
@@ -864,6 +866,7 @@ int qcdmrg_stats(const qcdmrg_ctx* ctx, qcdmrg_stats_t* out) {
   out->h2d_bytes = ctx->eng.h2d_bytes;
   out->tile_kmax = ctx->eng.tcfg.kmax;
   out->tile_width = ctx->eng.tcfg.width;
+  out->tile_chunk = ctx->eng.tcfg.chunk;
   out->tunes = ctx->eng.tunes;
   out->tune_seconds = ctx->eng.tune_seconds;
   out->d2h_bytes = ctx->eng.d2h_bytes;

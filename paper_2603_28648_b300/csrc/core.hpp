@@ -152,6 +152,16 @@ struct Executor {
   virtual void scale(uint64_t x, double a, int64_t n) = 0;
   // y = a x + b y
   virtual void axpby(uint64_t y, double a, uint64_t x, double b, int64_t n) = 0;
+  // out[k] = xs[k] . y for k < m (host results; one round trip on a device)
+  virtual void mdot(const uint64_t* xs, int m, uint64_t y, int64_t n, double* out) {
+    for (int k = 0; k < m; ++k) out[k] = dot(xs[k], y, n);
+  }
+  // y = sum_k c[k] xs[k] + b y (b = 0: y is not read)
+  virtual void mcombine(uint64_t y, const uint64_t* xs, const double* c, int m, double b, int64_t n) {
+    if (b == 0.0) zero(y, n);
+    else if (b != 1.0) scale(y, b, n);
+    for (int k = 0; k < m; ++k) axpby(y, c[k], xs[k], 1.0, n);
+  }
   // t = r / max(|d - theta|, floor) (Davidson preconditioner)
   virtual void precond(uint64_t t, uint64_t r, uint64_t d, double theta, double floor, int64_t n) = 0;
   // symmetric eigendecomposition in place: A (n x n, column-major) -> eigenvectors,

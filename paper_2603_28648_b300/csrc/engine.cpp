@@ -322,6 +322,7 @@ void Engine::heff(uint64_t psi, uint64_t sig, void* stream, int prec) {
     const int planes = (prec == 3 || mixed_planes) ? 3 : 1;
     if (pr->tiled_planes() < planes) {
       pr->prepare_tiled(plan_tiled(plan, lay, tcfg), planes);
+      pr->set_tiled_chunk(tcfg.chunk);
       if (autotune) {
         tune_tiled(psi, sig, prec);
         pr->zero_async(sig, lay.size, stream);
@@ -336,37 +337,50 @@ void Engine::heff(uint64_t psi, uint64_t sig, void* stream, int prec) {
   }
 }
 
-// Autotuner of the bf16 tensor-core path: times every candidate work-item
-// shape on this centre's task lists (the operand mirrors stay; only the items
-// change) and keeps the fastest. The choice is cached per problem-size class
-// (precision, psi size to a factor of two), so the centres of a sweep at the
-// same bond dimension are tuned once or twice, not at every step.
+// Autotuner of the bf16 tensor-core path. Phase 1 times every candidate
+// work-item shape on this centre's task lists (the operand mirrors stay; only
+// the items change); phase 2 times chunk byte targets of the kernels with the
+// best items (no re-planning: the target is a kernel argument). The choice is
+// cached per device and problem class: precision, psi size to a factor of two,
+// and two coarse features of the block-size histogram (flops per psi element,
+// which grows with the typical block dimension, and the number of stage-2
+// problems, to a factor of two each), so the centres of a sweep at the same
+// bond dimension and block structure are tuned once or twice, not at every step.
 void Engine::tune_tiled(uint64_t psi, uint64_t sig, int prec) {
   static std::mutex mu;
-  static std::map<std::pair<int, int>, TileCfg> cache;
-  int lg = 0;
-  while ((int64_t(1) << lg) < lay.size) ++lg;
-  const auto key = std::make_pair(prec, lg);
-  auto same = [](const TileCfg& a, const TileCfg& b) { return a.kmax == b.kmax && a.width == b.width; };
+  static std::map<std::array<int, 5>, TileCfg> cache;
+  auto lg2 = [](double v) {
+    int l = 0;
+    while (v > 1.0 && l < 62) {
+      v *= 0.5;
+      ++l;
+    }
+    return l;
+  };
+  size_t nprob2 = 0;
+  for (const Launch& l : plan.stage2) nprob2 += l.probs.size();
+  const std::array<int, 5> key = {device, prec, lg2((double)lay.size), lg2(plan.flops / std::max<int64_t>(1, lay.size)),
+                                  lg2((double)nprob2)};
+  auto same_items = [](const TileCfg& a, const TileCfg& b) { return a.kmax == b.kmax && a.width == b.width; };
   {
     std::lock_guard<std::mutex> g(mu);
     auto it = cache.find(key);
     if (it != cache.end()) {
-      if (!same(it->second, tcfg)) {
-        tcfg = it->second;
-        pr->set_tiled_items(plan_tiled(plan, lay, tcfg));
-      }
+      if (!same_items(it->second, tcfg)) pr->set_tiled_items(plan_tiled(plan, lay, it->second));
+      tcfg = it->second;
+      pr->set_tiled_chunk(tcfg.chunk);
       return;
     }
   }
   auto t0 = std::chrono::steady_clock::now();
   // BF16x3 keeps the FP32 accumulation of one item to K <= 4096
-  std::vector<TileCfg> cands = {{4096, TP_B}, {1024, TP_B}, {4096, 128}, {1024, 128}};
-  if (prec != 3) cands.push_back({1 << 30, TP_B});
+  std::vector<TileCfg> cands = {{4096, TP_B, 0}, {1024, TP_B, 0}, {4096, 128, 0}, {1024, 128, 0}};
+  if (prec != 3) cands.push_back({1 << 30, TP_B, 0});
   TileCfg loaded = tcfg, best = tcfg;
+  pr->set_tiled_chunk(0);
   double tbest = 1e30;
   for (const TileCfg& c : cands) {
-    if (!same(c, loaded)) {
+    if (!same_items(c, loaded)) {
       pr->set_tiled_items(plan_tiled(plan, lay, c));
       loaded = c;
     }
@@ -376,7 +390,16 @@ void Engine::tune_tiled(uint64_t psi, uint64_t sig, int prec) {
       best = c;
     }
   }
-  if (!same(best, loaded)) pr->set_tiled_items(plan_tiled(plan, lay, best));
+  if (!same_items(best, loaded)) pr->set_tiled_items(plan_tiled(plan, lay, best));
+  for (int chunk : {32768, 49152, 65536}) {
+    pr->set_tiled_chunk(chunk);
+    const double t = pr->time_tiled(psi, sig, prec, 2);
+    if (t < tbest) {
+      tbest = t;
+      best.chunk = chunk;
+    }
+  }
+  pr->set_tiled_chunk(best.chunk);
   tcfg = best;
   {
     std::lock_guard<std::mutex> g(mu);
@@ -445,6 +468,16 @@ DavResult Engine::davidson(const DavOpts& o) {
     int m = 1;
     std::vector<double> Hs((size_t)mmax * mmax, 0.0);
     Hs[0] = ex->dot(V[0], W[0], n);
+    // classical Gram-Schmidt against V[0..k), twice (one batched dot and one
+    // batched update per pass)
+    auto orth = [&](uint64_t tv, int k) {
+      std::vector<double> c(k);
+      for (int pass = 0; pass < 2; ++pass) {
+        ex->mdot(V.data(), k, tv, n, c.data());
+        for (double& v : c) v = -v;
+        ex->mcombine(tv, V.data(), c.data(), k, 1.0, n);
+      }
+    };
     double theta = Hs[0];
     std::vector<double> phase_res;   // residuals of the current precision phase
     for (int it = 0; it < o.max_iter; ++it) {
@@ -459,12 +492,11 @@ DavResult Engine::davidson(const DavOpts& o) {
         ex->copy(wp, w, n);
         have_prev = true;
       }
-      ex->zero(x, n);
-      ex->zero(w, n);
-      for (int k = 0; k < m; ++k) {
-        double y = vec[(size_t)k * m + 0];
-        ex->axpby(x, y, V[k], 1.0, n);
-        ex->axpby(w, y, W[k], 1.0, n);
+      {
+        std::vector<double> y(m);
+        for (int k = 0; k < m; ++k) y[k] = vec[(size_t)k * m + 0];
+        ex->mcombine(x, V.data(), y.data(), m, 0.0, n);
+        ex->mcombine(w, W.data(), y.data(), m, 0.0, n);
       }
       ex->copy(r, w, n);
       ex->axpby(r, -theta, x, 1.0, n);
@@ -543,19 +575,11 @@ DavResult Engine::davidson(const DavOpts& o) {
       }
       // correction vector: preconditioned residual, orthogonalised twice
       ex->precond(t, r, ddiag, theta, o.floor, n);
-      for (int pass = 0; pass < 2; ++pass)
-        for (int k = 0; k < m; ++k) {
-          double c = ex->dot(V[k], t, n);
-          ex->axpby(t, -c, V[k], 1.0, n);
-        }
+      orth(t, m);
       double tn = std::sqrt(ex->dot(t, t, n));
       if (!(tn > 1e-14)) {  // no new direction: take the residual itself
         ex->copy(t, r, n);
-        for (int pass = 0; pass < 2; ++pass)
-          for (int k = 0; k < m; ++k) {
-            double c = ex->dot(V[k], t, n);
-            ex->axpby(t, -c, V[k], 1.0, n);
-          }
+        orth(t, m);
         tn = std::sqrt(ex->dot(t, t, n));
         if (!(tn > 1e-14)) { R.converged = rn < o.tol; break; }
       }
@@ -588,23 +612,23 @@ DavResult Engine::davidson(const DavOpts& o) {
             m = 2;
           }
         }
-        for (int pass = 0; pass < 2; ++pass)
-          for (int k = 0; k < m; ++k) {
-            double c = ex->dot(V[k], t, n);
-            ex->axpby(t, -c, V[k], 1.0, n);
-          }
+        orth(t, m);
         tn = std::sqrt(ex->dot(t, t, n));
       }
       ex->copy(V[m], t, n);
       ex->scale(V[m], 1.0 / tn, n);
       apply(V[m], W[m]);
-      for (int i = 0; i <= m; ++i) {
+      {
         // after an FP64 check W0 = H V0 is exact: the coupling of V0 with a new
         // direction is taken as V_m . (H V0) (H symmetric), whose error does not
         // swamp the small true coupling the way V0 . (H V_m) in BF16x3 would
-        double v = (i == 0 && w0_exact) ? ex->dot(V[m], W[0], n) : ex->dot(V[i], W[m], n);
-        Hs[(size_t)i * mmax + m] = v;
-        Hs[(size_t)m * mmax + i] = v;
+        std::vector<double> col(m + 1);
+        ex->mdot(V.data(), m + 1, W[m], n, col.data());
+        if (w0_exact) col[0] = ex->dot(V[m], W[0], n);
+        for (int i = 0; i <= m; ++i) {
+          Hs[(size_t)i * mmax + m] = col[i];
+          Hs[(size_t)m * mmax + i] = col[i];
+        }
       }
       ++m;
     }

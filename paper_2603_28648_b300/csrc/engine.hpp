@@ -40,6 +40,7 @@ struct Engine {
   // SU(2) spin adaptation: bond labels (n, 2S) of multiplets, reduced
   // operators (rules_su2.cpp); two_s is then twice the total spin
   bool su2 = false;
+  int device = 0;           // CUDA ordinal (autotuner cache key)
   int64_t tmp_budget = 0;
   // cut of the normal/complementary switch: left blocks at cuts <= pair_switch
   // and right blocks at cuts > pair_switch hold normal pairs (0: normal pairs

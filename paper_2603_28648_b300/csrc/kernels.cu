@@ -215,6 +215,58 @@ __global__ void axpby_kernel(double* y, double a, const double* x, double b, lon
     y[i] = a * x[i] + b * y[i];
 }
 
+// Batched dots and linear combinations of Davidson basis vectors: one launch
+// pair and one host round trip for up to MVEC vectors instead of one per vector.
+constexpr int MVEC = 64;
+struct VecList {
+  const double* p[MVEC];
+  double c[MVEC];
+};
+
+// part[k * gridDim.x + b] = block b's contiguous share of xs[k] . y (the share
+// of y stays in L1 across the m vectors)
+__global__ void mdot_partial(VecList xs, int m, const double* y, long long n, double* part) {
+  __shared__ double sh[256];
+  const long long per = (n + gridDim.x - 1) / gridDim.x;
+  const long long lo = (long long)blockIdx.x * per, hi = min(n, lo + per);
+  for (int k = 0; k < m; ++k) {
+    const double* x = xs.p[k];
+    double s = 0;
+    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) s = fma(x[i], y[i], s);
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+      if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) part[(long long)k * gridDim.x + blockIdx.x] = sh[0];
+  }
+}
+
+// out[k] = sum of the nb block shares of vector k (block k)
+__global__ void mdot_reduce(const double* part, int nb, double* out) {
+  __shared__ double sh[256];
+  double s = 0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) s += part[(long long)blockIdx.x * nb + b];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = sh[0];
+}
+
+// y = sum_k c_k x_k + b y (b = 0: y is not read)
+__global__ void mcombine_kernel(double* y, VecList xs, int m, double b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double s = 0;
+    for (int k = 0; k < m; ++k) s = fma(xs.c[k], xs.p[k][i], s);
+    y[i] = (b == 0.0) ? s : fma(b, y[i], s);
+  }
+}
+
 __global__ void precond_kernel(double* t, const double* r, const double* d, double theta, double fl,
                                long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -515,6 +567,44 @@ class CudaExec : public Executor, public PreparedRunner {
     for (int i = 0; i < nb; ++i) s += h[i];
     return s;
   }
+  void mdot(const uint64_t* xs, int m, uint64_t y, int64_t n, double* out) override {
+    for (int k0 = 0; k0 < m; k0 += MVEC) {
+      const int mk = std::min(MVEC, m - k0);
+      if (n <= 0) {
+        for (int k = 0; k < mk; ++k) out[k0 + k] = 0.0;
+        continue;
+      }
+      VecList v{};
+      for (int k = 0; k < mk; ++k) v.p[k] = reinterpret_cast<const double*>(xs[k0 + k]);
+      const int nb = 2 * 148;
+      grow(&part_, &part_cap_, (size_t)(mk * nb + mk) * sizeof(double));
+      double* part = (double*)part_;
+      mdot_partial<<<nb, 256, 0, st_>>>(v, mk, reinterpret_cast<const double*>(y), n, part);
+      mdot_reduce<<<mk, 256, 0, st_>>>(part, nb, part + (size_t)mk * nb);
+      CK(cudaGetLastError());
+      CK(cudaMemcpyAsync(out + k0, part + (size_t)mk * nb, mk * sizeof(double), cudaMemcpyDeviceToHost, st_));
+      CK(cudaStreamSynchronize(st_));
+    }
+  }
+  void mcombine(uint64_t y, const uint64_t* xs, const double* c, int m, double b, int64_t n) override {
+    if (n <= 0) return;
+    if (m <= 0) {
+      if (b == 0.0) zero(y, n);
+      else if (b != 1.0) scale(y, b, n);
+      return;
+    }
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 148 * 16);
+    for (int k0 = 0; k0 < m; k0 += MVEC) {
+      const int mk = std::min(MVEC, m - k0);
+      VecList v{};
+      for (int k = 0; k < mk; ++k) {
+        v.p[k] = reinterpret_cast<const double*>(xs[k0 + k]);
+        v.c[k] = c[k0 + k];
+      }
+      mcombine_kernel<<<blocks, 256, 0, st_>>>(reinterpret_cast<double*>(y), v, mk, k0 == 0 ? b : 1.0, n);
+      CK(cudaGetLastError());
+    }
+  }
   void axpby(uint64_t y, double a, uint64_t x, double b, int64_t n) override {
     if (n <= 0) return;
     int blocks = (int)std::min<int64_t>((n + 255) / 256, 148 * 16);
@@ -633,6 +723,7 @@ class CudaExec : public Executor, public PreparedRunner {
     live_ += t.bytes;
     peak_ = std::max(peak_, live_);
   }
+  void set_tiled_chunk(int bytes) override { chunk_ = std::max(0, std::min(bytes, 65536)); }
   void set_tiled_items(const TiledPlan& P) override {
     if (!td_.planes) throw std::runtime_error("tiled path not prepared");
     CK(cudaStreamSynchronize(st_));
@@ -672,9 +763,10 @@ class CudaExec : public Executor, public PreparedRunner {
       throw std::runtime_error("tiled tensor-core path not prepared for this precision");
     cudaStream_t s = (cudaStream_t)stream;
     CK(launch_tile_views(t.psiv, t.npsiv, t.psi, t.psiplane, t.planes, reinterpret_cast<const double*>(psi), s));
-    CK(launch_tiled_stage1(mode, t.i1, t.ni1, t.v1, t.psi, t.psiplane, t.b, t.bplane, t.t, t.tplane, nsm_, err_, s));
+    CK(launch_tiled_stage1(mode, t.i1, t.ni1, t.v1, t.psi, t.psiplane, t.b, t.bplane, t.t, t.tplane, chunk_, nsm_,
+                           err_, s));
     CK(launch_tiled_stage2(mode, t.i2, t.ni2, t.s2, t.a, t.aplane, t.t, t.tplane, reinterpret_cast<double*>(sig),
-                           nsm_, err_, s));
+                           chunk_, nsm_, err_, s));
   }
   void run_prepared(int h, uint64_t psi, uint64_t sig, void* stream, int precision) override {
     const DevLaunch& d = prepared_.at(h);
@@ -801,6 +893,7 @@ class CudaExec : public Executor, public PreparedRunner {
   void* tau_ = nullptr;
   void* part_ = nullptr;
   size_t part_cap_ = 0;
+  int chunk_ = 0;   // chunk byte target of the tiled kernels
 };
 
 cudaError_t launch_f64_prepared(const void* handle, uint64_t psi, uint64_t sig, uint64_t scratch,

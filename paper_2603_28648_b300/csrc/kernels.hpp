@@ -31,6 +31,8 @@ struct PreparedRunner {
   virtual void prepare_tiled(const TiledPlan& plan, int planes) = 0;
   // replaces the work items only (same arenas: another TileCfg of the same plan)
   virtual void set_tiled_items(const TiledPlan& plan) = 0;
+  // chunk byte target of the tiled kernels (0: fixed K depth per chunk)
+  virtual void set_tiled_chunk(int bytes) { (void)bytes; }
   virtual int tiled_planes() const = 0;
   // device seconds of one H_eff psi on the tiled path (mean of reps, after one warm-up)
   virtual double time_tiled(uint64_t psi, uint64_t sig, int precision, int reps) = 0;

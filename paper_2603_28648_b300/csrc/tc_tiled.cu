@@ -174,6 +174,7 @@ struct Stage1Args {
   int64_t bplane;
   uint8_t* T;
   int64_t tplane;
+  int kcb;             // chunk byte target (0: KC elements of K per chunk)
 };
 struct Stage2Args {
   const K2Item* items;
@@ -183,6 +184,7 @@ struct Stage2Args {
   const uint8_t* B;    // T arena
   int64_t bplane;
   double* sig;
+  int kcb;             // chunk byte target (0: KC elements of K per chunk)
 };
 
 // One chunk as the MMA issuer sees it: up to MAXOPS (A, B) pairs, each over
@@ -223,6 +225,16 @@ struct Smem {
   static constexpr uint32_t VCM = ECNT + NR * 4;                   // record holds a commit point
   static constexpr uint32_t SMEM = VCM + NR;
 };
+
+// K elements per chunk of a work item: KC, or with a byte target kcb > 0 the
+// largest multiple of 16 (at most 256) whose chunk of per8 bytes per 8 K
+// elements stays within kcb; never fewer than KC. Fewer, larger chunks cut the
+// producer's and the MMA issuer's per-chunk work on small operand panels.
+template <int KC>
+__device__ __forceinline__ int chunk_depth(int kcb, int per8) {
+  if (kcb <= 0) return KC;
+  return min(256, max(KC, 16 * (kcb / (2 * per8))));
+}
 
 __device__ __forceinline__ void set_op(Op& o, uint32_t a, uint32_t b, uint32_t lboa, uint32_t lbob, uint32_t idesc,
                                        uint32_t tcol, uint32_t nk16, uint32_t astride, uint32_t bstride, uint32_t zero) {
@@ -399,8 +411,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) tiled_gemm(Args args, int nitems,
       if constexpr (STAGE == 1) {
         const K1View mv = sub0;
         const int kp = tiled_c8(it.k) * 8;
-        for (int k0 = 0; k0 < kp && ok; k0 += KC) {
-          const int ck = min(KC, kp - k0), cc = ck / 8;
+        const int kc = chunk_depth<KC>(
+            args.kcb, NP * ((int)__reduce_add_sync(0xffffffffu, lane < it.nv ? (unsigned)mv.pa8 : 0u) + it.pb8) * 128);
+        for (int k0 = 0; k0 < kp && ok; k0 += kc) {
+          const int ck = min(kc, kp - k0), cc = ck / 8;
           // A parts of the views side by side (exclusive prefix over lanes), then B
           const uint32_t mine = lane < it.nv ? (uint32_t)mv.pa8 * cc * 128 : 0u;
           uint32_t pre = mine;
@@ -424,7 +438,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tiled_gemm(Args args, int nitems,
           }
           if (lane == 0) {
             meta[r].nops = (uint32_t)it.nv;
-            meta[r].flags = (k0 == 0 ? F_FIRST : 0u) | (k0 + KC >= kp ? F_LAST : 0u) |
+            meta[r].flags = (k0 == 0 ? F_FIRST : 0u) | (k0 + kc >= kp ? F_LAST : 0u) |
                             (RingAlloc<MODE>::commit_point(ring.chunk) ? F_COMMIT : 0u);
             meta[r].li = (uint32_t)li;
           }
@@ -449,6 +463,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tiled_gemm(Args args, int nitems,
       } else {
         const int pa8 = (it.mrows + 7) / 8, pb8 = (it.nrows + 7) / 8;
         const uint32_t id = idesc_bf16(16 * ((it.nrows + 15) / 16), 0);
+        const int kc = chunk_depth<KC>(args.kcb, NP * (pa8 + pb8) * 128);
+        const uint32_t pack = max(S::PACK, (uint32_t)max(args.kcb, 0));
         bool first = true;  // no chunk of this item issued yet
         K2Seg mg_n = sub0;  // segments of the next batch (loaded one batch ahead)
         for (int sb = it.s0; sb < it.s1 && ok; sb += 32) {
@@ -460,7 +476,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tiled_gemm(Args args, int nitems,
           // than one chunk, or no segment)
           const int mkp = tiled_c8(mg.k) * 8;
           const uint32_t mna = (uint32_t)pa8 * (mkp / 8) * 128, mnb = (uint32_t)pb8 * (mkp / 8) * 128;
-          const uint32_t msz = (lane < cnt && mkp > 0 && mkp <= KC) ? NP * (mna + mnb) : 0u;
+          const uint32_t msz = (lane < cnt && mkp > 0 && mkp <= kc) ? NP * (mna + mnb) : 0u;
           // inclusive prefix sum of the piece sizes over the lanes
           uint32_t cum = msz;
 #pragma unroll
@@ -476,14 +492,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) tiled_gemm(Args args, int nitems,
               ++j;
               continue;
             }
-            if (kp > KC) {
-              // a long segment: chunks of KC along K, one op each
+            if (kp > kc) {
+              // a long segment: chunks of kc along K, one op each
               const int64_t ga = shfl64(mg.a, j), gb = shfl64(mg.b, j);
               const int c8 = kp / 8;
               const int64_t ab = ga + (int64_t)it.mp * (TP_A / 8) * c8 * 128;
               const int64_t bb = gb + (int64_t)it.np * (TP_B / 8) * c8 * 128;
-              for (int k0 = 0; k0 < kp; k0 += KC) {
-                const int ck = min(KC, kp - k0), cc = ck / 8;
+              for (int k0 = 0; k0 < kp; k0 += kc) {
+                const int ck = min(kc, kp - k0), cc = ck / 8;
                 const uint32_t na = (uint32_t)pa8 * cc * 128, nb = (uint32_t)pb8 * cc * 128;
                 uint32_t off;
                 if (!next(NP * (na + nb), off)) { ok = false; break; }
@@ -495,7 +511,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tiled_gemm(Args args, int nitems,
                   set_op(o, ca, cb, (uint32_t)pa8 * 128, (uint32_t)pb8 * 128, id, 0u, (uint32_t)(ck / 16), na, nb,
                          first ? 1u : 0u);
                   meta[r].nops = 1;
-                  meta[r].flags = (first ? F_FIRST : 0u) | (sb + j == it.s1 - 1 && k0 + KC >= kp ? F_LAST : 0u) |
+                  meta[r].flags = (first ? F_FIRST : 0u) | (sb + j == it.s1 - 1 && k0 + kc >= kp ? F_LAST : 0u) |
                                   (RingAlloc<MODE>::commit_point(ring.chunk) ? F_COMMIT : 0u);
                   meta[r].li = (uint32_t)li;
                   mbar_expect_tx(full(r), NP * (na + nb));
@@ -519,9 +535,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) tiled_gemm(Args args, int nitems,
             }
             // short segments j .. j2-1 packed into one chunk, one op each: the
             // group ends before the first lane whose piece is not short, would
-            // overflow PACK bytes, or is the (MAXOPS+1)-th
+            // overflow the pack size (PACK, or the chunk byte target when it is
+            // larger), or is the (MAXOPS+1)-th
             const uint32_t base = __shfl_sync(0xffffffffu, cum - msz, j);
-            const unsigned stop = __ballot_sync(0xffffffffu, lane > j && (msz == 0 || cum - base > S::PACK ||
+            const unsigned stop = __ballot_sync(0xffffffffu, lane > j && (msz == 0 || cum - base > pack ||
                                                                          lane - j >= MAXOPS));
             const int j2 = min(cnt, stop ? __ffs(stop) - 1 : 32);
             const uint32_t tot = __shfl_sync(0xffffffffu, cum, j2 - 1) - base;
@@ -822,10 +839,10 @@ cudaError_t launch_tile_views(const TView* views, int nviews, uint8_t* dst, int6
 
 cudaError_t launch_tiled_stage1(int mode, const K1Item* items, int nitems, const K1View* views,
                                 const uint8_t* psi_arena, int64_t psi_plane, const uint8_t* r_arena,
-                                int64_t r_plane, uint8_t* t_arena, int64_t t_plane, int grid, int* err,
-                                cudaStream_t st) {
+                                int64_t r_plane, uint8_t* t_arena, int64_t t_plane, int chunk_bytes, int grid,
+                                int* err, cudaStream_t st) {
   // A operands: right views; B operand: psi
-  Stage1Args a{items, views, r_arena, r_plane, psi_arena, psi_plane, t_arena, t_plane};
+  Stage1Args a{items, views, r_arena, r_plane, psi_arena, psi_plane, t_arena, t_plane, chunk_bytes};
   if (mode == TT_BF16) return launch<TT_BF16, 1>(a, nitems, grid, err, st);
   if (mode == TT_BF16X3) return launch<TT_BF16X3, 1>(a, nitems, grid, err, st);
   return cudaErrorInvalidValue;
@@ -833,8 +850,9 @@ cudaError_t launch_tiled_stage1(int mode, const K1Item* items, int nitems, const
 
 cudaError_t launch_tiled_stage2(int mode, const K2Item* items, int nitems, const K2Seg* segs,
                                 const uint8_t* a_arena, int64_t a_plane, const uint8_t* t_arena,
-                                int64_t t_plane, double* sigma, int grid, int* err, cudaStream_t st) {
-  Stage2Args a{items, segs, a_arena, a_plane, t_arena, t_plane, sigma};
+                                int64_t t_plane, double* sigma, int chunk_bytes, int grid, int* err,
+                                cudaStream_t st) {
+  Stage2Args a{items, segs, a_arena, a_plane, t_arena, t_plane, sigma, chunk_bytes};
   if (mode == TT_BF16) return launch<TT_BF16, 2>(a, nitems, grid, err, st);
   if (mode == TT_BF16X3) return launch<TT_BF16X3, 2>(a, nitems, grid, err, st);
   return cudaErrorInvalidValue;

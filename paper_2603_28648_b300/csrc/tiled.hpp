@@ -101,9 +101,12 @@ struct TiledPlan {
 //   kmax : summed K of one stage-2 item before a sigma block's segments are
 //          split over several items (more parallelism, FP64 atomics)
 //   width: accumulator columns of one stage-1 item (views side by side)
+//   chunk: chunk byte target of the kernels (0: fixed K depth per chunk; the
+//          items do not depend on it)
 struct TileCfg {
   int kmax = 4096;
   int width = TP_B;
+  int chunk = 0;
 };
 
 // The operand arenas (views, offsets, sizes) do not depend on the TileCfg,

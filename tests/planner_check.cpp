@@ -196,6 +196,50 @@ void check_tiled(const HeffPlan& P, const PsiLayout& lay, const RecEx& ex, const
                 (mma1 + mma2) / T.flops, kch1, kch2, T.abytes / 1e9, T.bbytes / 1e9, T.psibytes / 1e9,
                 T.tbytes / 1e9);
   }
+  if (std::getenv("PLANNER_CHUNK_STATS") && cfg.kmax == 4096 && cfg.width == 256) {
+    // chunks the tiled kernel's producer issues per product, for a fixed K depth per
+    // chunk (KC) or one chosen per item so that a chunk holds about `target` bytes
+    for (int np : {1, 3}) {
+      const int KC = np == 1 ? 64 : 32;
+      for (int target : {0, 32768, 49152, 65536}) {
+        auto depth = [&](int per8) {
+          if (target == 0) return KC;
+          const int c = std::min(256, std::max(KC, 16 * (target / (2 * per8))));
+          return c;
+        };
+        double c1 = 0, c2 = 0;
+        for (const K1Item& it : T.i1) {
+          int pa = 0;
+          for (int v = it.v0; v < it.v0 + it.nv; ++v) pa += T.v1[v].pa8;
+          const int kc = depth(np * (pa + it.pb8) * 128);
+          const int kp = tiled_c8(it.k) * 8;
+          c1 += (kp + kc - 1) / kc;
+        }
+        for (const K2Item& it : T.i2) {
+          const int pa8 = (it.mrows + 7) / 8, pb8 = (it.nrows + 7) / 8;
+          const int kc = depth(np * (pa8 + pb8) * 128);
+          int packed = 0, bytes = 0;
+          for (int sg = it.s0; sg < it.s1; ++sg) {
+            const int kp = tiled_c8(T.s2[sg].k) * 8;
+            if (kp == 0) continue;
+            if (kp > kc) {
+              c2 += (kp + kc - 1) / kc;
+              continue;
+            }
+            const int b = np * (pa8 + pb8) * (kp / 8) * 128;
+            if (packed == 0 || packed == 16 || bytes + b > std::max(32768, target)) {
+              c2 += 1;
+              packed = 0;
+              bytes = 0;
+            }
+            ++packed;
+            bytes += b;
+          }
+        }
+        std::printf("chunks: planes %d target %d: stage 1 %.0f, stage 2 %.0f\n", np, target, c1, c2);
+      }
+    }
+  }
   if (T.flops != P.flops) fail("tiled plan: flop count differs from the FP64 plan");
   // conversion views
   auto views_ok = [&](const std::vector<TView>& vs, int64_t arena, const char* what) {

@@ -38,7 +38,8 @@ def test_header_compiles_as_c():
 
 
 @pytest.mark.parametrize("field,value", [("pair_switch", -1), ("sum_gemm", 2), ("sum_gemm", -2),
-                                         ("hbm_budget_gb", -1.0), ("tmp_budget_gb", -1.0), ("symmetry", 7)])
+                                         ("hbm_budget_gb", -1.0), ("tmp_budget_gb", -1.0), ("symmetry", 7),
+                                         ("tile_chunk", -1), ("tile_chunk", 65537)])
 def test_create_rejects_bad_configuration_before_cuda(field, value):
     """Configuration errors are EINVAL whether or not a device is present (no CUDA call is
     made for them)."""

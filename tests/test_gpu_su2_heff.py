@@ -98,3 +98,33 @@ def test_su2_cas54_shape_symmetric_with_probe_diagonal():
         out = ctx.apply_heff(x, qd.PRECISIONS[prec])
         assert np.linalg.norm(out - hx) <= BOUND[prec] * np.linalg.norm(hx)
     ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["bf16", "bf16x3"])
+def test_su2_chunk_targets_give_the_fixed_depth_sigma(prec):
+    """The chunk byte target only regroups the K steps the kernels issue (same MMAs in
+    the same order per accumulator column), so every target reproduces the fixed-depth
+    sigma up to the order of the FP64 atomics of split items; each is within the form's
+    bound of FP64. CAS(54,36) shape at D = 256 multiplets: many chunks per item."""
+    import paper_2603_28648_b300 as qd
+    ensure_built()
+    L, N, D = 36, 54, 256
+    h, V = q.make_integrals(L, q.integrals.BASE_SEED + 2)
+    x = None
+    out = {}
+    for chunk in [0, 32768, 49152, 65536]:
+        ctx = qd.Context(symmetry=qd.SU2, autotune=False, tile_chunk=chunk)
+        ctx.load_integrals(h, V)
+        ctx.set_target(N, 0)
+        ctx.init_mps(D, 3, 17)
+        ctx.build_env()
+        if x is None:
+            x = np.random.default_rng(5).normal(size=ctx.psi_size())
+            ref = ctx.apply_heff(x, qd.FP64)
+        out[chunk] = ctx.apply_heff(x, qd.PRECISIONS[prec])
+        assert ctx.stats()["tile_chunk"] == chunk
+        ctx.close()
+    for chunk, o in out.items():
+        assert np.linalg.norm(o - ref) <= BOUND[prec] * np.linalg.norm(ref), chunk
+        assert np.linalg.norm(o - out[0]) <= 1e-12 * np.linalg.norm(out[0]), chunk
+

@@ -53,6 +53,43 @@ def test_noalloc_matches_device_entry_point_twice():
         assert np.linalg.norm(o - r) <= TOL_FP64 * np.linalg.norm(r), trial
 
 
+def test_noalloc_allocates_nothing_and_runs_inside_graph_capture():
+    """After one warm call the entry point allocates no device memory (free bytes
+    unchanged around an eager call), and it can be captured into a CUDA graph
+    (capture rejects any allocation or synchronisation); the replayed sigma equals
+    the device entry point's."""
+    import torch
+    ctx = _ctx()
+    n = ctx.psi_size()
+    x = torch.tensor(np.random.default_rng(11).normal(size=n), device="cuda")
+    ref = torch.empty_like(x)
+    out = torch.full_like(x, float("nan"))
+    stream = torch.cuda.current_stream()
+    ctx.apply_heff_dev(x.data_ptr(), ref.data_ptr(), stream.cuda_stream)
+    ctx.apply_heff_noalloc(x.data_ptr(), out.data_ptr(), stream.cuda_stream)   # warm call
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    ctx.apply_heff_noalloc(x.data_ptr(), out.data_ptr(), stream.cuda_stream)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    out.fill_(float("nan"))
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side):
+            ctx.apply_heff_noalloc(x.data_ptr(), out.data_ptr(), side.cuda_stream)
+    torch.cuda.synchronize()
+    for _ in range(2):
+        g.replay()
+    torch.cuda.synchronize()
+    r, o = ref.cpu().numpy(), out.cpu().numpy()
+    assert np.all(np.isfinite(o))
+    assert np.linalg.norm(o - r) <= TOL_FP64 * np.linalg.norm(r)
+    ctx.close()
+
+
 def test_noalloc_rejects_too_large_problem():
     import paper_2603_28648_b300 as qd
     import torch
