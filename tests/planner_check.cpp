@@ -425,6 +425,36 @@ int main(int argc, char** argv) {
           }
         }
       }
+    if (std::getenv("PLANNER_REGION_STATS")) {
+      // FP64 executed by warp regions of rh x rw outputs (exact K), per region shape
+      // and with the best shape chosen per problem; and at 8 x 8 granularity
+      const int shapes[3][2] = {{16, 32}, {8, 64}, {32, 16}};
+      double ex[3] = {0, 0, 0}, best = 0, fine = 0;
+      for (auto* Lv : {&E.plan.stage1, &E.plan.stage2})
+        for (const Launch& l : *Lv)
+          for (const Prob& p : l.probs) {
+            double kk = 0;
+            for (int k = 0; k < p.nseg; ++k) {
+              const Seg& g = l.segs[p.seg0 + k];
+              if (!(g.a == 0 && g.abuf == 0)) kk += g.k;
+            }
+            const int tm = tsz(p.m), tn = tsz(p.n);
+            double e3[3] = {0, 0, 0};
+            for (int m0 = 0; m0 < p.m; m0 += tm)
+              for (int n0 = 0; n0 < p.n; n0 += tn) {
+                const int rm = std::min(tm, p.m - m0), rn = std::min(tn, p.n - n0);
+                for (int sh = 0; sh < 3; ++sh) {
+                  const int rh = shapes[sh][0], rw = shapes[sh][1];
+                  e3[sh] += 2.0 * (rh * ((rm + rh - 1) / rh)) * (rw * ((rn + rw - 1) / rw)) * kk;
+                }
+              }
+            for (int sh = 0; sh < 3; ++sh) ex[sh] += e3[sh];
+            best += std::min(e3[0], std::min(e3[1], e3[2]));
+            fine += 2.0 * (8.0 * ((p.m + 7) / 8)) * (8.0 * ((p.n + 7) / 8)) * kk;
+          }
+      std::printf("fp64 regions: useful/executed 16x32 %.3f, 8x64 %.3f, 32x16 %.3f, best per problem %.3f, "
+                  "8x8 %.3f\n", useful / ex[0], useful / ex[1], useful / ex[2], useful / best, useful / fine);
+    }
     std::printf("fp64 padding: useful %.3f TFLOP, executed %.3f TFLOP, efficiency %.3f (exact K %.3f, K by 8 %.3f, "
                 "tiles by 16 up to 64 and K by 8 %.3f, warp skipping %.3f)\n", useful / 1e12, exec_fl / 1e12,
                 useful / exec_fl, useful / exec_k, useful / exec_k8, useful / exec_16, useful / exec_w);
