@@ -1114,7 +1114,7 @@ std::vector<double> Engine::rdm1_su2() {
 }
 
 std::vector<double> Engine::rdm2_sweep() {
-  if (su2) throw StateError("density matrices are measured with the U(1) operators; not available with SU(2)");
+  if (su2) throw StateError("the centre walk measures with the U(1) operators; with SU(2) use rdm2 (probes)");
   // Gamma_pqrs = sum over spins sigma, tau of <a+_{p sigma} a+_{r tau} a_{s tau} a_{q sigma}>,
   // each element measured at the one centre (s1, s2 = s1 + 1) where its four
   // operators split into at most two on the left block (stored C, A, B), any
@@ -1306,7 +1306,8 @@ std::vector<double> Engine::rdm2_sweep() {
 }
 
 std::vector<double> Engine::rdm2() {
-  if (su2) throw StateError("density matrices are measured with the U(1) operators; not available with SU(2)");
+  // Either symmetry: the probes only rebuild the environment with other integrals
+  // and read <H_eff>; Gamma is the spin-summed (spin-free) 2-RDM in both.
   // At fixed MPS the energy is linear in V: with h = 0, e_core = 0 and V the
   // unit tensor on one permutation orbit {pqrs, qprs, pqsr, qpsr, rspq, srpq,
   // rsqp, srqp}, <H_eff> = 1/2 sum over the orbit's distinct elements of

@@ -456,6 +456,14 @@ int main(int argc, char** argv) {
       std::fclose(o4);
       return 0;
     }
+    if (argc >= 4 && std::string(argv[3]) == "rdm2") {
+      const std::vector<double> g = E.rdm2();
+      FILE* o6 = std::fopen(argv[2], "wb");
+      if (!o6) throw std::runtime_error("cannot open output");
+      std::fwrite(g.data(), 8, g.size(), o6);
+      std::fclose(o6);
+      return 0;
+    }
     if (argc >= 4 && std::string(argv[3]) == "rdm1") {
       const std::vector<double> g = E.rdm1();
       FILE* o3 = std::fopen(argv[2], "wb");

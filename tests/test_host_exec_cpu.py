@@ -371,3 +371,32 @@ def test_su2_rdm1_is_the_energy_gradient_in_h(host_exec, tmp_path, L, N, two_s, 
         fd = (energy(h + eps * dh) - energy(h - eps * dh)) / (2 * eps)
         an = g[p, r] + (g[r, p] if p != r else 0.0)
         assert abs(fd - an) <= 1e-8 * max(1.0, abs(an))
+
+
+@pytest.mark.parametrize("L,N,two_s,D", [(5, 5, 1, 8), (5, 4, 2, 8)])
+def test_su2_rdm2_equals_the_fci_rdm_of_the_expanded_state(host_exec, tmp_path, L, N, two_s, D):
+    """The SU(2) two-particle density matrix (environment probes with unit integrals on
+    each permutation orbit of (pq|rs)) against the plain definition: the two-site state
+    expanded to determinants (Clebsch-Gordan map of its reduced elements, the projector of
+    the oracle tests), its 2-RDM by the FCI oracle's E_pq action, averaged over the 8
+    permutations; gamma the same way; and E = sum h gamma + 1/2 sum V Gamma."""
+    from oracle.dmrgsu2 import DMRGSU2, MPSSU2
+    from oracle.fci import FCI
+    from tests.test_oracle_dmrgsu2 import projector
+    mps = MPSSU2.from_raw(q.random_mps_blocks(L, N, two_s, D, q.SYM_SU2, 5, L - 2))
+    h, V = q.make_integrals(L, 11)
+    G = _run_su2(host_exec, tmp_path, mps, h, V, ["rdm2"]).reshape(L, L, L, L)
+    g = _run_su2(host_exec, tmp_path, mps, h, V, ["rdm1"]).reshape(L, L)
+    P, pairs, space = projector(mps)
+    x = np.array([mps.psi[a, b] for a, b in pairs])
+    v = P @ x
+    g1, Gf = FCI(h, V, N, two_s).rdm12(v / np.linalg.norm(v))
+    axes = [(0, 1, 2, 3), (1, 0, 2, 3), (0, 1, 3, 2), (1, 0, 3, 2),
+            (2, 3, 0, 1), (3, 2, 0, 1), (2, 3, 1, 0), (3, 2, 1, 0)]
+    Gs = sum(Gf.transpose(a) for a in axes) / 8.0
+    assert np.abs(G - Gs).max() <= 1e-10
+    assert np.abs(g - g1).max() <= 1e-10
+    sig = mps.psi_to_flat(DMRGSU2(h, V, N, two_s).sigma(mps))
+    psi = mps.psi_to_flat()
+    E = psi @ sig / (psi @ psi)
+    assert abs(np.sum(h * g) + 0.5 * np.sum(V * G) - E) <= 1e-10 * abs(E)
