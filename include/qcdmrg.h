@@ -181,9 +181,12 @@ typedef struct {
   int n_steps;           /* two-site optimisations (2L-4) */
 } qcdmrg_sweep_report;
 
-/* Create a context on cfg->device. Errors: EINVAL (unknown symmetry, negative
- * budgets, pair_switch < 0, sum_gemm outside -1..1; checked before any CUDA
- * call), ECUDA, ENOMEM. */
+/* Create a context on cfg->device: one solver of the paper's spin-adapted DMRG
+ * (Method section) on one GPU (Hardware specific implementations section).
+ * *out receives the handle (owned by the caller, released by
+ * qcdmrg_destroy). Errors: EINVAL (unknown symmetry, negative budgets,
+ * pair_switch < 0, sum_gemm outside -1..1, an SU(2) context with
+ * pair_switch; checked before any CUDA call), ECUDA, ENOMEM. */
 int qcdmrg_create(qcdmrg_ctx** out, const qcdmrg_config* cfg);
 int qcdmrg_destroy(qcdmrg_ctx* ctx);
 /* Message of the last failed call (empty if none); owned by the context. */
@@ -191,18 +194,23 @@ const char* qcdmrg_last_error(const qcdmrg_ctx* ctx);
 
 /*
  * Load the active-space integrals: h (L*L) and V (L^4, (pq|rs) at
- * ((p*L+q)*L+r)*L+s). The arrays are copied. Errors: EINVAL for L < 2,
- * non-finite values or a non-symmetric h.
+ * ((p*L+q)*L+r)*L+s), the one- and two-electron integrals of the model
+ * Hamiltonian of the Method section over the L orbitals of the active space
+ * (CAS(54,36): L = 36, Model system section). The arrays are copied.
+ * Errors: EINVAL for L < 2, non-finite values or a non-symmetric h.
  */
 int qcdmrg_load_integrals(qcdmrg_ctx* ctx, int L, const double* h, const double* V,
                           double e_core);
 
-/* Target particle number and 2Sz (U1). Errors: EINVAL on parity mismatch. */
+/* Target particle number N and two_s: 2S for QCDMRG_SU2 (the spin of the
+ * multiplet, S = 0 for the CAS(54,36) ground state of the Model system
+ * section), 2Sz for QCDMRG_U1. Errors: EINVAL on parity mismatch, a negative
+ * 2S, or a target outside the Fock space of the loaded L. */
 int qcdmrg_set_target(qcdmrg_ctx* ctx, int N, int two_s);
 
 /*
- * Import a mixed-canonical MPS around a two-site centre (layout above). The
- * tensors must be canonical (left tensors U_q with orthonormal columns,
+ * Import a mixed-canonical MPS (Eq. (mps) of the Method section) around a
+ * two-site centre (layout above). The tensors must be canonical (left tensors U_q with orthonormal columns,
  * right tensors V_q with orthonormal rows); they are copied to the device.
  * n is the number of doubles in data. Errors: EINVAL (layout mismatch),
  * ESTATE (integrals or target missing).
@@ -262,7 +270,10 @@ int qcdmrg_set_psi(qcdmrg_ctx* ctx, const double* psi, size_t n);
  * Renormalize the left block up to the centre and the right block down to
  * it (the operator renormalization of every truncation step, replayed for
  * the imported tensors), enlarge both by their dot site and build the
- * H_eff task list. Errors: ESTATE (no MPS), ECUDA, ENOMEM.
+ * H_eff task list. These renormalized operators are the O(N^2 D^2) memory of
+ * the Method section's cost model. Renormalization has no entry point of its
+ * own: this call runs it from both ends, and qcdmrg_truncate runs it for the
+ * grown block of each step. Errors: ESTATE (no MPS), ECUDA, ENOMEM.
  */
 int qcdmrg_build_env(qcdmrg_ctx* ctx);
 
@@ -285,23 +296,29 @@ int qcdmrg_psi_layout(const qcdmrg_ctx* ctx, int* blocks, int cap, int* nblocks,
  * product), dpsi = dE/dpsi = 2 (H_eff psi - E psi)/<psi|psi> (psi size),
  * gamma1 = dE/dh (L*L, as qcdmrg_rdm1: needs the centre at (L-2, L-1)),
  * gamma2 = 2 dE/dV for 8-fold symmetric V (L^4, as qcdmrg_rdm2: L^4/8
- * environment builds, for L <= 10; beyond, the permutation average of
- * qcdmrg_rdm2_sweep). The derivatives the paper's DMRG-SCF needs (New
+ * environment builds, for L <= 10, either symmetry; beyond, QCDMRG_U1 only,
+ * the permutation average of qcdmrg_rdm2_sweep). The derivatives the paper's DMRG-SCF needs (New
  * benchmark system section). Errors: ESTATE, EINVAL, ENOMEM, ECUDA.
  */
 int qcdmrg_energy_grad(qcdmrg_ctx* ctx, double* energy, double* dpsi, double* gamma1, double* gamma2);
 
 /*
- * sigma = H_eff psi on host arrays of psi_size elements (layout above).
- * precision: one of QCDMRG_FP64, _TF32, _BF16, _BF16X3. Errors: ESTATE (no
- * environment), EINVAL, ETIMEOUT (a bounded wait of a tensor-core kernel gave
- * up; sigma is then not valid).
+ * sigma = H_eff psi on host arrays of psi_size elements (layout above): the
+ * sigma step of the iterative diagonalization (Numerical procedure section),
+ * whose block contractions are the O(N^4 D^3) compute of the Method section's
+ * cost model and the FLOP rate of the Numerical results. precision: one of
+ * QCDMRG_FP64, _TF32, _BF16, _BF16X3 (the mixed-precision forms stand where
+ * the paper emulates FP64 on tensor cores, Hardware specific implementations
+ * section). The copies between host and device are part of the call. Errors:
+ * ESTATE (no environment), EINVAL, ETIMEOUT (a bounded wait of a tensor-core
+ * kernel gave up; sigma is then not valid).
  */
 int qcdmrg_apply_heff(qcdmrg_ctx* ctx, int precision, const double* psi, double* sigma);
 
 /* Same on device arrays, enqueued on stream (a cudaStream_t; NULL is the
  * legacy default stream); returns after enqueueing. psi and sigma must not
- * overlap and must stay alive until the stream reaches the work. */
+ * overlap and must stay alive until the stream reaches the work. A bounded
+ * device wait that gave up is reported by qcdmrg_check_device. */
 int qcdmrg_apply_heff_dev(qcdmrg_ctx* ctx, int precision, const void* psi, void* sigma,
                           void* stream);
 
@@ -354,7 +371,8 @@ int qcdmrg_rdm1(qcdmrg_ctx* ctx, double* gamma);
  * system section). Computed by exact linearity in V: for each permutation
  * orbit the environment is rebuilt with h = 0 and unit integrals on that
  * orbit, and <H_eff> at the centre gives half the orbit's sum of Gamma; that
- * is L^4/8 environment builds, meant for small active spaces. Any centre.
+ * is L^4/8 environment builds, meant for small active spaces. Any centre,
+ * either symmetry (with QCDMRG_SU2 the spin-free Gamma of the multiplet).
  * The context's integrals and environment are restored before returning.
  * Errors: ESTATE (no environment), EINVAL, ENOMEM, ECUDA.
  */
@@ -373,7 +391,7 @@ int qcdmrg_rdm2(qcdmrg_ctx* ctx, double* gamma2);
  * walks the chain once by exact moves (every state above the rounding noise of
  * its sector's density-matrix eigenvalues is kept); afterwards the MPS (site
  * tensors, bonds, psi at its centre) is restored as it was and the environment
- * rebuilt once. With
+ * rebuilt once. QCDMRG_U1 only (ESTATE with QCDMRG_SU2). With
  * pair_switch set, the environment is rebuilt with normal pairs on the left
  * for the walk and the switched one restored afterwards.
  * Errors: ESTATE (no environment), EINVAL, ENOMEM, ECUDA.
@@ -382,14 +400,19 @@ int qcdmrg_rdm2_sweep(qcdmrg_ctx* ctx, double* gamma2);
 
 /* Diagonal of H_eff at the centre (psi layout, n = psi size), as used by the
  * Davidson preconditioner: sum over terms of c_t diag(O_L) (x) diag(O_R)
- * restricted to diagonal quantum-number blocks. */
+ * restricted to diagonal quantum-number blocks. The paper names Lanczos
+ * (Numerical procedure section), which needs no preconditioner: this call has
+ * no counterpart there. Errors: ESTATE, EINVAL (n differs from the psi size). */
 int qcdmrg_heff_diag(qcdmrg_ctx* ctx, double* out, size_t n);
 
 /*
  * Davidson solve of the two-site problem at the centre (FP64 vectors, FP64
  * Gram-Schmidt and subspace eigenproblem; H psi in the precision the policy
  * selects), starting from the current wavefunction; the converged Ritz vector
- * replaces it. Preconditioner (diag(H_eff) - theta)^-1 with |.| floored at
+ * replaces it. The iterative diagonalization of the Numerical procedure
+ * section (residual 1e-6); its mixed policy stands for the emulated FP64 of
+ * the Mixed precision and hardware section, with the final energy from an
+ * FP64 product. Preconditioner (diag(H_eff) - theta)^-1 with |.| floored at
  * 1e-8; restart keeps the Ritz vector. Any pointer may be NULL. Errors:
  * ESTATE, ENOTCONV (results still written), ETIMEOUT.
  */
@@ -397,7 +420,9 @@ int qcdmrg_davidson(qcdmrg_ctx* ctx, const qcdmrg_dav_opts* opts, double* energy
                     int* iters);
 
 /*
- * Truncation step of the sweep: density matrix of the two-site wavefunction
+ * Truncation step of the sweep (the truncation error of the Method section:
+ * the discarded Schmidt weight; D fixed per run as in the Numerical
+ * procedure section, counted in multiplets for QCDMRG_SU2): density matrix of the two-site wavefunction
  * per quantum-number sector (rho = Psi Psi^T for dir = +1, Psi^T Psi for
  * dir = -1), FP64 eigendecomposition, the D states of largest weight kept
  * across sectors (ties: weight, then label, then in-sector order; weights
@@ -409,11 +434,15 @@ int qcdmrg_davidson(qcdmrg_ctx* ctx, const qcdmrg_dav_opts* opts, double* energy
  */
 int qcdmrg_truncate(qcdmrg_ctx* ctx, int D, int dir, double* trunc_err);
 
-/* Move the centre without truncation (only weights <= 1e-14, rounding noise, dropped). */
+/* Move the centre to sites (target, target+1) without truncation (only
+ * weights <= 1e-14, rounding noise, dropped), renormalizing each grown
+ * block (Method section). Errors: ESTATE, EINVAL (target outside 0..L-2). */
 int qcdmrg_move_center(qcdmrg_ctx* ctx, int target);
 
 /*
- * One full sweep: the centre is first moved (exactly) to sites (0, 1), then
+ * One full sweep of the Numerical procedure section (the paper sweeps until
+ * the energy of three sweeps agrees to 1e-5; the caller repeats this call):
+ * the centre is first moved (exactly) to sites (0, 1), then
  * optimised and moved right to (L-2, L-1), then back to (0, 1): 2L-4 two-site
  * optimisations, each a Davidson solve followed by qcdmrg_truncate. Errors:
  * ESTATE, EINVAL, ENOTCONV (a Davidson solve hit max_iter; the sweep completes).
@@ -427,7 +456,9 @@ int qcdmrg_check_device(qcdmrg_ctx* ctx);
 /*
  * Batched H_eff psi in one CUDA graph: all quantum-number blocks of one or
  * several independent H_eff psi products in one replay, instead of one
- * product after another. The H_eff psi of each context (memset of sigma plus its
+ * product after another. The paper runs one problem at a time and names no
+ * batching; this is the launch-side form of its GPU-accelerated sigma step
+ * (Hardware specific implementations section). The H_eff psi of each context (memset of sigma plus its
  * grouped-GEMM launches) is captured once, contexts as parallel branches,
  * with psi[i] and sigma[i] (device arrays of each context's psi size) baked
  * into the graph; qcdmrg_graph_launch replays it on a stream. The contexts'
@@ -444,7 +475,8 @@ int qcdmrg_graph_launch(qcdmrg_graph* graph, void* stream);
 int qcdmrg_graph_info(const qcdmrg_graph* graph, double* flops, int* nodes);
 int qcdmrg_graph_destroy(qcdmrg_graph* graph);
 
-/* Counters of the last calls. */
+/* Counters of the last calls (flop counts, device times, bytes): the FLOP
+ * rate and wall times the Numerical results section reports. */
 int qcdmrg_stats(const qcdmrg_ctx* ctx, qcdmrg_stats_t* out);
 
 #ifdef __cplusplus
