@@ -48,7 +48,7 @@ extern "C" {
 #define QCDMRG_SU2 1 /* SU(2) spin adaptation (the paper's spin-adapted DMRG, Method section;
                         bond dimensions D_SU(2) count multiplets, Numerical procedure section):
                         sector labels (N, 2S), operators stored as reduced matrix elements
-                        between multiplets, the target's two_s is 2S; needs pair_switch = 0 */
+                        between multiplets, the target's two_s is 2S */
 
 /* precision of the block contractions (all accumulate sigma in FP64 across
  * problems; inside one output tile the tensor-core forms accumulate in FP32) */
@@ -75,8 +75,12 @@ typedef struct {
                            pair operators A_kl, B_kl of their own modes; the others keep the
                            complementary P_ij, Q_il of the modes across the cut. At L/2 this is
                            the N/2 rule: the pairs are stored on the side with fewer modes,
-                           which halves the operator volume of a sweep environment. 0 keeps
-                           normal pairs on the left at every cut. Negative: QCDMRG_EINVAL */
+                           which halves the operator volume of a sweep environment (SU(2),
+                           CAS(54,36) shape: 2.1-2.4x less environment, 3.1-3.9x fewer
+                           environment-build flops). Both symmetries. A switch one cut past
+                           the centre keeps the centre's complementary pairs as references
+                           instead of sums. 0 keeps normal pairs on the left at every cut.
+                           Negative: QCDMRG_EINVAL */
   int sum_gemm;         /* renormalization-side sums of many stored operators (the S', H', P',
                            Q' of an enlarged block): 1 runs each group of at least 8 as a GEMM of
                            a coefficient matrix with the operators' blocks, -1 sums them block

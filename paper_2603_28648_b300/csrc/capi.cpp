@@ -98,8 +98,6 @@ int qcdmrg_create(qcdmrg_ctx** out, const qcdmrg_config* cfg) {
   if (!out || !cfg) return QCDMRG_EINVAL;
   *out = nullptr;
   if (cfg->symmetry != QCDMRG_U1 && cfg->symmetry != QCDMRG_SU2) return QCDMRG_EINVAL;
-  // the spin-adapted rules keep normal pairs on the left at every cut
-  if (cfg->symmetry == QCDMRG_SU2 && cfg->pair_switch != 0) return QCDMRG_EINVAL;
   // the configuration is checked before any CUDA call
   if (!(cfg->hbm_budget_gb >= 0) || !(cfg->tmp_budget_gb >= 0) || cfg->pair_switch < 0 || cfg->sum_gemm < -1 ||
       cfg->sum_gemm > 1 || cfg->tile_chunk < 0 || cfg->tile_chunk > 65536)

@@ -324,11 +324,13 @@ HeffPlan plan_heff(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay,
 // Same for an arbitrary list of operator-product terms (expectation values).
 HeffPlan plan_terms(const Enlarged& Lp, const Enlarged& Rp, const PsiLayout& lay,
                     const std::vector<CenterTerm>& terms, int64_t tmp_budget);
-// SU(2) spin-adapted rules (rules_su2.cpp). Left blocks keep the normal
-// operators c_p, A^k_pq, B^k_pq (p <= q) of their orbitals, right blocks the
-// complementary T_m, P^k_pq, Q^k_pq (p <= q) of the orbitals to their left;
-// both keep c_p of their own orbitals and their Hamiltonian.
-void enlarge_su2(const EnvBlock& B, const Integrals& I, Executor& ex, Enlarged& out);
+// SU(2) spin-adapted rules (rules_su2.cpp). Every block keeps c_p of its own
+// orbitals, T_m of the orbitals outside it and its Hamiltonian; the pair
+// operators are the normal A^k_pq, B^k_pq (p <= q) of its own orbitals or the
+// complementary P^k_pq, Q^k_pq (p <= q) of the orbitals outside it, on the
+// side normal_pairs() gives (as in the U(1) rules; a block with normal pairs
+// can become complementary when enlarged, the reverse is not possible).
+void enlarge_su2(const EnvBlock& B, const Integrals& I, Executor& ex, Enlarged& out, bool normal);
 std::vector<CenterTerm> center_terms_su2(const Enlarged& Lp, const Enlarged& Rp, const Integrals& I);
 // SU(2) adjoint tensor of a view whose references index sub-blocks of pb
 // (enlarged) or sectors of basis (renormalized): transposed references with

@@ -243,7 +243,7 @@ void Engine::build_env() {
   for (int p = 0; p < center; ++p) {
     Enlarged E;
     E.batched = batched_sums();
-    if (su2) enlarge_su2(lenv[p], I, *ex, E);
+    if (su2) enlarge_su2(lenv[p], I, *ex, E, normal_at(true, p + 1));
     else enlarge(lenv[p], I, *ex, E, &fl, normal_at(true, p + 1));
     EnvBlock nb;
     nb.cut = p + 1;
@@ -257,7 +257,7 @@ void Engine::build_env() {
   for (int p = L - 1; p >= center + 2; --p) {
     Enlarged E;
     E.batched = batched_sums();
-    if (su2) enlarge_su2(renv[p + 1], I, *ex, E);
+    if (su2) enlarge_su2(renv[p + 1], I, *ex, E, normal_at(false, p));
     else enlarge(renv[p + 1], I, *ex, E, &fl, normal_at(false, p));
     EnvBlock nb;
     nb.cut = p;
@@ -281,8 +281,8 @@ void Engine::prepare_center() {
   ensure_resident(renv.at(center + 2));
   Lp.batched = Rp.batched = batched_sums();
   if (su2) {
-    enlarge_su2(lenv.at(center), I, *ex, Lp);
-    enlarge_su2(renv.at(center + 2), I, *ex, Rp);
+    enlarge_su2(lenv.at(center), I, *ex, Lp, normal_at(true, center + 1));
+    enlarge_su2(renv.at(center + 2), I, *ex, Rp, normal_at(false, center + 1));
   } else {
     enlarge(lenv.at(center), I, *ex, Lp, &fl, normal_at(true, center + 1));
     enlarge(renv.at(center + 2), I, *ex, Rp, &fl, normal_at(false, center + 1));
@@ -1005,7 +1005,8 @@ double Engine::expect(const std::vector<CenterTerm>& terms) {
 }
 
 std::vector<double> Engine::rdm1() {
-  if (su2) return rdm1_su2();
+  // (SU(2): rdm1_su2, after the same rebuild when the blocks at the centre hold
+  // complementary pairs on the left.)
   // At the centre (L-2, L-1) the left enlarged block L' holds the normal
   // operators a+_k a_l of every spin-orbital of sites 0..L-2, and the right
   // enlarged block is the last site alone, so every E_pq is a product of
@@ -1034,6 +1035,7 @@ std::vector<double> Engine::rdm1() {
     build_env();
     return g;
   }
+  if (su2) return rdm1_su2();
   const double nrm = ex->dot(dpsi, dpsi, lay.size);
   auto get = [](const Enlarged& E, Key k) -> const OpView* {
     auto it = E.ops.find(k);

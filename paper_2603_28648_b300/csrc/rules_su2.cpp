@@ -17,14 +17,20 @@
 //   Q^0_ij = sum_{k,l} (2 (ij|kl) - (il|kj)) B^0_kl, Q^1_ij = sqrt(3) sum_{k,l} (il|kj) B^1_kl
 //   (sums over the block's orbitals; P^k_rp = (-1)^k P^k_pr, Q^k_ji = (-1)^k adjoint(Q^k_ij),
 //   stored for p <= r, i <= j).
-// Left blocks keep c, A, B of their orbitals, T of the orbitals to their right
-// and H; right blocks keep c of their orbitals, T, P, Q of the orbitals to
-// their left and H. At a cut L|R the Hamiltonian is the sum of scalar
-// couplings (each "+ h.c." adds the Hermitian conjugate, [X x Y]^0 ->
-// e [X~ x Y~]^0 with e = -1 for two odd operators):
+// Every block keeps c of its orbitals, T of the orbitals outside it and H;
+// the pair operators are A, B of its own orbitals (normal) or P, Q of the
+// orbitals outside it (complementary). Left blocks at cuts up to the switch
+// and right blocks beyond it hold normal pairs, so that at every cut exactly
+// one side does; without a switch the normal pairs are on the left everywhere,
+// with the switch at L/2 they are on the side with fewer orbitals (the N/2
+// rule). At a cut L|R with normal pairs on the left the Hamiltonian is the sum
+// of scalar couplings (each "+ h.c." adds the Hermitian conjugate,
+// [X x Y]^0 -> e [X~ x Y~]^0 with e = -1 for two odd operators):
 //   H = H_L + H_R - sqrt(2) sum_{p in L} [c_p x T_p]^0 - sqrt(2) sum_{m in R} [T_m x c_m]^0 + h.c.
 //     + sum_{p<=r in L} f_pr (-1)^(1+k) sqrt(2k+1) [A^k_pr x P^k_pr]^0 + h.c.   (f = 1, or 1/2 at p = r)
-//     + sum_{i<j in L} [B^k_ij x Q^k_ij]^0 + h.c. + sum_i [B^k_ii x Q^k_ii]^0.
+//     + sum_{i<j in L} [B^k_ij x Q^k_ij]^0 + h.c. + sum_i [B^k_ii x Q^k_ii]^0;
+// with normal pairs on the right the pair sums run over R with the same
+// coefficients, [P^k_pr x A^k_pr]^0 and [Q^k_ij x B^k_ij]^0.
 // The reduced element of a product O_1 O_2 of operators on the two parts of a
 // coupled basis (part 1 first in the fermion order) is the 9j factor of
 // su2::coupled times (-1)^(parity of O_2 x particle number of the part-1 ket).
@@ -458,12 +464,18 @@ OpView adjoint_su2(const OpView& o, const ProdBasis* pb, const Basis* basis) {
   return t;
 }
 
-void enlarge_su2(const EnvBlock& B, const Integrals& I, Executor& ex, Enlarged& E) {
+void enlarge_su2(const EnvBlock& B, const Integrals& I, Executor& ex, Enlarged& E, bool normal) {
+  // normal: the enlarged block keeps the pair operators A^k, B^k of its own
+  // orbitals; otherwise P^k, Q^k of the orbitals outside it. A block with
+  // normal pairs may switch here (its pairs then form the block-block part of
+  // P' and Q'); complementary pairs cannot become normal.
+  if (normal && !B.normal) throw std::logic_error("enlarge_su2: complementary pairs cannot become normal");
   const int L = I.L;
-  E.left = B.left;
-  E.normal = B.left;
+  const bool left = B.left;
+  E.left = left;
+  E.normal = normal;
   E.ops.clear();
-  E.pb = make_prod(B.basis, B.left);
+  E.pb = make_prod(B.basis, left);
   Ctx2 x(B, I, E);
   const SiteOps& S = site();
   const S3& I3 = S.I;
@@ -479,50 +491,73 @@ void enlarge_su2(const EnvBlock& B, const Integrals& I, Executor& ex, Enlarged& 
     as[k] = su2::assoc(1, 1, 1, 0, 2 * k, 1);
   }
   auto sgnk = [](int k) { return (k & 1) ? -1.0 : 1.0; };
-  if (B.left) {
-    const int c = B.cut;   // X = [0, c), site o = c
-    const int o = c;
-    E.cut = c + 1;
-    x.view(Key(F_I), {mk(nullptr, false, I3, 0, 0, 0, 1.0, false)}, false, 0);
-    for (int p = 0; p < c; ++p)
-      if (auto C = x.get(Key(F_C, p))) x.view(Key(F_C, p), {mk(C, false, I3, 1, 0, 1, 1.0, false)}, true, 1);
-    x.view(Key(F_C, o), {mk(nullptr, false, S.c, 0, 1, 1, 1.0, true)}, true, 1);
+  // the added site o, the block's orbitals [b0, b1), the orbitals outside the
+  // enlarged block [u0, u1); on a right block the site part comes first, and
+  // an even rank-k operator X and an odd spin-1/2 one Y couple as
+  // [X x Y]^1/2 = (-1)^k [Y x X]^1/2 (they commute, Clebsch-Gordan symmetry)
+  const int o = left ? B.cut : B.cut - 1;
+  const int b0 = left ? 0 : o + 1, b1 = left ? o : L;
+  const int u0 = left ? o + 1 : 0, u1 = left ? L : o;
+  E.cut = left ? o + 1 : o;
+  auto key2 = [](int f, int p, int q, int K) { return p <= q ? Key(f, p, q, K) : Key(f, q, p, K); };
+  x.view(Key(F_I), {mk(nullptr, false, I3, 0, 0, 0, 1.0, false)}, false, 0);
+  for (int p = b0; p < b1; ++p)
+    if (auto C = x.get(Key(F_C, p))) x.view(Key(F_C, p), {mk(C, false, I3, 1, 0, 1, 1.0, !left)}, true, 1);
+  x.view(Key(F_C, o), {mk(nullptr, false, S.c, 0, 1, 1, 1.0, left)}, true, 1);
+  if (normal) {
+    // A'^k, B'^k of the enlarged block's orbitals (p <= q): the block's own,
+    // the block orbital with the site ([c_p x c_o], [c_p x d_o] on a left
+    // block; [c_o x c_q], [c_o x d_q] on a right one) and the site's
     for (int k = 0; k < 2; ++k) {
       const int K = 2 * k;
-      for (int p = 0; p < c; ++p)
-        for (int q = p; q < c; ++q) {
+      for (int p = b0; p < b1; ++p)
+        for (int q = p; q < b1; ++q) {
           if (auto A = x.get(Key(F_A, p, q, K))) x.view(Key(F_A, p, q, K), {mk(A, false, I3, K, 0, K, 1.0, false)}, false, K);
           if (auto Bv = x.get(Key(F_B, p, q, K))) x.view(Key(F_B, p, q, K), {mk(Bv, false, I3, K, 0, K, 1.0, false)}, false, K);
         }
-      for (int p = 0; p < c; ++p)
+      for (int p = b0; p < b1; ++p)
         if (auto C = x.get(Key(F_C, p))) {
-          x.view(Key(F_A, p, o, K), {mk(C, false, S.c, 1, 1, K, 1.0, true)}, false, K);   // [c_p x c_o]^k
-          x.view(Key(F_B, p, o, K), {mk(C, false, S.d, 1, 1, K, 1.0, true)}, false, K);   // [c_p x d_o]^k
+          if (left) {
+            x.view(Key(F_A, p, o, K), {mk(C, false, S.c, 1, 1, K, 1.0, true)}, false, K);
+            x.view(Key(F_B, p, o, K), {mk(C, false, S.d, 1, 1, K, 1.0, true)}, false, K);
+          } else {
+            x.view(Key(F_A, o, p, K), {mk(C, false, S.c, 1, 1, K, 1.0, true)}, false, K);
+            x.view(Key(F_B, o, p, K), {mk(C, true, S.c, 1, 1, K, 1.0, true)}, false, K);
+          }
         }
       x.view(Key(F_B, o, o, K), {mk(nullptr, false, S.B[k], 0, K, K, 1.0, false)}, false, K);
     }
     x.view(Key(F_A, o, o, 0), {mk(nullptr, false, S.A0, 0, 0, 0, 1.0, false)}, false, 0);
-    // T'_m, m > o
-    for (int m = o + 1; m < L; ++m) {
-      std::vector<C2> cs;
-      if (auto T = x.get(Key(F_S, m))) cs.push_back(mk(T, false, I3, 1, 0, 1, 1.0, false));
-      cs.push_back(mk(nullptr, false, site_T(I, m, o), 0, 1, 1, 1.0, true));
-      for (int q = 0; q < c; ++q) {
-        auto Cq = x.get(Key(F_C, q));
-        if (!Cq) continue;
-        // (b) q = r = o, s = q in X: (mq|oo) [d_q x n_o]^1/2
-        cs.push_back(mk(Cq, true, S.n, 1, 0, 1, V(I, m, q, o, o), false));
-        // (e) r = s = o: (mo|qo) E_qo d_o = -sqrt(2) assoc_0 [c_q x [d_o x d_o]^0]^1/2
-        cs.push_back(mk(Cq, false, S.DD0, 1, 0, 1, -SQ2 * as[0] * V(I, m, o, q, o), false));
-        // (f) q = s = o, r = q in X: (mo|oq) E_oq d_o; reordered d_q c_o d_o (sign -1),
-        // tree (1, (0 2)K): -sqrt(2) (-1) (-1)^k swap23_K [d_q x B^K_oo]^1/2
-        for (int k = 0; k < 2; ++k)
-          cs.push_back(mk(Cq, true, S.B[k], 1, 2 * k, 1, SQ2 * sgnk(k) * sw[k] * V(I, m, o, o, q), false));
-      }
-      for (int k = 0; k < 2; ++k) {
-        const int K = 2 * k;
-        for (int p = 0; p < c; ++p)
-          for (int q = p; q < c; ++q) {
+  }
+  // T'_m for the orbitals m outside the enlarged block
+  for (int m = u0; m < u1; ++m) {
+    std::vector<C2> cs;
+    if (auto T = x.get(Key(F_S, m))) cs.push_back(mk(T, false, I3, 1, 0, 1, 1.0, !left));
+    cs.push_back(mk(nullptr, false, site_T(I, m, o), 0, 1, 1, 1.0, left));
+    // one block operator, two on the site
+    for (int q = b0; q < b1; ++q) {
+      auto Cq = x.get(Key(F_C, q));
+      if (!Cq) continue;
+      // (b) q = r = o, s = q in the block: (mq|oo) [d_q x n_o]^1/2 (n has rank 0)
+      cs.push_back(mk(Cq, true, S.n, 1, 0, 1, V(I, m, q, o, o), !left));
+      // (e) r = s = o: (mo|qo) E_qo d_o = -sqrt(2) assoc_0 [c_q x [d_o x d_o]^0]^1/2
+      // (left); on a right block reordered d_o d_o c_q (sign +1), tree ((1 2)0, 0)
+      cs.push_back(mk(Cq, false, S.DD0, 1, 0, 1, -SQ2 * as[0] * V(I, m, o, q, o), !left));
+      // (f) q = s = o: (mo|oq) E_oq d_o. Left: reordered d_q c_o d_o (sign -1),
+      // tree (1, (0 2)K): -sqrt(2) (-1) (-1)^k swap23_K [d_q x B^K_oo]^1/2.
+      // Right: reordered c_o d_o d_q (sign -1), tree ((0 2)K, 1): sqrt(2) swap23_K [B^K_oo x d_q]
+      for (int k = 0; k < 2; ++k)
+        cs.push_back(mk(Cq, true, S.B[k], 1, 2 * k, 1, SQ2 * (left ? sgnk(k) : 1.0) * sw[k] * V(I, m, o, o, q), !left));
+    }
+    // two block operators, one on the site
+    for (int k = 0; k < 2; ++k) {
+      const int K = 2 * k;
+      if (B.normal) {
+        // from the block's pairs, written block part first ([X x Y]); a right
+        // block takes the site part first, hence the factor (-1)^k there
+        const double rs = left ? 1.0 : sgnk(k);
+        for (int p = b0; p < b1; ++p)
+          for (int q = p; q < b1; ++q) {
             // (a) s = o: (mo|pq) E_pq d_o = -sqrt(2) [B^0_pq x d_o]; B^0_qp = adjoint(B^0_pq)
             // (c) r = o: (ms|qo) E_qo d_s, reordered c_q d_s d_o (sign -1), tree ((0 2)K, 1):
             //     -sqrt(2) (-1) swap23_K [B^K_qs x d_o]; B^K_sq = (-1)^k adjoint(B^K_qs)
@@ -533,8 +568,8 @@ void enlarge_su2(const EnvBlock& B, const Integrals& I, Executor& ex, Enlarged& 
                 direct += -SQ2 * V(I, m, o, p, q);
                 if (p != q) adj += -SQ2 * V(I, m, o, q, p);
               }
-              cs.push_back(mk(Bv, false, S.d, K, 1, 1, direct, true));
-              if (adj != 0.0) cs.push_back(mk(Bv, true, S.d, K, 1, 1, adj, true));
+              cs.push_back(mk(Bv, false, S.d, K, 1, 1, rs * direct, left));
+              if (adj != 0.0) cs.push_back(mk(Bv, true, S.d, K, 1, 1, rs * adj, left));
             }
             // (d) q = o: (ms|or) E_or d_s, reordered d_r d_s c_o (sign +1), tree ((1 2)K, 0):
             //     -sqrt(2) (-1)^k assoc_K [[d_r x d_s]^K x c_o]; [d_r x d_s]^K = -adjoint(A^K_rs),
@@ -542,29 +577,111 @@ void enlarge_su2(const EnvBlock& B, const Integrals& I, Executor& ex, Enlarged& 
             if (auto A = x.get(Key(F_A, p, q, K))) {
               double w = V(I, m, q, o, p);                   // (r, s) = (p, q)
               if (p != q) w += sgnk(k) * V(I, m, p, o, q);   // (r, s) = (q, p)
-              cs.push_back(mk(A, true, S.c, K, 1, 1, SQ2 * sgnk(k) * as[k] * w, true));
+              cs.push_back(mk(A, true, S.c, K, 1, 1, rs * SQ2 * sgnk(k) * as[k] * w, left));
             }
           }
+      } else {
+        // from the block's complementary pairs of (m, o):
+        //   (a) + (c) = -1/sqrt(2) [d_o x Q^k_mo]^1/2,  (d) = -sqrt(2) assoc_K [c_o x P^K_mo]^1/2;
+        // a left block stores (o, m) (o < m): Q^k_mo = (-1)^k adjoint(Q^k_om),
+        // P^k_mo = (-1)^k P^k_om, and the block part comes first ((-1)^k again)
+        if (auto Q = x.get(key2(F_Q, m, o, K))) cs.push_back(mk(Q, left, S.d, K, 1, 1, -1.0 / SQ2, left));
+        if (auto P = x.get(key2(F_P, m, o, K))) cs.push_back(mk(P, false, S.c, K, 1, 1, -SQ2 * as[k], left));
       }
-      x.materialize(Key(F_S, m), std::move(cs), true, 1);
     }
-    // H' = H_X + H_o + the terms of H across the cut X | o
-    {
-      std::vector<C2> cs;
-      if (auto H = x.get(Key(F_H))) cs.push_back(mk(H, false, I3, 0, 0, 0, 1.0, false));
-      cs.push_back(mk(nullptr, false, site_H(I, o), 0, 0, 0, 1.0, false));
-      for (int p = 0; p < c; ++p)
-        if (auto C = x.get(Key(F_C, p))) {
-          const S3 T = site_T(I, p, o);
-          cs.push_back(mk(C, false, T, 1, 1, 0, -SQ2, true));
-          cs.push_back(mk(C, true, s_adj(T, 1), 1, 1, 0, SQ2, true));
+    x.materialize(Key(F_S, m), std::move(cs), true, 1);
+  }
+  if (!normal) {
+    // P'^k_pr, Q'^k_ij for p <= r, i <= j outside the enlarged block:
+    //   P^k_pr = sum_{s,q} (pq|rs) [d_s x d_q]^k,  Q^k_ij = sum_{k,l} q^k_ijkl [c_k x d_l]^k
+    // over the block's orbitals and the site; the block-block part is the
+    // block's own P, Q, or (at the switch) formed from its A, B:
+    //   [d_a x d_b]^k = -adjoint(A^k_ab), [d_b x d_a]^k = (-1)^k [d_a x d_b]^k (a != b),
+    //   [c_b x d_a]^k = (-1)^k adjoint(B^k_ab)
+    for (int k = 0; k < 2; ++k) {
+      const int K = 2 * k;
+      for (int p = u0; p < u1; ++p)
+        for (int r = p; r < u1; ++r) {
+          std::vector<C2> cs;
+          if (!B.normal) {
+            if (auto P = x.get(Key(F_P, p, r, K))) cs.push_back(mk(P, false, I3, K, 0, K, 1.0, false));
+          } else {
+            for (int a = b0; a < b1; ++a)
+              for (int b = a; b < b1; ++b)
+                if (auto A = x.get(Key(F_A, a, b, K))) {
+                  const double w = V(I, p, b, r, a) + (a != b ? sgnk(k) * V(I, p, a, r, b) : 0.0);
+                  if (w != 0.0) cs.push_back(mk(A, true, I3, K, 0, K, -w, false));
+                }
+          }
+          if (k == 0) cs.push_back(mk(nullptr, false, S.DD0, 0, 0, 0, V(I, p, o, r, o), false));
+          // one operator on the block (orbital a), one on the site: left
+          // [d_a x d_o]^k with (po|ra) + (-1)^k (pa|ro); right [d_o x d_a]^k
+          // with (pa|ro) + (-1)^k (po|ra)
+          for (int a = b0; a < b1; ++a)
+            if (auto Ca = x.get(Key(F_C, a))) {
+              const double w = left ? V(I, p, o, r, a) + sgnk(k) * V(I, p, a, r, o)
+                                    : V(I, p, a, r, o) + sgnk(k) * V(I, p, o, r, a);
+              if (w != 0.0) cs.push_back(mk(Ca, true, S.d, 1, 1, K, w, true));
+            }
+          x.materialize(Key(F_P, p, r, K), std::move(cs), false, K);
         }
-      if (auto T = x.get(Key(F_S, o))) {
-        cs.push_back(mk(T, false, S.c, 1, 1, 0, -SQ2, true));
-        cs.push_back(mk(T, true, S.d, 1, 1, 0, SQ2, true));
+      for (int i = u0; i < u1; ++i)
+        for (int j = i; j < u1; ++j) {
+          std::vector<C2> cs;
+          if (!B.normal) {
+            if (auto Q = x.get(Key(F_Q, i, j, K))) cs.push_back(mk(Q, false, I3, K, 0, K, 1.0, false));
+          } else {
+            for (int a = b0; a < b1; ++a)
+              for (int b = a; b < b1; ++b)
+                if (auto Bv = x.get(Key(F_B, a, b, K))) {
+                  const double w1 = qcoef(I, K, i, j, a, b);
+                  if (w1 != 0.0) cs.push_back(mk(Bv, false, I3, K, 0, K, w1, false));
+                  const double w2 = a != b ? sgnk(k) * qcoef(I, K, i, j, b, a) : 0.0;
+                  if (w2 != 0.0) cs.push_back(mk(Bv, true, I3, K, 0, K, w2, false));
+                }
+          }
+          cs.push_back(mk(nullptr, false, S.B[k], 0, K, K, qcoef(I, K, i, j, o, o), false));
+          for (int a = b0; a < b1; ++a)
+            if (auto Ca = x.get(Key(F_C, a))) {
+              if (left) {
+                // (k, l) = (a, o): q^k_ijao [c_a x d_o]^k; (o, a): q^k_ijoa [c_o x d_a]^k = (-1)^k q^k_ijoa [d_a x c_o]^k
+                const double w1 = qcoef(I, K, i, j, a, o);
+                if (w1 != 0.0) cs.push_back(mk(Ca, false, S.d, 1, 1, K, w1, true));
+                const double w2 = sgnk(k) * qcoef(I, K, i, j, o, a);
+                if (w2 != 0.0) cs.push_back(mk(Ca, true, S.c, 1, 1, K, w2, true));
+              } else {
+                // (k, l) = (o, a): q^k_ijoa [c_o x d_a]^k; (a, o): q^k_ijao [c_a x d_o]^k = (-1)^k q^k_ijao [d_o x c_a]^k
+                const double w1 = qcoef(I, K, i, j, o, a);
+                if (w1 != 0.0) cs.push_back(mk(Ca, true, S.c, 1, 1, K, w1, true));
+                const double w2 = sgnk(k) * qcoef(I, K, i, j, a, o);
+                if (w2 != 0.0) cs.push_back(mk(Ca, false, S.d, 1, 1, K, w2, true));
+              }
+            }
+          x.materialize(Key(F_Q, i, j, K), std::move(cs), false, K);
+        }
+    }
+  }
+  // H' = H of the block + H of the site + the terms of H across the block | site cut
+  {
+    std::vector<C2> cs;
+    if (auto H = x.get(Key(F_H))) cs.push_back(mk(H, false, I3, 0, 0, 0, 1.0, false));
+    cs.push_back(mk(nullptr, false, site_H(I, o), 0, 0, 0, 1.0, false));
+    // -sqrt(2) [c_p x T_p(site)]^0 over the block's orbitals and -sqrt(2) [T_o(block) x c_o]^0
+    // (left; a right block writes the site part first), each with its Hermitian conjugate
+    for (int p = b0; p < b1; ++p)
+      if (auto C = x.get(Key(F_C, p))) {
+        const S3 T = site_T(I, p, o);
+        cs.push_back(mk(C, false, T, 1, 1, 0, -SQ2, true));
+        cs.push_back(mk(C, true, s_adj(T, 1), 1, 1, 0, SQ2, true));
       }
-      for (int p = 0; p < c; ++p)
-        for (int r = p; r < c; ++r) {
+    if (auto T = x.get(Key(F_S, o))) {
+      cs.push_back(mk(T, false, S.c, 1, 1, 0, -SQ2, true));
+      cs.push_back(mk(T, true, S.d, 1, 1, 0, SQ2, true));
+    }
+    if (B.normal) {
+      // pairs of the block with P, Q of the site (the order of two even factors is free)
+      for (int p = b0; p < b1; ++p)
+        for (int r = p; r < b1; ++r) {
           // P^0_pr(o) = (po|ro) [d_o x d_o]^0 (P^1 of one site vanishes)
           if (auto A = x.get(Key(F_A, p, r, 0))) {
             const double coef = (p == r ? 0.5 : 1.0) * -1.0 * V(I, p, o, r, o);
@@ -579,98 +696,16 @@ void enlarge_su2(const EnvBlock& B, const Integrals& I, Executor& ex, Enlarged& 
               if (p != r) cs.push_back(mk(Bv, true, s_adj(S.B[k], 2 * k), 2 * k, 2 * k, 0, qc, false));
             }
         }
-      x.materialize(Key(F_H), std::move(cs), false, 0);
-    }
-  } else {
-    const int o = B.cut - 1;   // site o, Y = [o+1, L)
-    E.cut = o;
-    x.view(Key(F_I), {mk(nullptr, false, I3, 0, 0, 0, 1.0, false)}, false, 0);
-    x.view(Key(F_C, o), {mk(nullptr, false, S.c, 0, 1, 1, 1.0, false)}, true, 1);
-    for (int p = o + 1; p < L; ++p)
-      if (auto C = x.get(Key(F_C, p))) x.view(Key(F_C, p), {mk(C, false, I3, 1, 0, 1, 1.0, true)}, true, 1);
-    // T'_m, m < o
-    for (int m = 0; m < o; ++m) {
-      std::vector<C2> cs;
-      cs.push_back(mk(nullptr, false, site_T(I, m, o), 0, 1, 1, 1.0, false));
-      if (auto T = x.get(Key(F_S, m))) cs.push_back(mk(T, false, I3, 1, 0, 1, 1.0, true));
-      for (int k = 0; k < 2; ++k) {
-        // (a) + (c): -sqrt(2) [d_o x sum (mo|qr) B^0_qr] + sqrt(2) (-1)^k swap23_K [d_o x sum (ms|qo) B^K_qs]
-        //   = -1/sqrt(2) [d_o x Q^k_mo(Y)] for k = 0, 1
-        if (auto Q = x.get(Key(F_Q, m, o, 2 * k))) cs.push_back(mk(Q, false, S.d, 2 * k, 1, 1, -1.0 / SQ2, false));
-        // (d) q = o: (ms|or) E_or d_s = -sqrt(2) assoc_K [c_o x [d_r x d_s]^K], sum = P^K_mo(Y)
-        if (auto P = x.get(Key(F_P, m, o, 2 * k))) cs.push_back(mk(P, false, S.c, 2 * k, 1, 1, -SQ2 * as[k], false));
-      }
-      for (int q = o + 1; q < L; ++q) {
-        auto Cq = x.get(Key(F_C, q));
-        if (!Cq) continue;
-        // (b) q = r = o: (mq|oo) [n_o x d_q]^1/2
-        cs.push_back(mk(Cq, true, S.n, 1, 0, 1, V(I, m, q, o, o), true));
-        // (e) r = s = o: (mo|qo) E_qo d_o, reordered d_o d_o c_q (sign +1), tree ((1 2)0, 0):
-        //     -sqrt(2) assoc_0 [[d_o x d_o]^0 x c_q]
-        cs.push_back(mk(Cq, false, S.DD0, 1, 0, 1, -SQ2 * as[0] * V(I, m, o, q, o), true));
-        // (f) q = s = o: (mo|oq) E_oq d_o, reordered c_o d_o d_q (sign -1), tree ((0 2)K, 1):
-        //     sqrt(2) swap23_K [B^K_oo x d_q]
-        for (int k = 0; k < 2; ++k)
-          cs.push_back(mk(Cq, true, S.B[k], 1, 2 * k, 1, SQ2 * sw[k] * V(I, m, o, o, q), true));
-      }
-      x.materialize(Key(F_S, m), std::move(cs), true, 1);
-    }
-    // P'^k_pr, Q'^k_ij for p <= r < o, i <= j < o
-    for (int k = 0; k < 2; ++k) {
-      const int K = 2 * k;
-      for (int p = 0; p < o; ++p)
-        for (int r = p; r < o; ++r) {
-          std::vector<C2> cs;
-          if (auto P = x.get(Key(F_P, p, r, K))) cs.push_back(mk(P, false, I3, K, 0, K, 1.0, false));
-          if (k == 0) cs.push_back(mk(nullptr, false, S.DD0, 0, 0, 0, V(I, p, o, r, o), false));
-          // s = o, q in Y: (pq|ro) [d_o x d_q]^k; s in Y, q = o: (po|rs) [d_s x d_o]^k = (-1)^k (po|rs) [d_o x d_s]^k
-          for (int q = o + 1; q < L; ++q)
-            if (auto Cq = x.get(Key(F_C, q))) {
-              const double w = V(I, p, q, r, o) + sgnk(k) * V(I, p, o, r, q);
-              if (w != 0.0) cs.push_back(mk(Cq, true, S.d, 1, 1, K, w, true));
-            }
-          x.materialize(Key(F_P, p, r, K), std::move(cs), false, K);
-        }
-      for (int i = 0; i < o; ++i)
-        for (int j = i; j < o; ++j) {
-          std::vector<C2> cs;
-          if (auto Q = x.get(Key(F_Q, i, j, K))) cs.push_back(mk(Q, false, I3, K, 0, K, 1.0, false));
-          cs.push_back(mk(nullptr, false, S.B[k], 0, K, K, qcoef(I, K, i, j, o, o), false));
-          for (int l = o + 1; l < L; ++l)
-            if (auto Cl = x.get(Key(F_C, l))) {
-              // (k, l) = (o, l): q^k_ijol [c_o x d_l]^k
-              const double w1 = qcoef(I, K, i, j, o, l);
-              if (w1 != 0.0) cs.push_back(mk(Cl, true, S.c, 1, 1, K, w1, true));
-              // (k, l) = (l, o): q^k_ijlo [c_l x d_o]^k = (-1)^k q^k_ijlo [d_o x c_l]^k
-              const double w2 = sgnk(k) * qcoef(I, K, i, j, l, o);
-              if (w2 != 0.0) cs.push_back(mk(Cl, false, S.d, 1, 1, K, w2, true));
-            }
-          x.materialize(Key(F_Q, i, j, K), std::move(cs), false, K);
-        }
-    }
-    // H' = H_o + H_Y + the terms of H across the cut o | Y
-    {
-      std::vector<C2> cs;
-      cs.push_back(mk(nullptr, false, site_H(I, o), 0, 0, 0, 1.0, false));
-      if (auto H = x.get(Key(F_H))) cs.push_back(mk(H, false, I3, 0, 0, 0, 1.0, false));
-      if (auto T = x.get(Key(F_S, o))) {
-        cs.push_back(mk(T, false, S.c, 1, 1, 0, -SQ2, true));
-        cs.push_back(mk(T, true, S.d, 1, 1, 0, SQ2, true));
-      }
-      for (int m = o + 1; m < L; ++m)
-        if (auto C = x.get(Key(F_C, m))) {
-          const S3 T = site_T(I, m, o);
-          cs.push_back(mk(C, false, T, 1, 1, 0, -SQ2, true));
-          cs.push_back(mk(C, true, s_adj(T, 1), 1, 1, 0, SQ2, true));
-        }
+    } else {
+      // the block's P, Q of the site orbital with the site's pairs
       if (auto P = x.get(Key(F_P, o, o, 0))) {
         cs.push_back(mk(P, false, S.A0, 0, 0, 0, -0.5, false));
         cs.push_back(mk(P, true, s_adj(S.A0, 0), 0, 0, 0, -0.5, false));
       }
       for (int k = 0; k < 2; ++k)
         if (auto Q = x.get(Key(F_Q, o, o, 2 * k))) cs.push_back(mk(Q, false, S.B[k], 2 * k, 2 * k, 0, 1.0, false));
-      x.materialize(Key(F_H), std::move(cs), false, 0);
     }
+    x.materialize(Key(F_H), std::move(cs), false, 0);
   }
   x.finish(ex);
 }
@@ -709,23 +744,36 @@ std::vector<CenterTerm> center_terms_su2(const Enlarged& Lp, const Enlarged& Rp,
     add(T, false, C, false, -SQ2, 1);
     add(T, true, C, true, SQ2, 1);
   }
+  if (Lp.normal == Rp.normal) throw std::logic_error("center_terms_su2: exactly one enlarged block must hold normal pairs");
+  // pair terms over the orbitals of the side with normal pairs; with normal
+  // pairs on the right the factors are [P x A]^0 and [Q x B]^0, equal to
+  // [A x P]^0 and [B x Q]^0 (even operators of equal rank coupled to 0), and
+  // the spin sums of a+a+aa with both creators on one side give the same
+  // coefficients whichever side that is
+  const int n0 = Lp.normal ? 0 : c, n1 = Lp.normal ? c : L;
+  const Enlarged& NE = Lp.normal ? Lp : Rp;   // normal pairs A, B
+  const Enlarged& CE = Lp.normal ? Rp : Lp;   // complementary pairs P, Q
+  auto add_pair = [&](const OpView* nrm, bool nt, const OpView* cmp, bool ct, double coef, int k2) {
+    if (Lp.normal) add(nrm, nt, cmp, ct, coef, k2);
+    else add(cmp, ct, nrm, nt, coef, k2);
+  };
   for (int k = 0; k < 2; ++k) {
     const int K = 2 * k;
     const double ak = ((1 + k) & 1 ? -1.0 : 1.0) * std::sqrt(2.0 * k + 1.0);
-    for (int p = 0; p < c; ++p)
-      for (int r = p; r < c; ++r) {
-        auto A = get(Lp, Key(F_A, p, r, K));
-        auto P = get(Rp, Key(F_P, p, r, K));
+    for (int p = n0; p < n1; ++p)
+      for (int r = p; r < n1; ++r) {
+        auto A = get(NE, Key(F_A, p, r, K));
+        auto P = get(CE, Key(F_P, p, r, K));
         if (A && P) {
           const double coef = (p == r ? 0.5 : 1.0) * ak;
-          add(A, false, P, false, coef, K);
-          add(A, true, P, true, coef, K);
+          add_pair(A, false, P, false, coef, K);
+          add_pair(A, true, P, true, coef, K);
         }
-        auto Bv = get(Lp, Key(F_B, p, r, K));
-        auto Q = get(Rp, Key(F_Q, p, r, K));
+        auto Bv = get(NE, Key(F_B, p, r, K));
+        auto Q = get(CE, Key(F_Q, p, r, K));
         if (Bv && Q) {
-          add(Bv, false, Q, false, 1.0, K);
-          if (p != r) add(Bv, true, Q, true, 1.0, K);
+          add_pair(Bv, false, Q, false, 1.0, K);
+          if (p != r) add_pair(Bv, true, Q, true, 1.0, K);
         }
       }
   }

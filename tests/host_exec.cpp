@@ -439,6 +439,32 @@ int main(int argc, char** argv) {
       std::fclose(o5);
       return 0;
     }
+    if (argc >= 5 && std::string(argv[3]) == "moveto") {
+      // exact centre moves to sites (t, t+1) for each t of a comma-separated
+      // list in turn, then psi and sigma at the last one
+      std::string ts = argv[4];
+      size_t pos = 0;
+      while (pos <= ts.size()) {
+        const size_t e = ts.find(',', pos);
+        const int t = std::atoi(ts.substr(pos, e == std::string::npos ? std::string::npos : e - pos).c_str());
+        while (E.center > t) E.truncate_move(1 << 30, -1, 1e-28);
+        while (E.center < t) E.truncate_move(1 << 30, +1, 1e-28);
+        if (e == std::string::npos) break;
+        pos = e + 1;
+      }
+      const int64_t n2 = E.lay.size;
+      const uint64_t sg2 = ex.alloc(n2);
+      E.heff(E.dpsi, sg2, nullptr, 0);
+      std::vector<double> ps((size_t)n2), sv((size_t)n2);
+      ex.download(ps.data(), E.dpsi, n2);
+      ex.download(sv.data(), sg2, n2);
+      FILE* o7 = std::fopen(argv[2], "wb");
+      if (!o7) throw std::runtime_error("cannot open output");
+      std::fwrite(ps.data(), 8, ps.size(), o7);
+      std::fwrite(sv.data(), 8, sv.size(), o7);
+      std::fclose(o7);
+      return 0;
+    }
     if (argc >= 4 && std::string(argv[3]) == "rdm2sweep") {
       const std::vector<double> g = E.rdm2_sweep();
       FILE* o4 = std::fopen(argv[2], "wb");

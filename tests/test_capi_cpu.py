@@ -53,12 +53,16 @@ def test_create_rejects_bad_configuration_before_cuda(field, value):
     assert not h.value
 
 
-def test_su2_needs_normal_pairs_on_the_left():
-    """The spin-adapted rules keep normal pairs on the left at every cut: an SU(2) context
-    with the normal/complementary switch is rejected before any CUDA call."""
+def test_su2_accepts_the_normal_complementary_switch():
+    """The spin-adapted rules place the pair operators on either side of a cut, so an SU(2)
+    context with the normal/complementary switch is a valid configuration: it is not
+    rejected as EINVAL (without a GPU the call then fails at its first CUDA call)."""
     import paper_2603_28648_b300 as qd
     path = ensure_built()
     lib = ctypes.CDLL(path)
     cfg = qd.Config(qd.SU2, 0, 0.0, 0.0, 0, 3, 0)
     h = ctypes.c_void_p()
-    assert lib.qcdmrg_create(ctypes.byref(h), ctypes.byref(cfg)) == -1
+    rc = lib.qcdmrg_create(ctypes.byref(h), ctypes.byref(cfg))
+    assert rc != -1
+    if rc == 0:
+        lib.qcdmrg_destroy(h)

@@ -400,3 +400,92 @@ def test_su2_rdm2_equals_the_fci_rdm_of_the_expanded_state(host_exec, tmp_path, 
     psi = mps.psi_to_flat()
     E = psi @ sig / (psi @ psi)
     assert abs(np.sum(h * g) + 0.5 * np.sum(V * G) - E) <= 1e-10 * abs(E)
+
+
+# SU(2) with the normal/complementary switch: left blocks past the switch cut hold P^k, Q^k
+# of the orbitals to their right (formed from their A^k, B^k at the switch), right blocks
+# beyond it hold A^k, B^k of their own orbitals, and the centre terms pair the sides
+# accordingly. The oracle keeps normal operators on both sides, so its sigma does not
+# depend on the switch.
+@pytest.mark.parametrize("L,N,two_s,D,c,switch", [(8, 8, 0, 20, 3, s) for s in range(1, 8)] +
+                         [(7, 6, 2, 8, 2, 1), (7, 6, 2, 8, 2, 3), (7, 6, 2, 8, 2, 5), (6, 5, 1, 6, 4, 2),
+                          (6, 5, 1, 6, 4, 5), (5, 5, 1, 8, 1, 2)])
+def test_su2_switched_task_lists_match_the_oracle(host_exec, tmp_path, L, N, two_s, D, c, switch):
+    from oracle.dmrgsu2 import DMRGSU2, MPSSU2
+    mps = MPSSU2.from_raw(q.random_mps_blocks(L, N, two_s, D, q.SYM_SU2, 5, c))
+    h, V = q.make_integrals(L, 11)
+    fin, fout = str(tmp_path / "in.bin"), str(tmp_path / "out.bin")
+    _write_su2(fin, mps, h, V)
+    r = subprocess.run([host_exec, fin, fout], capture_output=True, text=True, timeout=900,
+                       env=dict(_env(switch), HOST_EXEC_SU2="1"))
+    assert r.returncode == 0, r.stderr
+    out = np.fromfile(fout, "<f8")
+    n = len(out) // 2
+    ref = mps.psi_to_flat(DMRGSU2(h, V, N, two_s).sigma(mps))
+    assert n == len(ref)
+    for s in (out[:n], out[n:]):
+        assert np.linalg.norm(s - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("L,N,two_s,D,c,switch", [(6, 6, 0, 8, 2, 3), (6, 5, 1, 8, 2, 2), (7, 7, 1, 10, 2, 3)])
+def test_su2_switched_sweeps_match_the_oracle(host_exec, tmp_path, L, N, two_s, D, c, switch):
+    """Two sweeps across the switch cut in both directions (truncation, renormalization
+    of normal and complementary pairs, the switching enlargement on either side)."""
+    from oracle.dmrgsu2 import DMRGSU2, MPSSU2
+    mps = MPSSU2.from_raw(q.random_mps_blocks(L, N, two_s, D, q.SYM_SU2, 2, c))
+    h, V = q.make_integrals(L, 13)
+    fin, fout = str(tmp_path / "in.bin"), str(tmp_path / "out.bin")
+    _write_su2(fin, mps, h, V)
+    r = subprocess.run([host_exec, fin, fout, "sweep", str(D), "2", "1e-10"], capture_output=True, text=True,
+                       timeout=900, env=dict(_env(switch), HOST_EXEC_SU2="1"))
+    assert r.returncode == 0, r.stderr
+    E = np.fromfile(fout, "<f8")
+    Eo, _, _ = DMRGSU2(h, V, N, two_s).sweeps(mps, D, nsweeps=2, tol=1e-12)
+    assert np.abs(E - np.array(Eo)).max() <= 1e-9
+
+
+def test_su2_switch_leaves_sigma_unchanged_after_moves(host_exec, tmp_path):
+    """Exact centre moves in both directions renormalize blocks on either side of the
+    switch; at every centre reached the wavefunction and sigma equal those without it."""
+    from oracle.dmrgsu2 import MPSSU2
+    L, N, two_s, D, c = 6, 6, 0, 8, 2
+    mps = MPSSU2.from_raw(q.random_mps_blocks(L, N, two_s, D, q.SYM_SU2, 2, c))
+    h, V = q.make_integrals(L, 13)
+    fin, fout = str(tmp_path / "in.bin"), str(tmp_path / "out.bin")
+    _write_su2(fin, mps, h, V)
+
+    def run(switch, targets):
+        r = subprocess.run([host_exec, fin, fout, "moveto", targets], capture_output=True, text=True, timeout=900,
+                           env=dict(_env(switch), HOST_EXEC_SU2="1"))
+        assert r.returncode == 0, r.stderr
+        o = np.fromfile(fout, "<f8")
+        return o[:len(o) // 2], o[len(o) // 2:]
+
+    for targets in ("0,4", "4,1", "0,4,0"):
+        p0, s0 = run(0, targets)
+        for switch in (1, 2, 3, 4):
+            p1, s1 = run(switch, targets)
+            assert np.abs(p1 - p0).max() <= 1e-13
+            assert np.linalg.norm(s1 - s0) <= 1e-13 * np.linalg.norm(s0)
+
+
+def test_su2_switched_rdm1_and_rdm2_equal_unswitched(host_exec, tmp_path):
+    """With the switch the blocks at the centre (L-2, L-1) hold complementary pairs on the
+    left: the one-particle density matrix is taken after a rebuild with normal pairs on the
+    left (the switched environment is restored), and the probes of the two-particle density
+    matrix read <H_eff> of whichever partition is built; both equal the unswitched ones."""
+    from oracle.dmrgsu2 import MPSSU2
+    L, N, two_s, D = 6, 6, 0, 8
+    mps = MPSSU2.from_raw(q.random_mps_blocks(L, N, two_s, D, q.SYM_SU2, 5, L - 2))
+    h, V = q.make_integrals(L, 11)
+    fin, fout = str(tmp_path / "in.bin"), str(tmp_path / "out.bin")
+    _write_su2(fin, mps, h, V)
+    out = {}
+    for switch in (0, 3):
+        for mode in ("rdm1", "rdm2"):
+            r = subprocess.run([host_exec, fin, fout, mode], capture_output=True, text=True, timeout=900,
+                               env=dict(_env(switch), HOST_EXEC_SU2="1"))
+            assert r.returncode == 0, r.stderr
+            out[switch, mode] = np.fromfile(fout, "<f8")
+    assert np.abs(out[3, "rdm1"] - out[0, "rdm1"]).max() <= 1e-12
+    assert np.abs(out[3, "rdm2"] - out[0, "rdm2"]).max() <= 1e-11

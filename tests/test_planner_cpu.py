@@ -46,11 +46,13 @@ def test_plans_stay_in_bounds(checker, L, N, D, switch, sum_gemm):
     assert "fails=0" in r.stdout
 
 
-@pytest.mark.parametrize("L,N,D", [(6, 6, 16), (12, 12, 64), (36, 54, 256)])
-def test_su2_plans_stay_in_bounds(checker, L, N, D):
+@pytest.mark.parametrize("L,N,D,switch", [(6, 6, 16, 0), (12, 12, 64, 0), (36, 54, 256, 0), (12, 12, 64, 6),
+                                          (36, 54, 256, 18), (36, 54, 256, 19)])
+def test_su2_plans_stay_in_bounds(checker, L, N, D, switch):
     """The SU(2) reduced-operator task lists (environment build, enlargement sums, centre
-    FP64 segments and tiled work items) at the CAS(54,36) shape and smaller."""
-    r = subprocess.run([checker, str(L), str(N), str(D), "0", "0", "1"], capture_output=True, text=True,
+    FP64 segments and tiled work items) at the CAS(54,36) shape and smaller, with normal
+    pairs on the left at every cut and with the switch at and past the centre cut."""
+    r = subprocess.run([checker, str(L), str(N), str(D), str(switch), "0", "1"], capture_output=True, text=True,
                        timeout=600)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "fails=0" in r.stdout
