@@ -148,6 +148,11 @@ typedef struct {
   double dav_seconds;    /* its wall time */
   double dav_energy_mixed; /* its last Ritz value before the FP64 correction (policy 1) */
   int tile_chunk;        /* chunk byte target of the BF16 forms in use (0: fixed K depth) */
+  int tile_passes;       /* passes of the BF16 forms' stage-1 intermediates: 1 when every T_t
+                            of the product fits the device next to the operand mirrors,
+                            more when they are split (QCDMRG_TILED_T_BYTES in the environment
+                            sets the bytes of one pass's plane instead) */
+  int64_t tile_t_bytes;  /* bytes of one plane of the T arena in use */
 } qcdmrg_stats_t;
 
 /* Davidson options (zero fields take the defaults in brackets). */

@@ -71,7 +71,7 @@ class Stats(ctypes.Structure):
                 ("tune_seconds", ctypes.c_double), ("f64_tiles", ctypes.c_int64 * 4),
                 ("f64_split_tiles", ctypes.c_int64), ("dav_hpsi", ctypes.c_int * 4),
                 ("dav_seconds", ctypes.c_double), ("dav_energy_mixed", ctypes.c_double),
-                ("tile_chunk", ctypes.c_int)]
+                ("tile_chunk", ctypes.c_int), ("tile_passes", ctypes.c_int), ("tile_t_bytes", ctypes.c_int64)]
 
 
 EXPORTS = [

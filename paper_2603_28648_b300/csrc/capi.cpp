@@ -865,6 +865,8 @@ int qcdmrg_stats(const qcdmrg_ctx* ctx, qcdmrg_stats_t* out) {
   out->tile_kmax = ctx->eng.tcfg.kmax;
   out->tile_width = ctx->eng.tcfg.width;
   out->tile_chunk = ctx->eng.tcfg.chunk;
+  out->tile_passes = ctx->eng.tiled_passes;
+  out->tile_t_bytes = ctx->eng.tiled_t_plane;
   out->tunes = ctx->eng.tunes;
   out->tune_seconds = ctx->eng.tune_seconds;
   out->d2h_bytes = ctx->eng.d2h_bytes;

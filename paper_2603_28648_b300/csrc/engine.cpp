@@ -321,7 +321,12 @@ void Engine::heff(uint64_t psi, uint64_t sig, void* stream, int prec) {
     // the BF16 form reads plane 0, which is the same round-to-nearest bf16
     const int planes = (prec == 3 || mixed_planes) ? 3 : 1;
     if (pr->tiled_planes() < planes) {
-      pr->prepare_tiled(plan_tiled(plan, lay, tcfg), planes);
+      TiledPlan tp = plan_tiled(plan, lay, tcfg);
+      tiled_tbudget = tiled_t_bytes(planes, tp);
+      if (tiled_tbudget > 0) tp = plan_tiled(plan, lay, tcfg, tiled_tbudget);
+      tiled_passes = tp.npasses();
+      tiled_t_plane = tp.tbytes;
+      pr->prepare_tiled(tp, planes);
       pr->set_tiled_chunk(tcfg.chunk);
       if (autotune) {
         tune_tiled(psi, sig, prec);
@@ -335,6 +340,27 @@ void Engine::heff(uint64_t psi, uint64_t sig, void* stream, int prec) {
     pr->run_prepared(h.first, psi, sig, stream, prec);
     pr->run_prepared(h.second, psi, sig, stream, prec);
   }
+}
+
+// T arena of the tiled path: one pass when the operand mirrors and every T_t
+// of the product fit the free device memory with a 4 GB margin (for the
+// Davidson vectors and the other work of a step); otherwise the T_t are split
+// into passes of the bytes left. QCDMRG_TILED_T_BYTES (bytes of one plane)
+// sets the budget instead, to exercise the passes on small problems.
+int64_t Engine::tiled_t_bytes(int planes, const TiledPlan& full) {
+  if (const char* e = std::getenv("QCDMRG_TILED_T_BYTES")) {
+    const long long v = std::atoll(e);
+    if (v > 0) return (int64_t)v;
+  }
+  const int64_t free = pr->free_device_bytes();
+  if (free == INT64_MAX) return 0;
+  const int64_t margin = (int64_t)4 << 30;
+  const int64_t mirrors = (full.abytes + full.bbytes + full.psibytes) * planes;
+  if (mirrors + full.tbytes * planes + margin <= free) return 0;
+  const int64_t left = (free - margin - mirrors) / planes;
+  if (left < ((int64_t)64 << 20))
+    throw std::runtime_error("tiled path: the bf16 operand mirrors leave no room for the stage-1 intermediates");
+  return left;
 }
 
 // Autotuner of the bf16 tensor-core path. Phase 1 times every candidate
@@ -366,7 +392,7 @@ void Engine::tune_tiled(uint64_t psi, uint64_t sig, int prec) {
     std::lock_guard<std::mutex> g(mu);
     auto it = cache.find(key);
     if (it != cache.end()) {
-      if (!same_items(it->second, tcfg)) pr->set_tiled_items(plan_tiled(plan, lay, it->second));
+      if (!same_items(it->second, tcfg)) pr->set_tiled_items(plan_tiled(plan, lay, it->second, tiled_tbudget));
       tcfg = it->second;
       pr->set_tiled_chunk(tcfg.chunk);
       return;
@@ -381,7 +407,7 @@ void Engine::tune_tiled(uint64_t psi, uint64_t sig, int prec) {
   double tbest = 1e30;
   for (const TileCfg& c : cands) {
     if (!same_items(c, loaded)) {
-      pr->set_tiled_items(plan_tiled(plan, lay, c));
+      pr->set_tiled_items(plan_tiled(plan, lay, c, tiled_tbudget));
       loaded = c;
     }
     const double t = pr->time_tiled(psi, sig, prec, 2);
@@ -390,7 +416,7 @@ void Engine::tune_tiled(uint64_t psi, uint64_t sig, int prec) {
       best = c;
     }
   }
-  if (!same_items(best, loaded)) pr->set_tiled_items(plan_tiled(plan, lay, best));
+  if (!same_items(best, loaded)) pr->set_tiled_items(plan_tiled(plan, lay, best, tiled_tbudget));
   for (int chunk : {32768, 49152, 65536}) {
     pr->set_tiled_chunk(chunk);
     const double t = pr->time_tiled(psi, sig, prec, 2);

@@ -76,6 +76,10 @@ struct Engine {
   int evictions = 0, restores = 0;
   // work-item shape of the bf16 tensor-core path and its autotuner
   TileCfg tcfg;
+  int64_t tiled_tbudget = 0;       // T arena bytes per plane of the prepared centre (0: one pass)
+  int tiled_passes = 1;
+  int64_t tiled_t_plane = 0;       // bytes of one plane of the T arena in use
+  int64_t tiled_t_bytes(int planes, const TiledPlan& full);   // budget for a prepared centre
   bool autotune = true;
   bool mixed_planes = false;       // prepare the three bf16 planes even for the BF16 form
   double tune_seconds = 0;

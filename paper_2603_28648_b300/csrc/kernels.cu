@@ -736,6 +736,11 @@ class CudaExec : public Executor, public PreparedRunner {
     peak_ = std::max(peak_, live_);
   }
   int tiled_planes() const override { return td_.planes; }
+  int64_t free_device_bytes() const override {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return INT64_MAX;
+    return (int64_t)fr + td_.bytes;
+  }
   double time_tiled(uint64_t psi, uint64_t sig, int precision, int reps) override {
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
@@ -763,10 +768,17 @@ class CudaExec : public Executor, public PreparedRunner {
       throw std::runtime_error("tiled tensor-core path not prepared for this precision");
     cudaStream_t s = (cudaStream_t)stream;
     CK(launch_tile_views(t.psiv, t.npsiv, t.psi, t.psiplane, t.planes, reinterpret_cast<const double*>(psi), s));
-    CK(launch_tiled_stage1(mode, t.i1, t.ni1, t.v1, t.psi, t.psiplane, t.b, t.bplane, t.t, t.tplane, chunk_, nsm_,
-                           err_, s));
-    CK(launch_tiled_stage2(mode, t.i2, t.ni2, t.s2, t.a, t.aplane, t.t, t.tplane, reinterpret_cast<double*>(sig),
-                           chunk_, nsm_, err_, s));
+    // one stage-1 and one stage-2 launch per pass of the T arena (stage-1 pads
+    // of T that a pass does not write may hold an earlier pass's finite values:
+    // its K pads meet the zero K pads of the left views, its row pads only reach
+    // sigma columns the stage-2 epilogue discards)
+    for (size_t p = 0; p + 1 < t.pass1.size(); ++p) {
+      const int a1 = t.pass1[p], n1 = t.pass1[p + 1] - a1, a2 = t.pass2[p], n2 = t.pass2[p + 1] - a2;
+      CK(launch_tiled_stage1(mode, t.i1 + a1, n1, t.v1, t.psi, t.psiplane, t.b, t.bplane, t.t, t.tplane, chunk_,
+                             nsm_, err_, s));
+      CK(launch_tiled_stage2(mode, t.i2 + a2, n2, t.s2, t.a, t.aplane, t.t, t.tplane,
+                             reinterpret_cast<double*>(sig), chunk_, nsm_, err_, s));
+    }
   }
   void run_prepared(int h, uint64_t psi, uint64_t sig, void* stream, int precision) override {
     const DevLaunch& d = prepared_.at(h);
@@ -834,6 +846,7 @@ class CudaExec : public Executor, public PreparedRunner {
     K2Item* i2 = nullptr;
     K2Seg* s2 = nullptr;
     int npsiv = 0, ni1 = 0, ni2 = 0;
+    std::vector<int> pass1, pass2;   // item ranges of the passes (host copies)
     int64_t bytes = 0, items_bytes = 0;
   };
   void upload(void** d, const void* src, size_t bytes, int64_t* count) {
@@ -850,6 +863,10 @@ class CudaExec : public Executor, public PreparedRunner {
     upload(reinterpret_cast<void**>(&t.s2), P.s2.data(), P.s2.size() * sizeof(K2Seg), &b);
     t.ni1 = (int)P.i1.size();
     t.ni2 = (int)P.i2.size();
+    t.pass1 = P.pass1;
+    t.pass2 = P.pass2;
+    if (t.pass1.size() < 2 || t.pass1.size() != t.pass2.size() || t.pass1.back() != t.ni1 || t.pass2.back() != t.ni2)
+      throw std::runtime_error("tiled plan: inconsistent passes");
     t.items_bytes = b;
     t.bytes += b;
   }

@@ -34,6 +34,10 @@ struct PreparedRunner {
   // chunk byte target of the tiled kernels (0: fixed K depth per chunk)
   virtual void set_tiled_chunk(int bytes) { (void)bytes; }
   virtual int tiled_planes() const = 0;
+  // device bytes free now, counting the tiled path's current arenas as free (the
+  // tiled path sizes its T arena from it when it prepares a centre, which
+  // releases those arenas first)
+  virtual int64_t free_device_bytes() const { return INT64_MAX; }
   // device seconds of one H_eff psi on the tiled path (mean of reps, after one warm-up)
   virtual double time_tiled(uint64_t psi, uint64_t sig, int precision, int reps) = 0;
   // sigma must be zero; precision 2 (BF16) or 3 (BF16x3)

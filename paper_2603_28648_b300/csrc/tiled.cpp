@@ -40,13 +40,14 @@ struct SigBlk {
   int64_t out;
   int m, n, ldc;
   std::vector<K2Seg> segs;
+  std::vector<int> tp;   // the T_t of each segment
 };
 
 inline int round16(int x) { return 16 * ((x + 15) / 16); }
 
 }  // namespace
 
-TiledPlan plan_tiled(const HeffPlan& plan, const PsiLayout& lay, const TileCfg& cfg) {
+TiledPlan plan_tiled(const HeffPlan& plan, const PsiLayout& lay, const TileCfg& cfg, int64_t tbudget) {
   const int kmax = cfg.kmax;
   TiledPlan P;
   P.flops = plan.flops;
@@ -98,7 +99,7 @@ TiledPlan plan_tiled(const HeffPlan& plan, const PsiLayout& lay, const TileCfg& 
       if (it == sig_of.end()) {
         si = (int)sig.size();
         sig_of[(int64_t)p.c] = si;
-        sig.push_back({(int64_t)p.c, p.m, p.n, p.ldc, {}});
+        sig.push_back({(int64_t)p.c, p.m, p.n, p.ldc, {}, {}});
       } else {
         si = it->second;
       }
@@ -131,10 +132,31 @@ TiledPlan plan_tiled(const HeffPlan& plan, const PsiLayout& lay, const TileCfg& 
                                                          : am.add(g.a, 0, g.lda, g.ta, p.m, g.k, g.asc);
         if (g.k <= 0) throw std::runtime_error("tiled plan: stage-2 segment without K");
         sig[si].segs.push_back({a, tps[tp].tout, g.k, 0});
+        sig[si].tp.push_back(tp);
       }
     }
   }
 
+  // passes: T_t in creation order, a new pass when the next one would take
+  // the pass beyond the budget; offsets rebased to the pass start
+  std::vector<int> tpass(tps.size(), 0);
+  int npass = 1;
+  if (tbudget > 0 && P.tbytes > tbudget) {
+    int64_t start = 0, top = 0;
+    for (size_t i = 0; i < tps.size(); ++i) {
+      const int64_t sz = tiled_bytes(tps[i].n, lay.blks[tps[i].blk].rows, TP_B);
+      if (tps[i].tout + sz - start > tbudget && tps[i].tout > start) {
+        start = tps[i].tout;
+        ++npass;
+      }
+      tpass[i] = npass - 1;
+      tps[i].tout -= start;
+      top = std::max(top, tps[i].tout + sz);
+    }
+    P.tbytes = top;
+    for (SigBlk& sb : sig)
+      for (size_t k = 0; k < sb.segs.size(); ++k) sb.segs[k].b = tps[sb.tp[k]].tout;
+  }
   // stage 1: T_t grouped by psi block, blocks ordered by right then left
   // sector so that consecutive items reuse the same right views from L2; an
   // item holds views while their accumulator columns fit the width and their
@@ -146,8 +168,13 @@ TiledPlan plan_tiled(const HeffPlan& plan, const PsiLayout& lay, const TileCfg& 
   std::sort(order.begin(), order.end(), [&](int x, int y) {
     return std::make_pair(lay.blks[x].rsub, lay.blks[x].lsub) < std::make_pair(lay.blks[y].rsub, lay.blks[y].lsub);
   });
+  P.pass1.assign(1, 0);
+  for (int pass = 0; pass < npass; ++pass) {
   for (int blk : order) {
     if (by_blk[blk].empty()) continue;
+    bool any = false;
+    for (int tp : by_blk[blk]) any = any || tpass[tp] == pass;
+    if (!any) continue;
     const auto& pb = lay.blks[blk];
     const int c8 = tiled_c8(pb.cols);
     for (int np = 0; np * TP_B < pb.rows; ++np) {
@@ -164,6 +191,7 @@ TiledPlan plan_tiled(const HeffPlan& plan, const PsiLayout& lay, const TileCfg& 
       it.nv = 0;
       int col = 0, rows = 0;
       for (int tp : by_blk[blk]) {
+        if (tpass[tp] != pass) continue;
         const TProd& t = tps[tp];
         for (int mp = 0; mp * TP_A < t.n; ++mp) {
           const int mrows = std::min(TP_A, t.n - mp * TP_A);
@@ -193,45 +221,61 @@ TiledPlan plan_tiled(const HeffPlan& plan, const PsiLayout& lay, const TileCfg& 
       if (it.nv) P.i1.push_back(it);
     }
   }
-
-  // stage 2: sigma blocks, segment ranges of summed K <= kmax, costliest first
-  std::vector<std::pair<double, K2Item>> items;
-  for (const SigBlk& sb : sig) {
-    if (sb.segs.empty()) continue;
-    std::vector<std::pair<int, int>> ranges;
-    int s0 = (int)P.s2.size(), ks = 0;
-    for (const K2Seg& g : sb.segs) {
-      const int s = (int)P.s2.size();
-      if (s > s0 && ks + g.k > kmax) {
-        ranges.push_back({s0, s});
-        s0 = s;
-        ks = 0;
-      }
-      ks += g.k;
-      P.s2.push_back(g);
-    }
-    ranges.push_back({s0, (int)P.s2.size()});
-    const int split = ranges.size() > 1 ? 1 : 0;
-    for (int mp = 0; mp * TP_A < sb.m; ++mp)
-      for (int np = 0; np * TP_B < sb.n; ++np)
-        for (auto& r : ranges) {
-          K2Item it{};
-          it.out = sb.out;
-          it.ldc = sb.ldc;
-          it.mrows = std::min(TP_A, sb.m - mp * TP_A);
-          it.nrows = std::min(TP_B, sb.n - np * TP_B);
-          it.mp = mp;
-          it.np = np;
-          it.s0 = r.first;
-          it.s1 = r.second;
-          it.split = split;
-          double cost = 0;
-          for (int s = r.first; s < r.second; ++s) cost += P.s2[s].k + 16;
-          items.push_back({cost * round16(it.nrows), it});
-        }
+  P.pass1.push_back((int)P.i1.size());
   }
-  std::stable_sort(items.begin(), items.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
-  for (auto& x : items) P.i2.push_back(x.second);
+
+  // stage 2: per pass, the segments of each sigma block in that pass, ranges
+  // of summed K <= kmax, costliest first; a block split over several ranges
+  // or passes adds with atomics
+  P.pass2.assign(1, 0);
+  for (int pass = 0; pass < npass; ++pass) {
+    std::vector<std::pair<double, K2Item>> items;
+    for (const SigBlk& sb : sig) {
+      if (sb.segs.empty()) continue;
+      bool here = false, elsewhere = false;
+      for (int tp : sb.tp) {
+        if (tpass[tp] == pass) here = true;
+        else elsewhere = true;
+      }
+      if (!here) continue;
+      std::vector<std::pair<int, int>> ranges;
+      int s0 = (int)P.s2.size(), ks = 0;
+      for (size_t k = 0; k < sb.segs.size(); ++k) {
+        if (tpass[sb.tp[k]] != pass) continue;
+        const K2Seg& g = sb.segs[k];
+        const int s = (int)P.s2.size();
+        if (s > s0 && ks + g.k > kmax) {
+          ranges.push_back({s0, s});
+          s0 = s;
+          ks = 0;
+        }
+        ks += g.k;
+        P.s2.push_back(g);
+      }
+      ranges.push_back({s0, (int)P.s2.size()});
+      const int split = (ranges.size() > 1 || elsewhere) ? 1 : 0;
+      for (int mp = 0; mp * TP_A < sb.m; ++mp)
+        for (int np = 0; np * TP_B < sb.n; ++np)
+          for (auto& r : ranges) {
+            K2Item it{};
+            it.out = sb.out;
+            it.ldc = sb.ldc;
+            it.mrows = std::min(TP_A, sb.m - mp * TP_A);
+            it.nrows = std::min(TP_B, sb.n - np * TP_B);
+            it.mp = mp;
+            it.np = np;
+            it.s0 = r.first;
+            it.s1 = r.second;
+            it.split = split;
+            double cost = 0;
+            for (int s = r.first; s < r.second; ++s) cost += P.s2[s].k + 16;
+            items.push_back({cost * round16(it.nrows), it});
+          }
+    }
+    std::stable_sort(items.begin(), items.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+    for (auto& x : items) P.i2.push_back(x.second);
+    P.pass2.push_back((int)P.i2.size());
+  }
   return P;
 }
 

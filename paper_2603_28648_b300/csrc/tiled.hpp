@@ -94,7 +94,12 @@ struct TiledPlan {
   std::vector<K1Item> i1;
   std::vector<K2Seg> s2;
   std::vector<K2Item> i2;
+  // passes: the T_t of pass p occupy the T arena together (offsets rebased to
+  // its start), stage-1 items [pass1[p], pass1[p+1]) write them and stage-2
+  // items [pass2[p], pass2[p+1]) read them; the arena holds the largest pass
+  std::vector<int> pass1, pass2;
   double flops = 0;                     // algorithmic, same count as the FP64 plan
+  int npasses() const { return (int)pass1.size() - 1; }
 };
 
 // Work-item shape, picked per problem-size class by the autotuner.
@@ -110,7 +115,10 @@ struct TileCfg {
 };
 
 // The operand arenas (views, offsets, sizes) do not depend on the TileCfg,
-// only the work items do.
-TiledPlan plan_tiled(const HeffPlan& plan, const PsiLayout& lay, const TileCfg& cfg);
+// only the work items do. tbudget (bytes of one plane, 0: unlimited) bounds
+// the T arena: the T_t are split into passes in creation order, each pass
+// within the budget (a single T_t larger than it makes a pass of its own).
+// A sigma block whose segments fall in several passes adds with atomics.
+TiledPlan plan_tiled(const HeffPlan& plan, const PsiLayout& lay, const TileCfg& cfg, int64_t tbudget = 0);
 
 }  // namespace qd

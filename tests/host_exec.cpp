@@ -265,15 +265,22 @@ double view_at(const TView& v, int r, int c, const double* psi) {
 }
 
 // sigma of the tiled work items evaluated in FP64
-std::vector<double> tiled_sigma(const HeffPlan& plan, const PsiLayout& lay, const double* psi, const TileCfg& cfg) {
-  const TiledPlan T = plan_tiled(plan, lay, cfg);
+std::vector<double> tiled_sigma(const HeffPlan& plan, const PsiLayout& lay, const double* psi, const TileCfg& cfg,
+                                int64_t tbudget, int* npasses) {
+  const TiledPlan T = plan_tiled(plan, lay, cfg, tbudget);
+  if (npasses) *npasses = T.npasses();
   std::map<int64_t, const TView*> A, B, Ps;  // arena offset of a view -> view
   for (auto& v : T.avw) A[v.dst] = &v;
   for (auto& v : T.bvw) B[v.dst] = &v;
   for (auto& v : T.psivw) Ps[v.dst] = &v;
+  std::vector<double> sig((size_t)lay.size, 0.0);
+  // pass by pass: the T arena offsets of a pass are its own (rebased), so the
+  // T_t of one pass are forgotten before the next pass writes its own
+  for (int pass = 0; pass < T.npasses(); ++pass) {
   std::map<int64_t, std::vector<double>> Tt;  // T arena offset -> T_t^T (ntot x mtot, row-major)
   std::map<int64_t, int> Tcols;
-  for (const K1Item& it : T.i1) {
+  for (int ii = T.pass1[pass]; ii < T.pass1[pass + 1]; ++ii) {
+    const K1Item& it = T.i1[ii];
     const int c8 = tiled_c8(it.k);
     const TView* pv = Ps.at(it.b - (int64_t)it.np * (TP_B / 8) * c8 * 128);
     for (int vi = it.v0; vi < it.v0 + it.nv; ++vi) {
@@ -295,8 +302,8 @@ std::vector<double> tiled_sigma(const HeffPlan& plan, const PsiLayout& lay, cons
       }
     }
   }
-  std::vector<double> sig((size_t)lay.size, 0.0);
-  for (const K2Item& it : T.i2)
+  for (int ii = T.pass2[pass]; ii < T.pass2[pass + 1]; ++ii) {
+    const K2Item& it = T.i2[ii];
     for (int s = it.s0; s < it.s1; ++s) {
       const K2Seg& g = T.s2[s];
       const TView* av = A.at(g.a);
@@ -310,6 +317,8 @@ std::vector<double> tiled_sigma(const HeffPlan& plan, const PsiLayout& lay, cons
           sig[(size_t)it.out + (size_t)R * it.ldc + C] += acc;
         }
     }
+  }
+  }
   return sig;
 }
 
@@ -507,8 +516,12 @@ int main(int argc, char** argv) {
     TileCfg cfg;
     cfg.kmax = 8;  // small: many split stage-2 items
     cfg.width = 128;
-    std::vector<double> st = tiled_sigma(E.plan, E.lay, reinterpret_cast<const double*>(E.dpsi), cfg);
+    int64_t tb = 0;
+    if (const char* e = std::getenv("HOST_EXEC_T_BUDGET")) tb = std::atoll(e);
+    int npasses = 1;
+    std::vector<double> st = tiled_sigma(E.plan, E.lay, reinterpret_cast<const double*>(E.dpsi), cfg, tb, &npasses);
     std::fprintf(stderr, "heff_flops=%.0f\n", E.plan.flops);
+    std::fprintf(stderr, "tiled_passes=%d\n", npasses);
     FILE* o = std::fopen(argv[2], "wb");
     if (!o) throw std::runtime_error("cannot open output");
     std::fwrite(s64.data(), 8, s64.size(), o);

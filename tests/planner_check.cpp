@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <map>
+#include <set>
 #include <string>
 
 #include "engine.hpp"
@@ -172,8 +173,23 @@ void check_fp64(const HeffPlan& P, const PsiLayout& lay, const RecEx& ex) {
     }
 }
 
-void check_tiled(const HeffPlan& P, const PsiLayout& lay, const RecEx& ex, const TileCfg& cfg) {
-  const TiledPlan T = plan_tiled(P, lay, cfg);
+void check_tiled(const HeffPlan& P, const PsiLayout& lay, const RecEx& ex, const TileCfg& cfg, int64_t tbudget = 0) {
+  const TiledPlan T = plan_tiled(P, lay, cfg, tbudget);
+  // passes: item ranges cover both stages in order, and every T_t a stage-2
+  // segment reads is written by a stage-1 view of the same pass
+  if (T.pass1.size() < 2 || T.pass1.size() != T.pass2.size() || T.pass1.front() != 0 || T.pass2.front() != 0 ||
+      T.pass1.back() != (int)T.i1.size() || T.pass2.back() != (int)T.i2.size())
+    fail("tiled passes do not cover the items");
+  for (int p = 0; p + 1 < (int)T.pass1.size(); ++p) {
+    if (T.pass1[p + 1] < T.pass1[p] || T.pass2[p + 1] < T.pass2[p]) fail("tiled pass ranges out of order");
+    std::set<int64_t> written;
+    for (int i = T.pass1[p]; i < T.pass1[p + 1]; ++i)
+      for (int v = T.i1[i].v0; v < T.i1[i].v0 + T.i1[i].nv; ++v) written.insert(T.v1[v].tout);
+    for (int i = T.pass2[p]; i < T.pass2[p + 1]; ++i)
+      for (int sg = T.i2[i].s0; sg < T.i2[i].s1; ++sg)
+        if (!written.count(T.s2[sg].b)) fail("stage-2 segment reads a T tile its pass does not write");
+  }
+  if (tbudget == 0 && T.npasses() != 1) fail("unbounded tiled plan with more than one pass");
   if (std::getenv("PLANNER_TILED_STATS") && cfg.kmax == 4096 && cfg.width == 256) {
     // MMA work of both stages (M = 128 rows per A panel, N = the B panel rows rounded to 16,
     // K rounded to 16) against the algorithmic flops; chunks of 64 K per MMA group
@@ -393,6 +409,9 @@ int main(int argc, char** argv) {
       cfg.kmax = kmax;
       cfg.width = width;
       check_tiled(E.plan, E.lay, ex, cfg);
+      // T arena split into about five passes
+      const int64_t tb = plan_tiled(E.plan, E.lay, cfg).tbytes;
+      check_tiled(E.plan, E.lay, ex, cfg, std::max<int64_t>(1, tb / 5));
     }
   {
     // executed (padded) FP64 flops of the centre product: tiles of 64 or 32 (least

@@ -489,3 +489,26 @@ def test_su2_switched_rdm1_and_rdm2_equal_unswitched(host_exec, tmp_path):
             out[switch, mode] = np.fromfile(fout, "<f8")
     assert np.abs(out[3, "rdm1"] - out[0, "rdm1"]).max() <= 1e-12
     assert np.abs(out[3, "rdm2"] - out[0, "rdm2"]).max() <= 1e-11
+
+
+@pytest.mark.parametrize("L,N,two_s,D,c,budget", [(8, 8, 0, 20, 3, 4096), (8, 8, 0, 20, 3, 1), (6, 5, 1, 6, 4, 2048)])
+def test_tiled_passes_match_the_oracle(host_exec, tmp_path, L, N, two_s, D, c, budget):
+    """The tiled work items with the T arena split into passes (budget: bytes of one plane
+    per pass; 1 gives one T_t per pass): evaluated pass by pass, each pass's T_t forgotten
+    before the next, sigma equals the oracle's; the unbounded plan has one pass."""
+    from oracle.dmrgsu2 import DMRGSU2, MPSSU2
+    mps = MPSSU2.from_raw(q.random_mps_blocks(L, N, two_s, D, q.SYM_SU2, 5, c))
+    h, V = q.make_integrals(L, 11)
+    fin, fout = str(tmp_path / "in.bin"), str(tmp_path / "out.bin")
+    _write_su2(fin, mps, h, V)
+    ref = mps.psi_to_flat(DMRGSU2(h, V, N, two_s).sigma(mps))
+    passes = {}
+    for b in (0, budget):
+        r = subprocess.run([host_exec, fin, fout], capture_output=True, text=True, timeout=900,
+                           env=dict(os.environ, HOST_EXEC_SU2="1", HOST_EXEC_T_BUDGET=str(b)))
+        assert r.returncode == 0, r.stderr
+        passes[b] = int(r.stderr.split("tiled_passes=")[1].split()[0])
+        out = np.fromfile(fout, "<f8")
+        n = len(out) // 2
+        assert np.linalg.norm(out[n:] - ref) <= 1e-12 * np.linalg.norm(ref)
+    assert passes[0] == 1 and passes[budget] > 1
