@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--precision", default="bf16", choices=["fp64", "tf32", "bf16", "bf16x3"],
                     help="form whose throughput is the headline value (all forms are timed)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-solves", action="store_true",
+                    help="stop after the single products of every form and print them (no Davidson solves)")
     ap.add_argument("--no-fp64-solve", action="store_true",
                     help="skip the FP64 reference solve (for bond dimensions where it takes many minutes); "
                          "the line then projects its time from the FP64 product time")
@@ -63,9 +65,11 @@ def parse():
     ap.add_argument("--hbm-budget", type=float, default=0.0,
                     help="device GB for renormalized operator blocks (0: unlimited); blocks beyond it "
                          "live in pinned host memory, so only the centre's blocks stay on the device")
-    ap.add_argument("--pair-switch", type=int, default=0,
+    ap.add_argument("--pair-switch", type=int, default=None,
                     help="cut of the normal/complementary switch (0: normal pairs on the left at every "
-                         "cut; L/2: the N/2 rule, which the D=4096 environment needs to fit)")
+                         "cut; near L/2: the N/2 rule, which the D=4096 environment needs to fit). Default: "
+                         "one cut past the centre (L/2 + 1) for SU(2), where the centre's complementary "
+                         "pairs stay references; 0 for U(1)")
     ap.add_argument("--sum-gemm", type=int, default=0, choices=[-1, 0, 1],
                     help="operator sums of the renormalization side as GEMMs (1), block by block (-1), "
                          "or as GEMMs only with the switch (0)")
@@ -74,7 +78,10 @@ def parse():
                          "captures under profiles/ run); prints a short line")
     ap.add_argument("--profile", action="store_true",
                     help="bracket the timed region with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.pair_switch is None:
+        args.pair_switch = args.L // 2 + 1 if (args.symmetry == "su2" and not args.adjoint) else 0
+    return args
 
 
 class Clocks:
@@ -130,6 +137,15 @@ class Clocks:
 # product), keyed by (form, symmetry, L, N, D); each capture and its command are
 # summarised under profiles/. A key that is absent reports null.
 DRAM_TRAFFIC = {}
+
+
+_T0 = time.perf_counter()
+
+
+def progress(msg):
+    """One timestamped line on stderr per phase, so that a run cut off by a time limit
+    still shows where its time went (the JSON line goes to stdout at the end)."""
+    print(f"[bench +{time.perf_counter() - _T0:8.1f} s] {msg}", file=sys.stderr, flush=True)
 
 
 def measured_peaks():
@@ -289,11 +305,14 @@ def run_ours(args, rank, world, local):
     ctx.init_mps(D, q.integrals.BASE_SEED + 1002, center)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    progress(f"environment build: L={L} N={N} D={D} switch={args.pair_switch} budget={args.hbm_budget} GB")
     ctx.build_env()
     torch.cuda.synchronize()
     env_s = time.perf_counter() - t0
     st = ctx.stats()
     flops = st["heff_flops"]
+    progress(f"environment built in {env_s:.1f} s, {st['live_bytes'] / 1e9:.1f} GB live, "
+             f"{st['evictions']} blocks evicted, H_eff psi {flops / 1e9:.1f} GFLOP")
     psi = torch.tensor(ctx.psi(), device="cuda")
     sig = torch.empty_like(psi)
     stream = torch.cuda.current_stream()
@@ -326,13 +345,31 @@ def run_ours(args, rank, world, local):
                        "sigma_rel_err_vs_fp64": float((torch.linalg.norm(sig - sig64) /
                                                        torch.linalg.norm(sig64)).item()),
                        "psi_h_psi_minus_fp64": float(torch.dot(psi, sig).item()) - e_fp64}
+        progress(f"{name}: {t * 1e3:.1f} ms per product, {flops / t / 1e12:.2f} TFLOP/s, sigma error "
+                 f"{forms[name]['sigma_rel_err_vs_fp64']:.2e}, {ctx.stats()['tile_passes']} T passes")
     for f in forms.values():
         f["speedup_vs_fp64"] = forms["fp64"]["ms_per_product"] / f["ms_per_product"]
+    if args.no_solves:
+        st2 = ctx.stats()
+        print(json.dumps({"metric": "H_eff psi TFLOP/s per form (single products, no solves)",
+                          "value": forms["bf16x3"]["tflops"], "unit": "TFLOP/s", "n_gpus": 1,
+                          "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+                          "dtype": "bf16+f64", "data": "synthetic",
+                          "config": {"workload": f"su2_L{L}_N{N}_S0_D{D}" if su2 else f"u1_L{L}_N{N}_Sz0_D{D}",
+                                     "heff_gflop": flops / 1e9, "psi_size": st["psi_size"],
+                                     "env_build_s": env_s, "env_build_tflops": st["env_flops"] / env_s / 1e12,
+                                     "device_bytes": st2["device_bytes"], "products": forms,
+                                     "t_passes": st2["tile_passes"], "t_arena_gb_per_plane": st2["tile_t_bytes"] / 1e9,
+                                     "pair_switch": args.pair_switch, "hbm_budget_gb": args.hbm_budget,
+                                     "evictions": st2["evictions"], "d2h_gb": st2["d2h_bytes"] / 1e9}}), flush=True)
+        return
 
     # --- start vector of the solves: the random MPS's centre, brought to a residual of
     # 1e-3 by a mixed solve (setup, untimed), so that the FP64 reference solve stays short
     ctx.davidson(allow_notconv=True, policy=1, tol=1e-3, max_iter=args.max_iter)
     psi0 = ctx.psi()
+    progress(f"start vector at residual 1e-3: {ctx.stats()['dav_seconds']:.1f} s, products "
+             f"{ctx.stats()['dav_hpsi']}")
 
     def solve(policy):
         """One Davidson solve from psi0; device time by events on the legacy default stream
@@ -346,6 +383,8 @@ def run_ours(args, rank, world, local):
         e1.record()
         torch.cuda.synchronize()
         s2 = ctx.stats()
+        progress(f"{policy} solve: {e0.elapsed_time(e1) / 1e3:.2f} s, E = {e:.10f}, residual {r:.1e}, "
+                 f"products {s2['dav_hpsi']}")
         return {"energy": e, "residual": r, "iterations": it, "seconds": e0.elapsed_time(e1) / 1e3,
                 "hpsi": dict(zip(["fp64", "tf32", "bf16", "bf16x3"], s2["dav_hpsi"])),
                 "energy_before_fp64_correction": s2["dav_energy_mixed"]}
@@ -387,6 +426,7 @@ def run_ours(args, rank, world, local):
     e1.record()
     torch.cuda.synchronize()
     trunc_s = e0.elapsed_time(e1) / 1e3
+    progress(f"end-to-end solve {e2e_s:.2f} s; truncation and renormalization {trunc_s:.2f} s")
     if dist:
         per_step, e2e_s = max_over_ranks([per_step, e2e_s], dist, "cuda")
     value = replica_throughput(step_flops, per_step, world)
@@ -522,7 +562,7 @@ def run_products(args, rank, world, local):
     L, N, D = args.L, args.N, args.D
     h, V = q.make_integrals(L, q.integrals.BASE_SEED + 2)
     ctx = qd.Context(device=local, symmetry=qd.SU2 if args.symmetry == "su2" else qd.U1,
-                     hbm_budget_gb=args.hbm_budget)
+                     hbm_budget_gb=args.hbm_budget, pair_switch=args.pair_switch)
     ctx.load_integrals(h, V)
     ctx.set_target(N, 0)
     ctx.init_mps(D, q.integrals.BASE_SEED + 1002, L // 2 - 1)
@@ -801,16 +841,17 @@ def run_outofcore(args, rank, world, local):
     del src, dst
     torch.cuda.empty_cache()
     h, V = q.make_integrals(L, w["int_seed"], diag=w["diag"])
-    ctx = qd.Context(device=local, symmetry=qd.SU2, hbm_budget_gb=args.hbm_budget)
+    c0 = L // 2 - 1
+    ctx = qd.Context(device=local, symmetry=qd.SU2, hbm_budget_gb=args.hbm_budget, pair_switch=c0 + 2)
     ctx.load_integrals(h, V)
     ctx.set_target(N, two_s)
-    c0 = L // 2 - 1
     ctx.init_mps(D, w["mps_seed"], c0)
     t0 = time.perf_counter()
     ctx.build_env()
     torch.cuda.synchronize()
     env_s = time.perf_counter() - t0
     st_env = ctx.stats()
+    progress(f"out-of-core environment built in {env_s:.1f} s, {st_env['evictions']} evictions")
     clocks = Clocks(local)
     clocks.start()
     steps = []
@@ -823,6 +864,9 @@ def run_outofcore(args, rank, world, local):
         torch.cuda.synchronize()
         t3 = time.perf_counter()
         s1 = ctx.stats()
+        progress(f"out-of-core step {k}: Davidson {t2 - t1:.1f} s, move {t3 - t2:.1f} s, "
+                 f"H2D {(s1['h2d_bytes'] - s0['h2d_bytes']) / 1e9:.2f} GB, copy wait "
+                 f"{s1['copy_wait_seconds'] - s0['copy_wait_seconds']:.2f} s")
         steps.append({"davidson_s": t2 - t1, "move_s": t3 - t2, "energy": e, "resid": r, "iters": it,
                       "h2d_bytes": s1["h2d_bytes"] - s0["h2d_bytes"],
                       "d2h_bytes": s1["d2h_bytes"] - s0["d2h_bytes"],
@@ -838,7 +882,7 @@ def run_outofcore(args, rank, world, local):
         "value": wall / max(1, len(steps)), "unit": "s/step", "n_gpus": 1, "steps": len(steps), "warmup": 0,
         "higher_is_better": False, "dtype": "mixed", "data": "synthetic",
         "config": {"workload": f"su2_L{L}_N{N}_S{two_s}_D{D} random MPS, centre {c0} moving right",
-                   "hbm_budget_gb": args.hbm_budget, "env_build_s": env_s,
+                   "hbm_budget_gb": args.hbm_budget, "pair_switch": c0 + 2, "env_build_s": env_s,
                    "env_evictions": st_env["evictions"], "env_d2h_gb": st_env["d2h_bytes"] / 1e9,
                    "device_peak_gb": st["device_bytes"] / 1e9, "device_live_gb": st["live_bytes"] / 1e9,
                    "h2d_gb": h2d / 1e9, "h2d_gb_per_s_steps": (h2d / wall / 1e9) if wall > 0 else None,
