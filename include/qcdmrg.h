@@ -177,8 +177,14 @@ typedef struct {
 } qcdmrg_dav_opts;
 
 typedef struct {
-  int D;                 /* bond dimension kept by every truncation (U(1) states) */
+  int D;                 /* bond dimension kept by every truncation (U(1) states, SU(2)
+                            multiplets); with trunc_eps > 0 the largest one */
   qcdmrg_dav_opts dav;
+  double trunc_eps;      /* > 0: dynamic block-state selection, each truncation keeps the
+                            smallest bond dimension in [D_min, D] whose discarded weight is at
+                            most trunc_eps (the fixed-truncation-error alternative the paper's
+                            Numerical procedure section mentions); 0: fixed D */
+  int D_min;             /* smallest bond dimension of the dynamic selection */
 } qcdmrg_sweep_opts;
 
 typedef struct {
@@ -188,6 +194,7 @@ typedef struct {
   double seconds;        /* wall time of the sweep */
   int n_hpsi[4];         /* H psi products per precision (FP64, TF32, BF16, BF16x3) */
   int n_steps;           /* two-site optimisations (2L-4) */
+  int max_D;             /* largest bond dimension kept by the sweep's truncations */
 } qcdmrg_sweep_report;
 
 /* Create a context on cfg->device: one solver of the paper's spin-adapted DMRG
@@ -442,6 +449,35 @@ int qcdmrg_davidson(qcdmrg_ctx* ctx, const qcdmrg_dav_opts* opts, double* energy
  * the discarded weight. Errors: ESTATE, EINVAL.
  */
 int qcdmrg_truncate(qcdmrg_ctx* ctx, int D, int dir, double* trunc_err);
+
+/*
+ * Truncation step with dynamic block-state selection: the bond dimension is
+ * the smallest D in [D_min, D_max] whose discarded weight (the sum of all
+ * density-matrix weights beyond the D largest) is at most eps, after which the
+ * selection of qcdmrg_truncate runs with that D (a group of weights tied at the
+ * cut is dropped as a whole, which can leave the discarded weight a little
+ * above eps). The fixed-truncation-error alternative to a fixed D that the
+ * paper's Numerical procedure section mentions. *kept receives the number of
+ * states (SU(2): multiplets) kept; trunc_err and kept may be NULL. Errors:
+ * ESTATE, EINVAL (1 <= D_min <= D_max, eps > 0, dir +1 or -1, a move off the
+ * chain).
+ */
+int qcdmrg_truncate_dbss(qcdmrg_ctx* ctx, int D_min, int D_max, double eps, int dir, double* trunc_err,
+                         int* kept);
+
+/*
+ * Extrapolation of energies to the truncation-free limit: the least-squares
+ * polynomial E(x) = coef[0] + coef[1] x + ... + coef[degree] x^degree (degree
+ * 1..3) through n points (x[i], energy[i]); coef[0] is the extrapolated energy.
+ * The paper's Numerical benchmark section extrapolates its fixed-D series in
+ * two ways: a second-order polynomial in x = 1/D, and the energy against the
+ * largest truncation error of the last sweep (x = that error; the fit's form is
+ * not stated there, degree 1 is the usual choice). Host arrays, coef holds
+ * degree + 1 doubles. No context, no device. Errors: EINVAL (degree outside
+ * 1..3, n < degree + 1, NULL arrays, non-finite values, points that do not fix
+ * the polynomial).
+ */
+int qcdmrg_extrapolate(const double* x, const double* energy, int n, int degree, double* coef);
 
 /* Move the centre to sites (target, target+1) without truncation (only
  * weights <= 1e-14, rounding noise, dropped), renormalizing each grown

@@ -901,12 +901,24 @@ class DMRGSU2:
             l -= 1
         return MPSSU2(self.L, self.N, self.two_s, l, lb, rb, A, R, psi)
 
-    def sweeps(self, mps, D, nsweeps=1, tol=1e-12):
+    def sweeps(self, mps, D, nsweeps=1, tol=1e-12, trunc_eps=0.0, D_min=1):
         """Full sweeps at bond dimension D (SU(2) multiplets); as the U(1)
         oracle: the centre starts at 0, each sweep optimises centres 0..L-3
         moving right and L-2..1 moving left and ends at 0. Returns (energies,
-        max discarded weights, final MPS)."""
-        from .dmrgu1 import select_kept
+        max discarded weights, final MPS). trunc_eps > 0: dynamic block-state
+        selection in [D_min, D] (dmrgu1.dbss_bond_dimension on the multiplet
+        weights); self.max_kept and self.total_kept are the largest and the summed
+        numbers of multiplets kept."""
+        from .dmrgu1 import select_kept, dbss_bond_dimension
+        self.max_kept = 0
+        self.total_kept = 0
+
+        def choose(blocks):
+            Dk = dbss_bond_dimension(blocks, trunc_eps, D_min, D) if trunc_eps > 0 else D
+            kept, disc = select_kept(blocks, Dk)
+            self.max_kept = max(self.max_kept, sum(len(v) for v in kept.values()))
+            self.total_kept += sum(len(v) for v in kept.values())
+            return kept, disc
         L = self.L
         mps = self.move_center_left(mps, 0)
         A, R = dict(mps.A), dict(mps.R)
@@ -928,7 +940,7 @@ class DMRGSU2:
                 En, x = lowest_eig(heff, psi, tol=tol)
                 if d > 0:
                     blocks = svd_left(x, Lp.prod, Rp.prod, heff.mask)
-                    kept, disc = select_kept(blocks, D)
+                    kept, disc = choose(blocks)
                     bnew, U, SV = self._factor_left(blocks, kept, Lp, Rp)
                     A[l] = U
                     lb[l + 1] = bnew
@@ -937,7 +949,7 @@ class DMRGSU2:
                     psi = recouple_right_move(Lnew, Rp.prod, R.pop(l + 2), SV, self.two_s, rb[l + 2])
                 else:
                     blocks = svd_right(x, Lp.prod, Rp.prod, heff.mask)
-                    kept, disc = select_kept(blocks, D)
+                    kept, disc = choose(blocks)
                     bnew, Vt, US = self._factor_right(blocks, kept, Lp, Rp)
                     R[l + 1] = Vt
                     rb[l + 1] = bnew

@@ -415,6 +415,20 @@ def select_kept(blocks, D, drop_below=WEIGHT_FLOOR):
     return {q: sorted(v) for q, v in kept.items()}, float(disc)
 
 
+def dbss_bond_dimension(blocks, eps, D_min, D_max):
+    """Dynamic block-state selection (the fixed-truncation-error alternative to
+    a fixed D in the paper's Numerical procedure section): the smallest D in
+    [D_min, D_max] whose discarded weight, the sum of all weights sv^2 beyond
+    the D largest, is at most eps; D_max (or the number of weights) when none
+    is. The selection itself then runs select_kept with that D."""
+    w = sorted((float(x) * float(x) for (_, _, _, sv, _) in blocks.values() for x in sv), reverse=True)
+    top = min(D_max, len(w))
+    for D in range(max(1, D_min), top + 1):
+        if sum(w[D:]) <= eps:
+            return D
+    return max(1, top)
+
+
 def left_factor(blocks, kept, dL, dR):
     bnew = Bond({qn: len(ks) for qn, ks in kept.items()})
     U = np.zeros((dL, bnew.dim))
@@ -505,14 +519,18 @@ class DMRGU1:
             l -= 1
         return MPSU1(self.L, self.N, self.two_sz, l, lb, rb, A, R, psi)
 
-    def sweeps(self, mps, D, nsweeps=1, tol=1e-12):
+    def sweeps(self, mps, D, nsweeps=1, tol=1e-12, trunc_eps=0.0, D_min=1):
         """Full sweeps; returns (energies, max discarded weights, final MPS).
 
         The MPS is first moved to centre 0. Each sweep optimises centres
         0..L-3 moving right and L-2..1 moving left (2L-4 optimisations) and
         ends with the centre back at 0. The energy of a sweep is that of its
-        last optimisation.
+        last optimisation. trunc_eps > 0: each truncation keeps the bond
+        dimension dbss_bond_dimension gives in [D_min, D]; self.max_kept and
+        self.total_kept are the largest and the summed numbers of states kept.
         """
+        self.max_kept = 0
+        self.total_kept = 0
         L = self.L
         mps = self.move_center_left(mps, 0)
         A, R = dict(mps.A), dict(mps.R)
@@ -534,7 +552,10 @@ class DMRGU1:
                 DX, DY = psi.shape[0], psi.shape[3]
                 E, x = lowest_eig(heff, to_mat(psi), tol=tol)
                 blocks = svd_sectors(x, Lp.n, Lp.s, Rp.n, Rp.s, self.N, self.two_sz)
-                kept, disc = select_kept(blocks, D)
+                Dk = dbss_bond_dimension(blocks, trunc_eps, D_min, D) if trunc_eps > 0 else D
+                kept, disc = select_kept(blocks, Dk)
+                self.max_kept = max(self.max_kept, sum(len(v) for v in kept.values()))
+                self.total_kept += sum(len(v) for v in kept.values())
                 maxerr = max(maxerr, disc)
                 if d > 0:
                     bnew, U, SV = left_factor(blocks, kept, Lp.dim, Rp.dim)

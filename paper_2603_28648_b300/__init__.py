@@ -49,13 +49,13 @@ class DavOpts(ctypes.Structure):
 
 
 class SweepOpts(ctypes.Structure):
-    _fields_ = [("D", ctypes.c_int), ("dav", DavOpts)]
+    _fields_ = [("D", ctypes.c_int), ("dav", DavOpts), ("trunc_eps", ctypes.c_double), ("D_min", ctypes.c_int)]
 
 
 class SweepReport(ctypes.Structure):
     _fields_ = [("energy", ctypes.c_double), ("energy_mixed", ctypes.c_double),
                 ("max_trunc_err", ctypes.c_double), ("seconds", ctypes.c_double),
-                ("n_hpsi", ctypes.c_int * 4), ("n_steps", ctypes.c_int)]
+                ("n_hpsi", ctypes.c_int * 4), ("n_steps", ctypes.c_int), ("max_D", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -83,7 +83,7 @@ EXPORTS = [
     "qcdmrg_apply_heff_noalloc", "qcdmrg_graph_create", "qcdmrg_graph_launch",
     "qcdmrg_graph_info", "qcdmrg_graph_destroy", "qcdmrg_rdm1", "qcdmrg_rdm2", "qcdmrg_rdm2_sweep", "qcdmrg_set_psi",
     "qcdmrg_export_mps", "qcdmrg_checkpoint", "qcdmrg_restore", "qcdmrg_psi_layout",
-    "qcdmrg_energy_grad",
+    "qcdmrg_energy_grad", "qcdmrg_truncate_dbss", "qcdmrg_extrapolate",
 ]
 
 _lib = None
@@ -138,6 +138,8 @@ def load(path=None):
     lib.qcdmrg_restore.argtypes = [P, ctypes.c_char_p]
     lib.qcdmrg_set_psi.argtypes = [P, dp, ctypes.c_size_t]
     lib.qcdmrg_sweep.argtypes = [P, ctypes.POINTER(SweepOpts), ctypes.POINTER(SweepReport)]
+    lib.qcdmrg_truncate_dbss.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, dp, ip]
+    lib.qcdmrg_extrapolate.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, dp]
     for f in EXPORTS:
         getattr(lib, f).restype = getattr(lib, f).restype or ctypes.c_int
     lib.qcdmrg_last_error.restype = ctypes.c_char_p
@@ -328,14 +330,23 @@ class Context:
     def move_center(self, target):
         self._check(self.lib.qcdmrg_move_center(self.h, target))
 
-    def sweep(self, D, allow_notconv=False, **kw):
-        o = SweepOpts(D, self.dav_opts(**kw))
+    def sweep(self, D, allow_notconv=False, trunc_eps=0.0, D_min=1, **kw):
+        """One sweep; trunc_eps > 0 selects the bond dimension of each truncation
+        dynamically in [D_min, D]."""
+        o = SweepOpts(D, self.dav_opts(**kw), trunc_eps, D_min)
         r = SweepReport()
         rc = self.lib.qcdmrg_sweep(self.h, ctypes.byref(o), ctypes.byref(r))
         if not (allow_notconv and rc == -5):
             self._check(rc)
         return {"energy": r.energy, "energy_mixed": r.energy_mixed, "max_trunc_err": r.max_trunc_err,
-                "seconds": r.seconds, "n_hpsi": list(r.n_hpsi), "n_steps": r.n_steps}
+                "seconds": r.seconds, "n_hpsi": list(r.n_hpsi), "n_steps": r.n_steps, "max_D": r.max_D}
+
+    def truncate_dbss(self, D_min, D_max, eps, direction):
+        """Returns (discarded weight, states kept)."""
+        err, kept = ctypes.c_double(), ctypes.c_int()
+        self._check(self.lib.qcdmrg_truncate_dbss(self.h, D_min, D_max, eps, direction, ctypes.byref(err),
+                                                  ctypes.byref(kept)))
+        return err.value, kept.value
 
     def check_device(self):
         self._check(self.lib.qcdmrg_check_device(self.h))
@@ -345,6 +356,23 @@ class Context:
         self._check(self.lib.qcdmrg_stats(self.h, ctypes.byref(s)))
         out = {f: getattr(s, f) for f, _ in Stats._fields_}
         return {f: (list(v) if isinstance(v, ctypes.Array) else v) for f, v in out.items()}
+
+
+def extrapolate(x, energy, degree=1, lib=None):
+    """qcdmrg_extrapolate: least-squares polynomial of the given degree through the
+    points (x[i], energy[i]); returns its coefficients, the first being the value at
+    x = 0."""
+    import numpy as np
+    lib = lib or load()
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    e = np.ascontiguousarray(energy, dtype=np.float64)
+    if x.shape != e.shape:
+        raise ValueError("x and energy differ in length")
+    c = np.zeros(degree + 1)
+    rc = lib.qcdmrg_extrapolate(_dptr(x), _dptr(e), len(x), degree, _dptr(c))
+    if rc != 0:
+        raise QcdmrgError(rc, "qcdmrg_extrapolate: invalid points")
+    return c
 
 
 class HeffGraph:

@@ -752,6 +752,65 @@ int qcdmrg_truncate(qcdmrg_ctx* ctx, int D, int dir, double* trunc_err) {
   });
 }
 
+int qcdmrg_truncate_dbss(qcdmrg_ctx* ctx, int D_min, int D_max, double eps, int dir, double* trunc_err,
+                         int* kept) {
+  return guard(ctx, [&]() {
+    Engine& E = ctx->eng;
+    if (!E.have_env) throw Fail{QCDMRG_ESTATE, "build_env first"};
+    if (D_min < 1 || D_max < D_min || !(eps > 0.0) || (dir != 1 && dir != -1))
+      throw Fail{QCDMRG_EINVAL, "1 <= D_min <= D_max, eps > 0 and dir = +1 or -1"};
+    if ((dir > 0 && E.center + 2 >= E.L) || (dir < 0 && E.center == 0))
+      throw Fail{QCDMRG_EINVAL, "the centre cannot move further in that direction"};
+    int nk = 0;
+    double e = E.truncate_move(D_max, dir, 0.0, eps, D_min, &nk);
+    if (trunc_err) *trunc_err = e;
+    if (kept) *kept = nk;
+    return QCDMRG_OK;
+  });
+}
+
+int qcdmrg_extrapolate(const double* x, const double* energy, int n, int degree, double* coef) {
+  // least-squares polynomial E(x) = coef[0] + coef[1] x + ... + coef[degree] x^degree
+  // through the n points; x is scaled to [-1, 1] for the normal equations, whose
+  // (degree + 1)^2 system is solved by Gaussian elimination with partial pivoting
+  if (!x || !energy || !coef || degree < 1 || degree > 3 || n < degree + 1) return QCDMRG_EINVAL;
+  double xs = 0;
+  for (int i = 0; i < n; ++i) {
+    if (!std::isfinite(x[i]) || !std::isfinite(energy[i])) return QCDMRG_EINVAL;
+    xs = std::max(xs, std::fabs(x[i]));
+  }
+  if (!(xs > 0)) return QCDMRG_EINVAL;
+  const int m = degree + 1;
+  long double A[4][5] = {};
+  for (int i = 0; i < n; ++i) {
+    long double p[4];
+    p[0] = 1;
+    for (int k = 1; k < m; ++k) p[k] = p[k - 1] * (x[i] / xs);
+    for (int r = 0; r < m; ++r) {
+      for (int c = 0; c < m; ++c) A[r][c] += p[r] * p[c];
+      A[r][m] += p[r] * energy[i];
+    }
+  }
+  for (int c = 0; c < m; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < m; ++r)
+      if (std::fabs((double)A[r][c]) > std::fabs((double)A[piv][c])) piv = r;
+    if (!(std::fabs((double)A[piv][c]) > 0)) return QCDMRG_EINVAL;   // points do not fix the polynomial
+    for (int k = 0; k <= m; ++k) std::swap(A[c][k], A[piv][k]);
+    for (int r = 0; r < m; ++r) {
+      if (r == c) continue;
+      const long double f = A[r][c] / A[c][c];
+      for (int k = c; k <= m; ++k) A[r][k] -= f * A[c][k];
+    }
+  }
+  double sc = 1.0;
+  for (int k = 0; k < m; ++k) {
+    coef[k] = (double)(A[k][m] / A[k][k]) / sc;
+    sc *= xs;
+  }
+  return QCDMRG_OK;
+}
+
 int qcdmrg_move_center(qcdmrg_ctx* ctx, int target) {
   return guard(ctx, [&]() {
     Engine& E = ctx->eng;
@@ -768,6 +827,8 @@ int qcdmrg_sweep(qcdmrg_ctx* ctx, const qcdmrg_sweep_opts* o, qcdmrg_sweep_repor
     Engine& E = ctx->eng;
     if (!E.have_env) throw Fail{QCDMRG_ESTATE, "build_env first"};
     if (!o || o->D < 1) throw Fail{QCDMRG_EINVAL, "sweep options with D >= 1 required"};
+    if (o->trunc_eps < 0.0 || (o->trunc_eps > 0.0 && (o->D_min < 1 || o->D_min > o->D)))
+      throw Fail{QCDMRG_EINVAL, "dynamic selection needs 1 <= D_min <= D"};
     if (E.L < 3) throw Fail{QCDMRG_EINVAL, "sweeps need L >= 3"};
     auto t0 = std::chrono::steady_clock::now();
     while (E.center > 0) E.truncate_move(1 << 30, -1, 1e-28);
@@ -781,8 +842,10 @@ int qcdmrg_sweep(qcdmrg_ctx* ctx, const qcdmrg_sweep_opts* o, qcdmrg_sweep_repor
       R.energy = r.energy;
       R.energy_mixed = r.energy_mixed;
       R.n_steps++;
-      double e = E.truncate_move(o->D, dir, 0.0);
+      int nk = 0;
+      double e = E.truncate_move(o->D, dir, 0.0, o->trunc_eps, o->D_min, &nk);
       R.max_trunc_err = std::max(R.max_trunc_err, e);
+      R.max_D = std::max(R.max_D, nk);
     };
     for (int l = 0; l < E.L - 2; ++l) step(+1);
     for (int l = E.L - 2; l > 0; --l) step(-1);

@@ -670,7 +670,7 @@ DavResult Engine::davidson(const DavOpts& o) {
   return R;
 }
 
-double Engine::truncate_move(int D, int dir, double drop_below) {
+double Engine::truncate_move(int D, int dir, double drop_below, double eps, int Dmin, int* kept) {
   // a negative drop_below keeps every weight above the rounding noise of its
   // own sector's eigenvalues (exact moves for measurements); otherwise weights
   // at the global rounding floor are always dropped
@@ -763,6 +763,19 @@ double Engine::truncate_move(int D, int dir, double drop_below) {
     if (std::get<1>(a) != std::get<1>(b)) return std::get<1>(a) < std::get<1>(b);
     return std::get<2>(a) < std::get<2>(b);
   });
+  if (eps > 0.0) {
+    // dynamic block-state selection: tail[j] = sum of the weights from j on
+    const int n = (int)cand.size();
+    std::vector<double> tail(n + 1, 0.0);
+    for (int j = n - 1; j >= 0; --j) tail[j] = tail[j + 1] + std::max(0.0, -std::get<0>(cand[j]));
+    int De = std::min(D, n);
+    for (int d = std::max(1, Dmin); d <= std::min(D, n); ++d)
+      if (tail[d] <= eps) {
+        De = d;
+        break;
+      }
+    D = std::max(1, De);
+  }
   // weights equal up to rounding (within TIE_REL of the D-th) are kept or
   // dropped together: a group straddling the cut is dropped (spin-flip pairs
   // of Sz = 0 states carry equal weights; rounding must not pick one)
@@ -794,6 +807,7 @@ double Engine::truncate_move(int D, int dir, double drop_below) {
     }
   }
   if (nk == 0) throw std::runtime_error("truncation kept no state");
+  if (kept) *kept = nk;
   // new bond basis
   Basis nb;
   nb.su2 = su2;

@@ -108,7 +108,11 @@ struct Engine {
   // rounding floor 1e-14; a negative drop_below keeps every positive weight),
   // renormalize and move the centre by dir (+1 right, -1 left); returns the
   // discarded weight
-  double truncate_move(int D, int dir, double drop_below);
+  // eps > 0: dynamic block-state selection, the bond dimension is the smallest
+  // D' in [Dmin, D] whose discarded weight (all weights beyond the D' largest)
+  // is at most eps, then the selection above runs with D'; *kept (if given)
+  // receives the number of states kept
+  double truncate_move(int D, int dir, double drop_below, double eps = 0.0, int Dmin = 1, int* kept = nullptr);
   // <psi| sum_t c_t O_L (x) O_R |psi> for a list of centre terms
   double expect(const std::vector<CenterTerm>& terms);
   // spin-summed one-particle density matrix gamma_pq = <E_pq> of the

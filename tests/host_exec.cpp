@@ -401,19 +401,33 @@ int main(int argc, char** argv) {
       const int D = std::atoi(argv[4]), nsw = std::atoi(argv[5]);
       DavOpts o;
       o.tol = std::atof(argv[6]);
+      // optional dynamic block-state selection: eps and D_min
+      const double eps = argc >= 8 ? std::atof(argv[7]) : 0.0;
+      const int dmin = argc >= 9 ? std::atoi(argv[8]) : 1;
       while (E.center > 0) E.truncate_move(1 << 30, -1, 1e-28);
       std::vector<double> energies;
+      int maxk = 0, sumk = 0;
       for (int sw = 0; sw < nsw; ++sw) {
         double e = 0.0;
         for (int l = 0; l < L - 2; ++l) {
           e = E.davidson(o).energy;
-          E.truncate_move(D, +1, 0.0);
+          int k = 0;
+          E.truncate_move(D, +1, 0.0, eps, dmin, &k);
+          maxk = std::max(maxk, k);
+          sumk += k;
         }
         for (int l = L - 2; l > 0; --l) {
           e = E.davidson(o).energy;
-          E.truncate_move(D, -1, 0.0);
+          int k = 0;
+          E.truncate_move(D, -1, 0.0, eps, dmin, &k);
+          maxk = std::max(maxk, k);
+          sumk += k;
         }
         energies.push_back(e);
+      }
+      if (eps > 0.0) {
+        energies.push_back((double)maxk);
+        energies.push_back((double)sumk);
       }
       FILE* o2 = std::fopen(argv[2], "wb");
       if (!o2) throw std::runtime_error("cannot open output");

@@ -66,3 +66,29 @@ def test_su2_accepts_the_normal_complementary_switch():
     assert rc != -1
     if rc == 0:
         lib.qcdmrg_destroy(h)
+
+
+def test_extrapolation_recovers_exact_polynomials():
+    """qcdmrg_extrapolate (no context, no device): points on a known line or parabola give
+    back its coefficients, whose first is the truncation-free energy; the paper's two
+    extrapolations are a parabola in 1/D and a line in the truncation error."""
+    import numpy as np
+    import paper_2603_28648_b300 as qd
+    lib = qd.load(ensure_built())
+    eps = np.array([3e-5, 2e-5, 1.2e-5, 6e-6, 2.5e-6])
+    e0, a = -327.2469, 41.7
+    c = qd.extrapolate(eps, e0 + a * eps, 1, lib=lib)
+    assert abs(c[0] - e0) < 1e-10 and abs(c[1] - a) < 1e-6 * abs(a)
+    inv_d = 1.0 / np.array([1024, 2048, 4096, 8192, 12288])
+    b, q2 = 0.93, -310.0
+    c = qd.extrapolate(inv_d, e0 + b * inv_d + q2 * inv_d ** 2, 2, lib=lib)
+    assert abs(c[0] - e0) < 1e-9 and abs(c[1] - b) < 1e-6 and abs(c[2] - q2) < 1e-3
+    # least squares: symmetric noise around a line leaves the line
+    x = np.array([1.0, 2.0, 3.0, 4.0])
+    y = 2.0 + 0.5 * x + np.array([0.1, -0.1, -0.1, 0.1])
+    c = qd.extrapolate(x, y, 1, lib=lib)
+    assert abs(c[0] - 2.0) < 1e-12 and abs(c[1] - 0.5) < 1e-12
+    # too few points, equal abscissae, bad degree
+    for xs, ys, deg in (([1.0], [1.0], 1), ([1.0, 1.0, 1.0], [1.0, 2.0, 3.0], 1), ([1.0, 2.0], [1.0, 2.0], 4)):
+        with pytest.raises(qd.QcdmrgError):
+            qd.extrapolate(xs, ys, deg, lib=lib)

@@ -512,3 +512,39 @@ def test_tiled_passes_match_the_oracle(host_exec, tmp_path, L, N, two_s, D, c, b
         n = len(out) // 2
         assert np.linalg.norm(out[n:] - ref) <= 1e-12 * np.linalg.norm(ref)
     assert passes[0] == 1 and passes[budget] > 1
+
+
+@pytest.mark.parametrize("sym,L,N,s,D,c,eps,dmin", [("u1", 6, 6, 0, 16, 2, 1e-4, 2), ("su2", 6, 6, 0, 12, 2, 1e-2, 2),
+                                                    ("su2", 6, 5, 1, 12, 2, 1e-3, 3)])
+def test_dynamic_selection_sweeps_match_the_oracle(host_exec, tmp_path, sym, L, N, s, D, c, eps, dmin):
+    """Sweeps whose truncations keep the smallest bond dimension in [D_min, D] with a
+    discarded weight of at most eps, against the oracle's sweeps with the same rule:
+    energies (1e-9) and the largest number of states kept."""
+    if sym == "u1":
+        from oracle.dmrgu1 import DMRGU1
+        from oracle.mpsu1 import MPSU1
+        mps = MPSU1.from_raw(q.random_mps_blocks(L, N, s, D, q.SYM_U1, 2, c))
+        h, V = q.make_integrals(L, 13)
+        fin, fout = str(tmp_path / "in.bin"), str(tmp_path / "out.bin")
+        _write(fin, mps, h, V)
+        env = _env(0)
+        orc = DMRGU1(h, V, N, s)
+    else:
+        from oracle.dmrgsu2 import DMRGSU2, MPSSU2
+        mps = MPSSU2.from_raw(q.random_mps_blocks(L, N, s, D, q.SYM_SU2, 2, c))
+        h, V = q.make_integrals(L, 13)
+        fin, fout = str(tmp_path / "in.bin"), str(tmp_path / "out.bin")
+        _write_su2(fin, mps, h, V)
+        env = dict(_env(0), HOST_EXEC_SU2="1")
+        orc = DMRGSU2(h, V, N, s)
+    r = subprocess.run([host_exec, fin, fout, "sweep", str(D), "2", "1e-10", repr(eps), str(dmin)],
+                       capture_output=True, text=True, timeout=900, env=env)
+    assert r.returncode == 0, r.stderr
+    out = np.fromfile(fout, "<f8")
+    E, maxk, sumk = out[:-2], int(out[-2]), int(out[-1])
+    Eo, _, _ = orc.sweeps(mps, D, nsweeps=2, tol=1e-12, trunc_eps=eps, D_min=dmin)
+    assert np.abs(E - np.array(Eo)).max() <= 1e-9
+    assert (maxk, sumk) == (orc.max_kept, orc.total_kept)
+    # the rule kept fewer states than the fixed bond dimension does
+    orc.sweeps(mps, D, nsweeps=2, tol=1e-12)
+    assert sumk < orc.total_kept

@@ -80,3 +80,29 @@ def test_kept_plus_discarded_is_the_total_and_matches_brute_force():
         assert abs(sum(_kept_weights(w, kept)) + disc - 1.0) < 1e-13
         for qn, ks in kept.items():
             assert ks == sorted(set(ks))
+
+
+# Dynamic block-state selection (dbss_bond_dimension): the smallest D in
+# [D_min, D_max] whose tail of weights beyond the D largest is at most eps.
+def test_dbss_picks_the_smallest_bond_dimension_within_the_error():
+    from oracle.dmrgu1 import dbss_bond_dimension
+    # weights 0.5, 0.3 | 0.15 | 0.04, 0.01 over three sectors; tails after D = 1..5:
+    # 0.5, 0.2, 0.05, 0.01, 0
+    w = {(2, 0): [0.5, 0.04], (3, 1): [0.3, 0.01], (1, 1): [0.15]}
+    b = _blocks(w)
+    assert dbss_bond_dimension(b, 0.05 + 1e-15, 1, 10) == 3
+    assert dbss_bond_dimension(b, 0.049, 1, 10) == 4
+    assert dbss_bond_dimension(b, 0.6, 1, 10) == 1
+    assert dbss_bond_dimension(b, 1e-6, 1, 10) == 5
+    # bounds: D_min raises it, D_max caps it
+    assert dbss_bond_dimension(b, 0.6, 4, 10) == 4
+    assert dbss_bond_dimension(b, 1e-6, 1, 2) == 2
+    # the selection with that D discards at most eps (no ties here)
+    for eps in (0.3, 0.2, 0.05 + 1e-15, 0.011, 1e-3):
+        kept, disc = select_kept(b, dbss_bond_dimension(b, eps, 1, 10))
+        assert disc <= eps
+        # and one state fewer would discard more than eps
+        n = sum(len(v) for v in kept.values())
+        if n > 1:
+            _, disc1 = select_kept(b, n - 1)
+            assert disc1 > eps
