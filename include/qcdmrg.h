@@ -479,6 +479,35 @@ int qcdmrg_truncate_dbss(qcdmrg_ctx* ctx, int D_min, int D_max, double eps, int 
  */
 int qcdmrg_extrapolate(const double* x, const double* energy, int n, int degree, double* coef);
 
+/*
+ * DMRG-SCF orbital step, host arrays, no context and no device (the paper's
+ * CAS-SCF orbital optimisation around its DMRG, New benchmark system section).
+ * n orbitals: core 0..ncore-1 doubly occupied, active ncore..ncore+nact-1 (the
+ * DMRG active space, in chain order), virtual the rest; h n*n, V n^4 as in
+ * qcdmrg_load_integrals. Errors: EINVAL (sizes, NULL arrays).
+ *
+ * qcdmrg_active_space: the frozen-core energy e_core = sum_c 2 h_cc +
+ * sum_cd (2 (cc|dd) - (cd|dc)), the active one-electron integrals h_act
+ * (nact*nact) = h_tu + sum_c (2 (tu|cc) - (tc|cu)) and V_act (nact^4) = (tu|vw),
+ * ready for qcdmrg_load_integrals(ctx, nact, h_act, V_act, e_core).
+ *
+ * qcdmrg_orbital_gradient: grad (n*n, antisymmetric) = dE/dkappa_pq of
+ * E = e_core + sum h_act gamma1 + 1/2 sum V_act gamma2 at fixed density matrices
+ * (gamma1 nact*nact as qcdmrg_rdm1, gamma2 nact^4 as qcdmrg_rdm2) when the
+ * orbitals rotate as the columns of exp(kappa), one parameter per pair p > q;
+ * grad = 2 (F - F^T) with the generalised Fock matrix F.
+ *
+ * qcdmrg_rotate_orbitals: U = exp(kappa) for an antisymmetric kappa (n*n; EINVAL
+ * otherwise), h_out = U^T h U, V_out = (pq|rs) in the rotated orbitals; U may be
+ * NULL. A steepest-descent step is kappa = -step * grad.
+ */
+int qcdmrg_active_space(int n, int ncore, int nact, const double* h, const double* V, double* e_core,
+                        double* h_act, double* V_act);
+int qcdmrg_orbital_gradient(int n, int ncore, int nact, const double* h, const double* V, const double* gamma1,
+                            const double* gamma2, double* grad);
+int qcdmrg_rotate_orbitals(int n, const double* kappa, const double* h, const double* V, double* U, double* h_out,
+                           double* V_out);
+
 /* Move the centre to sites (target, target+1) without truncation (only
  * weights <= 1e-14, rounding noise, dropped), renormalizing each grown
  * block (Method section). Errors: ESTATE, EINVAL (target outside 0..L-2). */

@@ -83,7 +83,8 @@ EXPORTS = [
     "qcdmrg_apply_heff_noalloc", "qcdmrg_graph_create", "qcdmrg_graph_launch",
     "qcdmrg_graph_info", "qcdmrg_graph_destroy", "qcdmrg_rdm1", "qcdmrg_rdm2", "qcdmrg_rdm2_sweep", "qcdmrg_set_psi",
     "qcdmrg_export_mps", "qcdmrg_checkpoint", "qcdmrg_restore", "qcdmrg_psi_layout",
-    "qcdmrg_energy_grad", "qcdmrg_truncate_dbss", "qcdmrg_extrapolate",
+    "qcdmrg_energy_grad", "qcdmrg_truncate_dbss", "qcdmrg_extrapolate", "qcdmrg_active_space",
+    "qcdmrg_orbital_gradient", "qcdmrg_rotate_orbitals",
 ]
 
 _lib = None
@@ -140,6 +141,10 @@ def load(path=None):
     lib.qcdmrg_sweep.argtypes = [P, ctypes.POINTER(SweepOpts), ctypes.POINTER(SweepReport)]
     lib.qcdmrg_truncate_dbss.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, dp, ip]
     lib.qcdmrg_extrapolate.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, dp]
+    ci = ctypes.c_int
+    lib.qcdmrg_active_space.argtypes = [ci, ci, ci, dp, dp, dp, dp, dp]
+    lib.qcdmrg_orbital_gradient.argtypes = [ci, ci, ci, dp, dp, dp, dp, dp]
+    lib.qcdmrg_rotate_orbitals.argtypes = [ci, dp, dp, dp, dp, dp, dp]
     for f in EXPORTS:
         getattr(lib, f).restype = getattr(lib, f).restype or ctypes.c_int
     lib.qcdmrg_last_error.restype = ctypes.c_char_p
@@ -373,6 +378,51 @@ def extrapolate(x, energy, degree=1, lib=None):
     if rc != 0:
         raise QcdmrgError(rc, "qcdmrg_extrapolate: invalid points")
     return c
+
+
+def _f64(a):
+    import numpy as np
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def active_space(h, V, ncore, nact, lib=None):
+    """qcdmrg_active_space: (e_core, h_act, V_act) of the frozen-core active space."""
+    import numpy as np
+    lib = lib or load()
+    h, V = _f64(h), _f64(V)
+    n = h.shape[0]
+    e = ctypes.c_double()
+    ha, Va = np.zeros((nact, nact)), np.zeros((nact,) * 4)
+    rc = lib.qcdmrg_active_space(n, ncore, nact, _dptr(h), _dptr(V), ctypes.byref(e), _dptr(ha), _dptr(Va))
+    if rc != 0:
+        raise QcdmrgError(rc, "qcdmrg_active_space: invalid arguments")
+    return e.value, ha, Va
+
+
+def orbital_gradient(h, V, ncore, nact, gamma1, gamma2, lib=None):
+    """qcdmrg_orbital_gradient: dE/dkappa (n x n, antisymmetric)."""
+    import numpy as np
+    lib = lib or load()
+    h, V, g1, g2 = _f64(h), _f64(V), _f64(gamma1), _f64(gamma2)
+    n = h.shape[0]
+    G = np.zeros((n, n))
+    rc = lib.qcdmrg_orbital_gradient(n, ncore, nact, _dptr(h), _dptr(V), _dptr(g1), _dptr(g2), _dptr(G))
+    if rc != 0:
+        raise QcdmrgError(rc, "qcdmrg_orbital_gradient: invalid arguments")
+    return G
+
+
+def rotate_orbitals(kappa, h, V, lib=None):
+    """qcdmrg_rotate_orbitals: (U = exp(kappa), h', V') for an antisymmetric kappa."""
+    import numpy as np
+    lib = lib or load()
+    k, h, V = _f64(kappa), _f64(h), _f64(V)
+    n = h.shape[0]
+    U, h2, V2 = np.zeros((n, n)), np.zeros((n, n)), np.zeros((n,) * 4)
+    rc = lib.qcdmrg_rotate_orbitals(n, _dptr(k), _dptr(h), _dptr(V), _dptr(U), _dptr(h2), _dptr(V2))
+    if rc != 0:
+        raise QcdmrgError(rc, "qcdmrg_rotate_orbitals: kappa must be antisymmetric")
+    return U, h2, V2
 
 
 class HeffGraph:

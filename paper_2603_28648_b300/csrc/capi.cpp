@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/qcdmrg.h"
+#include "orbitals.hpp"
 #include "core.hpp"
 #include "engine.hpp"
 #include "kernels.hpp"
@@ -808,6 +809,37 @@ int qcdmrg_extrapolate(const double* x, const double* energy, int n, int degree,
     coef[k] = (double)(A[k][m] / A[k][k]) / sc;
     sc *= xs;
   }
+  return QCDMRG_OK;
+}
+
+int qcdmrg_active_space(int n, int ncore, int nact, const double* h, const double* V, double* e_core,
+                        double* h_act, double* V_act) {
+  if (n < 1 || ncore < 0 || nact < 1 || ncore + nact > n || !h || !V || !e_core || !h_act || !V_act)
+    return QCDMRG_EINVAL;
+  active_space(n, ncore, nact, h, V, e_core, h_act, V_act);
+  return QCDMRG_OK;
+}
+
+int qcdmrg_orbital_gradient(int n, int ncore, int nact, const double* h, const double* V, const double* gamma1,
+                            const double* gamma2, double* grad) {
+  if (n < 1 || ncore < 0 || nact < 1 || ncore + nact > n || !h || !V || !gamma1 || !gamma2 || !grad)
+    return QCDMRG_EINVAL;
+  orbital_gradient(n, ncore, nact, h, V, gamma1, gamma2, grad);
+  return QCDMRG_OK;
+}
+
+int qcdmrg_rotate_orbitals(int n, const double* kappa, const double* h, const double* V, double* U, double* h_out,
+                           double* V_out) {
+  if (n < 1 || !kappa || !h || !V || !h_out || !V_out) return QCDMRG_EINVAL;
+  for (int p = 0; p < n; ++p)
+    for (int q = 0; q <= p; ++q) {
+      const double a = kappa[(size_t)p * n + q], b = kappa[(size_t)q * n + p];
+      if (!std::isfinite(a) || std::fabs(a + b) > 1e-12 * std::max(1.0, std::fabs(a))) return QCDMRG_EINVAL;
+    }
+  std::vector<double> u((size_t)n * n);
+  expm_antisym(n, kappa, u.data());
+  rotate_integrals(n, u.data(), h, V, h_out, V_out);
+  if (U) std::copy(u.begin(), u.end(), U);
   return QCDMRG_OK;
 }
 
