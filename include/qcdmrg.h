@@ -312,8 +312,8 @@ int qcdmrg_psi_layout(const qcdmrg_ctx* ctx, int* blocks, int cap, int* nblocks,
  * product), dpsi = dE/dpsi = 2 (H_eff psi - E psi)/<psi|psi> (psi size),
  * gamma1 = dE/dh (L*L, as qcdmrg_rdm1: needs the centre at (L-2, L-1)),
  * gamma2 = 2 dE/dV for 8-fold symmetric V (L^4, as qcdmrg_rdm2: L^4/8
- * environment builds, for L <= 10, either symmetry; beyond, QCDMRG_U1 only,
- * the permutation average of qcdmrg_rdm2_sweep). The derivatives the paper's DMRG-SCF needs (New
+ * environment builds, for L <= 10; beyond, the permutation average of
+ * qcdmrg_rdm2_sweep; either symmetry). The derivatives the paper's DMRG-SCF needs (New
  * benchmark system section). Errors: ESTATE, EINVAL, ENOMEM, ECUDA.
  */
 int qcdmrg_energy_grad(qcdmrg_ctx* ctx, double* energy, double* dpsi, double* gamma1, double* gamma2);
@@ -407,7 +407,10 @@ int qcdmrg_rdm2(qcdmrg_ctx* ctx, double* gamma2);
  * walks the chain once by exact moves (every state above the rounding noise of
  * its sector's density-matrix eigenvalues is kept); afterwards the MPS (site
  * tensors, bonds, psi at its centre) is restored as it was and the environment
- * rebuilt once. QCDMRG_U1 only (ESTATE with QCDMRG_SU2). With
+ * rebuilt once. With QCDMRG_SU2 the walk runs on the state's M = S expansion (the
+ * same state as a U(1) MPS whose bond states are all M components of the
+ * multiplets, about 2-3 times as many states), in a temporary U(1) engine; the
+ * SU(2) context is unchanged and its centre prepared again afterwards. With
  * pair_switch set, the environment is rebuilt with normal pairs on the left
  * for the walk and the switched one restored afterwards.
  * Errors: ESTATE (no environment), EINVAL, ENOMEM, ECUDA.

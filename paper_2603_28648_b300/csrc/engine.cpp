@@ -3,6 +3,7 @@
 // two-site wavefunction transformation that moves the centre.
 #include "engine.hpp"
 #include "su2.hpp"
+#include "su2expand.hpp"
 
 #include <algorithm>
 #include <deque>
@@ -1156,7 +1157,7 @@ std::vector<double> Engine::rdm1_su2() {
 }
 
 std::vector<double> Engine::rdm2_sweep() {
-  if (su2) throw StateError("the centre walk measures with the U(1) operators; with SU(2) use rdm2 (probes)");
+  if (su2) return rdm2_sweep_su2();
   // Gamma_pqrs = sum over spins sigma, tau of <a+_{p sigma} a+_{r tau} a_{s tau} a_{q sigma}>,
   // each element measured at the one centre (s1, s2 = s1 + 1) where its four
   // operators split into at most two on the left block (stored C, A, B), any
@@ -1345,6 +1346,73 @@ std::vector<double> Engine::rdm2_sweep() {
   }
   restore();
   return G;
+}
+
+std::vector<double> Engine::rdm2_sweep_su2() {
+  if (!have_env) throw StateError("build_env first");
+  SU2Mps in;
+  in.L = L;
+  in.center = center;
+  in.N = N;
+  in.two_s = two_s;
+  in.bonds = bonds;
+  in.site_off = site_off;
+  in.site_nb = site_nb;
+  in.site.resize(L);
+  for (int p = 0; p < L; ++p) {
+    if (!site[p]) continue;
+    const bool left = p < center;
+    const ProdBasis pb = make_prod(left ? bonds[p] : bonds[p + 1], left);
+    const Basis& to = left ? bonds[p + 1] : bonds[p];
+    int64_t n = 0;
+    for (int q = 0; q < pb.prod.nsec(); ++q)
+      if (site_off[p][q] >= 0) n = std::max<int64_t>(n, site_off[p][q] + (int64_t)pb.prod.dim[q] * to.dim[site_nb[p][q]]);
+    in.site[p].resize((size_t)n);
+    if (n) ex->download(in.site[p].data(), site[p], n);
+  }
+  in.psi = get_psi_host();
+  U1Mps out;
+  expand_mps_su2(in, out);
+  Engine U;
+  U.ex = ex;
+  U.pr = pr;
+  U.I = I;
+  U.N = N;
+  U.two_s = two_s;
+  U.L = L;
+  U.su2 = false;
+  U.device = device;
+  U.tmp_budget = tmp_budget;
+  U.hbm_budget = hbm_budget;
+  U.autotune = autotune;
+  U.bonds = out.bonds;
+  U.site.assign(L, 0);
+  U.site_off = out.site_off;
+  U.site_nb = out.site_nb;
+  std::vector<double> g;
+  try {
+    for (int p = 0; p < L; ++p) {
+      if (p == center || p == center + 1) continue;
+      U.site[p] = ex->alloc((int64_t)out.site[p].size());
+      ex->upload(U.site[p], out.site[p].data(), (int64_t)out.site[p].size());
+    }
+    U.center = center;
+    U.set_psi_host(out.psi);
+    U.build_env();
+    g = U.rdm2_sweep();
+  } catch (...) {
+    U.clear();
+    U.ex = nullptr;   // its destructor must not drop the runner's lists again
+    U.pr = nullptr;
+    prepare_center();
+    throw;
+  }
+  U.clear();
+  U.ex = nullptr;
+  U.pr = nullptr;
+  // the U(1) engine's centre replaced this engine's prepared task lists
+  prepare_center();
+  return g;
 }
 
 std::vector<double> Engine::rdm2() {

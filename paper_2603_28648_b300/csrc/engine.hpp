@@ -129,6 +129,10 @@ struct Engine {
   // centres instead of L^4/8 environment builds); the MPS is restored
   // afterwards and its environment rebuilt
   std::vector<double> rdm2_sweep();
+  // SU(2): the same by the walk of a U(1) engine holding the M = S expansion of
+  // the state (its bond states are all M components of the multiplets); this
+  // engine's MPS is untouched and its centre prepared again afterwards
+  std::vector<double> rdm2_sweep_su2();
 };
 
 }  // namespace qd

@@ -17,7 +17,7 @@ import qcinputs as q
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_2603_28648_b300", "csrc")
-HOST_SOURCES = ["core.cpp", "rules.cpp", "rules_su2.cpp", "su2.cpp", "init.cpp", "engine.cpp", "tiled.cpp"]
+HOST_SOURCES = ["core.cpp", "rules.cpp", "rules_su2.cpp", "su2.cpp", "su2expand.cpp", "init.cpp", "engine.cpp", "tiled.cpp"]
 
 
 @pytest.fixture(scope="module")
@@ -548,3 +548,30 @@ def test_dynamic_selection_sweeps_match_the_oracle(host_exec, tmp_path, sym, L, 
     # the rule kept fewer states than the fixed bond dimension does
     orc.sweeps(mps, D, nsweeps=2, tol=1e-12)
     assert sumk < orc.total_kept
+
+
+@pytest.mark.parametrize("L,N,two_s,D,c", [(5, 5, 1, 8, 1), (5, 4, 2, 8, 2), (6, 6, 0, 8, 2)])
+def test_su2_rdm2_by_expanded_walk_equals_the_fci_rdm(host_exec, tmp_path, L, N, two_s, D, c):
+    """The SU(2) two-particle density matrix element by element: the state's M = S
+    expansion (its site tensors and two-site state written through Clebsch-Gordan
+    coefficients as a U(1) MPS) walked by the U(1) centre walk, against the FCI 2-RDM of
+    the determinant-expanded state (no permutation average); afterwards the SU(2) state
+    and its sigma are unchanged."""
+    from oracle.dmrgsu2 import DMRGSU2, MPSSU2
+    from oracle.fci import FCI
+    from tests.test_oracle_dmrgsu2 import projector
+    mps = MPSSU2.from_raw(q.random_mps_blocks(L, N, two_s, D, q.SYM_SU2, 5, c))
+    h, V = q.make_integrals(L, 11)
+    out = _run_su2(host_exec, tmp_path, mps, h, V, ["rdm2sweep"])
+    G = out[:L ** 4].reshape(L, L, L, L)
+    rest = out[L ** 4:]
+    ps, sg = rest[:len(rest) // 2], rest[len(rest) // 2:]
+    P, pairs, space = projector(mps)
+    x = np.array([mps.psi[a, b] for a, b in pairs])
+    v = P @ x
+    _, Gf = FCI(h, V, N, two_s).rdm12(v / np.linalg.norm(v))
+    assert np.abs(G - Gf).max() <= 1e-10
+    psi = mps.psi_to_flat()
+    assert np.abs(ps - psi).max() <= 1e-12
+    ref = mps.psi_to_flat(DMRGSU2(h, V, N, two_s).sigma(mps))
+    assert np.linalg.norm(sg - ref) <= 1e-12 * np.linalg.norm(ref)

@@ -12,7 +12,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_2603_28648_b300", "csrc")
-HOST_SOURCES = ["core.cpp", "rules.cpp", "rules_su2.cpp", "su2.cpp", "init.cpp", "engine.cpp", "tiled.cpp"]
+HOST_SOURCES = ["core.cpp", "rules.cpp", "rules_su2.cpp", "su2.cpp", "su2expand.cpp", "init.cpp", "engine.cpp", "tiled.cpp"]
 
 
 @pytest.fixture(scope="module")
