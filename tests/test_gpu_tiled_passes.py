@@ -63,3 +63,41 @@ def test_one_pass_without_a_budget():
     out, st, mps, h, V = _products(0, 8, 8, 0, 20, 3)
     assert st["tile_passes"] == 1
     assert np.linalg.norm(out[qd.BF16X3] - out[qd.FP64]) <= 2.0 ** -14 * np.linalg.norm(out[qd.FP64])
+
+
+def test_passes_at_the_cas54_36_shape():
+    """L=36, N=54, S=0, D=256 (SU(2), random MPS, centre bond): the BF16x3 product with the
+    T arena split into about eight passes stays within the form's bound of the FP64 product
+    and of the one-pass product."""
+    import paper_2603_28648_b300 as qd
+    ensure_built()
+    h, V = q.make_integrals(36, q.integrals.BASE_SEED + 2)
+    out = {}
+    for budget in (0, None):
+        old = os.environ.get("QCDMRG_TILED_T_BYTES")
+        if budget is None:
+            # an eighth of the one-pass arena
+            os.environ["QCDMRG_TILED_T_BYTES"] = str(max(1, out[0][2] // 8))
+        try:
+            ctx = qd.Context(symmetry=qd.SU2, pair_switch=19)
+            ctx.load_integrals(h, V)
+            ctx.set_target(54, 0)
+            ctx.init_mps(256, q.integrals.BASE_SEED + 1002, 17)
+            ctx.build_env()
+            psi = ctx.psi()
+            s64 = ctx.apply_heff(psi, qd.FP64)
+            s3 = ctx.apply_heff(psi, qd.BF16X3)
+            st = ctx.stats()
+            out[budget] = (s64, s3, st["tile_t_bytes"], st["tile_passes"])
+            ctx.close()
+        finally:
+            if old is None:
+                os.environ.pop("QCDMRG_TILED_T_BYTES", None)
+            else:
+                os.environ["QCDMRG_TILED_T_BYTES"] = old
+    s64, s3a, _, p1 = out[0]
+    _, s3b, _, p8 = out[None]
+    nrm = np.linalg.norm(s64)
+    assert p1 == 1 and p8 >= 6
+    assert np.linalg.norm(s3b - s64) <= 2.0 ** -14 * nrm
+    assert np.linalg.norm(s3b - s3a) <= 2.0 ** -14 * nrm
