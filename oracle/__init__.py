@@ -15,6 +15,10 @@ Modules
              plain definition H_eff = P^T H_FCI P in that space; the same space
              written as a U(1) MPS with the Clebsch-Gordan map of the
              two-site coefficients
+  su2alg     Clebsch-Gordan coefficients, 6j and 9j symbols, recoupling factors
+  dmrgsu2    operator-based SU(2) two-site DMRG with reduced operators
+  casscf     orbital rotation, frozen-core active space and the energy of
+             rotated orbitals at fixed density matrices (DMRG-SCF pieces)
 
 Conventions (the paper states none; fixed here and used by both sides):
   H = sum_pq h_pq E_pq + 1/2 sum_pqrs (pq|rs) (E_pq E_rs - delta_qr E_ps) + e_core,

@@ -1,4 +1,8 @@
-"""Plain orbital-optimisation pieces of DMRG-SCF (test infrastructure only).
+"""Plain orbital-optimisation pieces of DMRG-SCF (oracle).
+
+TEST INFRASTRUCTURE (oracle): imported only by tests/, smoke() and bench.py's
+CPU-baseline leg.
+
 
 The paper couples its spin-adapted DMRG to a CAS-SCF orbital optimisation (New benchmark
 system section): the active-space solver supplies the one- and two-particle density
