@@ -3,7 +3,6 @@
 TEST INFRASTRUCTURE (oracle): imported only by tests/, smoke() and bench.py's
 CPU-baseline leg.
 
-
 The paper couples its spin-adapted DMRG to a CAS-SCF orbital optimisation (New benchmark
 system section): the active-space solver supplies the one- and two-particle density
 matrices, and the orbitals are rotated to lower the energy. The formulas are not printed
