@@ -1255,62 +1255,7 @@ std::vector<double> Engine::rdm2_sweep() {
     const int64_t n = lay.size;
     const double nrm = ex->dot(dpsi, dpsi, n);
     if (!(nrm > 0)) throw std::runtime_error("zero wavefunction");
-    // elements are evaluated in batches: each element's single-term task list
-    // writes its own slot of a batch of vectors (its stage-1 scratch at its own
-    // offset), the lists of a batch run merged chunk by chunk, and one batched
-    // dot with psi gives all elements of the batch (instead of a synchronous
-    // product and dot per element)
-    const int64_t nn = std::max<int64_t>(1, n);
-    const int bmax = (int)std::max<int64_t>(1, std::min<int64_t>(512, ((int64_t)1 << 29) / nn));
-    uint64_t tau = ex->alloc(nn * bmax);
-    struct Pending { std::array<int, 4> t; int slot; };
-    std::vector<Pending> batch;
-    std::vector<HeffPlan> plans;
-    std::vector<int64_t> toff;
-    int64_t tmp_used = 0;
-    auto flush = [&]() {
-      if (batch.empty()) return;
-      ex->tmp(std::max<int64_t>(1, tmp_used));
-      ex->zero(tau, nn * (int64_t)batch.size());
-      size_t rounds = 0;
-      for (const auto& pl : plans) rounds = std::max(rounds, pl.stage1.size());
-      for (size_t r = 0; r < rounds; ++r)
-        for (int st = 0; st < 2; ++st) {
-          Launch m;
-          for (size_t e = 0; e < plans.size(); ++e) {
-            if (r >= plans[e].stage1.size()) continue;
-            const Launch& l = st == 0 ? plans[e].stage1[r] : plans[e].stage2[r];
-            const int s0 = (int)m.segs.size();
-            for (Seg g : l.segs) {
-              if (g.abuf == B_TMP) g.a += (uint64_t)toff[e];
-              if (g.bbuf == B_TMP) g.b += (uint64_t)toff[e];
-              m.segs.push_back(g);
-            }
-            for (Prob pr2 : l.probs) {
-              if (pr2.cbuf == B_TMP) pr2.c += (uint64_t)toff[e];
-              else if (pr2.cbuf == B_SIG) pr2.c += (uint64_t)(nn * batch[e].slot);
-              else throw std::logic_error("rdm2_sweep: unexpected output buffer");
-              pr2.seg0 += s0;
-              m.probs.push_back(pr2);
-            }
-            m.flops += l.flops;
-          }
-          if (!m.empty()) ex->run(m, dpsi, tau);
-        }
-      std::vector<uint64_t> xs(batch.size());
-      for (size_t e = 0; e < batch.size(); ++e) xs[e] = tau + 8ull * (uint64_t)(nn * batch[e].slot);
-      std::vector<double> out(batch.size());
-      ex->mdot(xs.data(), (int)xs.size(), dpsi, n, out.data());
-      for (size_t e = 0; e < batch.size(); ++e) {
-        const double v = out[e] / nrm;
-        const int p = batch[e].t[0], q = batch[e].t[1], r = batch[e].t[2], s = batch[e].t[3];
-        G[at(p, q, r, s)] = G[at(r, s, p, q)] = G[at(q, p, s, r)] = G[at(s, r, q, p)] = v;
-      }
-      batch.clear();
-      plans.clear();
-      toff.clear();
-      tmp_used = 0;
-    };
+    uint64_t tau = ex->alloc(std::max<int64_t>(1, n));
     try {
       for (const auto& t : todo[s1]) {
         std::deque<OpView> views;
@@ -1375,16 +1320,20 @@ std::vector<double> Engine::rdm2_sweep() {
             if (X->empty() || Y->empty()) continue;
             terms.push_back({X, false, Y, false, (inv & 1) ? -1.0 : 1.0});
           }
-        if (terms.empty()) continue;   // the element is zero (G starts at zero)
-        HeffPlan pl = plan_terms(Lp, Rp, lay, terms, tmp_budget);
-        if (!batch.empty() && tmp_used + pl.tmp_elems > std::max<int64_t>(tmp_budget, pl.tmp_elems)) flush();
-        batch.push_back({t, (int)batch.size()});
-        toff.push_back(tmp_used);
-        tmp_used += pl.tmp_elems;
-        plans.push_back(std::move(pl));
-        if ((int)batch.size() == bmax) flush();
+        double v = 0.0;
+        if (!terms.empty()) {
+          HeffPlan pl = plan_terms(Lp, Rp, lay, terms, tmp_budget);
+          ex->tmp(std::max<int64_t>(1, pl.tmp_elems));
+          ex->zero(tau, n);
+          for (size_t k = 0; k < pl.stage1.size(); ++k) {
+            ex->run(pl.stage1[k], dpsi, tau);
+            ex->run(pl.stage2[k], dpsi, tau);
+          }
+          v = ex->dot(dpsi, tau, n) / nrm;
+        }
+        const int p = t[0], q = t[1], r = t[2], s = t[3];
+        G[at(p, q, r, s)] = G[at(r, s, p, q)] = G[at(q, p, s, r)] = G[at(s, r, q, p)] = v;
       }
-      flush();
     } catch (...) {
       ex->release(tau);
       throw;
