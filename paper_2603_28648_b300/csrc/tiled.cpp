@@ -2,9 +2,11 @@
 // from the FP64 task lists of the same product.
 #include "tiled.hpp"
 
+#include <cstring>
 #include <map>
 #include <stdexcept>
 #include <tuple>
+#include <unordered_map>
 
 namespace qd {
 
@@ -12,11 +14,42 @@ namespace {
 
 using VKey = std::tuple<uint64_t, int, int, int, int, int, double>;  // src, buf, ld, tr, rows, cols, scale
 
+inline uint64_t mix(uint64_t h, uint64_t v) {
+  // splitmix64 finaliser of the running value
+  h ^= v + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+  h ^= h >> 30;
+  h *= 0xbf58476d1ce4e5b9ull;
+  h ^= h >> 27;
+  h *= 0x94d049bb133111ebull;
+  return h ^ (h >> 31);
+}
+struct VKeyHash {
+  size_t operator()(const VKey& k) const {
+    uint64_t sb = 0;
+    const double sc = std::get<6>(k);
+    if (sc != 0.0) std::memcpy(&sb, &sc, 8);   // +0 and -0 compare equal: one hash
+    uint64_t h = mix(0, std::get<0>(k));
+    h = mix(h, ((uint64_t)(uint32_t)std::get<1>(k) << 32) | (uint32_t)std::get<2>(k));
+    h = mix(h, ((uint64_t)(uint32_t)std::get<3>(k) << 32) | (uint32_t)std::get<4>(k));
+    h = mix(h, (uint64_t)(uint32_t)std::get<5>(k));
+    return (size_t)mix(h, sb);
+  }
+};
+struct PairHash {
+  size_t operator()(const std::pair<int64_t, double>& k) const {
+    uint64_t sb = 0;
+    if (k.second != 0.0) std::memcpy(&sb, &k.second, 8);
+    return (size_t)mix(mix(0, (uint64_t)k.first), sb);
+  }
+};
+
+// views are deduplicated through a hash index; offsets follow insertion order,
+// so the arenas do not depend on the index's iteration order
 struct Arena {
   std::vector<TView>* views;
   int64_t* bytes;
   int panel;
-  std::map<VKey, int64_t> index;
+  std::unordered_map<VKey, int64_t, VKeyHash> index;
   int64_t add(uint64_t src, int buf, int ld, int tr, int rows, int cols, double scale) {
     VKey k{src, buf, ld, tr, rows, cols, scale};
     auto it = index.find(k);
@@ -55,7 +88,7 @@ TiledPlan plan_tiled(const HeffPlan& plan, const PsiLayout& lay, const TileCfg& 
   Arena psi{&P.psivw, &P.psibytes, TP_B, {}};
   Arena am{&P.avw, &P.abytes, TP_A, {}};
   Arena bm{&P.bvw, &P.bbytes, TP_A, {}};
-  std::map<int64_t, int> blk_of_off;
+  std::unordered_map<int64_t, int> blk_of_off;
   std::vector<int64_t> psi_off(lay.blks.size());
   for (size_t i = 0; i < lay.blks.size(); ++i) {
     const auto& b = lay.blks[i];
@@ -72,19 +105,26 @@ TiledPlan plan_tiled(const HeffPlan& plan, const PsiLayout& lay, const TileCfg& 
   };
 
   std::vector<TProd> tps;
+  {
+    size_t n1 = 0, n2 = 0;
+    for (const Launch& l : plan.stage1) n1 += l.probs.size();
+    for (const Launch& l : plan.stage2) n2 += l.segs.size();
+    tps.reserve(n1 + n2 / 8 + 16);
+  }
   auto add_t = [&](int blk, int64_t b, int n, int k, double osc) {
     tps.push_back({blk, b, P.tbytes, n, k, osc});
     P.tbytes += tiled_bytes(n, lay.blks[blk].rows, TP_B);  // transposed: n rows, K = psi rows
     return (int)tps.size() - 1;
   };
-  std::map<std::pair<int64_t, double>, int> copies;  // (psi offset, scalar) -> T_t of psi itself
-  std::map<int64_t, int> sig_of;
+  std::unordered_map<std::pair<int64_t, double>, int, PairHash> copies;  // (psi offset, scalar) -> T_t of psi itself
+  std::unordered_map<int64_t, int> sig_of;
   std::vector<SigBlk> sig;
 
   for (size_t c = 0; c < plan.stage1.size(); ++c) {
     const Launch& L1 = plan.stage1[c];
     const Launch& L2 = plan.stage2[c];
-    std::map<uint64_t, int> t_of;  // FP64 stage-1 output offset of this chunk -> T_t
+    std::unordered_map<uint64_t, int> t_of;  // FP64 stage-1 output offset of this chunk -> T_t
+    t_of.reserve(L1.probs.size());
     for (const Prob& p : L1.probs) {
       const Seg& h = L1.segs[p.seg0];
       const int blk = blk_at((int64_t)h.a);
