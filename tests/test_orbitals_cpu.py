@@ -90,3 +90,21 @@ def test_steepest_descent_step_lowers_the_energy():
     pred = -step * 0.5 * np.sum(G * G)
     assert e1 < e0
     assert abs((e1 - e0) - pred) <= 0.05 * abs(pred)
+
+
+def test_invalid_orbital_spaces_are_rejected():
+    """EINVAL for orbital spaces that do not fit (core + active > n, no active orbital,
+    negative core) and for NULL arrays, before any work."""
+    import ctypes
+    import paper_2603_28648_b300 as qd
+    lib = qd.load(ensure_built())
+    h, V = q.make_integrals(5, 3)
+    for ncore, nact in ((3, 3), (0, 0), (-1, 2)):
+        with pytest.raises(qd.QcdmrgError):
+            qd.active_space(h, V, ncore, nact, lib=lib)
+        with pytest.raises(qd.QcdmrgError):
+            qd.orbital_gradient(h, V, ncore, nact, np.zeros((2, 2)), np.zeros((2,) * 4), lib=lib)
+    dp = ctypes.POINTER(ctypes.c_double)
+    null = ctypes.cast(None, dp)
+    assert lib.qcdmrg_rotate_orbitals(5, null, null, null, null, null, null) == -1
+    assert lib.qcdmrg_active_space(5, 1, 2, null, null, null, null, null) == -1
