@@ -511,6 +511,47 @@ int qcdmrg_orbital_gradient(int n, int ncore, int nact, const double* h, const d
 int qcdmrg_rotate_orbitals(int n, const double* kappa, const double* h, const double* V, double* U, double* h_out,
                            double* V_out);
 
+/*
+ * Orbital entanglement for the chain ordering: the paper pre-optimises its
+ * chain topology with the quantum-information protocols of Barcza et al.
+ * (2011) and Szalay et al. (2015) (Numerical procedure section).
+ *
+ * qcdmrg_orbital_rdm: the two-orbital reduced density matrices rho_ij of the
+ * normalised state, the partial trace of |Psi><Psi| over every orbital other
+ * than i and j, with the creation operators of orbitals i and j moved to the
+ * front of each determinant (sign of that reordering included). rho: host
+ * array of L*L*256 doubles, block (i, j) at (i*L + j)*256 for i < j, a
+ * row-major 16 x 16 matrix with row (and column) 4 x + y, x the state of
+ * orbital i and y that of orbital j (0 empty, 1 up, 2 down, 3 a+_up a+_dn|0>);
+ * blocks with i >= j are written as zeros. QCDMRG_SU2: of the state's M = S
+ * component. The centre walks the chain once from bond 0 by exact moves (no
+ * truncation) and every right block holds the 16 matrix units of each of its
+ * orbitals (16 (L - p) extra operators in the block at site p); the MPS, its
+ * centre and the environment are restored afterwards. Errors: ESTATE (no
+ * environment), EINVAL (NULL), ENOMEM, ECUDA.
+ *
+ * qcdmrg_orbital_entanglement (host only, no context): from those blocks,
+ * s1[i] = -Tr rho_i ln rho_i (rho_i = Tr_j rho_ij from the pair (i, i+1), or
+ * (i-1, i) for the last orbital; s1 may be NULL) and mutual (L*L, symmetric,
+ * zero diagonal) I_ij = s1[i] + s1[j] + Tr rho_ij ln rho_ij. Eigenvalues at or
+ * below zero add nothing. Errors: EINVAL (L < 2, NULL rho or mutual,
+ * non-finite entries).
+ *
+ * qcdmrg_fiedler_order (host only): order (L, a permutation of 0..L-1) sorts
+ * the orbitals by their component of the Fiedler vector (eigenvector of the
+ * second smallest eigenvalue) of the Laplacian diag(sum_j I_ij) - I; ties keep
+ * index order. fiedler (L, may be NULL) gets the vector, unit length, its first
+ * component of magnitude above 1e-8 of the largest made negative. When the
+ * second eigenvalue is degenerate (a mutual-information graph in several
+ * disconnected parts, or a symmetric one) the vector is one of several and so
+ * is the order. Reordering the integrals as h[order][order], V likewise, puts
+ * strongly entangled orbitals next to each other on the chain. Errors: EINVAL
+ * (L < 2, NULL, mutual not symmetric to 1e-12 or not finite).
+ */
+int qcdmrg_orbital_rdm(qcdmrg_ctx* ctx, double* rho);
+int qcdmrg_orbital_entanglement(int L, const double* rho, double* s1, double* mutual);
+int qcdmrg_fiedler_order(int L, const double* mutual, int* order, double* fiedler);
+
 /* Move the centre to sites (target, target+1) without truncation (only
  * weights <= 1e-14, rounding noise, dropped), renormalizing each grown
  * block (Method section). Errors: ESTATE, EINVAL (target outside 0..L-2). */

@@ -19,6 +19,8 @@ Modules
   dmrgsu2    operator-based SU(2) two-site DMRG with reduced operators
   casscf     orbital rotation, frozen-core active space and the energy of
              rotated orbitals at fixed density matrices (DMRG-SCF pieces)
+  orbital_qi two-orbital reduced density matrices of a determinant vector,
+             orbital entropies, mutual information, Fiedler ordering
 
 Conventions (the paper states none; fixed here and used by both sides):
   H = sum_pq h_pq E_pq + 1/2 sum_pqrs (pq|rs) (E_pq E_rs - delta_qr E_ps) + e_core,

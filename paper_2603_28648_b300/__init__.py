@@ -84,7 +84,8 @@ EXPORTS = [
     "qcdmrg_graph_info", "qcdmrg_graph_destroy", "qcdmrg_rdm1", "qcdmrg_rdm2", "qcdmrg_rdm2_sweep", "qcdmrg_set_psi",
     "qcdmrg_export_mps", "qcdmrg_checkpoint", "qcdmrg_restore", "qcdmrg_psi_layout",
     "qcdmrg_energy_grad", "qcdmrg_truncate_dbss", "qcdmrg_extrapolate", "qcdmrg_active_space",
-    "qcdmrg_orbital_gradient", "qcdmrg_rotate_orbitals",
+    "qcdmrg_orbital_gradient", "qcdmrg_rotate_orbitals", "qcdmrg_orbital_rdm",
+    "qcdmrg_orbital_entanglement", "qcdmrg_fiedler_order",
 ]
 
 _lib = None
@@ -145,6 +146,9 @@ def load(path=None):
     lib.qcdmrg_active_space.argtypes = [ci, ci, ci, dp, dp, dp, dp, dp]
     lib.qcdmrg_orbital_gradient.argtypes = [ci, ci, ci, dp, dp, dp, dp, dp]
     lib.qcdmrg_rotate_orbitals.argtypes = [ci, dp, dp, dp, dp, dp, dp]
+    lib.qcdmrg_orbital_rdm.argtypes = [P, dp]
+    lib.qcdmrg_orbital_entanglement.argtypes = [ci, dp, dp, dp]
+    lib.qcdmrg_fiedler_order.argtypes = [ci, dp, ip, dp]
     for f in EXPORTS:
         getattr(lib, f).restype = getattr(lib, f).restype or ctypes.c_int
     lib.qcdmrg_last_error.restype = ctypes.c_char_p
@@ -322,6 +326,14 @@ class Context:
         self._check(self.lib.qcdmrg_rdm2_sweep(self.h, _dptr(g)))
         return g
 
+    def orbital_rdm(self, L):
+        """Two-orbital reduced density matrices, shape (L, L, 16, 16): [i, j] for i < j is
+        rho_ij with row 4 x + y (x, y the states of orbitals i, j), zero for i >= j; one walk
+        of the centre (the MPS is restored afterwards)."""
+        r = np.empty((L, L, 16, 16))
+        self._check(self.lib.qcdmrg_orbital_rdm(self.h, _dptr(r)))
+        return r
+
     def heff_diag(self):
         out = np.empty(self.psi_size())
         self._check(self.lib.qcdmrg_heff_diag(self.h, _dptr(out), out.size))
@@ -423,6 +435,43 @@ def rotate_orbitals(kappa, h, V, lib=None):
     if rc != 0:
         raise QcdmrgError(rc, "qcdmrg_rotate_orbitals: kappa must be antisymmetric")
     return U, h2, V2
+
+
+def orbital_entanglement(rho, lib=None):
+    """qcdmrg_orbital_entanglement: (s1, mutual) from the (L, L, 16, 16) blocks of
+    Context.orbital_rdm."""
+    import numpy as np
+    lib = lib or load()
+    r = _f64(rho)
+    L = r.shape[0]
+    if r.shape != (L, L, 16, 16):
+        raise ValueError("rho must have shape (L, L, 16, 16)")
+    s1, mi = np.zeros(L), np.zeros((L, L))
+    rc = lib.qcdmrg_orbital_entanglement(L, _dptr(r), _dptr(s1), _dptr(mi))
+    if rc != 0:
+        raise QcdmrgError(rc, "qcdmrg_orbital_entanglement: invalid arguments")
+    return s1, mi
+
+
+def fiedler_order(mutual, lib=None):
+    """qcdmrg_fiedler_order: (order, fiedler vector) of a symmetric mutual-information
+    matrix; h[np.ix_(order, order)] is the reordered chain."""
+    import numpy as np
+    lib = lib or load()
+    m = _f64(mutual)
+    L = m.shape[0]
+    order, f = np.zeros(L, dtype=np.int32), np.zeros(L)
+    rc = lib.qcdmrg_fiedler_order(L, _dptr(m), order.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dptr(f))
+    if rc != 0:
+        raise QcdmrgError(rc, "qcdmrg_fiedler_order: invalid arguments")
+    return order.astype(np.int64), f
+
+
+def reorder_integrals(h, V, order):
+    """Integrals of the chain in the given orbital order: h[o][o], V[o][o][o][o]."""
+    import numpy as np
+    o = np.asarray(order)
+    return _f64(h)[np.ix_(o, o)], _f64(V)[np.ix_(o, o, o, o)]
 
 
 class HeffGraph:

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/qcdmrg.h"
+#include "entanglement.hpp"
 #include "orbitals.hpp"
 #include "core.hpp"
 #include "engine.hpp"
@@ -710,6 +711,37 @@ int qcdmrg_rdm2_sweep(qcdmrg_ctx* ctx, double* gamma2) {
     std::copy(g.begin(), g.end(), gamma2);
     return QCDMRG_OK;
   });
+}
+
+int qcdmrg_orbital_rdm(qcdmrg_ctx* ctx, double* rho) {
+  return guard(ctx, [&]() {
+    Engine& E = ctx->eng;
+    if (!E.have_env) throw Fail{QCDMRG_ESTATE, "build_env first"};
+    if (!rho) throw Fail{QCDMRG_EINVAL, "null argument"};
+    std::vector<double> r = E.orbital_rdm2();
+    std::copy(r.begin(), r.end(), rho);
+    return QCDMRG_OK;
+  });
+}
+
+int qcdmrg_orbital_entanglement(int L, const double* rho, double* s1, double* mutual) {
+  if (L < 2 || !rho || !mutual) return QCDMRG_EINVAL;
+  for (size_t k = 0; k < (size_t)L * L * 256; ++k)
+    if (!std::isfinite(rho[k])) return QCDMRG_EINVAL;
+  orbital_entanglement(L, rho, s1, mutual);
+  return QCDMRG_OK;
+}
+
+int qcdmrg_fiedler_order(int L, const double* mutual, int* order, double* fiedler) {
+  if (L < 2 || !mutual || !order) return QCDMRG_EINVAL;
+  for (int i = 0; i < L; ++i)
+    for (int j = 0; j <= i; ++j) {
+      const double a = mutual[(size_t)i * L + j], b = mutual[(size_t)j * L + i];
+      if (!std::isfinite(a) || !std::isfinite(b) || std::fabs(a - b) > 1e-12 * std::max(1.0, std::fabs(a)))
+        return QCDMRG_EINVAL;
+    }
+  fiedler_order(L, mutual, order, fiedler);
+  return QCDMRG_OK;
 }
 
 int qcdmrg_heff_diag(qcdmrg_ctx* ctx, double* out, size_t n) {

@@ -90,7 +90,8 @@ struct OpView {
 OpView transpose(const OpView& o);
 
 // Operator keys.
-enum Fam : int { F_I = 0, F_C, F_A, F_B, F_S, F_P, F_Q, F_H };
+enum Fam : int { F_I = 0, F_C, F_A, F_B, F_S, F_P, F_Q, F_H,
+                 F_L };  // F_L: matrix unit |a><b| of one spatial orbital (index a, unit 4a + b)
 struct Key {
   int f, a, b, k;   // family, indices, twice the SU(2) rank (0 in U(1))
   Key(int f_ = 0, int a_ = -1, int b_ = -1, int k_ = 0) : f(f_), a(a_), b(b_), k(k_) {}
@@ -229,6 +230,8 @@ inline bool normal_pairs(bool left, int cut, int mid) { return left ? cut <= mid
 struct Enlarged {
   bool left = true;
   bool normal = true;       // pair operators: normal (A, B) or complementary (P, Q)
+  bool local = false;       // set by the caller: a right block also keeps the 16 matrix units
+                            // |a><b| of each of its orbitals (F_L), for orbital density matrices
   bool batched = false;     // set by the caller: wide sums of block operators run as GEMMs
                             // over a coefficient matrix, and renormalized operators store
                             // their blocks in sector order (equal strides across operators)

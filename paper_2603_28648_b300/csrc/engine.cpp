@@ -258,6 +258,7 @@ void Engine::build_env() {
   for (int p = L - 1; p >= center + 2; --p) {
     Enlarged E;
     E.batched = batched_sums();
+    E.local = keep_local && !su2;
     if (su2) enlarge_su2(renv[p + 1], I, *ex, E, normal_at(false, p));
     else enlarge(renv[p + 1], I, *ex, E, &fl, normal_at(false, p));
     EnvBlock nb;
@@ -1413,6 +1414,172 @@ std::vector<double> Engine::rdm2_sweep_su2() {
   // the U(1) engine's centre replaced this engine's prepared task lists
   prepare_center();
   return g;
+}
+
+std::vector<double> Engine::orbital_rdm2() {
+  if (!have_env) throw StateError("build_env first");
+  if (su2) {
+    // the same measurement on the state's M = S expansion (see rdm2_sweep_su2)
+    SU2Mps in;
+    in.L = L;
+    in.center = center;
+    in.N = N;
+    in.two_s = two_s;
+    in.bonds = bonds;
+    in.site_off = site_off;
+    in.site_nb = site_nb;
+    in.site.resize(L);
+    for (int p = 0; p < L; ++p) {
+      if (!site[p]) continue;
+      const bool left = p < center;
+      const ProdBasis pb = make_prod(left ? bonds[p] : bonds[p + 1], left);
+      const Basis& to = left ? bonds[p + 1] : bonds[p];
+      int64_t n = 0;
+      for (int q = 0; q < pb.prod.nsec(); ++q)
+        if (site_off[p][q] >= 0) n = std::max<int64_t>(n, site_off[p][q] + (int64_t)pb.prod.dim[q] * to.dim[site_nb[p][q]]);
+      in.site[p].resize((size_t)n);
+      if (n) ex->download(in.site[p].data(), site[p], n);
+    }
+    in.psi = get_psi_host();
+    U1Mps out;
+    expand_mps_su2(in, out);
+    Engine U;
+    U.ex = ex;
+    U.pr = pr;
+    U.I = I;
+    U.N = N;
+    U.two_s = two_s;
+    U.L = L;
+    U.device = device;
+    U.tmp_budget = tmp_budget;
+    U.hbm_budget = hbm_budget;
+    U.autotune = autotune;
+    U.bonds = out.bonds;
+    U.site.assign(L, 0);
+    U.site_off = out.site_off;
+    U.site_nb = out.site_nb;
+    std::vector<double> r;
+    try {
+      for (int p = 0; p < L; ++p) {
+        if (p == center || p == center + 1) continue;
+        U.site[p] = ex->alloc((int64_t)out.site[p].size());
+        ex->upload(U.site[p], out.site[p].data(), (int64_t)out.site[p].size());
+      }
+      U.center = center;
+      U.set_psi_host(out.psi);
+      U.build_env();
+      r = U.orbital_rdm2();
+    } catch (...) {
+      U.clear();
+      U.ex = nullptr;
+      U.pr = nullptr;
+      prepare_center();
+      throw;
+    }
+    U.clear();
+    U.ex = nullptr;
+    U.pr = nullptr;
+    prepare_center();
+    return r;
+  }
+  std::vector<double> R((size_t)L * L * 256, 0.0);
+  // the MPS before the walk, restored exactly afterwards
+  const int c0 = center;
+  const std::vector<Basis> bonds0 = bonds;
+  const std::vector<std::vector<int64_t>> off0 = site_off;
+  const std::vector<std::vector<int>> nb0 = site_nb;
+  const std::vector<double> psi0 = get_psi_host();
+  std::vector<std::vector<double>> site0(L);
+  for (int p = 0; p < L; ++p) {
+    if (!site[p]) continue;
+    const bool left = p < center;
+    const ProdBasis pb = make_prod(left ? bonds[p] : bonds[p + 1], left);
+    const Basis& to = left ? bonds[p + 1] : bonds[p];
+    int64_t n = 0;
+    for (int q = 0; q < pb.prod.nsec(); ++q)
+      if (site_off[p][q] >= 0) n = std::max<int64_t>(n, site_off[p][q] + (int64_t)pb.prod.dim[q] * to.dim[site_nb[p][q]]);
+    site0[p].resize((size_t)n);
+    if (n) ex->download(site0[p].data(), site[p], n);
+  }
+  auto restore = [&]() {
+    keep_local = false;
+    clear_env();
+    for (auto& t : site)
+      if (t) ex->release(t);
+    site.assign(L, 0);
+    for (int p = 0; p < L; ++p) {
+      if (site0[p].empty()) continue;
+      site[p] = ex->alloc((int64_t)site0[p].size());
+      ex->upload(site[p], site0[p].data(), (int64_t)site0[p].size());
+    }
+    bonds = bonds0;
+    site_off = off0;
+    site_nb = nb0;
+    center = c0;
+    set_psi_host(psi0);
+    build_env();
+  };
+  static const int NOCC[4] = {0, 1, 1, 2};
+  static const int SZ2[4] = {0, 1, -1, 0};
+  auto unit = [](int u) {
+    Mat4 m;
+    m(u / 4, u % 4) = 1.0;
+    return m;
+  };
+  auto get = [](const EnvBlock& B, Key k) -> const OpView* {
+    auto it = B.ops.find(k);
+    if (it == B.ops.end() || it->second.empty()) return nullptr;
+    return &it->second;
+  };
+  try {
+    while (center > 0) truncate_move(1 << 30, -1, -1.0);
+    keep_local = true;
+    build_env();   // right blocks with the matrix units of their orbitals
+    for (int s1 = 0; s1 <= L - 2; ++s1) {
+      if (s1 > 0) truncate_move(1 << 30, +1, -1.0);
+      const int s2 = s1 + 1;
+      const EnvBlock& LB = lenv.at(s1);
+      const EnvBlock& RB = renv.at(s2 + 1);
+      const double nrm = ex->dot(dpsi, dpsi, lay.size);
+      if (!(nrm > 0)) throw std::runtime_error("zero wavefunction");
+      for (int j = s2; j < L; ++j)
+        for (int u = 0; u < 16; ++u)
+          for (int v = 0; v < 16; ++v) {
+            const int dn = NOCC[u / 4] - NOCC[u % 4] + NOCC[v / 4] - NOCC[v % 4];
+            const int ds = SZ2[u / 4] - SZ2[u % 4] + SZ2[v / 4] - SZ2[v % 4];
+            if (dn != 0 || ds != 0) continue;
+            const bool ou = (NOCC[u / 4] + NOCC[u % 4]) & 1, ov = (NOCC[v / 4] + NOCC[v % 4]) & 1;
+            Contrib xl;
+            xl.src = nullptr; xl.srcT = false; xl.o = unit(u); xl.coef = 1.0; xl.par = ou;
+            Contrib yr;
+            yr.srcT = false; yr.coef = 1.0;
+            if (j == s2) {
+              yr.src = nullptr; yr.o = unit(v); yr.par = false;
+            } else {
+              yr.src = get(RB, Key(F_L, j, v));
+              if (!yr.src) continue;
+              yr.o = Mat4::id(); yr.par = ov;
+            }
+            OpView X = product_view(LB, I, Lp, {xl}, ou);
+            OpView Y = product_view(RB, I, Rp, {yr}, ov);
+            if (X.empty() || Y.empty()) continue;
+            const double val = expect({CenterTerm{&X, false, &Y, false, 1.0}}) / nrm;
+            // In the basis with orbitals i, j first, E_u(i) = |s_i><r_i| (x) 1 and
+            // E_v(j) = P_i^odd(v) (x) |s_j><r_j| (the fermion string of orbital j's
+            // operators crosses orbital i), so <E_u E_v> = (-1)^(n(r_i) odd(v))
+            // rho_ij[(r_i r_j), (s_i s_j)] with rho_ij = Tr_rest |Psi><Psi|,
+            // u = 4 s_i + r_i, v = 4 s_j + r_j
+            const int r = 4 * (u % 4) + (v % 4), sc = 4 * (u / 4) + (v / 4);
+            const double sg = ((NOCC[u % 4] & 1) && ov) ? -1.0 : 1.0;
+            R[((size_t)s1 * L + j) * 256 + (size_t)r * 16 + sc] = sg * val;
+          }
+    }
+  } catch (...) {
+    restore();
+    throw;
+  }
+  restore();
+  return R;
 }
 
 std::vector<double> Engine::rdm2() {

@@ -133,6 +133,13 @@ struct Engine {
   // the state (its bond states are all M components of the multiplets); this
   // engine's MPS is untouched and its centre prepared again afterwards
   std::vector<double> rdm2_sweep_su2();
+  // two-orbital reduced density matrices rho_ij (16 x 16 in the site basis of
+  // orbitals i < j, row (x_i, y_j) = 4 x + y) of the normalised state for every
+  // pair, as L*L blocks of 256 (i >= j left zero): the centre walks the chain
+  // once by exact moves, right blocks keep the matrix units of their orbitals;
+  // the MPS is restored afterwards. SU(2): of the M = S expansion.
+  bool keep_local = false;
+  std::vector<double> orbital_rdm2();
 };
 
 }  // namespace qd

@@ -771,6 +771,20 @@ void enlarge(const EnvBlock& B, const Integrals& I, Executor& ex, Enlarged& E, d
     const int sm[2] = {2 * c, 2 * c + 1};
     const int y0 = 2 * (c + 1);
     x.view(Key(F_I), {C_(nullptr, false, I4, 1.0, false)}, false);
+    if (E.local) {
+      // matrix units |a><b| of every orbital of s + Y: the site's own (site part
+      // first, no string), the block's carried over with the site's parity when
+      // the unit changes the particle number by one
+      static const int NOCC[4] = {0, 1, 1, 2};
+      for (int u = 0; u < 16; ++u) {
+        const bool odd = (NOCC[u / 4] + NOCC[u % 4]) & 1;
+        Mat4 m;
+        m(u / 4, u % 4) = 1.0;
+        x.view(Key(F_L, c, u), {C_(nullptr, false, m, 1.0, false)}, odd);
+        for (int j = c + 1; j < L; ++j)
+          if (auto U = x.get(Key(F_L, j, u))) x.view(Key(F_L, j, u), {C_(U, false, I4, 1.0, odd)}, odd);
+      }
+    }
     for (int s = 0; s < 2; ++s) x.view(Key(F_C, sm[s]), {C_(nullptr, false, cre(s), 1.0, false)}, true);
     for (int k = y0; k < 2 * L; ++k)
       if (auto C = x.get(Key(F_C, k))) x.view(Key(F_C, k), {C_(C, false, I4, 1.0, true)}, true);

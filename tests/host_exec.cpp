@@ -17,6 +17,8 @@
 //        host_exec in.bin out.bin rdm1                    (1-RDM, centre at L-2)
 //        host_exec in.bin out.bin rdm2sweep               (2-RDM by the centre walk, then
 //                                                          psi and sigma at the centre)
+//        host_exec in.bin out.bin orbrdm                  (two-orbital density matrices,
+//                                                          L*L blocks of 256, then psi, sigma)
 //   in : int64 L, N, two_sz, center, nsec_len (= L+1), sec_len, data_len;
 //        h (L*L), V (L^4) doubles; bond_nsec, bond_sec int32; data doubles
 //   out: sigma of the FP64 task lists, then sigma of the tiled work items; or
@@ -503,6 +505,24 @@ int main(int argc, char** argv) {
       std::fwrite(ps.data(), 8, ps.size(), o4);
       std::fwrite(sv.data(), 8, sv.size(), o4);
       std::fclose(o4);
+      return 0;
+    }
+    if (argc >= 4 && std::string(argv[3]) == "orbrdm") {
+      const std::vector<double> g = E.orbital_rdm2();
+      FILE* o8 = std::fopen(argv[2], "wb");
+      if (!o8) throw std::runtime_error("cannot open output");
+      std::fwrite(g.data(), 8, g.size(), o8);
+      // then psi and sigma at the centre the walk returned to
+      const int64_t n8 = E.lay.size;
+      const uint64_t sg8 = ex.alloc(n8);
+      E.heff(E.dpsi, sg8, nullptr, 0);
+      std::vector<double> ps8((size_t)n8), sv8((size_t)n8);
+      ex.download(ps8.data(), E.dpsi, n8);
+      ex.download(sv8.data(), sg8, n8);
+      std::fwrite(ps8.data(), 8, ps8.size(), o8);
+      std::fwrite(sv8.data(), 8, sv8.size(), o8);
+      ex.release(sg8);
+      std::fclose(o8);
       return 0;
     }
     if (argc >= 4 && std::string(argv[3]) == "rdm2") {

@@ -575,3 +575,85 @@ def test_su2_rdm2_by_expanded_walk_equals_the_fci_rdm(host_exec, tmp_path, L, N,
     assert np.abs(ps - psi).max() <= 1e-12
     ref = mps.psi_to_flat(DMRGSU2(h, V, N, two_s).sigma(mps))
     assert np.linalg.norm(sg - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def _orbital_rdm_ref(dets, v, L):
+    from oracle import orbital_qi as qi
+    R = np.zeros((L, L, 16, 16))
+    for i in range(L):
+        for j in range(i + 1, L):
+            R[i, j] = qi.two_orbital_rdm(dets, v, i, j)
+    return R
+
+
+@pytest.mark.parametrize("L,N,two_sz,D,c,seed,switch,sum_gemm", [(4, 4, 0, 8, 1, 3, 0, 0), (5, 5, 1, 8, 1, 3, 0, 0),
+                                                                  (6, 5, 1, 16, 0, 6, 0, 0), (7, 7, 1, 16, 5, 8, 3, 0),
+                                                                  (7, 7, 1, 16, 5, 8, 4, 1), (8, 8, 0, 32, 3, 7, 0, -1)])
+def test_orbital_rdm_by_centre_walk_matches_the_partial_trace(host_exec, tmp_path, L, N, two_sz, D, c, seed, switch,
+                                                                sum_gemm):
+    """Two-orbital density matrices of every pair by one walk of the centre (right blocks
+    keeping the matrix units of their orbitals) against the partial trace of the expanded
+    MPS vector, element by element; afterwards the MPS is the one imported."""
+    from oracle.fci import FCI
+    from oracle.mpsu1 import MPSU1, Projector
+    m = MPSU1.from_raw(q.random_mps_blocks(L, N, two_sz, D, q.SYM_U1, seed, c))
+    h, V = q.make_integrals(L, seed + 1)
+    fin, fout = str(tmp_path / "o_in.bin"), str(tmp_path / "o_out.bin")
+    _write(fin, m, h, V)
+    r = subprocess.run([host_exec, fin, fout, "orbrdm"], capture_output=True, text=True, timeout=600,
+                       env=_env(switch, sum_gemm))
+    assert r.returncode == 0, r.stderr
+    out = np.fromfile(fout, "<f8")
+    R = out[:L * L * 256].reshape(L, L, 16, 16)
+    f = FCI(h, V, N, two_sz)
+    v = Projector(m, f.space).apply(m.psi)
+    assert np.abs(R - _orbital_rdm_ref(f.space.dets, v, L)).max() <= 1e-12
+    rest = out[L * L * 256:]
+    assert np.array_equal(rest[:rest.size // 2], m.psi_to_flat())
+
+
+@pytest.mark.parametrize("L,N,two_s,D,c", [(5, 5, 1, 8, 1), (5, 4, 2, 8, 2), (6, 6, 0, 8, 2)])
+def test_su2_orbital_rdm_of_the_m_equals_s_component(host_exec, tmp_path, L, N, two_s, D, c):
+    """SU(2): the same walk on the state's M = S expansion against the partial trace of the
+    determinant-expanded state; the SU(2) state and its sigma are unchanged afterwards."""
+    from oracle.dmrgsu2 import DMRGSU2, MPSSU2
+    from tests.test_oracle_dmrgsu2 import projector
+    mps = MPSSU2.from_raw(q.random_mps_blocks(L, N, two_s, D, q.SYM_SU2, 5, c))
+    h, V = q.make_integrals(L, 11)
+    out = _run_su2(host_exec, tmp_path, mps, h, V, ["orbrdm"])
+    R = out[:L * L * 256].reshape(L, L, 16, 16)
+    P, pairs, space = projector(mps)
+    v = P @ np.array([mps.psi[a, b] for a, b in pairs])
+    assert np.abs(R - _orbital_rdm_ref(space.dets, v, L)).max() <= 1e-12
+    rest = out[L * L * 256:]
+    ps, sg = rest[:rest.size // 2], rest[rest.size // 2:]
+    assert np.abs(ps - mps.psi_to_flat()).max() <= 1e-12
+    ref = mps.psi_to_flat(DMRGSU2(h, V, N, two_s).sigma(mps))
+    assert np.linalg.norm(sg - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def test_orbital_rdm_identities_at_L12(host_exec, tmp_path):
+    """Beyond brute-force sizes (L=12, N=12, D=32): every rho_ij has unit trace, is symmetric
+    and positive semidefinite, and the one-orbital matrix of orbital i is the same from
+    every pair that holds it."""
+    from oracle.mpsu1 import MPSU1
+    L, N, D, c = 12, 12, 32, 5
+    m = MPSU1.from_raw(q.random_mps_blocks(L, N, 0, D, q.SYM_U1, 5, c))
+    h, V = q.make_integrals(L, 6)
+    fin, fout = str(tmp_path / "o_in.bin"), str(tmp_path / "o_out.bin")
+    _write(fin, m, h, V)
+    r = subprocess.run([host_exec, fin, fout, "orbrdm"], capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stderr
+    R = np.fromfile(fout, "<f8")[:L * L * 256].reshape(L, L, 16, 16)
+    one = {}
+    for i in range(L):
+        for j in range(i + 1, L):
+            rr = R[i, j]
+            assert abs(np.trace(rr) - 1) <= 1e-12
+            assert np.abs(rr - rr.T).max() <= 1e-13
+            assert np.linalg.eigvalsh(rr).min() >= -1e-12
+            t = rr.reshape(4, 4, 4, 4)
+            one.setdefault(i, []).append(np.einsum("xyzy->xz", t))
+            one.setdefault(j, []).append(np.einsum("xyxz->yz", t))
+    for i, mats in one.items():
+        assert max(np.abs(mm - mats[0]).max() for mm in mats) <= 1e-12
