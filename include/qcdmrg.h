@@ -552,6 +552,59 @@ int qcdmrg_orbital_rdm(qcdmrg_ctx* ctx, double* rho);
 int qcdmrg_orbital_entanglement(int L, const double* rho, double* s1, double* mutual);
 int qcdmrg_fiedler_order(int L, const double* mutual, int* order, double* fiedler);
 
+/*
+ * Configuration-space warm start: the paper converges its runs with an
+ * SU(2)-aware dynamically extended active space procedure (SU(2)-DEAS, Legeza
+ * et al. 2003; Numerical benchmark section), whose warm-up sweep takes the
+ * environment of each step from a small configuration space rather than from
+ * a previous sweep. Here: select configurations, write them as an MPS whose
+ * left bond bases are exactly their prefixes (centre at the right end), import
+ * it, and run one right-to-left half sweep before the full sweeps.
+ *
+ * Configurations are step vectors of L bytes in chain order, the site-state
+ * indices of the import layout: U(1) 0 = |0>, 1 = a+_up|0>, 2 = a+_dn|0>,
+ * 3 = a+_up a+_dn|0> (a determinant); QCDMRG_SU2 0 = empty, 1 = singly
+ * occupied raising the spin of the orbitals so far by 1/2, 2 = singly occupied
+ * lowering it by 1/2, 3 = doubly occupied (a configuration state function in
+ * the left-to-right, genealogical coupling; the spin so far never negative).
+ *
+ * qcdmrg_select_configs (host only): up to nmax configurations of the target
+ * (N, two_s) ranked by energy, from the aufbau reference (U(1): the orbitals of
+ * lowest h_pp filled with (N + two_s)/2 up and (N - two_s)/2 down electrons;
+ * SU(2): (N - two_s)/2 doubly occupied, the next two_s singly occupied with
+ * all steps up) and every configuration at most two electrons away from it
+ * (SU(2): spatial occupations, each with all of its couplings). Energy: U(1)
+ * <D|H|D>; SU(2) the average of <D|H|D> over the determinants of the spatial
+ * occupation (e_core excluded). Ties: fewer electrons moved, then the step
+ * vector in lexicographic order. steps: nmax * L bytes, energy: nmax doubles
+ * (may be NULL), *count: configurations written. Errors: EINVAL (L < 2,
+ * nmax < 1, NULL, a target outside the Fock space).
+ *
+ * qcdmrg_config_mps (host only): the import description (qcdmrg_import_mps)
+ * of the MPS sum_k coef[k] |config_k> with centre L-2: bond b <= L-2 holds one
+ * state per distinct prefix of length b, the left site tensors are 0/1
+ * selectors, the two-site wavefunction holds the coefficients (repeated
+ * configurations add); bond L-1 has no sectors, bond L is the vacuum. Sizes
+ * as for qcdmrg_export_mps: call with NULL bond_sec and data to get *n_sec
+ * (triples) and *n_data; bond_nsec takes L+1 ints, sec_cap counts ints (3 per
+ * triple), cap doubles. Errors: EINVAL (steps outside 0..3, a configuration
+ * outside the target or with a negative SU(2) spin, all coefficients zero,
+ * buffers too small).
+ *
+ * qcdmrg_sweep_left: from the current centre, one Davidson solve and one
+ * truncation (as in qcdmrg_sweep) per step, moving left until the centre is
+ * at sites (0, 1); no exact move first. After an import of qcdmrg_config_mps
+ * this is the warm-up half sweep: each step's left block is the span of the
+ * configurations' prefixes. report->n_steps = the steps taken. Errors: as
+ * qcdmrg_sweep.
+ */
+int qcdmrg_select_configs(int symmetry, int L, int N, int two_s, const double* h, const double* V, int nmax,
+                          uint8_t* steps, double* energy, int* count);
+int qcdmrg_config_mps(int symmetry, int L, int N, int two_s, int n, const uint8_t* steps, const double* coef,
+                      int* center, int* bond_nsec, int* bond_sec, int sec_cap, double* data, size_t cap,
+                      int* n_sec, size_t* n_data);
+int qcdmrg_sweep_left(qcdmrg_ctx* ctx, const qcdmrg_sweep_opts* opts, qcdmrg_sweep_report* report);
+
 /* Move the centre to sites (target, target+1) without truncation (only
  * weights <= 1e-14, rounding noise, dropped), renormalizing each grown
  * block (Method section). Errors: ESTATE, EINVAL (target outside 0..L-2). */

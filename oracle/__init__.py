@@ -21,6 +21,8 @@ Modules
              rotated orbitals at fixed density matrices (DMRG-SCF pieces)
   orbital_qi two-orbital reduced density matrices of a determinant vector,
              orbital entropies, mutual information, Fiedler ordering
+  configs    configuration selection near the aufbau reference and the
+             determinant expansion of determinants and genealogical spin states
 
 Conventions (the paper states none; fixed here and used by both sides):
   H = sum_pq h_pq E_pq + 1/2 sum_pqrs (pq|rs) (E_pq E_rs - delta_qr E_ps) + e_core,

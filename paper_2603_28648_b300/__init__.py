@@ -85,7 +85,8 @@ EXPORTS = [
     "qcdmrg_export_mps", "qcdmrg_checkpoint", "qcdmrg_restore", "qcdmrg_psi_layout",
     "qcdmrg_energy_grad", "qcdmrg_truncate_dbss", "qcdmrg_extrapolate", "qcdmrg_active_space",
     "qcdmrg_orbital_gradient", "qcdmrg_rotate_orbitals", "qcdmrg_orbital_rdm",
-    "qcdmrg_orbital_entanglement", "qcdmrg_fiedler_order",
+    "qcdmrg_orbital_entanglement", "qcdmrg_fiedler_order", "qcdmrg_select_configs", "qcdmrg_config_mps",
+    "qcdmrg_sweep_left",
 ]
 
 _lib = None
@@ -149,6 +150,11 @@ def load(path=None):
     lib.qcdmrg_orbital_rdm.argtypes = [P, dp]
     lib.qcdmrg_orbital_entanglement.argtypes = [ci, dp, dp, dp]
     lib.qcdmrg_fiedler_order.argtypes = [ci, dp, ip, dp]
+    u8p = ctypes.POINTER(ctypes.c_uint8)
+    lib.qcdmrg_select_configs.argtypes = [ci, ci, ci, ci, dp, dp, ci, u8p, dp, ip]
+    lib.qcdmrg_config_mps.argtypes = [ci, ci, ci, ci, ci, u8p, dp, ip, ip, ip, ci, dp, ctypes.c_size_t, ip,
+                                      ctypes.POINTER(ctypes.c_size_t)]
+    lib.qcdmrg_sweep_left.argtypes = [P, ctypes.POINTER(SweepOpts), ctypes.POINTER(SweepReport)]
     for f in EXPORTS:
         getattr(lib, f).restype = getattr(lib, f).restype or ctypes.c_int
     lib.qcdmrg_last_error.restype = ctypes.c_char_p
@@ -167,6 +173,7 @@ class Context:
     def __init__(self, device=0, symmetry=U1, tmp_budget_gb=0.0, hbm_budget_gb=0.0, autotune=True,
                  pair_switch=0, sum_gemm=0, tile_chunk=0, lib=None):
         self.lib = lib or load()
+        self.symmetry = symmetry
         self.h = ctypes.c_void_p()
         cfg = Config(symmetry, device, tmp_budget_gb, hbm_budget_gb, 0 if autotune else 1, pair_switch, sum_gemm,
                      tile_chunk)
@@ -358,6 +365,24 @@ class Context:
         return {"energy": r.energy, "energy_mixed": r.energy_mixed, "max_trunc_err": r.max_trunc_err,
                 "seconds": r.seconds, "n_hpsi": list(r.n_hpsi), "n_steps": r.n_steps, "max_D": r.max_D}
 
+    def sweep_left(self, D, allow_notconv=False, trunc_eps=0.0, D_min=1, **kw):
+        """Optimise and truncate from the current centre leftwards to sites (0, 1): the
+        warm-up half sweep after import_configs."""
+        o = SweepOpts(D, self.dav_opts(**kw), trunc_eps, D_min)
+        r = SweepReport()
+        rc = self.lib.qcdmrg_sweep_left(self.h, ctypes.byref(o), ctypes.byref(r))
+        if not (allow_notconv and rc == -5):
+            self._check(rc)
+        return {"energy": r.energy, "energy_mixed": r.energy_mixed, "max_trunc_err": r.max_trunc_err,
+                "seconds": r.seconds, "n_hpsi": list(r.n_hpsi), "n_steps": r.n_steps, "max_D": r.max_D}
+
+    def import_configs(self, L, N, two_s, steps, coef, symmetry=None):
+        """Import the MPS of sum_k coef[k] |config_k> (qcdmrg_config_mps), centre L-2."""
+        sym = self.symmetry if symmetry is None else symmetry
+        center, nsec, sec, data = config_mps(sym, L, N, two_s, steps, coef, lib=self.lib)
+        self.import_mps(L, center, nsec, sec, data)
+        return center
+
     def truncate_dbss(self, D_min, D_max, eps, direction):
         """Returns (discarded weight, states kept)."""
         err, kept = ctypes.c_double(), ctypes.c_int()
@@ -465,6 +490,48 @@ def fiedler_order(mutual, lib=None):
     if rc != 0:
         raise QcdmrgError(rc, "qcdmrg_fiedler_order: invalid arguments")
     return order.astype(np.int64), f
+
+
+def select_configs(symmetry, h, V, N, two_s, nmax, lib=None):
+    """qcdmrg_select_configs: (steps (count x L uint8), energies) of the nmax lowest
+    configurations within two electrons of the aufbau reference."""
+    lib = lib or load()
+    h, V = _f64(h), _f64(V)
+    L = h.shape[0]
+    steps = np.zeros((nmax, L), dtype=np.uint8)
+    en = np.zeros(nmax)
+    cnt = ctypes.c_int()
+    rc = lib.qcdmrg_select_configs(symmetry, L, N, two_s, _dptr(h), _dptr(V), nmax,
+                                   steps.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), _dptr(en),
+                                   ctypes.byref(cnt))
+    if rc != 0:
+        raise QcdmrgError(rc, "qcdmrg_select_configs: invalid arguments")
+    return steps[:cnt.value].copy(), en[:cnt.value].copy()
+
+
+def config_mps(symmetry, L, N, two_s, steps, coef, lib=None):
+    """qcdmrg_config_mps: (center, bond_nsec, bond_sec, data) of sum_k coef[k] |config_k>."""
+    lib = lib or load()
+    st = np.ascontiguousarray(steps, dtype=np.uint8).reshape(-1, L)
+    c = _f64(coef).reshape(-1)
+    if c.size != st.shape[0]:
+        raise ValueError("one coefficient per configuration")
+    u8 = st.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+    ip = ctypes.POINTER(ctypes.c_int)
+    center, nsec_n, ndata = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
+    nsec = np.zeros(L + 1, dtype=np.int32)
+    rc = lib.qcdmrg_config_mps(symmetry, L, N, two_s, st.shape[0], u8, _dptr(c), ctypes.byref(center),
+                               nsec.ctypes.data_as(ip), None, 0, None, 0, ctypes.byref(nsec_n), ctypes.byref(ndata))
+    if rc != 0:
+        raise QcdmrgError(rc, "qcdmrg_config_mps: invalid configurations")
+    sec = np.zeros(max(3, 3 * nsec_n.value), dtype=np.int32)
+    data = np.zeros(max(1, ndata.value))
+    rc = lib.qcdmrg_config_mps(symmetry, L, N, two_s, st.shape[0], u8, _dptr(c), ctypes.byref(center),
+                               nsec.ctypes.data_as(ip), sec.ctypes.data_as(ip), sec.size, _dptr(data), data.size,
+                               ctypes.byref(nsec_n), ctypes.byref(ndata))
+    if rc != 0:
+        raise QcdmrgError(rc, "qcdmrg_config_mps: invalid configurations")
+    return center.value, nsec, sec[:3 * nsec_n.value], data[:ndata.value]
 
 
 def reorder_integrals(h, V, order):

@@ -4,7 +4,7 @@ import os
 import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRC = ["csrc/core.cpp", "csrc/rules.cpp", "csrc/rules_su2.cpp", "csrc/su2.cpp", "csrc/init.cpp", "csrc/engine.cpp", "csrc/tiled.cpp", "csrc/capi.cpp", "csrc/orbitals.cpp", "csrc/su2expand.cpp", "csrc/entanglement.cpp", "csrc/kernels.cu", "csrc/tc_gemm.cu", "csrc/noalloc.cu", "csrc/graph.cu", "csrc/tc_tiled.cu"]
+SRC = ["csrc/core.cpp", "csrc/rules.cpp", "csrc/rules_su2.cpp", "csrc/su2.cpp", "csrc/init.cpp", "csrc/engine.cpp", "csrc/tiled.cpp", "csrc/capi.cpp", "csrc/orbitals.cpp", "csrc/su2expand.cpp", "csrc/entanglement.cpp", "csrc/configs.cpp", "csrc/kernels.cu", "csrc/tc_gemm.cu", "csrc/noalloc.cu", "csrc/graph.cu", "csrc/tc_tiled.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -5,11 +5,13 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <new>
 #include <stdexcept>
 #include <string>
 #include <vector>
 
 #include "../../include/qcdmrg.h"
+#include "configs.hpp"
 #include "entanglement.hpp"
 #include "orbitals.hpp"
 #include "core.hpp"
@@ -920,6 +922,78 @@ int qcdmrg_sweep(qcdmrg_ctx* ctx, const qcdmrg_sweep_opts* o, qcdmrg_sweep_repor
     ctx->st.psi_size = E.lay.size;
     return conv ? QCDMRG_OK : QCDMRG_ENOTCONV;
   });
+}
+
+int qcdmrg_sweep_left(qcdmrg_ctx* ctx, const qcdmrg_sweep_opts* o, qcdmrg_sweep_report* rep) {
+  return guard(ctx, [&]() {
+    Engine& E = ctx->eng;
+    if (!E.have_env) throw Fail{QCDMRG_ESTATE, "build_env first"};
+    if (!o || o->D < 1) throw Fail{QCDMRG_EINVAL, "sweep options with D >= 1 required"};
+    if (o->trunc_eps < 0.0 || (o->trunc_eps > 0.0 && (o->D_min < 1 || o->D_min > o->D)))
+      throw Fail{QCDMRG_EINVAL, "dynamic selection needs 1 <= D_min <= D"};
+    auto t0 = std::chrono::steady_clock::now();
+    DavOpts dop = dav_opts(&o->dav);
+    qcdmrg_sweep_report R{};
+    bool conv = true;
+    while (E.center > 0) {
+      DavResult r = E.davidson(dop);
+      conv = conv && r.converged;
+      for (int k = 0; k < 4; ++k) R.n_hpsi[k] += r.hpsi[k];
+      R.energy = r.energy;
+      R.energy_mixed = r.energy_mixed;
+      R.n_steps++;
+      int nk = 0;
+      double e = E.truncate_move(o->D, -1, 0.0, o->trunc_eps, o->D_min, &nk);
+      R.max_trunc_err = std::max(R.max_trunc_err, e);
+      R.max_D = std::max(R.max_D, nk);
+    }
+    R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (rep) *rep = R;
+    return conv ? QCDMRG_OK : QCDMRG_ENOTCONV;
+  });
+}
+
+int qcdmrg_select_configs(int symmetry, int L, int N, int two_s, const double* h, const double* V, int nmax,
+                          uint8_t* steps, double* energy, int* count) {
+  if ((symmetry != QCDMRG_U1 && symmetry != QCDMRG_SU2) || L < 2 || L > 4096 || nmax < 1 || !h || !V ||
+      !steps || !count)
+    return QCDMRG_EINVAL;
+  try {
+    std::vector<uint8_t> st;
+    std::vector<double> en;
+    const int m = select_configs(L, symmetry == QCDMRG_SU2, N, two_s, h, V, nmax, st, en);
+    std::copy(st.begin(), st.end(), steps);
+    if (energy) std::copy(en.begin(), en.end(), energy);
+    *count = m;
+    return QCDMRG_OK;
+  } catch (const std::invalid_argument&) {
+    return QCDMRG_EINVAL;
+  } catch (const std::bad_alloc&) {
+    return QCDMRG_ENOMEM;
+  }
+}
+
+int qcdmrg_config_mps(int symmetry, int L, int N, int two_s, int n, const uint8_t* steps, const double* coef,
+                      int* center, int* bond_nsec, int* bond_sec, int sec_cap, double* data, size_t cap,
+                      int* n_sec, size_t* n_data) {
+  if ((symmetry != QCDMRG_U1 && symmetry != QCDMRG_SU2) || L < 2 || n < 1 || !steps || !coef)
+    return QCDMRG_EINVAL;
+  try {
+    ImportArrays A;
+    configs_to_mps(L, symmetry == QCDMRG_SU2, N, two_s, n, steps, coef, A);
+    if ((bond_sec && sec_cap < (int)A.sec.size()) || (data && cap < A.data.size())) return QCDMRG_EINVAL;
+    if (center) *center = A.center;
+    if (n_sec) *n_sec = (int)(A.sec.size() / 3);
+    if (n_data) *n_data = A.data.size();
+    if (bond_nsec) std::copy(A.nsec.begin(), A.nsec.end(), bond_nsec);
+    if (bond_sec) std::copy(A.sec.begin(), A.sec.end(), bond_sec);
+    if (data) std::copy(A.data.begin(), A.data.end(), data);
+    return QCDMRG_OK;
+  } catch (const std::invalid_argument&) {
+    return QCDMRG_EINVAL;
+  } catch (const std::bad_alloc&) {
+    return QCDMRG_ENOMEM;
+  }
 }
 
 int qcdmrg_check_device(qcdmrg_ctx* ctx) {

@@ -922,6 +922,9 @@ cudaError_t launch_f64_prepared(const void* handle, uint64_t psi, uint64_t sig, 
   B.b[1] = psi;
   B.b[2] = sig;
   B.b[3] = scratch;
+  // a launch error left pending by earlier work on this thread is not this call's:
+  // clear it so that the value returned below belongs to these launches
+  (void)cudaGetLastError();
   launch_f64(d->p, d->s, d->t, d->cls, B, st);
   return cudaGetLastError();
 }

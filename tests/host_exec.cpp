@@ -19,6 +19,8 @@
 //                                                          psi and sigma at the centre)
 //        host_exec in.bin out.bin orbrdm                  (two-orbital density matrices,
 //                                                          L*L blocks of 256, then psi, sigma)
+//        host_exec in.bin out.bin warmup D nsweeps tol    (half sweep left from the
+//                                                          imported centre, then sweeps)
 //   in : int64 L, N, two_sz, center, nsec_len (= L+1), sec_len, data_len;
 //        h (L*L), V (L^4) doubles; bond_nsec, bond_sec int32; data doubles
 //   out: sigma of the FP64 task lists, then sigma of the tiled work items; or
@@ -435,6 +437,40 @@ int main(int argc, char** argv) {
       if (!o2) throw std::runtime_error("cannot open output");
       std::fwrite(energies.data(), 8, energies.size(), o2);
       std::fclose(o2);
+      return 0;
+    }
+    if (argc >= 7 && std::string(argv[3]) == "warmup") {
+      // the warm-up half sweep from the imported centre to (0, 1) (as qcdmrg_sweep_left),
+      // then nsw full sweeps (as qcdmrg_sweep); out: the energy of the first solve, the
+      // energy at the end of the half sweep, then one energy per full sweep
+      const int D = std::atoi(argv[4]), nsw = std::atoi(argv[5]);
+      DavOpts o;
+      o.tol = std::atof(argv[6]);
+      std::vector<double> energies;
+      double e = 0.0;
+      bool first = true;
+      while (E.center > 0) {
+        e = E.davidson(o).energy;
+        if (first) energies.push_back(e);
+        first = false;
+        E.truncate_move(D, -1, 0.0);
+      }
+      energies.push_back(e);
+      for (int sw = 0; sw < nsw; ++sw) {
+        for (int l = 0; l < L - 2; ++l) {
+          e = E.davidson(o).energy;
+          E.truncate_move(D, +1, 0.0);
+        }
+        for (int l = L - 2; l > 0; --l) {
+          e = E.davidson(o).energy;
+          E.truncate_move(D, -1, 0.0);
+        }
+        energies.push_back(e);
+      }
+      FILE* o9 = std::fopen(argv[2], "wb");
+      if (!o9) throw std::runtime_error("cannot open output");
+      std::fwrite(energies.data(), 8, energies.size(), o9);
+      std::fclose(o9);
       return 0;
     }
     if (argc >= 4 && std::string(argv[3]) == "davidson") {

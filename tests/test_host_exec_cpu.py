@@ -657,3 +657,74 @@ def test_orbital_rdm_identities_at_L12(host_exec, tmp_path):
             one.setdefault(j, []).append(np.einsum("xyxz->yz", t))
     for i, mats in one.items():
         assert max(np.abs(mm - mats[0]).max() for mm in mats) <= 1e-12
+
+
+def _write_arrays(path, L, N, two_s, center, nsec, sec, data, h, V):
+    with open(path, "wb") as f:
+        f.write(struct.pack("<7q", L, N, two_s, center, len(nsec), len(sec), len(data)))
+        f.write(np.ascontiguousarray(h, "<f8").tobytes())
+        f.write(np.ascontiguousarray(V, "<f8").tobytes())
+        f.write(np.asarray(nsec, "<i4").tobytes())
+        f.write(np.asarray(sec, "<i4").tobytes())
+        f.write(np.asarray(data, "<f8").tobytes())
+
+
+@pytest.mark.parametrize("sym,L,N,two_s,nmax", [(0, 5, 4, 0, 20), (0, 6, 5, 1, 40), (1, 5, 4, 0, 12),
+                                                (1, 6, 5, 1, 30), (1, 6, 6, 2, 30)])
+def test_config_mps_is_the_configuration_state(host_exec, tmp_path, sym, L, N, two_s, nmax):
+    """The library's MPS of sum_k c_k |config_k> (selected configurations, random c_k)
+    carries exactly that state: its 2-RDM by the centre walk equals the FCI 2-RDM of the
+    oracle's determinant expansion of the configurations (CSFs by Clebsch-Gordan
+    coefficients for SU(2)), element by element."""
+    import paper_2603_28648_b300 as qd
+    from oracle import configs as oc
+    from oracle.fci import FCI
+    from tests._lib import ensure_built
+    lib = qd.load(ensure_built())
+    h, V = q.make_integrals(L, 5)
+    steps, _ = qd.select_configs(sym, h, V, N, two_s, nmax, lib=lib)
+    coef = np.random.default_rng(1).normal(size=len(steps))
+    center, nsec, sec, data = qd.config_mps(sym, L, N, two_s, steps, coef, lib=lib)
+    fin, fout = str(tmp_path / "c_in.bin"), str(tmp_path / "c_out.bin")
+    _write_arrays(fin, L, N, two_s, center, nsec, sec, data, h, V)
+    env = dict(os.environ, HOST_EXEC_SU2="1") if sym else dict(os.environ)
+    r = subprocess.run([host_exec, fin, fout, "rdm2sweep"], capture_output=True, text=True, timeout=600, env=env)
+    assert r.returncode == 0, r.stderr
+    G = np.fromfile(fout, "<f8")[:L ** 4].reshape(L, L, L, L)
+    _, v = oc.config_vector([tuple(int(x) for x in s) for s in steps], coef, L, N, two_s, bool(sym))
+    _, Gf = FCI(h, V, N, two_s).rdm12(v / np.linalg.norm(v))
+    assert np.abs(G - Gf).max() <= 1e-12
+
+
+@pytest.mark.parametrize("sym,L,N,two_s,nmax,D", [(0, 6, 6, 0, 30, 64), (1, 6, 6, 0, 30, 64),
+                                                  (1, 6, 5, 1, 20, 64)])
+def test_warmup_half_sweep_bounds_and_limit(host_exec, tmp_path, sym, L, N, two_s, nmax, D):
+    """The warm-up from the reference alone (the other selected configurations only span the
+    left bases): the first solve, at the right end, is at or below the CI energy of the
+    selected configurations (its space contains theirs), and at a bond dimension that
+    truncates nothing the following sweeps reach the FCI energy."""
+    import scipy.linalg as sl
+    import paper_2603_28648_b300 as qd
+    from oracle import configs as oc
+    from oracle.fci import FCI
+    from tests._lib import ensure_built
+    lib = qd.load(ensure_built())
+    h, V = q.make_integrals(L, 5)
+    steps, _ = qd.select_configs(sym, h, V, N, two_s, nmax, lib=lib)
+    coef = np.zeros(len(steps))
+    coef[0] = 1.0
+    center, nsec, sec, data = qd.config_mps(sym, L, N, two_s, steps, coef, lib=lib)
+    fin, fout = str(tmp_path / "w_in.bin"), str(tmp_path / "w_out.bin")
+    _write_arrays(fin, L, N, two_s, center, nsec, sec, data, h, V)
+    env = dict(os.environ, HOST_EXEC_SU2="1") if sym else dict(os.environ)
+    r = subprocess.run([host_exec, fin, fout, "warmup", str(D), "2", "1e-10"], capture_output=True, text=True,
+                       timeout=900, env=env)
+    assert r.returncode == 0, r.stderr
+    E = np.fromfile(fout, "<f8")
+    f = FCI(h, V, N, two_s)
+    P = np.stack([oc.config_vector([tuple(int(x) for x in s)], [1.0], L, N, two_s, bool(sym))[1] for s in steps], 1)
+    H = f.matrix()
+    e_ci = sl.eigh(P.T @ (H @ P), P.T @ P, eigvals_only=True)[0]
+    e_fci, _ = f.ground_state(two_s=two_s)
+    assert E[0] <= e_ci + 1e-9
+    assert abs(E[-1] - e_fci) <= 1e-8
