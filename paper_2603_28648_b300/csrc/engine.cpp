@@ -1209,43 +1209,7 @@ std::vector<double> Engine::rdm2_sweep() {
     return &it->second;
   };
   // the MPS before the walk, restored exactly afterwards (the walk re-gauges it)
-  struct Snap {
-    int center;
-    std::vector<Basis> bonds;
-    std::vector<std::vector<int64_t>> off;
-    std::vector<std::vector<int>> nb;
-    std::vector<std::vector<double>> site;
-    std::vector<double> psi;
-  } snap{center, bonds, site_off, site_nb, {}, get_psi_host()};
-  snap.site.resize(L);
-  for (int p = 0; p < L; ++p) {
-    if (!site[p]) continue;
-    const bool left = p < center;
-    const ProdBasis pb = make_prod(left ? bonds[p] : bonds[p + 1], left);
-    const Basis& to = left ? bonds[p + 1] : bonds[p];
-    int64_t n = 0;
-    for (int q = 0; q < pb.prod.nsec(); ++q)
-      if (site_off[p][q] >= 0) n = std::max<int64_t>(n, site_off[p][q] + (int64_t)pb.prod.dim[q] * to.dim[site_nb[p][q]]);
-    snap.site[p].resize((size_t)n);
-    if (n) ex->download(snap.site[p].data(), site[p], n);
-  }
-  auto restore = [&]() {
-    clear_env();
-    for (auto& t : site)
-      if (t) ex->release(t);
-    site.assign(L, 0);
-    for (int p = 0; p < L; ++p) {
-      if (snap.site[p].empty()) continue;
-      site[p] = ex->alloc((int64_t)snap.site[p].size());
-      ex->upload(site[p], snap.site[p].data(), (int64_t)snap.site[p].size());
-    }
-    bonds = snap.bonds;
-    site_off = snap.off;
-    site_nb = snap.nb;
-    center = snap.center;
-    set_psi_host(snap.psi);
-    build_env();
-  };
+  const MpsSnapshot snap = snapshot();
   try {
   while (center > 0) truncate_move(1 << 30, -1, -1.0);
   for (int s1 = 0; s1 <= L - 2; ++s1) {
@@ -1342,24 +1306,20 @@ std::vector<double> Engine::rdm2_sweep() {
     ex->release(tau);
   }
   } catch (...) {
-    restore();
+    restore(snap);
     throw;
   }
-  restore();
+  restore(snap);
   return G;
 }
 
-std::vector<double> Engine::rdm2_sweep_su2() {
-  if (!have_env) throw StateError("build_env first");
-  SU2Mps in;
-  in.L = L;
-  in.center = center;
-  in.N = N;
-  in.two_s = two_s;
-  in.bonds = bonds;
-  in.site_off = site_off;
-  in.site_nb = site_nb;
-  in.site.resize(L);
+Engine::MpsSnapshot Engine::snapshot() {
+  MpsSnapshot sn;
+  sn.center = center;
+  sn.bonds = bonds;
+  sn.off = site_off;
+  sn.nb = site_nb;
+  sn.site.resize(L);
   for (int p = 0; p < L; ++p) {
     if (!site[p]) continue;
     const bool left = p < center;
@@ -1368,10 +1328,44 @@ std::vector<double> Engine::rdm2_sweep_su2() {
     int64_t n = 0;
     for (int q = 0; q < pb.prod.nsec(); ++q)
       if (site_off[p][q] >= 0) n = std::max<int64_t>(n, site_off[p][q] + (int64_t)pb.prod.dim[q] * to.dim[site_nb[p][q]]);
-    in.site[p].resize((size_t)n);
-    if (n) ex->download(in.site[p].data(), site[p], n);
+    sn.site[p].resize((size_t)n);
+    if (n) ex->download(sn.site[p].data(), site[p], n);
   }
-  in.psi = get_psi_host();
+  sn.psi = get_psi_host();
+  return sn;
+}
+
+void Engine::restore(const MpsSnapshot& sn) {
+  clear_env();
+  for (auto& t : site)
+    if (t) ex->release(t);
+  site.assign(L, 0);
+  for (int p = 0; p < L; ++p) {
+    if (sn.site[p].empty()) continue;
+    site[p] = ex->alloc((int64_t)sn.site[p].size());
+    ex->upload(site[p], sn.site[p].data(), (int64_t)sn.site[p].size());
+  }
+  bonds = sn.bonds;
+  site_off = sn.off;
+  site_nb = sn.nb;
+  center = sn.center;
+  set_psi_host(sn.psi);
+  build_env();
+}
+
+std::vector<double> Engine::on_m_expansion(const std::function<std::vector<double>(Engine&)>& f) {
+  if (!have_env) throw StateError("build_env first");
+  MpsSnapshot sn = snapshot();
+  SU2Mps in;
+  in.L = L;
+  in.center = center;
+  in.N = N;
+  in.two_s = two_s;
+  in.bonds = std::move(sn.bonds);
+  in.site_off = std::move(sn.off);
+  in.site_nb = std::move(sn.nb);
+  in.site = std::move(sn.site);
+  in.psi = std::move(sn.psi);
   U1Mps out;
   expand_mps_su2(in, out);
   Engine U;
@@ -1390,7 +1384,14 @@ std::vector<double> Engine::rdm2_sweep_su2() {
   U.site.assign(L, 0);
   U.site_off = out.site_off;
   U.site_nb = out.site_nb;
-  std::vector<double> g;
+  std::vector<double> r;
+  auto done = [&]() {
+    U.clear();
+    U.ex = nullptr;   // its destructor must not drop the runner's lists again
+    U.pr = nullptr;
+    // the U(1) engine's centre replaced this engine's prepared task lists
+    prepare_center();
+  };
   try {
     for (int p = 0; p < L; ++p) {
       if (p == center || p == center + 1) continue;
@@ -1400,124 +1401,29 @@ std::vector<double> Engine::rdm2_sweep_su2() {
     U.center = center;
     U.set_psi_host(out.psi);
     U.build_env();
-    g = U.rdm2_sweep();
+    r = f(U);
   } catch (...) {
-    U.clear();
-    U.ex = nullptr;   // its destructor must not drop the runner's lists again
-    U.pr = nullptr;
-    prepare_center();
+    done();
     throw;
   }
-  U.clear();
-  U.ex = nullptr;
-  U.pr = nullptr;
-  // the U(1) engine's centre replaced this engine's prepared task lists
-  prepare_center();
-  return g;
+  done();
+  return r;
+}
+
+std::vector<double> Engine::rdm2_sweep_su2() {
+  return on_m_expansion([](Engine& U) { return U.rdm2_sweep(); });
 }
 
 std::vector<double> Engine::orbital_rdm2() {
   if (!have_env) throw StateError("build_env first");
-  if (su2) {
-    // the same measurement on the state's M = S expansion (see rdm2_sweep_su2)
-    SU2Mps in;
-    in.L = L;
-    in.center = center;
-    in.N = N;
-    in.two_s = two_s;
-    in.bonds = bonds;
-    in.site_off = site_off;
-    in.site_nb = site_nb;
-    in.site.resize(L);
-    for (int p = 0; p < L; ++p) {
-      if (!site[p]) continue;
-      const bool left = p < center;
-      const ProdBasis pb = make_prod(left ? bonds[p] : bonds[p + 1], left);
-      const Basis& to = left ? bonds[p + 1] : bonds[p];
-      int64_t n = 0;
-      for (int q = 0; q < pb.prod.nsec(); ++q)
-        if (site_off[p][q] >= 0) n = std::max<int64_t>(n, site_off[p][q] + (int64_t)pb.prod.dim[q] * to.dim[site_nb[p][q]]);
-      in.site[p].resize((size_t)n);
-      if (n) ex->download(in.site[p].data(), site[p], n);
-    }
-    in.psi = get_psi_host();
-    U1Mps out;
-    expand_mps_su2(in, out);
-    Engine U;
-    U.ex = ex;
-    U.pr = pr;
-    U.I = I;
-    U.N = N;
-    U.two_s = two_s;
-    U.L = L;
-    U.device = device;
-    U.tmp_budget = tmp_budget;
-    U.hbm_budget = hbm_budget;
-    U.autotune = autotune;
-    U.bonds = out.bonds;
-    U.site.assign(L, 0);
-    U.site_off = out.site_off;
-    U.site_nb = out.site_nb;
-    std::vector<double> r;
-    try {
-      for (int p = 0; p < L; ++p) {
-        if (p == center || p == center + 1) continue;
-        U.site[p] = ex->alloc((int64_t)out.site[p].size());
-        ex->upload(U.site[p], out.site[p].data(), (int64_t)out.site[p].size());
-      }
-      U.center = center;
-      U.set_psi_host(out.psi);
-      U.build_env();
-      r = U.orbital_rdm2();
-    } catch (...) {
-      U.clear();
-      U.ex = nullptr;
-      U.pr = nullptr;
-      prepare_center();
-      throw;
-    }
-    U.clear();
-    U.ex = nullptr;
-    U.pr = nullptr;
-    prepare_center();
-    return r;
-  }
+  // SU(2): the same measurement on the state's M = S expansion
+  if (su2) return on_m_expansion([](Engine& U) { return U.orbital_rdm2(); });
   std::vector<double> R((size_t)L * L * 256, 0.0);
   // the MPS before the walk, restored exactly afterwards
-  const int c0 = center;
-  const std::vector<Basis> bonds0 = bonds;
-  const std::vector<std::vector<int64_t>> off0 = site_off;
-  const std::vector<std::vector<int>> nb0 = site_nb;
-  const std::vector<double> psi0 = get_psi_host();
-  std::vector<std::vector<double>> site0(L);
-  for (int p = 0; p < L; ++p) {
-    if (!site[p]) continue;
-    const bool left = p < center;
-    const ProdBasis pb = make_prod(left ? bonds[p] : bonds[p + 1], left);
-    const Basis& to = left ? bonds[p + 1] : bonds[p];
-    int64_t n = 0;
-    for (int q = 0; q < pb.prod.nsec(); ++q)
-      if (site_off[p][q] >= 0) n = std::max<int64_t>(n, site_off[p][q] + (int64_t)pb.prod.dim[q] * to.dim[site_nb[p][q]]);
-    site0[p].resize((size_t)n);
-    if (n) ex->download(site0[p].data(), site[p], n);
-  }
-  auto restore = [&]() {
+  const MpsSnapshot snap = snapshot();
+  auto put_back = [&]() {
     keep_local = false;
-    clear_env();
-    for (auto& t : site)
-      if (t) ex->release(t);
-    site.assign(L, 0);
-    for (int p = 0; p < L; ++p) {
-      if (site0[p].empty()) continue;
-      site[p] = ex->alloc((int64_t)site0[p].size());
-      ex->upload(site[p], site0[p].data(), (int64_t)site0[p].size());
-    }
-    bonds = bonds0;
-    site_off = off0;
-    site_nb = nb0;
-    center = c0;
-    set_psi_host(psi0);
-    build_env();
+    restore(snap);
   };
   static const int NOCC[4] = {0, 1, 1, 2};
   static const int SZ2[4] = {0, 1, -1, 0};
@@ -1575,10 +1481,10 @@ std::vector<double> Engine::orbital_rdm2() {
           }
     }
   } catch (...) {
-    restore();
+    put_back();
     throw;
   }
-  restore();
+  put_back();
   return R;
 }
 

@@ -1,5 +1,6 @@
 // Sweep engine: MPS, renormalized blocks, H_eff plan, Davidson, truncation.
 #pragma once
+#include <functional>
 #include <map>
 #include <stdexcept>
 #include <vector>
@@ -140,6 +141,23 @@ struct Engine {
   // the MPS is restored afterwards. SU(2): of the M = S expansion.
   bool keep_local = false;
   std::vector<double> orbital_rdm2();
+
+  // Host copy of the MPS (centre, bases, site tensors, two-site state): the
+  // walks above re-gauge the MPS and put it back exactly from one of these.
+  struct MpsSnapshot {
+    int center = -1;
+    std::vector<Basis> bonds;
+    std::vector<std::vector<int64_t>> off;
+    std::vector<std::vector<int>> nb;
+    std::vector<std::vector<double>> site;   // empty for the two centre sites
+    std::vector<double> psi;
+  };
+  MpsSnapshot snapshot();
+  void restore(const MpsSnapshot& s);   // uploads the tensors and rebuilds the environment
+  // f run on a U(1) engine (same executor, integrals, target and centre) that
+  // holds this SU(2) state's M = S expansion; this engine's centre is prepared
+  // again afterwards
+  std::vector<double> on_m_expansion(const std::function<std::vector<double>(Engine&)>& f);
 };
 
 }  // namespace qd
