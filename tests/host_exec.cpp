@@ -21,6 +21,8 @@
 //                                                          L*L blocks of 256, then psi, sigma)
 //        host_exec in.bin out.bin warmup D nsweeps tol    (half sweep left from the
 //                                                          imported centre, then sweeps)
+//        host_exec in.bin out.bin sweeprdm D nsweeps tol  (sweeps, then the two-orbital
+//                                                          density matrices)
 //   in : int64 L, N, two_sz, center, nsec_len (= L+1), sec_len, data_len;
 //        h (L*L), V (L^4) doubles; bond_nsec, bond_sec int32; data doubles
 //   out: sigma of the FP64 task lists, then sigma of the tiled work items; or
@@ -437,6 +439,34 @@ int main(int argc, char** argv) {
       if (!o2) throw std::runtime_error("cannot open output");
       std::fwrite(energies.data(), 8, energies.size(), o2);
       std::fclose(o2);
+      return 0;
+    }
+    if (argc >= 7 && std::string(argv[3]) == "sweeprdm") {
+      // nsw sweeps (as in "sweep", fixed D), then the two-orbital density matrices of
+      // the final state; out: one energy per sweep, then L*L blocks of 256
+      const int D = std::atoi(argv[4]), nsw = std::atoi(argv[5]);
+      DavOpts o;
+      o.tol = std::atof(argv[6]);
+      while (E.center > 0) E.truncate_move(1 << 30, -1, 1e-28);
+      std::vector<double> out;
+      for (int sw = 0; sw < nsw; ++sw) {
+        double e = 0.0;
+        for (int l = 0; l < L - 2; ++l) {
+          e = E.davidson(o).energy;
+          E.truncate_move(D, +1, 0.0);
+        }
+        for (int l = L - 2; l > 0; --l) {
+          e = E.davidson(o).energy;
+          E.truncate_move(D, -1, 0.0);
+        }
+        out.push_back(e);
+      }
+      const std::vector<double> r = E.orbital_rdm2();
+      out.insert(out.end(), r.begin(), r.end());
+      FILE* o10 = std::fopen(argv[2], "wb");
+      if (!o10) throw std::runtime_error("cannot open output");
+      std::fwrite(out.data(), 8, out.size(), o10);
+      std::fclose(o10);
       return 0;
     }
     if (argc >= 7 && std::string(argv[3]) == "warmup") {
