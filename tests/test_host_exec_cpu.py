@@ -773,3 +773,44 @@ def test_qi_ordering_recovers_the_chain_energy(host_exec, tmp_path, seed):
     e_true, _ = dmrg(*qd.reorder_integrals(h, V, perm))
     assert e_qi <= e_true + 1e-6
     assert e_scr - e_qi > 0.05
+
+
+@pytest.mark.parametrize("L,N,two_sz,D,c", [(2, 2, 0, 4, 0), (2, 1, -1, 4, 0), (3, 1, 1, 4, 0), (3, 2, 0, 16, 1),
+                                            (4, 0, 0, 4, 1), (4, 8, 0, 4, 1), (4, 7, 1, 8, 1), (5, 5, 5, 4, 2)])
+def test_degenerate_fillings_and_minimal_chains_u1(host_exec, tmp_path, L, N, two_sz, D, c):
+    """The edge cases of the method: the shortest chain (L = 2, both sites at the centre, no
+    environment), the empty and the full chain (one state; sigma = 0 and sigma = E_full psi),
+    one electron, one hole, the fully polarised state (2Sz = N = L, one state): both
+    host-executed forms equal the oracle's sigma."""
+    from oracle.dmrgu1 import DMRGU1
+    from oracle.mpsu1 import MPSU1
+    m = MPSU1.from_raw(q.random_mps_blocks(L, N, two_sz, D, q.SYM_U1, 3, c))
+    h, V = q.make_integrals(L, 4)
+    s64, st = _run(host_exec, tmp_path, m, h, V)
+    ref = m.psi_to_flat(DMRGU1(h, V, N, two_sz).sigma(m))
+    scale = max(np.linalg.norm(ref), np.linalg.norm(m.psi_to_flat()))
+    assert np.linalg.norm(s64 - ref) <= 1e-13 * scale
+    assert np.linalg.norm(st - ref) <= 1e-13 * scale
+    if N == 2 * L:
+        # the full chain: sigma = (2 sum_p h_pp + sum_pq (2 (pp|qq) - (pq|qp))) psi
+        e = 2 * np.trace(h) + sum(2 * V[p, p, r, r] - V[p, r, r, p] for p in range(L) for r in range(L))
+        assert np.linalg.norm(s64 - e * m.psi_to_flat()) <= 1e-12 * abs(e) * np.linalg.norm(m.psi_to_flat())
+    if N == 0:
+        assert not np.any(s64) and not np.any(st)
+
+
+@pytest.mark.parametrize("L,N,two_s,D,c", [(2, 2, 0, 4, 0), (3, 1, 1, 4, 0), (3, 6, 0, 4, 1), (4, 0, 0, 4, 1),
+                                           (4, 4, 4, 4, 1), (3, 3, 3, 4, 1), (5, 9, 1, 6, 2)])
+def test_degenerate_fillings_and_minimal_chains_su2(host_exec, tmp_path, L, N, two_s, D, c):
+    """SU(2) edge cases: L = 2, one electron, the full and the empty chain, the maximal spin
+    S = N/2 (one multiplet), one hole: the reduced-operator task lists equal the SU(2)
+    oracle's sigma."""
+    from oracle.dmrgsu2 import DMRGSU2, MPSSU2
+    mps = MPSSU2.from_raw(q.random_mps_blocks(L, N, two_s, D, q.SYM_SU2, 5, c))
+    h, V = q.make_integrals(L, 11)
+    out = _run_su2(host_exec, tmp_path, mps, h, V)
+    n = out.size // 2
+    ref = mps.psi_to_flat(DMRGSU2(h, V, N, two_s).sigma(mps))
+    scale = max(np.linalg.norm(ref), np.linalg.norm(mps.psi_to_flat()))
+    assert np.linalg.norm(out[:n] - ref) <= 1e-13 * scale
+    assert np.linalg.norm(out[n:] - ref) <= 1e-13 * scale
