@@ -47,11 +47,14 @@ def test_plans_stay_in_bounds(checker, L, N, D, switch, sum_gemm):
 
 
 @pytest.mark.parametrize("L,N,D,switch", [(6, 6, 16, 0), (12, 12, 64, 0), (36, 54, 256, 0), (12, 12, 64, 6),
-                                          (36, 54, 256, 18), (36, 54, 256, 19)])
+                                          (36, 54, 256, 18), (36, 54, 256, 19), (36, 54, 2048, 19),
+                                          (36, 54, 4096, 19)])
 def test_su2_plans_stay_in_bounds(checker, L, N, D, switch):
     """The SU(2) reduced-operator task lists (environment build, enlargement sums, centre
     FP64 segments and tiled work items) at the CAS(54,36) shape and smaller, with normal
-    pairs on the left at every cut and with the switch at and past the centre cut."""
+    pairs on the left at every cut and with the switch at and past the centre cut; D = 2048
+    and 4096 with the switch one cut past the centre are the benchmark's own launch
+    configurations (task lists only: about 14 s each)."""
     r = subprocess.run([checker, str(L), str(N), str(D), str(switch), "0", "1"], capture_output=True, text=True,
                        timeout=600)
     assert r.returncode == 0, r.stdout + r.stderr
