@@ -888,33 +888,45 @@ int qcdmrg_move_center(qcdmrg_ctx* ctx, int target) {
   });
 }
 
+namespace {
+
+void check_sweep_opts(const Engine& E, const qcdmrg_sweep_opts* o) {
+  if (!E.have_env) throw Fail{QCDMRG_ESTATE, "build_env first"};
+  if (!o || o->D < 1) throw Fail{QCDMRG_EINVAL, "sweep options with D >= 1 required"};
+  if (o->trunc_eps < 0.0 || (o->trunc_eps > 0.0 && (o->D_min < 1 || o->D_min > o->D)))
+    throw Fail{QCDMRG_EINVAL, "dynamic selection needs 1 <= D_min <= D"};
+}
+
+// one two-site optimisation of a sweep: Davidson at the centre, then the
+// truncation that moves the centre by dir
+void sweep_step(Engine& E, const qcdmrg_sweep_opts* o, const DavOpts& dop, int dir, qcdmrg_sweep_report& R,
+                bool& conv) {
+  DavResult r = E.davidson(dop);
+  conv = conv && r.converged;
+  for (int k = 0; k < 4; ++k) R.n_hpsi[k] += r.hpsi[k];
+  R.energy = r.energy;
+  R.energy_mixed = r.energy_mixed;
+  R.n_steps++;
+  int nk = 0;
+  double e = E.truncate_move(o->D, dir, 0.0, o->trunc_eps, o->D_min, &nk);
+  R.max_trunc_err = std::max(R.max_trunc_err, e);
+  R.max_D = std::max(R.max_D, nk);
+}
+
+}  // namespace
+
 int qcdmrg_sweep(qcdmrg_ctx* ctx, const qcdmrg_sweep_opts* o, qcdmrg_sweep_report* rep) {
   return guard(ctx, [&]() {
     Engine& E = ctx->eng;
-    if (!E.have_env) throw Fail{QCDMRG_ESTATE, "build_env first"};
-    if (!o || o->D < 1) throw Fail{QCDMRG_EINVAL, "sweep options with D >= 1 required"};
-    if (o->trunc_eps < 0.0 || (o->trunc_eps > 0.0 && (o->D_min < 1 || o->D_min > o->D)))
-      throw Fail{QCDMRG_EINVAL, "dynamic selection needs 1 <= D_min <= D"};
+    check_sweep_opts(E, o);
     if (E.L < 3) throw Fail{QCDMRG_EINVAL, "sweeps need L >= 3"};
     auto t0 = std::chrono::steady_clock::now();
     while (E.center > 0) E.truncate_move(1 << 30, -1, 1e-28);
     DavOpts dop = dav_opts(&o->dav);
     qcdmrg_sweep_report R{};
     bool conv = true;
-    auto step = [&](int dir) {
-      DavResult r = E.davidson(dop);
-      conv = conv && r.converged;
-      for (int k = 0; k < 4; ++k) R.n_hpsi[k] += r.hpsi[k];
-      R.energy = r.energy;
-      R.energy_mixed = r.energy_mixed;
-      R.n_steps++;
-      int nk = 0;
-      double e = E.truncate_move(o->D, dir, 0.0, o->trunc_eps, o->D_min, &nk);
-      R.max_trunc_err = std::max(R.max_trunc_err, e);
-      R.max_D = std::max(R.max_D, nk);
-    };
-    for (int l = 0; l < E.L - 2; ++l) step(+1);
-    for (int l = E.L - 2; l > 0; --l) step(-1);
+    for (int l = 0; l < E.L - 2; ++l) sweep_step(E, o, dop, +1, R, conv);
+    for (int l = E.L - 2; l > 0; --l) sweep_step(E, o, dop, -1, R, conv);
     R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (rep) *rep = R;
     ctx->st.heff_flops = E.plan.flops;
@@ -927,26 +939,12 @@ int qcdmrg_sweep(qcdmrg_ctx* ctx, const qcdmrg_sweep_opts* o, qcdmrg_sweep_repor
 int qcdmrg_sweep_left(qcdmrg_ctx* ctx, const qcdmrg_sweep_opts* o, qcdmrg_sweep_report* rep) {
   return guard(ctx, [&]() {
     Engine& E = ctx->eng;
-    if (!E.have_env) throw Fail{QCDMRG_ESTATE, "build_env first"};
-    if (!o || o->D < 1) throw Fail{QCDMRG_EINVAL, "sweep options with D >= 1 required"};
-    if (o->trunc_eps < 0.0 || (o->trunc_eps > 0.0 && (o->D_min < 1 || o->D_min > o->D)))
-      throw Fail{QCDMRG_EINVAL, "dynamic selection needs 1 <= D_min <= D"};
+    check_sweep_opts(E, o);
     auto t0 = std::chrono::steady_clock::now();
     DavOpts dop = dav_opts(&o->dav);
     qcdmrg_sweep_report R{};
     bool conv = true;
-    while (E.center > 0) {
-      DavResult r = E.davidson(dop);
-      conv = conv && r.converged;
-      for (int k = 0; k < 4; ++k) R.n_hpsi[k] += r.hpsi[k];
-      R.energy = r.energy;
-      R.energy_mixed = r.energy_mixed;
-      R.n_steps++;
-      int nk = 0;
-      double e = E.truncate_move(o->D, -1, 0.0, o->trunc_eps, o->D_min, &nk);
-      R.max_trunc_err = std::max(R.max_trunc_err, e);
-      R.max_D = std::max(R.max_D, nk);
-    }
+    while (E.center > 0) sweep_step(E, o, dop, -1, R, conv);
     R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (rep) *rep = R;
     return conv ? QCDMRG_OK : QCDMRG_ENOTCONV;
