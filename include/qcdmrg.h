@@ -14,6 +14,8 @@
  * Conventions
  *   - Every call returns an int status: QCDMRG_OK (0) or a negative code.
  *     qcdmrg_last_error() gives the message of the last failure on a context.
+ *     No C++ exception leaves a call: a failed internal consistency check
+ *     returns QCDMRG_EINTERNAL.
  *   - The library owns all device memory, the operators and the MPS. Caller
  *     arrays are copied on input; output arrays are caller-allocated.
  *   - Pointers are host pointers unless the function name ends in _dev; _dev
@@ -42,6 +44,7 @@ extern "C" {
 #define QCDMRG_ENOTCONV (-5) /* iteration limit reached; results are still written */
 #define QCDMRG_ETIMEOUT (-6) /* a bounded device wait gave up */
 #define QCDMRG_EIO (-7)      /* file error */
+#define QCDMRG_EINTERNAL (-8) /* an internal consistency check of the library failed (a bug) */
 
 /* symmetry */
 #define QCDMRG_U1 0  /* U(1)xU(1): sector labels (N, 2Sz), bond dimensions count states */

@@ -20,7 +20,7 @@ FP64, TF32, BF16, BF16X3 = 0, 1, 2, 3
 PRECISIONS = {"fp64": FP64, "tf32": TF32, "bf16": BF16, "bf16x3": BF16X3}
 
 _ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ESTATE", -5: "ENOTCONV",
-           -6: "ETIMEOUT", -7: "EIO"}
+           -6: "ETIMEOUT", -7: "EIO", -8: "EINTERNAL"}
 
 
 class QcdmrgError(RuntimeError):

@@ -77,6 +77,29 @@ int guard(qcdmrg_ctx* c, F&& f) {
     std::string m = e.what();
     if (m.find("out of memory") != std::string::npos) return QCDMRG_ENOMEM;
     return QCDMRG_ECUDA;
+  } catch (const std::invalid_argument& e) {
+    c->err = e.what();
+    return QCDMRG_EINVAL;
+  } catch (const std::exception& e) {
+    c->err = e.what();
+    return QCDMRG_EINTERNAL;
+  } catch (...) {
+    c->err = "unknown exception";
+    return QCDMRG_EINTERNAL;
+  }
+}
+
+// host-only calls (no context): exceptions become status codes at the C boundary
+template <class F>
+int host_guard(F&& f) {
+  try {
+    return f();
+  } catch (const std::invalid_argument&) {
+    return QCDMRG_EINVAL;
+  } catch (const std::bad_alloc&) {
+    return QCDMRG_ENOMEM;
+  } catch (...) {
+    return QCDMRG_EINTERNAL;
   }
 }
 
@@ -727,23 +750,27 @@ int qcdmrg_orbital_rdm(qcdmrg_ctx* ctx, double* rho) {
 }
 
 int qcdmrg_orbital_entanglement(int L, const double* rho, double* s1, double* mutual) {
-  if (L < 2 || !rho || !mutual) return QCDMRG_EINVAL;
-  for (size_t k = 0; k < (size_t)L * L * 256; ++k)
-    if (!std::isfinite(rho[k])) return QCDMRG_EINVAL;
-  orbital_entanglement(L, rho, s1, mutual);
-  return QCDMRG_OK;
+  return host_guard([&]() {
+    if (L < 2 || !rho || !mutual) return QCDMRG_EINVAL;
+    for (size_t k = 0; k < (size_t)L * L * 256; ++k)
+      if (!std::isfinite(rho[k])) return QCDMRG_EINVAL;
+    orbital_entanglement(L, rho, s1, mutual);
+    return QCDMRG_OK;
+  });
 }
 
 int qcdmrg_fiedler_order(int L, const double* mutual, int* order, double* fiedler) {
-  if (L < 2 || !mutual || !order) return QCDMRG_EINVAL;
-  for (int i = 0; i < L; ++i)
-    for (int j = 0; j <= i; ++j) {
-      const double a = mutual[(size_t)i * L + j], b = mutual[(size_t)j * L + i];
-      if (!std::isfinite(a) || !std::isfinite(b) || std::fabs(a - b) > 1e-12 * std::max(1.0, std::fabs(a)))
-        return QCDMRG_EINVAL;
-    }
-  fiedler_order(L, mutual, order, fiedler);
-  return QCDMRG_OK;
+  return host_guard([&]() {
+    if (L < 2 || !mutual || !order) return QCDMRG_EINVAL;
+    for (int i = 0; i < L; ++i)
+      for (int j = 0; j <= i; ++j) {
+        const double a = mutual[(size_t)i * L + j], b = mutual[(size_t)j * L + i];
+        if (!std::isfinite(a) || !std::isfinite(b) || std::fabs(a - b) > 1e-12 * std::max(1.0, std::fabs(a)))
+          return QCDMRG_EINVAL;
+      }
+    fiedler_order(L, mutual, order, fiedler);
+    return QCDMRG_OK;
+  });
 }
 
 int qcdmrg_heff_diag(qcdmrg_ctx* ctx, double* out, size_t n) {
@@ -805,76 +832,84 @@ int qcdmrg_truncate_dbss(qcdmrg_ctx* ctx, int D_min, int D_max, double eps, int 
 }
 
 int qcdmrg_extrapolate(const double* x, const double* energy, int n, int degree, double* coef) {
-  // least-squares polynomial E(x) = coef[0] + coef[1] x + ... + coef[degree] x^degree
-  // through the n points; x is scaled to [-1, 1] for the normal equations, whose
-  // (degree + 1)^2 system is solved by Gaussian elimination with partial pivoting
-  if (!x || !energy || !coef || degree < 1 || degree > 3 || n < degree + 1) return QCDMRG_EINVAL;
-  double xs = 0;
-  for (int i = 0; i < n; ++i) {
-    if (!std::isfinite(x[i]) || !std::isfinite(energy[i])) return QCDMRG_EINVAL;
-    xs = std::max(xs, std::fabs(x[i]));
-  }
-  if (!(xs > 0)) return QCDMRG_EINVAL;
-  const int m = degree + 1;
-  long double A[4][5] = {};
-  for (int i = 0; i < n; ++i) {
-    long double p[4];
-    p[0] = 1;
-    for (int k = 1; k < m; ++k) p[k] = p[k - 1] * (x[i] / xs);
-    for (int r = 0; r < m; ++r) {
-      for (int c = 0; c < m; ++c) A[r][c] += p[r] * p[c];
-      A[r][m] += p[r] * energy[i];
+  return host_guard([&]() {
+    // least-squares polynomial E(x) = coef[0] + coef[1] x + ... + coef[degree] x^degree
+    // through the n points; x is scaled to [-1, 1] for the normal equations, whose
+    // (degree + 1)^2 system is solved by Gaussian elimination with partial pivoting
+    if (!x || !energy || !coef || degree < 1 || degree > 3 || n < degree + 1) return QCDMRG_EINVAL;
+    double xs = 0;
+    for (int i = 0; i < n; ++i) {
+      if (!std::isfinite(x[i]) || !std::isfinite(energy[i])) return QCDMRG_EINVAL;
+      xs = std::max(xs, std::fabs(x[i]));
     }
-  }
-  for (int c = 0; c < m; ++c) {
-    int piv = c;
-    for (int r = c + 1; r < m; ++r)
-      if (std::fabs((double)A[r][c]) > std::fabs((double)A[piv][c])) piv = r;
-    if (!(std::fabs((double)A[piv][c]) > 0)) return QCDMRG_EINVAL;   // points do not fix the polynomial
-    for (int k = 0; k <= m; ++k) std::swap(A[c][k], A[piv][k]);
-    for (int r = 0; r < m; ++r) {
-      if (r == c) continue;
-      const long double f = A[r][c] / A[c][c];
-      for (int k = c; k <= m; ++k) A[r][k] -= f * A[c][k];
+    if (!(xs > 0)) return QCDMRG_EINVAL;
+    const int m = degree + 1;
+    long double A[4][5] = {};
+    for (int i = 0; i < n; ++i) {
+      long double p[4];
+      p[0] = 1;
+      for (int k = 1; k < m; ++k) p[k] = p[k - 1] * (x[i] / xs);
+      for (int r = 0; r < m; ++r) {
+        for (int c = 0; c < m; ++c) A[r][c] += p[r] * p[c];
+        A[r][m] += p[r] * energy[i];
+      }
     }
-  }
-  double sc = 1.0;
-  for (int k = 0; k < m; ++k) {
-    coef[k] = (double)(A[k][m] / A[k][k]) / sc;
-    sc *= xs;
-  }
-  return QCDMRG_OK;
+    for (int c = 0; c < m; ++c) {
+      int piv = c;
+      for (int r = c + 1; r < m; ++r)
+        if (std::fabs((double)A[r][c]) > std::fabs((double)A[piv][c])) piv = r;
+      if (!(std::fabs((double)A[piv][c]) > 0)) return QCDMRG_EINVAL;   // points do not fix the polynomial
+      for (int k = 0; k <= m; ++k) std::swap(A[c][k], A[piv][k]);
+      for (int r = 0; r < m; ++r) {
+        if (r == c) continue;
+        const long double f = A[r][c] / A[c][c];
+        for (int k = c; k <= m; ++k) A[r][k] -= f * A[c][k];
+      }
+    }
+    double sc = 1.0;
+    for (int k = 0; k < m; ++k) {
+      coef[k] = (double)(A[k][m] / A[k][k]) / sc;
+      sc *= xs;
+    }
+    return QCDMRG_OK;
+  });
 }
 
 int qcdmrg_active_space(int n, int ncore, int nact, const double* h, const double* V, double* e_core,
                         double* h_act, double* V_act) {
-  if (n < 1 || ncore < 0 || nact < 1 || ncore + nact > n || !h || !V || !e_core || !h_act || !V_act)
-    return QCDMRG_EINVAL;
-  active_space(n, ncore, nact, h, V, e_core, h_act, V_act);
-  return QCDMRG_OK;
+  return host_guard([&]() {
+    if (n < 1 || ncore < 0 || nact < 1 || ncore + nact > n || !h || !V || !e_core || !h_act || !V_act)
+      return QCDMRG_EINVAL;
+    active_space(n, ncore, nact, h, V, e_core, h_act, V_act);
+    return QCDMRG_OK;
+  });
 }
 
 int qcdmrg_orbital_gradient(int n, int ncore, int nact, const double* h, const double* V, const double* gamma1,
                             const double* gamma2, double* grad) {
-  if (n < 1 || ncore < 0 || nact < 1 || ncore + nact > n || !h || !V || !gamma1 || !gamma2 || !grad)
-    return QCDMRG_EINVAL;
-  orbital_gradient(n, ncore, nact, h, V, gamma1, gamma2, grad);
-  return QCDMRG_OK;
+  return host_guard([&]() {
+    if (n < 1 || ncore < 0 || nact < 1 || ncore + nact > n || !h || !V || !gamma1 || !gamma2 || !grad)
+      return QCDMRG_EINVAL;
+    orbital_gradient(n, ncore, nact, h, V, gamma1, gamma2, grad);
+    return QCDMRG_OK;
+  });
 }
 
 int qcdmrg_rotate_orbitals(int n, const double* kappa, const double* h, const double* V, double* U, double* h_out,
                            double* V_out) {
-  if (n < 1 || !kappa || !h || !V || !h_out || !V_out) return QCDMRG_EINVAL;
-  for (int p = 0; p < n; ++p)
-    for (int q = 0; q <= p; ++q) {
-      const double a = kappa[(size_t)p * n + q], b = kappa[(size_t)q * n + p];
-      if (!std::isfinite(a) || std::fabs(a + b) > 1e-12 * std::max(1.0, std::fabs(a))) return QCDMRG_EINVAL;
-    }
-  std::vector<double> u((size_t)n * n);
-  expm_antisym(n, kappa, u.data());
-  rotate_integrals(n, u.data(), h, V, h_out, V_out);
-  if (U) std::copy(u.begin(), u.end(), U);
-  return QCDMRG_OK;
+  return host_guard([&]() {
+    if (n < 1 || !kappa || !h || !V || !h_out || !V_out) return QCDMRG_EINVAL;
+    for (int p = 0; p < n; ++p)
+      for (int q = 0; q <= p; ++q) {
+        const double a = kappa[(size_t)p * n + q], b = kappa[(size_t)q * n + p];
+        if (!std::isfinite(a) || std::fabs(a + b) > 1e-12 * std::max(1.0, std::fabs(a))) return QCDMRG_EINVAL;
+      }
+    std::vector<double> u((size_t)n * n);
+    expm_antisym(n, kappa, u.data());
+    rotate_integrals(n, u.data(), h, V, h_out, V_out);
+    if (U) std::copy(u.begin(), u.end(), U);
+    return QCDMRG_OK;
+  });
 }
 
 int qcdmrg_move_center(qcdmrg_ctx* ctx, int target) {
@@ -956,7 +991,7 @@ int qcdmrg_select_configs(int symmetry, int L, int N, int two_s, const double* h
   if ((symmetry != QCDMRG_U1 && symmetry != QCDMRG_SU2) || L < 2 || L > 4096 || nmax < 1 || !h || !V ||
       !steps || !count)
     return QCDMRG_EINVAL;
-  try {
+  return host_guard([&]() {
     std::vector<uint8_t> st;
     std::vector<double> en;
     const int m = select_configs(L, symmetry == QCDMRG_SU2, N, two_s, h, V, nmax, st, en);
@@ -964,11 +999,7 @@ int qcdmrg_select_configs(int symmetry, int L, int N, int two_s, const double* h
     if (energy) std::copy(en.begin(), en.end(), energy);
     *count = m;
     return QCDMRG_OK;
-  } catch (const std::invalid_argument&) {
-    return QCDMRG_EINVAL;
-  } catch (const std::bad_alloc&) {
-    return QCDMRG_ENOMEM;
-  }
+  });
 }
 
 int qcdmrg_config_mps(int symmetry, int L, int N, int two_s, int n, const uint8_t* steps, const double* coef,
@@ -976,7 +1007,7 @@ int qcdmrg_config_mps(int symmetry, int L, int N, int two_s, int n, const uint8_
                       int* n_sec, size_t* n_data) {
   if ((symmetry != QCDMRG_U1 && symmetry != QCDMRG_SU2) || L < 2 || n < 1 || !steps || !coef)
     return QCDMRG_EINVAL;
-  try {
+  return host_guard([&]() {
     ImportArrays A;
     configs_to_mps(L, symmetry == QCDMRG_SU2, N, two_s, n, steps, coef, A);
     if ((bond_sec && sec_cap < (int)A.sec.size()) || (data && cap < A.data.size())) return QCDMRG_EINVAL;
@@ -987,11 +1018,7 @@ int qcdmrg_config_mps(int symmetry, int L, int N, int two_s, int n, const uint8_
     if (bond_sec) std::copy(A.sec.begin(), A.sec.end(), bond_sec);
     if (data) std::copy(A.data.begin(), A.data.end(), data);
     return QCDMRG_OK;
-  } catch (const std::invalid_argument&) {
-    return QCDMRG_EINVAL;
-  } catch (const std::bad_alloc&) {
-    return QCDMRG_ENOMEM;
-  }
+  });
 }
 
 int qcdmrg_check_device(qcdmrg_ctx* ctx) {

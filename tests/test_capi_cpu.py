@@ -22,6 +22,14 @@ def test_binding_lists_the_header():
     assert sorted(qd.EXPORTS) == header_functions()
 
 
+def test_binding_names_every_status_code():
+    import re
+    import paper_2603_28648_b300 as qd
+    with open(HEADER) as f:
+        codes = {int(v): n for n, v in re.findall(r"#define QCDMRG_(E[A-Z]+) \((-\d+)\)", f.read())}
+    assert codes and codes == qd._ERRORS
+
+
 def test_create_without_device_fails_cleanly():
     import paper_2603_28648_b300 as qd
     from tests._lib import cuda_available
