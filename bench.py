@@ -81,6 +81,14 @@ def parse():
     ap.add_argument("--sum-gemm", type=int, default=0, choices=[-1, 0, 1],
                     help="operator sums of the renormalization side as GEMMs (1), block by block (-1), "
                          "or as GEMMs only with the switch (0)")
+    ap.add_argument("--qi", action="store_true",
+                    help="orbital-entanglement mode: the two-orbital density matrices of every pair by one "
+                         "walk of the centre, entropies, mutual information and the Fiedler order, timed "
+                         "(random MPS at --D, --symmetry)")
+    ap.add_argument("--warm-start", type=int, default=0, metavar="NMAX",
+                    help="configuration warm-start mode: NMAX selected configurations imported as an MPS, "
+                         "the warm-up half sweep and --steps sweeps at --D, against the same sweeps from a "
+                         "random MPS (energies and times per sweep)")
     ap.add_argument("--products", default=None, choices=["fp64", "tf32", "bf16", "bf16x3"],
                     help="only time single H_eff psi products of one form (the command the ncu "
                          "captures under profiles/ run); prints a short line")
@@ -820,6 +828,105 @@ def run_adjoint(args, rank, world, local):
     ctx.close()
 
 
+def run_qi(args, rank, world, local):
+    """Orbital entanglement through the public API: qcdmrg_orbital_rdm (one walk of the centre,
+    the right blocks holding the matrix units of their orbitals) on a random MPS, then the
+    entropies, mutual information and Fiedler order (host calls), each timed; checks that every
+    rho_ij has unit trace and that the order is a permutation."""
+    import numpy as np
+    import torch
+    import qcinputs as q
+    import paper_2603_28648_b300 as qd
+    torch.cuda.set_device(local)
+    L, N, D = args.L, args.N, args.D
+    sym = qd.SU2 if args.symmetry == "su2" else qd.U1
+    h, V = q.make_integrals(L, q.integrals.BASE_SEED + 2)
+    ctx = qd.Context(device=local, symmetry=sym, hbm_budget_gb=args.hbm_budget, pair_switch=args.pair_switch,
+                     sum_gemm=args.sum_gemm)
+    ctx.load_integrals(h, V)
+    ctx.set_target(N, 0)
+    ctx.init_mps(D, q.integrals.BASE_SEED + 1002, L // 2 - 1)
+    ctx.build_env()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    R = ctx.orbital_rdm(L)
+    t1 = time.perf_counter()
+    s1, I = qd.orbital_entanglement(R)
+    order, _ = qd.fiedler_order(I)
+    t2 = time.perf_counter()
+    st = ctx.stats()
+    ctx.close()
+    tr = [abs(np.trace(R[i, j]) - 1.0) for i in range(L) for j in range(i + 1, L)]
+    line = {
+        "metric": f"orbital entanglement seconds at L={L}", "value": t2 - t0, "unit": "s", "n_gpus": 1,
+        "steps": 1, "warmup": 0, "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.symmetry}_L{L}_N{N}_S0_D{D} random MPS",
+                   "orbital_rdm_walk_s": t1 - t0, "entropies_order_s": t2 - t1,
+                   "max_trace_error": float(max(tr)), "order_is_permutation": sorted(order.tolist()) == list(range(L)),
+                   "max_mutual_information": float(I.max()), "fiedler_order": order.tolist(),
+                   "device_bytes_peak": st["device_bytes"], "pair_switch": args.pair_switch},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_warm_start(args, rank, world, local):
+    """Configuration warm start through the public API against a random start: the NMAX
+    lowest configurations within two electrons of the aufbau reference (qcdmrg_select_configs)
+    imported as an MPS (qcdmrg_config_mps, reference coefficient only), the warm-up half sweep
+    (qcdmrg_sweep_left) and --steps full sweeps; then the same sweeps from a random MPS at the
+    same D. Energies and times per sweep, mixed policy."""
+    import numpy as np
+    import torch
+    import qcinputs as q
+    import paper_2603_28648_b300 as qd
+    torch.cuda.set_device(local)
+    L, N, D = args.L, args.N, args.D
+    sym = qd.SU2 if args.symmetry == "su2" else qd.U1
+    h, V = q.make_integrals(L, q.integrals.BASE_SEED + 2)
+
+    def context():
+        ctx = qd.Context(device=local, symmetry=sym, hbm_budget_gb=args.hbm_budget, pair_switch=args.pair_switch,
+                         sum_gemm=args.sum_gemm)
+        ctx.load_integrals(h, V)
+        ctx.set_target(N, 0)
+        return ctx
+
+    t0 = time.perf_counter()
+    steps, en = qd.select_configs(sym, h, V, N, 0, args.warm_start)
+    coef = np.zeros(len(steps))
+    coef[0] = 1.0
+    ctx = context()
+    ctx.import_configs(L, N, 0, steps, coef)
+    ctx.build_env()
+    t1 = time.perf_counter()
+    half = ctx.sweep_left(D, allow_notconv=True, tol=1e-6, policy=1)
+    warm = []
+    for _ in range(args.steps):
+        r = ctx.sweep(D, allow_notconv=True, tol=1e-6, policy=1)
+        warm.append({"energy": r["energy"], "seconds": r["seconds"]})
+        progress(f"warm start sweep: E = {r['energy']:.10f}, {r['seconds']:.1f} s")
+    ctx.close()
+    ctx = context()
+    ctx.init_mps(D, q.integrals.BASE_SEED + 1002, L // 2 - 1)
+    ctx.build_env()
+    rand = []
+    for _ in range(args.steps):
+        r = ctx.sweep(D, allow_notconv=True, tol=1e-6, policy=1)
+        rand.append({"energy": r["energy"], "seconds": r["seconds"]})
+        progress(f"random start sweep: E = {r['energy']:.10f}, {r['seconds']:.1f} s")
+    ctx.close()
+    line = {
+        "metric": f"energy after {args.steps} sweeps from the configuration warm start", "value": warm[-1]["energy"],
+        "unit": "Eh", "n_gpus": 1, "steps": args.steps, "warmup": 0, "higher_is_better": False,
+        "dtype": "mixed", "data": "synthetic",
+        "config": {"workload": f"{args.symmetry}_L{L}_N{N}_S0_D{D}", "nmax": args.warm_start,
+                   "configs": len(steps), "reference_energy": float(en[0]),
+                   "select_and_import_s": t1 - t0, "half_sweep": {"energy": half["energy"], "seconds": half["seconds"]},
+                   "warm_sweeps": warm, "random_sweeps": rand, "pair_switch": args.pair_switch},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_outofcore(args, rank, world, local):
     """Out-of-core operator store on the CAS(89,102)-shaped sextet (L=102, N=89, 2S=5,
     SU(2), open-shell orbital profile; the paper's large benchmark system, whose operators
@@ -987,6 +1094,12 @@ def main():
     elif args.scf:
         if rank == 0:
             run_scf(args, rank, world, local)
+    elif args.qi:
+        if rank == 0:
+            run_qi(args, rank, world, local)
+    elif args.warm_start:
+        if rank == 0:
+            run_warm_start(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
 
