@@ -556,6 +556,21 @@ int qcdmrg_orbital_entanglement(int L, const double* rho, double* s1, double* mu
 int qcdmrg_fiedler_order(int L, const double* mutual, int* order, double* fiedler);
 
 /*
+ * qcdmrg_ordering_cost (host only): *cost = sum_{i<j} mutual_ij |pos_i - pos_j|^eta
+ * with pos_i the position of orbital i in order (order[k] = the orbital at
+ * position k, a permutation of 0..L-1): the distance cost of entangled orbitals
+ * along the chain of Barcza et al. (2011); the Fiedler vector minimises its
+ * eta = 2 form relaxed to real positions.
+ * qcdmrg_refine_order (host only): order improved in place by exchanging the
+ * positions of two orbitals, the best exchange first, while one lowers the cost
+ * (at most max_swaps exchanges); *swaps (may be NULL) gets the number made.
+ * Errors: EINVAL (L < 2, NULL, order not a permutation, eta not finite or <= 0,
+ * mutual not symmetric to 1e-12 or not finite, max_swaps < 0).
+ */
+int qcdmrg_ordering_cost(int L, const double* mutual, const int* order, double eta, double* cost);
+int qcdmrg_refine_order(int L, const double* mutual, double eta, int* order, int max_swaps, int* swaps);
+
+/*
  * Configuration-space warm start: the paper converges its runs with an
  * SU(2)-aware dynamically extended active space procedure (SU(2)-DEAS, Legeza
  * et al. 2003; Numerical benchmark section), whose warm-up sweep takes the

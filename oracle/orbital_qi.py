@@ -99,3 +99,18 @@ def fiedler_order(I):
     if f[lead] > 0:
         f = -f
     return np.argsort(f, kind="stable"), f
+
+
+def ordering_cost(I, order, eta=2.0):
+    """sum_{i<j} I_ij |pos_i - pos_j|^eta, pos_i the position of orbital i in order."""
+    L = len(order)
+    pos = np.empty(L, int)
+    pos[np.asarray(order)] = np.arange(L)
+    return float(sum(I[i, j] * abs(pos[i] - pos[j]) ** eta for i in range(L) for j in range(i + 1, L)))
+
+
+def best_order(I, eta=2.0):
+    """The lowest-cost chain order by brute force over all permutations (small L only)."""
+    import itertools
+    L = I.shape[0]
+    return min(itertools.permutations(range(L)), key=lambda o: ordering_cost(I, o, eta))

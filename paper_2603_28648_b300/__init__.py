@@ -86,7 +86,7 @@ EXPORTS = [
     "qcdmrg_energy_grad", "qcdmrg_truncate_dbss", "qcdmrg_extrapolate", "qcdmrg_active_space",
     "qcdmrg_orbital_gradient", "qcdmrg_rotate_orbitals", "qcdmrg_orbital_rdm",
     "qcdmrg_orbital_entanglement", "qcdmrg_fiedler_order", "qcdmrg_select_configs", "qcdmrg_config_mps",
-    "qcdmrg_sweep_left",
+    "qcdmrg_sweep_left", "qcdmrg_ordering_cost", "qcdmrg_refine_order",
 ]
 
 _lib = None
@@ -155,6 +155,8 @@ def load(path=None):
     lib.qcdmrg_config_mps.argtypes = [ci, ci, ci, ci, ci, u8p, dp, ip, ip, ip, ci, dp, ctypes.c_size_t, ip,
                                       ctypes.POINTER(ctypes.c_size_t)]
     lib.qcdmrg_sweep_left.argtypes = [P, ctypes.POINTER(SweepOpts), ctypes.POINTER(SweepReport)]
+    lib.qcdmrg_ordering_cost.argtypes = [ci, dp, ip, ctypes.c_double, dp]
+    lib.qcdmrg_refine_order.argtypes = [ci, dp, ctypes.c_double, ip, ci, ip]
     for f in EXPORTS:
         getattr(lib, f).restype = getattr(lib, f).restype or ctypes.c_int
     lib.qcdmrg_last_error.restype = ctypes.c_char_p
@@ -532,6 +534,32 @@ def config_mps(symmetry, L, N, two_s, steps, coef, lib=None):
     if rc != 0:
         raise QcdmrgError(rc, "qcdmrg_config_mps: invalid configurations")
     return center.value, nsec, sec[:3 * nsec_n.value], data[:ndata.value]
+
+
+def ordering_cost(mutual, order, eta=2.0, lib=None):
+    """qcdmrg_ordering_cost: sum_{i<j} I_ij |pos_i - pos_j|^eta of a chain order."""
+    lib = lib or load()
+    m = _f64(mutual)
+    o = np.ascontiguousarray(order, dtype=np.int32)
+    c = ctypes.c_double()
+    rc = lib.qcdmrg_ordering_cost(m.shape[0], _dptr(m), o.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), eta,
+                                  ctypes.byref(c))
+    if rc != 0:
+        raise QcdmrgError(rc, "qcdmrg_ordering_cost: invalid arguments")
+    return c.value
+
+
+def refine_order(mutual, order, eta=2.0, max_swaps=10000, lib=None):
+    """qcdmrg_refine_order: (improved order, exchanges made)."""
+    lib = lib or load()
+    m = _f64(mutual)
+    o = np.array(order, dtype=np.int32)
+    n = ctypes.c_int()
+    rc = lib.qcdmrg_refine_order(m.shape[0], _dptr(m), eta, o.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                 max_swaps, ctypes.byref(n))
+    if rc != 0:
+        raise QcdmrgError(rc, "qcdmrg_refine_order: invalid arguments")
+    return o.astype(np.int64), n.value
 
 
 def reorder_integrals(h, V, order):

@@ -773,6 +773,48 @@ int qcdmrg_fiedler_order(int L, const double* mutual, int* order, double* fiedle
   });
 }
 
+namespace {
+
+bool symmetric_finite(int L, const double* m) {
+  for (int i = 0; i < L; ++i)
+    for (int j = 0; j <= i; ++j) {
+      const double a = m[(size_t)i * L + j], b = m[(size_t)j * L + i];
+      if (!std::isfinite(a) || !std::isfinite(b) || std::fabs(a - b) > 1e-12 * std::max(1.0, std::fabs(a)))
+        return false;
+    }
+  return true;
+}
+
+bool permutation(int L, const int* order) {
+  std::vector<char> seen(L, 0);
+  for (int k = 0; k < L; ++k) {
+    if (order[k] < 0 || order[k] >= L || seen[order[k]]) return false;
+    seen[order[k]] = 1;
+  }
+  return true;
+}
+
+}  // namespace
+
+int qcdmrg_ordering_cost(int L, const double* mutual, const int* order, double eta, double* cost) {
+  return host_guard([&]() {
+    if (L < 2 || !mutual || !order || !cost || !std::isfinite(eta) || !(eta > 0)) return QCDMRG_EINVAL;
+    if (!symmetric_finite(L, mutual) || !permutation(L, order)) return QCDMRG_EINVAL;
+    *cost = ordering_cost(L, mutual, order, eta);
+    return QCDMRG_OK;
+  });
+}
+
+int qcdmrg_refine_order(int L, const double* mutual, double eta, int* order, int max_swaps, int* swaps) {
+  return host_guard([&]() {
+    if (L < 2 || !mutual || !order || !std::isfinite(eta) || !(eta > 0) || max_swaps < 0) return QCDMRG_EINVAL;
+    if (!symmetric_finite(L, mutual) || !permutation(L, order)) return QCDMRG_EINVAL;
+    const int n = refine_order(L, mutual, eta, order, max_swaps);
+    if (swaps) *swaps = n;
+    return QCDMRG_OK;
+  });
+}
+
 int qcdmrg_heff_diag(qcdmrg_ctx* ctx, double* out, size_t n) {
   return guard(ctx, [&]() {
     Engine& E = ctx->eng;

@@ -154,4 +154,49 @@ void fiedler_order(int L, const double* mutual, int* order, double* fiedler) {
   if (fiedler) std::copy(f.begin(), f.end(), fiedler);
 }
 
+double ordering_cost(int L, const double* mutual, const int* order, double eta) {
+  std::vector<int> pos(L);
+  for (int k = 0; k < L; ++k) pos[order[k]] = k;
+  double c = 0.0;
+  for (int i = 0; i < L; ++i)
+    for (int j = i + 1; j < L; ++j) c += mutual[(size_t)i * L + j] * std::pow(std::abs(pos[i] - pos[j]), eta);
+  return c;
+}
+
+int refine_order(int L, const double* mutual, double eta, int* order, int max_passes) {
+  // steepest descent over position exchanges: each candidate exchange of the
+  // orbitals at positions a < b is scored by the change of the terms that
+  // involve them (O(L) each), the best improving one is taken
+  std::vector<int> pos(L);
+  for (int k = 0; k < L; ++k) pos[order[k]] = k;
+  auto M = [&](int i, int j) { return mutual[(size_t)i * L + j]; };
+  auto d = [&](int x) { return std::pow(std::abs(x), eta); };
+  int made = 0;
+  while (made < max_passes) {
+    double best = 0.0;
+    int ba = -1, bb = -1;
+    for (int a = 0; a < L; ++a)
+      for (int b = a + 1; b < L; ++b) {
+        const int oa = order[a], ob = order[b];
+        double delta = 0.0;
+        for (int k = 0; k < L; ++k) {
+          if (k == oa || k == ob) continue;
+          const int pk = pos[k];
+          delta += M(oa, k) * (d(b - pk) - d(a - pk)) + M(ob, k) * (d(a - pk) - d(b - pk));
+        }
+        if (delta < best - 1e-12 * (1.0 + std::fabs(best))) {
+          best = delta;
+          ba = a;
+          bb = b;
+        }
+      }
+    if (ba < 0) break;
+    std::swap(order[ba], order[bb]);
+    pos[order[ba]] = ba;
+    pos[order[bb]] = bb;
+    ++made;
+  }
+  return made;
+}
+
 }  // namespace qd

@@ -23,4 +23,13 @@ void orbital_entanglement(int L, const double* rho, double* s1, double* mutual);
 // component of magnitude above 1e-8 of the largest made negative.
 void fiedler_order(int L, const double* mutual, int* order, double* fiedler);
 
+// sum_{i<j} mutual_ij |pos_i - pos_j|^eta for the chain order (order[k] = the
+// orbital at position k)
+double ordering_cost(int L, const double* mutual, const int* order, double eta);
+
+// order improved in place by exchanging the positions of two orbitals while an
+// exchange lowers ordering_cost (best exchange first, at most max_passes
+// exchanges); returns the exchanges made
+int refine_order(int L, const double* mutual, double eta, int* order, int max_passes);
+
 }  // namespace qd

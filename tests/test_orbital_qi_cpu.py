@@ -93,3 +93,61 @@ def test_invalid_entanglement_arguments_are_rejected():
     assert lib.qcdmrg_fiedler_order(3, mp, op, null_d) == 0
     with pytest.raises(qd.QcdmrgError):
         qd.fiedler_order(np.array([[0.0, 1.0], [2.0, 0.0]]), lib=lib)
+
+
+@pytest.mark.parametrize("L,eta,seed", [(5, 2.0, 1), (8, 2.0, 2), (8, 1.0, 3), (12, 1.5, 4)])
+def test_ordering_cost_and_refinement(L, eta, seed):
+    """The cost equals its plain definition; the refined order is never worse than its start
+    and no single exchange of two orbitals lowers it further (checked over all exchanges)."""
+    import itertools
+    import paper_2603_28648_b300 as qd
+    from oracle import orbital_qi as qi
+    lib = qd.load(ensure_built())
+    rng = np.random.default_rng(seed)
+    A = rng.exponential(size=(L, L))
+    A = A + A.T
+    np.fill_diagonal(A, 0.0)
+    start = rng.permutation(L)
+    c0 = qd.ordering_cost(A, start, eta, lib=lib)
+    assert abs(c0 - qi.ordering_cost(A, start, eta)) <= 1e-12 * c0
+    o, n = qd.refine_order(A, start, eta, lib=lib)
+    assert sorted(o) == list(range(L))
+    c1 = qi.ordering_cost(A, o, eta)
+    assert c1 <= c0 + 1e-12 and (n == 0 or c1 < c0)
+    for a, b in itertools.combinations(range(L), 2):
+        t = o.copy()
+        t[a], t[b] = t[b], t[a]
+        assert qi.ordering_cost(A, t, eta) >= c1 - 1e-9 * c1
+
+
+def test_path_graph_order_is_the_global_minimum():
+    """On a path graph with hidden labels the Fiedler order has the smallest possible cost
+    (brute force over all 720 orders of six orbitals) and the refinement leaves it alone."""
+    import paper_2603_28648_b300 as qd
+    from oracle import orbital_qi as qi
+    lib = qd.load(ensure_built())
+    n = 6
+    perm = np.random.default_rng(5).permutation(n)
+    I = np.zeros((n, n))
+    for k in range(n - 1):
+        I[perm[k], perm[k + 1]] = I[perm[k + 1], perm[k]] = 1.0
+    order, _ = qd.fiedler_order(I, lib=lib)
+    best = qi.best_order(I)
+    assert qd.ordering_cost(I, order, lib=lib) == qi.ordering_cost(I, best) == n - 1
+    o, swaps = qd.refine_order(I, order, lib=lib)
+    assert swaps == 0 and list(o) == list(order)
+
+
+def test_invalid_ordering_arguments_are_rejected():
+    import paper_2603_28648_b300 as qd
+    lib = qd.load(ensure_built())
+    I = np.ones((4, 4)) - np.eye(4)
+    for order, eta in (([0, 1, 1, 3], 2.0), ([0, 1, 2, 4], 2.0), ([0, 1, 2, 3], 0.0), ([0, 1, 2, 3], np.nan)):
+        with pytest.raises(qd.QcdmrgError):
+            qd.ordering_cost(I, order, eta, lib=lib)
+        with pytest.raises(qd.QcdmrgError):
+            qd.refine_order(I, order, eta, lib=lib)
+    J = I.copy()
+    J[0, 1] = 2.0
+    with pytest.raises(qd.QcdmrgError):
+        qd.ordering_cost(J, [0, 1, 2, 3], lib=lib)
