@@ -494,5 +494,6 @@ int main(int argc, char** argv) {
               "heff_gb=%.3f env_tflop=%.2f\n", L, N, D, (long long)E.lay.size, E.plan.nterms, E.plan.flops / 1e9,
               (long long)ex.launches_checked, fails, ex.peak / 1e9, ex.cur_live / 1e9, env / 1e9, E.plan.bytes / 1e9,
               E.env_flops / 1e12);
+  std::printf("heff plan: flops=%.17g bytes=%.17g\n", E.plan.flops, E.plan.bytes);
   return fails ? 1 : 0;
 }
