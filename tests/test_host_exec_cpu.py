@@ -6,7 +6,6 @@ MPS of several shapes, edge centres included, and on the M-expansion of an SU(2)
 the normal/complementary switch at several cuts as well. Every launch is bounds-checked.
 tests/host_exec.cpp holds the test-only host executor; the product path still needs CUDA."""
 import os
-import shutil
 import struct
 import subprocess
 
@@ -15,21 +14,13 @@ import pytest
 
 import qcinputs as q
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-CSRC = os.path.join(ROOT, "paper_2603_28648_b300", "csrc")
-HOST_SOURCES = ["core.cpp", "rules.cpp", "rules_su2.cpp", "su2.cpp", "su2expand.cpp", "init.cpp", "engine.cpp", "tiled.cpp"]
-
 
 @pytest.fixture(scope="module")
 def host_exec(tmp_path_factory):
-    if shutil.which("g++") is None:
+    from tests._lib import build_host_executable
+    out = build_host_executable("host_exec.cpp", str(tmp_path_factory.mktemp("hostexec") / "host_exec"))
+    if out is None:
         pytest.skip("g++ not available")
-    out = str(tmp_path_factory.mktemp("hostexec") / "host_exec")
-    inc = ["-I", CSRC]
-    if os.path.isdir("/usr/local/cuda/include"):
-        inc += ["-I", "/usr/local/cuda/include"]
-    subprocess.run(["g++", "-O2", "-std=c++17", "-pthread"] + inc + [os.path.join(ROOT, "tests", "host_exec.cpp")] +
-                   [os.path.join(CSRC, s) for s in HOST_SOURCES] + ["-o", out], check=True)
     return out
 
 

@@ -4,29 +4,17 @@ FP64 segments and the tiled tensor-core work items — stay inside the buffers t
 address, no work item is empty, and both H_eff plans count the same algorithmic flops.
 The library's host sources are compiled with g++ together with tests/planner_check.cpp,
 which records allocations instead of computing."""
-import os
-import shutil
 import subprocess
 
 import pytest
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-CSRC = os.path.join(ROOT, "paper_2603_28648_b300", "csrc")
-HOST_SOURCES = ["core.cpp", "rules.cpp", "rules_su2.cpp", "su2.cpp", "su2expand.cpp", "init.cpp", "engine.cpp", "tiled.cpp"]
-
 
 @pytest.fixture(scope="module")
 def checker(tmp_path_factory):
-    if shutil.which("g++") is None:
+    from tests._lib import build_host_executable
+    out = build_host_executable("planner_check.cpp", str(tmp_path_factory.mktemp("planner") / "planner_check"))
+    if out is None:
         pytest.skip("g++ not available")
-    out = str(tmp_path_factory.mktemp("planner") / "planner_check")
-    inc = ["-I", CSRC]
-    cuda_inc = "/usr/local/cuda/include"
-    if os.path.isdir(cuda_inc):
-        inc += ["-I", cuda_inc]
-    cmd = (["g++", "-O2", "-std=c++17", "-pthread"] + inc + [os.path.join(ROOT, "tests", "planner_check.cpp")] +
-           [os.path.join(CSRC, s) for s in HOST_SOURCES] + ["-o", out])
-    subprocess.run(cmd, check=True)
     return out
 
 
