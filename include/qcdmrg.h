@@ -526,8 +526,10 @@ int qcdmrg_rotate_orbitals(int n, const double* kappa, const double* h, const do
  * array of L*L*256 doubles, block (i, j) at (i*L + j)*256 for i < j, a
  * row-major 16 x 16 matrix with row (and column) 4 x + y, x the state of
  * orbital i and y that of orbital j (0 empty, 1 up, 2 down, 3 a+_up a+_dn|0>);
- * blocks with i >= j are written as zeros. QCDMRG_SU2: of the state's M = S
- * component. The centre walks the chain once from bond 0 by exact moves (no
+ * blocks with i >= j are written as zeros. QCDMRG_SU2: the average over the
+ * multiplet's 2S + 1 components (one component's rho_ij depends on M when
+ * S > 0; the average does not), one walk per component. The centre walks the
+ * chain once from bond 0 by exact moves (no
  * truncation) and every right block holds the 16 matrix units of each of its
  * orbitals (16 (L - p) extra operators in the block at site p); the MPS, its
  * centre and the environment are restored afterwards. Errors: ESTATE (no

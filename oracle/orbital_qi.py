@@ -13,7 +13,8 @@ as FCI coefficients over determinants |D> = prod_k (a+_k)^{n_k}|vac> (k = 2p + s
   {|0>, |up>, |dn>, |up dn> = a+_up a+_dn|0>};
 * rho_ij[(x y), (x' y')] = sum over determinant pairs with the same rest of
   s(D) c_D s(D') c_D' (the partial trace over the other orbitals);
-  rho_i likewise with orbital i alone;
+  rho_i likewise with orbital i alone; for a spin multiplet, the average of rho_ij over its
+  2S + 1 components (the components of one multiplet give different rho_ij when S > 0);
 * S = -sum lambda ln lambda over the eigenvalues; I_ij = S_i + S_j - S_ij;
 * the ordering sorts the orbitals by the eigenvector of the second smallest eigenvalue
   (the Fiedler vector) of the graph Laplacian diag(sum_j I_ij) - I (Barcza et al. 2011,
@@ -114,3 +115,27 @@ def best_order(I, eta=2.0):
     import itertools
     L = I.shape[0]
     return min(itertools.permutations(range(L)), key=lambda o: ordering_cost(I, o, eta))
+
+
+def multiplet_components(L, N, two_s, v):
+    """[(dets, vector)] of the 2S + 1 components of the spin multiplet whose M = S component
+    is v (a vector of DetSpace(L, N, two_s)): S_- = sum_p a+_{p dn} a_{p up} applied again and
+    again, each result normalised."""
+    from oracle.fci import DetSpace, excitation_matrix
+    sp = DetSpace(L, N, two_s)
+    cur = np.asarray(v, float) / np.linalg.norm(v)
+    out = [(sp.dets, cur)]
+    for m in range(two_s - 2, -two_s - 1, -2):
+        sp2 = DetSpace(L, N, m)
+        lower = sum(excitation_matrix(sp, sp2, 2 * p + 1, 2 * p) for p in range(L))
+        cur = lower @ cur
+        cur = cur / np.linalg.norm(cur)
+        out.append((sp2.dets, cur))
+        sp = sp2
+    return out
+
+
+def multiplet_rdm(L, N, two_s, v, i, j):
+    """rho_ij averaged over the 2S + 1 components of the multiplet (independent of M)."""
+    comps = multiplet_components(L, N, two_s, v)
+    return sum(two_orbital_rdm(d, c, i, j) for d, c in comps) / len(comps)

@@ -6,6 +6,7 @@
 #include "su2expand.hpp"
 
 #include <algorithm>
+#include <climits>
 #include <deque>
 #include <chrono>
 #include <cmath>
@@ -1353,8 +1354,9 @@ void Engine::restore(const MpsSnapshot& sn) {
   build_env();
 }
 
-std::vector<double> Engine::on_m_expansion(const std::function<std::vector<double>(Engine&)>& f) {
+std::vector<double> Engine::on_m_expansion(const std::function<std::vector<double>(Engine&)>& f, int two_m) {
   if (!have_env) throw StateError("build_env first");
+  if (two_m == INT_MIN) two_m = two_s;
   MpsSnapshot sn = snapshot();
   SU2Mps in;
   in.L = L;
@@ -1367,13 +1369,13 @@ std::vector<double> Engine::on_m_expansion(const std::function<std::vector<doubl
   in.site = std::move(sn.site);
   in.psi = std::move(sn.psi);
   U1Mps out;
-  expand_mps_su2(in, out);
+  expand_mps_su2(in, out, two_m);
   Engine U;
   U.ex = ex;
   U.pr = pr;
   U.I = I;
   U.N = N;
-  U.two_s = two_s;
+  U.two_s = two_m;
   U.L = L;
   U.su2 = false;
   U.device = device;
@@ -1416,8 +1418,16 @@ std::vector<double> Engine::rdm2_sweep_su2() {
 
 std::vector<double> Engine::orbital_rdm2() {
   if (!have_env) throw StateError("build_env first");
-  // SU(2): the same measurement on the state's M = S expansion
-  if (su2) return on_m_expansion([](Engine& U) { return U.orbital_rdm2(); });
+  if (su2) {
+    // rho_ij of one component depends on M; the average over the multiplet
+    // does not (it is what the spin-free entropies of the state are made of)
+    std::vector<double> avg((size_t)L * L * 256, 0.0);
+    for (int m = -two_s; m <= two_s; m += 2) {
+      const std::vector<double> r = on_m_expansion([](Engine& U) { return U.orbital_rdm2(); }, m);
+      for (size_t k = 0; k < avg.size(); ++k) avg[k] += r[k] / (two_s + 1);
+    }
+    return avg;
+  }
   std::vector<double> R((size_t)L * L * 256, 0.0);
   // the MPS before the walk, restored exactly afterwards
   const MpsSnapshot snap = snapshot();

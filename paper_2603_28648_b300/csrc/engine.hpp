@@ -1,5 +1,6 @@
 // Sweep engine: MPS, renormalized blocks, H_eff plan, Davidson, truncation.
 #pragma once
+#include <climits>
 #include <functional>
 #include <map>
 #include <stdexcept>
@@ -138,7 +139,8 @@ struct Engine {
   // orbitals i < j, row (x_i, y_j) = 4 x + y) of the normalised state for every
   // pair, as L*L blocks of 256 (i >= j left zero): the centre walks the chain
   // once by exact moves, right blocks keep the matrix units of their orbitals;
-  // the MPS is restored afterwards. SU(2): of the M = S expansion.
+  // the MPS is restored afterwards. SU(2): the average over the multiplet's
+  // 2S + 1 components (one walk of each component's expansion).
   bool keep_local = false;
   std::vector<double> orbital_rdm2();
 
@@ -154,10 +156,11 @@ struct Engine {
   };
   MpsSnapshot snapshot();
   void restore(const MpsSnapshot& s);   // uploads the tensors and rebuilds the environment
-  // f run on a U(1) engine (same executor, integrals, target and centre) that
-  // holds this SU(2) state's M = S expansion; this engine's centre is prepared
-  // again afterwards
-  std::vector<double> on_m_expansion(const std::function<std::vector<double>(Engine&)>& f);
+  // f run on a U(1) engine (same executor, integrals, particle number and
+  // centre) that holds this SU(2) state's expansion at the component 2M = two_m
+  // (M = S when two_m is the default); this engine's centre is prepared again
+  // afterwards
+  std::vector<double> on_m_expansion(const std::function<std::vector<double>(Engine&)>& f, int two_m = INT_MIN);
 };
 
 }  // namespace qd

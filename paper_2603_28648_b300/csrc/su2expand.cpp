@@ -83,7 +83,11 @@ ExpandedBond expand_bond(const Basis& b) {
   return e;
 }
 
-void expand_mps_su2(const SU2Mps& in, U1Mps& out) {
+void expand_mps_su2(const SU2Mps& in, U1Mps& out) { expand_mps_su2(in, out, in.two_s); }
+
+void expand_mps_su2(const SU2Mps& in, U1Mps& out, int two_m) {
+  if (std::abs(two_m) > in.two_s || ((in.two_s - two_m) & 1))
+    throw std::invalid_argument("expand_mps_su2: M outside the multiplet");
   const int L = in.L, c = in.center;
   std::vector<ExpandedBond> eb(L + 1);
   out.bonds.assign(L + 1, Basis());
@@ -156,13 +160,13 @@ void expand_mps_su2(const SU2Mps& in, U1Mps& out) {
         }
     }
   }
-  // the two-site state: ((x s1) J_a, (s2 y) J_b) S at M = S
+  // the two-site state: ((x s1) J_a, (s2 y) J_b) S at the component M
   ProdBasis L2 = make_prod(in.bonds[c], true), R2 = make_prod(in.bonds[c + 2], false);
   ProdBasis L1 = make_prod(out.bonds[c], true), R1 = make_prod(out.bonds[c + 2], false);
   const PsiLayout lay2 = make_psi_layout(L2, R2, QN{in.N, in.two_s});
-  const PsiLayout lay1 = make_psi_layout(L1, R1, QN{in.N, in.two_s});
+  const PsiLayout lay1 = make_psi_layout(L1, R1, QN{in.N, two_m});
   out.psi.assign((size_t)lay1.size, 0.0);
-  const int S = in.two_s;
+  const int S = in.two_s, M = two_m;
   int st2[2], sm2[2], ns2 = 0;
   for (const auto& b2 : lay2.blks) {
     const int Ja = L2.sub_qn(b2.lsub).s, Jb = R2.sub_qn(b2.rsub).s;
@@ -171,9 +175,9 @@ void expand_mps_su2(const SU2Mps& in, U1Mps& out) {
     chan_states(b2.i, st, sm, &ns);
     chan_states(b2.j, st2, sm2, &ns2);
     for (int ma = -Ja; ma <= Ja; ma += 2) {
-      const int mb = S - ma;
+      const int mb = M - ma;
       if (std::abs(mb) > Jb) continue;
-      const double c0 = cg2(Ja, ma, Jb, mb, S, S);
+      const double c0 = cg2(Ja, ma, Jb, mb, S, M);
       if (c0 == 0.0) continue;
       for (int u = 0; u < ns; ++u) {
         const int mx = ma - sm[u];

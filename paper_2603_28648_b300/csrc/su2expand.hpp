@@ -40,5 +40,8 @@ struct U1Mps {
 };
 // The state at M = S as a U(1) MPS with 2Sz = two_s.
 void expand_mps_su2(const SU2Mps& in, U1Mps& out);
+// the same with the two-site state coupled to the component 2M = two_m
+// (-two_s <= two_m <= two_s, two_m = two_s mod 2) instead of M = S
+void expand_mps_su2(const SU2Mps& in, U1Mps& out, int two_m);
 
 }  // namespace qd

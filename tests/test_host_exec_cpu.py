@@ -604,18 +604,23 @@ def test_orbital_rdm_by_centre_walk_matches_the_partial_trace(host_exec, tmp_pat
 
 
 @pytest.mark.parametrize("L,N,two_s,D,c", [(5, 5, 1, 8, 1), (5, 4, 2, 8, 2), (6, 6, 0, 8, 2)])
-def test_su2_orbital_rdm_of_the_m_equals_s_component(host_exec, tmp_path, L, N, two_s, D, c):
-    """SU(2): the same walk on the state's M = S expansion against the partial trace of the
-    determinant-expanded state; the SU(2) state and its sigma are unchanged afterwards."""
+def test_su2_orbital_rdm_is_the_multiplet_average(host_exec, tmp_path, L, N, two_s, D, c):
+    """SU(2): the same walk on the expansion of each of the state's 2S + 1 components,
+    averaged, against the oracle's multiplet average of the partial trace (components by S_-
+    from the determinant-expanded M = S state); the SU(2) state and its sigma are unchanged
+    afterwards."""
     from oracle.dmrgsu2 import DMRGSU2, MPSSU2
     from tests.test_oracle_dmrgsu2 import projector
     mps = MPSSU2.from_raw(q.random_mps_blocks(L, N, two_s, D, q.SYM_SU2, 5, c))
     h, V = q.make_integrals(L, 11)
     out = _run_su2(host_exec, tmp_path, mps, h, V, ["orbrdm"])
     R = out[:L * L * 256].reshape(L, L, 16, 16)
+    from oracle import orbital_qi as qi
     P, pairs, space = projector(mps)
     v = P @ np.array([mps.psi[a, b] for a, b in pairs])
-    assert np.abs(R - _orbital_rdm_ref(space.dets, v, L)).max() <= 1e-12
+    for i in range(L):
+        for j in range(i + 1, L):
+            assert np.abs(R[i, j] - qi.multiplet_rdm(L, N, two_s, v, i, j)).max() <= 1e-12
     rest = out[L * L * 256:]
     ps, sg = rest[:rest.size // 2], rest[rest.size // 2:]
     assert np.abs(ps - mps.psi_to_flat()).max() <= 1e-12

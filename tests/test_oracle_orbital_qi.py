@@ -176,3 +176,33 @@ def test_mutual_information_order_recovers_a_hidden_chain(seed):
     _, I = qi.mutual_information(rho, L)
     order, _ = qi.fiedler_order(I)
     assert list(order) in (list(perm), list(perm[::-1]))
+
+
+def _pair_spin_ops():
+    """S_z and S_+ of orbitals i and j together on the 16 states of the pair."""
+    cre = _local_ops()
+    ann = [a.T for a in cre]
+    sz = 0.5 * sum(cre[2 * o] @ ann[2 * o] - cre[2 * o + 1] @ ann[2 * o + 1] for o in (0, 1))
+    sp = sum(cre[2 * o] @ ann[2 * o + 1] for o in (0, 1))
+    return sz, sp
+
+
+@pytest.mark.parametrize("L,N,two_s,seed", [(4, 4, 0, 3), (5, 5, 1, 4), (5, 4, 2, 6), (5, 5, 3, 2)])
+def test_multiplet_average_is_spin_invariant(L, N, two_s, seed):
+    """The multiplet average of rho_ij commutes with the total spin of the pair (it is the
+    partial trace of a rotation-invariant operator); for a singlet it is the plain rho_ij, and
+    for S > 0 the M = S component alone does not commute with S_+ (so the average matters)."""
+    f, c = _ground(L, N, two_s, seed)
+    sz, sp = _pair_spin_ops()
+    broken = 0.0
+    for i, j in itertools.combinations(range(L), 2):
+        r = qi.multiplet_rdm(L, N, two_s, c, i, j)
+        assert abs(np.trace(r) - 1) <= 1e-12
+        assert np.abs(r @ sz - sz @ r).max() <= 1e-12
+        assert np.abs(r @ sp - sp @ r).max() <= 1e-12
+        r0 = qi.two_orbital_rdm(f.space.dets, c, i, j)
+        if two_s == 0:
+            assert np.abs(r - r0).max() <= 1e-13
+        broken = max(broken, np.abs(r0 @ sp - sp @ r0).max())
+    if two_s > 0:
+        assert broken > 1e-3
