@@ -513,6 +513,17 @@ int qcdmrg_orbital_gradient(int n, int ncore, int nact, const double* h, const d
                             const double* gamma2, double* grad);
 int qcdmrg_rotate_orbitals(int n, const double* kappa, const double* h, const double* V, double* U, double* h_out,
                            double* V_out);
+/*
+ * qcdmrg_orbital_hessian_diag (host only): hdiag (n*n, symmetric, zero
+ * diagonal) = d^2 E / d kappa_pq^2 at kappa = 0 for the one-pair rotation
+ * exp(kappa_pq (e_pq - e_qp)), E and the arguments as qcdmrg_orbital_gradient.
+ * Along that rotation E is a trigonometric polynomial of degree 4, so nine
+ * samples give the value exactly (no finite-difference error); O(n^3 + nact^4)
+ * per sample. With the gradient it gives the diagonal-Newton step
+ * kappa_pq = -grad_pq / hdiag_pq where hdiag_pq > 0. Errors: EINVAL.
+ */
+int qcdmrg_orbital_hessian_diag(int n, int ncore, int nact, const double* h, const double* V, const double* gamma1,
+                                const double* gamma2, double* hdiag);
 
 /*
  * Orbital entanglement for the chain ordering: the paper pre-optimises its

@@ -86,7 +86,7 @@ EXPORTS = [
     "qcdmrg_energy_grad", "qcdmrg_truncate_dbss", "qcdmrg_extrapolate", "qcdmrg_active_space",
     "qcdmrg_orbital_gradient", "qcdmrg_rotate_orbitals", "qcdmrg_orbital_rdm",
     "qcdmrg_orbital_entanglement", "qcdmrg_fiedler_order", "qcdmrg_select_configs", "qcdmrg_config_mps",
-    "qcdmrg_sweep_left", "qcdmrg_ordering_cost", "qcdmrg_refine_order",
+    "qcdmrg_sweep_left", "qcdmrg_ordering_cost", "qcdmrg_refine_order", "qcdmrg_orbital_hessian_diag",
 ]
 
 _lib = None
@@ -147,6 +147,7 @@ def load(path=None):
     lib.qcdmrg_active_space.argtypes = [ci, ci, ci, dp, dp, dp, dp, dp]
     lib.qcdmrg_orbital_gradient.argtypes = [ci, ci, ci, dp, dp, dp, dp, dp]
     lib.qcdmrg_rotate_orbitals.argtypes = [ci, dp, dp, dp, dp, dp, dp]
+    lib.qcdmrg_orbital_hessian_diag.argtypes = [ci, ci, ci, dp, dp, dp, dp, dp]
     lib.qcdmrg_orbital_rdm.argtypes = [P, dp]
     lib.qcdmrg_orbital_entanglement.argtypes = [ci, dp, dp, dp]
     lib.qcdmrg_fiedler_order.argtypes = [ci, dp, ip, dp]
@@ -449,6 +450,18 @@ def orbital_gradient(h, V, ncore, nact, gamma1, gamma2, lib=None):
     if rc != 0:
         raise QcdmrgError(rc, "qcdmrg_orbital_gradient: invalid arguments")
     return G
+
+
+def orbital_hessian_diag(h, V, ncore, nact, gamma1, gamma2, lib=None):
+    """qcdmrg_orbital_hessian_diag: d^2E/dkappa_pq^2 (n x n, symmetric, zero diagonal)."""
+    lib = lib or load()
+    h, V, g1, g2 = _f64(h), _f64(V), _f64(gamma1), _f64(gamma2)
+    n = h.shape[0]
+    H = np.zeros((n, n))
+    rc = lib.qcdmrg_orbital_hessian_diag(n, ncore, nact, _dptr(h), _dptr(V), _dptr(g1), _dptr(g2), _dptr(H))
+    if rc != 0:
+        raise QcdmrgError(rc, "qcdmrg_orbital_hessian_diag: invalid arguments")
+    return H
 
 
 def rotate_orbitals(kappa, h, V, lib=None):

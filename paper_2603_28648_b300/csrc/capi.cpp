@@ -937,6 +937,16 @@ int qcdmrg_orbital_gradient(int n, int ncore, int nact, const double* h, const d
   });
 }
 
+int qcdmrg_orbital_hessian_diag(int n, int ncore, int nact, const double* h, const double* V, const double* gamma1,
+                                const double* gamma2, double* hdiag) {
+  return host_guard([&]() {
+    if (n < 1 || ncore < 0 || nact < 1 || ncore + nact > n || !h || !V || !gamma1 || !gamma2 || !hdiag)
+      return QCDMRG_EINVAL;
+    orbital_hessian_diag(n, ncore, nact, h, V, gamma1, gamma2, hdiag);
+    return QCDMRG_OK;
+  });
+}
+
 int qcdmrg_rotate_orbitals(int n, const double* kappa, const double* h, const double* V, double* U, double* h_out,
                            double* V_out) {
   return host_guard([&]() {

@@ -174,4 +174,74 @@ void rotate_integrals(int n, const double* U, const double* h, const double* V, 
   for (size_t i = 0; i < n4; ++i) V_out[i] = A[i];
 }
 
+double fixed_density_energy(int n, int ncore, int nact, const double* h, const double* V, const double* gamma,
+                            const double* Gamma) {
+  double e_core = 0.0;
+  std::vector<double> ha((size_t)nact * nact), Va((size_t)nact * nact * nact * nact);
+  active_space(n, ncore, nact, h, V, &e_core, ha.data(), Va.data());
+  double e = e_core;
+  for (size_t k = 0; k < ha.size(); ++k) e += ha[k] * gamma[k];
+  double g = 0.0;
+  for (size_t k = 0; k < Va.size(); ++k) g += Va[k] * Gamma[k];
+  return e + 0.5 * g;
+}
+
+void orbital_hessian_diag(int n, int ncore, int nact, const double* h, const double* V, const double* gamma,
+                          const double* Gamma, double* H) {
+  // Along U(t) = exp(t (e_pq - e_qp)) only orbitals p and q mix,
+  //   phi_p' = cos t phi_p - sin t phi_q,  phi_q' = sin t phi_p + cos t phi_q,
+  // and the energy at fixed density matrices is a trigonometric polynomial of
+  // degree 4 in t (the two-electron integrals are quartic in U). Its values at
+  // t_j = 2 pi j / 9, j = 0..8, fix it exactly: a_k = (2/9) sum_j E_j cos(k t_j)
+  // and E''(0) = -sum_k k^2 a_k. Each sample rotates the integral slices with an
+  // index on p or q in place and puts them back from a copy afterwards.
+  const double PI = 3.14159265358979323846;
+  std::vector<double> hw(h, h + (size_t)n * n), Vw(V, V + (size_t)n * n * n * n);
+  std::fill(H, H + (size_t)n * n, 0.0);
+  std::vector<std::pair<size_t, double>> saved;
+  auto rot = [&](double* x, double* y, double c, double sn) {   // (x, y) <- (c x - s y, s x + c y)
+    const double a = *x, b = *y;
+    *x = c * a - sn * b;
+    *y = sn * a + c * b;
+  };
+  for (int p = 0; p < n; ++p)
+    for (int q = 0; q < p; ++q) {
+      // every entry with an index on p or q (the slices of each position; an
+      // entry in several slices is saved more than once, always with its
+      // original value)
+      saved.clear();
+      for (int o : {p, q})
+        for (int x = 0; x < n; ++x)
+          for (int y = 0; y < n; ++y)
+            for (int z = 0; z < n; ++z)
+              for (size_t at : {I4(n, o, x, y, z), I4(n, x, o, y, z), I4(n, x, y, o, z), I4(n, x, y, z, o)})
+                saved.emplace_back(at, Vw[at]);
+      std::vector<double> hsave(hw);
+      double a[5] = {0, 0, 0, 0, 0};
+      for (int jt = 0; jt < 9; ++jt) {
+        const double t = 2.0 * PI * jt / 9.0, c = std::cos(t), sn = std::sin(t);
+        for (int i = 0; i < n; ++i) rot(&hw[(size_t)p * n + i], &hw[(size_t)q * n + i], c, sn);
+        for (int i = 0; i < n; ++i) rot(&hw[(size_t)i * n + p], &hw[(size_t)i * n + q], c, sn);
+        for (int x = 0; x < n; ++x)
+          for (int y = 0; y < n; ++y)
+            for (int z = 0; z < n; ++z) rot(&Vw[I4(n, p, x, y, z)], &Vw[I4(n, q, x, y, z)], c, sn);
+        for (int x = 0; x < n; ++x)
+          for (int y = 0; y < n; ++y)
+            for (int z = 0; z < n; ++z) rot(&Vw[I4(n, x, p, y, z)], &Vw[I4(n, x, q, y, z)], c, sn);
+        for (int x = 0; x < n; ++x)
+          for (int y = 0; y < n; ++y)
+            for (int z = 0; z < n; ++z) rot(&Vw[I4(n, x, y, p, z)], &Vw[I4(n, x, y, q, z)], c, sn);
+        for (int x = 0; x < n; ++x)
+          for (int y = 0; y < n; ++y)
+            for (int z = 0; z < n; ++z) rot(&Vw[I4(n, x, y, z, p)], &Vw[I4(n, x, y, z, q)], c, sn);
+        const double e = fixed_density_energy(n, ncore, nact, hw.data(), Vw.data(), gamma, Gamma);
+        for (int k = 1; k <= 4; ++k) a[k] += (2.0 / 9.0) * e * std::cos(k * t);
+        hw = hsave;
+        for (const auto& sv : saved) Vw[sv.first] = sv.second;
+      }
+      const double d2 = -(a[1] + 4.0 * a[2] + 9.0 * a[3] + 16.0 * a[4]);
+      H[(size_t)p * n + q] = H[(size_t)q * n + p] = d2;
+    }
+}
+
 }  // namespace qd

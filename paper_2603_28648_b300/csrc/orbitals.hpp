@@ -13,5 +13,12 @@ void orbital_gradient(int n, int ncore, int nact, const double* h, const double*
                       const double* Gamma, double* G);
 void expm_antisym(int n, const double* kappa, double* U);
 void rotate_integrals(int n, const double* U, const double* h, const double* V, double* h_out, double* V_out);
+// E = e_core + sum h_act gamma + 1/2 sum V_act Gamma of the given orbitals
+double fixed_density_energy(int n, int ncore, int nact, const double* h, const double* V, const double* gamma,
+                            const double* Gamma);
+// H (n*n, symmetric, zero diagonal): H_pq = d^2 E / d kappa_pq^2 at kappa = 0
+// for the rotation exp(kappa_pq (e_pq - e_qp)), E at fixed density matrices
+void orbital_hessian_diag(int n, int ncore, int nact, const double* h, const double* V, const double* gamma,
+                          const double* Gamma, double* H);
 
 }  // namespace qd

@@ -108,3 +108,97 @@ def test_invalid_orbital_spaces_are_rejected():
     null = ctypes.cast(None, dp)
     assert lib.qcdmrg_rotate_orbitals(5, null, null, null, null, null, null) == -1
     assert lib.qcdmrg_active_space(5, 1, 2, null, null, null, null, null) == -1
+
+
+@pytest.mark.parametrize("ncore,nact,nel,two_s", [(2, 4, 4, 0), (1, 4, 3, 1), (0, 5, 4, 2)])
+def test_orbital_hessian_diagonal_equals_second_differences(ncore, nact, nel, two_s):
+    """The exact diagonal of the orbital Hessian (nine samples of the one-pair rotation)
+    against central second differences of the oracle's energy of rotated orbitals at fixed
+    FCI density matrices, for every pair type."""
+    import paper_2603_28648_b300 as qd
+    from oracle import casscf
+    lib = qd.load(ensure_built())
+    h, V, ncore, nact, g1, g2 = _setup(7, ncore, nact, nel, two_s)
+    H = qd.orbital_hessian_diag(h, V, ncore, nact, g1, g2, lib=lib)
+    n = h.shape[0]
+    assert np.abs(H - H.T).max() == 0 and not np.diag(H).any()
+    e0 = casscf.energy(h, V, ncore, nact, g1, g2)
+    step = 1e-3
+    for p in range(n):
+        for q in range(p):
+            k = np.zeros((n, n))
+            k[p, q], k[q, p] = step, -step
+            ep = casscf.energy_rotated(h, V, ncore, nact, g1, g2, k)
+            em = casscf.energy_rotated(h, V, ncore, nact, g1, g2, -k)
+            fd = (ep - 2 * e0 + em) / step ** 2
+            assert abs(H[p, q] - fd) <= 1e-5 * max(1.0, abs(fd))
+
+
+def test_diagonal_newton_step_lowers_the_energy():
+    """kappa_pq = -G_pq / H_pq on the pairs with H_pq > 0 (scaled to a small step) lowers the
+    energy at fixed density matrices by about its first-order amount."""
+    import paper_2603_28648_b300 as qd
+    from oracle import casscf
+    lib = qd.load(ensure_built())
+    h, V, ncore, nact, g1, g2 = _setup()
+    G = qd.orbital_gradient(h, V, ncore, nact, g1, g2, lib=lib)
+    H = qd.orbital_hessian_diag(h, V, ncore, nact, g1, g2, lib=lib)
+    k = np.where(H > 1e-8, -G / np.where(H > 1e-8, H, 1.0), 0.0)
+    k = 1e-3 * k / np.abs(k).max()
+    k = np.tril(k, -1)
+    k = k - k.T
+    e0 = casscf.energy(h, V, ncore, nact, g1, g2)
+    e1 = casscf.energy_rotated(h, V, ncore, nact, g1, g2, k)
+    pred = float(np.sum(np.tril(G, -1) * np.tril(k, -1)))
+    assert pred < 0 and e1 < e0
+    assert abs((e1 - e0) - pred) <= 0.05 * abs(pred)
+
+
+def _scf(newton, iters):
+    """Macro-iterations with the FCI oracle as the active-space solver (test only): the
+    library's active-space integrals, gradient, Hessian diagonal and rotation; a halving line
+    search on the re-solved energy in both variants."""
+    import paper_2603_28648_b300 as qd
+    from oracle.fci import FCI
+    lib = qd.load(ensure_built())
+    n, nc, na, N = 8, 2, 4, 4
+    h, V = q.make_integrals(n, 12)
+
+    def solve(h, V):
+        e_core, ha, Va = qd.active_space(h, V, nc, na, lib=lib)
+        f = FCI(ha, Va, N, 0, e_core)
+        e, c = f.ground_state(two_s=0)
+        g1, g2 = f.rdm12(c)
+        return e, g1, g2
+
+    e, g1, g2 = solve(h, V)
+    step = 0.05
+    for _ in range(iters):
+        G = qd.orbital_gradient(h, V, nc, na, g1, g2, lib=lib)
+        if newton:
+            H = qd.orbital_hessian_diag(h, V, nc, na, g1, g2, lib=lib)
+            d = -G / np.maximum(np.abs(H), 1e-2)
+            d = np.tril(d, -1)
+            d = d - d.T
+            d *= min(1.0, 0.5 / np.abs(d).max())
+            lam = 1.0
+        else:
+            d, lam = -G, step
+        while lam > 1e-8:
+            _, h2, V2 = qd.rotate_orbitals(lam * d, h, V, lib=lib)
+            e2, g12, g22 = solve(h2, V2)
+            if e2 < e:
+                h, V, e, g1, g2 = h2, V2, e2, g12, g22
+                step = lam * 1.5
+                break
+            lam *= 0.5
+    return e
+
+
+def test_diagonal_newton_macro_iterations_beat_steepest_descent():
+    """DMRG-SCF-shaped macro-iterations (8 orbitals, 2 core, CAS(4,4)) from random orbitals:
+    six diagonal-Newton steps (step capped at 0.5 rad, |H| floored at 1e-2) end well below six
+    steepest-descent steps (measured -93.04 against -84.98 Eh)."""
+    e_sd = _scf(False, 6)
+    e_nt = _scf(True, 6)
+    assert e_nt < e_sd - 1.0
