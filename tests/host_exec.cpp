@@ -23,6 +23,8 @@
 //                                                          imported centre, then sweeps)
 //        host_exec in.bin out.bin sweeprdm D nsweeps tol  (sweeps, then the two-orbital
 //                                                          density matrices)
+//        host_exec in.bin out.bin sweepgamma D nsweeps tol (sweeps, then the 2-RDM by the
+//                                                          walk of the centre)
 //   in : int64 L, N, two_sz, center, nsec_len (= L+1), sec_len, data_len;
 //        h (L*L), V (L^4) doubles; bond_nsec, bond_sec int32; data doubles
 //   out: sigma of the FP64 task lists, then sigma of the tiled work items; or
@@ -439,6 +441,31 @@ int main(int argc, char** argv) {
       if (!o2) throw std::runtime_error("cannot open output");
       std::fwrite(energies.data(), 8, energies.size(), o2);
       std::fclose(o2);
+      return 0;
+    }
+    if (argc >= 7 && std::string(argv[3]) == "sweepgamma") {
+      // nsw sweeps (fixed D), then the 2-RDM by the walk; out: the last energy, then Gamma
+      const int D = std::atoi(argv[4]), nsw = std::atoi(argv[5]);
+      DavOpts o;
+      o.tol = std::atof(argv[6]);
+      while (E.center > 0) E.truncate_move(1 << 30, -1, 1e-28);
+      double e = 0.0;
+      for (int sw = 0; sw < nsw; ++sw) {
+        for (int l = 0; l < L - 2; ++l) {
+          e = E.davidson(o).energy;
+          E.truncate_move(D, +1, 0.0);
+        }
+        for (int l = L - 2; l > 0; --l) {
+          e = E.davidson(o).energy;
+          E.truncate_move(D, -1, 0.0);
+        }
+      }
+      const std::vector<double> g = E.rdm2_sweep();
+      FILE* o11 = std::fopen(argv[2], "wb");
+      if (!o11) throw std::runtime_error("cannot open output");
+      std::fwrite(&e, 8, 1, o11);
+      std::fwrite(g.data(), 8, g.size(), o11);
+      std::fclose(o11);
       return 0;
     }
     if (argc >= 7 && std::string(argv[3]) == "sweeprdm") {

@@ -810,3 +810,54 @@ def test_degenerate_fillings_and_minimal_chains_su2(host_exec, tmp_path, L, N, t
     scale = max(np.linalg.norm(ref), np.linalg.norm(mps.psi_to_flat()))
     assert np.linalg.norm(out[:n] - ref) <= 1e-13 * scale
     assert np.linalg.norm(out[n:] - ref) <= 1e-13 * scale
+
+
+@pytest.mark.parametrize("sym", ["u1", "su2"])
+def test_dmrg_scf_macro_iterations_match_the_fci_pipeline(host_exec, tmp_path, sym):
+    """Two DMRG-SCF macro-iterations (7 orbitals, 1 core, CAS(4,5), S = 0) with the library's
+    own DMRG as the active-space solver (host-executed sweeps at a bond dimension that
+    truncates nothing, then Gamma by the walk and gamma = sum_r Gamma_pqrr / (N - 1)), and with
+    the FCI oracle as the solver (the lowest 2Sz = 0 state for U(1), the lowest singlet for
+    SU(2)): at each macro-iteration the energies agree to 1e-8, the
+    density matrices to 1e-7 and the library's orbital gradients from either to 1e-6; the
+    steepest-descent rotation between them is the library's."""
+    import paper_2603_28648_b300 as qd
+    from oracle.fci import FCI
+    from tests._lib import ensure_built
+    lib = qd.load(ensure_built())
+    n, nc, na, N = 7, 1, 5, 4
+    h, V = q.make_integrals(n, 21)
+    for it in range(2):
+        e_core, ha, Va = qd.active_space(h, V, nc, na, lib=lib)
+        if sym == "u1":
+            from oracle.mpsu1 import MPSU1
+            m = MPSU1.from_raw(q.random_mps_blocks(na, N, 0, 16, q.SYM_U1, 3 + it, 1))
+            fin = str(tmp_path / "scf_in.bin")
+            _write(fin, m, ha, Va)
+            env = dict(os.environ)
+            D = 16
+        else:
+            from oracle.dmrgsu2 import MPSSU2
+            m = MPSSU2.from_raw(q.random_mps_blocks(na, N, 0, 10, q.SYM_SU2, 3 + it, 1))
+            fin = str(tmp_path / "scf_in.bin")
+            _write_su2(fin, m, ha, Va)
+            env = dict(os.environ, HOST_EXEC_SU2="1")
+            D = 10
+        fout = str(tmp_path / "scf_out.bin")
+        r = subprocess.run([host_exec, fin, fout, "sweepgamma", str(D), "4", "1e-11"], capture_output=True,
+                           text=True, timeout=600, env=env)
+        assert r.returncode == 0, r.stderr
+        out = np.fromfile(fout, "<f8")
+        e_dmrg, G2 = out[0] + e_core, out[1:].reshape(na, na, na, na)
+        g1 = np.einsum("pqrr->pq", G2) / (N - 1)
+        f = FCI(ha, Va, N, 0, e_core)
+        # U(1) fixes 2Sz = 0 only (its ground state may be a triplet's M = 0 component);
+        # SU(2) fixes S = 0
+        e_fci, c = f.ground_state(two_s=0 if sym == "su2" else None)
+        f1, f2 = f.rdm12(c)
+        assert abs(e_dmrg - e_fci) <= 1e-8
+        assert np.abs(g1 - f1).max() <= 1e-7 and np.abs(G2 - f2).max() <= 1e-7
+        G = qd.orbital_gradient(h, V, nc, na, g1, G2, lib=lib)
+        Gf = qd.orbital_gradient(h, V, nc, na, f1, f2, lib=lib)
+        assert np.abs(G - Gf).max() <= 1e-6 * max(1.0, np.abs(Gf).max())
+        _, h, V = qd.rotate_orbitals(-0.01 * G, h, V, lib=lib)
