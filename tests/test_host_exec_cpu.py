@@ -603,7 +603,7 @@ def test_orbital_rdm_by_centre_walk_matches_the_partial_trace(host_exec, tmp_pat
     assert np.array_equal(rest[:rest.size // 2], m.psi_to_flat())
 
 
-@pytest.mark.parametrize("L,N,two_s,D,c", [(5, 5, 1, 8, 1), (5, 4, 2, 8, 2), (6, 6, 0, 8, 2)])
+@pytest.mark.parametrize("L,N,two_s,D,c", [(5, 5, 1, 8, 1), (5, 4, 2, 8, 2), (6, 6, 0, 8, 2), (5, 5, 3, 6, 2)])
 def test_su2_orbital_rdm_is_the_multiplet_average(host_exec, tmp_path, L, N, two_s, D, c):
     """SU(2): the same walk on the expansion of each of the state's 2S + 1 components,
     averaged, against the oracle's multiplet average of the partial trace (components by S_-
