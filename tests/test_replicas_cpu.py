@@ -48,3 +48,22 @@ def test_replica_throughput_counts_every_replica():
     import bench
     assert bench.replica_throughput(2e12, 0.5, 1) == pytest.approx(4.0)
     assert bench.replica_throughput(2e12, 0.5, 4) == pytest.approx(16.0)
+
+
+def test_bench_defaults_and_modes_parse(monkeypatch):
+    """The default bench line keeps N = 1, the SU(2) CAS(54,36) shape at D = 2048 and the switch one
+    cut past the centre; U(1) and the adjoint keep normal pairs everywhere; the opt-in modes
+    parse without touching the default."""
+    import sys
+    import bench
+    monkeypatch.setattr(sys, "argv", ["bench.py"])
+    a = bench.parse()
+    assert (a.gpus, a.symmetry, a.L, a.N, a.D, a.pair_switch) == (1, "su2", 36, 54, 2048, 19)
+    assert a.warmup >= 3 and not a.qi and a.warm_start == 0 and a.scf_step == "steepest"
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--symmetry", "u1"])
+    assert bench.parse().pair_switch == 0
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--adjoint"])
+    assert bench.parse().pair_switch == 0
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--qi", "--warm-start", "64", "--scf", "--scf-step", "newton"])
+    a = bench.parse()
+    assert a.qi and a.warm_start == 64 and a.scf and a.scf_step == "newton"
