@@ -105,3 +105,25 @@ def test_invalid_configurations_are_rejected():
                                nsec.ctypes.data_as(ip), sec.ctypes.data_as(ip), sec.size, data.ctypes.data_as(dp),
                                0, None, None)
     assert rc == -1
+
+
+def test_selection_at_the_cas54_36_shape():
+    """L = 36, N = 54, S = 0: asking for every candidate returns the 1 + 2 * 27 * 9 +
+    2 * C(27,2) * C(9,2) + (27 * 9)^2 = 84,808 determinants within two electrons of the aufbau
+    reference, sorted by energy, all distinct; the lowest is the reference (at these integrals)
+    with the closed-shell energy 2 sum_i h_ii + sum_ij (2 (ii|jj) - (ij|ji)) over its orbitals."""
+    import math
+    import paper_2603_28648_b300 as qd
+    lib = qd.load(ensure_built())
+    L, N = 36, 54
+    h, V = q.make_integrals(L, q.integrals.BASE_SEED + 2)
+    steps, en = qd.select_configs(qd.U1, h, V, N, 0, 100000, lib=lib)
+    nocc, nvir = 27, 9
+    total = 1 + 2 * nocc * nvir + 2 * math.comb(nocc, 2) * math.comb(nvir, 2) + (nocc * nvir) ** 2
+    assert len(steps) == total == 84808
+    assert np.all(np.diff(en) >= 0)
+    assert len({s.tobytes() for s in steps}) == total
+    occ = [p for p in range(L) if steps[0][p] == 3]
+    assert len(occ) == nocc and not np.any((steps[0] == 1) | (steps[0] == 2))
+    e = 2 * sum(h[i, i] for i in occ) + sum(2 * V[i, i, j, j] - V[i, j, j, i] for i in occ for j in occ)
+    assert abs(en[0] - e) <= 1e-9 * abs(e)
