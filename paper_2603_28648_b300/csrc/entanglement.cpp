@@ -170,7 +170,9 @@ int refine_order(int L, const double* mutual, double eta, int* order, int max_pa
   std::vector<int> pos(L);
   for (int k = 0; k < L; ++k) pos[order[k]] = k;
   auto M = [&](int i, int j) { return mutual[(size_t)i * L + j]; };
-  auto d = [&](int x) { return std::pow(std::abs(x), eta); };
+  std::vector<double> dpow(L);   // |x|^eta for the distances 0..L-1
+  for (int x = 0; x < L; ++x) dpow[x] = std::pow((double)x, eta);
+  auto d = [&](int x) { return dpow[std::abs(x)]; };
   int made = 0;
   while (made < max_passes) {
     double best = 0.0;
