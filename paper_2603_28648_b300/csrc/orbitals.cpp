@@ -176,13 +176,28 @@ void rotate_integrals(int n, const double* U, const double* h, const double* V, 
 
 double fixed_density_energy(int n, int ncore, int nact, const double* h, const double* V, const double* gamma,
                             const double* Gamma) {
-  double e_core = 0.0;
-  std::vector<double> ha((size_t)nact * nact), Va((size_t)nact * nact * nact * nact);
-  active_space(n, ncore, nact, h, V, &e_core, ha.data(), Va.data());
-  double e = e_core;
-  for (size_t k = 0; k < ha.size(); ++k) e += ha[k] * gamma[k];
+  // the frozen-core energy and the active terms of active_space, read straight
+  // from V (no active-space copy)
+  double e = 0.0;
+  for (int c = 0; c < ncore; ++c) {
+    e += 2.0 * h[(size_t)c * n + c];
+    for (int d = 0; d < ncore; ++d) e += 2.0 * V[I4(n, c, c, d, d)] - V[I4(n, c, d, d, c)];
+  }
+  const int a0 = ncore;
+  for (int t = 0; t < nact; ++t)
+    for (int u = 0; u < nact; ++u) {
+      double hv = h[(size_t)(a0 + t) * n + a0 + u];
+      for (int c = 0; c < ncore; ++c) hv += 2.0 * V[I4(n, a0 + t, a0 + u, c, c)] - V[I4(n, a0 + t, c, c, a0 + u)];
+      e += hv * gamma[(size_t)t * nact + u];
+    }
   double g = 0.0;
-  for (size_t k = 0; k < Va.size(); ++k) g += Va[k] * Gamma[k];
+  for (int t = 0; t < nact; ++t)
+    for (int u = 0; u < nact; ++u)
+      for (int v = 0; v < nact; ++v) {
+        const double* row = V + I4(n, a0 + t, a0 + u, a0 + v, a0);
+        const double* G = Gamma + (((size_t)t * nact + u) * nact + v) * nact;
+        for (int w = 0; w < nact; ++w) g += row[w] * G[w];
+      }
   return e + 0.5 * g;
 }
 
